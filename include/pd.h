@@ -1,0 +1,192 @@
+/*
+ * pd.h — C ABI of the GB300 pixel-detector correction and photon-finding
+ * library (libpd.so).
+ *
+ * The library runs, per frame, the classical integrating-pixel-detector chain
+ * that Blaj, Chang and Kenney, "Ultrafast Processing of Pixel Detector Data
+ * with Machine Learning Frameworks" (AIP Conf. Proc. 2054, 060077, 2019)
+ * recast as fixed-weight tensor models:
+ *
+ *   raw -> dark (pedestal) subtraction           (Fig. b, "Dark and Gain")
+ *       -> common-mode removal per unit           (Fig. c, "Common Mode")
+ *       -> gain correction                        (Fig. b)
+ *       -> noise zeroing, local maximum,          (Fig. e, "Photon Charge
+ *          3x3 charge sum, photon count              Summing")
+ *       -> centre-of-mass subpixel offset         (Fig. f, "Photon Subpixel
+ *                                                   Resolution")
+ *       -> sparse hit list, photon-count map,     ("Summarization")
+ *          pixel and hit energy histograms
+ *
+ * Every step runs in hand-written sm_103a CUDA kernels; there is no CPU
+ * fallback.  The arithmetic is FP32 with every operation rounded to nearest
+ * in a fixed order, so results are reproducible bit for bit.
+ *
+ * Conventions common to all entry points
+ *   - Return value: PD_OK (0) or one of the PD_E* codes below.  No C++
+ *     exception crosses this boundary.  pd_strerror() names a code and
+ *     pd_last_error() returns a thread-local message for the last failure.
+ *   - "device" pointers are CUDA global-memory addresses on the current
+ *     device; "host" pointers are ordinary (optionally page-locked) memory.
+ *   - stream arguments are a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Calls that take a stream are asynchronous unless
+ *     their comment says otherwise.
+ *   - One pd_ctx may be used from one host thread / stream at a time.
+ *
+ * Frame layout (paper: rank-4 minibatch N x H x W x 1, section "Dark and
+ * Gain"): raw frames are uint16 [n_frames][n_modules][rows][cols], row-major
+ * and contiguous.  A module is one contiguous sensor; the 3x3 stencil never
+ * crosses a module edge.  A common-mode unit is a unit_rows x unit_cols
+ * rectangle; units tile every module (row units: unit_rows = 1; banks:
+ * unit_rows x unit_cols sub-arrays).
+ */
+#ifndef PD_H
+#define PD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define PD_OK 0
+#define PD_EINVAL 1     /* invalid argument or inconsistent geometry        */
+#define PD_EALIGN 2     /* pointer or size not aligned as required          */
+#define PD_ENOMEM 3     /* a device or host allocation failed               */
+#define PD_EOVERFLOW 4  /* more hits than hit_capacity (count still exact)  */
+#define PD_ETIMEDOUT 5  /* a bounded device-side or host-side wait gave up  */
+#define PD_ECUDA 6      /* a CUDA runtime call failed                       */
+#define PD_ENOTSUP 7    /* valid request this build does not support        */
+#define PD_EBUSY 8      /* admission refused: no slot or memory budget free */
+
+/* ---- common-mode estimators (paper Fig. c and its text) --------------- */
+#define PD_CM_MEDIAN 0 /* lower median of d = raw - pedestal over d < cut  */
+#define PD_CM_NONE 1   /* no common-mode correction (cm = 0)               */
+
+/* ---- hit flags -------------------------------------------------------- */
+#define PD_HIT_EDGE 1u      /* seed pixel lies on its module's border       */
+#define PD_HIT_SATURATED 2u /* rint(E / photon_kev) exceeded 255 and clipped */
+
+/* Detector geometry.  Requirements (PD_EINVAL otherwise): all sizes > 0,
+ * rows % unit_rows == 0, cols % unit_cols == 0, and the pixel count of one
+ * frame, n_modules * rows * cols, a multiple of 8 (so every frame starts on
+ * a 16-byte boundary). */
+typedef struct {
+    uint32_t n_modules;
+    uint32_t rows, cols;           /* pixels of one module                  */
+    uint32_t unit_rows, unit_cols; /* common-mode unit                      */
+    uint32_t cm_mode;              /* PD_CM_MEDIAN or PD_CM_NONE            */
+} pd_geometry;
+
+/* Thresholds and summary binning.  The paper exposes two noise thresholds
+ * (section "Accuracy", Figs. c and e); the common-mode cut here is in ADU
+ * because the correction is taken before gain.  Requirements: 0 <=
+ * zero_thr_kev <= seed_thr_kev, photon_kev > 0, hist_bin_kev > 0,
+ * 1 <= hist_bins <= PD_MAX_HIST_BINS, all finite. */
+typedef struct {
+    float cm_cut_adu;       /* pixel enters the common-mode set iff d < cut  */
+    float zero_thr_kev;     /* s = e > zero_thr ? e : 0      (Fig. e)        */
+    float seed_thr_kev;     /* a seed needs e > seed_thr                     */
+    float photon_kev;       /* count n = rint(E / photon_kev)                */
+    uint32_t cm_min_count;  /* min pixels below cut; 0 = ceil(sqrt(unit px)) */
+    float hist_lo_kev;      /* histogram bin b covers lo + [b, b+1) * width  */
+    float hist_bin_kev;     /*   (computed as floor((v - lo) * (1/width)))   */
+    uint32_t hist_bins;     /* end bins are clamped                          */
+} pd_thresholds;
+
+#define PD_MAX_HIST_BINS 4096u
+
+/* One photon hit (24 bytes).  pixel = module*rows*cols + row*cols + col of
+ * the seed; dx, dy are the charge centre of mass in pixel pitches relative
+ * to the seed pixel centre (Fig. f), so the position is
+ * (col + 0.5 + dx, row + 0.5 + dy) in the module. */
+typedef struct {
+    uint32_t frame;      /* frame_base + index of the frame in the call      */
+    uint32_t pixel;
+    float energy_kev;    /* E: 3x3 sum of the zeroed signal                  */
+    float dx, dy;
+    uint8_t count;       /* n = clamp(rint(E / photon_kev), 0, 255), >= 1    */
+    uint8_t npix;        /* pixels of the 3x3 with signal > 0                */
+    uint16_t flags;      /* PD_HIT_* bits                                    */
+} pd_hit;
+
+/* Per-call outputs of pd_process.  All pointers are device memory owned by
+ * the caller.  hits / n_hits are required; the others may be NULL. */
+typedef struct {
+    pd_hit* hits;          /* hit_capacity records; order is unspecified     */
+    uint32_t hit_capacity;
+    uint32_t* n_hits;      /* 1 x u32: set to the call's true hit count      */
+    float* corrected;      /* [n_frames][pixels] e (keV) or NULL             */
+    float* cm;             /* [n_frames][units]  common mode (ADU) or NULL   */
+} pd_outputs;
+
+typedef struct pd_ctx pd_ctx;
+
+/* Sizes derived from a context. */
+typedef struct {
+    uint32_t pixels_per_frame;
+    uint32_t units_per_frame;
+    uint32_t unit_pixels;
+    uint32_t cm_min_count;   /* resolved value (0 replaced by the default) */
+    uint32_t hist_bins;
+    uint32_t masked_pixels;  /* pixels whose gain was <= 0 or not finite   */
+} pd_info;
+
+/* pd_create — validate the geometry and thresholds, copy the pedestal and
+ * gain maps (host float32 [n_modules][rows][cols]; pedestal in ADU, gain in
+ * ADU/keV) to the device, and compute inv_gain = 1.0f / gain there-from on
+ * the host (round to nearest; gain <= 0 or non-finite -> inv_gain = 0, the
+ * pixel is masked).  Allocates the context's device state: maps, photon
+ * count map (u32 per pixel) and two u64 histograms, all zeroed.  The device
+ * is the current CUDA device.  On failure *out is NULL. */
+int pd_create(const pd_geometry* geometry, const float* pedestal_host,
+              const float* gain_host, const pd_thresholds* thresholds,
+              pd_ctx** out);
+
+int pd_query(const pd_ctx* ctx, pd_info* info);
+
+/* pd_process — run the whole chain on n_frames device-resident raw frames
+ * (16-byte aligned) and enqueue it on `stream`.  Writes the hit list and
+ * *n_hits (zeroed by the call itself), and adds the frames' contributions
+ * to the context's count map and histograms.  When more than hit_capacity
+ * hits occur, the surplus records are dropped and *n_hits still holds the
+ * true count (the caller compares after synchronising).  n_frames == 0 only
+ * zeroes *n_hits.  Asynchronous: errors of the launch itself are returned,
+ * device results are valid once the stream reaches this point. */
+int pd_process(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frames,
+               uint32_t frame_base, const pd_outputs* out, void* stream);
+
+/* pd_process_host — the same chain on host-resident frames.  Copies the
+ * frames to the device in chunks (pipelined on two internal streams, so
+ * page-locked host memory gives full link speed), processes them, and
+ * copies the hit list and its count back.  Synchronous: returns after the
+ * hits are in hits_host.  Returns PD_EOVERFLOW if more than hit_capacity
+ * hits occurred (*n_hits_host is then the true count, hits_host holds the
+ * first hit_capacity records in unspecified order). */
+int pd_process_host(pd_ctx* ctx, const uint16_t* frames_host,
+                    uint32_t n_frames, uint32_t frame_base, pd_hit* hits_host,
+                    uint32_t hit_capacity, uint32_t* n_hits_host);
+
+/* pd_get_summary — copy the accumulated summaries to host buffers (any may
+ * be NULL): count_map u32 [pixels], hist_pix u64 [hist_bins] (every
+ * corrected pixel e), hist_hit u64 [hist_bins] (the 3x3 energy E of every
+ * seed).  Synchronous on `stream`. */
+int pd_get_summary(pd_ctx* ctx, uint32_t* count_map_host,
+                   uint64_t* hist_pix_host, uint64_t* hist_hit_host,
+                   void* stream);
+
+/* pd_reset_summary — zero the count map and histograms (async on stream). */
+int pd_reset_summary(pd_ctx* ctx, void* stream);
+
+/* pd_destroy — free the context's device state (NULL is a no-op).  Waits
+ * for the device to finish work that may use it. */
+void pd_destroy(pd_ctx* ctx);
+
+const char* pd_strerror(int code);
+const char* pd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PD_H */

@@ -1,0 +1,295 @@
+/*
+ * pd_oracle.c — CPU oracle of the pixel-detector correction chain.
+ *
+ * TEST INFRASTRUCTURE.  This file defines what the chain computes; it is a
+ * plain, slow, single-threaded restatement of the method, step by step, in
+ * the paper's order.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load it.  It shares no code, header or constant with
+ * the CUDA library: its structs below mirror the public layout field by
+ * field but are declared here.
+ *
+ * Paper: G. Blaj, C.-E. Chang, C. J. Kenney, "Ultrafast Processing of Pixel
+ * Detector Data with Machine Learning Frameworks", AIP Conf. Proc. 2054,
+ * 060077 (2019).  Section names below refer to it.
+ *
+ * Arithmetic: IEEE binary32, round to nearest, one rounding per written
+ * operation (build with -ffp-contract=off, never -ffast-math).  For each
+ * frame, each module in order:
+ *
+ *  1. Dark: d = (float)raw - pedestal                 (Fig. b, "Frames0")
+ *  2. Common mode, per unit u (section "Common Mode", Fig. c): the set of
+ *     pixels of u whose d < cm_cut ("pixels without signal" are segmented
+ *     by a threshold).  With n pixels in the set and n >= n_min, cm_u is
+ *     the element of rank floor((n-1)/2) of the set sorted ascending (the
+ *     lower median; the paper's figure averages the set, the median is the
+ *     robust estimator this library uses); otherwise cm_u = 0, which plays
+ *     the role of the figure's sqrt(HW) guard against estimating from too
+ *     few pixels.  n_min defaults to ceil(sqrt(unit pixels)).
+ *     Ascending order is IEEE order refined so -0 sorts below +0.
+ *  3. c = d - cm_u
+ *  4. Gain: e = c * inv_gain with inv_gain = 1.0f / gain computed once
+ *     (Fig. b divides by the gain map; the reciprocal is taken once per
+ *     pixel); gain <= 0 or non-finite masks the pixel (inv_gain = 0).
+ *  5. Noise zeroing (Fig. e "Signal? / Signal"): s = e > zero_thr ? e : 0.
+ *  6. Seed (charge goes to the pixel with the highest signal, section
+ *     "Photon Charge Summing"): p is a seed iff s_p > seed_thr and, for each
+ *     of its 8 neighbours q inside the module, s_p > s_q when q comes before
+ *     p in the module's raster order and s_p >= s_q when q comes after it.
+ *     Neighbours outside the module do not exist (zero padding; since
+ *     s_p > 0 they never block a seed).
+ *  7. Charge sum: E = sum of s over the 3x3 around the seed (out-of-module
+ *     terms are 0), accumulated row-major from 0.0f (Fig. e "Frames3").
+ *     Photon count (same section, high-flux paragraph): n = rint(E /
+ *     photon_kev), ties to even, clipped to [0, 255].  A hit is emitted iff
+ *     n >= 1.
+ *  8. Centroid (section "Photon Subpixel Resolution", Fig. f): with column
+ *     offsets ox and row offsets oy in {-1, 0, 1},
+ *     Mx = sum s_q * ox_q, My = sum s_q * oy_q in the same row-major order,
+ *     dx = Mx / E, dy = My / E, in pixel pitches from the seed centre.
+ *  9. Summaries (section "Summarization"): count_map[seed] += n for every
+ *     hit; hist_pix[bin(e)] += 1 for every pixel; hist_hit[bin(E)] += 1 for
+ *     every seed, where bin(v) = floor((v - lo) * inv_w), inv_w = 1.0f /
+ *     width, clipped to [0, bins-1] (NaN -> 0).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    uint32_t n_modules, rows, cols, unit_rows, unit_cols, cm_mode;
+} og_geometry;
+
+typedef struct {
+    float cm_cut_adu, zero_thr_kev, seed_thr_kev, photon_kev;
+    uint32_t cm_min_count;
+    float hist_lo_kev, hist_bin_kev;
+    uint32_t hist_bins;
+} og_thresholds;
+
+typedef struct {
+    uint32_t frame, pixel;
+    float energy_kev, dx, dy;
+    uint8_t count, npix;
+    uint16_t flags;
+} og_hit;
+
+enum { OG_CM_MEDIAN = 0, OG_CM_NONE = 1 };
+enum { OG_EDGE = 1, OG_SATURATED = 2 };
+
+/* The 32-bit pattern of a float mapped so that unsigned comparison of the
+ * keys is the ascending IEEE order with -0 below +0. */
+static uint32_t order_key(float v) {
+    uint32_t b;
+    memcpy(&b, &v, 4);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+static int cmp_float(const void* a, const void* b) {
+    uint32_t ka = order_key(*(const float*)a), kb = order_key(*(const float*)b);
+    return (ka > kb) - (ka < kb);
+}
+
+/* smallest k with k*k >= n */
+static uint32_t ceil_sqrt(uint32_t n) {
+    uint32_t k = 0;
+    while ((uint64_t)k * k < n) k++;
+    return k;
+}
+
+uint32_t oracle_default_min_count(uint32_t unit_pixels) {
+    return ceil_sqrt(unit_pixels);
+}
+
+static uint32_t bin_of(float v, float lo, float inv_w, uint32_t bins) {
+    float t = (v - lo) * inv_w;
+    if (!(t >= 0.0f)) return 0;
+    if (t >= (float)bins) return bins - 1;
+    return (uint32_t)t; /* truncation == floor for t >= 0 */
+}
+
+/* Lower median of the values of `set` (n of them), sorted in place. */
+float oracle_lower_median(float* set, uint32_t n) {
+    qsort(set, n, sizeof(float), cmp_float);
+    return set[(n - 1) / 2];
+}
+
+int oracle_check(const og_geometry* g, const og_thresholds* t) {
+    if (!g || !t) return 1;
+    if (!g->n_modules || !g->rows || !g->cols || !g->unit_rows ||
+        !g->unit_cols)
+        return 1;
+    if (g->rows % g->unit_rows || g->cols % g->unit_cols) return 1;
+    if (g->cm_mode != OG_CM_MEDIAN && g->cm_mode != OG_CM_NONE) return 1;
+    if (!(t->zero_thr_kev >= 0.0f) || !(t->seed_thr_kev >= t->zero_thr_kev))
+        return 1;
+    if (!(t->photon_kev > 0.0f) || !(t->hist_bin_kev > 0.0f)) return 1;
+    if (!isfinite(t->seed_thr_kev) || !isfinite(t->photon_kev) ||
+        !isfinite(t->hist_lo_kev) || !isfinite(t->hist_bin_kev) ||
+        isnan(t->cm_cut_adu))
+        return 1;
+    if (t->hist_bins < 1 || t->hist_bins > 4096) return 1;
+    return 0;
+}
+
+/*
+ * oracle_process — run the chain on n_frames raw frames.
+ *   ped, gain:  float [n_modules][rows][cols] (ADU, ADU/keV)
+ *   raw:        uint16 [n_frames][n_modules][rows][cols]
+ *   hits:       up to cap records, written in (frame, module, row, col)
+ *               order; *n_hits receives the true number of hits
+ *   count_map:  u32 [pixels]   (accumulated, not cleared)
+ *   hist_pix, hist_hit: u64 [hist_bins] (accumulated, not cleared)
+ *   corrected:  float [n_frames][pixels] e values, or NULL
+ *   cm_out:     float [n_frames][units] common mode, or NULL
+ *   n_seeds:    receives the number of seeds (hits plus seeds with n = 0),
+ *               or NULL
+ * Returns 0, or 1 on invalid input.
+ */
+int oracle_process(const og_geometry* g, const og_thresholds* t,
+                   const float* ped, const float* gain, const uint16_t* raw,
+                   uint32_t n_frames, uint32_t frame_base, og_hit* hits,
+                   uint32_t cap, uint32_t* n_hits, uint32_t* count_map,
+                   uint64_t* hist_pix, uint64_t* hist_hit, float* corrected,
+                   float* cm_out, uint64_t* n_seeds) {
+    if (oracle_check(g, t)) return 1;
+    const uint32_t R = g->rows, C = g->cols;
+    const size_t mpx = (size_t)R * C;
+    const size_t fpx = mpx * g->n_modules;
+    const uint32_t urows = R / g->unit_rows, ucols = C / g->unit_cols;
+    const uint32_t upm = urows * ucols;
+    const uint32_t unit_px = g->unit_rows * g->unit_cols;
+    const uint32_t n_min =
+        t->cm_min_count ? t->cm_min_count : ceil_sqrt(unit_px);
+    const float inv_w = 1.0f / t->hist_bin_kev;
+
+    float* inv_gain = (float*)malloc(fpx * sizeof(float));
+    float* d = (float*)malloc(mpx * sizeof(float));
+    float* e = (float*)malloc(mpx * sizeof(float));
+    float* s = (float*)malloc(mpx * sizeof(float));
+    float* set = (float*)malloc((size_t)unit_px * sizeof(float));
+    float* cmu = (float*)malloc((size_t)upm * sizeof(float));
+    if (!inv_gain || !d || !e || !s || !set || !cmu) {
+        free(inv_gain); free(d); free(e); free(s); free(set); free(cmu);
+        return 1;
+    }
+    for (size_t p = 0; p < fpx; p++) {
+        const float gp = gain[p];
+        inv_gain[p] = (gp > 0.0f && isfinite(gp)) ? 1.0f / gp : 0.0f;
+    }
+
+    uint32_t nh = 0;
+    uint64_t ns = 0;
+    for (uint32_t f = 0; f < n_frames; f++) {
+        for (uint32_t m = 0; m < g->n_modules; m++) {
+            const size_t base = m * mpx;
+            const uint16_t* rw = raw + (size_t)f * fpx + base;
+            /* 1. dark */
+            for (size_t p = 0; p < mpx; p++) d[p] = (float)rw[p] - ped[base + p];
+            /* 2. common mode per unit */
+            for (uint32_t ur = 0; ur < urows; ur++) {
+                for (uint32_t uc = 0; uc < ucols; uc++) {
+                    float cm = 0.0f;
+                    if (g->cm_mode == OG_CM_MEDIAN) {
+                        uint32_t n = 0;
+                        for (uint32_t r = 0; r < g->unit_rows; r++) {
+                            for (uint32_t c = 0; c < g->unit_cols; c++) {
+                                const size_t p =
+                                    (size_t)(ur * g->unit_rows + r) * C +
+                                    uc * g->unit_cols + c;
+                                if (d[p] < t->cm_cut_adu) set[n++] = d[p];
+                            }
+                        }
+                        if (n >= n_min && n > 0) cm = oracle_lower_median(set, n);
+                    }
+                    cmu[ur * ucols + uc] = cm;
+                    if (cm_out)
+                        cm_out[(size_t)f * g->n_modules * upm + m * upm +
+                               ur * ucols + uc] = cm;
+                }
+            }
+            /* 3.-5. subtract common mode, gain, zero noise; pixel histogram */
+            for (uint32_t r = 0; r < R; r++) {
+                for (uint32_t c = 0; c < C; c++) {
+                    const size_t p = (size_t)r * C + c;
+                    const float cm =
+                        cmu[(r / g->unit_rows) * ucols + c / g->unit_cols];
+                    const float cc = d[p] - cm;
+                    const float ev = cc * inv_gain[base + p];
+                    e[p] = ev;
+                    s[p] = ev > t->zero_thr_kev ? ev : 0.0f;
+                    hist_pix[bin_of(ev, t->hist_lo_kev, inv_w, t->hist_bins)]++;
+                    if (corrected) corrected[(size_t)f * fpx + base + p] = ev;
+                }
+            }
+            /* 6.-9. seeds, charge sum, count, centroid, summaries */
+            for (uint32_t r = 0; r < R; r++) {
+                for (uint32_t c = 0; c < C; c++) {
+                    const size_t p = (size_t)r * C + c;
+                    const float sp = s[p];
+                    if (!(sp > t->seed_thr_kev)) continue;
+                    int seed = 1;
+                    for (int dy = -1; dy <= 1 && seed; dy++) {
+                        for (int dx = -1; dx <= 1; dx++) {
+                            if (!dy && !dx) continue;
+                            const long rr = (long)r + dy, cc = (long)c + dx;
+                            if (rr < 0 || rr >= (long)R || cc < 0 || cc >= (long)C)
+                                continue;
+                            const float sq = s[(size_t)rr * C + cc];
+                            const int before = dy < 0 || (dy == 0 && dx < 0);
+                            if (before ? !(sp > sq) : !(sp >= sq)) {
+                                seed = 0;
+                                break;
+                            }
+                        }
+                    }
+                    if (!seed) continue;
+                    float E = 0.0f, Mx = 0.0f, My = 0.0f;
+                    uint32_t npix = 0;
+                    for (int dy = -1; dy <= 1; dy++) {
+                        for (int dx = -1; dx <= 1; dx++) {
+                            const long rr = (long)r + dy, cc = (long)c + dx;
+                            float sq = 0.0f;
+                            if (rr >= 0 && rr < (long)R && cc >= 0 && cc < (long)C)
+                                sq = s[(size_t)rr * C + cc];
+                            E = E + sq;
+                            Mx = Mx + sq * (float)dx;
+                            My = My + sq * (float)dy;
+                            if (sq > 0.0f) npix++;
+                        }
+                    }
+                    ns++;
+                    hist_hit[bin_of(E, t->hist_lo_kev, inv_w, t->hist_bins)]++;
+                    const float q = E / t->photon_kev;
+                    const float qr = nearbyintf(q);
+                    uint32_t n;
+                    uint16_t flags = 0;
+                    if (!(qr >= 0.0f)) n = 0;
+                    else if (qr > 255.0f) { n = 255; flags |= OG_SATURATED; }
+                    else n = (uint32_t)qr;
+                    if (n < 1) continue;
+                    if (r == 0 || c == 0 || r == R - 1 || c == C - 1)
+                        flags |= OG_EDGE;
+                    const uint32_t pix = (uint32_t)(base + p);
+                    count_map[pix] += n;
+                    if (nh < cap) {
+                        og_hit* h = &hits[nh];
+                        h->frame = frame_base + f;
+                        h->pixel = pix;
+                        h->energy_kev = E;
+                        h->dx = Mx / E;
+                        h->dy = My / E;
+                        h->count = (uint8_t)n;
+                        h->npix = (uint8_t)npix;
+                        h->flags = flags;
+                    }
+                    nh++;
+                }
+            }
+        }
+    }
+    *n_hits = nh;
+    if (n_seeds) *n_seeds = ns;
+    free(inv_gain); free(d); free(e); free(s); free(set); free(cmu);
+    return 0;
+}
