@@ -1,0 +1,328 @@
+#!/usr/bin/env python3
+"""Benchmark of the detector chain on the 2.2 Mpixel CSPAD-like workload.
+
+One step = the whole chain (dark, median common mode per 185x194 bank, gain,
+zeroing, 3x3 local max, charge sum, count, centroid, hit compaction, count
+map and histograms) over a batch of 1024 frames of 32 x 185 x 388 uint16
+pixels, synthetic (seeded generator), occupancy 0.5 %, 8 keV photons.  The
+batch (4.7 GB) is larger than L2, so no flush is needed between steps.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (a
+bounded sample of the same workload on the host cores).
+
+Multi-GPU (torchrun): each rank processes its own batch (weak scaling), no
+collective on the data path; the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("frames/s and HBM GB/s (fraction of peak) on 2.2 Mpx frames; "
+          "p99 latency at 100kHz")
+FRAMES_PER_STEP = 1024
+HIT_BYTES = 24
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pd", choices=["pd", "reference"])
+    ap.add_argument("--frames", type=int, default=FRAMES_PER_STEP)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1903_06838_gb300 import synth
+    return synth.cspad_2p2m()
+
+
+def workload_config(det, frames):
+    return {
+        "workload": f"cspad_2p2m: {det.n_modules}x{det.rows}x{det.cols} uint16 "
+                    f"(2.2 Mpx), common mode per {det.unit_rows}x{det.unit_cols} "
+                    f"bank, occupancy {det.occupancy:.1%}, {det.photon_kev:g} keV, "
+                    f"cloud sigma {det.cloud_sigma} px",
+        "frames_per_step": frames,
+        "pixels_per_frame": det.pixels_per_frame,
+        "l2": "inputs larger than L2 (no flush): "
+              f"{frames * det.pixels_per_frame * 2 / 1e9:.2f} GB of raw per step",
+    }
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in out.strip().splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(det, ped, gain, raw_first, target_s=12.0):
+    """The oracle as it stands, single-threaded, on a bounded sample."""
+    import oracle
+    g = oracle.geometry(**det.geometry())
+    t = oracle.thresholds(**det.thresholds())
+    t0 = time.perf_counter()
+    oracle.process(g, t, ped, gain, raw_first[:1])
+    one = time.perf_counter() - t0
+    n = int(max(1, min(len(raw_first), target_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.process(g, t, ped, gain, raw_first[:n])
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} frames of the batch (seed 1), single thread, "
+                      f"{dt:.1f} s; generation excluded"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1903_06838_gb300 import synth
+    import oracle
+    det = workload()
+    ped, gain = synth.maps(det)
+    sample = 2
+    raw, _ = synth.frames(det, ped, gain, 0, sample * (args.warmup + args.steps),
+                          truth=False)
+    g = oracle.geometry(**det.geometry())
+    t = oracle.thresholds(**det.thresholds())
+    for w in range(args.warmup):
+        oracle.process(g, t, ped, gain, raw[w * sample:(w + 1) * sample])
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        a = (args.warmup + s) * sample
+        oracle.process(g, t, ped, gain, raw[a:a + sample])
+    dt = time.perf_counter() - t0
+    fps = sample * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": dict(workload_config(det, sample),
+                       note="each step is a bounded sample of the batch"),
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"{sample} frames per step, single thread"},
+        "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_pd(args):
+    import torch
+    from paper_1903_06838_gb300 import pd, synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else torch.cuda.current_device())
+    pd.build()
+    det = workload()
+    nf = args.frames
+    ped, gain = synth.maps(det)
+    # frames generated straight into page-locked host memory (reused by e2e)
+    host = torch.empty((nf,) + det.frame_shape, dtype=torch.int16, pin_memory=True)
+    raw = host.numpy().view(np.uint16)
+    synth.frames(det, ped, gain, rank * nf, nf, truth=False, out=raw)
+    frames = host.to(dev, non_blocking=False)
+    ctx = pd.pd_create(det.geometry(), ped, gain, det.thresholds())
+    cap = nf * 16384
+    out = pd.Outputs(ctx, nf, cap, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        pd.pd_process(ctx, frames.data_ptr(), nf, 0, stream=stream, **out.ptrs())
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+    n_hits = int(out.n_hits.item())
+
+    clocks = Clocks(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    pd.pd_set_profiling(ctx, True)
+    pd.pd_read_profile(ctx)  # clear
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    prof = pd.pd_read_profile(ctx)
+    pd.pd_set_profiling(ctx, False)
+    clk = clocks.stop()
+    ms_step = ms / args.steps
+    if ws > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    fps = nf * ws / (ms_step / 1e3)
+
+    # roofline of the dominant kernel: algorithmic bytes / its mean duration
+    peak, peak_kind = read_peaks()
+    fpx = det.pixels_per_frame
+    raw_b = nf * fpx * 2
+    hits_b = n_hits * HIT_BYTES
+    maps_b = fpx * 4           # one FP32 map, read once per launch
+    cmap_b = fpx * 4 * 2       # photon-count map, read and written once
+    cm_b = nf * ctx.units_per_frame * 4
+    # algorithmic bytes of one launch of each kernel
+    kernel_bytes = {
+        "cm_select": raw_b + maps_b + cm_b,
+        "stencil": raw_b + 2 * maps_b + cm_b + hits_b + cmap_b,
+        "fused_chain": raw_b + 2 * maps_b + hits_b + cmap_b,
+    }
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    if dom:
+        name, (launches, tot) = dom
+        per_launch_ms = tot / launches
+        b = kernel_bytes.get(name, raw_b)
+        ach = b / (per_launch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+                "traffic": None, "bytes_per_launch": int(b),
+                "ms_per_launch": per_launch_ms,
+                "kernel_share": {k: round(v[1] / sum(x[1] for x in prof.values()), 4)
+                                 for k, v in prof.items()}}
+    launches_per_step = sum(v[0] for v in prof.values()) / max(args.steps, 1) if prof else 0
+    chain_bytes = raw_b + 2 * maps_b + hits_b + cmap_b
+    line = {
+        "metric": METRIC, "value": round(fps, 1), "unit": "frames/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(det, nf),
+        "pixels_per_s": fps * fpx,
+        "chain_hbm_gbs": round(chain_bytes * ws / (ms_step / 1e3) / 1e9, 1),
+        "chain_frac_of_peak": round(chain_bytes * ws / (ms_step / 1e3) / 1e9 / peak, 4),
+        "hits_per_frame": n_hits / nf,
+        "roofline": roof,
+        "clocks": clk,
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+    }
+
+    # end to end through the host-buffer entry point (pinned host frames)
+    if not args.no_e2e:
+        hits_host = np.empty(cap, pd.HIT_DTYPE)
+        pd.pd_process_host(ctx, raw, 0, out=hits_host)
+        torch.cuda.synchronize(dev)
+        e_steps = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        nh = 0
+        for _ in range(e_steps):
+            _, nh = pd.pd_process_host(ctx, raw, 0, out=hits_host)
+        dt = (time.perf_counter() - t0) / e_steps
+        if ws > 1:
+            t = torch.tensor([dt], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        line["e2e"] = {"value": round(nf * ws / dt, 1), "unit": "frames/s",
+                       "h2d_bytes_per_step": raw_b, "d2h_bytes_per_step": nh * HIT_BYTES + 4,
+                       "api": "pd_process_host (page-locked host frames, hits back to host)"}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(det, ped, gain, raw[:64])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_pd(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

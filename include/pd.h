@@ -69,9 +69,8 @@ extern "C" {
 #define PD_HIT_SATURATED 2u /* rint(E / photon_kev) exceeded 255 and clipped */
 
 /* Detector geometry.  Requirements (PD_EINVAL otherwise): all sizes > 0,
- * rows % unit_rows == 0, cols % unit_cols == 0, and the pixel count of one
- * frame, n_modules * rows * cols, a multiple of 8 (so every frame starts on
- * a 16-byte boundary). */
+ * rows, cols <= 65535, fewer than 2^31 pixels per frame, rows % unit_rows
+ * == 0 and cols % unit_cols == 0. */
 typedef struct {
     uint32_t n_modules;
     uint32_t rows, cols;           /* pixels of one module                  */
@@ -182,6 +181,22 @@ int pd_reset_summary(pd_ctx* ctx, void* stream);
 /* pd_destroy — free the context's device state (NULL is a no-op).  Waits
  * for the device to finish work that may use it. */
 void pd_destroy(pd_ctx* ctx);
+
+/* Kernel timing.  When enabled on a context, every kernel the context
+ * launches is bracketed by CUDA events recorded on the launching stream;
+ * pd_read_profile synchronises the device, reports the summed device time
+ * and launch count per kernel name since the last read, and clears them.
+ * Disabled by default; when disabled no event is recorded. */
+#define PD_PROFILE_MAX_KERNELS 8
+typedef struct {
+    uint32_t n_kernels;
+    char name[PD_PROFILE_MAX_KERNELS][32];
+    uint32_t launches[PD_PROFILE_MAX_KERNELS];
+    double total_ms[PD_PROFILE_MAX_KERNELS];
+} pd_profile;
+
+int pd_set_profiling(pd_ctx* ctx, int enable);
+int pd_read_profile(pd_ctx* ctx, pd_profile* out);
 
 const char* pd_strerror(int code);
 const char* pd_last_error(void);

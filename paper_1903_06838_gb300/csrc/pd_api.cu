@@ -1,0 +1,508 @@
+// pd_api.cu — host implementation of the C ABI declared in include/pd.h.
+//
+// A pd_ctx owns the device copies of the pedestal and inverse-gain maps,
+// the accumulated summaries (photon-count map, two histograms) and the
+// scratch it needs per call.  Compiled with -ffp-contract=off so the host
+// reciprocal of the gain is the plain IEEE division.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pd.h"
+#include "pd_internal.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* what) {
+    g_last_error = what;
+    return code;
+}
+
+int fail_cuda(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return PD_ECUDA;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+}  // namespace
+
+struct pd_ctx {
+    pd_geometry geom;
+    pd_thresholds thr;
+    pd::ChainParams params;
+    int device = 0;
+    uint32_t masked = 0;
+    // device state
+    float* d_ped = nullptr;
+    float* d_inv_gain = nullptr;
+    uint32_t* d_count_map = nullptr;
+    unsigned long long* d_hist_pix = nullptr;
+    unsigned long long* d_hist_hit = nullptr;
+    // per-call scratch: common mode of each (frame, unit)
+    float* d_cm = nullptr;
+    size_t cm_cap = 0;  // floats
+    // host-path staging (pd_process_host)
+    uint16_t* d_stage[2] = {nullptr, nullptr};
+    uint32_t stage_frames = 0;
+    pd_hit* d_host_hits = nullptr;
+    uint32_t host_hit_cap = 0;
+    uint32_t* d_host_nhits = nullptr;
+    cudaStream_t hstream[2] = {nullptr, nullptr};
+    cudaEvent_t hevent[4] = {nullptr, nullptr, nullptr, nullptr};
+    // kernel timing (pd_set_profiling)
+    bool profiling = false;
+    struct Mark { int kernel; cudaEvent_t a, b; };
+    std::vector<Mark> marks;        // recorded since the last read
+    std::vector<cudaEvent_t> spare; // event pool
+};
+
+namespace {
+
+const char* const kKernelNames[] = {"cm_select", "stencil", "fused_chain"};
+constexpr int kNumKernelNames = 3;
+
+cudaEvent_t take_event(pd_ctx* c) {
+    if (!c->spare.empty()) {
+        cudaEvent_t e = c->spare.back();
+        c->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket one launch with events when profiling is on.
+struct ProfileScope {
+    pd_ctx* c;
+    int kernel;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    ProfileScope(pd_ctx* c_, int k, cudaStream_t s_) : c(c_), kernel(k), s(s_) {
+        if (c->profiling) {
+            a = take_event(c);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~ProfileScope() {
+        if (a) {
+            cudaEvent_t b = take_event(c);
+            cudaEventRecord(b, s);
+            c->marks.push_back({kernel, a, b});
+        }
+    }
+};
+
+}  // namespace
+
+namespace pd {
+
+int device_sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 1;
+    }
+    return cached[dev];
+}
+
+}  // namespace pd
+
+namespace {
+
+int check_geometry(const pd_geometry* g) {
+    if (!g) return fail(PD_EINVAL, "geometry is NULL");
+    if (!g->n_modules || !g->rows || !g->cols || !g->unit_rows || !g->unit_cols)
+        return fail(PD_EINVAL, "geometry sizes must be > 0");
+    if (g->rows % g->unit_rows || g->cols % g->unit_cols)
+        return fail(PD_EINVAL, "common-mode units must tile each module");
+    if (g->cm_mode != PD_CM_MEDIAN && g->cm_mode != PD_CM_NONE)
+        return fail(PD_EINVAL, "unknown cm_mode");
+    const unsigned long long fpx =
+        (unsigned long long)g->n_modules * g->rows * g->cols;
+    if (fpx >= (1ull << 31)) return fail(PD_EINVAL, "frame too large");
+    if (g->rows > 65535 || g->cols > 65535) return fail(PD_EINVAL, "module too large");
+    return PD_OK;
+}
+
+int check_thresholds(const pd_thresholds* t) {
+    if (!t) return fail(PD_EINVAL, "thresholds is NULL");
+    if (!(t->zero_thr_kev >= 0.0f) || !(t->seed_thr_kev >= t->zero_thr_kev) ||
+        !isfinite(t->seed_thr_kev))
+        return fail(PD_EINVAL, "need 0 <= zero_thr_kev <= seed_thr_kev, finite");
+    if (!(t->photon_kev > 0.0f) || !isfinite(t->photon_kev))
+        return fail(PD_EINVAL, "photon_kev must be finite and > 0");
+    if (!(t->hist_bin_kev > 0.0f) || !isfinite(t->hist_bin_kev) ||
+        !isfinite(t->hist_lo_kev))
+        return fail(PD_EINVAL, "histogram lo and bin width must be finite, width > 0");
+    if (t->hist_bins < 1 || t->hist_bins > PD_MAX_HIST_BINS)
+        return fail(PD_EINVAL, "hist_bins must be in [1, PD_MAX_HIST_BINS]");
+    if (isnan(t->cm_cut_adu)) return fail(PD_EINVAL, "cm_cut_adu is NaN");
+    return PD_OK;
+}
+
+uint32_t ceil_sqrt_u32(uint32_t n) {
+    uint32_t k = (uint32_t)sqrt((double)n);
+    while ((uint64_t)k * k < n) k++;
+    while (k && (uint64_t)(k - 1) * (k - 1) >= n) k--;
+    return k;
+}
+
+void free_ctx(pd_ctx* c) {
+    if (!c) return;
+    cudaFree(c->d_ped);
+    cudaFree(c->d_inv_gain);
+    cudaFree(c->d_count_map);
+    cudaFree(c->d_hist_pix);
+    cudaFree(c->d_hist_hit);
+    cudaFree(c->d_cm);
+    cudaFree(c->d_stage[0]);
+    cudaFree(c->d_stage[1]);
+    cudaFree(c->d_host_hits);
+    cudaFree(c->d_host_nhits);
+    for (int i = 0; i < 2; i++)
+        if (c->hstream[i]) cudaStreamDestroy(c->hstream[i]);
+    for (int i = 0; i < 4; i++)
+        if (c->hevent[i]) cudaEventDestroy(c->hevent[i]);
+    for (auto& m : c->marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    for (auto e : c->spare) cudaEventDestroy(e);
+    delete c;
+}
+
+int ensure_cm(pd_ctx* c, uint32_t n_frames) {
+    const size_t need = (size_t)n_frames * c->params.units_per_frame;
+    if (need <= c->cm_cap) return PD_OK;
+    // growth reallocates: any work on the old buffer must be finished
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail_cuda(e, "synchronise before scratch growth");
+    cudaFree(c->d_cm);
+    c->d_cm = nullptr;
+    c->cm_cap = 0;
+    e = cudaMalloc(&c->d_cm, need * sizeof(float));
+    if (e != cudaSuccess) return fail(PD_ENOMEM, "common-mode scratch allocation failed");
+    c->cm_cap = need;
+    return PD_OK;
+}
+
+int run_chain(pd_ctx* c, const uint16_t* frames, uint32_t n_frames, uint32_t frame_base,
+              const pd_outputs* out, cudaStream_t s, bool zero = true) {
+    cudaError_t e = cudaSuccess;
+    if (zero && (e = cudaMemsetAsync(out->n_hits, 0, sizeof(uint32_t), s)) != cudaSuccess)
+        return fail_cuda(e, "zero n_hits");
+    if (n_frames == 0) return PD_OK;
+    float* cm = out->cm;
+    if (!cm) {
+        int rc = ensure_cm(c, n_frames);
+        if (rc) return rc;
+        cm = c->d_cm;
+    }
+    {
+        ProfileScope ps(c, 0, s);
+        e = pd::launch_cm_select(c->params, frames, n_frames, cm, s);
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "common-mode kernel launch");
+    pd::CallOut co{out->hits, out->hit_capacity, out->n_hits, out->corrected, cm};
+    {
+        ProfileScope ps(c, 1, s);
+        e = pd::launch_stencil(c->params, frames, n_frames, frame_base, co, s);
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "stencil kernel launch");
+    return PD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pd_strerror(int code) {
+    switch (code) {
+        case PD_OK: return "ok";
+        case PD_EINVAL: return "invalid argument";
+        case PD_EALIGN: return "misaligned pointer or size";
+        case PD_ENOMEM: return "out of memory";
+        case PD_EOVERFLOW: return "hit capacity exceeded";
+        case PD_ETIMEDOUT: return "timed out";
+        case PD_ECUDA: return "CUDA error";
+        case PD_ENOTSUP: return "not supported";
+        case PD_EBUSY: return "busy";
+        default: return "unknown error";
+    }
+}
+
+const char* pd_last_error(void) { return g_last_error.c_str(); }
+
+int pd_create(const pd_geometry* geometry, const float* pedestal_host,
+              const float* gain_host, const pd_thresholds* thresholds, pd_ctx** out) {
+    if (!out) return fail(PD_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = check_geometry(geometry);
+    if (rc) return rc;
+    rc = check_thresholds(thresholds);
+    if (rc) return rc;
+    if (!pedestal_host || !gain_host) return fail(PD_EINVAL, "maps are NULL");
+
+    pd_ctx* c = new (std::nothrow) pd_ctx();
+    if (!c) return fail(PD_ENOMEM, "host allocation failed");
+    c->geom = *geometry;
+    c->thr = *thresholds;
+    cudaGetDevice(&c->device);
+    const pd_geometry& g = *geometry;
+    pd::ChainParams& p = c->params;
+    p.n_modules = g.n_modules;
+    p.rows = g.rows;
+    p.cols = g.cols;
+    p.unit_rows = g.unit_rows;
+    p.unit_cols = g.unit_cols;
+    p.units_per_row = g.cols / g.unit_cols;
+    p.units_per_module = (g.rows / g.unit_rows) * p.units_per_row;
+    p.unit_px = g.unit_rows * g.unit_cols;
+    p.module_px = g.rows * g.cols;
+    p.frame_px = g.n_modules * p.module_px;
+    p.units_per_frame = g.n_modules * p.units_per_module;
+    p.cm_mode = g.cm_mode;
+    p.cm_min_count = thresholds->cm_min_count ? thresholds->cm_min_count
+                                              : ceil_sqrt_u32(p.unit_px);
+    p.cm_cut = thresholds->cm_cut_adu;
+    p.zero_thr = thresholds->zero_thr_kev;
+    p.seed_thr = thresholds->seed_thr_kev;
+    p.photon_kev = thresholds->photon_kev;
+    p.hist_lo = thresholds->hist_lo_kev;
+    p.hist_inv_w = 1.0f / thresholds->hist_bin_kev;
+    p.hist_bins = thresholds->hist_bins;
+
+    const size_t fpx = p.frame_px;
+    std::vector<float> inv(fpx);
+    uint32_t masked = 0;
+    for (size_t i = 0; i < fpx; i++) {
+        const float gv = gain_host[i];
+        if (gv > 0.0f && isfinite(gv)) {
+            inv[i] = 1.0f / gv;
+        } else {
+            inv[i] = 0.0f;
+            masked++;
+        }
+    }
+    c->masked = masked;
+    cudaError_t e;
+    if ((e = cudaMalloc(&c->d_ped, fpx * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_inv_gain, fpx * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_count_map, fpx * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_hist_pix, p.hist_bins * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_hist_hit, p.hist_bins * 8)) != cudaSuccess) {
+        free_ctx(c);
+        return fail(PD_ENOMEM, "device allocation failed in pd_create");
+    }
+    if ((e = cudaMemcpy(c->d_ped, pedestal_host, fpx * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->d_inv_gain, inv.data(), fpx * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemset(c->d_count_map, 0, fpx * 4)) ||
+        (e = cudaMemset(c->d_hist_pix, 0, p.hist_bins * 8)) ||
+        (e = cudaMemset(c->d_hist_hit, 0, p.hist_bins * 8))) {
+        free_ctx(c);
+        return fail_cuda(e, "pd_create upload");
+    }
+    p.ped = c->d_ped;
+    p.inv_gain = c->d_inv_gain;
+    p.count_map = c->d_count_map;
+    p.hist_pix = c->d_hist_pix;
+    p.hist_hit = c->d_hist_hit;
+    *out = c;
+    return PD_OK;
+}
+
+int pd_query(const pd_ctx* c, pd_info* info) {
+    if (!c || !info) return fail(PD_EINVAL, "NULL argument");
+    info->pixels_per_frame = c->params.frame_px;
+    info->units_per_frame = c->params.units_per_frame;
+    info->unit_pixels = c->params.unit_px;
+    info->cm_min_count = c->params.cm_min_count;
+    info->hist_bins = c->params.hist_bins;
+    info->masked_pixels = c->masked;
+    return PD_OK;
+}
+
+int pd_process(pd_ctx* c, const uint16_t* frames_dev, uint32_t n_frames,
+               uint32_t frame_base, const pd_outputs* out, void* stream) {
+    if (!c || !out) return fail(PD_EINVAL, "NULL argument");
+    if (!out->n_hits || (!out->hits && out->hit_capacity))
+        return fail(PD_EINVAL, "hits/n_hits are required");
+    if (n_frames && !frames_dev) return fail(PD_EINVAL, "frames are NULL");
+    if (!aligned(frames_dev, 16)) return fail(PD_EALIGN, "frames must be 16-byte aligned");
+    if (!aligned(out->n_hits, 4) || !aligned(out->hits, 8))
+        return fail(PD_EALIGN, "hit buffers misaligned");
+    if ((out->corrected && !aligned(out->corrected, 4)) || (out->cm && !aligned(out->cm, 4)))
+        return fail(PD_EALIGN, "float outputs must be 4-byte aligned");
+    return run_chain(c, frames_dev, n_frames, frame_base, out, (cudaStream_t)stream);
+}
+
+int pd_process_host(pd_ctx* c, const uint16_t* frames_host, uint32_t n_frames,
+                    uint32_t frame_base, pd_hit* hits_host, uint32_t hit_capacity,
+                    uint32_t* n_hits_host) {
+    if (!c || !n_hits_host || (hit_capacity && !hits_host) || (n_frames && !frames_host))
+        return fail(PD_EINVAL, "NULL argument");
+    cudaError_t e;
+    const size_t fbytes = (size_t)c->params.frame_px * sizeof(uint16_t);
+    // chunk: about 64 MB of frames per stage buffer
+    uint32_t chunk = (uint32_t)std::max<size_t>(1, (64u << 20) / fbytes);
+    chunk = std::min<uint32_t>(chunk, std::max<uint32_t>(n_frames, 1));
+    if (c->stage_frames < chunk) {
+        cudaDeviceSynchronize();
+        for (int i = 0; i < 2; i++) {
+            cudaFree(c->d_stage[i]);
+            c->d_stage[i] = nullptr;
+        }
+        c->stage_frames = 0;
+        for (int i = 0; i < 2; i++)
+            if (cudaMalloc(&c->d_stage[i], chunk * fbytes) != cudaSuccess)
+                return fail(PD_ENOMEM, "staging allocation failed");
+        c->stage_frames = chunk;
+    }
+    for (int i = 0; i < 2; i++)
+        if (!c->hstream[i] &&
+            (e = cudaStreamCreateWithFlags(&c->hstream[i], cudaStreamNonBlocking)))
+            return fail_cuda(e, "stream create");
+    for (int i = 0; i < 4; i++)
+        if (!c->hevent[i] &&
+            (e = cudaEventCreateWithFlags(&c->hevent[i], cudaEventDisableTiming)))
+            return fail_cuda(e, "event create");
+    const uint32_t cap = std::max<uint32_t>(hit_capacity, 1);
+    if (c->host_hit_cap < cap) {
+        cudaDeviceSynchronize();
+        cudaFree(c->d_host_hits);
+        c->d_host_hits = nullptr;
+        c->host_hit_cap = 0;
+        if (cudaMalloc(&c->d_host_hits, (size_t)cap * sizeof(pd_hit)) != cudaSuccess)
+            return fail(PD_ENOMEM, "hit buffer allocation failed");
+        c->host_hit_cap = cap;
+    }
+    if (!c->d_host_nhits && cudaMalloc(&c->d_host_nhits, sizeof(uint32_t)) != cudaSuccess)
+        return fail(PD_ENOMEM, "counter allocation failed");
+    int rc = ensure_cm(c, chunk);
+    if (rc) return rc;
+
+    // Copies run on hstream[1], processing on hstream[0]; chunk k uses
+    // staging buffer k%2.  copy(k) waits for process(k-2) (same buffer),
+    // process(k) waits for copy(k), so the upload of chunk k+1 overlaps the
+    // processing of chunk k.  One device counter spans all chunks, so the
+    // hit list is contiguous and read back once at the end.
+    cudaStream_t s0 = c->hstream[0], s1 = c->hstream[1];
+    if ((e = cudaMemsetAsync(c->d_host_nhits, 0, sizeof(uint32_t), s0)))
+        return fail_cuda(e, "zero counter");
+    cudaEvent_t copied[2] = {c->hevent[0], c->hevent[1]};
+    cudaEvent_t processed[2] = {c->hevent[2], c->hevent[3]};
+    uint32_t done = 0, k = 0;
+    while (done < n_frames) {
+        const uint32_t nf = std::min(chunk, n_frames - done);
+        const int b = k & 1;
+        if (k >= 2) cudaStreamWaitEvent(s1, processed[b], 0);
+        if ((e = cudaMemcpyAsync(c->d_stage[b], frames_host + (size_t)done * c->params.frame_px,
+                                 nf * fbytes, cudaMemcpyHostToDevice, s1)))
+            return fail_cuda(e, "frame upload");
+        cudaEventRecord(copied[b], s1);
+        cudaStreamWaitEvent(s0, copied[b], 0);
+        pd_outputs o{};
+        o.hit_capacity = hit_capacity;
+        o.hits = c->d_host_hits;
+        o.n_hits = c->d_host_nhits;
+        rc = run_chain(c, c->d_stage[b], nf, frame_base + done, &o, s0, /*zero=*/false);
+        if (rc) return rc;
+        cudaEventRecord(processed[b], s0);
+        done += nf;
+        k++;
+    }
+    uint32_t total = 0;
+    if ((e = cudaMemcpyAsync(&total, c->d_host_nhits, 4, cudaMemcpyDeviceToHost, s0)) ||
+        (e = cudaStreamSynchronize(s0)))
+        return fail_cuda(e, "hit count readback");
+    const uint32_t keep = std::min(total, hit_capacity);
+    if (keep && ((e = cudaMemcpyAsync(hits_host, c->d_host_hits, (size_t)keep * sizeof(pd_hit),
+                                      cudaMemcpyDeviceToHost, s0)) ||
+                 (e = cudaStreamSynchronize(s0))))
+        return fail_cuda(e, "hit download");
+    if ((e = cudaStreamSynchronize(s1))) return fail_cuda(e, "host path synchronise");
+    *n_hits_host = total;
+    return total > hit_capacity ? fail(PD_EOVERFLOW, "hit capacity exceeded") : PD_OK;
+}
+
+int pd_get_summary(pd_ctx* c, uint32_t* count_map_host, uint64_t* hist_pix_host,
+                   uint64_t* hist_hit_host, void* stream) {
+    if (!c) return fail(PD_EINVAL, "NULL context");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (count_map_host && (e = cudaMemcpyAsync(count_map_host, c->d_count_map,
+                                               (size_t)c->params.frame_px * 4,
+                                               cudaMemcpyDeviceToHost, s)))
+        return fail_cuda(e, "count map download");
+    if (hist_pix_host && (e = cudaMemcpyAsync(hist_pix_host, c->d_hist_pix,
+                                              (size_t)c->params.hist_bins * 8,
+                                              cudaMemcpyDeviceToHost, s)))
+        return fail_cuda(e, "histogram download");
+    if (hist_hit_host && (e = cudaMemcpyAsync(hist_hit_host, c->d_hist_hit,
+                                              (size_t)c->params.hist_bins * 8,
+                                              cudaMemcpyDeviceToHost, s)))
+        return fail_cuda(e, "histogram download");
+    if ((e = cudaStreamSynchronize(s))) return fail_cuda(e, "summary synchronise");
+    return PD_OK;
+}
+
+int pd_reset_summary(pd_ctx* c, void* stream) {
+    if (!c) return fail(PD_EINVAL, "NULL context");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->d_count_map, 0, (size_t)c->params.frame_px * 4, s)) ||
+        (e = cudaMemsetAsync(c->d_hist_pix, 0, (size_t)c->params.hist_bins * 8, s)) ||
+        (e = cudaMemsetAsync(c->d_hist_hit, 0, (size_t)c->params.hist_bins * 8, s)))
+        return fail_cuda(e, "summary reset");
+    return PD_OK;
+}
+
+int pd_set_profiling(pd_ctx* c, int enable) {
+    if (!c) return fail(PD_EINVAL, "NULL context");
+    c->profiling = enable != 0;
+    return PD_OK;
+}
+
+int pd_read_profile(pd_ctx* c, pd_profile* out) {
+    if (!c || !out) return fail(PD_EINVAL, "NULL argument");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail_cuda(e, "profile synchronise");
+    memset(out, 0, sizeof(*out));
+    out->n_kernels = kNumKernelNames;
+    for (int k = 0; k < kNumKernelNames; k++)
+        snprintf(out->name[k], sizeof(out->name[k]), "%s", kKernelNames[k]);
+    for (auto& m : c->marks) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+            out->launches[m.kernel]++;
+            out->total_ms[m.kernel] += ms;
+        }
+        c->spare.push_back(m.a);
+        c->spare.push_back(m.b);
+    }
+    c->marks.clear();
+    return PD_OK;
+}
+
+void pd_destroy(pd_ctx* c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_ctx(c);
+}
+
+}  // extern "C"

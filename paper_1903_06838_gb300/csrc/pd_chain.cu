@@ -1,0 +1,338 @@
+// pd_chain.cu — the per-frame correction chain as two kernels:
+//
+//   cm_select_kernel  common mode of one unit (paper section "Common Mode",
+//                     Fig. c): exact lower median of d = raw - pedestal over
+//                     the unit's pixels with d < cut, found by a 4-pass
+//                     8-bit radix select on order-preserving 32-bit keys.
+//   stencil_kernel    dark, common mode and gain correction (Fig. b), noise
+//                     zeroing, 3x3 local maximum, charge sum, photon count
+//                     (Fig. e), centre-of-mass offset (Fig. f), warp-ballot
+//                     hit compaction and the summaries ("Summarization").
+//
+// Every floating-point operation is written as an explicit round-to-nearest
+// intrinsic in the order the chain defines, and the file is compiled with
+// --fmad=false, so results are reproducible bit for bit.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pd_internal.cuh"
+
+namespace pd {
+
+namespace {
+
+constexpr uint32_t kSentinel = 0xFFFFFFFFu;  // "not in the common-mode set"
+
+// Unsigned order of the keys == ascending IEEE order, with -0 below +0.
+__device__ __forceinline__ uint32_t order_key(float v) {
+    const uint32_t b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_value(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+__device__ __forceinline__ uint32_t hist_bin(float v, float lo, float inv_w,
+                                             uint32_t bins) {
+    const float t = __fmul_rn(__fsub_rn(v, lo), inv_w);
+    if (!(t >= 0.0f)) return 0;
+    if (t >= (float)bins) return bins - 1;
+    return (uint32_t)t;  // truncation == floor for t >= 0
+}
+
+// ---------------------------------------------------------------------------
+// Common mode: one CTA per (frame, unit).
+constexpr int kCmThreads = 256;
+
+template <bool KEYS_IN_SMEM>
+__global__ void __launch_bounds__(kCmThreads)
+    cm_select_kernel(ChainParams p, const uint16_t* __restrict__ raw,
+                     float* __restrict__ cm_out) {
+    extern __shared__ uint32_t keys[];
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t warp_cnt[kCmThreads / 32];
+    __shared__ uint32_t s_prefix, s_rank;
+
+    const uint32_t item = blockIdx.x;
+    const uint32_t f = item / p.units_per_frame;
+    const uint32_t u = item % p.units_per_frame;
+    if (p.cm_mode == PD_CM_NONE) {
+        if (threadIdx.x == 0) cm_out[item] = 0.0f;
+        return;
+    }
+    const uint32_t m = u / p.units_per_module;
+    const uint32_t um = u % p.units_per_module;
+    const uint32_t r0 = (um / p.units_per_row) * p.unit_rows;
+    const uint32_t c0 = (um % p.units_per_row) * p.unit_cols;
+    const size_t mod_base = (size_t)m * p.module_px;
+    const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
+    const float* pm = p.ped + mod_base;
+
+    auto key_at = [&](uint32_t i) -> uint32_t {
+        const uint32_t off = (r0 + i / p.unit_cols) * p.cols + c0 + i % p.unit_cols;
+        const float d = __fsub_rn(__uint2float_rn(fr[off]), pm[off]);
+        return d < p.cm_cut ? order_key(d) : kSentinel;
+    };
+
+    uint32_t cnt = 0;
+    for (uint32_t i = threadIdx.x; i < p.unit_px; i += kCmThreads) {
+        const uint32_t k = key_at(i);
+        if (KEYS_IN_SMEM) keys[i] = k;
+        cnt += (k != kSentinel);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) warp_cnt[warp] = cnt;
+    __syncthreads();
+    uint32_t n = 0;
+#pragma unroll
+    for (int w = 0; w < kCmThreads / 32; w++) n += warp_cnt[w];
+    if (n == 0 || n < p.cm_min_count) {
+        if (threadIdx.x == 0) cm_out[item] = 0.0f;
+        return;
+    }
+    if (threadIdx.x == 0) {
+        s_prefix = 0;
+        s_rank = (n - 1) / 2;
+    }
+    // Radix select, most significant byte first.
+    for (int pass = 0; pass < 4; pass++) {
+        const int shift = 24 - 8 * pass;
+        for (int b = threadIdx.x; b < 256; b += kCmThreads) hist[b] = 0;
+        __syncthreads();
+        const uint32_t prefix = s_prefix;
+        for (uint32_t i = threadIdx.x; i < p.unit_px; i += kCmThreads) {
+            const uint32_t k = KEYS_IN_SMEM ? keys[i] : key_at(i);
+            if (k == kSentinel) continue;
+            if (pass > 0 && (k >> (shift + 8)) != prefix) continue;
+            atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // lane l owns bins 8l..8l+7
+            uint32_t loc[8], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                loc[j] = hist[lane * 8 + j];
+                sum += loc[j];
+            }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const uint32_t excl = incl - sum;
+            const uint32_t rank = s_rank;
+            if (excl <= rank && rank < incl) {
+                uint32_t below = excl;
+                int digit = lane * 8;
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    if (below + loc[j] > rank) {
+                        digit = lane * 8 + j;
+                        break;
+                    }
+                    below += loc[j];
+                }
+                s_prefix = (prefix << 8) | (uint32_t)digit;
+                s_rank = rank - below;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) cm_out[item] = key_value(s_prefix);
+}
+
+// ---------------------------------------------------------------------------
+// Stencil: grid-stride over TY x TX tiles of (frame, module).
+constexpr int kTY = 16, kTX = 64, kStThreads = 256;
+constexpr int kHY = kTY + 2, kHX = kTX + 2;
+
+__global__ void __launch_bounds__(kStThreads)
+    stencil_kernel(ChainParams p, const uint16_t* __restrict__ raw,
+                   uint32_t frame_base, CallOut out, uint32_t tiles_y,
+                   uint32_t tiles_x, unsigned long long n_tiles) {
+    extern __shared__ uint32_t hsm[];
+    __shared__ float tile[kHY][kHX];
+    uint32_t* hpix = hsm;
+    uint32_t* hhit = hsm + p.hist_bins;
+    for (uint32_t b = threadIdx.x; b < 2 * p.hist_bins; b += kStThreads) hsm[b] = 0;
+    __syncthreads();
+
+    const int R = (int)p.rows, C = (int)p.cols;
+    const int lane = threadIdx.x & 31;
+    for (unsigned long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        unsigned long long q = t;
+        const int tx = (int)(q % tiles_x);
+        q /= tiles_x;
+        const int ty = (int)(q % tiles_y);
+        q /= tiles_y;
+        const uint32_t m = (uint32_t)(q % p.n_modules);
+        const uint32_t f = (uint32_t)(q / p.n_modules);
+        const int r0 = ty * kTY, c0 = tx * kTX;
+        const size_t mod_base = (size_t)m * p.module_px;
+        const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
+        const float* cmf = out.cm + (size_t)f * p.units_per_frame +
+                           (size_t)m * p.units_per_module;
+
+        // 1. corrected signal of the tile and its 1-pixel halo
+        for (int j = threadIdx.x; j < kHY * kHX; j += kStThreads) {
+            const int hr = j / kHX, hc = j % kHX;
+            const int r = r0 + hr - 1, c = c0 + hc - 1;
+            float s = 0.0f;
+            if (r >= 0 && r < R && c >= 0 && c < C) {
+                const uint32_t off = (uint32_t)r * p.cols + (uint32_t)c;
+                const float cm = cmf[((uint32_t)r / p.unit_rows) * p.units_per_row +
+                                     (uint32_t)c / p.unit_cols];
+                const float d = __fsub_rn(__uint2float_rn(fr[off]), p.ped[mod_base + off]);
+                const float e = __fmul_rn(__fsub_rn(d, cm), p.inv_gain[mod_base + off]);
+                s = e > p.zero_thr ? e : 0.0f;
+                if (hr >= 1 && hr <= kTY && hc >= 1 && hc <= kTX) {
+                    atomicAdd(&hpix[hist_bin(e, p.hist_lo, p.hist_inv_w, p.hist_bins)], 1u);
+                    if (out.corrected)
+                        out.corrected[(size_t)f * p.frame_px + mod_base + off] = e;
+                }
+            }
+            tile[hr][hc] = s;
+        }
+        __syncthreads();
+
+        // 2. seeds, sums, count, centroid; warp-aggregated emission
+        for (int base = 0; base < kTY * kTX; base += kStThreads) {
+            const int j = base + threadIdx.x;
+            const int ir = j / kTX, ic = j % kTX;
+            const int r = r0 + ir, c = c0 + ic;
+            bool emit = false;
+            pd_hit h;
+            uint32_t n = 0, pix = 0;
+            if (r < R && c < C) {
+                const float sp = tile[ir + 1][ic + 1];
+                if (sp > p.seed_thr) {
+                    bool seed = true;
+#pragma unroll
+                    for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+                        for (int dx = -1; dx <= 1; dx++) {
+                            if (!dy && !dx) continue;
+                            const float sq = tile[ir + 1 + dy][ic + 1 + dx];
+                            const bool before = dy < 0 || (dy == 0 && dx < 0);
+                            seed = seed && (before ? (sp > sq) : (sp >= sq));
+                        }
+                    if (seed) {
+                        float E = 0.0f, Mx = 0.0f, My = 0.0f;
+                        uint32_t npix = 0;
+#pragma unroll
+                        for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+                            for (int dx = -1; dx <= 1; dx++) {
+                                const float sq = tile[ir + 1 + dy][ic + 1 + dx];
+                                E = __fadd_rn(E, sq);
+                                Mx = __fadd_rn(Mx, __fmul_rn(sq, (float)dx));
+                                My = __fadd_rn(My, __fmul_rn(sq, (float)dy));
+                                npix += sq > 0.0f;
+                            }
+                        atomicAdd(&hhit[hist_bin(E, p.hist_lo, p.hist_inv_w, p.hist_bins)], 1u);
+                        const float qr = rintf(__fdiv_rn(E, p.photon_kev));
+                        uint16_t flags = 0;
+                        if (!(qr >= 0.0f)) {
+                            n = 0;
+                        } else if (qr > 255.0f) {
+                            n = 255;
+                            flags |= PD_HIT_SATURATED;
+                        } else {
+                            n = (uint32_t)qr;
+                        }
+                        if (n >= 1) {
+                            if (r == 0 || c == 0 || r == R - 1 || c == C - 1)
+                                flags |= PD_HIT_EDGE;
+                            pix = (uint32_t)mod_base + (uint32_t)r * p.cols + (uint32_t)c;
+                            h.frame = frame_base + f;
+                            h.pixel = pix;
+                            h.energy_kev = E;
+                            h.dx = __fdiv_rn(Mx, E);
+                            h.dy = __fdiv_rn(My, E);
+                            h.count = (uint8_t)n;
+                            h.npix = (uint8_t)npix;
+                            h.flags = flags;
+                            emit = true;
+                        }
+                    }
+                }
+            }
+            const uint32_t mask = __ballot_sync(0xffffffffu, emit);
+            if (mask) {
+                uint32_t slot = 0;
+                if (lane == __ffs(mask) - 1) slot = atomicAdd(out.n_hits, __popc(mask));
+                slot = __shfl_sync(0xffffffffu, slot, __ffs(mask) - 1);
+                if (emit) {
+                    slot += __popc(mask & ((1u << lane) - 1u));
+                    atomicAdd(&p.count_map[pix], n);
+                    if (slot < out.hit_capacity) out.hits[slot] = h;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (uint32_t b = threadIdx.x; b < p.hist_bins; b += kStThreads) {
+        if (hpix[b]) atomicAdd(&p.hist_pix[b], (unsigned long long)hpix[b]);
+        if (hhit[b]) atomicAdd(&p.hist_hit[b], (unsigned long long)hhit[b]);
+    }
+}
+
+}  // namespace
+
+size_t cm_select_smem_bytes(const ChainParams& p) {
+    return (size_t)p.unit_px * sizeof(uint32_t);
+}
+
+static constexpr size_t kMaxDynSmem = 200 * 1024;
+
+cudaError_t launch_cm_select(const ChainParams& p, const uint16_t* raw,
+                             uint32_t n_frames, float* cm, cudaStream_t stream) {
+    const unsigned long long items = (unsigned long long)n_frames * p.units_per_frame;
+    if (items == 0) return cudaSuccess;
+    const size_t smem = cm_select_smem_bytes(p);
+    if (smem <= kMaxDynSmem) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(cm_select_kernel<true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kMaxDynSmem);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        cm_select_kernel<true><<<(unsigned)items, kCmThreads, smem, stream>>>(p, raw, cm);
+    } else {
+        cm_select_kernel<false><<<(unsigned)items, kCmThreads, 0, stream>>>(p, raw, cm);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stencil(const ChainParams& p, const uint16_t* raw,
+                           uint32_t n_frames, uint32_t frame_base,
+                           const CallOut& out, cudaStream_t stream) {
+    const uint32_t tiles_y = (p.rows + kTY - 1) / kTY;
+    const uint32_t tiles_x = (p.cols + kTX - 1) / kTX;
+    const unsigned long long n_tiles =
+        (unsigned long long)n_frames * p.n_modules * tiles_y * tiles_x;
+    if (n_tiles == 0) return cudaSuccess;
+    const size_t smem = 2 * (size_t)p.hist_bins * sizeof(uint32_t);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(stencil_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(2 * PD_MAX_HIST_BINS * sizeof(uint32_t)));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    unsigned long long grid = (unsigned long long)device_sm_count() * 4;
+    if (grid > n_tiles) grid = n_tiles;
+    stencil_kernel<<<(unsigned)grid, kStThreads, smem, stream>>>(p, raw, frame_base, out,
+                                                                 tiles_y, tiles_x, n_tiles);
+    return cudaGetLastError();
+}
+
+}  // namespace pd

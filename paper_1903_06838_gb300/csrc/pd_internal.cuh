@@ -1,0 +1,59 @@
+// pd_internal.cuh — device-side parameter block and kernel launchers shared
+// by the translation units of libpd (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pd.h"
+
+namespace pd {
+
+// Everything a kernel needs to know about one detector context.  Passed by
+// value as a kernel parameter (and stored in device memory for the batched
+// launch), so it holds only plain values and device pointers.
+struct ChainParams {
+    // geometry
+    uint32_t n_modules, rows, cols;
+    uint32_t unit_rows, unit_cols;
+    uint32_t units_per_row;     // cols / unit_cols
+    uint32_t units_per_module;  // (rows / unit_rows) * units_per_row
+    uint32_t unit_px;           // unit_rows * unit_cols
+    uint32_t module_px;         // rows * cols
+    uint32_t frame_px;          // n_modules * module_px
+    uint32_t units_per_frame;
+    uint32_t cm_mode;
+    uint32_t cm_min_count;      // resolved n_min
+    // thresholds
+    float cm_cut, zero_thr, seed_thr, photon_kev;
+    float hist_lo, hist_inv_w;  // bin(v) = floor((v - lo) * inv_w)
+    uint32_t hist_bins;
+    // device state owned by the context
+    const float* ped;           // [frame_px]
+    const float* inv_gain;      // [frame_px]
+    uint32_t* count_map;        // [frame_px]
+    unsigned long long* hist_pix;  // [hist_bins]
+    unsigned long long* hist_hit;  // [hist_bins]
+};
+
+// Per-call outputs (device pointers).
+struct CallOut {
+    pd_hit* hits;
+    uint32_t hit_capacity;
+    uint32_t* n_hits;
+    float* corrected;  // may be null
+    float* cm;         // [n_frames][units_per_frame]; never null here
+};
+
+// Launchers (pd_chain.cu).  All are asynchronous on `stream` and return the
+// CUDA launch status.
+cudaError_t launch_cm_select(const ChainParams& p, const uint16_t* raw,
+                             uint32_t n_frames, float* cm, cudaStream_t stream);
+cudaError_t launch_stencil(const ChainParams& p, const uint16_t* raw,
+                           uint32_t n_frames, uint32_t frame_base,
+                           const CallOut& out, cudaStream_t stream);
+size_t cm_select_smem_bytes(const ChainParams& p);
+
+int device_sm_count();
+
+}  // namespace pd

@@ -1,0 +1,371 @@
+"""Thin Python binding of libpd (include/pd.h), with the same entry names.
+
+Only argument marshalling happens here: every step of the chain runs in the
+CUDA kernels of ``csrc/``.  PyTorch supplies device memory and streams.  If
+the compiled library cannot be loaded the binding raises; there is no CPU
+path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_PKG)
+_CSRC = os.path.join(_PKG, "csrc")
+_INCLUDE = os.path.join(_ROOT, "include")
+_BUILD = os.path.join(_PKG, "_build")
+LIB_PATH = os.path.join(_PKG, "libpd.so")
+SOURCES = ["pd_api.cu", "pd_chain.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false",
+              "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+              "-Xptxas", "-warn-spills"]
+
+_lock = threading.Lock()
+_lib = None
+
+# ---- public constants (mirror include/pd.h) -------------------------------
+PD_OK, PD_EINVAL, PD_EALIGN, PD_ENOMEM, PD_EOVERFLOW = 0, 1, 2, 3, 4
+PD_ETIMEDOUT, PD_ECUDA, PD_ENOTSUP, PD_EBUSY = 5, 6, 7, 8
+PD_CM_MEDIAN, PD_CM_NONE = 0, 1
+PD_HIT_EDGE, PD_HIT_SATURATED = 1, 2
+PD_MAX_HIST_BINS = 4096
+
+HIT_DTYPE = np.dtype([("frame", "<u4"), ("pixel", "<u4"), ("energy_kev", "<f4"),
+                      ("dx", "<f4"), ("dy", "<f4"), ("count", "u1"),
+                      ("npix", "u1"), ("flags", "<u2")])
+assert HIT_DTYPE.itemsize == 24
+
+
+class PdGeometry(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in
+                ("n_modules", "rows", "cols", "unit_rows", "unit_cols",
+                 "cm_mode")]
+
+
+class PdThresholds(ctypes.Structure):
+    _fields_ = [("cm_cut_adu", ctypes.c_float), ("zero_thr_kev", ctypes.c_float),
+                ("seed_thr_kev", ctypes.c_float), ("photon_kev", ctypes.c_float),
+                ("cm_min_count", ctypes.c_uint32),
+                ("hist_lo_kev", ctypes.c_float), ("hist_bin_kev", ctypes.c_float),
+                ("hist_bins", ctypes.c_uint32)]
+
+
+class PdOutputs(ctypes.Structure):
+    _fields_ = [("hits", ctypes.c_void_p), ("hit_capacity", ctypes.c_uint32),
+                ("n_hits", ctypes.c_void_p), ("corrected", ctypes.c_void_p),
+                ("cm", ctypes.c_void_p)]
+
+
+class PdInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in
+                ("pixels_per_frame", "units_per_frame", "unit_pixels",
+                 "cm_min_count", "hist_bins", "masked_pixels")]
+
+
+class PdProfile(ctypes.Structure):
+    _fields_ = [("n_kernels", ctypes.c_uint32),
+                ("name", (ctypes.c_char * 32) * 8),
+                ("launches", ctypes.c_uint32 * 8),
+                ("total_ms", ctypes.c_double * 8)]
+
+
+class PdError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        lib = _lib
+        detail = lib.pd_last_error().decode() if lib is not None else ""
+        name = lib.pd_strerror(code).decode() if lib is not None else str(code)
+        super().__init__(f"{where}: {name} ({code}): {detail}")
+
+
+# ---- build & load ----------------------------------------------------------
+def _stale() -> bool:
+    if not os.path.exists(LIB_PATH):
+        return True
+    t = os.path.getmtime(LIB_PATH)
+    deps = [os.path.join(_CSRC, f) for f in os.listdir(_CSRC)]
+    deps += [os.path.join(_INCLUDE, f) for f in os.listdir(_INCLUDE)]
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libpd.so in-tree for sm_103a (translation units in parallel)."""
+    with _lock:
+        if not force and not _stale():
+            return LIB_PATH
+        os.makedirs(_BUILD, exist_ok=True)
+        procs, objs = [], []
+        for src in SOURCES:
+            obj = os.path.join(_BUILD, src.replace(".cu", ".o"))
+            objs.append(obj)
+            cmd = ["nvcc", *ARCH, *NVCC_FLAGS, "-I", _INCLUDE, "-I", _CSRC,
+                   "-c", os.path.join(_CSRC, src), "-o", obj]
+            procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE,
+                                                stderr=subprocess.STDOUT)))
+        for cmd, pr in procs:
+            out, _ = pr.communicate()
+            if pr.returncode:
+                raise RuntimeError("nvcc failed: " + " ".join(cmd) + "\n" +
+                                   out.decode(errors="replace"))
+            if verbose and out:
+                print(out.decode(errors="replace"))
+        tmp = LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["nvcc", *ARCH, "-shared", "-o", tmp, *objs,
+                               "-lcudart"])
+        os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+def _declare(lib):
+    vp, u32, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int
+    sig = {
+        "pd_create": ([ctypes.POINTER(PdGeometry), vp, vp,
+                       ctypes.POINTER(PdThresholds), ctypes.POINTER(vp)], i32),
+        "pd_query": ([vp, ctypes.POINTER(PdInfo)], i32),
+        "pd_process": ([vp, vp, u32, u32, ctypes.POINTER(PdOutputs), vp], i32),
+        "pd_process_host": ([vp, vp, u32, u32, vp, u32,
+                             ctypes.POINTER(u32)], i32),
+        "pd_get_summary": ([vp, vp, vp, vp, vp], i32),
+        "pd_reset_summary": ([vp, vp], i32),
+        "pd_destroy": ([vp], None),
+        "pd_set_profiling": ([vp, i32], i32),
+        "pd_read_profile": ([vp, ctypes.POINTER(PdProfile)], i32),
+        "pd_strerror": ([i32], ctypes.c_char_p),
+        "pd_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+
+
+def load(build_if_missing: bool = True):
+    """Load libpd.so (building it first if needed).  Raises if unavailable."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            pass
+        if build_if_missing:
+            build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpd is not built ({LIB_PATH})")
+        lib = ctypes.CDLL(LIB_PATH)
+        _declare(lib)
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    """Names the shared object exports (read from its dynamic symbol table)."""
+    out = subprocess.check_output(["nm", "-D", "--defined-only", LIB_PATH])
+    return {ln.split()[-1] for ln in out.decode().splitlines() if ln.strip()}
+
+
+def _check(rc, where):
+    if rc != PD_OK:
+        raise PdError(rc, where)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- context ----------------------------------------------------------------
+class Context:
+    """Owns one pd_ctx (device maps and summaries)."""
+
+    def __init__(self, handle, geometry: PdGeometry, thresholds: PdThresholds):
+        self.handle = handle
+        self.geometry = geometry
+        self.thresholds = thresholds
+        self.info = pd_query(self)
+
+    @property
+    def pixels_per_frame(self) -> int:
+        return self.info.pixels_per_frame
+
+    @property
+    def units_per_frame(self) -> int:
+        return self.info.units_per_frame
+
+    def close(self):
+        if self.handle:
+            pd_destroy(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_geometry(n_modules, rows, cols, unit_rows, unit_cols,
+                  cm_mode=PD_CM_MEDIAN) -> PdGeometry:
+    return PdGeometry(n_modules, rows, cols, unit_rows, unit_cols, cm_mode)
+
+
+def make_thresholds(cm_cut_adu, zero_thr_kev, seed_thr_kev, photon_kev,
+                    cm_min_count=0, hist_lo_kev=-4.0, hist_bin_kev=0.05,
+                    hist_bins=1296) -> PdThresholds:
+    return PdThresholds(cm_cut_adu, zero_thr_kev, seed_thr_kev, photon_kev,
+                        cm_min_count, hist_lo_kev, hist_bin_kev, hist_bins)
+
+
+def pd_create(geometry, pedestal, gain, thresholds) -> Context:
+    """geometry / thresholds: PdGeometry / PdThresholds or dicts of fields."""
+    lib = load()
+    if isinstance(geometry, dict):
+        geometry = make_geometry(**geometry)
+    if isinstance(thresholds, dict):
+        thresholds = make_thresholds(**thresholds)
+    ped = np.ascontiguousarray(pedestal, np.float32).reshape(-1)
+    gain = np.ascontiguousarray(gain, np.float32).reshape(-1)
+    npx = geometry.n_modules * geometry.rows * geometry.cols
+    if ped.size != npx or gain.size != npx:
+        raise ValueError("pedestal/gain size does not match the geometry")
+    h = ctypes.c_void_p()
+    _check(lib.pd_create(ctypes.byref(geometry), ped.ctypes.data,
+                         gain.ctypes.data, ctypes.byref(thresholds),
+                         ctypes.byref(h)), "pd_create")
+    return Context(h.value, geometry, thresholds)
+
+
+def pd_query(ctx: Context) -> PdInfo:
+    info = PdInfo()
+    _check(load().pd_query(ctx.handle, ctypes.byref(info)), "pd_query")
+    return info
+
+
+def pd_process(ctx: Context, frames_ptr: int, n_frames: int, frame_base: int,
+               hits_ptr: int, hit_capacity: int, n_hits_ptr: int,
+               corrected_ptr: int | None = None, cm_ptr: int | None = None,
+               stream=None) -> None:
+    """Enqueue the chain on device frames (raw device pointers)."""
+    out = PdOutputs(hits_ptr, hit_capacity, n_hits_ptr, corrected_ptr, cm_ptr)
+    _check(load().pd_process(ctx.handle, frames_ptr, n_frames, frame_base,
+                             ctypes.byref(out), _stream_handle(stream)),
+           "pd_process")
+
+
+def pd_process_host(ctx: Context, frames: np.ndarray, frame_base: int = 0,
+                    hit_capacity: int | None = None, out: np.ndarray | None = None):
+    """Chain on host frames (uint16 [n, ...]); returns (hits, n_hits).
+    PD_EOVERFLOW is reported through n_hits > len(hits), not raised."""
+    lib = load()
+    fr = np.ascontiguousarray(frames)
+    assert fr.dtype == np.uint16
+    n = fr.size // ctx.pixels_per_frame
+    assert n * ctx.pixels_per_frame == fr.size
+    if out is None:
+        cap = hit_capacity if hit_capacity is not None else \
+            max(1024, n * ctx.pixels_per_frame // 16)
+        out = np.empty(cap, HIT_DTYPE)
+    nh = ctypes.c_uint32(0)
+    rc = lib.pd_process_host(ctx.handle, fr.ctypes.data, n, frame_base,
+                             out.ctypes.data, len(out), ctypes.byref(nh))
+    if rc not in (PD_OK, PD_EOVERFLOW):
+        raise PdError(rc, "pd_process_host")
+    return out[:min(nh.value, len(out))], nh.value
+
+
+def pd_get_summary(ctx: Context, stream=None):
+    """(count_map u32 [pixels], hist_pix u64 [bins], hist_hit u64 [bins])."""
+    cm = np.empty(ctx.pixels_per_frame, np.uint32)
+    hp = np.empty(ctx.info.hist_bins, np.uint64)
+    hh = np.empty(ctx.info.hist_bins, np.uint64)
+    _check(load().pd_get_summary(ctx.handle, cm.ctypes.data, hp.ctypes.data,
+                                 hh.ctypes.data, _stream_handle(stream)),
+           "pd_get_summary")
+    return cm, hp, hh
+
+
+def pd_reset_summary(ctx: Context, stream=None) -> None:
+    _check(load().pd_reset_summary(ctx.handle, _stream_handle(stream)),
+           "pd_reset_summary")
+
+
+def pd_destroy(ctx: Context) -> None:
+    if ctx.handle:
+        load().pd_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def pd_set_profiling(ctx: Context, enable: bool) -> None:
+    _check(load().pd_set_profiling(ctx.handle, int(bool(enable))),
+           "pd_set_profiling")
+
+
+def pd_read_profile(ctx: Context) -> dict:
+    """{kernel name: (launches, total device ms)} since the last read."""
+    pr = PdProfile()
+    _check(load().pd_read_profile(ctx.handle, ctypes.byref(pr)),
+           "pd_read_profile")
+    return {pr.name[k].value.decode(): (pr.launches[k], pr.total_ms[k])
+            for k in range(pr.n_kernels) if pr.launches[k]}
+
+
+def pd_strerror(code: int) -> str:
+    return load().pd_strerror(code).decode()
+
+
+# ---- torch-side convenience (allocation only) --------------------------------
+class Outputs:
+    """Device output buffers of one pd_process call, allocated with torch."""
+
+    def __init__(self, ctx: Context, n_frames: int, hit_capacity: int,
+                 corrected: bool = False, cm: bool = False, device="cuda"):
+        import torch
+        self.hits = torch.empty((max(hit_capacity, 1), HIT_DTYPE.itemsize),
+                                dtype=torch.uint8, device=device)
+        self.hit_capacity = hit_capacity
+        self.n_hits = torch.zeros(1, dtype=torch.int32, device=device)
+        self.corrected = torch.empty((n_frames, ctx.pixels_per_frame),
+                                     dtype=torch.float32, device=device) \
+            if corrected else None
+        self.cm = torch.empty((n_frames, ctx.units_per_frame),
+                              dtype=torch.float32, device=device) if cm else None
+
+    def ptrs(self):
+        return dict(hits_ptr=self.hits.data_ptr(), hit_capacity=self.hit_capacity,
+                    n_hits_ptr=self.n_hits.data_ptr(),
+                    corrected_ptr=self.corrected.data_ptr()
+                    if self.corrected is not None else None,
+                    cm_ptr=self.cm.data_ptr() if self.cm is not None else None)
+
+    def hits_host(self):
+        n = int(self.n_hits.item())
+        k = min(n, self.hit_capacity)
+        raw = self.hits[:k].cpu().numpy()
+        return raw.view(HIT_DTYPE).reshape(-1), n
+
+
+def frames_to_device(frames: np.ndarray, device="cuda"):
+    """uint16 frames -> torch int16 tensor on the device (same bits)."""
+    import torch
+    a = np.ascontiguousarray(frames, np.uint16)
+    return torch.from_numpy(a.view(np.int16)).to(device)
+
+
+def process(ctx: Context, frames_dev, hit_capacity: int | None = None,
+            frame_base: int = 0, corrected: bool = False, cm: bool = False,
+            stream=None) -> Outputs:
+    """pd_process on a device tensor of frames; returns the Outputs."""
+    n = frames_dev.numel() // ctx.pixels_per_frame
+    assert n * ctx.pixels_per_frame == frames_dev.numel()
+    cap = hit_capacity if hit_capacity is not None else \
+        max(1024, n * ctx.pixels_per_frame // 4)
+    out = Outputs(ctx, n, cap, corrected, cm, device=frames_dev.device)
+    pd_process(ctx, frames_dev.data_ptr(), n, frame_base, stream=stream,
+               **out.ptrs())
+    return out

@@ -1,0 +1,241 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+The plain chain is bit-exact: hit lists (after sorting by frame and pixel),
+common mode, corrected frames, count map and both histograms must be equal
+bit for bit.  Cases span several 16x64 tiles and ragged tails, row and bank
+common-mode units, units too large to stage in shared memory, empty calls,
+hit-capacity overflow, frame offsets and the host-buffer entry point.  The
+full 2.2 Mpixel batch of 1024 frames runs in the benchmark's configuration
+and is checked on sampled frames plus size-independent properties.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1903_06838_gb300 import pd, synth
+from tests._cases import (expected_cm, expected_hits, load_cases, sort_hits,
+                          sparse_to_dense)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = load_cases()
+
+
+def _ctx(geom: dict, thr: dict, ped, gain):
+    return pd.pd_create(geom, ped, gain, thr)
+
+
+def _oracle(geom: dict, thr: dict, ped, gain, raw, **kw):
+    return oracle.process(oracle.geometry(**geom), oracle.thresholds(**thr),
+                          ped, gain, raw, **kw)
+
+
+def _compare(ctx, out, ref, n_frames, check_corrected=True):
+    hits, n = out.hits_host()
+    assert n == ref.n_hits
+    assert len(hits) == n, "hit capacity too small for a full comparison"
+    assert sort_hits(hits).tobytes() == sort_hits(ref.hits).tobytes()
+    got_cm = out.cm.cpu().numpy()
+    assert got_cm.tobytes() == ref.cm.reshape(n_frames, -1).tobytes()
+    if check_corrected and out.corrected is not None:
+        got = out.corrected.cpu().numpy()
+        assert got.tobytes() == ref.corrected.reshape(n_frames, -1).tobytes()
+    cmap, hp, hh = pd.pd_get_summary(ctx)
+    np.testing.assert_array_equal(cmap, ref.count_map)
+    np.testing.assert_array_equal(hp, ref.hist_pix)
+    np.testing.assert_array_equal(hh, ref.hist_hit)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c["name"] for c in CASES])
+def test_golden_cases_on_gpu(case):
+    geom, thr = case["geometry"], case["thresholds"]
+    ctx = _ctx(geom, thr, case["ped_arr"], case["gain_arr"])
+    dev = pd.frames_to_device(case["raw_arr"])
+    out = pd.process(ctx, dev, hit_capacity=64, corrected=True, cm=True)
+    torch.cuda.synchronize()
+    hits, n = out.hits_host()
+    exp = expected_hits(case)
+    assert n == len(exp)
+    assert sort_hits(hits).tobytes() == exp.tobytes()
+    assert out.cm.cpu().numpy().tobytes() == expected_cm(case).tobytes()
+    cmap, hp, hh = pd.pd_get_summary(ctx)
+    bins = thr["hist_bins"]
+    np.testing.assert_array_equal(hp, sparse_to_dense(case["expect"]["hist_pix"], bins))
+    np.testing.assert_array_equal(hh, sparse_to_dense(case["expect"]["hist_hit"], bins))
+    np.testing.assert_array_equal(
+        cmap, sparse_to_dense(case["expect"]["count_map"], cmap.size, np.uint32))
+
+
+WORKLOADS = {
+    # the 16-frame single-ASIC workload in full
+    "asic_352x384_x16": (synth.asic_352x384(), 16),
+    "cspad_2modules_x4": (synth.cspad_2p2m(n_modules=2), 4),
+    "epix_704x768_x2": (synth.epix_704x768(occupancy=0.02), 2),
+    "asic16_x1": (synth.asic16_352x384(n_modules=3), 1),
+    # ragged against 16x64 tiles; bank units of 37x15
+    "ragged_37x45_banks": (synth.Detector(n_modules=3, rows=37, cols=45 + 3,
+                                          unit_rows=37, unit_cols=16,
+                                          occupancy=0.03), 5),
+    "ragged_rows_odd": (synth.Detector(n_modules=1, rows=19, cols=104,
+                                       unit_rows=1, unit_cols=52,
+                                       occupancy=0.05, cloud_sigma=0.5), 7),
+    # a 65536-pixel unit does not fit in shared memory (global-key path)
+    "big_unit_256x256": (synth.Detector(n_modules=1, rows=256, cols=256,
+                                        unit_rows=256, unit_cols=256,
+                                        occupancy=0.01), 2),
+    "high_occupancy_pileup": (synth.asic_352x384(rows=64, occupancy=0.1,
+                                                 cloud_sigma_hi=0.5,
+                                                 cloud_sigma=0.2), 3),
+}
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_generated_workloads_bit_exact(name):
+    det, n = WORKLOADS[name]
+    ped, gain = synth.maps(det)
+    raw, _ = synth.frames(det, ped, gain, 0, n)
+    geom, thr = det.geometry(), det.thresholds()
+    ctx = _ctx(geom, thr, ped, gain)
+    out = pd.process(ctx, pd.frames_to_device(raw), corrected=True, cm=True)
+    torch.cuda.synchronize()
+    ref = _oracle(geom, thr, ped, gain, raw, want_corrected=True)
+    assert ref.n_hits > 0 or name == "big_unit_256x256"
+    _compare(ctx, out, ref, n)
+
+
+def test_cm_none_and_masked_pixels():
+    det = synth.asic_352x384(rows=32)
+    ped, gain = synth.maps(det)
+    gain.reshape(-1)[::97] = 0.0
+    gain.reshape(-1)[5] = -1.0
+    raw, _ = synth.frames(det, ped, gain, 0, 3)
+    geom = dict(det.geometry(), cm_mode=pd.PD_CM_NONE)
+    thr = det.thresholds()
+    ctx = _ctx(geom, thr, ped, gain)
+    assert ctx.info.masked_pixels == len(range(0, gain.size, 97)) + 1
+    out = pd.process(ctx, pd.frames_to_device(raw), corrected=True, cm=True)
+    torch.cuda.synchronize()
+    ref = _oracle(dict(geom), thr, ped, gain, raw, want_corrected=True)
+    _compare(ctx, out, ref, 3)
+
+
+def test_empty_call_zeroes_count():
+    det = synth.asic_352x384(rows=16)
+    ped, gain = synth.maps(det)
+    ctx = _ctx(det.geometry(), det.thresholds(), ped, gain)
+    out = pd.Outputs(ctx, 0, 8)
+    out.n_hits.fill_(1234)
+    dummy = torch.zeros(8, dtype=torch.int16, device="cuda")
+    pd.pd_process(ctx, dummy.data_ptr(), 0, 0, **out.ptrs())
+    torch.cuda.synchronize()
+    assert int(out.n_hits.item()) == 0
+    cmap, hp, hh = pd.pd_get_summary(ctx)
+    assert cmap.sum() == 0 and hp.sum() == 0 and hh.sum() == 0
+
+
+def test_hit_capacity_overflow_keeps_true_count():
+    det = synth.asic_352x384(rows=64, occupancy=0.03)
+    ped, gain = synth.maps(det)
+    raw, _ = synth.frames(det, ped, gain, 0, 2)
+    ctx = _ctx(det.geometry(), det.thresholds(), ped, gain)
+    ref = _oracle(det.geometry(), det.thresholds(), ped, gain, raw)
+    cap = ref.n_hits // 3
+    out = pd.process(ctx, pd.frames_to_device(raw), hit_capacity=cap)
+    torch.cuda.synchronize()
+    hits, n = out.hits_host()
+    assert n == ref.n_hits and len(hits) == cap
+    ref_set = {h.tobytes() for h in ref.hits}
+    assert all(h.tobytes() in ref_set for h in hits)
+    assert len({h.tobytes() for h in hits}) == cap
+
+
+def test_frame_base_and_accumulation_over_calls():
+    det = synth.cspad_2p2m(n_modules=1)
+    ped, gain = synth.maps(det)
+    raw, _ = synth.frames(det, ped, gain, 0, 5)
+    geom, thr = det.geometry(), det.thresholds()
+    ctx = _ctx(geom, thr, ped, gain)
+    dev = pd.frames_to_device(raw)
+    a = pd.process(ctx, dev[:2])
+    b = pd.process(ctx, dev[2:], frame_base=2)
+    torch.cuda.synchronize()
+    ref = _oracle(geom, thr, ped, gain, raw)
+    ha, _ = a.hits_host()
+    hb, _ = b.hits_host()
+    got = sort_hits(np.concatenate([ha, hb]))
+    assert got.tobytes() == sort_hits(ref.hits).tobytes()
+    cmap, hp, hh = pd.pd_get_summary(ctx)
+    np.testing.assert_array_equal(cmap, ref.count_map)
+    np.testing.assert_array_equal(hp, ref.hist_pix)
+    np.testing.assert_array_equal(hh, ref.hist_hit)
+    pd.pd_reset_summary(ctx)
+    cmap, hp, hh = pd.pd_get_summary(ctx)
+    assert cmap.sum() == 0 and hp.sum() == 0 and hh.sum() == 0
+
+
+def test_host_buffer_entry_point():
+    det = synth.epix_704x768()
+    ped, gain = synth.maps(det)
+    raw, _ = synth.frames(det, ped, gain, 0, 150)  # > one 64 MB chunk
+    geom, thr = det.geometry(), det.thresholds()
+    ctx = _ctx(geom, thr, ped, gain)
+    hits, n = pd.pd_process_host(ctx, raw, frame_base=10)
+    sample = [0, 77, 149]
+    ref = _oracle(geom, thr, ped, gain, raw[sample])
+    got = hits[np.isin(hits["frame"], [10 + s for s in sample])]
+    exp = ref.hits.copy()
+    exp["frame"] = np.array([10 + sample[f] for f in ref.hits["frame"]], np.uint32)
+    assert sort_hits(got).tobytes() == sort_hits(exp).tobytes()
+    assert n == len(hits)
+    # overflow through the host path reports the true count
+    small, n2 = pd.pd_process_host(ctx, raw[:3], hit_capacity=10)
+    assert len(small) == 10 and n2 > 10
+
+
+def test_invalid_arguments_rejected():
+    det = synth.asic_352x384(rows=16)
+    ped, gain = synth.maps(det)
+    bad = dict(det.geometry(), unit_cols=100)
+    with pytest.raises(pd.PdError) as ei:
+        pd.pd_create(bad, ped, gain, det.thresholds())
+    assert ei.value.code == pd.PD_EINVAL
+    bad_thr = dict(det.thresholds(), zero_thr_kev=2.0, seed_thr_kev=1.0)
+    with pytest.raises(pd.PdError):
+        pd.pd_create(det.geometry(), ped, gain, bad_thr)
+    ctx = _ctx(det.geometry(), det.thresholds(), ped, gain)
+    out = pd.Outputs(ctx, 1, 8)
+    buf = torch.zeros(ctx.pixels_per_frame + 8, dtype=torch.int16, device="cuda")
+    with pytest.raises(pd.PdError) as ei:
+        pd.pd_process(ctx, buf.data_ptr() + 2, 1, 0, **out.ptrs())
+    assert ei.value.code == pd.PD_EALIGN
+
+
+def test_full_size_cspad_batch_sampled():
+    """1024 frames of the 32x185x388 geometry in one call (the benchmark's
+    launch): sampled frames equal the oracle bit for bit, and the summaries
+    obey size-independent identities."""
+    det = synth.cspad_2p2m()
+    ped, gain = synth.maps(det)
+    n = 1024
+    raw, _ = synth.frames(det, ped, gain, 0, n, truth=False)
+    geom, thr = det.geometry(), det.thresholds()
+    ctx = _ctx(geom, thr, ped, gain)
+    dev = pd.frames_to_device(raw)
+    out = pd.process(ctx, dev, hit_capacity=n * 16384, cm=True)
+    torch.cuda.synchronize()
+    hits, nh = out.hits_host()
+    assert nh == len(hits) > 0
+    cm_all = out.cm.cpu().numpy()
+    cmap, hp, hh = pd.pd_get_summary(ctx)
+    assert hp.sum() == n * det.pixels_per_frame
+    assert hh.sum() >= nh
+    assert int(cmap.astype(np.int64).sum()) == int(hits["count"].astype(np.int64).sum())
+    for f in (0, 1, 517, n - 1):
+        ref = _oracle(geom, thr, ped, gain, raw[f:f + 1])
+        mine = hits[hits["frame"] == f].copy()
+        mine["frame"] = 0
+        assert sort_hits(mine).tobytes() == sort_hits(ref.hits).tobytes()
+        assert cm_all[f].tobytes() == ref.cm.reshape(-1).tobytes()
