@@ -48,8 +48,13 @@
  *     dx = Mx / E, dy = My / E, in pixel pitches from the seed centre.
  *  9. Summaries (section "Summarization"): count_map[seed] += n for every
  *     hit; hist_pix[bin(e)] += 1 for every pixel; hist_hit[bin(E)] += 1 for
- *     every seed, where bin(v) = floor((v - lo) * inv_w), inv_w = 1.0f /
- *     width, clipped to [0, bins-1] (NaN -> 0).
+ *     every seed.  The paper does not define its bins; here bin b covers
+ *     [lo + b*width, lo + (b+1)*width) in the sense bin(v) = floor(t) with
+ *     t = fmaf(v, inv_w, -lo_s), inv_w = 1.0f / width and lo_s = lo * inv_w
+ *     (each rounded to nearest once; fmaf rounds once), clipped to
+ *     [0, bins-1].
+ *
+ * Inputs must be finite (pedestal finite; non-finite gains are masked).
  */
 #include <math.h>
 #include <stdint.h>
@@ -101,8 +106,8 @@ uint32_t oracle_default_min_count(uint32_t unit_pixels) {
     return ceil_sqrt(unit_pixels);
 }
 
-static uint32_t bin_of(float v, float lo, float inv_w, uint32_t bins) {
-    float t = (v - lo) * inv_w;
+static uint32_t bin_of(float v, float lo_s, float inv_w, uint32_t bins) {
+    const float t = fmaf(v, inv_w, -lo_s);
     if (!(t >= 0.0f)) return 0;
     if (t >= (float)bins) return bins - 1;
     return (uint32_t)t; /* truncation == floor for t >= 0 */
@@ -162,6 +167,7 @@ int oracle_process(const og_geometry* g, const og_thresholds* t,
     const uint32_t n_min =
         t->cm_min_count ? t->cm_min_count : ceil_sqrt(unit_px);
     const float inv_w = 1.0f / t->hist_bin_kev;
+    const float lo_s = t->hist_lo_kev * inv_w;
 
     float* inv_gain = (float*)malloc(fpx * sizeof(float));
     float* d = (float*)malloc(mpx * sizeof(float));
@@ -174,6 +180,10 @@ int oracle_process(const og_geometry* g, const og_thresholds* t,
         return 1;
     }
     for (size_t p = 0; p < fpx; p++) {
+        if (!isfinite(ped[p])) {
+            free(inv_gain); free(d); free(e); free(s); free(set); free(cmu);
+            return 1;
+        }
         const float gp = gain[p];
         inv_gain[p] = (gp > 0.0f && isfinite(gp)) ? 1.0f / gp : 0.0f;
     }
@@ -218,7 +228,7 @@ int oracle_process(const og_geometry* g, const og_thresholds* t,
                     const float ev = cc * inv_gain[base + p];
                     e[p] = ev;
                     s[p] = ev > t->zero_thr_kev ? ev : 0.0f;
-                    hist_pix[bin_of(ev, t->hist_lo_kev, inv_w, t->hist_bins)]++;
+                    hist_pix[bin_of(ev, lo_s, inv_w, t->hist_bins)]++;
                     if (corrected) corrected[(size_t)f * fpx + base + p] = ev;
                 }
             }
@@ -259,7 +269,7 @@ int oracle_process(const og_geometry* g, const og_thresholds* t,
                         }
                     }
                     ns++;
-                    hist_hit[bin_of(E, t->hist_lo_kev, inv_w, t->hist_bins)]++;
+                    hist_hit[bin_of(E, lo_s, inv_w, t->hist_bins)]++;
                     const float q = E / t->photon_kev;
                     const float qr = nearbyintf(q);
                     uint32_t n;

@@ -441,7 +441,8 @@ def test_summary_totals(name):
 
 
 def test_histogram_bins_and_clipping():
-    """bin(v) = floor((v - lo) * (1/width)), end bins clipped."""
+    """bin(v) = floor(fma(v, 1/width, -lo/width)), end bins clipped (here all
+    operands are dyadic, so t = 2e + 4 exactly)."""
     C = 8
     g = _geom(n_modules=1, rows=1, cols=C, unit_rows=1, unit_cols=C,
               cm_mode=oracle.CM_NONE)
@@ -456,7 +457,7 @@ def test_histogram_bins_and_clipping():
     exp = np.zeros(10, np.uint64)
     inv_w = np.float32(1) / np.float32(0.5)
     for e in (-3, -2, -1.75, 0, 0.5, 2.49, 2.5, 40):
-        tt = (np.float32(e) - np.float32(-2)) * inv_w
+        tt = float(np.float32(e)) * float(inv_w) + 4.0
         exp[int(min(max(math.floor(tt), 0), 9))] += 1
     np.testing.assert_array_equal(r.hist_pix, exp)
     assert list(np.nonzero(r.hist_pix)[0]) == [0, 4, 5, 8, 9]
