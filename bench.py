@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--frames", type=int, default=FRAMES_PER_STEP)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--band-rows", type=int, default=0)
+    ap.add_argument("--no-overlap", action="store_true")
     return ap.parse_args()
 
 
@@ -206,6 +209,8 @@ def run_pd(args):
     synth.frames(det, ped, gain, rank * nf, nf, truth=False, out=raw)
     frames = host.to(dev, non_blocking=False)
     ctx = pd.pd_create(det.geometry(), ped, gain, det.thresholds())
+    if args.chunk or args.band_rows or args.no_overlap:
+        pd.pd_set_tuning(ctx, args.chunk, args.band_rows, 0 if args.no_overlap else 1)
     cap = nf * 16384
     out = pd.Outputs(ctx, nf, cap, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -254,7 +259,7 @@ def run_pd(args):
     cm_b = nf * ctx.units_per_frame * 4
     # algorithmic bytes of one launch of each kernel
     kernel_bytes = {
-        "cm_select": raw_b + maps_b + cm_b,
+        "common_mode": raw_b + maps_b + cm_b,
         "stencil": raw_b + 2 * maps_b + cm_b + hits_b + cmap_b,
         "fused_chain": raw_b + 2 * maps_b + hits_b + cmap_b,
     }
@@ -262,14 +267,16 @@ def run_pd(args):
     roof = None
     if dom:
         name, (launches, tot) = dom
-        per_launch_ms = tot / launches
-        b = kernel_bytes.get(name, raw_b)
-        ach = b / (per_launch_ms / 1e3) / 1e9
+        # algorithmic bytes of all of the kernel's launches in the timed
+        # region over their summed device time
+        b = kernel_bytes.get(name, raw_b) * args.steps
+        ach = b / (tot / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
                 "peak_kind": f"{peak_kind} copy bandwidth (burst)",
-                "traffic": None, "bytes_per_launch": int(b),
-                "ms_per_launch": per_launch_ms,
+                "traffic": None, "bytes_per_step": int(b / args.steps),
+                "launches_per_step": launches / args.steps,
+                "ms_per_launch": tot / launches,
                 "kernel_share": {k: round(v[1] / sum(x[1] for x in prof.values()), 4)
                                  for k, v in prof.items()}}
     launches_per_step = sum(v[0] for v in prof.values()) / max(args.steps, 1) if prof else 0
@@ -279,7 +286,7 @@ def run_pd(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(det, nf),
+        "config": dict(workload_config(det, nf), tuning=pd.pd_get_tuning(ctx)),
         "pixels_per_s": fps * fpx,
         "chain_hbm_gbs": round(chain_bytes * ws / (ms_step / 1e3) / 1e9, 1),
         "chain_frac_of_peak": round(chain_bytes * ws / (ms_step / 1e3) / 1e9 / peak, 4),

@@ -116,7 +116,7 @@ typedef struct {
     pd_hit* hits;          /* hit_capacity records; order is unspecified     */
     uint32_t hit_capacity;
     uint32_t* n_hits;      /* 1 x u32: set to the call's true hit count      */
-    float* corrected;      /* [n_frames][pixels] e (keV) or NULL             */
+    float* corrected;      /* [n_frames][pixels] e (keV) or NULL; 16-B aligned */
     float* cm;             /* [n_frames][units]  common mode (ADU) or NULL   */
 } pd_outputs;
 
@@ -136,7 +136,8 @@ typedef struct {
  * gain maps (host float32 [n_modules][rows][cols]; pedestal in ADU, gain in
  * ADU/keV) to the device, and compute inv_gain = 1.0f / gain there-from on
  * the host (round to nearest; gain <= 0 or non-finite -> inv_gain = 0, the
- * pixel is masked).  Allocates the context's device state: maps, photon
+ * pixel is masked; a non-finite pedestal is PD_EINVAL).  Allocates the
+ * context's device state: maps, photon
  * count map (u32 per pixel) and two u64 histograms, all zeroed.  The device
  * is the current CUDA device.  On failure *out is NULL. */
 int pd_create(const pd_geometry* geometry, const float* pedestal_host,
@@ -181,6 +182,22 @@ int pd_reset_summary(pd_ctx* ctx, void* stream);
 /* pd_destroy — free the context's device state (NULL is a no-op).  Waits
  * for the device to finish work that may use it. */
 void pd_destroy(pd_ctx* ctx);
+
+/* Launch tuning of a context (the autotuner's search space).  Zero fields
+ * keep the current value.  chunk_frames: frames per common-mode/stencil
+ * launch pair (a chunk's raw frames are re-read from L2 by the second
+ * pass); band_rows: rows per stencil tile; overlap: 1 runs the common mode
+ * of the next chunk on a second stream beside the stencil of the current
+ * one.  Results never depend on tuning. */
+typedef struct {
+    uint32_t chunk_frames;
+    uint32_t band_rows;
+    uint32_t overlap;
+    uint32_t reserved;
+} pd_tuning;
+
+int pd_get_tuning(const pd_ctx* ctx, pd_tuning* tuning);
+int pd_set_tuning(pd_ctx* ctx, const pd_tuning* tuning);
 
 /* Kernel timing.  When enabled on a context, every kernel the context
  * launches is bracketed by CUDA events recorded on the launching stream;

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "pd.h"
+#include "pd_fast.cuh"
 #include "pd_internal.cuh"
 
 namespace {
@@ -40,10 +41,19 @@ struct pd_ctx {
     pd_geometry geom;
     pd_thresholds thr;
     pd::ChainParams params;
+    pd::CmBigConfig cm_cfg;
+    pd::BandConfig band_cfg;
+    bool use_cm_big = false, use_band = false;
+    uint32_t chunk_frames = 1;  // frames per common-mode/stencil launch pair
+    uint32_t overlap = 1;       // common mode of chunk c+1 beside stencil of c
+    cudaStream_t aux = nullptr; // second stream of the chunk pipeline
+    cudaEvent_t ev_fork = nullptr, ev_cm[2] = {nullptr, nullptr};
+    cudaEvent_t ev_st[2] = {nullptr, nullptr};
     int device = 0;
     uint32_t masked = 0;
     // device state
     float* d_ped = nullptr;
+    float* d_nped = nullptr;
     float* d_inv_gain = nullptr;
     uint32_t* d_count_map = nullptr;
     unsigned long long* d_hist_pix = nullptr;
@@ -68,7 +78,7 @@ struct pd_ctx {
 
 namespace {
 
-const char* const kKernelNames[] = {"cm_select", "stencil", "fused_chain"};
+const char* const kKernelNames[] = {"common_mode", "stencil", "fused_chain"};
 constexpr int kNumKernelNames = 3;
 
 cudaEvent_t take_event(pd_ctx* c) {
@@ -165,6 +175,7 @@ uint32_t ceil_sqrt_u32(uint32_t n) {
 void free_ctx(pd_ctx* c) {
     if (!c) return;
     cudaFree(c->d_ped);
+    cudaFree(c->d_nped);
     cudaFree(c->d_inv_gain);
     cudaFree(c->d_count_map);
     cudaFree(c->d_hist_pix);
@@ -178,6 +189,12 @@ void free_ctx(pd_ctx* c) {
         if (c->hstream[i]) cudaStreamDestroy(c->hstream[i]);
     for (int i = 0; i < 4; i++)
         if (c->hevent[i]) cudaEventDestroy(c->hevent[i]);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    for (int i = 0; i < 2; i++) {
+        if (c->ev_cm[i]) cudaEventDestroy(c->ev_cm[i]);
+        if (c->ev_st[i]) cudaEventDestroy(c->ev_st[i]);
+    }
     for (auto& m : c->marks) {
         cudaEventDestroy(m.a);
         cudaEventDestroy(m.b);
@@ -213,17 +230,49 @@ int run_chain(pd_ctx* c, const uint16_t* frames, uint32_t n_frames, uint32_t fra
         if (rc) return rc;
         cm = c->d_cm;
     }
-    {
-        ProfileScope ps(c, 0, s);
-        e = pd::launch_cm_select(c->params, frames, n_frames, cm, s);
+    // Frames go in chunks sized so raw stays resident in L2 between the
+    // common-mode pass and the stencil pass that re-reads it.  With overlap,
+    // the common mode of chunk c+1 runs on the auxiliary stream beside the
+    // stencil of chunk c (and waits for the stencil of chunk c-1), so at most
+    // two chunks are in flight.
+    const bool two = c->overlap && n_frames > c->chunk_frames;
+    cudaStream_t sc = s;
+    if (two) {
+        if ((e = cudaEventRecord(c->ev_fork, s)) || (e = cudaStreamWaitEvent(c->aux, c->ev_fork, 0)))
+            return fail_cuda(e, "chunk pipeline fork");
+        sc = c->aux;
     }
-    if (e != cudaSuccess) return fail_cuda(e, "common-mode kernel launch");
-    pd::CallOut co{out->hits, out->hit_capacity, out->n_hits, out->corrected, cm};
-    {
-        ProfileScope ps(c, 1, s);
-        e = pd::launch_stencil(c->params, frames, n_frames, frame_base, co, s);
+    uint32_t k = 0;
+    for (uint32_t done = 0; done < n_frames; k++) {
+        const uint32_t nf = std::min(c->chunk_frames, n_frames - done);
+        const uint16_t* fr = frames + (size_t)done * c->params.frame_px;
+        float* cmc = cm + (size_t)done * c->params.units_per_frame;
+        if (two && k >= 2 && (e = cudaStreamWaitEvent(sc, c->ev_st[k & 1], 0)))
+            return fail_cuda(e, "chunk pipeline wait");
+        {
+            ProfileScope ps(c, 0, sc);
+            e = c->use_cm_big ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, cmc, sc)
+                              : pd::launch_cm_select(c->params, fr, nf, cmc, sc);
+        }
+        if (e != cudaSuccess) return fail_cuda(e, "common-mode kernel launch");
+        if (two && ((e = cudaEventRecord(c->ev_cm[k & 1], sc)) ||
+                    (e = cudaStreamWaitEvent(s, c->ev_cm[k & 1], 0))))
+            return fail_cuda(e, "chunk pipeline join");
+        pd::CallOut co{out->hits, out->hit_capacity, out->n_hits,
+                       out->corrected ? out->corrected + (size_t)done * c->params.frame_px
+                                      : nullptr,
+                       cmc};
+        {
+            ProfileScope ps(c, 1, s);
+            e = c->use_band ? pd::launch_stencil_band(c->params, c->band_cfg, fr, nf,
+                                                      frame_base + done, co, s)
+                            : pd::launch_stencil(c->params, fr, nf, frame_base + done, co, s);
+        }
+        if (e != cudaSuccess) return fail_cuda(e, "stencil kernel launch");
+        if (two && (e = cudaEventRecord(c->ev_st[k & 1], s)))
+            return fail_cuda(e, "chunk pipeline record");
+        done += nf;
     }
-    if (e != cudaSuccess) return fail_cuda(e, "stencil kernel launch");
     return PD_OK;
 }
 
@@ -283,11 +332,26 @@ int pd_create(const pd_geometry* geometry, const float* pedestal_host,
     p.zero_thr = thresholds->zero_thr_kev;
     p.seed_thr = thresholds->seed_thr_kev;
     p.photon_kev = thresholds->photon_kev;
-    p.hist_lo = thresholds->hist_lo_kev;
     p.hist_inv_w = 1.0f / thresholds->hist_bin_kev;
+    p.hist_neg_lo_s = -(thresholds->hist_lo_kev * p.hist_inv_w);
     p.hist_bins = thresholds->hist_bins;
 
+    c->cm_cfg = pd::make_cm_big_config(p);
+    c->use_cm_big = g.cm_mode == PD_CM_MEDIAN && pd::cm_big_supported(p, c->cm_cfg);
+    c->band_cfg = pd::make_band_config(p);
+    c->use_band = c->band_cfg.ok;
+    {
+        const size_t fbytes = (size_t)p.frame_px * 2;
+        const size_t target = 96u << 20;  // raw bytes per chunk (measured best)
+        c->chunk_frames = (uint32_t)std::max<size_t>(1, target / fbytes);
+    }
+
     const size_t fpx = p.frame_px;
+    for (size_t i = 0; i < fpx; i++)
+        if (!isfinite(pedestal_host[i])) {
+            free_ctx(c);
+            return fail(PD_EINVAL, "pedestal values must be finite");
+        }
     std::vector<float> inv(fpx);
     uint32_t masked = 0;
     for (size_t i = 0; i < fpx; i++) {
@@ -301,7 +365,10 @@ int pd_create(const pd_geometry* geometry, const float* pedestal_host,
     }
     c->masked = masked;
     cudaError_t e;
+    std::vector<float> nped(fpx);
+    for (size_t i = 0; i < fpx; i++) nped[i] = -pedestal_host[i];
     if ((e = cudaMalloc(&c->d_ped, fpx * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_nped, fpx * 4)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_inv_gain, fpx * 4)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_count_map, fpx * 4)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_hist_pix, p.hist_bins * 8)) != cudaSuccess ||
@@ -310,6 +377,7 @@ int pd_create(const pd_geometry* geometry, const float* pedestal_host,
         return fail(PD_ENOMEM, "device allocation failed in pd_create");
     }
     if ((e = cudaMemcpy(c->d_ped, pedestal_host, fpx * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->d_nped, nped.data(), fpx * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->d_inv_gain, inv.data(), fpx * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemset(c->d_count_map, 0, fpx * 4)) ||
         (e = cudaMemset(c->d_hist_pix, 0, p.hist_bins * 8)) ||
@@ -317,7 +385,17 @@ int pd_create(const pd_geometry* geometry, const float* pedestal_host,
         free_ctx(c);
         return fail_cuda(e, "pd_create upload");
     }
+    if ((e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&c->ev_cm[0], cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&c->ev_cm[1], cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&c->ev_st[0], cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&c->ev_st[1], cudaEventDisableTiming))) {
+        free_ctx(c);
+        return fail_cuda(e, "pd_create streams");
+    }
     p.ped = c->d_ped;
+    p.nped = c->d_nped;
     p.inv_gain = c->d_inv_gain;
     p.count_map = c->d_count_map;
     p.hist_pix = c->d_hist_pix;
@@ -346,8 +424,8 @@ int pd_process(pd_ctx* c, const uint16_t* frames_dev, uint32_t n_frames,
     if (!aligned(frames_dev, 16)) return fail(PD_EALIGN, "frames must be 16-byte aligned");
     if (!aligned(out->n_hits, 4) || !aligned(out->hits, 8))
         return fail(PD_EALIGN, "hit buffers misaligned");
-    if ((out->corrected && !aligned(out->corrected, 4)) || (out->cm && !aligned(out->cm, 4)))
-        return fail(PD_EALIGN, "float outputs must be 4-byte aligned");
+    if ((out->corrected && !aligned(out->corrected, 16)) || (out->cm && !aligned(out->cm, 4)))
+        return fail(PD_EALIGN, "corrected must be 16-byte and cm 4-byte aligned");
     return run_chain(c, frames_dev, n_frames, frame_base, out, (cudaStream_t)stream);
 }
 
@@ -469,6 +547,31 @@ int pd_reset_summary(pd_ctx* c, void* stream) {
         (e = cudaMemsetAsync(c->d_hist_pix, 0, (size_t)c->params.hist_bins * 8, s)) ||
         (e = cudaMemsetAsync(c->d_hist_hit, 0, (size_t)c->params.hist_bins * 8, s)))
         return fail_cuda(e, "summary reset");
+    return PD_OK;
+}
+
+int pd_get_tuning(const pd_ctx* c, pd_tuning* t) {
+    if (!c || !t) return fail(PD_EINVAL, "NULL argument");
+    t->chunk_frames = c->chunk_frames;
+    t->band_rows = c->use_band ? c->band_cfg.rb : 0;
+    t->overlap = c->overlap;
+    t->reserved = 0;
+    return PD_OK;
+}
+
+int pd_set_tuning(pd_ctx* c, const pd_tuning* t) {
+    if (!c || !t) return fail(PD_EINVAL, "NULL argument");
+    if (t->chunk_frames) c->chunk_frames = t->chunk_frames;
+    if (t->band_rows && c->use_band) {
+        const uint32_t rb = std::min(t->band_rows, c->params.rows);
+        if (pd::band_smem_bytes(c->params, rb, c->band_cfg.pitch) > 200 * 1024)
+            return fail(PD_EINVAL, "band too tall for shared memory");
+        if (((rb + 2 + c->band_cfg.ty - 1) / c->band_cfg.ty) * c->band_cfg.vec > 64)
+            return fail(PD_EINVAL, "band too tall for the per-thread candidate mask");
+        c->band_cfg.rb = rb;
+        c->band_cfg.n_bands = (c->params.rows + rb - 1) / rb;
+    }
+    c->overlap = t->overlap ? 1 : 0;
     return PD_OK;
 }
 

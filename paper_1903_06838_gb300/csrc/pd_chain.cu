@@ -33,9 +33,9 @@ __device__ __forceinline__ float key_value(uint32_t k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
-__device__ __forceinline__ uint32_t hist_bin(float v, float lo, float inv_w,
+__device__ __forceinline__ uint32_t hist_bin(float v, float neg_lo_s, float inv_w,
                                              uint32_t bins) {
-    const float t = __fmul_rn(__fsub_rn(v, lo), inv_w);
+    const float t = __fmaf_rn(v, inv_w, neg_lo_s);
     if (!(t >= 0.0f)) return 0;
     if (t >= (float)bins) return bins - 1;
     return (uint32_t)t;  // truncation == floor for t >= 0
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kStThreads)
                 const float e = __fmul_rn(__fsub_rn(d, cm), p.inv_gain[mod_base + off]);
                 s = e > p.zero_thr ? e : 0.0f;
                 if (hr >= 1 && hr <= kTY && hc >= 1 && hc <= kTX) {
-                    atomicAdd(&hpix[hist_bin(e, p.hist_lo, p.hist_inv_w, p.hist_bins)], 1u);
+                    atomicAdd(&hpix[hist_bin(e, p.hist_neg_lo_s, p.hist_inv_w, p.hist_bins)], 1u);
                     if (out.corrected)
                         out.corrected[(size_t)f * p.frame_px + mod_base + off] = e;
                 }
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kStThreads)
                                 My = __fadd_rn(My, __fmul_rn(sq, (float)dy));
                                 npix += sq > 0.0f;
                             }
-                        atomicAdd(&hhit[hist_bin(E, p.hist_lo, p.hist_inv_w, p.hist_bins)], 1u);
+                        atomicAdd(&hhit[hist_bin(E, p.hist_neg_lo_s, p.hist_inv_w, p.hist_bins)], 1u);
                         const float qr = rintf(__fdiv_rn(E, p.photon_kev));
                         uint16_t flags = 0;
                         if (!(qr >= 0.0f)) {

@@ -1,0 +1,892 @@
+// pd_fast.cu — throughput kernels of the chain.
+//
+//   cm_big_kernel      common mode of one large unit (a bank of thousands of
+//                      pixels) per CTA (paper section "Common Mode", Fig. c;
+//                      the estimator is the lower median over d < cut).
+//                      Pass A histograms d into 4096 bins of 1/8 ADU whose
+//                      window [cut - 512, cut) ends exactly at the cut, keeping
+//                      every pixel's 16-bit bin code in shared memory.  The
+//                      bin holding rank floor((n-1)/2) is found by a scan;
+//                      pass B gathers that bin's pixels (recomputing their d
+//                      from L2-resident raw and pedestal) and an exact radix
+//                      select over them gives the median.  When the median
+//                      falls in the window's open-ended bottom bin, or the
+//                      bin holds more candidates than the buffer, the CTA
+//                      selects over the whole unit instead (same result).
+//   stencil_band_kernel  dark, common mode, gain (Fig. b), zeroing, 3x3 local
+//                      maximum, charge sum, count (Fig. e), centroid (Fig. f),
+//                      hits and summaries for a band of full-width rows of a
+//                      module.  Each thread owns one 4-pixel column chunk for
+//                      all rows of the band, so its unit/column bookkeeping is
+//                      computed once.  The zeroed signal of the band and its
+//                      two halo rows is staged in shared memory; seed
+//                      candidates are compacted into a list before the 3x3
+//                      work.
+//
+// Bin codes use the floor-by-magic-number identity: for |t| < 2^22,
+// fadd_rd(t, 1.5*2^23) has bit pattern 0x4B400000 + floor(t), and a fused
+// multiply-add rounded down computes floor(8*(d - lo)) exactly when 8*lo is an
+// integer (8*d is exact).  All arithmetic on values that reach an output is
+// round-to-nearest in the chain's order (compiled with --fmad=false).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pd_fast.cuh"
+
+namespace pd {
+
+namespace {
+
+constexpr uint32_t kSent = 0xFFFFFFFFu;
+constexpr uint32_t kMagicBits = 0x4B400000u;  // bit pattern of 1.5 * 2^23
+constexpr float kMagic = 12582912.0f;         // 1.5 * 2^23
+
+__device__ __forceinline__ uint32_t order_key(float v) {
+    const uint32_t b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_value(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// Exact float of a 16-bit raw value: 2^23 + raw has the raw value as its low
+// mantissa bits; subtracting 2^23 is exact.
+__device__ __forceinline__ float raw_lo(uint32_t x) {
+    return __fsub_rn(__uint_as_float(__byte_perm(x, 0x4B00u, 0x5410u)), 8388608.0f);
+}
+__device__ __forceinline__ float raw_hi(uint32_t x) {
+    return __fsub_rn(__uint_as_float(__byte_perm(x, 0x4B00u, 0x5432u)), 8388608.0f);
+}
+
+// Histogram bin of the summaries: floor(fma(v, inv_w, -lo_s)) clipped to
+// [0, bins-1], as the code of an element of a 32-bit histogram array.
+__device__ __forceinline__ uint32_t summary_bin(float v, float inv_w, float neg_lo_s,
+                                                int max_bits) {
+    const float t = __fmaf_rn(v, inv_w, neg_lo_s);
+    int b = __float_as_int(__fadd_rd(t, kMagic));
+    b = max(b, (int)kMagicBits);
+    b = min(b, max_bits);
+    return (uint32_t)(b - (int)kMagicBits);
+}
+
+// Two raw values of a packed pair as exact floats (2^23 + raw, minus 2^23).
+__device__ __forceinline__ float2 raw_pair(uint32_t x) {
+    const float2 biased = make_float2(__uint_as_float(__byte_perm(x, 0x4B00u, 0x5410u)),
+                                      __uint_as_float(__byte_perm(x, 0x4B00u, 0x5432u)));
+    return __fadd2_rn(biased, make_float2(-8388608.0f, -8388608.0f));
+}
+
+// Common-mode bin code of d: floor(8 * (d - lo)) clipped below at 0 and
+// above at 0xFFFF; codes >= kCmBins mean d >= cut (anchored window).
+__device__ __forceinline__ uint32_t cm_code(float d, float magic_w) {
+    int b = __float_as_int(__fmaf_rd(d, 8.0f, magic_w));
+    b = max(b, (int)kMagicBits);
+    b = min(b, (int)(kMagicBits + 0xFFFFu));
+    return (uint32_t)(b - (int)kMagicBits);
+}
+
+// Asynchronous 4-byte global -> shared copy (no register staging), and the
+// wait for all of this thread's copies.
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide exact radix select: the element of rank `rank` (0-based,
+// ascending) among the keys key_at(i), i < count, that are not kSent.
+// hist256: 256 words of shared memory.  All threads must call it.
+template <class KeyFn>
+__device__ uint32_t block_radix_select(KeyFn key_at, uint32_t count, uint32_t rank,
+                                       uint32_t* hist256, uint32_t* s_prefix,
+                                       uint32_t* s_rank) {
+    const uint32_t nthr = blockDim.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        *s_prefix = 0;
+        *s_rank = rank;
+    }
+    for (int pass = 0; pass < 4; pass++) {
+        const int shift = 24 - 8 * pass;
+        for (uint32_t b = tid; b < 256; b += nthr) hist256[b] = 0;
+        __syncthreads();
+        const uint32_t prefix = *s_prefix;
+        for (uint32_t i = tid; i < count; i += nthr) {
+            const uint32_t k = key_at(i);
+            if (k == kSent) continue;
+            if (pass > 0 && (k >> (shift + 8)) != prefix) continue;
+            atomicAdd(&hist256[(k >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t loc[8], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                loc[j] = hist256[lane * 8 + j];
+                sum += loc[j];
+            }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const uint32_t excl = incl - sum;
+            const uint32_t r = *s_rank;
+            if (excl <= r && r < incl) {
+                uint32_t below = excl;
+                int digit = lane * 8;
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    if (below + loc[j] > r) {
+                        digit = lane * 8 + j;
+                        break;
+                    }
+                    below += loc[j];
+                }
+                *s_prefix = (prefix << 8) | (uint32_t)digit;
+                *s_rank = r - below;
+            }
+        }
+        __syncthreads();
+    }
+    return *s_prefix;
+}
+
+// Block-wide exclusive prefix sum of one value per thread; *s_total gets the
+// sum.  s_warp: 32 words of shared memory.  All threads must call it.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp,
+                                                    uint32_t* s_total) {
+    const uint32_t tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31 || tid == blockDim.x - 1) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < nwarps ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += x;
+        }
+        if (lane < nwarps) s_warp[lane] = wi - w;
+        if (lane == 31) *s_total = wi;
+    }
+    __syncthreads();
+    return s_warp[warp] + incl - v;
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide location of a rank in a histogram of NB bins (NB = 1024 * G):
+// sums of 32-bin groups, then one warp scans the group sums and the group.
+// target_of(total) gives the rank to find (or total or more for none).
+// Results in *s_total, *s_bin, *s_rank (rank within the bin); *s_bin = NB
+// when no bin holds the target.  All threads must call it.
+template <int NB, class TargetFn>
+__device__ void find_rank(const uint32_t* hist, TargetFn target_of, uint32_t* gsum,
+                          uint32_t* s_total, uint32_t* s_bin, uint32_t* s_rank) {
+    constexpr int NG = NB / 32;  // groups
+    constexpr int G = NG / 32;   // groups per lane
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (uint32_t g = tid; g < (uint32_t)NG; g += nthr) {
+        const uint4* h4 = reinterpret_cast<const uint4*>(hist + g * 32);
+        uint32_t sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const uint4 v = h4[j];
+            sum += v.x + v.y + v.z + v.w;
+        }
+        gsum[g] = sum;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t loc[G], sum = 0;
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            loc[j] = gsum[lane * G + j];
+            sum += loc[j];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t k = target_of(total);
+        const bool ok = k < total;
+        const uint32_t excl = incl - sum;
+        const bool mine = ok && excl <= k && k < incl;
+        const uint32_t who = __ballot_sync(0xffffffffu, mine);
+        uint32_t group = 0, grank = 0;
+        if (mine) {
+            uint32_t below = excl;
+            int gj = 0;
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                if (below + loc[j] > k) {
+                    gj = j;
+                    break;
+                }
+                below += loc[j];
+            }
+            group = lane * G + gj;
+            grank = k - below;
+        }
+        if (lane == 0) {
+            *s_total = total;
+            *s_bin = NB;
+        }
+        __syncwarp();
+        if (ok) {
+            const int src = __ffs(who) - 1;
+            group = __shfl_sync(0xffffffffu, group, src);
+            grank = __shfl_sync(0xffffffffu, grank, src);
+            const uint32_t hv = hist[group * 32 + lane];
+            uint32_t hi = hv;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, hi, o);
+                if (lane >= o) hi += v;
+            }
+            const uint32_t he = hi - hv;
+            if (he <= grank && grank < hi) {
+                *s_bin = group * 32 + lane;
+                *s_rank = grank - he;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Common mode of large units.
+template <int VEC>
+__global__ void __launch_bounds__(512, 2)
+    cm_big_kernel(ChainParams p, const uint16_t* __restrict__ raw,
+                  float* __restrict__ cm_out, CmBigConfig cfg) {
+    extern __shared__ __align__(16) uint32_t cm_smem[];
+    uint32_t* hist = cm_smem;                            // kCmBins + spare + pad
+    float* cand = reinterpret_cast<float*>(hist + kCmBins + 4);  // kCandCap
+    uint32_t* codes = reinterpret_cast<uint32_t*>(cand + kCandCap);  // VEC=2: pairs
+    __shared__ uint32_t gsum[kCmBins / 32];
+    __shared__ uint32_t swarp[32];
+    __shared__ uint32_t s_bin, s_rank, s_n, s_cand, s_prefix, s_rrank;
+
+    const uint32_t item = blockIdx.x;
+    const uint32_t f = item / p.units_per_frame;
+    const uint32_t u = item % p.units_per_frame;
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    if (p.cm_mode == PD_CM_NONE) {
+        if (tid == 0) cm_out[item] = 0.0f;
+        return;
+    }
+    const uint32_t m = u / p.units_per_module;
+    const uint32_t um = u % p.units_per_module;
+    const uint32_t r0 = (um / p.units_per_row) * p.unit_rows;
+    const uint32_t c0 = (um % p.units_per_row) * p.unit_cols;
+    const size_t mod_base = (size_t)m * p.module_px;
+    const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
+    const float* npm = p.nped + mod_base;
+    const uint32_t TX = cfg.tx, TY = cfg.ty;
+    const uint32_t tx = tid % TX, ty = tid / TX;
+    const bool active = ty < TY;
+
+    for (uint32_t i = tid; i < kCmBins / 4; i += nthr)
+        reinterpret_cast<uint4*>(hist)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        s_cand = 0;
+        hist[kCmBins] = 0;
+    }
+    __syncthreads();
+
+    // pass A: histogram of bin codes, codes kept for pass B.  Loads of U
+    // rows are issued before any of them is used, to keep several memory
+    // requests of every thread in flight.  Every pixel does one atomic: a
+    // pixel with d >= cut adds to the spare bin kCmBins, which is never read.
+    if (active) {
+        if (VEC == 2) {
+            // all raw pairs of the unit are copied into the code buffer at
+            // once (one request per pair, none held in registers); each pair
+            // is then replaced in place by its two bin codes
+            {
+                const uint32_t* src = reinterpret_cast<const uint32_t*>(fr + (r0 + ty) * p.cols + c0) + tx;
+                const uint32_t sstride = TY * p.cols / 2;
+                uint32_t* dst = codes + ty * TX + tx;
+                for (uint32_t r = ty; r < p.unit_rows; r += TY) {
+                    cp_async4(dst, src);
+                    src += sstride;
+                    dst += TY * TX;
+                }
+                cp_async_wait_all();
+            }
+            __syncwarp();
+            constexpr int U = 8;
+            const float2* prow = reinterpret_cast<const float2*>(npm + (r0 + ty) * p.cols + c0) + tx;
+            const uint32_t stride = TY * p.cols / 2;  // pairs between a thread's rows
+            uint32_t* cptr = codes + ty * TX + tx;
+            const uint32_t cstride = TY * TX;
+            const float2 eight = make_float2(8.0f, 8.0f);
+            const float2 mw = make_float2(cfg.magic_w, cfg.magic_w);
+            uint32_t r = ty;
+            for (; r + (U - 1) * TY < p.unit_rows; r += U * TY) {
+                float2 pp[U];
+#pragma unroll
+                for (int j = 0; j < U; j++) pp[j] = prow[j * stride];
+#pragma unroll
+                for (int j = 0; j < U; j++) {
+                    const float2 d = __fadd2_rn(raw_pair(cptr[j * cstride]), pp[j]);
+                    const float2 u = __ffma2_rd(d, eight, mw);
+                    const int b0 = min(max(__float_as_int(u.x), (int)kMagicBits),
+                                       (int)(kMagicBits + kCmBins));
+                    const int b1 = min(max(__float_as_int(u.y), (int)kMagicBits),
+                                       (int)(kMagicBits + kCmBins));
+                    atomicAdd(&hist[(uint32_t)b0 - kMagicBits], 1u);
+                    atomicAdd(&hist[(uint32_t)b1 - kMagicBits], 1u);
+                    cptr[j * cstride] = __byte_perm((uint32_t)b0, (uint32_t)b1, 0x5410u);
+                }
+                prow += U * stride;
+                cptr += U * cstride;
+            }
+            for (; r < p.unit_rows; r += TY) {
+                const float2 d = __fadd2_rn(raw_pair(*cptr), *prow);
+                const float2 u = __ffma2_rd(d, eight, mw);
+                const int b0 = min(max(__float_as_int(u.x), (int)kMagicBits),
+                                   (int)(kMagicBits + kCmBins));
+                const int b1 = min(max(__float_as_int(u.y), (int)kMagicBits),
+                                   (int)(kMagicBits + kCmBins));
+                atomicAdd(&hist[(uint32_t)b0 - kMagicBits], 1u);
+                atomicAdd(&hist[(uint32_t)b1 - kMagicBits], 1u);
+                *cptr = __byte_perm((uint32_t)b0, (uint32_t)b1, 0x5410u);
+                prow += stride;
+                cptr += cstride;
+            }
+        } else {
+            uint32_t off = (r0 + ty) * p.cols + c0 + tx;
+            for (uint32_t r = ty; r < p.unit_rows; r += TY, off += TY * p.cols) {
+                const float d = __fadd_rn(__uint2float_rn(fr[off]), npm[off]);
+                uint32_t k = cm_code(d, cfg.magic_w);
+                k = min(k, kCmBins);
+                atomicAdd(&hist[k], 1u);
+                reinterpret_cast<uint16_t*>(codes)[r * TX + tx] = (uint16_t)k;
+            }
+        }
+    }
+    __syncthreads();
+
+    // locate rank floor((n-1)/2) of the values below the cut
+    const uint32_t min_count = p.cm_min_count;
+    find_rank<kCmBins>(
+        hist,
+        [min_count](uint32_t total) {
+            return (total > 0 && total >= min_count) ? (total - 1) / 2 : total;
+        },
+        gsum, &s_n, &s_bin, &s_rank);
+    const uint32_t n = s_n;
+    if (n == 0 || n < min_count) {
+        if (tid == 0) cm_out[item] = 0.0f;
+        return;
+    }
+    const uint32_t bin = s_bin, brank = s_rank;
+
+    // the key of pixel i of the unit (kSent when d >= cut)
+    auto unit_key = [&](uint32_t i) -> uint32_t {
+        const uint32_t off = (r0 + i / p.unit_cols) * p.cols + c0 + i % p.unit_cols;
+        const float d = __fadd_rn(__uint2float_rn(fr[off]), npm[off]);
+        return d < p.cm_cut ? order_key(d) : kSent;
+    };
+
+    if (bin != 0) {
+        // pass B: positions of the winning bin's pixels (shared memory only),
+        // then one parallel fetch of their raw value and pedestal
+        uint32_t* cidx = reinterpret_cast<uint32_t*>(cand);
+        const uint32_t both = bin | (bin << 16);
+        uint32_t mine = 0;  // this thread's candidates (no atomics in the loop)
+        if (active) {
+            for (uint32_t r = ty; r < p.unit_rows; r += TY) {
+                const uint32_t w = r * TX + tx;
+                if (VEC == 2) {
+                    const uint32_t y = codes[w] ^ both;
+                    mine += ((y & 0xFFFFu) == 0) + ((y >> 16) == 0);
+                } else {
+                    mine += reinterpret_cast<const uint16_t*>(codes)[w] == bin;
+                }
+            }
+        }
+        uint32_t at = block_excl_scan(mine, swarp, &s_cand);
+        if (active && mine) {
+            for (uint32_t r = ty; r < p.unit_rows && at < kCandCap; r += TY) {
+                const uint32_t w = r * TX + tx;
+                if (VEC == 2) {
+                    const uint32_t y = codes[w] ^ both;
+                    if ((y & 0xFFFFu) == 0 && at < kCandCap) cidx[at++] = 2 * w;
+                    if ((y >> 16) == 0 && at < kCandCap) cidx[at++] = 2 * w + 1;
+                } else if (reinterpret_cast<const uint16_t*>(codes)[w] == bin) {
+                    cidx[at++] = w;
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t mc = s_cand;
+        if (mc <= kCandCap) {
+            // position i (row-major in the unit) -> d, in place
+            for (uint32_t t = tid; t < mc; t += nthr) {
+                const uint32_t i = cidx[t];
+                const uint32_t off = (r0 + i / p.unit_cols) * p.cols + c0 + i % p.unit_cols;
+                cand[t] = __fadd_rn(__uint2float_rn(fr[off]), npm[off]);
+            }
+            __syncthreads();
+            // exact select inside the bin: 1024 sub-bins of 1/8192 ADU (d - lo
+            // rounded to nearest is monotone in d, so sub-bins stay ordered),
+            // then the few values of the target sub-bin are ranked by counting
+            const float lo_b = __fadd_rn(cfg.w_lo, __fmul_rn((float)bin, 0.125f));
+            uint32_t* sub = hist;  // reuse: 1024 sub-bins
+            for (uint32_t i = tid; i < 1024 / 4; i += nthr)
+                reinterpret_cast<uint4*>(sub)[i] = make_uint4(0, 0, 0, 0);
+            __syncthreads();
+            for (uint32_t t = tid; t < mc; t += nthr) {
+                const float x = __fmul_rn(__fsub_rn(cand[t], lo_b), 8192.0f);
+                const uint32_t sb = min((uint32_t)max(__float2int_rd(x), 0), 1023u);
+                codes[t] = sb;  // codes are no longer needed: keep each sub-bin
+                atomicAdd(&sub[sb], 1u);
+            }
+            __syncthreads();
+            find_rank<1024>(
+                sub, [brank](uint32_t) { return brank; }, gsum, &s_prefix, &s_bin, &s_rank);
+            const uint32_t sbin = s_bin, srank = s_rank;
+            // values of the target sub-bin, then rank by counting among them
+            float* few = reinterpret_cast<float*>(sub + 1024);
+            if (tid == 0) s_rrank = 0;
+            __syncthreads();
+            for (uint32_t t = tid; t < mc; t += nthr)
+                if (codes[t] == sbin) few[atomicAdd(&s_rrank, 1u)] = cand[t];
+            __syncthreads();
+            const uint32_t nf = s_rrank;
+            for (uint32_t t = tid; t < nf; t += nthr) {
+                const uint32_t kt = order_key(few[t]);
+                uint32_t less = 0, leq = 0;
+                for (uint32_t j = 0; j < nf; j++) {
+                    const uint32_t kj = order_key(few[j]);
+                    less += kj < kt;
+                    leq += kj <= kt;
+                }
+                if (less <= srank && srank < leq) cm_out[item] = few[t];
+            }
+            return;
+        }
+    }
+    // whole-unit exact selection (bottom bin or candidate overflow)
+    const uint32_t key = block_radix_select(unit_key, p.unit_px, (n - 1) / 2, hist,
+                                            &s_prefix, &s_rrank);
+    if (tid == 0) cm_out[item] = key_value(key);
+}
+
+// ---------------------------------------------------------------------------
+// Stencil over bands of full-width rows.
+template <int VEC>
+__global__ void __launch_bounds__(kBandThreads)
+    stencil_band_kernel(ChainParams p, const uint16_t* __restrict__ raw,
+                        uint32_t frame_base, CallOut out, BandConfig bc,
+                        unsigned long long n_tiles) {
+    extern __shared__ __align__(16) uint32_t band_smem[];
+    const uint32_t P = bc.pitch;                 // floats per s-tile row
+    float* stile = reinterpret_cast<float*>(band_smem);          // (rb+2) * P
+    uint32_t* hpix = band_smem + (bc.rb + 2) * P;               // hist_bins + spare
+    uint32_t* hhit = hpix + p.hist_bins + 4;                     // hist_bins
+    uint32_t* list = hhit + p.hist_bins;                         // kSeedCap
+    float* cmt = reinterpret_cast<float*>(list + kSeedCap);      // (rb+2) * upr
+    __shared__ uint32_t s_list_n;
+    __shared__ uint32_t swarp[32];
+
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31;
+    const int R = (int)p.rows, C = (int)p.cols;
+    const uint32_t TX = bc.tx, TY = bc.ty;
+    const uint32_t tx = tid % TX, ty = tid / TX;
+    const bool active = ty < TY;
+    const int col = (int)(tx * VEC);  // first column of this thread's chunk
+    // unit columns of the chunk's first and last pixel, and where it splits
+    const uint32_t uca = (uint32_t)col / p.unit_cols;
+    const uint32_t ucb = (uint32_t)(col + VEC - 1) / p.unit_cols;
+    const int split = (int)(ucb * p.unit_cols) - col;  // pixels i >= split use ucb
+    const int max_bits = (int)(kMagicBits + p.hist_bins - 1);
+    const int trash_bits = (int)(kMagicBits + p.hist_bins);  // spare bin of hpix
+    const bool seed_eq = p.seed_thr == p.zero_thr;
+
+    // zero the whole s-tile once (pad columns stay zero), and the histograms
+    for (uint32_t i = tid; i < (bc.rb + 2) * P; i += nthr) stile[i] = 0.0f;
+    for (uint32_t i = tid; i < 2 * p.hist_bins + 4; i += nthr) hpix[i] = 0;
+    __syncthreads();
+
+    for (unsigned long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        unsigned long long q = t;
+        const int band = (int)(q % bc.n_bands);
+        q /= bc.n_bands;
+        const uint32_t m = (uint32_t)(q % p.n_modules);
+        const uint32_t f = (uint32_t)(q / p.n_modules);
+        const int r0 = band * (int)bc.rb;
+        const int rows_here = min((int)bc.rb, R - r0);
+        const size_t mod_base = (size_t)m * p.module_px;
+        const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
+        const float* npm = p.nped + mod_base;
+        const float* gm = p.inv_gain + mod_base;
+        const float* cmf = out.cm + (size_t)f * p.units_per_frame +
+                           (size_t)m * p.units_per_module;
+
+        // negated common mode of every (tile row, unit column)
+        for (uint32_t i = tid; i < (bc.rb + 2) * p.units_per_row; i += nthr) {
+            const int rl = (int)(i / p.units_per_row);
+            const int r = r0 - 1 + rl;
+            float v = 0.0f;
+            if (r >= 0 && r < R)
+                v = -cmf[((uint32_t)r / p.unit_rows) * p.units_per_row + i % p.units_per_row];
+            cmt[i] = v;
+        }
+        if (tid == 0) s_list_n = 0;
+        __syncthreads();
+
+        // 1. zeroed signal of rows r0-1 .. r0+rows_here (halo rows included);
+        //    loads of two rows are issued before either is used.  Halo rows
+        //    are not histogrammed: their bins are clamped to the spare bin.
+        uint64_t cmask = 0;  // seed candidates of this thread: bit k*VEC + i
+        if (active) {
+            const int nrows = rows_here + 2;
+            int kk = 0;
+            for (int rl0 = (int)ty; rl0 < nrows; rl0 += 2 * (int)TY, kk += 2) {
+                constexpr int U = 2;
+                uint2 rr[U];
+                float4 pp[U], gg[U];
+                uint16_t r1[U];
+                float p1[U], g1[U];
+                bool in[U];
+#pragma unroll
+                for (int j = 0; j < U; j++) {
+                    const int rl = rl0 + j * (int)TY;
+                    const int r = r0 - 1 + rl;
+                    in[j] = rl < nrows && r >= 0 && r < R;
+                    const uint32_t off = in[j] ? (uint32_t)r * p.cols + (uint32_t)col : 0u;
+                    if (VEC == 4) {
+                        if (in[j]) {
+                            rr[j] = *reinterpret_cast<const uint2*>(fr + off);
+                            pp[j] = *reinterpret_cast<const float4*>(npm + off);
+                            gg[j] = *reinterpret_cast<const float4*>(gm + off);
+                        }
+                    } else {
+                        if (in[j]) {
+                            r1[j] = fr[off];
+                            p1[j] = npm[off];
+                            g1[j] = gm[off];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < U; j++) {
+                    const int rl = rl0 + j * (int)TY;
+                    if (rl >= nrows) continue;
+                    float* srow = stile + rl * P + 4 + col;
+                    if (!in[j]) {
+#pragma unroll
+                        for (int i = 0; i < VEC; i++) srow[i] = 0.0f;
+                        continue;
+                    }
+                    const int r = r0 - 1 + rl;
+                    const bool own = rl >= 1 && rl <= rows_here;
+                    const int blo = own ? (int)kMagicBits : trash_bits;
+                    const int bhi = own ? max_bits : trash_bits;
+                    const float ncma = cmt[rl * p.units_per_row + uca];
+                    const float ncmb = cmt[rl * p.units_per_row + ucb];
+                    float e[VEC];
+                    if (VEC == 4) {
+                        const float2 d01 = __fadd2_rn(raw_pair(rr[j].x), make_float2(pp[j].x, pp[j].y));
+                        const float2 d23 = __fadd2_rn(raw_pair(rr[j].y), make_float2(pp[j].z, pp[j].w));
+                        const float2 n01 = make_float2(split > 0 ? ncma : ncmb, split > 1 ? ncma : ncmb);
+                        const float2 n23 = make_float2(split > 2 ? ncma : ncmb, split > 3 ? ncma : ncmb);
+                        const float2 e01 = __fmul2_rn(__fadd2_rn(d01, n01), make_float2(gg[j].x, gg[j].y));
+                        const float2 e23 = __fmul2_rn(__fadd2_rn(d23, n23), make_float2(gg[j].z, gg[j].w));
+                        e[0] = e01.x;
+                        e[1] = e01.y;
+                        e[2] = e23.x;
+                        e[3] = e23.y;
+                        // summary histogram of e (packed: bins of two pixels at once)
+                        const float2 iw = make_float2(p.hist_inv_w, p.hist_inv_w);
+                        const float2 nl = make_float2(p.hist_neg_lo_s, p.hist_neg_lo_s);
+                        const float2 mg = make_float2(kMagic, kMagic);
+                        const float2 u01 = __fadd2_rd(__ffma2_rn(e01, iw, nl), mg);
+                        const float2 u23 = __fadd2_rd(__ffma2_rn(e23, iw, nl), mg);
+                        atomicAdd(&hpix[(uint32_t)min(max(__float_as_int(u01.x), blo), bhi) - kMagicBits], 1u);
+                        atomicAdd(&hpix[(uint32_t)min(max(__float_as_int(u01.y), blo), bhi) - kMagicBits], 1u);
+                        atomicAdd(&hpix[(uint32_t)min(max(__float_as_int(u23.x), blo), bhi) - kMagicBits], 1u);
+                        atomicAdd(&hpix[(uint32_t)min(max(__float_as_int(u23.y), blo), bhi) - kMagicBits], 1u);
+                    } else {
+                        e[0] = __fmul_rn(__fadd_rn(__fadd_rn(__uint2float_rn(r1[j]), p1[j]), ncma),
+                                         g1[j]);
+                        const float u = __fadd_rd(__fmaf_rn(e[0], p.hist_inv_w, p.hist_neg_lo_s),
+                                                  kMagic);
+                        atomicAdd(&hpix[(uint32_t)min(max(__float_as_int(u), blo), bhi) - kMagicBits], 1u);
+                    }
+                    float sv[VEC];
+                    bool cand = false;
+#pragma unroll
+                    for (int i = 0; i < VEC; i++) {
+                        const bool sig = e[i] > p.zero_thr;
+                        sv[i] = sig ? e[i] : 0.0f;
+                        cand = cand || (seed_eq ? sig : (sv[i] > p.seed_thr));
+                    }
+                    if (VEC == 4)
+                        *reinterpret_cast<float4*>(srow) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+                    else
+                        srow[0] = sv[0];
+                    if (own && out.corrected) {
+                        const uint32_t off = (uint32_t)r * p.cols + (uint32_t)col;
+                        float* dst = out.corrected + (size_t)f * p.frame_px + mod_base + off;
+                        if (VEC == 4)
+                            *reinterpret_cast<float4*>(dst) = make_float4(e[0], e[1], e[2], e[3]);
+                        else
+                            dst[0] = e[0];
+                    }
+                    if (own && cand) {
+#pragma unroll
+                        for (int i = 0; i < VEC; i++)
+                            if (sv[i] > p.seed_thr) cmask |= 1ull << ((kk + j) * VEC + i);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        // compaction of the candidates: counts, block scan, then writes
+        {
+            uint32_t at = block_excl_scan((uint32_t)__popcll(cmask), swarp, &s_list_n);
+            while (cmask && at < kSeedCap) {
+                const int b = __ffsll((long long)cmask) - 1;
+                cmask &= cmask - 1;
+                const int rl = (int)ty + (b / VEC) * (int)TY;
+                list[at++] = ((uint32_t)rl << 16) | (uint32_t)(col + b % VEC);
+            }
+        }
+        __syncthreads();
+
+        // 2. seeds: local maximum test, sums, count, centroid, emission
+        const uint32_t n_list = s_list_n;
+        const bool scan = n_list > kSeedCap;  // overflow: test every owned pixel
+        const uint32_t n_work = scan ? (uint32_t)rows_here * (uint32_t)C : n_list;
+        for (uint32_t base = 0; base < n_work; base += nthr) {
+            const uint32_t j = base + tid;
+            bool emit = false;
+            pd_hit h;
+            uint32_t n = 0, pix = 0;
+            if (j < n_work) {
+                int rl, c;
+                if (scan) {
+                    rl = 1 + (int)(j / (uint32_t)C);
+                    c = (int)(j % (uint32_t)C);
+                } else {
+                    const uint32_t e = list[j];
+                    rl = (int)(e >> 16);
+                    c = (int)(e & 0xFFFFu);
+                }
+                const float* sc = stile + rl * P + 4 + c;
+                const float sp = sc[0];
+                if (sp > p.seed_thr) {
+                    const float nb[9] = {sc[-(int)P - 1], sc[-(int)P], sc[-(int)P + 1],
+                                         sc[-1],          sp,          sc[1],
+                                         sc[P - 1],       sc[P],       sc[P + 1]};
+                    const bool seed = sp > nb[0] && sp > nb[1] && sp > nb[2] && sp > nb[3] &&
+                                      sp >= nb[5] && sp >= nb[6] && sp >= nb[7] && sp >= nb[8];
+                    if (seed) {
+                        float E = 0.0f, Mx = 0.0f, My = 0.0f;
+                        uint32_t npix = 0;
+#pragma unroll
+                        for (int k = 0; k < 9; k++) {
+                            const float ox = (float)(k % 3 - 1), oy = (float)(k / 3 - 1);
+                            E = __fadd_rn(E, nb[k]);
+                            Mx = __fadd_rn(Mx, __fmul_rn(nb[k], ox));
+                            My = __fadd_rn(My, __fmul_rn(nb[k], oy));
+                            npix += nb[k] > 0.0f;
+                        }
+                        atomicAdd(&hhit[summary_bin(E, p.hist_inv_w, p.hist_neg_lo_s, max_bits)],
+                                  1u);
+                        const float qr = rintf(__fdiv_rn(E, p.photon_kev));
+                        uint16_t flags = 0;
+                        if (!(qr >= 0.0f)) {
+                            n = 0;
+                        } else if (qr > 255.0f) {
+                            n = 255;
+                            flags |= PD_HIT_SATURATED;
+                        } else {
+                            n = (uint32_t)qr;
+                        }
+                        if (n >= 1) {
+                            const int r = r0 - 1 + rl;
+                            if (r == 0 || c == 0 || r == R - 1 || c == C - 1) flags |= PD_HIT_EDGE;
+                            pix = (uint32_t)mod_base + (uint32_t)r * p.cols + (uint32_t)c;
+                            h.frame = frame_base + f;
+                            h.pixel = pix;
+                            h.energy_kev = E;
+                            h.dx = __fdiv_rn(Mx, E);
+                            h.dy = __fdiv_rn(My, E);
+                            h.count = (uint8_t)n;
+                            h.npix = (uint8_t)npix;
+                            h.flags = flags;
+                            emit = true;
+                        }
+                    }
+                }
+            }
+            const uint32_t mask = __ballot_sync(0xffffffffu, emit);
+            if (mask) {
+                const int leader = __ffs(mask) - 1;
+                uint32_t slot = 0;
+                if (lane == leader) slot = atomicAdd(out.n_hits, __popc(mask));
+                slot = __shfl_sync(0xffffffffu, slot, leader);
+                if (emit) {
+                    slot += __popc(mask & ((1u << lane) - 1u));
+                    atomicAdd(&p.count_map[pix], n);
+                    if (slot < out.hit_capacity) out.hits[slot] = h;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (uint32_t b = tid; b < p.hist_bins; b += nthr) {
+        if (hpix[b]) atomicAdd(&p.hist_pix[b], (unsigned long long)hpix[b]);
+        if (hhit[b]) atomicAdd(&p.hist_hit[b], (unsigned long long)hhit[b]);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+bool cm_big_supported(const ChainParams& p, const CmBigConfig& cfg) {
+    return cfg.ok && p.unit_rows * p.unit_cols >= kCmBigMinPx &&
+           cm_big_smem_bytes(p) <= kCmBigMaxSmem;
+}
+
+size_t cm_big_smem_bytes(const ChainParams& p) {
+    const size_t codes = ((size_t)p.unit_rows * p.unit_cols * 2 + 15) / 16 * 16;
+    return (size_t)(kCmBins + 4) * 4 + (size_t)kCandCap * 4 + codes;
+}
+
+CmBigConfig make_cm_big_config(const ChainParams& p) {
+    CmBigConfig cfg{};
+    cfg.ok = false;
+    // the window [cut - 512, cut) must have 8*(cut - 512) an integer, so the
+    // rounded-down fma computes floor(8 * (d - lo)) exactly
+    const double cut = p.cm_cut;
+    const double lo8 = (cut - 512.0) * 8.0;
+    if (!(cut > -1e6 && cut < 1e6) || lo8 != (double)(long long)lo8) return cfg;
+    cfg.magic_w = (float)(12582912.0 - lo8);
+    cfg.w_lo = (float)(cut - 512.0);
+    if ((double)cfg.magic_w != 12582912.0 - lo8) return cfg;
+    const bool vec2 = p.unit_cols % 2 == 0 && p.cols % 2 == 0;
+    cfg.vec = vec2 ? 2 : 1;
+    const uint32_t tx = p.unit_cols / cfg.vec;
+    if (tx == 0 || tx > 512) return cfg;
+    cfg.tx = tx;
+    cfg.ty = std::max<uint32_t>(1, 512 / tx);
+    if (cfg.ty > p.unit_rows) cfg.ty = p.unit_rows;
+    cfg.ok = true;
+    return cfg;
+}
+
+static int g_attr_dev_cm = -1, g_attr_dev_band = -1;
+
+cudaError_t launch_cm_big(const ChainParams& p, const CmBigConfig& cfg, const uint16_t* raw,
+                          uint32_t n_frames, float* cm, cudaStream_t stream) {
+    const unsigned long long items = (unsigned long long)n_frames * p.units_per_frame;
+    if (items == 0) return cudaSuccess;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (g_attr_dev_cm != dev) {
+        cudaError_t e = cudaFuncSetAttribute(cm_big_kernel<2>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kCmBigMaxSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(cm_big_kernel<1>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kCmBigMaxSmem);
+        if (e != cudaSuccess) return e;
+        g_attr_dev_cm = dev;
+    }
+    const size_t smem = cm_big_smem_bytes(p);
+    const unsigned threads = cfg.tx * cfg.ty;
+    if (cfg.vec == 2)
+        cm_big_kernel<2><<<(unsigned)items, threads, smem, stream>>>(p, raw, cm, cfg);
+    else
+        cm_big_kernel<1><<<(unsigned)items, threads, smem, stream>>>(p, raw, cm, cfg);
+    return cudaGetLastError();
+}
+
+BandConfig make_band_config(const ChainParams& p) {
+    BandConfig bc{};
+    const bool vec4 = p.cols % 4 == 0 && p.module_px % 4 == 0 && p.frame_px % 4 == 0;
+    bc.vec = vec4 ? 4 : 1;
+    bc.tx = p.cols / bc.vec;
+    bc.ok = bc.tx <= kBandThreads;
+    if (!bc.ok) return bc;
+    bc.ty = std::max<uint32_t>(1, kBandThreads / bc.tx);
+    bc.pitch = (p.cols + 8 + 3) / 4 * 4;  // 4 zero columns left, >= 1 right
+    // about 12k pixels per band, at least 4 rows
+    uint32_t rb = std::max<uint32_t>(4, 12288 / p.cols);
+    rb = std::min<uint32_t>(rb, p.rows);
+    // keep the shared memory of one CTA under about 100 KB, and the rows a
+    // thread visits (times pixels per chunk) within its 64-bit candidate mask
+    while (rb > 1 && band_smem_bytes(p, rb, bc.pitch) > 100 * 1024) rb--;
+    while (rb > 1 && ((rb + 2 + bc.ty - 1) / bc.ty) * bc.vec > 64) rb--;
+    bc.rb = rb;
+    bc.n_bands = (p.rows + rb - 1) / rb;
+    return bc;
+}
+
+size_t band_smem_bytes(const ChainParams& p, uint32_t rb, uint32_t pitch) {
+    return (size_t)(rb + 2) * pitch * 4 + (2 * (size_t)p.hist_bins + 4) * 4 +
+           (size_t)kSeedCap * 4 + (size_t)(rb + 2) * p.units_per_row * 4;
+}
+
+cudaError_t launch_stencil_band(const ChainParams& p, const BandConfig& bc, const uint16_t* raw,
+                                uint32_t n_frames, uint32_t frame_base, const CallOut& out,
+                                cudaStream_t stream) {
+    const unsigned long long n_tiles = (unsigned long long)n_frames * p.n_modules * bc.n_bands;
+    if (n_tiles == 0) return cudaSuccess;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (g_attr_dev_band != dev) {
+        cudaError_t e = cudaFuncSetAttribute(stencil_band_kernel<4>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(stencil_band_kernel<1>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        g_attr_dev_band = dev;
+    }
+    const size_t smem = band_smem_bytes(p, bc.rb, bc.pitch);
+    const unsigned threads = bc.tx * bc.ty;
+    int per_sm = (int)((200 * 1024) / std::max<size_t>(smem, 1));
+    per_sm = std::max(1, std::min(per_sm, 4));
+    unsigned long long grid = (unsigned long long)device_sm_count() * per_sm;
+    if (grid > n_tiles) grid = n_tiles;
+    if (bc.vec == 4)
+        stencil_band_kernel<4><<<(unsigned)grid, threads, smem, stream>>>(p, raw, frame_base, out,
+                                                                           bc, n_tiles);
+    else
+        stencil_band_kernel<1><<<(unsigned)grid, threads, smem, stream>>>(p, raw, frame_base, out,
+                                                                           bc, n_tiles);
+    return cudaGetLastError();
+}
+
+}  // namespace pd

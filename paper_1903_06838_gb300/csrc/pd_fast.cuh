@@ -1,0 +1,50 @@
+// pd_fast.cuh — configuration and launchers of the throughput kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "pd_internal.cuh"
+
+namespace pd {
+
+constexpr uint32_t kCmBins = 4096;     // common-mode bins of 1/8 ADU (512 ADU)
+constexpr uint32_t kCandCap = 2048;    // candidates of the winning bin
+constexpr uint32_t kCmBigMinPx = 4096; // smaller units use the generic kernel (the
+                                       // code buffer must hold kCandCap words)
+constexpr size_t kCmBigMaxSmem = 112 * 1024;
+constexpr uint32_t kBandThreads = 512;
+constexpr uint32_t kSeedCap = 4096;    // seed candidates per band tile
+
+struct CmBigConfig {
+    float magic_w;  // 1.5*2^23 - 8*(cut - 512)
+    float w_lo;     // cut - 512: lower edge of bin 0
+    uint32_t vec;   // pixels per load (2 or 1)
+    uint32_t tx, ty;
+    bool ok;
+};
+
+struct BandConfig {
+    uint32_t vec;     // pixels per chunk (4 or 1)
+    uint32_t tx, ty;  // chunk columns x row lanes
+    uint32_t pitch;   // floats per s-tile row
+    uint32_t rb;      // rows per band
+    uint32_t n_bands;
+    bool ok;
+};
+
+CmBigConfig make_cm_big_config(const ChainParams& p);
+bool cm_big_supported(const ChainParams& p, const CmBigConfig& cfg);
+size_t cm_big_smem_bytes(const ChainParams& p);
+cudaError_t launch_cm_big(const ChainParams& p, const CmBigConfig& cfg, const uint16_t* raw,
+                          uint32_t n_frames, float* cm, cudaStream_t stream);
+
+BandConfig make_band_config(const ChainParams& p);
+size_t band_smem_bytes(const ChainParams& p, uint32_t rb, uint32_t pitch);
+cudaError_t launch_stencil_band(const ChainParams& p, const BandConfig& bc, const uint16_t* raw,
+                                uint32_t n_frames, uint32_t frame_base, const CallOut& out,
+                                cudaStream_t stream);
+
+}  // namespace pd

@@ -26,10 +26,11 @@ struct ChainParams {
     uint32_t cm_min_count;      // resolved n_min
     // thresholds
     float cm_cut, zero_thr, seed_thr, photon_kev;
-    float hist_lo, hist_inv_w;  // bin(v) = floor((v - lo) * inv_w)
+    float hist_inv_w, hist_neg_lo_s;  // bin(v) = floor(fma(v, inv_w, neg_lo_s))
     uint32_t hist_bins;
     // device state owned by the context
     const float* ped;           // [frame_px]
+    const float* nped;          // [frame_px] -pedestal (d = raw + nped)
     const float* inv_gain;      // [frame_px]
     uint32_t* count_map;        // [frame_px]
     unsigned long long* hist_pix;  // [hist_bins]

@@ -20,7 +20,7 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_PKG, "libpd.so")
-SOURCES = ["pd_api.cu", "pd_chain.cu"]
+SOURCES = ["pd_api.cu", "pd_chain.cu", "pd_fast.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
@@ -73,6 +73,11 @@ class PdProfile(ctypes.Structure):
                 ("name", (ctypes.c_char * 32) * 8),
                 ("launches", ctypes.c_uint32 * 8),
                 ("total_ms", ctypes.c_double * 8)]
+
+
+class PdTuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in
+                ("chunk_frames", "band_rows", "overlap", "reserved")]
 
 
 class PdError(RuntimeError):
@@ -135,6 +140,8 @@ def _declare(lib):
         "pd_reset_summary": ([vp, vp], i32),
         "pd_destroy": ([vp], None),
         "pd_set_profiling": ([vp, i32], i32),
+        "pd_get_tuning": ([vp, ctypes.POINTER(PdTuning)], i32),
+        "pd_set_tuning": ([vp, ctypes.POINTER(PdTuning)], i32),
         "pd_read_profile": ([vp, ctypes.POINTER(PdProfile)], i32),
         "pd_strerror": ([i32], ctypes.c_char_p),
         "pd_last_error": ([], ctypes.c_char_p),
@@ -299,6 +306,18 @@ def pd_destroy(ctx: Context) -> None:
     if ctx.handle:
         load().pd_destroy(ctx.handle)
         ctx.handle = None
+
+
+def pd_get_tuning(ctx: Context) -> dict:
+    t = PdTuning()
+    _check(load().pd_get_tuning(ctx.handle, ctypes.byref(t)), "pd_get_tuning")
+    return dict(chunk_frames=t.chunk_frames, band_rows=t.band_rows,
+                overlap=t.overlap)
+
+
+def pd_set_tuning(ctx: Context, chunk_frames=0, band_rows=0, overlap=1) -> None:
+    t = PdTuning(chunk_frames, band_rows, overlap, 0)
+    _check(load().pd_set_tuning(ctx.handle, ctypes.byref(t)), "pd_set_tuning")
 
 
 def pd_set_profiling(ctx: Context, enable: bool) -> None:

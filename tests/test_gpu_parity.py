@@ -106,6 +106,55 @@ def test_generated_workloads_bit_exact(name):
     _compare(ctx, out, ref, n)
 
 
+# Special paths of the large-unit common-mode kernel and the band stencil.
+def _run_case(det, n, ped_shift=0.0, thr_over=None, integer_ped=False):
+    ped, gain = synth.maps(det)
+    if integer_ped:
+        ped = np.rint(ped).astype(np.float32)
+    raw, _ = synth.frames(det, ped, gain, 0, n)
+    ped_chain = (ped + np.float32(ped_shift)).astype(np.float32)
+    geom, thr = det.geometry(), dict(det.thresholds(), **(thr_over or {}))
+    ctx = _ctx(geom, thr, ped_chain, gain)
+    out = pd.process(ctx, pd.frames_to_device(raw), corrected=True, cm=True)
+    torch.cuda.synchronize()
+    ref = _oracle(geom, thr, ped_chain, gain, raw, want_corrected=True)
+    _compare(ctx, out, ref, n)
+    return ref
+
+
+def test_bank_odd_columns_scalar_paths():
+    # unit_cols odd (scalar common-mode loads), cols % 4 != 0 (scalar stencil)
+    det = synth.Detector(n_modules=2, rows=64, cols=198, unit_rows=64,
+                         unit_cols=99, occupancy=0.02)
+    assert _run_case(det, 3).n_hits > 0
+
+
+def test_bank_median_below_window_uses_whole_unit_select():
+    # d is about -400 ADU, below the window [cut - 512, cut) = [-312, 200)
+    det = synth.cspad_2p2m(n_modules=2)
+    ref = _run_case(det, 2, ped_shift=400.0)
+    assert ref.n_hits > 0 and float(ref.cm.max()) < -312.0
+
+
+def test_bank_flat_frames_overflow_candidates():
+    # no noise and integer pedestals: every d of a bank is the same value,
+    # so one 1/8-ADU bin holds the whole bank (more than the candidate buffer)
+    det = synth.cspad_2p2m(n_modules=2, noise_sigma=0.0)
+    ref = _run_case(det, 2, integer_ped=True)
+    assert ref.n_hits > 0
+
+
+def test_bank_unanchored_cut_generic_path():
+    det = synth.cspad_2p2m(n_modules=2)
+    _run_case(det, 2, thr_over=dict(cm_cut_adu=200.3))
+
+
+def test_bank_min_count_not_reached():
+    det = synth.cspad_2p2m(n_modules=1, occupancy=0.02)
+    ref = _run_case(det, 2, thr_over=dict(cm_min_count=40000))
+    assert not ref.cm.any()
+
+
 def test_cm_none_and_masked_pixels():
     det = synth.asic_352x384(rows=32)
     ped, gain = synth.maps(det)
@@ -239,3 +288,24 @@ def test_full_size_cspad_batch_sampled():
         mine["frame"] = 0
         assert sort_hits(mine).tobytes() == sort_hits(ref.hits).tobytes()
         assert cm_all[f].tobytes() == ref.cm.reshape(-1).tobytes()
+
+
+@pytest.mark.parametrize("tuning", [dict(chunk_frames=1, overlap=1),
+                                    dict(chunk_frames=3, overlap=0),
+                                    dict(chunk_frames=2, band_rows=4, overlap=1),
+                                    dict(chunk_frames=5, band_rows=17, overlap=1)])
+def test_results_independent_of_tuning(tuning):
+    """Chunking, band height and the two-stream overlap change only the
+    launch schedule: hits (as a set), common mode and summaries are equal."""
+    det = synth.cspad_2p2m(n_modules=3, occupancy=0.01)
+    ped, gain = synth.maps(det)
+    raw, _ = synth.frames(det, ped, gain, 0, 11)
+    geom, thr = det.geometry(), det.thresholds()
+    ctx = _ctx(geom, thr, ped, gain)
+    pd.pd_set_tuning(ctx, **tuning)
+    got = pd.pd_get_tuning(ctx)
+    assert got["chunk_frames"] == tuning["chunk_frames"]
+    out = pd.process(ctx, pd.frames_to_device(raw), corrected=True, cm=True)
+    torch.cuda.synchronize()
+    ref = _oracle(geom, thr, ped, gain, raw, want_corrected=True)
+    _compare(ctx, out, ref, 11)
