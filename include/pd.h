@@ -157,6 +157,31 @@ int pd_query(const pd_ctx* ctx, pd_info* info);
 int pd_process(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frames,
                uint32_t frame_base, const pd_outputs* out, void* stream);
 
+/* pd_process_noalloc — the same chain as pd_process, for callers that must
+ * not allocate device memory during processing: for example a real-time
+ * acquisition thread whose latency budget forbids the device-wide
+ * synchronisation an allocation can cause, or a process whose device memory
+ * is entirely owned by another allocator, so cudaMalloc would fail.
+ * pd_process may allocate (it grows its common-mode scratch on demand);
+ * this entry point never calls cudaMalloc, cudaFree or any allocating
+ * routine.  The paper has no counterpart; this is a deployment variant.
+ *
+ * Its common-mode scratch is one fixed device array inside the library,
+ * PD_NOALLOC_MAX_CM floats (4 MiB), present on every GPU that loads the
+ * library until the process exits.  Limit: when out->cm is NULL,
+ * n_frames * units_per_frame must not exceed PD_NOALLOC_MAX_CM, else the
+ * call returns PD_EINVAL (split the call, or pass out->cm, which is then
+ * used instead).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any
+ * stream capture.  The array is shared by all calls and keeps the last
+ * call's values; nothing in it needs clearing (every value is written
+ * before it is read), but calls whose work overlaps on the GPU (different
+ * streams, no ordering between them) race on it: order them.  Runs on
+ * `stream` alone.  Arguments, outputs and errors as pd_process. */
+#define PD_NOALLOC_MAX_CM (1u << 20)
+int pd_process_noalloc(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frames,
+                       uint32_t frame_base, const pd_outputs* out, void* stream);
+
 /* pd_process_host — the same chain on host-resident frames.  Copies the
  * frames to the device in chunks (pipelined on two internal streams, so
  * page-locked host memory gives full link speed), processes them, and

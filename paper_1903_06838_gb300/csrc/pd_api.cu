@@ -278,6 +278,61 @@ int run_chain(pd_ctx* c, const uint16_t* frames, uint32_t n_frames, uint32_t fra
 
 }  // namespace
 
+namespace pd {
+
+int internal_fail(int code, const char* why) { return fail(code, why ? why : "error"); }
+
+uint32_t internal_units_per_frame(const pd_ctx* c) { return c->params.units_per_frame; }
+
+int internal_check_process_args(const pd_ctx* c, const uint16_t* frames, uint32_t n_frames,
+                                const pd_outputs* out, const char** why) {
+    if (!c || !out) {
+        *why = "NULL argument";
+        return PD_EINVAL;
+    }
+    if (!out->n_hits || (!out->hits && out->hit_capacity)) {
+        *why = "hits/n_hits are required";
+        return PD_EINVAL;
+    }
+    if (n_frames && !frames) {
+        *why = "frames are NULL";
+        return PD_EINVAL;
+    }
+    if (!aligned(frames, 16) || !aligned(out->n_hits, 4) || !aligned(out->hits, 8) ||
+        (out->corrected && !aligned(out->corrected, 16)) || (out->cm && !aligned(out->cm, 4))) {
+        *why = "misaligned frames or output buffer";
+        return PD_EALIGN;
+    }
+    return PD_OK;
+}
+
+int internal_run_sequential(pd_ctx* c, const uint16_t* frames, uint32_t n_frames,
+                            uint32_t frame_base, const pd_outputs* out, float* cm,
+                            cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out->n_hits, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return fail_cuda(e, "zero n_hits");
+    for (uint32_t done = 0; done < n_frames;) {
+        const uint32_t nf = std::min(c->chunk_frames, n_frames - done);
+        const uint16_t* fr = frames + (size_t)done * c->params.frame_px;
+        float* cmc = cm + (size_t)done * c->params.units_per_frame;
+        e = c->use_cm_big ? launch_cm_big(c->params, c->cm_cfg, fr, nf, cmc, s)
+                          : launch_cm_select(c->params, fr, nf, cmc, s);
+        if (e != cudaSuccess) return fail_cuda(e, "common-mode kernel launch");
+        CallOut co{out->hits, out->hit_capacity, out->n_hits,
+                   out->corrected ? out->corrected + (size_t)done * c->params.frame_px
+                                  : nullptr,
+                   cmc};
+        e = c->use_band ? launch_stencil_band(c->params, c->band_cfg, fr, nf, frame_base + done,
+                                              co, s)
+                        : launch_stencil(c->params, fr, nf, frame_base + done, co, s);
+        if (e != cudaSuccess) return fail_cuda(e, "stencil kernel launch");
+        done += nf;
+    }
+    return PD_OK;
+}
+
+}  // namespace pd
+
 extern "C" {
 
 const char* pd_strerror(int code) {

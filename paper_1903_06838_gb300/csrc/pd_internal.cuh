@@ -57,4 +57,15 @@ size_t cm_select_smem_bytes(const ChainParams& p);
 
 int device_sm_count();
 
+// Helpers of pd_process_noalloc (pd_api.cu).  None of them allocates.
+int internal_fail(int code, const char* why);
+int internal_check_process_args(const pd_ctx* ctx, const uint16_t* frames, uint32_t n_frames,
+                                const pd_outputs* out, const char** why);
+uint32_t internal_units_per_frame(const pd_ctx* ctx);
+// The chain on `stream` only (no second stream), with caller-provided
+// common-mode storage of n_frames * units_per_frame floats.
+int internal_run_sequential(pd_ctx* ctx, const uint16_t* frames, uint32_t n_frames,
+                            uint32_t frame_base, const pd_outputs* out, float* cm,
+                            cudaStream_t stream);
+
 }  // namespace pd

@@ -20,7 +20,7 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_PKG, "libpd.so")
-SOURCES = ["pd_api.cu", "pd_chain.cu", "pd_fast.cu"]
+SOURCES = ["pd_api.cu", "pd_chain.cu", "pd_fast.cu", "pd_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
@@ -134,6 +134,7 @@ def _declare(lib):
                        ctypes.POINTER(PdThresholds), ctypes.POINTER(vp)], i32),
         "pd_query": ([vp, ctypes.POINTER(PdInfo)], i32),
         "pd_process": ([vp, vp, u32, u32, ctypes.POINTER(PdOutputs), vp], i32),
+        "pd_process_noalloc": ([vp, vp, u32, u32, ctypes.POINTER(PdOutputs), vp], i32),
         "pd_process_host": ([vp, vp, u32, u32, vp, u32,
                              ctypes.POINTER(u32)], i32),
         "pd_get_summary": ([vp, vp, vp, vp, vp], i32),
@@ -263,6 +264,20 @@ def pd_process(ctx: Context, frames_ptr: int, n_frames: int, frame_base: int,
     _check(load().pd_process(ctx.handle, frames_ptr, n_frames, frame_base,
                              ctypes.byref(out), _stream_handle(stream)),
            "pd_process")
+
+
+PD_NOALLOC_MAX_CM = 1 << 20
+
+
+def pd_process_noalloc(ctx: Context, frames_ptr: int, n_frames: int, frame_base: int,
+                       hits_ptr: int, hit_capacity: int, n_hits_ptr: int,
+                       corrected_ptr: int | None = None, cm_ptr: int | None = None,
+                       stream=None) -> None:
+    """pd_process without device allocation (fixed in-library scratch)."""
+    out = PdOutputs(hits_ptr, hit_capacity, n_hits_ptr, corrected_ptr, cm_ptr)
+    _check(load().pd_process_noalloc(ctx.handle, frames_ptr, n_frames, frame_base,
+                                     ctypes.byref(out), _stream_handle(stream)),
+           "pd_process_noalloc")
 
 
 def pd_process_host(ctx: Context, frames: np.ndarray, frame_base: int = 0,
