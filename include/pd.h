@@ -224,6 +224,51 @@ typedef struct {
 int pd_get_tuning(const pd_ctx* ctx, pd_tuning* tuning);
 int pd_set_tuning(pd_ctx* ctx, const pd_tuning* tuning);
 
+/* pd_autotune — choose the tuning of a context by timing candidates on the
+ * caller's device frames (n_frames, 16-byte aligned): chunk sizes of about
+ * 24-192 MB, band heights around the default, overlap on and off; each
+ * candidate runs once to warm up and twice timed (CUDA events).  The
+ * fastest is applied to the context and returned in *best (may be NULL),
+ * with its time per frame in microseconds.  Allocates and frees temporary
+ * device buffers; the context's summaries are saved and restored, so they
+ * are unchanged.  Synchronous.  The paper has no tuner; the tile shapes of
+ * a launch are this implementation's choice. */
+int pd_autotune(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frames,
+                pd_tuning* best, float* best_us_per_frame);
+
+/* Batched launches over contexts of different geometries.  One batch runs
+ * the common mode of every (item, frame, unit) in one persistent kernel and
+ * every stencil tile of every item in a second one, so frames of several
+ * detectors share two launches.  Each item is processed exactly as
+ * pd_process would (same results; summaries go to the item's context).
+ * Items must use the band stencil (every geometry with at most 2048
+ * columns per module); PD_ENOTSUP otherwise. */
+typedef struct {
+    pd_ctx* ctx;
+    const uint16_t* frames;  /* device, 16-byte aligned                     */
+    uint32_t n_frames;
+    uint32_t frame_base;
+    pd_outputs out;          /* as pd_process; out.cm NULL uses the batch's
+                                scratch                                     */
+} pd_batch_item;
+
+typedef struct pd_batch pd_batch;
+
+/* Allocates the device item table (max_items) and a common-mode scratch of
+ * max_cm_values floats for items that pass out.cm == NULL. */
+int pd_batch_create(uint32_t max_items, uint64_t max_cm_values, pd_batch** out);
+/* Enqueue a batch on `stream` (asynchronous). */
+int pd_batch_process(pd_batch* batch, const pd_batch_item* items, uint32_t n_items,
+                     void* stream);
+/* Record the same work as a CUDA graph held by the batch (replacing any
+ * earlier one); `stream` must not be the legacy default stream.  Nothing
+ * runs until pd_batch_replay.  The graph keeps the items' pointers: each
+ * replay processes whatever the same frame buffers hold at that time. */
+int pd_batch_capture(pd_batch* batch, const pd_batch_item* items, uint32_t n_items,
+                     void* stream);
+int pd_batch_replay(pd_batch* batch, void* stream);
+void pd_batch_destroy(pd_batch* batch);
+
 /* Kernel timing.  When enabled on a context, every kernel the context
  * launches is bracketed by CUDA events recorded on the launching stream;
  * pd_read_profile synchronises the device, reports the summed device time

@@ -657,6 +657,268 @@ int pd_read_profile(pd_ctx* c, pd_profile* out) {
     return PD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batched launches over contexts of different geometries.
+struct pd_batch {
+    uint32_t max_items = 0;
+    uint64_t max_cm = 0;
+    pd::BatchItem* d_table[2] = {nullptr, nullptr};  // [0] direct calls, [1] graph
+    pd::BatchItem* h_table[2] = {nullptr, nullptr};  // page-locked staging
+    cudaEvent_t copied = nullptr;                    // staging [0] free again
+    bool copy_pending = false;
+    float* d_cm = nullptr;  // common mode of items that pass out.cm == NULL
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void free_batch(pd_batch* b) {
+    if (!b) return;
+    for (int i = 0; i < 2; i++) {
+        cudaFree(b->d_table[i]);
+        cudaFreeHost(b->h_table[i]);
+    }
+    cudaFree(b->d_cm);
+    if (b->copied) cudaEventDestroy(b->copied);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    delete b;
+}
+
+int batch_enqueue(pd_batch* b, int slot, const pd_batch_item* items, uint32_t n,
+                  cudaStream_t s) {
+    if (!items || n == 0 || n > b->max_items) return fail(PD_EINVAL, "batch: 1..max_items items");
+    if (slot == 0 && b->copy_pending) {
+        cudaError_t e = cudaEventSynchronize(b->copied);
+        if (e != cudaSuccess) return fail_cuda(e, "batch staging wait");
+        b->copy_pending = false;
+    }
+    pd::BatchItem* h = b->h_table[slot];
+    unsigned long long cm_tasks = 0, tiles = 0;
+    uint64_t cm_used = 0;
+    size_t cm_smem = 0, band_smem = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        const pd_batch_item& it = items[i];
+        pd_ctx* c = it.ctx;
+        const char* why = nullptr;
+        int rc = pd::internal_check_process_args(c, it.frames, it.n_frames, &it.out, &why);
+        if (rc) return fail(rc, why);
+        if (!c->use_band) return fail(PD_ENOTSUP, "batch: geometry needs the band stencil");
+        pd::BatchItem& d = h[i];
+        d.p = c->params;
+        d.cm_cfg = c->cm_cfg;
+        d.band_cfg = c->band_cfg;
+        const size_t gen_keys = (size_t)c->params.unit_px * 4;
+        if (c->use_cm_big) {
+            d.cm_kind = c->cm_cfg.vec == 2 ? 0u : 1u;
+            cm_smem = std::max(cm_smem, pd::cm_big_smem_bytes(c->params));
+        } else if (gen_keys <= pd::kCmBigMaxSmem) {
+            d.cm_kind = 2;
+            cm_smem = std::max(cm_smem, gen_keys);
+        } else {
+            d.cm_kind = 3;
+        }
+        d.band_vec = c->band_cfg.vec;
+        band_smem = std::max(band_smem, pd::band_smem_bytes(c->params, c->band_cfg.rb,
+                                                            c->band_cfg.pitch));
+        d.raw = it.frames;
+        d.n_frames = it.n_frames;
+        d.frame_base = it.frame_base;
+        const uint64_t ncm = (uint64_t)it.n_frames * c->params.units_per_frame;
+        float* cm = it.out.cm;
+        if (!cm) {
+            if (cm_used + ncm > b->max_cm) return fail(PD_EINVAL, "batch: common-mode scratch too small");
+            cm = b->d_cm + cm_used;
+            cm_used += ncm;
+        }
+        d.out = pd::CallOut{it.out.hits, it.out.hit_capacity, it.out.n_hits, it.out.corrected, cm};
+        d.cm_first = cm_tasks;
+        d.st_first = tiles;
+        d.st_tiles = (unsigned long long)it.n_frames * c->params.n_modules * c->band_cfg.n_bands;
+        cm_tasks += ncm;
+        tiles += d.st_tiles;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_table[slot], h, n * sizeof(pd::BatchItem),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail_cuda(e, "batch table upload");
+    if (slot == 0) {
+        if ((e = cudaEventRecord(b->copied, s))) return fail_cuda(e, "batch event");
+        b->copy_pending = true;
+    }
+    for (uint32_t i = 0; i < n; i++)
+        if ((e = cudaMemsetAsync(items[i].out.n_hits, 0, sizeof(uint32_t), s)))
+            return fail_cuda(e, "zero n_hits");
+    e = pd::launch_batch(b->d_table[slot], n, cm_tasks, cm_smem, band_smem, s);
+    if (e != cudaSuccess) return fail_cuda(e, "batch kernel launch");
+    return PD_OK;
+}
+
+}  // namespace
+
+int pd_batch_create(uint32_t max_items, uint64_t max_cm_values, pd_batch** out) {
+    if (!out || !max_items) return fail(PD_EINVAL, "batch: need out and max_items > 0");
+    *out = nullptr;
+    pd_batch* b = new (std::nothrow) pd_batch();
+    if (!b) return fail(PD_ENOMEM, "host allocation failed");
+    b->max_items = max_items;
+    b->max_cm = max_cm_values;
+    cudaError_t e;
+    for (int i = 0; i < 2; i++) {
+        if ((e = cudaMalloc(&b->d_table[i], max_items * sizeof(pd::BatchItem))) ||
+            (e = cudaMallocHost(&b->h_table[i], max_items * sizeof(pd::BatchItem)))) {
+            free_batch(b);
+            return fail(PD_ENOMEM, "batch table allocation failed");
+        }
+    }
+    if (max_cm_values && (e = cudaMalloc(&b->d_cm, max_cm_values * sizeof(float)))) {
+        free_batch(b);
+        return fail(PD_ENOMEM, "batch scratch allocation failed");
+    }
+    if ((e = cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming))) {
+        free_batch(b);
+        return fail_cuda(e, "batch event");
+    }
+    // kernel attributes and the SM count are set up here, outside any capture
+    pd::device_sm_count();
+    if ((e = pd::launch_batch(nullptr, 0, 0, 0, 0, nullptr)) != cudaSuccess) {
+        free_batch(b);
+        return fail_cuda(e, "batch kernel attributes");
+    }
+    *out = b;
+    return PD_OK;
+}
+
+int pd_batch_process(pd_batch* b, const pd_batch_item* items, uint32_t n_items, void* stream) {
+    if (!b) return fail(PD_EINVAL, "NULL batch");
+    return batch_enqueue(b, 0, items, n_items, (cudaStream_t)stream);
+}
+
+int pd_batch_capture(pd_batch* b, const pd_batch_item* items, uint32_t n_items, void* stream) {
+    if (!b || !stream) return fail(PD_EINVAL, "batch capture needs a batch and a non-default stream");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(s);  // earlier replays may still read table [1]
+    if (e != cudaSuccess) return fail_cuda(e, "batch capture synchronise");
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)))
+        return fail_cuda(e, "begin capture");
+    int rc = batch_enqueue(b, 1, items, n_items, s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "end capture");
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        return fail_cuda(e, "graph instantiate");
+    }
+    return PD_OK;
+}
+
+int pd_batch_replay(pd_batch* b, void* stream) {
+    if (!b || !b->exec) return fail(PD_EINVAL, "batch has no captured graph");
+    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? PD_OK : fail_cuda(e, "graph launch");
+}
+
+void pd_batch_destroy(pd_batch* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    free_batch(b);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: times candidate launch settings on the caller's frames.
+int pd_autotune(pd_ctx* c, const uint16_t* frames_dev, uint32_t n_frames, pd_tuning* best,
+                float* best_us_per_frame) {
+    if (!c || !frames_dev || !n_frames) return fail(PD_EINVAL, "autotune needs frames");
+    if (!aligned(frames_dev, 16)) return fail(PD_EALIGN, "frames must be 16-byte aligned");
+    const pd::ChainParams& p = c->params;
+    const size_t fpx = p.frame_px;
+    const uint32_t cap = (uint32_t)std::min<uint64_t>((uint64_t)n_frames * fpx / 8 + 1024, 1u << 26);
+    pd_hit* hits = nullptr;
+    uint32_t* nh = nullptr;
+    uint32_t* save_map = nullptr;
+    unsigned long long* save_hist = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e;
+    int rc = PD_OK;
+    // the summaries are saved and restored around the timing runs
+    if ((e = cudaMalloc(&hits, (size_t)cap * sizeof(pd_hit))) ||
+        (e = cudaMalloc(&nh, sizeof(uint32_t))) ||
+        (e = cudaMalloc(&save_map, fpx * 4)) ||
+        (e = cudaMalloc(&save_hist, 2 * (size_t)p.hist_bins * 8)) ||
+        (e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1))) {
+        rc = fail(PD_ENOMEM, "autotune allocation failed");
+    }
+    pd_tuning orig{};
+    pd_get_tuning(c, &orig);
+    pd_tuning best_t = orig;
+    float best_ms = 1e30f;
+    if (!rc) {
+        cudaMemcpy(save_map, c->d_count_map, fpx * 4, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(save_hist, c->d_hist_pix, p.hist_bins * 8, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(save_hist + p.hist_bins, c->d_hist_hit, p.hist_bins * 8,
+                   cudaMemcpyDeviceToDevice);
+        const size_t fbytes = fpx * 2;
+        std::vector<uint32_t> chunks;
+        for (size_t mb : {24, 48, 96, 192}) {
+            const uint32_t cf = (uint32_t)std::max<size_t>(1, ((size_t)mb << 20) / fbytes);
+            if (std::find(chunks.begin(), chunks.end(), cf) == chunks.end()) chunks.push_back(cf);
+        }
+        std::vector<uint32_t> bands = {0};
+        if (c->use_band) {
+            const uint32_t rb = c->band_cfg.rb;
+            for (uint32_t v : {rb / 2, rb * 3 / 2, rb * 2})
+                if (v >= 2 && v != rb) bands.push_back(v);
+        }
+        pd_outputs o{};
+        o.hits = hits;
+        o.hit_capacity = cap;
+        o.n_hits = nh;
+        for (uint32_t cf : chunks)
+            for (uint32_t bd : bands)
+                for (uint32_t ov : {1u, 0u}) {
+                    pd_tuning t{cf, bd ? bd : orig.band_rows, ov, 0};
+                    if (pd_set_tuning(c, &t) != PD_OK) continue;
+                    if (run_chain(c, frames_dev, n_frames, 0, &o, nullptr) != PD_OK) continue;
+                    cudaEventRecord(e0, nullptr);
+                    for (int k = 0; k < 2; k++) run_chain(c, frames_dev, n_frames, 0, &o, nullptr);
+                    cudaEventRecord(e1, nullptr);
+                    if ((e = cudaEventSynchronize(e1))) {
+                        rc = fail_cuda(e, "autotune run");
+                        break;
+                    }
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        pd_get_tuning(c, &best_t);
+                    }
+                }
+        cudaMemcpy(c->d_count_map, save_map, fpx * 4, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(c->d_hist_pix, save_hist, p.hist_bins * 8, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(c->d_hist_hit, save_hist + p.hist_bins, p.hist_bins * 8,
+                   cudaMemcpyDeviceToDevice);
+    }
+    pd_set_tuning(c, rc ? &orig : &best_t);
+    cudaFree(hits);
+    cudaFree(nh);
+    cudaFree(save_map);
+    cudaFree(save_hist);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (best) *best = best_t;
+    if (best_us_per_frame) *best_us_per_frame = best_ms * 1e3f / (2.0f * n_frames);
+    return best_ms < 1e30f ? PD_OK : fail(PD_ECUDA, "autotune: no candidate ran");
+}
+
 void pd_destroy(pd_ctx* c) {
     if (!c) return;
     cudaDeviceSynchronize();

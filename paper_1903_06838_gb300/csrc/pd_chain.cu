@@ -3,7 +3,7 @@
 //   cm_select_kernel  common mode of one unit (paper section "Common Mode",
 //                     Fig. c): exact lower median of d = raw - pedestal over
 //                     the unit's pixels with d < cut, found by a 4-pass
-//                     8-bit radix select on order-preserving 32-bit keys.
+//                     8-bit radix select (pd_cm_generic.cuh).
 //   stencil_kernel    dark, common mode and gain correction (Fig. b), noise
 //                     zeroing, 3x3 local maximum, charge sum, photon count
 //                     (Fig. e), centre-of-mass offset (Fig. f), warp-ballot
@@ -15,23 +15,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "pd_cm_generic.cuh"
 #include "pd_internal.cuh"
 
 namespace pd {
 
 namespace {
-
-constexpr uint32_t kSentinel = 0xFFFFFFFFu;  // "not in the common-mode set"
-
-// Unsigned order of the keys == ascending IEEE order, with -0 below +0.
-__device__ __forceinline__ uint32_t order_key(float v) {
-    const uint32_t b = __float_as_uint(v);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-
-__device__ __forceinline__ float key_value(uint32_t k) {
-    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
-}
 
 __device__ __forceinline__ uint32_t hist_bin(float v, float neg_lo_s, float inv_w,
                                              uint32_t bins) {
@@ -50,100 +39,8 @@ __global__ void __launch_bounds__(kCmThreads)
     cm_select_kernel(ChainParams p, const uint16_t* __restrict__ raw,
                      float* __restrict__ cm_out) {
     extern __shared__ uint32_t keys[];
-    __shared__ uint32_t hist[256];
-    __shared__ uint32_t warp_cnt[kCmThreads / 32];
-    __shared__ uint32_t s_prefix, s_rank;
-
-    const uint32_t item = blockIdx.x;
-    const uint32_t f = item / p.units_per_frame;
-    const uint32_t u = item % p.units_per_frame;
-    if (p.cm_mode == PD_CM_NONE) {
-        if (threadIdx.x == 0) cm_out[item] = 0.0f;
-        return;
-    }
-    const uint32_t m = u / p.units_per_module;
-    const uint32_t um = u % p.units_per_module;
-    const uint32_t r0 = (um / p.units_per_row) * p.unit_rows;
-    const uint32_t c0 = (um % p.units_per_row) * p.unit_cols;
-    const size_t mod_base = (size_t)m * p.module_px;
-    const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
-    const float* pm = p.ped + mod_base;
-
-    auto key_at = [&](uint32_t i) -> uint32_t {
-        const uint32_t off = (r0 + i / p.unit_cols) * p.cols + c0 + i % p.unit_cols;
-        const float d = __fsub_rn(__uint2float_rn(fr[off]), pm[off]);
-        return d < p.cm_cut ? order_key(d) : kSentinel;
-    };
-
-    uint32_t cnt = 0;
-    for (uint32_t i = threadIdx.x; i < p.unit_px; i += kCmThreads) {
-        const uint32_t k = key_at(i);
-        if (KEYS_IN_SMEM) keys[i] = k;
-        cnt += (k != kSentinel);
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if (lane == 0) warp_cnt[warp] = cnt;
-    __syncthreads();
-    uint32_t n = 0;
-#pragma unroll
-    for (int w = 0; w < kCmThreads / 32; w++) n += warp_cnt[w];
-    if (n == 0 || n < p.cm_min_count) {
-        if (threadIdx.x == 0) cm_out[item] = 0.0f;
-        return;
-    }
-    if (threadIdx.x == 0) {
-        s_prefix = 0;
-        s_rank = (n - 1) / 2;
-    }
-    // Radix select, most significant byte first.
-    for (int pass = 0; pass < 4; pass++) {
-        const int shift = 24 - 8 * pass;
-        for (int b = threadIdx.x; b < 256; b += kCmThreads) hist[b] = 0;
-        __syncthreads();
-        const uint32_t prefix = s_prefix;
-        for (uint32_t i = threadIdx.x; i < p.unit_px; i += kCmThreads) {
-            const uint32_t k = KEYS_IN_SMEM ? keys[i] : key_at(i);
-            if (k == kSentinel) continue;
-            if (pass > 0 && (k >> (shift + 8)) != prefix) continue;
-            atomicAdd(&hist[(k >> shift) & 255u], 1u);
-        }
-        __syncthreads();
-        if (warp == 0) {
-            // lane l owns bins 8l..8l+7
-            uint32_t loc[8], sum = 0;
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                loc[j] = hist[lane * 8 + j];
-                sum += loc[j];
-            }
-            uint32_t incl = sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const uint32_t excl = incl - sum;
-            const uint32_t rank = s_rank;
-            if (excl <= rank && rank < incl) {
-                uint32_t below = excl;
-                int digit = lane * 8;
-#pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    if (below + loc[j] > rank) {
-                        digit = lane * 8 + j;
-                        break;
-                    }
-                    below += loc[j];
-                }
-                s_prefix = (prefix << 8) | (uint32_t)digit;
-                s_rank = rank - below;
-            }
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) cm_out[item] = key_value(s_prefix);
+    __shared__ generic_cm::Shared sh;
+    generic_cm::unit<KEYS_IN_SMEM>(p, raw, cm_out, blockIdx.x, keys, sh);
 }
 
 // ---------------------------------------------------------------------------

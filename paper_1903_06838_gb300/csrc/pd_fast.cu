@@ -31,6 +31,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "pd_cm_generic.cuh"
 #include "pd_fast.cuh"
 
 namespace pd {
@@ -50,14 +51,6 @@ __device__ __forceinline__ float key_value(uint32_t k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
-// Exact float of a 16-bit raw value: 2^23 + raw has the raw value as its low
-// mantissa bits; subtracting 2^23 is exact.
-__device__ __forceinline__ float raw_lo(uint32_t x) {
-    return __fsub_rn(__uint_as_float(__byte_perm(x, 0x4B00u, 0x5410u)), 8388608.0f);
-}
-__device__ __forceinline__ float raw_hi(uint32_t x) {
-    return __fsub_rn(__uint_as_float(__byte_perm(x, 0x4B00u, 0x5432u)), 8388608.0f);
-}
 
 // Histogram bin of the summaries: floor(fma(v, inv_w, -lo_s)) clipped to
 // [0, bins-1], as the code of an element of a 32-bit histogram array.
@@ -70,7 +63,8 @@ __device__ __forceinline__ uint32_t summary_bin(float v, float inv_w, float neg_
     return (uint32_t)(b - (int)kMagicBits);
 }
 
-// Two raw values of a packed pair as exact floats (2^23 + raw, minus 2^23).
+// Two raw values of a packed pair as exact floats: 2^23 + raw has the raw
+// value as its low mantissa bits, and subtracting 2^23 is exact.
 __device__ __forceinline__ float2 raw_pair(uint32_t x) {
     const float2 biased = make_float2(__uint_as_float(__byte_perm(x, 0x4B00u, 0x5410u)),
                                       __uint_as_float(__byte_perm(x, 0x4B00u, 0x5432u)));
@@ -274,23 +268,29 @@ __device__ void find_rank(const uint32_t* hist, TargetFn target_of, uint32_t* gs
 
 // ---------------------------------------------------------------------------
 // Common mode of large units.
+struct CmBigShared {
+    uint32_t gsum[kCmBins / 32];
+    uint32_t swarp[32];
+    uint32_t s_bin, s_rank, s_n, s_cand, s_prefix, s_rrank;
+};
+
+// Common mode of unit `item` (= frame * units_per_frame + unit) into
+// cm_out[item]; cm_smem: cm_big_smem_bytes(p) of dynamic shared memory.
 template <int VEC>
-__global__ void __launch_bounds__(512, 2)
-    cm_big_kernel(ChainParams p, const uint16_t* __restrict__ raw,
-                  float* __restrict__ cm_out, CmBigConfig cfg) {
-    extern __shared__ __align__(16) uint32_t cm_smem[];
+__device__ void cm_big_unit(const ChainParams& p, const uint16_t* __restrict__ raw,
+                            float* __restrict__ cm_out, const CmBigConfig& cfg, uint32_t item,
+                            uint32_t* cm_smem, CmBigShared& sh) {
     uint32_t* hist = cm_smem;                            // kCmBins + spare + pad
     float* cand = reinterpret_cast<float*>(hist + kCmBins + 4);  // kCandCap
     uint32_t* codes = reinterpret_cast<uint32_t*>(cand + kCandCap);  // VEC=2: pairs
-    __shared__ uint32_t gsum[kCmBins / 32];
-    __shared__ uint32_t swarp[32];
-    __shared__ uint32_t s_bin, s_rank, s_n, s_cand, s_prefix, s_rrank;
+    uint32_t* gsum = sh.gsum;
+    uint32_t* swarp = sh.swarp;
+    uint32_t &s_bin = sh.s_bin, &s_rank = sh.s_rank, &s_n = sh.s_n, &s_cand = sh.s_cand;
+    uint32_t &s_prefix = sh.s_prefix, &s_rrank = sh.s_rrank;
 
-    const uint32_t item = blockIdx.x;
     const uint32_t f = item / p.units_per_frame;
     const uint32_t u = item % p.units_per_frame;
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5;
     if (p.cm_mode == PD_CM_NONE) {
         if (tid == 0) cm_out[item] = 0.0f;
         return;
@@ -332,9 +332,8 @@ __global__ void __launch_bounds__(512, 2)
                     src += sstride;
                     dst += TY * TX;
                 }
-                cp_async_wait_all();
+                cp_async_wait_all();  // each thread reads back only its own copies
             }
-            __syncwarp();
             constexpr int U = 8;
             const float2* prow = reinterpret_cast<const float2*>(npm + (r0 + ty) * p.cols + c0) + tx;
             const uint32_t stride = TY * p.cols / 2;  // pairs between a thread's rows
@@ -495,22 +494,39 @@ __global__ void __launch_bounds__(512, 2)
     if (tid == 0) cm_out[item] = key_value(key);
 }
 
+template <int VEC>
+__global__ void __launch_bounds__(512, 2)
+    cm_big_kernel(ChainParams p, const uint16_t* __restrict__ raw,
+                  float* __restrict__ cm_out, CmBigConfig cfg) {
+    extern __shared__ __align__(16) uint32_t cm_smem[];
+    __shared__ CmBigShared sh;
+    cm_big_unit<VEC>(p, raw, cm_out, cfg, blockIdx.x, cm_smem, sh);
+}
+
 // ---------------------------------------------------------------------------
 // Stencil over bands of full-width rows.
+struct BandShared {
+    uint32_t s_list_n;
+    uint32_t swarp[32];
+};
+
+// Tiles first, first + step, ... < n_tiles of one call: tile t is band
+// t % n_bands of module (t / n_bands) % n_modules of frame t / (n_bands *
+// n_modules).  Zeroes this CTA's shared tile and histograms first and adds
+// the histograms to the context's at the end.
 template <int VEC>
-__global__ void __launch_bounds__(kBandThreads)
-    stencil_band_kernel(ChainParams p, const uint16_t* __restrict__ raw,
-                        uint32_t frame_base, CallOut out, BandConfig bc,
-                        unsigned long long n_tiles) {
-    extern __shared__ __align__(16) uint32_t band_smem[];
+__device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restrict__ raw,
+                                 uint32_t frame_base, const CallOut& out, const BandConfig& bc,
+                                 unsigned long long first, unsigned long long n_tiles,
+                                 unsigned long long step, uint32_t* band_smem, BandShared& bsh) {
     const uint32_t P = bc.pitch;                 // floats per s-tile row
     float* stile = reinterpret_cast<float*>(band_smem);          // (rb+2) * P
     uint32_t* hpix = band_smem + (bc.rb + 2) * P;               // hist_bins + spare
     uint32_t* hhit = hpix + p.hist_bins + 4;                     // hist_bins
     uint32_t* list = hhit + p.hist_bins;                         // kSeedCap
     float* cmt = reinterpret_cast<float*>(list + kSeedCap);      // (rb+2) * upr
-    __shared__ uint32_t s_list_n;
-    __shared__ uint32_t swarp[32];
+    uint32_t& s_list_n = bsh.s_list_n;
+    uint32_t* swarp = bsh.swarp;
 
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31;
@@ -532,7 +548,7 @@ __global__ void __launch_bounds__(kBandThreads)
     for (uint32_t i = tid; i < 2 * p.hist_bins + 4; i += nthr) hpix[i] = 0;
     __syncthreads();
 
-    for (unsigned long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    for (unsigned long long t = first; t < n_tiles; t += step) {
         unsigned long long q = t;
         const int band = (int)(q % bc.n_bands);
         q /= bc.n_bands;
@@ -768,7 +784,106 @@ __global__ void __launch_bounds__(kBandThreads)
     }
 }
 
+template <int VEC>
+__global__ void __launch_bounds__(kBandThreads)
+    stencil_band_kernel(ChainParams p, const uint16_t* __restrict__ raw,
+                        uint32_t frame_base, CallOut out, BandConfig bc,
+                        unsigned long long n_tiles) {
+    extern __shared__ __align__(16) uint32_t band_smem[];
+    __shared__ BandShared bsh;
+    stencil_band_run<VEC>(p, raw, frame_base, out, bc, blockIdx.x, n_tiles, gridDim.x,
+                          band_smem, bsh);
+}
+
+// ---------------------------------------------------------------------------
+// Batched launches: the common mode of every (item, frame, unit) task of a
+// batch of contexts in one persistent kernel, and every band tile of every
+// item in one persistent stencil kernel.  Each CTA dispatches on the item's
+// kind to the same device functions the single-context kernels use.
+__device__ __forceinline__ uint32_t find_item(const BatchItem* items, uint32_t n_items,
+                                              unsigned long long t, bool stencil) {
+    uint32_t lo = 0, hi = n_items;  // last item whose first task <= t
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        const unsigned long long first = stencil ? items[mid].st_first : items[mid].cm_first;
+        if (first <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(512, 2)
+    batch_cm_kernel(const BatchItem* __restrict__ items, uint32_t n_items,
+                    unsigned long long n_tasks) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ CmBigShared big;
+    __shared__ generic_cm::Shared gen;
+    for (unsigned long long t = blockIdx.x; t < n_tasks; t += gridDim.x) {
+        const uint32_t i = find_item(items, n_items, t, false);
+        const BatchItem& it = items[i];
+        const uint32_t local = (uint32_t)(t - it.cm_first);
+        switch (it.cm_kind) {
+            case 0: cm_big_unit<2>(it.p, it.raw, it.out.cm, it.cm_cfg, local, smem, big); break;
+            case 1: cm_big_unit<1>(it.p, it.raw, it.out.cm, it.cm_cfg, local, smem, big); break;
+            case 2: generic_cm::unit<true>(it.p, it.raw, it.out.cm, local, smem, gen); break;
+            default: generic_cm::unit<false>(it.p, it.raw, it.out.cm, local, smem, gen); break;
+        }
+        __syncthreads();  // shared memory is reused by the next task
+    }
+}
+
+__global__ void __launch_bounds__(kBandThreads, 2)
+    batch_stencil_kernel(const BatchItem* __restrict__ items, uint32_t n_items) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ BandShared bsh;
+    const unsigned long long G = gridDim.x, b = blockIdx.x;
+    for (uint32_t i = 0; i < n_items; i++) {
+        const BatchItem& it = items[i];
+        const unsigned long long n = it.st_tiles;
+        const unsigned long long first = (b + G - it.st_first % G) % G;
+        if (first >= n) continue;
+        if (it.band_vec == 4)
+            stencil_band_run<4>(it.p, it.raw, it.frame_base, it.out, it.band_cfg, first, n, G,
+                                smem, bsh);
+        else
+            stencil_band_run<1>(it.p, it.raw, it.frame_base, it.out, it.band_cfg, first, n, G,
+                                smem, bsh);
+        __syncthreads();  // the next item re-zeroes the shared tile and histograms
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_batch(const BatchItem* items_dev, uint32_t n_items,
+                         unsigned long long cm_tasks, size_t cm_smem, size_t band_smem,
+                         cudaStream_t stream) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static int attr_dev = -1;
+    if (attr_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(batch_cm_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kCmBigMaxSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batch_stencil_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    if (!items_dev) return cudaSuccess;  // attribute set-up only
+    const unsigned sms = (unsigned)device_sm_count();
+    if (cm_tasks) {
+        unsigned long long grid = 2ull * sms;
+        if (grid > cm_tasks) grid = cm_tasks;
+        batch_cm_kernel<<<(unsigned)grid, 512, cm_smem, stream>>>(items_dev, n_items, cm_tasks);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = (int)((200 * 1024) / std::max<size_t>(band_smem, 1));
+    per_sm = std::max(1, std::min(per_sm, 2));
+    batch_stencil_kernel<<<(unsigned)(sms * per_sm), kBandThreads, band_smem, stream>>>(items_dev,
+                                                                                       n_items);
+    return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------------------
 bool cm_big_supported(const ChainParams& p, const CmBigConfig& cfg) {

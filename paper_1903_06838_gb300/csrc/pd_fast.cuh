@@ -35,6 +35,28 @@ struct BandConfig {
     bool ok;
 };
 
+// One item of a batched launch (device-side table entry).
+struct BatchItem {
+    ChainParams p;
+    CmBigConfig cm_cfg;
+    BandConfig band_cfg;
+    uint32_t cm_kind;   // 0/1: large-unit kernel (2 or 1 pixels per load),
+                        // 2/3: generic radix select (keys in shared / global)
+    uint32_t band_vec;  // 4 or 1
+    const uint16_t* raw;
+    uint32_t n_frames, frame_base;
+    CallOut out;                        // out.cm: this item's common mode
+    unsigned long long cm_first;        // first common-mode task of the item
+    unsigned long long st_first;        // first stencil tile of the item
+    unsigned long long st_tiles;        // stencil tiles of the item
+};
+
+// Common mode of every item in one launch, then every stencil tile in one
+// launch (both persistent), on `stream`.
+cudaError_t launch_batch(const BatchItem* items_dev, uint32_t n_items,
+                         unsigned long long cm_tasks, size_t cm_smem, size_t band_smem,
+                         cudaStream_t stream);
+
 CmBigConfig make_cm_big_config(const ChainParams& p);
 bool cm_big_supported(const ChainParams& p, const CmBigConfig& cfg);
 size_t cm_big_smem_bytes(const ChainParams& p);

@@ -80,6 +80,12 @@ class PdTuning(ctypes.Structure):
                 ("chunk_frames", "band_rows", "overlap", "reserved")]
 
 
+class PdBatchItem(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("frames", ctypes.c_void_p),
+                ("n_frames", ctypes.c_uint32), ("frame_base", ctypes.c_uint32),
+                ("out", PdOutputs)]
+
+
 class PdError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -141,6 +147,13 @@ def _declare(lib):
         "pd_reset_summary": ([vp, vp], i32),
         "pd_destroy": ([vp], None),
         "pd_set_profiling": ([vp, i32], i32),
+        "pd_autotune": ([vp, vp, u32, ctypes.POINTER(PdTuning),
+                         ctypes.POINTER(ctypes.c_float)], i32),
+        "pd_batch_create": ([u32, ctypes.c_uint64, ctypes.POINTER(vp)], i32),
+        "pd_batch_process": ([vp, ctypes.POINTER(PdBatchItem), u32, vp], i32),
+        "pd_batch_capture": ([vp, ctypes.POINTER(PdBatchItem), u32, vp], i32),
+        "pd_batch_replay": ([vp, vp], i32),
+        "pd_batch_destroy": ([vp], None),
         "pd_get_tuning": ([vp, ctypes.POINTER(PdTuning)], i32),
         "pd_set_tuning": ([vp, ctypes.POINTER(PdTuning)], i32),
         "pd_read_profile": ([vp, ctypes.POINTER(PdProfile)], i32),
@@ -347,6 +360,75 @@ def pd_read_profile(ctx: Context) -> dict:
            "pd_read_profile")
     return {pr.name[k].value.decode(): (pr.launches[k], pr.total_ms[k])
             for k in range(pr.n_kernels) if pr.launches[k]}
+
+
+def pd_autotune(ctx: Context, frames_ptr: int, n_frames: int):
+    """Time candidate tunings on device frames; apply and return the best
+    as (tuning dict, microseconds per frame)."""
+    t = PdTuning()
+    us = ctypes.c_float(0)
+    _check(load().pd_autotune(ctx.handle, frames_ptr, n_frames, ctypes.byref(t),
+                              ctypes.byref(us)), "pd_autotune")
+    return (dict(chunk_frames=t.chunk_frames, band_rows=t.band_rows,
+                 overlap=t.overlap), float(us.value))
+
+
+class Batch:
+    """A pd_batch (device item table + scratch, optional captured graph)."""
+
+    def __init__(self, max_items: int, max_cm_values: int = 1 << 22):
+        h = ctypes.c_void_p()
+        _check(load().pd_batch_create(max_items, max_cm_values, ctypes.byref(h)),
+               "pd_batch_create")
+        self.handle = h.value
+        self._keep = None
+
+    def close(self):
+        if self.handle:
+            load().pd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _batch_items(items):
+    """items: sequence of (ctx, frames_ptr, n_frames, frame_base, Outputs)."""
+    arr = (PdBatchItem * len(items))()
+    for k, (ctx, fptr, n, base, out) in enumerate(items):
+        o = out.ptrs()
+        arr[k] = PdBatchItem(ctx.handle, fptr, n, base,
+                             PdOutputs(o["hits_ptr"], o["hit_capacity"], o["n_hits_ptr"],
+                                       o["corrected_ptr"], o["cm_ptr"]))
+    return arr
+
+
+def pd_batch_create(max_items: int, max_cm_values: int = 1 << 22) -> Batch:
+    return Batch(max_items, max_cm_values)
+
+
+def pd_batch_process(batch: Batch, items, stream=None) -> None:
+    arr = _batch_items(items)
+    _check(load().pd_batch_process(batch.handle, arr, len(items), _stream_handle(stream)),
+           "pd_batch_process")
+
+
+def pd_batch_capture(batch: Batch, items, stream) -> None:
+    arr = _batch_items(items)
+    batch._keep = arr
+    _check(load().pd_batch_capture(batch.handle, arr, len(items), _stream_handle(stream)),
+           "pd_batch_capture")
+
+
+def pd_batch_replay(batch: Batch, stream=None) -> None:
+    _check(load().pd_batch_replay(batch.handle, _stream_handle(stream)), "pd_batch_replay")
+
+
+def pd_batch_destroy(batch: Batch) -> None:
+    batch.close()
 
 
 def pd_strerror(code: int) -> str:
