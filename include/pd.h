@@ -67,6 +67,7 @@ extern "C" {
 /* ---- hit flags -------------------------------------------------------- */
 #define PD_HIT_EDGE 1u      /* seed pixel lies on its module's border       */
 #define PD_HIT_SATURATED 2u /* rint(E / photon_kev) exceeded 255 and clipped */
+#define PD_HIT_LEARNED 4u   /* count and dx, dy come from the learned network */
 
 /* Detector geometry.  Requirements (PD_EINVAL otherwise): all sizes > 0,
  * rows, cols <= 65535, fewer than 2^31 pixels per frame, rows % unit_rows
@@ -268,6 +269,57 @@ int pd_batch_capture(pd_batch* batch, const pd_batch_item* items, uint32_t n_ite
                      void* stream);
 int pd_batch_replay(pd_batch* batch, void* stream);
 void pd_batch_destroy(pd_batch* batch);
+
+/* ---- Learned count / subpixel refinement ---------------------------------
+ * The paper reports that off-the-shelf deep models lost photon information
+ * and offers its fixed filters as the start of future learned models
+ * (abstract; sections "Methods", "Conclusions").  pd_net is such a model: it
+ * reads the 5x5 neighbourhood of a hit's seed (e / photon_kev, zero outside
+ * the module) and predicts the photon count (0-4) and (dx, dy):
+ *   conv3x3x32 -> ReLU -> conv3x3x32 -> ReLU -> FC64 -> ReLU -> 7 outputs
+ * (5 count logits, dx, dy), 'same' zero padding.  Contractions run on the
+ * tensor cores with bfloat16 operands (rounded to nearest even) and float32
+ * accumulation.  Parameters are one float32 vector in the order W1 [32][9],
+ * b1 [32], W2 [32][288] (column k*32 + c_in, k = 3*(dy+1) + dx+1), b2,
+ * W3 [64][800] (column p*32 + c), b3, W4 [7][64], b4.
+ * Loss = mean softmax cross-entropy of the count + lambda * sum of squared
+ * (dx, dy) errors over hits with mask = 1, divided by n_reg. */
+typedef struct pd_net pd_net;
+
+uint32_t pd_net_num_params(void);
+/* Device state for batches of up to max_batch patches; weights and biases
+ * uniform in +-1/sqrt(fan_in) from a generator seeded with `seed`, Adam
+ * state zero. */
+int pd_net_create(uint32_t max_batch, uint64_t seed, pd_net** out);
+int pd_net_set_params(pd_net* net, const float* params_host, uint32_t n_params);
+int pd_net_get_params(pd_net* net, float* params_host, uint32_t n_params);
+/* 5x5 patches (float [n_hits][25], device) of the hits of one pd_process
+ * call: frames_dev, frame_base and cm_dev (out->cm of that call) as given
+ * to / returned by it. */
+int pd_net_gather(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t frame_base,
+                  const float* cm_dev, const pd_hit* hits_dev, uint32_t n_hits,
+                  float* patches_dev, void* stream);
+/* Network outputs float [n][7] (5 logits, dx, dy) for n patches (device). */
+int pd_net_forward(pd_net* net, const float* patches_dev, uint32_t n,
+                   float* out_dev, void* stream);
+/* Loss (added to *loss_dev if not NULL) and the gradient of every
+ * parameter (float [n_params] into grads_dev if not NULL) for one batch of
+ * n <= max_batch patches: counts u8 [n] (0-4), targets float [n][2],
+ * mask u8 [n]. */
+int pd_net_gradients(pd_net* net, const float* patches_dev, const uint8_t* counts_dev,
+                     const float* targets_dev, const uint8_t* mask_dev, uint32_t n,
+                     float n_reg, float lambda, float* grads_dev, float* loss_dev,
+                     void* stream);
+/* pd_net_gradients followed by one Adam step (beta 0.9 / 0.999, eps 1e-8). */
+int pd_net_train_step(pd_net* net, const float* patches_dev, const uint8_t* counts_dev,
+                      const float* targets_dev, const uint8_t* mask_dev, uint32_t n,
+                      float n_reg, float lambda, float lr, float* loss_dev, void* stream);
+/* Copy hits, replacing count and (dx, dy) by the network's where its
+ * softmax confidence is >= conf and its count >= 1 (flag PD_HIT_LEARNED);
+ * elsewhere the classical values stay (the fallback). */
+int pd_net_refine(const float* out_dev, const pd_hit* hits_in_dev, uint32_t n,
+                  float conf, pd_hit* hits_out_dev, void* stream);
+void pd_net_destroy(pd_net* net);
 
 /* Kernel timing.  When enabled on a context, every kernel the context
  * launches is bracketed by CUDA events recorded on the launching stream;

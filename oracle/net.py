@@ -94,19 +94,22 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
-def forward(params, x0):
+def forward(params, x0, operand=None):
+    """operand: optional rounding applied to both operands of every
+    contraction (e.g. bf16, to mirror tensor-core inputs)."""
+    r = operand if operand is not None else (lambda a: a)
     P = params
     x0 = np.asarray(x0, np.float64).reshape(-1, NPOS, 1)
     X1 = im2col(x0)                                   # [B, 25, 9]
-    z1 = X1 @ P["W1"].T + P["b1"]
+    z1 = r(X1) @ r(P["W1"]).T + P["b1"]
     h1 = relu(z1)
     X2 = im2col(h1)                                   # [B, 25, 288]
-    z2 = X2 @ P["W2"].T + P["b2"]
+    z2 = r(X2) @ r(P["W2"]).T + P["b2"]
     h2 = relu(z2)
     f = h2.reshape(h2.shape[0], NPOS * C2)            # column p*32 + c
-    z3 = f @ P["W3"].T + P["b3"]
+    z3 = r(f) @ r(P["W3"]).T + P["b3"]
     h3 = relu(z3)
-    out = h3 @ P["W4"].T + P["b4"]
+    out = r(h3) @ r(P["W4"]).T + P["b4"]
     cache = dict(X1=X1, z1=z1, h1=h1, X2=X2, z2=z2, h2=h2, f=f, z3=z3, h3=h3)
     return out, cache
 
@@ -133,44 +136,44 @@ def loss_and_dout(out, counts, targets, mask, lam):
     return ce + lam * mse, d
 
 
-def backward(params, cache, dout):
+def backward(params, cache, dout, operand=None):
+    """operand: optional rounding of both operands of every contraction."""
+    r = operand if operand is not None else (lambda a: a)
     P = params
     g = {}
     B = dout.shape[0]
-    g["W4"] = dout.T @ cache["h3"]
+    g["W4"] = r(dout).T @ r(cache["h3"])
     g["b4"] = dout.sum(axis=0)
-    dh3 = dout @ P["W4"]
+    dh3 = r(dout) @ r(P["W4"])
     dz3 = dh3 * (cache["z3"] > 0)
-    g["W3"] = dz3.T @ cache["f"]
+    g["W3"] = r(dz3).T @ r(cache["f"])
     g["b3"] = dz3.sum(axis=0)
-    df = dz3 @ P["W3"]
+    df = r(dz3) @ r(P["W3"])
     dz2 = df.reshape(B, NPOS, C2) * (cache["z2"] > 0)
-    g["W2"] = dz2.reshape(-1, C2).T @ cache["X2"].reshape(-1, 9 * C1)
+    g["W2"] = r(dz2.reshape(-1, C2)).T @ r(cache["X2"].reshape(-1, 9 * C1))
     g["b2"] = dz2.sum(axis=(0, 1))
-    dX2 = dz2 @ P["W2"]                                # [B, 25, 288]
+    dX2 = r(dz2) @ r(P["W2"])                          # [B, 25, 288]
     dh1 = col2im(dX2, C1)
     dz1 = dh1 * (cache["z1"] > 0)
-    g["W1"] = dz1.reshape(-1, C1).T @ cache["X1"].reshape(-1, 9)
+    g["W1"] = r(dz1.reshape(-1, C1)).T @ r(cache["X1"].reshape(-1, 9))
     g["b1"] = dz1.sum(axis=(0, 1))
     return g
 
 
-def loss_and_grad(params, x0, counts, targets, mask, lam):
-    out, cache = forward(params, x0)
+def loss_and_grad(params, x0, counts, targets, mask, lam, operand=None):
+    out, cache = forward(params, x0, operand)
     loss, dout = loss_and_dout(out, counts, targets, mask, lam)
-    return loss, backward(params, cache, dout), out
+    return loss, backward(params, cache, dout, operand), out
 
 
 def init_params(seed: int = 0):
-    """He-normal weights, zero biases (float64)."""
+    """Weights and biases uniform in +-1/sqrt(fan_in) (float64)."""
     rng = np.random.default_rng(seed)
     P = {}
-    for k in ORDER:
-        shp = SHAPES[k]
-        if k.startswith("W"):
-            P[k] = rng.normal(0.0, np.sqrt(2.0 / shp[1]), shp)
-        else:
-            P[k] = np.zeros(shp)
+    for w, b in (("W1", "b1"), ("W2", "b2"), ("W3", "b3"), ("W4", "b4")):
+        bound = 1.0 / np.sqrt(SHAPES[w][1])
+        P[w] = rng.uniform(-bound, bound, SHAPES[w])
+        P[b] = rng.uniform(-bound, bound, SHAPES[b])
     return P
 
 

@@ -919,6 +919,15 @@ int pd_autotune(pd_ctx* c, const uint16_t* frames_dev, uint32_t n_frames, pd_tun
     return best_ms < 1e30f ? PD_OK : fail(PD_ECUDA, "autotune: no candidate ran");
 }
 
+int pd_net_gather(pd_ctx* c, const uint16_t* frames_dev, uint32_t frame_base, const float* cm_dev,
+                  const pd_hit* hits_dev, uint32_t n_hits, float* patches_dev, void* stream) {
+    if (!c || (n_hits && (!frames_dev || !cm_dev || !hits_dev || !patches_dev)))
+        return fail(PD_EINVAL, "pd_net_gather: NULL argument");
+    cudaError_t e = pd::launch_gather(c->params, frames_dev, frame_base, cm_dev, hits_dev, n_hits,
+                                      patches_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? PD_OK : fail_cuda(e, "pd_net_gather");
+}
+
 void pd_destroy(pd_ctx* c) {
     if (!c) return;
     cudaDeviceSynchronize();

@@ -57,6 +57,11 @@ size_t cm_select_smem_bytes(const ChainParams& p);
 
 int device_sm_count();
 
+// 5x5 patches of e / photon_kev around hits (pd_net.cu).
+cudaError_t launch_gather(const ChainParams& p, const uint16_t* raw, uint32_t frame_base,
+                          const float* cm, const pd_hit* hits, uint32_t n, float* patches,
+                          cudaStream_t s);
+
 // Helpers of pd_process_noalloc (pd_api.cu).  None of them allocates.
 int internal_fail(int code, const char* why);
 int internal_check_process_args(const pd_ctx* ctx, const uint16_t* frames, uint32_t n_frames,

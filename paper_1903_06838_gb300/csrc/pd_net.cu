@@ -1,0 +1,543 @@
+// pd_net.cu — the learned photon count / subpixel network: patch gather,
+// forward, loss, backward and Adam, as hand-written kernels.
+//
+// The paper found off-the-shelf deep models lost photon information and
+// offered its fixed filters as the seed of future learned models (abstract,
+// sections "Methods" and "Conclusions").  This network refines the classical
+// count and centre of mass of each hit from the 5x5 neighbourhood of its
+// seed: conv3x3x32 -> conv3x3x32 -> FC64 -> {5 count logits, (dx, dy)}.
+//
+// Every layer with a contraction runs as a GEMM on the tensor cores
+// (mma.sync m16n8k16, bfloat16 operands rounded to nearest even, float32
+// accumulation).  Convolutions are implicit GEMMs: operand loaders read the
+// 3x3 neighbourhood (zero padded) directly, so no im2col buffer exists.
+// Biases, ReLU, the loss and the optimiser are float32.  Layouts follow the
+// oracle (oracle/net.py): activations [hit][position 0..24][channel].
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "pd.h"
+#include "pd_internal.cuh"
+
+namespace {
+
+constexpr int NPOS = 25, C1 = 32, C2 = 32, NH = 64, NOUT = 7;
+constexpr int NW1 = C1 * 9, NB1 = C1, NW2 = C2 * 9 * C1, NB2 = C2, NW3 = NH * NPOS * C2,
+              NB3 = NH, NW4 = NOUT * NH, NB4 = NOUT;
+constexpr int OW1 = 0, OB1 = OW1 + NW1, OW2 = OB1 + NB1, OB2 = OW2 + NW2, OW3 = OB2 + NB2,
+              OB3 = OW3 + NW3, OW4 = OB3 + NB3, OB4 = OW4 + NW4, NPARAM = OB4 + NB4;
+
+// ---------------------------------------------------------------------------
+// Tensor-core GEMM: C[M][N] = sum_k A(i, k) * B(k, j), operands from loader
+// functors, results to an epilogue functor ep(i, j, value).  Block tile
+// 64 x 64 x 32, four warps of 32 x 32; grid.z splits K (the epilogue then
+// accumulates atomically).
+constexpr int BM = 64, BN = 64, BK = 32, GT = 128, PADK = BK + 8;
+
+__device__ __forceinline__ uint16_t bf16_bits(float v) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    return *reinterpret_cast<const uint16_t*>(&b);
+}
+
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+        "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <class LA, class LB, class EP>
+__global__ void __launch_bounds__(GT)
+    gemm_kernel(int M, int N, int K, int k_split, LA la, LB lb, EP ep) {
+    __shared__ __align__(16) uint16_t As[BM][PADK];
+    __shared__ __align__(16) uint16_t Bs[BN][PADK];  // transposed: [n][k]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kbeg = blockIdx.z * k_split, kend = min(K, kbeg + k_split);
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[a][b][c] = 0.0f;
+
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        for (int e = tid; e < BM * BK; e += GT) {
+            const int r = e / BK, c = e % BK;
+            const int gi = m0 + r, gk = k0 + c;
+            As[r][c] = bf16_bits((gi < M && gk < kend) ? la(gi, gk) : 0.0f);
+        }
+        for (int e = tid; e < BN * BK; e += GT) {
+            const int n = e / BK, c = e % BK;
+            const int gj = n0 + n, gk = k0 + c;
+            Bs[n][c] = bf16_bits((gj < N && gk < kend) ? lb(gk, gj) : 0.0f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; mi++) {
+                const int row = wm + mi * 16 + g;
+                af[mi][0] = *reinterpret_cast<const uint32_t*>(&As[row][kk + 2 * tq]);
+                af[mi][1] = *reinterpret_cast<const uint32_t*>(&As[row + 8][kk + 2 * tq]);
+                af[mi][2] = *reinterpret_cast<const uint32_t*>(&As[row][kk + 8 + 2 * tq]);
+                af[mi][3] = *reinterpret_cast<const uint32_t*>(&As[row + 8][kk + 8 + 2 * tq]);
+            }
+#pragma unroll
+            for (int ni = 0; ni < 4; ni++) {
+                const int n = wn + ni * 8 + g;
+                bfr[ni][0] = *reinterpret_cast<const uint32_t*>(&Bs[n][kk + 2 * tq]);
+                bfr[ni][1] = *reinterpret_cast<const uint32_t*>(&Bs[n][kk + 8 + 2 * tq]);
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; mi++)
+#pragma unroll
+                for (int ni = 0; ni < 4; ni++) mma_bf16(acc[mi][ni], af[mi], bfr[ni]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; mi++)
+#pragma unroll
+        for (int ni = 0; ni < 4; ni++) {
+            const int r = m0 + wm + mi * 16 + g, c = n0 + wn + ni * 8 + 2 * tq;
+            if (r < M && c < N) ep(r, c, acc[mi][ni][0]);
+            if (r < M && c + 1 < N) ep(r, c + 1, acc[mi][ni][1]);
+            if (r + 8 < M && c < N) ep(r + 8, c, acc[mi][ni][2]);
+            if (r + 8 < M && c + 1 < N) ep(r + 8, c + 1, acc[mi][ni][3]);
+        }
+}
+
+template <class LA, class LB, class EP>
+cudaError_t gemm(int M, int N, int K, LA la, LB lb, EP ep, cudaStream_t s, int splits = 1) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    splits = std::max(1, std::min(splits, (K + BK - 1) / BK));
+    int k_split = (K + splits - 1) / splits;
+    k_split = (k_split + BK - 1) / BK * BK;
+    splits = (K + k_split - 1) / k_split;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
+    gemm_kernel<<<grid, GT, 0, s>>>(M, N, K, k_split, la, lb, ep);
+    return cudaGetLastError();
+}
+
+// ---- operand loaders --------------------------------------------------------
+// 3x3 neighbour of position p (0..24 on the 5x5 grid) at offset k, or -1.
+__device__ __forceinline__ int nbr(int p, int k) {
+    const int y = p / 5 + k / 3 - 1, x = p % 5 + k % 3 - 1;
+    return (y >= 0 && y < 5 && x >= 0 && x < 5) ? y * 5 + x : -1;
+}
+
+struct RowMajor {  // element (i, k) of a row-major matrix with leading dim ld
+    const float* a;
+    int ld;
+    __device__ float operator()(int i, int k) const { return a[(size_t)i * ld + k]; }
+};
+struct ColMajor {  // element (i, k) = a[k][i]: the transpose of a row-major matrix
+    const float* a;
+    int ld;
+    __device__ float operator()(int i, int k) const { return a[(size_t)k * ld + i]; }
+};
+struct Im2col {  // element ((hit, p), k*C + c) of the im2col of act [hit][25][C]
+    const float* act;
+    int C;
+    __device__ float operator()(int row, int col) const {
+        const int hit = row / NPOS, p = row % NPOS, k = col / C, c = col % C;
+        const int q = nbr(p, k);
+        return q < 0 ? 0.0f : act[((size_t)hit * NPOS + q) * C + c];
+    }
+};
+// Gradient of conv2's input: element ((hit, q), k*32 + c) = dz2[hit][q - off k][c]
+// (the position whose offset-k neighbour is q), zero outside the grid.
+struct ConvTransposeA {
+    const float* dz;
+    __device__ float operator()(int row, int col) const {
+        const int hit = row / NPOS, q = row % NPOS, k = col / C2, c = col % C2;
+        const int p = nbr(q, 8 - k);  // the mirrored offset
+        return p < 0 ? 0.0f : dz[((size_t)hit * NPOS + p) * C2 + c];
+    }
+};
+struct ConvTransposeB {  // element (k*32 + c, c_in) = W2[c][k*32 + c_in]
+    const float* w2;
+    __device__ float operator()(int kk, int cin) const {
+        const int k = kk / C2, c = kk % C2;
+        return w2[(size_t)c * (9 * C1) + k * C1 + cin];
+    }
+};
+
+// ---- epilogues -----------------------------------------------------------
+struct BiasAct {  // out[i][j] = act(acc + bias[j])
+    float* out;
+    int ld;
+    const float* bias;
+    bool relu;
+    __device__ void operator()(int i, int j, float v) const {
+        v = v + bias[j];
+        out[(size_t)i * ld + j] = relu ? fmaxf(v, 0.0f) : v;
+    }
+};
+struct ReluGrad {  // out[i][j] = acc * (act[i][j] > 0)
+    float* out;
+    const float* act;
+    int ld;
+    __device__ void operator()(int i, int j, float v) const {
+        const size_t o = (size_t)i * ld + j;
+        out[o] = act[o] > 0.0f ? v : 0.0f;
+    }
+};
+struct AtomicAcc {  // out[i][j] += acc
+    float* out;
+    int ld;
+    __device__ void operator()(int i, int j, float v) const { atomicAdd(&out[(size_t)i * ld + j], v); }
+};
+
+// ---- small kernels --------------------------------------------------------
+__global__ void colsum_kernel(const float* __restrict__ a, int M, int N, float* __restrict__ out) {
+    // out[j] += sum_i a[i][j]
+    const int j = blockIdx.x;
+    float s = 0.0f;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) s += a[(size_t)i * N + j];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ float ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; w++) t += ws[w];
+        atomicAdd(&out[j], t);
+    }
+}
+
+// Softmax cross-entropy over out[:, 0:5] and masked squared error of
+// out[:, 5:7]; dout and the loss (accumulated into *loss).
+__global__ void loss_kernel(const float* __restrict__ out, const uint8_t* __restrict__ counts,
+                            const float* __restrict__ tgt, const uint8_t* __restrict__ mask,
+                            int B, float nreg, float lam, float* __restrict__ dout,
+                            float* __restrict__ loss) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (b < B) {
+        const float* o = out + (size_t)b * NOUT;
+        float mx = o[0];
+        for (int k = 1; k < 5; k++) mx = fmaxf(mx, o[k]);
+        float e[5], s = 0.0f;
+        for (int k = 0; k < 5; k++) {
+            e[k] = expf(o[k] - mx);
+            s += e[k];
+        }
+        const int n = min((int)counts[b], 4);
+        float* d = dout + (size_t)b * NOUT;
+        for (int k = 0; k < 5; k++) d[k] = (e[k] / s - (k == n ? 1.0f : 0.0f)) / (float)B;
+        l = -logf(e[n] / s) / (float)B;
+        const float m = mask[b] ? 1.0f : 0.0f;
+        for (int k = 0; k < 2; k++) {
+            const float diff = (o[5 + k] - tgt[(size_t)b * 2 + k]) * m;
+            d[5 + k] = 2.0f * lam * diff / nreg;
+            l += lam * diff * diff / nreg;
+        }
+    }
+    for (int o2 = 16; o2; o2 >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o2);
+    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, l);
+}
+
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ gr,
+                            float* __restrict__ m, float* __restrict__ v, int n, float lr,
+                            float b1, float b2, float c1, float c2, float eps) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gv = gr[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gv;
+    const float vi = b2 * v[i] + (1.0f - b2) * gv * gv;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// 5x5 patch of e / photon_kev around each hit's seed (zero outside the
+// module): e recomputed exactly as the chain does, with the call's common
+// mode cm[frame - frame_base][unit].
+__global__ void gather_kernel(pd::ChainParams p, const uint16_t* __restrict__ raw,
+                              uint32_t frame_base, const float* __restrict__ cm,
+                              const pd_hit* __restrict__ hits, uint32_t n,
+                              float* __restrict__ patches) {
+    const uint32_t h = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (h >= n || lane >= NPOS) return;
+    const pd_hit hit = hits[h];
+    const uint32_t f = hit.frame - frame_base;
+    const uint32_t m = hit.pixel / p.module_px, within = hit.pixel % p.module_px;
+    const int r = (int)(within / p.cols) + lane / 5 - 2, c = (int)(within % p.cols) + lane % 5 - 2;
+    float v = 0.0f;
+    if (r >= 0 && r < (int)p.rows && c >= 0 && c < (int)p.cols) {
+        const size_t g = (size_t)m * p.module_px + (size_t)r * p.cols + c;
+        const uint32_t unit = m * p.units_per_module +
+                              ((uint32_t)r / p.unit_rows) * p.units_per_row + (uint32_t)c / p.unit_cols;
+        const float d = __fsub_rn(__uint2float_rn(raw[(size_t)f * p.frame_px + g]), p.ped[g]);
+        const float e = __fmul_rn(__fsub_rn(d, cm[(size_t)f * p.units_per_frame + unit]),
+                                  p.inv_gain[g]);
+        v = __fdiv_rn(e, p.photon_kev);
+    }
+    patches[(size_t)h * NPOS + lane] = v;
+}
+
+// Replace count and (dx, dy) of hits the network is confident about; keep
+// the classical values elsewhere.
+__global__ void refine_kernel(const float* __restrict__ out, const pd_hit* __restrict__ in,
+                              uint32_t n, float conf, pd_hit* __restrict__ res) {
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    pd_hit h = in[b];
+    const float* o = out + (size_t)b * NOUT;
+    float mx = o[0];
+    int arg = 0;
+    for (int k = 1; k < 5; k++)
+        if (o[k] > mx) {
+            mx = o[k];
+            arg = k;
+        }
+    float s = 0.0f;
+    for (int k = 0; k < 5; k++) s += expf(o[k] - mx);
+    const float pmax = 1.0f / s;
+    if (pmax >= conf && arg >= 1) {
+        h.count = (uint8_t)arg;
+        h.dx = o[5];
+        h.dy = o[6];
+        h.flags |= PD_HIT_LEARNED;
+    }
+    res[b] = h;
+}
+
+int net_fail(int code, const std::string& why) { return pd::internal_fail(code, why.c_str()); }
+int net_cuda(cudaError_t e, const char* what) {
+    return net_fail(PD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+struct pd_net {
+    uint32_t max_batch = 0;
+    float *w = nullptr, *gw = nullptr, *m = nullptr, *v = nullptr;
+    float *x0 = nullptr, *h1 = nullptr, *h2 = nullptr, *h3 = nullptr, *out = nullptr;
+    float *dout = nullptr, *dz3 = nullptr, *dz2 = nullptr, *dz1 = nullptr;
+    uint64_t step = 0;
+};
+
+namespace {
+
+void free_net(pd_net* n) {
+    if (!n) return;
+    for (float* p : {n->w, n->gw, n->m, n->v, n->x0, n->h1, n->h2, n->h3, n->out, n->dout,
+                     n->dz3, n->dz2, n->dz1})
+        cudaFree(p);
+    delete n;
+}
+
+// forward of n patches already in net->x0 (or at `x`) into net->out
+cudaError_t forward(pd_net* net, const float* x, int n, cudaStream_t s) {
+    const float* w = net->w;
+    cudaError_t e;
+    // conv1: [n*25, 9] x W1^T -> h1
+    if ((e = gemm(n * NPOS, C1, 9, Im2col{x, 1}, ColMajor{w + OW1, 9},
+                  BiasAct{net->h1, C1, w + OB1, true}, s)))
+        return e;
+    // conv2: [n*25, 288] x W2^T -> h2
+    if ((e = gemm(n * NPOS, C2, 9 * C1, Im2col{net->h1, C1}, ColMajor{w + OW2, 9 * C1},
+                  BiasAct{net->h2, C2, w + OB2, true}, s)))
+        return e;
+    // fc: [n, 800] x W3^T -> h3
+    if ((e = gemm(n, NH, NPOS * C2, RowMajor{net->h2, NPOS * C2}, ColMajor{w + OW3, NPOS * C2},
+                  BiasAct{net->h3, NH, w + OB3, true}, s)))
+        return e;
+    // heads: [n, 64] x W4^T -> out
+    return gemm(n, NOUT, NH, RowMajor{net->h3, NH}, ColMajor{w + OW4, NH},
+                BiasAct{net->out, NOUT, w + OB4, false}, s);
+}
+
+// loss, dout and all parameter gradients (into net->gw, zeroed first)
+cudaError_t backward(pd_net* net, const float* x, int n, const uint8_t* counts, const float* tgt,
+                     const uint8_t* mask, float nreg, float lam, float* loss, cudaStream_t s) {
+    const float* w = net->w;
+    float* gw = net->gw;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(gw, 0, NPARAM * sizeof(float), s))) return e;
+    loss_kernel<<<(n + 255) / 256, 256, 0, s>>>(net->out, counts, tgt, mask, n,
+                                                std::max(1.0f, nreg), lam, net->dout, loss);
+    if ((e = cudaGetLastError())) return e;
+    const int sp = std::max(1, std::min(64, n * NPOS / 4096));
+    // heads
+    if ((e = gemm(NOUT, NH, n, ColMajor{net->dout, NOUT}, RowMajor{net->h3, NH},
+                  AtomicAcc{gw + OW4, NH}, s, sp)))
+        return e;
+    colsum_kernel<<<NOUT, 256, 0, s>>>(net->dout, n, NOUT, gw + OB4);
+    if ((e = gemm(n, NH, NOUT, RowMajor{net->dout, NOUT}, RowMajor{w + OW4, NH},
+                  ReluGrad{net->dz3, net->h3, NH}, s)))
+        return e;
+    // fc
+    if ((e = gemm(NH, NPOS * C2, n, ColMajor{net->dz3, NH}, RowMajor{net->h2, NPOS * C2},
+                  AtomicAcc{gw + OW3, NPOS * C2}, s, sp)))
+        return e;
+    colsum_kernel<<<NH, 256, 0, s>>>(net->dz3, n, NH, gw + OB3);
+    if ((e = gemm(n, NPOS * C2, NH, RowMajor{net->dz3, NH}, RowMajor{w + OW3, NPOS * C2},
+                  ReluGrad{net->dz2, net->h2, NPOS * C2}, s)))
+        return e;
+    // conv2: weights, bias, input
+    if ((e = gemm(C2, 9 * C1, n * NPOS, ColMajor{net->dz2, C2}, Im2col{net->h1, C1},
+                  AtomicAcc{gw + OW2, 9 * C1}, s, sp)))
+        return e;
+    colsum_kernel<<<C2, 256, 0, s>>>(net->dz2, n * NPOS, C2, gw + OB2);
+    if ((e = gemm(n * NPOS, C1, 9 * C2, ConvTransposeA{net->dz2}, ConvTransposeB{w + OW2},
+                  ReluGrad{net->dz1, net->h1, C1}, s)))
+        return e;
+    // conv1: weights, bias
+    if ((e = gemm(C1, 9, n * NPOS, ColMajor{net->dz1, C1}, Im2col{x, 1}, AtomicAcc{gw + OW1, 9},
+                  s, sp)))
+        return e;
+    colsum_kernel<<<C1, 256, 0, s>>>(net->dz1, n * NPOS, C1, gw + OB1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+uint32_t pd_net_num_params(void) { return NPARAM; }
+
+int pd_net_create(uint32_t max_batch, uint64_t seed, pd_net** out) {
+    if (!out || !max_batch) return net_fail(PD_EINVAL, "pd_net_create: need out and max_batch");
+    *out = nullptr;
+    pd_net* n = new (std::nothrow) pd_net();
+    if (!n) return net_fail(PD_ENOMEM, "host allocation failed");
+    n->max_batch = max_batch;
+    const size_t B = max_batch;
+    struct { float** p; size_t count; } bufs[] = {
+        {&n->w, NPARAM}, {&n->gw, NPARAM}, {&n->m, NPARAM}, {&n->v, NPARAM},
+        {&n->x0, B * NPOS}, {&n->h1, B * NPOS * C1}, {&n->h2, B * NPOS * C2},
+        {&n->h3, B * NH}, {&n->out, B * NOUT}, {&n->dout, B * NOUT}, {&n->dz3, B * NH},
+        {&n->dz2, B * NPOS * C2}, {&n->dz1, B * NPOS * C1}};
+    for (auto& b : bufs)
+        if (cudaMalloc(b.p, b.count * sizeof(float)) != cudaSuccess) {
+            free_net(n);
+            return net_fail(PD_ENOMEM, "pd_net_create: device allocation failed");
+        }
+    // weights and biases uniform in +-1/sqrt(fan_in), from a seeded generator
+    std::vector<float> host(NPARAM, 0.0f);
+    std::mt19937_64 rng(seed);
+    auto fill = [&](int off, int count, int fan_in) {
+        const double b = 1.0 / std::sqrt((double)fan_in);
+        std::uniform_real_distribution<double> ud(-b, b);
+        for (int i = 0; i < count; i++) host[off + i] = (float)ud(rng);
+    };
+    fill(OW1, NW1, 9);
+    fill(OB1, NB1, 9);
+    fill(OW2, NW2, 9 * C1);
+    fill(OB2, NB2, 9 * C1);
+    fill(OW3, NW3, NPOS * C2);
+    fill(OB3, NB3, NPOS * C2);
+    fill(OW4, NW4, NH);
+    fill(OB4, NB4, NH);
+    if (cudaMemcpy(n->w, host.data(), NPARAM * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(n->m, 0, NPARAM * 4) != cudaSuccess ||
+        cudaMemset(n->v, 0, NPARAM * 4) != cudaSuccess) {
+        free_net(n);
+        return net_fail(PD_ECUDA, "pd_net_create: upload failed");
+    }
+    *out = n;
+    return PD_OK;
+}
+
+int pd_net_set_params(pd_net* n, const float* host, uint32_t count) {
+    if (!n || !host || count != NPARAM) return net_fail(PD_EINVAL, "pd_net_set_params: size");
+    cudaError_t e = cudaMemcpy(n->w, host, NPARAM * 4, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? PD_OK : net_cuda(e, "pd_net_set_params");
+}
+
+int pd_net_get_params(pd_net* n, float* host, uint32_t count) {
+    if (!n || !host || count != NPARAM) return net_fail(PD_EINVAL, "pd_net_get_params: size");
+    cudaError_t e = cudaMemcpy(host, n->w, NPARAM * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? PD_OK : net_cuda(e, "pd_net_get_params");
+}
+
+int pd_net_forward(pd_net* n, const float* patches, uint32_t count, float* out_dev, void* stream) {
+    if (!n || (count && (!patches || !out_dev))) return net_fail(PD_EINVAL, "pd_net_forward: args");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (uint32_t done = 0; done < count;) {
+        const uint32_t b = std::min(n->max_batch, count - done);
+        cudaError_t e = forward(n, patches + (size_t)done * NPOS, (int)b, s);
+        if (!e) e = cudaMemcpyAsync(out_dev + (size_t)done * NOUT, n->out, (size_t)b * NOUT * 4,
+                                    cudaMemcpyDeviceToDevice, s);
+        if (e) return net_cuda(e, "pd_net_forward");
+        done += b;
+    }
+    return PD_OK;
+}
+
+int pd_net_gradients(pd_net* n, const float* patches, const uint8_t* counts, const float* targets,
+                     const uint8_t* mask, uint32_t count, float n_reg, float lambda,
+                     float* grads_dev, float* loss_dev, void* stream) {
+    if (!n || !count || count > n->max_batch || !patches || !counts || !targets || !mask)
+        return net_fail(PD_EINVAL, "pd_net_gradients: args (count <= max_batch)");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = forward(n, patches, (int)count, s);
+    if (!e) e = backward(n, patches, (int)count, counts, targets, mask, n_reg, lambda, loss_dev, s);
+    if (!e && grads_dev)
+        e = cudaMemcpyAsync(grads_dev, n->gw, NPARAM * 4, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? PD_OK : net_cuda(e, "pd_net_gradients");
+}
+
+int pd_net_train_step(pd_net* n, const float* patches, const uint8_t* counts, const float* targets,
+                      const uint8_t* mask, uint32_t count, float n_reg, float lambda, float lr,
+                      float* loss_dev, void* stream) {
+    int rc = pd_net_gradients(n, patches, counts, targets, mask, count, n_reg, lambda, nullptr,
+                              loss_dev, stream);
+    if (rc) return rc;
+    n->step++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - (float)std::pow(0.9, (double)n->step);
+    const float c2 = 1.0f - (float)std::pow(0.999, (double)n->step);
+    adam_kernel<<<(NPARAM + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n->w, n->gw, n->m, n->v,
+                                                                        NPARAM, lr, b1, b2, c1, c2,
+                                                                        1e-8f);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PD_OK : net_cuda(e, "adam");
+}
+
+int pd_net_refine(const float* out_dev, const pd_hit* hits_in, uint32_t count, float conf,
+                  pd_hit* hits_out, void* stream) {
+    if (count && (!out_dev || !hits_in || !hits_out)) return net_fail(PD_EINVAL, "pd_net_refine");
+    if (!count) return PD_OK;
+    refine_kernel<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(out_dev, hits_in, count,
+                                                                         conf, hits_out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PD_OK : net_cuda(e, "refine");
+}
+
+void pd_net_destroy(pd_net* n) {
+    if (!n) return;
+    cudaDeviceSynchronize();
+    free_net(n);
+}
+
+}  // extern "C"
+
+namespace pd {
+cudaError_t launch_gather(const ChainParams& p, const uint16_t* raw, uint32_t frame_base,
+                          const float* cm, const pd_hit* hits, uint32_t n, float* patches,
+                          cudaStream_t s) {
+    if (!n) return cudaSuccess;
+    const uint32_t per = 8;  // hits per 256-thread block (one warp each)
+    gather_kernel<<<(n + per - 1) / per, 256, 0, s>>>(p, raw, frame_base, cm, hits, n, patches);
+    return cudaGetLastError();
+}
+}  // namespace pd

@@ -20,7 +20,7 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_PKG, "libpd.so")
-SOURCES = ["pd_api.cu", "pd_chain.cu", "pd_fast.cu", "pd_noalloc.cu"]
+SOURCES = ["pd_api.cu", "pd_chain.cu", "pd_fast.cu", "pd_noalloc.cu", "pd_net.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
@@ -33,7 +33,7 @@ _lib = None
 PD_OK, PD_EINVAL, PD_EALIGN, PD_ENOMEM, PD_EOVERFLOW = 0, 1, 2, 3, 4
 PD_ETIMEDOUT, PD_ECUDA, PD_ENOTSUP, PD_EBUSY = 5, 6, 7, 8
 PD_CM_MEDIAN, PD_CM_NONE = 0, 1
-PD_HIT_EDGE, PD_HIT_SATURATED = 1, 2
+PD_HIT_EDGE, PD_HIT_SATURATED, PD_HIT_LEARNED = 1, 2, 4
 PD_MAX_HIST_BINS = 4096
 
 HIT_DTYPE = np.dtype([("frame", "<u4"), ("pixel", "<u4"), ("energy_kev", "<f4"),
@@ -154,6 +154,18 @@ def _declare(lib):
         "pd_batch_capture": ([vp, ctypes.POINTER(PdBatchItem), u32, vp], i32),
         "pd_batch_replay": ([vp, vp], i32),
         "pd_batch_destroy": ([vp], None),
+        "pd_net_num_params": ([], u32),
+        "pd_net_create": ([u32, ctypes.c_uint64, ctypes.POINTER(vp)], i32),
+        "pd_net_set_params": ([vp, vp, u32], i32),
+        "pd_net_get_params": ([vp, vp, u32], i32),
+        "pd_net_gather": ([vp, vp, u32, vp, vp, u32, vp, vp], i32),
+        "pd_net_forward": ([vp, vp, u32, vp, vp], i32),
+        "pd_net_gradients": ([vp, vp, vp, vp, vp, u32, ctypes.c_float, ctypes.c_float, vp, vp,
+                              vp], i32),
+        "pd_net_train_step": ([vp, vp, vp, vp, vp, u32, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_float, vp, vp], i32),
+        "pd_net_refine": ([vp, vp, u32, ctypes.c_float, vp, vp], i32),
+        "pd_net_destroy": ([vp], None),
         "pd_get_tuning": ([vp, ctypes.POINTER(PdTuning)], i32),
         "pd_set_tuning": ([vp, ctypes.POINTER(PdTuning)], i32),
         "pd_read_profile": ([vp, ctypes.POINTER(PdProfile)], i32),
@@ -429,6 +441,80 @@ def pd_batch_replay(batch: Batch, stream=None) -> None:
 
 def pd_batch_destroy(batch: Batch) -> None:
     batch.close()
+
+
+# ---- learned refinement (device pointers; torch tensors for convenience) ----
+class Net:
+    def __init__(self, max_batch: int = 8192, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(load().pd_net_create(max_batch, seed, ctypes.byref(h)), "pd_net_create")
+        self.handle = h.value
+        self.max_batch = max_batch
+
+    def close(self):
+        if self.handle:
+            load().pd_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pd_net_num_params() -> int:
+    return int(load().pd_net_num_params())
+
+
+def pd_net_create(max_batch: int = 8192, seed: int = 0) -> Net:
+    return Net(max_batch, seed)
+
+
+def pd_net_set_params(net: Net, params: np.ndarray) -> None:
+    a = np.ascontiguousarray(params, np.float32)
+    _check(load().pd_net_set_params(net.handle, a.ctypes.data, a.size), "pd_net_set_params")
+
+
+def pd_net_get_params(net: Net) -> np.ndarray:
+    a = np.empty(pd_net_num_params(), np.float32)
+    _check(load().pd_net_get_params(net.handle, a.ctypes.data, a.size), "pd_net_get_params")
+    return a
+
+
+def pd_net_gather(ctx: Context, frames_ptr: int, frame_base: int, cm_ptr: int, hits_ptr: int,
+                  n_hits: int, patches_ptr: int, stream=None) -> None:
+    _check(load().pd_net_gather(ctx.handle, frames_ptr, frame_base, cm_ptr, hits_ptr, n_hits,
+                                patches_ptr, _stream_handle(stream)), "pd_net_gather")
+
+
+def pd_net_forward(net: Net, patches_ptr: int, n: int, out_ptr: int, stream=None) -> None:
+    _check(load().pd_net_forward(net.handle, patches_ptr, n, out_ptr, _stream_handle(stream)),
+           "pd_net_forward")
+
+
+def pd_net_gradients(net: Net, patches_ptr, counts_ptr, targets_ptr, mask_ptr, n, n_reg,
+                     lam, grads_ptr, loss_ptr, stream=None) -> None:
+    _check(load().pd_net_gradients(net.handle, patches_ptr, counts_ptr, targets_ptr, mask_ptr,
+                                   n, n_reg, lam, grads_ptr, loss_ptr,
+                                   _stream_handle(stream)), "pd_net_gradients")
+
+
+def pd_net_train_step(net: Net, patches_ptr, counts_ptr, targets_ptr, mask_ptr, n, n_reg,
+                      lam, lr, loss_ptr, stream=None) -> None:
+    _check(load().pd_net_train_step(net.handle, patches_ptr, counts_ptr, targets_ptr,
+                                    mask_ptr, n, n_reg, lam, lr, loss_ptr,
+                                    _stream_handle(stream)), "pd_net_train_step")
+
+
+def pd_net_refine(out_ptr: int, hits_in_ptr: int, n: int, conf: float, hits_out_ptr: int,
+                  stream=None) -> None:
+    _check(load().pd_net_refine(out_ptr, hits_in_ptr, n, conf, hits_out_ptr,
+                                _stream_handle(stream)), "pd_net_refine")
+
+
+def pd_net_destroy(net: Net) -> None:
+    net.close()
 
 
 def pd_strerror(code: int) -> str:
