@@ -43,7 +43,7 @@ struct pd_ctx {
     pd::ChainParams params;
     pd::CmBigConfig cm_cfg;
     pd::BandConfig band_cfg;
-    bool use_cm_big = false, use_band = false;
+    bool use_cm_big = false, use_cm_rows = false, use_band = false;
     uint32_t chunk_frames = 1;  // frames per common-mode/stencil launch pair
     uint32_t overlap = 1;       // common mode of chunk c+1 beside stencil of c
     cudaStream_t aux = nullptr; // second stream of the chunk pipeline
@@ -251,8 +251,9 @@ int run_chain(pd_ctx* c, const uint16_t* frames, uint32_t n_frames, uint32_t fra
             return fail_cuda(e, "chunk pipeline wait");
         {
             ProfileScope ps(c, 0, sc);
-            e = c->use_cm_big ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, cmc, sc)
-                              : pd::launch_cm_select(c->params, fr, nf, cmc, sc);
+            e = c->use_cm_big    ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, cmc, sc)
+                : c->use_cm_rows ? pd::launch_cm_rows(c->params, fr, nf, cmc, sc)
+                                 : pd::launch_cm_select(c->params, fr, nf, cmc, sc);
         }
         if (e != cudaSuccess) return fail_cuda(e, "common-mode kernel launch");
         if (two && ((e = cudaEventRecord(c->ev_cm[k & 1], sc)) ||
@@ -315,8 +316,9 @@ int internal_run_sequential(pd_ctx* c, const uint16_t* frames, uint32_t n_frames
         const uint32_t nf = std::min(c->chunk_frames, n_frames - done);
         const uint16_t* fr = frames + (size_t)done * c->params.frame_px;
         float* cmc = cm + (size_t)done * c->params.units_per_frame;
-        e = c->use_cm_big ? launch_cm_big(c->params, c->cm_cfg, fr, nf, cmc, s)
-                          : launch_cm_select(c->params, fr, nf, cmc, s);
+        e = c->use_cm_big    ? launch_cm_big(c->params, c->cm_cfg, fr, nf, cmc, s)
+            : c->use_cm_rows ? launch_cm_rows(c->params, fr, nf, cmc, s)
+                             : launch_cm_select(c->params, fr, nf, cmc, s);
         if (e != cudaSuccess) return fail_cuda(e, "common-mode kernel launch");
         CallOut co{out->hits, out->hit_capacity, out->n_hits,
                    out->corrected ? out->corrected + (size_t)done * c->params.frame_px
@@ -393,6 +395,7 @@ int pd_create(const pd_geometry* geometry, const float* pedestal_host,
 
     c->cm_cfg = pd::make_cm_big_config(p);
     c->use_cm_big = g.cm_mode == PD_CM_MEDIAN && pd::cm_big_supported(p, c->cm_cfg);
+    c->use_cm_rows = g.cm_mode == PD_CM_MEDIAN && !c->use_cm_big && pd::cm_rows_supported(p);
     c->band_cfg = pd::make_band_config(p);
     c->use_band = c->band_cfg.ok;
     {
@@ -708,9 +711,12 @@ int batch_enqueue(pd_batch* b, int slot, const pd_batch_item* items, uint32_t n,
         d.cm_cfg = c->cm_cfg;
         d.band_cfg = c->band_cfg;
         const size_t gen_keys = (size_t)c->params.unit_px * 4;
+        d.rows_magic = pd::cm_rows_magic(c->params);
         if (c->use_cm_big) {
             d.cm_kind = c->cm_cfg.vec == 2 ? 0u : 1u;
             cm_smem = std::max(cm_smem, pd::cm_big_smem_bytes(c->params));
+        } else if (c->use_cm_rows) {
+            d.cm_kind = 4;
         } else if (gen_keys <= pd::kCmBigMaxSmem) {
             d.cm_kind = 2;
             cm_smem = std::max(cm_smem, gen_keys);
@@ -734,7 +740,7 @@ int batch_enqueue(pd_batch* b, int slot, const pd_batch_item* items, uint32_t n,
         d.cm_first = cm_tasks;
         d.st_first = tiles;
         d.st_tiles = (unsigned long long)it.n_frames * c->params.n_modules * c->band_cfg.n_bands;
-        cm_tasks += ncm;
+        cm_tasks += d.cm_kind == 4 ? (ncm + 15) / 16 : ncm;
         tiles += d.st_tiles;
     }
     cudaError_t e = cudaMemcpyAsync(b->d_table[slot], h, n * sizeof(pd::BatchItem),

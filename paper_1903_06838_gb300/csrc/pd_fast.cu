@@ -504,6 +504,201 @@ __global__ void __launch_bounds__(512, 2)
 }
 
 // ---------------------------------------------------------------------------
+// Common mode of small units (at most kRowMaxPx pixels, e.g. 384-pixel ASIC
+// rows): one warp per unit, every pixel of the unit in the lanes' registers.
+// Level 1: 256 bins of 1 ADU over [cut - 256, cut) in warp-private shared
+// memory (d < cut - 256 in bin 0; d >= cut in the spare bin 256), a warp scan
+// finds the bin of rank floor((n-1)/2).  Level 2: the bin's values into 64
+// sub-bins of 1/64 ADU (RN(d - lo) is monotone in d), scan again.  Level 3:
+// the few values of that sub-bin, ranked by counting.  A median in bin 0
+// (open below) goes to a warp-level 4-pass radix select over the unit.
+constexpr int kRowMaxPx = 512;      // pixels per unit handled by one warp
+constexpr int kRowPerLane = kRowMaxPx / 32;
+constexpr int kRowWarps = 8;        // units per CTA
+struct RowWarpShared {
+    uint32_t hist[256 + 4];
+    uint32_t sub[64];
+    float few[64];
+    uint32_t n_few;
+};
+
+// warp inclusive scan of one value per lane
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += x;
+    }
+    return v;
+}
+
+// Locate rank k among bins hist[0..nb) (nb = 32 * per): *bin and the rank
+// within it; returns false when k >= total.
+template <int PER>
+__device__ __forceinline__ bool warp_find_rank(const uint32_t* hist, uint32_t k, int lane,
+                                               uint32_t* bin, uint32_t* krem) {
+    uint32_t loc[PER], sum = 0;
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        loc[j] = hist[lane * PER + j];
+        sum += loc[j];
+    }
+    const uint32_t incl = warp_incl_scan(sum, lane), excl = incl - sum;
+    const bool mine = excl <= k && k < incl;
+    uint32_t b = 0, r = 0;
+    if (mine) {
+        uint32_t below = excl;
+#pragma unroll
+        for (int j = 0; j < PER; j++) {
+            if (below + loc[j] > k) {
+                b = lane * PER + j;
+                r = k - below;
+                break;
+            }
+            below += loc[j];
+        }
+    }
+    const uint32_t who = __ballot_sync(0xffffffffu, mine);
+    if (!who) return false;
+    const int src = __ffs(who) - 1;
+    *bin = __shfl_sync(0xffffffffu, b, src);
+    *krem = __shfl_sync(0xffffffffu, r, src);
+    return true;
+}
+
+// Common mode of unit `item` by one whole warp (lane = lane index).
+__device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ raw,
+                             float* __restrict__ cm_out, unsigned long long item,
+                             float magic_1, RowWarpShared& S) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t f = (uint32_t)(item / p.units_per_frame);
+    const uint32_t u = (uint32_t)(item % p.units_per_frame);
+    if (p.cm_mode == PD_CM_NONE) {
+        if (lane == 0) cm_out[item] = 0.0f;
+        return;
+    }
+    const uint32_t m = u / p.units_per_module;
+    const uint32_t um = u % p.units_per_module;
+    const uint32_t r0 = (um / p.units_per_row) * p.unit_rows;
+    const uint32_t c0 = (um % p.units_per_row) * p.unit_cols;
+    const size_t mod_base = (size_t)m * p.module_px;
+    const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
+    const float* npm = p.nped + mod_base;
+    const uint32_t npx = p.unit_px;
+
+    for (int i = lane; i < 256 + 4; i += 32) S.hist[i] = 0;
+    for (int i = lane; i < 64; i += 32) S.sub[i] = 0;
+    if (lane == 0) S.n_few = 0;
+    __syncwarp();
+
+    // d of this lane's pixels (pixel i of the unit = lane + 32 * j)
+    float d[kRowPerLane];
+    uint32_t code[kRowPerLane];
+#pragma unroll
+    for (int j = 0; j < kRowPerLane; j++) {
+        const uint32_t i = lane + 32 * j;
+        d[j] = 0.0f;
+        code[j] = 256;
+        if (i < npx) {
+            const uint32_t off = p.unit_rows == 1
+                                     ? r0 * p.cols + c0 + i
+                                     : (r0 + i / p.unit_cols) * p.cols + c0 + i % p.unit_cols;
+            d[j] = __fadd_rn(__uint2float_rn(fr[off]), npm[off]);
+            int b = __float_as_int(__fmaf_rd(d[j], 1.0f, magic_1));
+            b = min(max(b, (int)kMagicBits), (int)(kMagicBits + 256));
+            code[j] = (uint32_t)b - kMagicBits;
+            atomicAdd(&S.hist[code[j]], 1u);
+        }
+    }
+    __syncwarp();
+    // n = values below the cut (every bin but the spare one)
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) cnt += S.hist[lane * 8 + j];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    const uint32_t n = cnt;
+    if (n == 0 || n < p.cm_min_count) {
+        if (lane == 0) cm_out[item] = 0.0f;
+        return;
+    }
+    const uint32_t k = (n - 1) / 2;
+    uint32_t bin = 0, kb = 0;
+    warp_find_rank<8>(S.hist, k, lane, &bin, &kb);
+    if (bin != 0) {
+        // level 2: sub-bins of the winning 1-ADU bin [lo, lo + 1)
+        const float lo = __fadd_rn(p.cm_cut, (float)((int)bin - 256));
+        uint32_t sb[kRowPerLane];
+#pragma unroll
+        for (int j = 0; j < kRowPerLane; j++) {
+            sb[j] = 64;
+            if (code[j] == bin) {
+                const float x = __fmul_rn(__fsub_rn(d[j], lo), 64.0f);
+                sb[j] = min((uint32_t)max(__float2int_rd(x), 0), 63u);
+                atomicAdd(&S.sub[sb[j]], 1u);
+            }
+        }
+        __syncwarp();
+        uint32_t sbin = 0, ks = 0;
+        warp_find_rank<2>(S.sub, kb, lane, &sbin, &ks);
+        // level 3: values of the winning sub-bin, ranked by counting
+#pragma unroll
+        for (int j = 0; j < kRowPerLane; j++)
+            if (sb[j] == sbin) {
+                const uint32_t slot = atomicAdd(&S.n_few, 1u);
+                if (slot < 64) S.few[slot] = d[j];
+            }
+        __syncwarp();
+        const uint32_t nf = S.n_few;
+        if (nf <= 64) {
+            for (uint32_t t = lane; t < nf; t += 32) {
+                const uint32_t kt = order_key(S.few[t]);
+                uint32_t less = 0, leq = 0;
+                for (uint32_t q = 0; q < nf; q++) {
+                    const uint32_t kq = order_key(S.few[q]);
+                    less += kq < kt;
+                    leq += kq <= kt;
+                }
+                if (less <= ks && ks < leq) cm_out[item] = S.few[t];
+            }
+            return;
+        }
+    }
+    // warp radix select over the whole unit (median below the window, or more
+    // than 64 values in one sub-bin): 4 passes of 8 bits on IEEE-order keys
+    uint32_t prefix = 0, krank = k;
+    for (int pass = 0; pass < 4; pass++) {
+        const int shift = 24 - 8 * pass;
+        for (int i = lane; i < 256; i += 32) S.hist[i] = 0;
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < kRowPerLane; j++) {
+            if (code[j] >= 256) continue;  // outside the unit or d >= cut
+            const uint32_t key = order_key(d[j]);
+            if (pass > 0 && (key >> (shift + 8)) != prefix) continue;
+            atomicAdd(&S.hist[(key >> shift) & 255u], 1u);
+        }
+        __syncwarp();
+        uint32_t digit = 0, rem = 0;
+        warp_find_rank<8>(S.hist, krank, lane, &digit, &rem);
+        prefix = (prefix << 8) | digit;
+        krank = rem;
+        __syncwarp();
+    }
+    if (lane == 0) cm_out[item] = key_value(prefix);
+}
+
+__global__ void __launch_bounds__(32 * kRowWarps)
+    cm_rows_kernel(ChainParams p, const uint16_t* __restrict__ raw, float* __restrict__ cm_out,
+                   unsigned long long n_items, float magic_1) {
+    __shared__ RowWarpShared ws[kRowWarps];
+    const int w = threadIdx.x >> 5;
+    const unsigned long long item = (unsigned long long)blockIdx.x * kRowWarps + w;
+    if (item >= n_items) return;  // whole warps only; no block-level barrier follows
+    cm_rows_unit(p, raw, cm_out, item, magic_1, ws[w]);
+}
+
+// ---------------------------------------------------------------------------
 // Stencil over bands of full-width rows.
 struct BandShared {
     uint32_t s_list_n;
@@ -817,10 +1012,18 @@ __global__ void __launch_bounds__(512, 2)
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ CmBigShared big;
     __shared__ generic_cm::Shared gen;
+    __shared__ RowWarpShared rows[16];
     for (unsigned long long t = blockIdx.x; t < n_tasks; t += gridDim.x) {
         const uint32_t i = find_item(items, n_items, t, false);
         const BatchItem& it = items[i];
         const uint32_t local = (uint32_t)(t - it.cm_first);
+        if (it.cm_kind == 4) {  // 16 row units per task, one per warp
+            const unsigned long long unit = (unsigned long long)local * 16 + (threadIdx.x >> 5);
+            const unsigned long long units = (unsigned long long)it.n_frames * it.p.units_per_frame;
+            if (unit < units) cm_rows_unit(it.p, it.raw, it.out.cm, unit, it.rows_magic, rows[threadIdx.x >> 5]);
+            __syncthreads();
+            continue;
+        }
         switch (it.cm_kind) {
             case 0: cm_big_unit<2>(it.p, it.raw, it.out.cm, it.cm_cfg, local, smem, big); break;
             case 1: cm_big_unit<1>(it.p, it.raw, it.out.cm, it.cm_cfg, local, smem, big); break;
@@ -882,6 +1085,27 @@ cudaError_t launch_batch(const BatchItem* items_dev, uint32_t n_items,
     per_sm = std::max(1, std::min(per_sm, 2));
     batch_stencil_kernel<<<(unsigned)(sms * per_sm), kBandThreads, band_smem, stream>>>(items_dev,
                                                                                        n_items);
+    return cudaGetLastError();
+}
+
+float cm_rows_magic(const ChainParams& p) {
+    return (float)(12582912.0 - ((double)p.cm_cut - 256.0));
+}
+
+bool cm_rows_supported(const ChainParams& p) {
+    const double lo = (double)p.cm_cut - 256.0;
+    return p.unit_rows * p.unit_cols <= (uint32_t)kRowMaxPx && p.cm_cut > -1e6f &&
+           p.cm_cut < 1e6f && lo == (double)(long long)lo;
+}
+
+cudaError_t launch_cm_rows(const ChainParams& p, const uint16_t* raw, uint32_t n_frames,
+                           float* cm, cudaStream_t stream) {
+    const unsigned long long items = (unsigned long long)n_frames * p.units_per_frame;
+    if (items == 0) return cudaSuccess;
+    // floor(d - (cut - 256)) by a rounded-down fma with a magic addend
+    const float magic_1 = cm_rows_magic(p);
+    const unsigned long long blocks = (items + kRowWarps - 1) / kRowWarps;
+    cm_rows_kernel<<<(unsigned)blocks, 32 * kRowWarps, 0, stream>>>(p, raw, cm, items, magic_1);
     return cudaGetLastError();
 }
 

@@ -41,7 +41,9 @@ struct BatchItem {
     CmBigConfig cm_cfg;
     BandConfig band_cfg;
     uint32_t cm_kind;   // 0/1: large-unit kernel (2 or 1 pixels per load),
-                        // 2/3: generic radix select (keys in shared / global)
+                        // 2/3: generic radix select (keys in shared / global),
+                        // 4: one warp per small unit, 16 units per task
+    float rows_magic;   // cm_rows_magic(p) for kind 4
     uint32_t band_vec;  // 4 or 1
     const uint16_t* raw;
     uint32_t n_frames, frame_base;
@@ -62,6 +64,12 @@ bool cm_big_supported(const ChainParams& p, const CmBigConfig& cfg);
 size_t cm_big_smem_bytes(const ChainParams& p);
 cudaError_t launch_cm_big(const ChainParams& p, const CmBigConfig& cfg, const uint16_t* raw,
                           uint32_t n_frames, float* cm, cudaStream_t stream);
+
+// Units of at most 512 pixels (one warp each), cut an integer in (-1e6, 1e6).
+float cm_rows_magic(const ChainParams& p);
+bool cm_rows_supported(const ChainParams& p);
+cudaError_t launch_cm_rows(const ChainParams& p, const uint16_t* raw, uint32_t n_frames,
+                           float* cm, cudaStream_t stream);
 
 BandConfig make_band_config(const ChainParams& p);
 size_t band_smem_bytes(const ChainParams& p, uint32_t rb, uint32_t pitch);

@@ -155,6 +155,26 @@ def test_bank_min_count_not_reached():
     assert not ref.cm.any()
 
 
+def test_rows_median_below_window_uses_radix_fallback():
+    # row units: window [cut - 256, cut) = [-56, 200); d is about -300 ADU
+    det = synth.asic_352x384(rows=24)
+    ref = _run_case(det, 2, ped_shift=300.0)
+    assert ref.n_hits > 0 and float(ref.cm.max()) < -56.0
+
+
+def test_rows_flat_frames_many_equal_values():
+    # integer pedestals, no noise: every d of a row is equal (> 64 values in
+    # one 1/64-ADU sub-bin)
+    det = synth.epix_704x768(rows=16, noise_sigma=0.0)
+    ref = _run_case(det, 2, integer_ped=True)
+    assert ref.n_hits > 0
+
+
+def test_rows_non_integer_cut_generic_kernel():
+    det = synth.asic_352x384(rows=24)
+    _run_case(det, 2, thr_over=dict(cm_cut_adu=200.25))
+
+
 def test_cm_none_and_masked_pixels():
     det = synth.asic_352x384(rows=32)
     ped, gain = synth.maps(det)
