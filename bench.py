@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--band-rows", type=int, default=0)
     ap.add_argument("--no-overlap", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=100000.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     return ap.parse_args()
 
 
@@ -314,6 +317,10 @@ def run_pd(args):
         line["e2e"] = {"value": round(nf * ws / dt, 1), "unit": "frames/s",
                        "h2d_bytes_per_step": raw_b, "d2h_bytes_per_step": nh * HIT_BYTES + 4,
                        "api": "pd_process_host (page-locked host frames, hits back to host)"}
+    if rank == 0 and ws == 1 and not args.no_serve:
+        del frames, out
+        torch.cuda.empty_cache()
+        line["serve"] = serve_run(args, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(det, ped, gain, raw[:64])
     if rank == 0:
@@ -322,6 +329,85 @@ def run_pd(args):
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return 0
+
+
+def h2d_bandwidth(dev, nbytes=1 << 30, reps=5):
+    """Page-locked host -> device copy bandwidth (GB/s), CUDA events."""
+    import torch
+    src = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    dst = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    dst.copy_(src, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        dst.copy_(src, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    return nbytes * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+
+def serve_run(args, dev):
+    """Streaming serve: Poisson arrivals at the target rate from page-locked
+    rings, 80 % ePix100-sized 704x768 frames and 20 % 2.2 Mpx CSPAD frames,
+    per-frame occupancy log-uniform in [0.1 %, 2 %]; continuous batching on
+    the device; latency = arrival to hits on the host."""
+    import torch
+    from paper_1903_06838_gb300 import pd, synth
+
+    dets = [synth.epix_704x768(occupancy=0.001, occupancy_hi=0.02, seed=41),
+            synth.cspad_2p2m(occupancy=0.001, occupancy_hi=0.02, seed=42)]
+    distinct, ring = 64, 512
+    ctxs, frames = [], []
+    for d in dets:
+        ped, gain = synth.maps(d)
+        raw, _ = synth.frames(d, ped, gain, 0, distinct, truth=False)
+        frames.append(raw.reshape(distinct, -1))
+        ctxs.append(pd.pd_create(d.geometry(), ped, gain, d.thresholds()))
+    sv = pd.Server(ctxs, n_slots=8, max_batch_frames=32, ring_frames=ring,
+                   hits_per_frame=49152, max_uploading=1)
+    for g in range(len(dets)):
+        for k in range(ring):
+            sv.ring_frame(g, k)[:] = frames[g][k % distinct]
+    link = h2d_bandwidth(dev)
+    out = {}
+    for name, mix in (("mix", [0.8, 0.2]), ("epix_only", [1.0, 0.0])):
+        sv.replay(args.serve_rate, 0.3, mix=mix, seed=1)       # warm-up
+        sv.drain(60.0)
+        sv.reset_stats()
+        clocks = Clocks(dev.index or 0)
+        clocks.start()
+        sv.replay(args.serve_rate, args.serve_seconds, mix=mix, seed=2, first_id=1 << 32)
+        sv.drain(120.0)
+        clk = clocks.stop()
+        out[name] = _serve_line(sv.stats(), args, mix, link, clk)
+        sv.reset_stats()
+    sv.close()
+    return out
+
+
+def _serve_line(st, args, mix, link, clk):
+    el = max(st["elapsed_s"], 1e-9)
+    return {
+        "workload": f"Poisson arrivals, {mix[0]:.0%} 704x768 / {mix[1]:.0%} 32x185x388, "
+                    "occupancy log-uniform 0.1-2%, page-locked rings pre-filled with 64 "
+                    "distinct frames per geometry; 8 slots, <= 32 frames per geometry per "
+                    "batch, 1 batch uploading at a time",
+        "offered_hz": args.serve_rate, "seconds": args.serve_seconds,
+        "frames_done": st["frames_done"], "frames_rejected": st["frames_rejected"],
+        "sustained_hz": round(st["frames_done"] / el, 1),
+        "p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1),
+        "max_us": round(st["max_us"], 1), "mean_us": round(st["mean_us"], 1),
+        "mean_batch_frames": round(st["frames_done"] / max(st["batches"], 1), 2),
+        "h2d_gbs": round(st["raw_bytes"] / el / 1e9, 1),
+        "h2d_link_gbs": round(link, 1),
+        "h2d_frac_of_link": round(st["raw_bytes"] / el / 1e9 / link, 3),
+        "compression_ratio": round(st["raw_bytes"] / max(st["compressed_bytes"], 1), 1),
+        "hits_per_frame": round(st["hits"] / max(st["frames_done"], 1), 1),
+        "latency": "arrival (scheduled Poisson time) to hits on the host",
+        "clocks": clk,
+    }
 
 
 def main():

@@ -321,6 +321,90 @@ int pd_net_refine(const float* out_dev, const pd_hit* hits_in_dev, uint32_t n,
                   float conf, pd_hit* hits_out_dev, void* stream);
 void pd_net_destroy(pd_net* net);
 
+/* ---- Streaming server -----------------------------------------------------
+ * The paper targets real-time reduction at LCLS-II rates (100 kHz; section
+ * "Introduction") and sparse photon lists that compress by about two orders
+ * of magnitude over raw frames (section "Performance").  This is the online
+ * form of the chain.  Continuous batching of frames of several geometries (one context each)
+ * from page-locked host rings.  A producer writes a frame into a ring slot
+ * (pd_server_acquire, or pd_server_ring_frame to pre-fill) and commits it
+ * with its id; the commit time is its arrival time.  A dispatcher thread
+ * keeps up to n_slots batches in flight, each on its own stream: when a
+ * slot frees it takes every committed frame (up to max_batch_frames per
+ * geometry), uploads, runs one pd_batch launch over all geometries and
+ * downloads the hit counts and then the hits.  Latency = arrival to hits on
+ * the host.  Host encoder threads then group the hits per frame, sort them
+ * by pixel and encode them (pd_compress_hits format); a frame is done when
+ * encoded.  Summaries accumulate in each context (running count map).
+ * The device budget (bytes) bounds the slots: admission waits for a free
+ * slot, and pd_server_create fails with PD_EBUSY if not even one fits. */
+typedef struct pd_server pd_server;
+
+typedef struct {
+    uint32_t n_slots;           /* batches in flight at most               */
+    uint32_t max_batch_frames;  /* frames per geometry per batch           */
+    uint32_t ring_frames;       /* host ring slots per geometry            */
+    uint32_t hits_per_frame;    /* hit capacity per frame of a batch       */
+    uint64_t device_budget;     /* bytes of slot buffers; 0 = free device  *
+                                 * memory at creation less 1 GiB            */
+    uint32_t keep_hits;         /* 1: keep each frame's hits and stream    */
+    uint32_t encode_threads;    /* host encoder threads; 0 = min(8, cores/2) */
+    uint32_t max_uploading;     /* batches still uploading frames at most;  *
+                                 * 0 = 1 (admission holds frames in the    *
+                                 * ring while the link is this busy)       */
+    uint32_t reserved;          /* 0 */
+} pd_serve_config;
+
+typedef struct {
+    uint64_t frames_committed, frames_done, frames_rejected;
+    uint64_t batches, max_batch_frames;
+    uint64_t raw_bytes, compressed_bytes, hits;
+    double elapsed_s;            /* first arrival to last completion        */
+    double p50_us, p99_us, max_us, mean_us;
+} pd_serve_stats;
+
+int pd_server_create(pd_ctx* const* ctxs, uint32_t n_geometries, const pd_serve_config* cfg,
+                     pd_server** out);
+int pd_server_slots(const pd_server* server, uint32_t* n_slots);
+/* hold != 0: issue no new batches (frames keep queueing in the rings);
+ * 0: resume.  Batches already in flight complete. */
+int pd_server_hold(pd_server* server, int hold);
+/* Pointer to ring slot `slot` of a geometry (to pre-fill frames). */
+int pd_server_ring_frame(pd_server* server, uint32_t geometry, uint32_t slot,
+                         uint16_t** frame_host);
+/* Next free slot of the geometry's ring (PD_EBUSY when the ring is full:
+ * back-pressure; the frame is counted as rejected). */
+int pd_server_acquire(pd_server* server, uint32_t geometry, uint16_t** frame_host,
+                      uint32_t* slot);
+int pd_server_commit(pd_server* server, uint32_t geometry, uint32_t slot, uint64_t frame_id);
+/* Built-in producer: Poisson arrivals at rate_hz for duration_s, geometry
+ * drawn with weights mix[n_geometries] (NULL = equal), each arrival commits
+ * the next ring slot of its geometry (its content as pre-filled) with the
+ * scheduled arrival time; ids from first_id.  Synchronous. */
+int pd_server_replay(pd_server* server, double rate_hz, double duration_s, const float* mix,
+                     uint64_t seed, uint64_t first_id);
+/* Wait until every committed frame is done (PD_ETIMEDOUT after timeout_s). */
+int pd_server_drain(pd_server* server, double timeout_s);
+int pd_server_stats(pd_server* server, pd_serve_stats* stats);
+int pd_server_reset_stats(pd_server* server);
+/* Hits of a finished frame (keep_hits = 1), sorted by pixel, with frame =
+ * the frame id; up to cap are copied, *n_hits is the full count. */
+int pd_server_frame_hits(pd_server* server, uint64_t frame_id, pd_hit* out, uint32_t cap,
+                         uint32_t* n_hits, float* latency_us);
+/* The frame's compact hit stream (format of pd_compress_hits); *len is its
+ * size (PD_EOVERFLOW if cap is smaller; out = NULL to query). */
+int pd_server_frame_stream(pd_server* server, uint64_t frame_id, uint8_t* out, size_t cap,
+                           size_t* len);
+void pd_server_destroy(pd_server* server);
+
+/* Compact hit stream of one frame (the sparse photon list of sections
+ * "Summarization" and "Performance"): varint count, then per hit (sorted by
+ * pixel) the varint pixel delta, energy u16 in 1/256 keV, dx and dy i8 in
+ * 1/128 pixel (clipped), count u8.  Lossless for pixel and count. */
+int pd_compress_hits(const pd_hit* hits, uint32_t n, uint8_t* out, size_t cap, size_t* out_len);
+int pd_decompress_hits(const uint8_t* in, size_t len, uint32_t frame, pd_hit* out, uint32_t cap,
+                       uint32_t* n_out);
+
 /* Kernel timing.  When enabled on a context, every kernel the context
  * launches is bracketed by CUDA events recorded on the launching stream;
  * pd_read_profile synchronises the device, reports the summed device time

@@ -20,7 +20,8 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_PKG, "libpd.so")
-SOURCES = ["pd_api.cu", "pd_chain.cu", "pd_fast.cu", "pd_noalloc.cu", "pd_net.cu"]
+SOURCES = ["pd_api.cu", "pd_chain.cu", "pd_fast.cu", "pd_noalloc.cu", "pd_net.cu",
+           "pd_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
@@ -84,6 +85,22 @@ class PdBatchItem(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("frames", ctypes.c_void_p),
                 ("n_frames", ctypes.c_uint32), ("frame_base", ctypes.c_uint32),
                 ("out", PdOutputs)]
+
+
+class PdServeConfig(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_uint32), ("max_batch_frames", ctypes.c_uint32),
+                ("ring_frames", ctypes.c_uint32), ("hits_per_frame", ctypes.c_uint32),
+                ("device_budget", ctypes.c_uint64), ("keep_hits", ctypes.c_uint32),
+                ("encode_threads", ctypes.c_uint32), ("max_uploading", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class PdServeStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in
+                ("frames_committed", "frames_done", "frames_rejected", "batches",
+                 "max_batch_frames", "raw_bytes", "compressed_bytes", "hits")] + \
+               [(n, ctypes.c_double) for n in
+                ("elapsed_s", "p50_us", "p99_us", "max_us", "mean_us")]
 
 
 class PdError(RuntimeError):
@@ -154,6 +171,25 @@ def _declare(lib):
         "pd_batch_capture": ([vp, ctypes.POINTER(PdBatchItem), u32, vp], i32),
         "pd_batch_replay": ([vp, vp], i32),
         "pd_batch_destroy": ([vp], None),
+        "pd_server_create": ([ctypes.POINTER(vp), u32, ctypes.POINTER(PdServeConfig),
+                              ctypes.POINTER(vp)], i32),
+        "pd_server_slots": ([vp, ctypes.POINTER(u32)], i32),
+        "pd_server_hold": ([vp, i32], i32),
+        "pd_server_ring_frame": ([vp, u32, u32, ctypes.POINTER(vp)], i32),
+        "pd_server_acquire": ([vp, u32, ctypes.POINTER(vp), ctypes.POINTER(u32)], i32),
+        "pd_server_commit": ([vp, u32, u32, ctypes.c_uint64], i32),
+        "pd_server_replay": ([vp, ctypes.c_double, ctypes.c_double, vp, ctypes.c_uint64,
+                              ctypes.c_uint64], i32),
+        "pd_server_drain": ([vp, ctypes.c_double], i32),
+        "pd_server_stats": ([vp, ctypes.POINTER(PdServeStats)], i32),
+        "pd_server_reset_stats": ([vp], i32),
+        "pd_server_frame_hits": ([vp, ctypes.c_uint64, vp, u32, ctypes.POINTER(u32),
+                                  ctypes.POINTER(ctypes.c_float)], i32),
+        "pd_server_frame_stream": ([vp, ctypes.c_uint64, vp, ctypes.c_size_t,
+                                    ctypes.POINTER(ctypes.c_size_t)], i32),
+        "pd_server_destroy": ([vp], None),
+        "pd_compress_hits": ([vp, u32, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], i32),
+        "pd_decompress_hits": ([vp, ctypes.c_size_t, u32, vp, u32, ctypes.POINTER(u32)], i32),
         "pd_net_num_params": ([], u32),
         "pd_net_create": ([u32, ctypes.c_uint64, ctypes.POINTER(vp)], i32),
         "pd_net_set_params": ([vp, vp, u32], i32),
@@ -515,6 +551,126 @@ def pd_net_refine(out_ptr: int, hits_in_ptr: int, n: int, conf: float, hits_out_
 
 def pd_net_destroy(net: Net) -> None:
     net.close()
+
+
+# ---- streaming server --------------------------------------------------------
+class Server:
+    def __init__(self, ctxs, n_slots=4, max_batch_frames=32, ring_frames=256,
+                 hits_per_frame=16384, device_budget=0, keep_hits=False, encode_threads=0,
+                 max_uploading=0):
+        arr = (ctypes.c_void_p * len(ctxs))(*[c.handle for c in ctxs])
+        cfg = PdServeConfig(n_slots, max_batch_frames, ring_frames, hits_per_frame,
+                            device_budget, int(keep_hits), encode_threads, max_uploading, 0)
+        h = ctypes.c_void_p()
+        _check(load().pd_server_create(arr, len(ctxs), ctypes.byref(cfg), ctypes.byref(h)),
+               "pd_server_create")
+        self.handle = h.value
+        self.ctxs = list(ctxs)
+        self.ring_frames = ring_frames
+
+    def slots(self) -> int:
+        n = ctypes.c_uint32()
+        _check(load().pd_server_slots(self.handle, ctypes.byref(n)), "pd_server_slots")
+        return n.value
+
+    def hold(self, on: bool = True) -> None:
+        _check(load().pd_server_hold(self.handle, int(bool(on))), "pd_server_hold")
+
+    def ring_frame(self, geometry: int, slot: int) -> np.ndarray:
+        """numpy view (uint16 [pixels]) of a ring slot's page-locked memory."""
+        p = ctypes.c_void_p()
+        _check(load().pd_server_ring_frame(self.handle, geometry, slot, ctypes.byref(p)),
+               "pd_server_ring_frame")
+        n = self.ctxs[geometry].pixels_per_frame
+        return np.ctypeslib.as_array((ctypes.c_uint16 * n).from_address(p.value))
+
+    def acquire(self, geometry: int):
+        p = ctypes.c_void_p()
+        slot = ctypes.c_uint32()
+        rc = load().pd_server_acquire(self.handle, geometry, ctypes.byref(p), ctypes.byref(slot))
+        if rc == PD_EBUSY:
+            return None
+        _check(rc, "pd_server_acquire")
+        n = self.ctxs[geometry].pixels_per_frame
+        return slot.value, np.ctypeslib.as_array((ctypes.c_uint16 * n).from_address(p.value))
+
+    def commit(self, geometry: int, slot: int, frame_id: int) -> None:
+        _check(load().pd_server_commit(self.handle, geometry, slot, frame_id), "pd_server_commit")
+
+    def replay(self, rate_hz, duration_s, mix=None, seed=0, first_id=0) -> None:
+        m = (ctypes.c_float * len(self.ctxs))(*mix) if mix is not None else None
+        _check(load().pd_server_replay(self.handle, rate_hz, duration_s, m, seed, first_id),
+               "pd_server_replay")
+
+    def drain(self, timeout_s=60.0) -> None:
+        _check(load().pd_server_drain(self.handle, timeout_s), "pd_server_drain")
+
+    def stats(self) -> dict:
+        st = PdServeStats()
+        _check(load().pd_server_stats(self.handle, ctypes.byref(st)), "pd_server_stats")
+        return {n: getattr(st, n) for n, _ in PdServeStats._fields_}
+
+    def reset_stats(self) -> None:
+        _check(load().pd_server_reset_stats(self.handle), "pd_server_reset_stats")
+
+    def frame_hits(self, frame_id: int, cap: int = 1 << 20):
+        out = np.empty(cap, HIT_DTYPE)
+        n = ctypes.c_uint32()
+        lat = ctypes.c_float()
+        _check(load().pd_server_frame_hits(self.handle, frame_id, out.ctypes.data, cap,
+                                           ctypes.byref(n), ctypes.byref(lat)),
+               "pd_server_frame_hits")
+        return out[:min(n.value, cap)], float(lat.value)
+
+    def frame_stream(self, frame_id: int) -> bytes:
+        n = ctypes.c_size_t()
+        _check(load().pd_server_frame_stream(self.handle, frame_id, None, 0, ctypes.byref(n)),
+               "pd_server_frame_stream")
+        buf = (ctypes.c_uint8 * max(n.value, 1))()
+        _check(load().pd_server_frame_stream(self.handle, frame_id, buf, n.value,
+                                             ctypes.byref(n)), "pd_server_frame_stream")
+        return bytes(buf[:n.value])
+
+    def close(self):
+        if self.handle:
+            load().pd_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pd_server_create(ctxs, **kw) -> Server:
+    return Server(ctxs, **kw)
+
+
+def pd_server_destroy(server: Server) -> None:
+    server.close()
+
+
+def pd_compress_hits(hits: np.ndarray) -> bytes:
+    h = np.ascontiguousarray(hits, HIT_DTYPE)
+    need = ctypes.c_size_t()
+    _check(load().pd_compress_hits(h.ctypes.data, len(h), None, 0, ctypes.byref(need)),
+           "pd_compress_hits")
+    buf = (ctypes.c_uint8 * max(need.value, 1))()
+    _check(load().pd_compress_hits(h.ctypes.data, len(h), buf, need.value, ctypes.byref(need)),
+           "pd_compress_hits")
+    return bytes(buf[:need.value])
+
+
+def pd_decompress_hits(data: bytes, frame: int = 0) -> np.ndarray:
+    src = (ctypes.c_uint8 * max(len(data), 1)).from_buffer_copy(data or b"\0")
+    n = ctypes.c_uint32()
+    _check(load().pd_decompress_hits(src, len(data), frame, None, 0, ctypes.byref(n)),
+           "pd_decompress_hits")
+    out = np.zeros(n.value, HIT_DTYPE)
+    _check(load().pd_decompress_hits(src, len(data), frame, out.ctypes.data, n.value,
+                                     ctypes.byref(n)), "pd_decompress_hits")
+    return out
 
 
 def pd_strerror(code: int) -> str:
