@@ -32,6 +32,10 @@ METRIC = ("frames/s and HBM GB/s (fraction of peak) on 2.2 Mpx frames; "
           "p99 latency at 100kHz")
 FRAMES_PER_STEP = 1024
 HIT_BYTES = 24
+# DRAM bytes (read + write) per frame of each kernel, from the ncu capture
+# summarised in profiles/cspad_2p2m_chain.md; set an entry to None when its
+# kernel changes until it is captured again.
+NCU_TRAFFIC_PER_FRAME = {"stencil": 129.202944e6 / 21, "common_mode": 108.918016e6 / 21}
 
 
 def parse():
@@ -277,7 +281,10 @@ def run_pd(args):
         roof = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
                 "peak_kind": f"{peak_kind} copy bandwidth (burst)",
-                "traffic": None, "bytes_per_step": int(b / args.steps),
+                "traffic": (None if NCU_TRAFFIC_PER_FRAME.get(name) is None else
+                            round(NCU_TRAFFIC_PER_FRAME[name] * nf * args.steps / launches)),
+                "bytes_per_launch": round(b / launches),
+                "bytes_per_step": int(b / args.steps),
                 "launches_per_step": launches / args.steps,
                 "ms_per_launch": tot / launches,
                 "kernel_share": {k: round(v[1] / sum(x[1] for x in prof.values()), 4)
