@@ -35,7 +35,8 @@ HIT_BYTES = 24
 # DRAM bytes (read + write) per frame of each kernel, from the ncu capture
 # summarised in profiles/cspad_2p2m_chain.md; set an entry to None when its
 # kernel changes until it is captured again.
-NCU_TRAFFIC_PER_FRAME = {"stencil": 129.202944e6 / 21, "common_mode": 108.918016e6 / 21}
+NCU_TRAFFIC_PER_FRAME = {"stencil": 129.202944e6 / 21, "common_mode": 108.918016e6 / 21,
+                         "fused_chain": None}
 
 
 def parse():
@@ -50,6 +51,8 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--band-rows", type=int, default=0)
     ap.add_argument("--no-overlap", action="store_true")
+    ap.add_argument("--fused", action="store_true",
+                    help="one-kernel chain instead of the common-mode + stencil pair")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=100000.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
@@ -216,8 +219,9 @@ def run_pd(args):
     synth.frames(det, ped, gain, rank * nf, nf, truth=False, out=raw)
     frames = host.to(dev, non_blocking=False)
     ctx = pd.pd_create(det.geometry(), ped, gain, det.thresholds())
-    if args.chunk or args.band_rows or args.no_overlap:
-        pd.pd_set_tuning(ctx, args.chunk, args.band_rows, 0 if args.no_overlap else 1)
+    if args.chunk or args.band_rows or args.no_overlap or args.fused:
+        pd.pd_set_tuning(ctx, args.chunk, args.band_rows, 0 if args.no_overlap else 1,
+                         0 if args.fused else 1)
     cap = nf * 16384
     out = pd.Outputs(ctx, nf, cap, device=dev)
     stream = torch.cuda.current_stream(dev)

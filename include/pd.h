@@ -214,12 +214,18 @@ void pd_destroy(pd_ctx* ctx);
  * launch pair (a chunk's raw frames are re-read from L2 by the second
  * pass); band_rows: rows per stencil tile; overlap: 1 runs the common mode
  * of the next chunk on a second stream beside the stencil of the current
- * one.  Results never depend on tuning. */
+ * one; two_pass: 0 runs the whole chain as one kernel per (frame, module)
+ * where the geometry allows it (common-mode units that are full-height
+ * column banks, at most two per module, or common mode off; columns a
+ * multiple of 4), 1 uses the common-mode + stencil kernel pair (the
+ * default; pd_get_tuning reports 1 when the one-kernel form is not
+ * available).
+ * Results never depend on tuning. */
 typedef struct {
     uint32_t chunk_frames;
     uint32_t band_rows;
     uint32_t overlap;
-    uint32_t reserved;
+    uint32_t two_pass;
 } pd_tuning;
 
 int pd_get_tuning(const pd_ctx* ctx, pd_tuning* tuning);
@@ -228,7 +234,8 @@ int pd_set_tuning(pd_ctx* ctx, const pd_tuning* tuning);
 /* pd_autotune — choose the tuning of a context by timing candidates on the
  * caller's device frames (n_frames, 16-byte aligned): chunk sizes of about
  * 24-192 MB, band heights around the default, overlap on and off; each
- * candidate runs once to warm up and twice timed (CUDA events).  The
+ * candidate (and the one-kernel chain where available) runs once to warm
+ * up and twice timed (CUDA events).  The
  * fastest is applied to the context and returned in *best (may be NULL),
  * with its time per frame in microseconds.  Allocates and frees temporary
  * device buffers; the context's summaries are saved and restored, so they

@@ -43,7 +43,11 @@ struct pd_ctx {
     pd::ChainParams params;
     pd::CmBigConfig cm_cfg;
     pd::BandConfig band_cfg;
+    pd::FusedConfig fused_cfg;
     bool use_cm_big = false, use_cm_rows = false, use_band = false;
+    bool use_fused = false;     // the geometry allows the one-kernel chain
+    uint32_t two_pass = 1;      // 1: common-mode and stencil kernels (measured
+                                // faster on GB300 so far); 0: the one-kernel chain
     uint32_t chunk_frames = 1;  // frames per common-mode/stencil launch pair
     uint32_t overlap = 1;       // common mode of chunk c+1 beside stencil of c
     cudaStream_t aux = nullptr; // second stream of the chunk pipeline
@@ -224,6 +228,12 @@ int run_chain(pd_ctx* c, const uint16_t* frames, uint32_t n_frames, uint32_t fra
     if (zero && (e = cudaMemsetAsync(out->n_hits, 0, sizeof(uint32_t), s)) != cudaSuccess)
         return fail_cuda(e, "zero n_hits");
     if (n_frames == 0) return PD_OK;
+    if (c->use_fused && !c->two_pass) {
+        pd::CallOut co{out->hits, out->hit_capacity, out->n_hits, out->corrected, out->cm};
+        ProfileScope ps(c, 2, s);
+        e = pd::launch_fused(c->params, c->fused_cfg, frames, n_frames, frame_base, co, s);
+        return e == cudaSuccess ? PD_OK : fail_cuda(e, "chain kernel launch");
+    }
     float* cm = out->cm;
     if (!cm) {
         int rc = ensure_cm(c, n_frames);
@@ -312,6 +322,11 @@ int internal_run_sequential(pd_ctx* c, const uint16_t* frames, uint32_t n_frames
                             cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(out->n_hits, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return fail_cuda(e, "zero n_hits");
+    if (c->use_fused && !c->two_pass) {
+        CallOut co{out->hits, out->hit_capacity, out->n_hits, out->corrected, out->cm};
+        e = launch_fused(c->params, c->fused_cfg, frames, n_frames, frame_base, co, s);
+        return e == cudaSuccess ? PD_OK : fail_cuda(e, "chain kernel launch");
+    }
     for (uint32_t done = 0; done < n_frames;) {
         const uint32_t nf = std::min(c->chunk_frames, n_frames - done);
         const uint16_t* fr = frames + (size_t)done * c->params.frame_px;
@@ -398,6 +413,8 @@ int pd_create(const pd_geometry* geometry, const float* pedestal_host,
     c->use_cm_rows = g.cm_mode == PD_CM_MEDIAN && !c->use_cm_big && pd::cm_rows_supported(p);
     c->band_cfg = pd::make_band_config(p);
     c->use_band = c->band_cfg.ok;
+    c->fused_cfg = pd::make_fused_config(p);
+    c->use_fused = c->fused_cfg.ok;
     {
         const size_t fbytes = (size_t)p.frame_px * 2;
         const size_t target = 96u << 20;  // raw bytes per chunk (measured best)
@@ -613,7 +630,7 @@ int pd_get_tuning(const pd_ctx* c, pd_tuning* t) {
     t->chunk_frames = c->chunk_frames;
     t->band_rows = c->use_band ? c->band_cfg.rb : 0;
     t->overlap = c->overlap;
-    t->reserved = 0;
+    t->two_pass = c->use_fused ? c->two_pass : 1;
     return PD_OK;
 }
 
@@ -630,6 +647,7 @@ int pd_set_tuning(pd_ctx* c, const pd_tuning* t) {
         c->band_cfg.n_bands = (c->params.rows + rb - 1) / rb;
     }
     c->overlap = t->overlap ? 1 : 0;
+    c->two_pass = t->two_pass ? 1 : 0;
     return PD_OK;
 }
 
@@ -887,10 +905,12 @@ int pd_autotune(pd_ctx* c, const uint16_t* frames_dev, uint32_t n_frames, pd_tun
         o.hits = hits;
         o.hit_capacity = cap;
         o.n_hits = nh;
+        std::vector<pd_tuning> cands;
+        if (c->use_fused) cands.push_back(pd_tuning{orig.chunk_frames, orig.band_rows, 1, 0});
         for (uint32_t cf : chunks)
             for (uint32_t bd : bands)
-                for (uint32_t ov : {1u, 0u}) {
-                    pd_tuning t{cf, bd ? bd : orig.band_rows, ov, 0};
+                for (uint32_t ov : {1u, 0u}) cands.push_back(pd_tuning{cf, bd ? bd : orig.band_rows, ov, 1});
+        for (const pd_tuning& t : cands) {
                     if (pd_set_tuning(c, &t) != PD_OK) continue;
                     if (run_chain(c, frames_dev, n_frames, 0, &o, nullptr) != PD_OK) continue;
                     cudaEventRecord(e0, nullptr);

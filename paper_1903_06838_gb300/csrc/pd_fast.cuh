@@ -77,4 +77,30 @@ cudaError_t launch_stencil_band(const ChainParams& p, const BandConfig& bc, cons
                                 uint32_t n_frames, uint32_t frame_base, const CallOut& out,
                                 cudaStream_t stream);
 
+// Whole chain in one persistent kernel per (frame, module) for modules whose
+// common-mode units are full-height column banks (at most kFusedMaxUnits per
+// module), or with common mode off; columns a multiple of 4.
+constexpr uint32_t kFusedCmBins = 3584;  // bins of 1/8 ADU: window [cut - 448, cut)
+constexpr uint32_t kFusedMaxUnits = 2;
+#ifndef PD_FUSED_MAX_TY
+#define PD_FUSED_MAX_TY 3
+#endif
+constexpr uint32_t kFusedMaxTy = PD_FUSED_MAX_TY;  // row lanes per CTA (registers: 2 CTAs / SM)
+
+struct FusedConfig {
+    float magic_w;                  // 1.5*2^23 - 8*(cut - 448)
+    float w_lo;                     // cut - 448: lower edge of bin 0
+    uint32_t tx, ty;                // chunk columns (cols / 4) x row lanes
+    uint32_t pitch;                 // floats per ring row (cols + 8)
+    uint32_t region_a_words;        // codes, then ring + seed lists
+    uint32_t region_b_words;        // histograms, then candidates
+    uint32_t smem_bytes;
+    bool ok;
+};
+
+FusedConfig make_fused_config(const ChainParams& p);
+cudaError_t launch_fused(const ChainParams& p, const FusedConfig& fc, const uint16_t* raw,
+                         uint32_t n_frames, uint32_t frame_base, const CallOut& out,
+                         cudaStream_t stream);
+
 }  // namespace pd

@@ -310,13 +310,15 @@ def test_full_size_cspad_batch_sampled():
         assert cm_all[f].tobytes() == ref.cm.reshape(-1).tobytes()
 
 
-@pytest.mark.parametrize("tuning", [dict(chunk_frames=1, overlap=1),
-                                    dict(chunk_frames=3, overlap=0),
-                                    dict(chunk_frames=2, band_rows=4, overlap=1),
-                                    dict(chunk_frames=5, band_rows=17, overlap=1)])
+@pytest.mark.parametrize("tuning", [dict(chunk_frames=1, overlap=1, two_pass=0),
+                                    dict(chunk_frames=1, overlap=1, two_pass=1),
+                                    dict(chunk_frames=3, overlap=0, two_pass=1),
+                                    dict(chunk_frames=2, band_rows=4, overlap=1, two_pass=1),
+                                    dict(chunk_frames=5, band_rows=17, overlap=1, two_pass=1)])
 def test_results_independent_of_tuning(tuning):
-    """Chunking, band height and the two-stream overlap change only the
-    launch schedule: hits (as a set), common mode and summaries are equal."""
+    """Chunking, band height, the two-stream overlap and the choice between
+    the one-kernel chain and the kernel pair change only the launch schedule:
+    hits (as a set), common mode and summaries are equal."""
     det = synth.cspad_2p2m(n_modules=3, occupancy=0.01)
     ped, gain = synth.maps(det)
     raw, _ = synth.frames(det, ped, gain, 0, 11)
