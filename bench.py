@@ -259,6 +259,15 @@ def run_pd(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_step = float(t.item())
     fps = nf * ws / (ms_step / 1e3)
+    merged = None
+    if ws > 1:
+        # the one exchange step (after the timed region): integer sums of the
+        # ranks' photon-count maps and histograms
+        from paper_1903_06838_gb300 import dist as pdist
+        cmap, hp, hh = pd.pd_get_summary(ctx)
+        cmap, hp, hh = pdist.merge_summaries(cmap, hp, hh, device=dev)
+        merged = {"photons": int(cmap.sum()), "pixels_histogrammed": int(hp.sum()),
+                  "seeds": int(hh.sum())}
 
     # roofline of the dominant kernel: algorithmic bytes / its mean duration
     peak, peak_kind = read_peaks()
@@ -309,6 +318,8 @@ def run_pd(args):
         "clocks": clk,
         "gpu_launches": int(round(launches_per_step * args.steps)),
     }
+    if merged is not None:
+        line["merged_summaries"] = merged
 
     # end to end through the host-buffer entry point (pinned host frames)
     if not args.no_e2e:
