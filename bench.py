@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--fused", action="store_true",
                     help="one-kernel chain instead of the common-mode + stencil pair")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-net", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=100000.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     return ap.parse_args()
@@ -92,6 +93,15 @@ def read_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def read_peaks_all() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {k: v for k, v in d.items() if isinstance(v, (int, float))}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
 class Clocks:
@@ -343,6 +353,8 @@ def run_pd(args):
         del frames, out
         torch.cuda.empty_cache()
         line["serve"] = serve_run(args, dev)
+    if rank == 0 and ws == 1 and not args.no_net:
+        line["net"] = net_run(args, dev, read_peaks_all())
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(det, ped, gain, raw[:64])
     if rank == 0:
@@ -429,6 +441,111 @@ def _serve_line(st, args, mix, link, clk):
         "hits_per_frame": round(st["hits"] / max(st["frames_done"], 1), 1),
         "latency": "arrival (scheduled Poisson time) to hits on the host",
         "clocks": clk,
+    }
+
+
+COUNT_CONF = 0.999   # softmax confidence above which the network's count replaces the
+                     # classical one (offsets are replaced from 0.9)
+NET_FWD_FLOP = 25 * 32 * 9 * 2 + 25 * 32 * 288 * 2 + 64 * 800 * 2 + 7 * 64 * 2  # per hit
+
+
+def net_run(args, dev, peaks):
+    """Learned count / offset network: training on generated hits with known
+    truth (occupancy log-uniform 0.5-5 %, cloud width U(0.2, 0.5) px,
+    352x384 ASIC at 8 keV), quality on held-out hits, and the tensor-core
+    throughput of inference (2^20 patches) and of training steps."""
+    import torch
+    from paper_1903_06838_gb300 import learn, pd, synth
+
+    det = synth.asic_352x384(occupancy=0.005, occupancy_hi=0.05, cloud_sigma=0.2,
+                             cloud_sigma_hi=0.5, seed=31)
+    _, ptr, _, lab_tr = learn.make_set(det, 40, 0)
+    hits_te, pte, (c_te, t_te, m_te), _ = learn.make_set(det, 12, 1000)
+    batch = 4096
+    net = pd.pd_net_create(1 << 16, seed=7)
+    t0 = time.perf_counter()
+    learn.train(net, ptr, lab_tr, steps=800, batch=2048, lr=2e-3)
+    train_wall = time.perf_counter() - t0
+    out = learn.predict(net, pte).cpu().numpy()
+    single = m_te == 1
+    com = np.stack([hits_te["dx"], hits_te["dy"]], 1)[single]
+    rms_com = float(np.sqrt(((com - t_te[single]) ** 2).mean()))
+    rms_net = float(np.sqrt(((out[single, 5:7] - t_te[single]) ** 2).mean()))
+    outs = torch.from_numpy(out).to(dev)
+    hin = torch.from_numpy(hits_te.view(np.uint8).reshape(len(hits_te), 24)).to(dev)
+    hout = torch.empty_like(hin)
+    gates = {}
+    for cc in (0.9, 0.99, 0.999, 2.0):
+        pd.pd_net_refine(outs.data_ptr(), hin.data_ptr(), len(hits_te), 0.9, cc,
+                         hout.data_ptr())
+        torch.cuda.synchronize(dev)
+        r = hout.cpu().numpy().view(pd.HIT_DTYPE).reshape(-1)
+        gates[cc] = r
+        if cc == COUNT_CONF:
+            ref = r
+    learned = (ref["flags"] & pd.PD_HIT_LEARNED) != 0
+    # refined hits against truth on the offsets they carry
+    rms_ref = float(np.sqrt(((np.stack([ref["dx"], ref["dy"]], 1)[single] - t_te[single]) ** 2)
+                            .mean()))
+    count_gates = {
+        ("never" if cc > 1 else str(cc)): {
+            "disagreement_vs_classical": round(float((r["count"] != hits_te["count"]).mean()), 5),
+            "agreement_with_truth": round(float((r["count"] == c_te).mean()), 4)}
+        for cc, r in gates.items()}
+    # throughput: inference over 2^20 patches, training steps of 4096
+    n_inf = 1 << 20
+    reps = (n_inf + pte.shape[0] - 1) // pte.shape[0]
+    big = pte.repeat(reps, 1)[:n_inf].contiguous()
+    o_big = torch.empty((n_inf, 7), dtype=torch.float32, device=dev)
+    pd.pd_net_forward(net, big.data_ptr(), n_inf, o_big.data_ptr())
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        pd.pd_net_forward(net, big.data_ptr(), n_inf, o_big.data_ptr())
+    e1.record()
+    torch.cuda.synchronize(dev)
+    inf_s = e0.elapsed_time(e1) / 5 / 1e3
+    counts, tgt, mask = lab_tr
+    idx = torch.arange(batch, device=dev) % ptr.shape[0]
+    x, c, t, m = (ptr[idx].contiguous(), counts[idx].contiguous(), tgt[idx].contiguous(),
+                  mask[idx].contiguous())
+    nreg = float(m.sum().item())
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        pd.pd_net_train_step(net, x.data_ptr(), c.data_ptr(), t.data_ptr(), m.data_ptr(),
+                             batch, nreg, 10.0, 0.0, loss.data_ptr())
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for _ in range(50):
+        pd.pd_net_train_step(net, x.data_ptr(), c.data_ptr(), t.data_ptr(), m.data_ptr(),
+                             batch, nreg, 10.0, 0.0, loss.data_ptr())
+    e1.record()
+    torch.cuda.synchronize(dev)
+    step_s = e0.elapsed_time(e1) / 50 / 1e3
+    bf16 = peaks.get("bf16_tflops")
+    inf_tf = n_inf * NET_FWD_FLOP / inf_s / 1e12
+    tr_tf = 3 * batch * NET_FWD_FLOP / step_s / 1e12
+    return {
+        "workload": "352x384 ASIC, 8 keV, occupancy 0.5-5 %, cloud sigma 0.2-0.5 px; "
+                    "train 800 Adam steps of 2048 hits from 40 frames, test on 12 other "
+                    "frames",
+        "train_hits": int(ptr.shape[0]), "test_hits": int(len(hits_te)),
+        "train_wall_s": round(train_wall, 2),
+        "rms_offset_px": {"centre_of_mass": round(rms_com, 4), "network": round(rms_net, 4),
+                          "refined_conf_0.9": round(rms_ref, 4)},
+        "learned_fraction": round(float(learned.mean()), 4),
+        "offset_conf": 0.9, "count_conf": COUNT_CONF,
+        "count_disagreement_vs_classical": round(
+            float((ref["count"] != hits_te["count"]).mean()), 5),
+        "classical_count_agreement_with_truth": round(float((hits_te["count"] == c_te).mean()), 4),
+        "count_gates": count_gates,
+        "inference": {"hits_per_s": round(n_inf / inf_s), "tflops": round(inf_tf, 1),
+                      "frac_of_bf16_peak": round(inf_tf / bf16, 4) if bf16 else None},
+        "training": {"samples_per_s": round(batch / step_s),
+                     "tflops": round(tr_tf, 1),
+                     "frac_of_bf16_peak": round(tr_tf / bf16, 4) if bf16 else None},
+        "flop_per_hit_forward": NET_FWD_FLOP,
     }
 
 

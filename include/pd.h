@@ -321,11 +321,13 @@ int pd_net_gradients(pd_net* net, const float* patches_dev, const uint8_t* count
 int pd_net_train_step(pd_net* net, const float* patches_dev, const uint8_t* counts_dev,
                       const float* targets_dev, const uint8_t* mask_dev, uint32_t n,
                       float n_reg, float lambda, float lr, float* loss_dev, void* stream);
-/* Copy hits, replacing count and (dx, dy) by the network's where its
- * softmax confidence is >= conf and its count >= 1 (flag PD_HIT_LEARNED);
- * elsewhere the classical values stay (the fallback). */
+/* Copy hits, replacing (dx, dy) by the network's where its softmax
+ * confidence is >= conf and its most likely count is >= 1 (flag
+ * PD_HIT_LEARNED), and the count too where the confidence is also >=
+ * count_conf; elsewhere the classical values stay (the fallback).
+ * count_conf > 1 never changes a count. */
 int pd_net_refine(const float* out_dev, const pd_hit* hits_in_dev, uint32_t n,
-                  float conf, pd_hit* hits_out_dev, void* stream);
+                  float conf, float count_conf, pd_hit* hits_out_dev, void* stream);
 void pd_net_destroy(pd_net* net);
 
 /* ---- Streaming server -----------------------------------------------------

@@ -295,7 +295,8 @@ __global__ void gather_kernel(pd::ChainParams p, const uint16_t* __restrict__ ra
 // Replace count and (dx, dy) of hits the network is confident about; keep
 // the classical values elsewhere.
 __global__ void refine_kernel(const float* __restrict__ out, const pd_hit* __restrict__ in,
-                              uint32_t n, float conf, pd_hit* __restrict__ res) {
+                              uint32_t n, float conf, float count_conf,
+                              pd_hit* __restrict__ res) {
     const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n) return;
     pd_hit h = in[b];
@@ -311,7 +312,7 @@ __global__ void refine_kernel(const float* __restrict__ out, const pd_hit* __res
     for (int k = 0; k < 5; k++) s += expf(o[k] - mx);
     const float pmax = 1.0f / s;
     if (pmax >= conf && arg >= 1) {
-        h.count = (uint8_t)arg;
+        if (pmax >= count_conf) h.count = (uint8_t)arg;
         h.dx = o[5];
         h.dy = o[6];
         h.flags |= PD_HIT_LEARNED;
@@ -514,11 +515,11 @@ int pd_net_train_step(pd_net* n, const float* patches, const uint8_t* counts, co
 }
 
 int pd_net_refine(const float* out_dev, const pd_hit* hits_in, uint32_t count, float conf,
-                  pd_hit* hits_out, void* stream) {
+                  float count_conf, pd_hit* hits_out, void* stream) {
     if (count && (!out_dev || !hits_in || !hits_out)) return net_fail(PD_EINVAL, "pd_net_refine");
     if (!count) return PD_OK;
-    refine_kernel<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(out_dev, hits_in, count,
-                                                                         conf, hits_out);
+    refine_kernel<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+        out_dev, hits_in, count, conf, count_conf, hits_out);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PD_OK : net_cuda(e, "refine");
 }

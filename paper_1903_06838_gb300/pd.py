@@ -200,7 +200,7 @@ def _declare(lib):
                               vp], i32),
         "pd_net_train_step": ([vp, vp, vp, vp, vp, u32, ctypes.c_float, ctypes.c_float,
                                ctypes.c_float, vp, vp], i32),
-        "pd_net_refine": ([vp, vp, u32, ctypes.c_float, vp, vp], i32),
+        "pd_net_refine": ([vp, vp, u32, ctypes.c_float, ctypes.c_float, vp, vp], i32),
         "pd_net_destroy": ([vp], None),
         "pd_get_tuning": ([vp, ctypes.POINTER(PdTuning)], i32),
         "pd_set_tuning": ([vp, ctypes.POINTER(PdTuning)], i32),
@@ -548,9 +548,9 @@ def pd_net_train_step(net: Net, patches_ptr, counts_ptr, targets_ptr, mask_ptr, 
                                     _stream_handle(stream)), "pd_net_train_step")
 
 
-def pd_net_refine(out_ptr: int, hits_in_ptr: int, n: int, conf: float, hits_out_ptr: int,
-                  stream=None) -> None:
-    _check(load().pd_net_refine(out_ptr, hits_in_ptr, n, conf, hits_out_ptr,
+def pd_net_refine(out_ptr: int, hits_in_ptr: int, n: int, conf: float, count_conf: float,
+                  hits_out_ptr: int, stream=None) -> None:
+    _check(load().pd_net_refine(out_ptr, hits_in_ptr, n, conf, count_conf, hits_out_ptr,
                                 _stream_handle(stream)), "pd_net_refine")
 
 

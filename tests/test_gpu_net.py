@@ -122,7 +122,7 @@ def test_training_beats_centre_of_mass():
     outs = torch.from_numpy(out).cuda()
     hin = torch.from_numpy(hits_te.view(np.uint8).reshape(len(hits_te), 24)).cuda()
     hout = torch.empty_like(hin)
-    pd.pd_net_refine(outs.data_ptr(), hin.data_ptr(), len(hits_te), 0.9, hout.data_ptr())
+    pd.pd_net_refine(outs.data_ptr(), hin.data_ptr(), len(hits_te), 0.9, 0.9, hout.data_ptr())
     torch.cuda.synchronize()
     ref = hout.cpu().numpy().view(pd.HIT_DTYPE).reshape(-1)
     learned_flag = (ref["flags"] & pd.PD_HIT_LEARNED) != 0
@@ -134,3 +134,9 @@ def test_training_beats_centre_of_mass():
     keep = ~learned_flag
     assert (ref["dx"][keep] == hits_te["dx"][keep]).all()
     assert (ref["count"][learned_flag] == probs.argmax(1)[learned_flag]).all()
+    # a count gate above 1 keeps every classical count, offsets still refined
+    pd.pd_net_refine(outs.data_ptr(), hin.data_ptr(), len(hits_te), 0.9, 2.0, hout.data_ptr())
+    torch.cuda.synchronize()
+    ref2 = hout.cpu().numpy().view(pd.HIT_DTYPE).reshape(-1)
+    assert (ref2["count"] == hits_te["count"]).all()
+    assert (ref2["dx"] == ref["dx"]).all() and (ref2["flags"] == ref["flags"]).all()
