@@ -35,6 +35,14 @@
 #include "pd_dev.cuh"
 #include "pd_fast.cuh"
 
+// rows of loads a thread keeps in flight (common mode, band stencil)
+#ifndef PD_CM_UNROLL
+#define PD_CM_UNROLL 8
+#endif
+#ifndef PD_BAND_UNROLL
+#define PD_BAND_UNROLL 2
+#endif
+
 namespace pd {
 
 namespace {
@@ -79,6 +87,20 @@ __device__ void cm_big_unit(const ChainParams& p, const uint16_t* __restrict__ r
     const uint32_t tx = tid % TX, ty = tid / TX;
     const bool active = ty < TY;
 
+    // VEC == 2: all raw pairs of the unit are copied into the code buffer
+    // at once (one request per pair, none held in registers), before the
+    // histogram is zeroed so the copies' latency overlaps it; each pair is
+    // replaced in place by its two bin codes in pass A
+    if (VEC == 2 && active) {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(fr + (r0 + ty) * p.cols + c0) + tx;
+        const uint32_t sstride = TY * p.cols / 2;
+        uint32_t* dst = codes + ty * TX + tx;
+        for (uint32_t r = ty; r < p.unit_rows; r += TY) {
+            cp_async4(dst, src);
+            src += sstride;
+            dst += TY * TX;
+        }
+    }
     for (uint32_t i = tid; i < kCmBins / 4; i += nthr)
         reinterpret_cast<uint4*>(hist)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
@@ -93,21 +115,8 @@ __device__ void cm_big_unit(const ChainParams& p, const uint16_t* __restrict__ r
     // pixel with d >= cut adds to the spare bin kCmBins, which is never read.
     if (active) {
         if (VEC == 2) {
-            // all raw pairs of the unit are copied into the code buffer at
-            // once (one request per pair, none held in registers); each pair
-            // is then replaced in place by its two bin codes
-            {
-                const uint32_t* src = reinterpret_cast<const uint32_t*>(fr + (r0 + ty) * p.cols + c0) + tx;
-                const uint32_t sstride = TY * p.cols / 2;
-                uint32_t* dst = codes + ty * TX + tx;
-                for (uint32_t r = ty; r < p.unit_rows; r += TY) {
-                    cp_async4(dst, src);
-                    src += sstride;
-                    dst += TY * TX;
-                }
-                cp_async_wait_all();  // each thread reads back only its own copies
-            }
-            constexpr int U = 8;
+            cp_async_wait_all();  // each thread reads back only its own copies
+            constexpr int U = PD_CM_UNROLL;
             const float2* prow = reinterpret_cast<const float2*>(npm + (r0 + ty) * p.cols + c0) + tx;
             const uint32_t stride = TY * p.cols / 2;  // pairs between a thread's rows
             uint32_t* cptr = codes + ty * TX + tx;
@@ -494,7 +503,6 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
     uint32_t* list = hhit + p.hist_bins;                         // kSeedCap
     float* cmt = reinterpret_cast<float*>(list + kSeedCap);      // (rb+2) * upr
     uint32_t& s_list_n = bsh.s_list_n;
-    uint32_t* swarp = bsh.swarp;
 
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31;
@@ -516,6 +524,21 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
     for (uint32_t i = tid; i < 2 * p.hist_bins + 4; i += nthr) hpix[i] = 0;
     __syncthreads();
 
+    // negated common mode of (tile row, unit column) entry i of tile tt;
+    // each thread holds its entries of the next tile in registers, loaded
+    // while the current tile's seeds are tested
+    // (tile indices of one call stay below 2^32)
+    const uint32_t ncmt = (bc.rb + 2) * p.units_per_row;
+    auto tile_cm = [&](uint32_t tt, uint32_t i) -> float {
+        const uint32_t fm = tt / bc.n_bands;
+        const int r = (int)(tt - fm * bc.n_bands) * (int)bc.rb - 1 + (int)(i / p.units_per_row);
+        if (r < 0 || r >= R) return 0.0f;
+        return -out.cm[(size_t)fm * p.units_per_module +
+                       ((uint32_t)r / p.unit_rows) * p.units_per_row + i % p.units_per_row];
+    };
+    float cmv = 0.0f;
+    if (first < n_tiles && tid < ncmt) cmv = tile_cm((uint32_t)first, tid);
+
     for (unsigned long long t = first; t < n_tiles; t += step) {
         unsigned long long q = t;
         const int band = (int)(q % bc.n_bands);
@@ -528,30 +551,22 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
         const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
         const float* npm = p.nped + mod_base;
         const float* gm = p.inv_gain + mod_base;
-        const float* cmf = out.cm + (size_t)f * p.units_per_frame +
-                           (size_t)m * p.units_per_module;
 
         // negated common mode of every (tile row, unit column)
-        for (uint32_t i = tid; i < (bc.rb + 2) * p.units_per_row; i += nthr) {
-            const int rl = (int)(i / p.units_per_row);
-            const int r = r0 - 1 + rl;
-            float v = 0.0f;
-            if (r >= 0 && r < R)
-                v = -cmf[((uint32_t)r / p.unit_rows) * p.units_per_row + i % p.units_per_row];
-            cmt[i] = v;
-        }
+        if (tid < ncmt) cmt[tid] = cmv;
+        for (uint32_t i = tid + nthr; i < ncmt; i += nthr) cmt[i] = tile_cm((uint32_t)t, i);
         if (tid == 0) s_list_n = 0;
         __syncthreads();
 
         // 1. zeroed signal of rows r0-1 .. r0+rows_here (halo rows included);
-        //    loads of two rows are issued before either is used.  Halo rows
+        //    loads of U rows are issued before any is used.  Halo rows
         //    are not histogrammed: their bins are clamped to the spare bin.
         uint64_t cmask = 0;  // seed candidates of this thread: bit k*VEC + i
         if (active) {
             const int nrows = rows_here + 2;
             int kk = 0;
-            for (int rl0 = (int)ty; rl0 < nrows; rl0 += 2 * (int)TY, kk += 2) {
-                constexpr int U = 2;
+            constexpr int U = PD_BAND_UNROLL;
+            for (int rl0 = (int)ty; rl0 < nrows; rl0 += U * (int)TY, kk += U) {
                 uint2 rr[U];
                 float4 pp[U], gg[U];
                 uint16_t r1[U];
@@ -650,11 +665,26 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
                 }
             }
         }
-        __syncthreads();
+        // the next tile's common mode, in flight during compaction and seeds
+        if (t + step < n_tiles && tid < ncmt) cmv = tile_cm((uint32_t)(t + step), tid);
 
-        // compaction of the candidates: counts, block scan, then writes
+        // compaction of the candidates: a warp scan and one shared atomic
+        // per warp reserve each thread's slots (list order is free)
         {
-            uint32_t at = block_excl_scan((uint32_t)__popcll(cmask), swarp, &s_list_n);
+            const unsigned wm = __activemask();
+            const uint32_t cnt = (uint32_t)__popcll(cmask);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(wm, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int wl = 31 - __clz((int)wm);
+            const uint32_t tot = __shfl_sync(wm, incl, wl);
+            uint32_t base = 0;
+            if (lane == wl && tot) base = atomicAdd(&s_list_n, tot);
+            base = __shfl_sync(wm, base, wl);
+            uint32_t at = base + incl - cnt;
             while (cmask && at < kSeedCap) {
                 const int b = __ffsll((long long)cmask) - 1;
                 cmask &= cmask - 1;
@@ -753,7 +783,7 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
 }
 
 template <int VEC>
-__global__ void __launch_bounds__(kBandThreads)
+__global__ void __launch_bounds__(kBandThreads, 2)
     stencil_band_kernel(ChainParams p, const uint16_t* __restrict__ raw,
                         uint32_t frame_base, CallOut out, BandConfig bc,
                         unsigned long long n_tiles) {
