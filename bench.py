@@ -444,7 +444,7 @@ def _serve_line(st, args, mix, link, clk):
     }
 
 
-COUNT_CONF = 0.999   # softmax confidence above which the network's count replaces the
+COUNT_CONF = 0.99    # softmax confidence above which the network's count replaces the
                      # classical one (offsets are replaced from 0.9)
 NET_FWD_FLOP = 25 * 32 * 9 * 2 + 25 * 32 * 288 * 2 + 64 * 800 * 2 + 7 * 64 * 2  # per hit
 

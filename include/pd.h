@@ -306,7 +306,10 @@ int pd_net_get_params(pd_net* net, float* params_host, uint32_t n_params);
 int pd_net_gather(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t frame_base,
                   const float* cm_dev, const pd_hit* hits_dev, uint32_t n_hits,
                   float* patches_dev, void* stream);
-/* Network outputs float [n][7] (5 logits, dx, dy) for n patches (device). */
+/* Network outputs float [n][7] (5 logits, dx, dy) for n patches (device),
+ * on the tcgen05 tensor cores (bf16 operands, f32 accumulation), in chunks
+ * of max_batch.  Synchronises `stream` at the end to report a timed-out
+ * tensor-core pipeline wait (PD_ETIMEDOUT). */
 int pd_net_forward(pd_net* net, const float* patches_dev, uint32_t n,
                    float* out_dev, void* stream);
 /* Loss (added to *loss_dev if not NULL) and the gradient of every

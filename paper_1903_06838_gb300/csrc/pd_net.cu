@@ -7,9 +7,10 @@
 // count and centre of mass of each hit from the 5x5 neighbourhood of its
 // seed: conv3x3x32 -> conv3x3x32 -> FC64 -> {5 count logits, (dx, dy)}.
 //
-// Every layer with a contraction runs as a GEMM on the tensor cores
-// (mma.sync m16n8k16, bfloat16 operands rounded to nearest even, float32
-// accumulation).  Convolutions are implicit GEMMs: operand loaders read the
+// Training runs every layer with a contraction as a GEMM on the tensor
+// cores (mma.sync m16n8k16, bfloat16 operands rounded to nearest even,
+// float32 accumulation); inference (pd_net_forward) runs on tcgen05 with
+// TMEM accumulators (pd_net_tc.cu), with the same operand rounding.  Convolutions are implicit GEMMs: operand loaders read the
 // 3x3 neighbourhood (zero padded) directly, so no im2col buffer exists.
 // Biases, ReLU, the loss and the optimiser are float32.  Layouts follow the
 // oracle (oracle/net.py): activations [hit][position 0..24][channel].
@@ -26,6 +27,7 @@
 
 #include "pd.h"
 #include "pd_internal.cuh"
+#include "pd_net_tc.cuh"
 
 namespace {
 
@@ -333,6 +335,10 @@ struct pd_net {
     float *x0 = nullptr, *h1 = nullptr, *h2 = nullptr, *h3 = nullptr, *out = nullptr;
     float *dout = nullptr, *dz3 = nullptr, *dz2 = nullptr, *dz1 = nullptr;
     uint64_t step = 0;
+    // tensor-core inference: bf16 weight image, bf16 h2, timeout flag
+    uint8_t* tc_img = nullptr;
+    uint16_t* tc_h2 = nullptr;
+    int* tc_err = nullptr;
 };
 
 namespace {
@@ -342,6 +348,9 @@ void free_net(pd_net* n) {
     for (float* p : {n->w, n->gw, n->m, n->v, n->x0, n->h1, n->h2, n->h3, n->out, n->dout,
                      n->dz3, n->dz2, n->dz1})
         cudaFree(p);
+    cudaFree(n->tc_img);
+    cudaFree(n->tc_h2);
+    cudaFree(n->tc_err);
     delete n;
 }
 
@@ -432,6 +441,13 @@ int pd_net_create(uint32_t max_batch, uint64_t seed, pd_net** out) {
             free_net(n);
             return net_fail(PD_ENOMEM, "pd_net_create: device allocation failed");
         }
+    if (cudaMalloc(&n->tc_img, pd::nettc::weight_image_bytes()) != cudaSuccess ||
+        cudaMalloc(&n->tc_h2, pd::nettc::h2_bytes(max_batch)) != cudaSuccess ||
+        cudaMalloc(&n->tc_err, sizeof(int)) != cudaSuccess ||
+        cudaMemset(n->tc_err, 0, sizeof(int)) != cudaSuccess) {
+        free_net(n);
+        return net_fail(PD_ENOMEM, "pd_net_create: device allocation failed");
+    }
     // weights and biases uniform in +-1/sqrt(fan_in), from a seeded generator
     std::vector<float> host(NPARAM, 0.0f);
     std::mt19937_64 rng(seed);
@@ -473,13 +489,25 @@ int pd_net_get_params(pd_net* n, float* host, uint32_t count) {
 int pd_net_forward(pd_net* n, const float* patches, uint32_t count, float* out_dev, void* stream) {
     if (!n || (count && (!patches || !out_dev))) return net_fail(PD_EINVAL, "pd_net_forward: args");
     cudaStream_t s = (cudaStream_t)stream;
+    const int sms = pd::device_sm_count();
     for (uint32_t done = 0; done < count;) {
         const uint32_t b = std::min(n->max_batch, count - done);
-        cudaError_t e = forward(n, patches + (size_t)done * NPOS, (int)b, s);
-        if (!e) e = cudaMemcpyAsync(out_dev + (size_t)done * NOUT, n->out, (size_t)b * NOUT * 4,
-                                    cudaMemcpyDeviceToDevice, s);
+        cudaError_t e = pd::nettc::forward(n->w, patches + (size_t)done * NPOS, b, n->tc_img,
+                                           n->tc_h2, out_dev + (size_t)done * NOUT, n->tc_err,
+                                           sms, s);
         if (e) return net_cuda(e, "pd_net_forward");
         done += b;
+    }
+    if (!count) return PD_OK;
+    // a timed-out wait inside the kernels is reported here (this synchronises
+    // the stream)
+    int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return net_cuda(e, "pd_net_forward");
+    if (flag) {
+        cudaMemsetAsync(n->tc_err, 0, sizeof(int), s);
+        return net_fail(PD_ETIMEDOUT, "pd_net_forward: tensor-core pipeline wait timed out");
     }
     return PD_OK;
 }

@@ -1,0 +1,565 @@
+// pd_net_tc.cu — inference of the learned count / offset network on the
+// fifth-generation tensor cores: tcgen05.mma with bfloat16 operands staged in
+// shared memory and float32 accumulators in tensor memory (TMEM).
+//
+// The network (conv3x3x32 -> conv3x3x32 -> FC64 -> 7 outputs on the 5x5
+// neighbourhood of a seed) is the learned refinement the paper proposes as
+// future work (abstract; sections "Methods", "Conclusions").  Numerics match
+// the training path: every contraction multiplies bfloat16-rounded operands
+// (weights, input patch, and the ReLU activations h1, h2, h3) and
+// accumulates in float32; biases and ReLU are float32.
+//
+//   conv_kernel  one CTA holds 64 hits: their patches, all of h1 (64 x 25 x
+//                32, bf16) and one 128-row im2col tile at a time.  conv1 and
+//                conv2 are implicit GEMMs whose rows are (position, hit)
+//                pairs: 13 tiles of 128 rows each (the last half full); a
+//                conv2 tile is 18 MMAs of 128x32x16.  Accumulators alternate
+//                between two 32-column TMEM buffers, so the epilogue of one
+//                tile (bias, ReLU, bf16, store of h2) runs while the next
+//                tile's MMAs execute.
+//   fc_kernel    FC3 on 128 hits per CTA: h2 streams in 160-column chunks
+//                (double-buffered) against W3 resident in shared memory;
+//                the epilogue adds b3, applies ReLU and computes the 7 heads
+//                (FC4) on the CUDA cores.
+//
+// Operand layout: the canonical no-swizzle K-major form: 8-row x 16-byte core
+// matrices, core matrix (r, k) of a tile with R rows at byte
+// ((k / 8) * (R / 8) + r / 8) * 128; descriptors carry the distance of
+// K-adjacent core matrices (leading) and of row-adjacent ones (stride).
+// Every wait on an mbarrier is bounded; a timeout sets an error flag.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "pd_net_tc.cuh"
+
+namespace pd {
+namespace nettc {
+
+namespace {
+
+constexpr int NPOS = 25, C1 = 32, C2 = 32, NH = 64, NOUT = 7;
+constexpr int K2 = 9 * C1;           // 288
+constexpr int K3 = NPOS * C2;        // 800
+constexpr int TB = 64;               // hits per conv tile
+constexpr int TF = 128;              // hits per fc tile
+constexpr int KCH = 160;             // fc K chunk
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+// weight offsets (floats) in the parameter vector, as the training path
+constexpr int OW1 = 0, OB1 = OW1 + C1 * 9, OW2 = OB1 + C1, OB2 = OW2 + C2 * K2, OW3 = OB2 + C2,
+              OB3 = OW3 + NH * K3, OW4 = OB3 + NH, OB4 = OW4 + NOUT * NH;
+
+// bf16 operand images of the weights (bytes)
+constexpr uint32_t W1_BYTES = 32 * 16 * 2, W2_BYTES = 32 * K2 * 2, W3_BYTES = NH * K3 * 2;
+constexpr uint32_t OFF_W1 = 0, OFF_W2 = OFF_W1 + W1_BYTES, OFF_W3 = OFF_W2 + W2_BYTES;
+
+__host__ __device__ __forceinline__ uint32_t cm_off(uint32_t r, uint32_t k, uint32_t rows) {
+    return ((k >> 3) * (rows >> 3) + (r >> 3)) * 128u + (r & 7u) * 16u + (k & 7u) * 2u;
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float v) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    return *reinterpret_cast<const uint16_t*>(&b);
+}
+__device__ __forceinline__ float bf16_round(float v) {
+    return __bfloat162float(__float2bfloat16_rn(v));
+}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+// kind::f16 instruction descriptor: f32 accumulate, bf16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__device__ __forceinline__ uint32_t idesc_bf16(uint32_t m, uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// bounded wait for the phase with parity `par`; false on timeout
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t par) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < kWaitLimit; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(a), "r"(par)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void bar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t cols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(dst)),
+                 "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t cols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// neighbour of position p at 3x3 offset k (k = 3 (dy + 1) + dx + 1), or -1
+__device__ __forceinline__ int nb(int p, int k) {
+    const int y = p / 5 + k / 3 - 1, x = p % 5 + k % 3 - 1;
+    return (y >= 0 && y < 5 && x >= 0 && x < 5) ? y * 5 + x : -1;
+}
+
+// ---------------------------------------------------------------------------
+// bf16 operand images of W1 (32 x 16, taps 9..15 zero), W2 (32 x 288) and
+// W3 (64 x 800), K-major core-matrix layout, from the float32 parameters.
+__global__ void prep_weights(const float* __restrict__ w, uint8_t* __restrict__ img) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 32 * 16) {
+        const int r = i / 16, k = i % 16;
+        *reinterpret_cast<uint16_t*>(img + OFF_W1 + cm_off(r, k, 32)) =
+            bf16_bits(k < 9 ? w[OW1 + r * 9 + k] : 0.0f);
+    }
+    if (i < 32 * K2) {
+        const int r = i / K2, k = i % K2;
+        *reinterpret_cast<uint16_t*>(img + OFF_W2 + cm_off(r, k, 32)) = bf16_bits(w[OW2 + i]);
+    }
+    if (i < NH * K3) {
+        const int r = i / K3, k = i % K3;
+        *reinterpret_cast<uint16_t*>(img + OFF_W3 + cm_off(r, k, NH)) = bf16_bits(w[OW3 + i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// conv1 + conv2 on tiles of 64 hits; h2 out as bf16 [n][800].
+//   conv1: the 13 im2col tiles (128 rows x 16 taps, 4 KB each) are built at
+//   once and their 13 MMAs issued back to back into 13 TMEM column blocks.
+//   conv2: an implicit GEMM read in place: h1 is kept per position as a
+//   64-hit x 32-channel K-major block (4 KB), so the contribution of tap k to
+//   position p is two 64x32x16 MMAs of block nb(p, k) against the W2 slice of
+//   tap k; taps outside the patch are skipped (zero padding costs nothing).
+//   Positions go in groups of 4 with two groups in flight in TMEM, so the
+//   epilogue of one group runs while the next group's MMAs execute.
+constexpr uint32_t CV_W2 = 0, CV_W1 = CV_W2 + W2_BYTES, CV_X0 = CV_W1 + W1_BYTES,
+                   CV_H1 = CV_X0 + TB * NPOS * 4, CV_A = CV_H1 + TB * NPOS * C1 * 2,
+                   CV_SMEM = CV_A + 13 * 4096;
+constexpr uint32_t kConvTmemCols = 512;  // 13 conv1 blocks of 32 columns
+constexpr int kGroup = 4;                // conv2 positions per TMEM group
+static_assert(CV_H1 % 128 == 0 && CV_A % 128 == 0, "alignment");
+static_assert(2 * kGroup * 32 <= (int)kConvTmemCols, "conv2 groups fit TMEM");
+
+__global__ void __launch_bounds__(256, 1)
+    conv_kernel(const float* __restrict__ x, int n, const float* __restrict__ w,
+                const uint8_t* __restrict__ img, uint16_t* __restrict__ h2, int* err) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar[3];  // 0: conv1, 1-2: conv2 K halves
+    __shared__ int s_nb[NPOS * 9];
+    // per position: its valid (tap, channel half) MMAs as descriptor address
+    // offsets (16-byte units): A block of the neighbour | W2 slice << 16
+    __shared__ uint32_t s_mma[NPOS * 18];
+    __shared__ int s_nmma[NPOS];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float* sx0 = reinterpret_cast<float*>(sm + CV_X0);
+    const uint32_t a_addr = smem_u32(sm + CV_A), w1_addr = smem_u32(sm + CV_W1),
+                   w2_addr = smem_u32(sm + CV_W2), h1_addr = smem_u32(sm + CV_H1);
+
+    if (warp == 0) tmem_alloc(&s_tmem, kConvTmemCols);
+    if (tid == 0)
+        for (int b = 0; b < 3; b++) bar_init(&s_bar[b]);
+    for (int i = tid; i < NPOS * 9; i += blockDim.x) s_nb[i] = nb(i / 9, i % 9);
+    if (tid < NPOS) {
+        int m = 0;
+        for (int k = 0; k < 9; k++) {
+            const int q = nb(tid, k);
+            if (q < 0) continue;
+            for (int kk = 0; kk < 2; kk++)
+                s_mma[tid * 18 + m++] =
+                    (uint32_t)((q * 4096 + kk * 2048) >> 4) |
+                    ((uint32_t)(((4 * k + 2 * kk) * 512) >> 4) << 16);
+        }
+        s_nmma[tid] = m;
+    }
+    for (uint32_t i = tid; i < W2_BYTES / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(sm + CV_W2)[i] = reinterpret_cast<const uint4*>(img + OFF_W2)[i];
+    for (uint32_t i = tid; i < W1_BYTES / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(sm + CV_W1)[i] = reinterpret_cast<const uint4*>(img + OFF_W1)[i];
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = s_tmem;
+    uint32_t par[3] = {0, 0, 0};
+    bool pend[3] = {false, false, false};
+    bool ok = true;
+    // every thread waits; __syncthreads_and makes the outcome uniform, and
+    // the phase advances only on success
+    auto waitp = [&](int b) -> bool {
+        const bool r = __syncthreads_and(wait_bar(&s_bar[b], par[b]));
+        if (r) {
+            par[b] ^= 1;
+            pend[b] = false;
+        }
+        return r;
+    };
+    const uint32_t id = idesc_bf16(128, 32);
+    const int n_tiles = (n + TB - 1) / TB;
+    const int half = warp >> 2;               // column half of the epilogue
+    const int erow = (warp & 3) * 32 + lane;  // TMEM lane = tile row
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    // this thread's conv1 im2col row and half of its 16 taps
+    const int brow = tid >> 1, bpart = tid & 1;
+
+    const uint32_t id64 = idesc_bf16(64, 32);
+    // conv2 MMAs of group g (positions kGroup*g ...) into TMEM half g & 1;
+    // issued by thread 0
+    const uint64_t a_desc0 = sdesc(h1_addr, 1024, 128), b_desc0 = sdesc(w2_addr, 512, 128);
+    auto issue_group = [&](int g) {
+        for (int i = 0; i < kGroup; i++) {
+            const int p = g * kGroup + i;
+            if (p >= NPOS) break;
+            const uint32_t d = tmem + (uint32_t)(((g & 1) * kGroup + i) * 32);
+            const int nm = s_nmma[p];
+            for (int e = 0; e < nm; e++) {
+                const uint32_t o = s_mma[p * 18 + e];
+                mma(d, a_desc0 + (o & 0xFFFFu), b_desc0 + (o >> 16), id64, e > 0);
+            }
+        }
+        commit(&s_bar[1 + (g & 1)]);
+    };
+    constexpr int NG = (NPOS + kGroup - 1) / kGroup;
+    // M = 64 accumulators: row r in TMEM lane (r / 16) * 32 + r % 16
+    const int qhit = (warp & 3) * 16 + lane;  // this lane's hit (lane < 16)
+
+    for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int hit0 = t * TB, nh = min(TB, n - hit0);
+        for (int e = tid; e < TB * NPOS; e += blockDim.x) {
+            const int hit = e / NPOS;
+            sx0[e] = hit < nh ? bf16_round(x[(size_t)hit0 * NPOS + e]) : 0.0f;
+        }
+        __syncthreads();
+        // ---- conv1: all 13 tiles of 128 (position, hit) rows at once -------
+        for (int j = 0; j < 13; j++) {
+            const int gr = j * 128 + brow, p = gr / TB, hit = gr % TB;
+            const int k0 = bpart * 8;
+            uint32_t v[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                uint16_t lo = 0, hi = 0;
+                const int ka = k0 + 2 * q, kb = ka + 1;
+                if (p < NPOS && ka < 9) {
+                    const int s2 = s_nb[p * 9 + ka];
+                    if (s2 >= 0) lo = bf16_bits(sx0[hit * NPOS + s2]);
+                }
+                if (p < NPOS && kb < 9) {
+                    const int s2 = s_nb[p * 9 + kb];
+                    if (s2 >= 0) hi = bf16_bits(sx0[hit * NPOS + s2]);
+                }
+                v[q] = (uint32_t)lo | ((uint32_t)hi << 16);
+            }
+            *reinterpret_cast<uint4*>(sm + CV_A + j * 4096 + cm_off(brow, k0, 128)) =
+                make_uint4(v[0], v[1], v[2], v[3]);
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (tid == 0) {
+            for (int j = 0; j < 13; j++)
+                mma(tmem + 32 * j, sdesc(a_addr + j * 4096, 16 * 128, 128),
+                    sdesc(w1_addr, 4 * 128, 128), id, 0);
+            commit(&s_bar[0]);
+        }
+        pend[0] = true;
+        ok = waitp(0);
+        if (!ok) break;
+        fence_after();
+        for (int j = 0; j < 13; j++) {
+            uint32_t r[16];
+            tmem_ld16(tmem + lane_base + 32 * j + half * 16, r);
+            const int gr = j * 128 + erow, p = gr / TB, hit = gr % TB;
+            if (p < NPOS) {
+                uint32_t pk[8];
+#pragma unroll
+                for (int c = 0; c < 16; c += 2) {
+                    const int ch = half * 16 + c;
+                    const float a0 = fmaxf(__uint_as_float(r[c]) + w[OB1 + ch], 0.0f);
+                    const float a1 = fmaxf(__uint_as_float(r[c + 1]) + w[OB1 + ch + 1], 0.0f);
+                    pk[c / 2] = (uint32_t)bf16_bits(a0) | ((uint32_t)bf16_bits(a1) << 16);
+                }
+                // h1 block of position p, K-major over 32 channels
+                uint8_t* blk = sm + CV_H1 + p * 4096;
+                *reinterpret_cast<uint4*>(blk + cm_off(hit, half * 16, TB)) =
+                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4*>(blk + cm_off(hit, half * 16 + 8, TB)) =
+                    make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+        }
+        fence_before();
+        __syncthreads();
+        // ---- conv2: implicit GEMM on h1 in place, groups of positions ----
+        fence_async_smem();  // h1 is read by the tensor cores
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (tid == 0) {
+            issue_group(0);
+            if (NG > 1) issue_group(1);
+        }
+        pend[1] = true;
+        pend[2] = NG > 1;
+        for (int g = 0; g < NG && ok; g++) {
+            ok = waitp(1 + (g & 1));
+            if (!ok) break;
+            fence_after();
+            for (int i = 0; i < kGroup; i++) {
+                const int p = g * kGroup + i;
+                if (p >= NPOS) break;
+                uint32_t r[16];
+                tmem_ld16(tmem + lane_base + (uint32_t)(((g & 1) * kGroup + i) * 32) + half * 16,
+                          r);
+                if (lane < 16 && qhit < nh) {
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int c = 0; c < 16; c += 2) {
+                        const int ch = half * 16 + c;
+                        const float a0 = fmaxf(__uint_as_float(r[c]) + w[OB2 + ch], 0.0f);
+                        const float a1 = fmaxf(__uint_as_float(r[c + 1]) + w[OB2 + ch + 1], 0.0f);
+                        pk[c / 2] = (uint32_t)bf16_bits(a0) | ((uint32_t)bf16_bits(a1) << 16);
+                    }
+                    uint4* dst = reinterpret_cast<uint4*>(h2 + (size_t)(hit0 + qhit) * K3 +
+                                                          p * C2 + half * 16);
+                    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                }
+            }
+            fence_before();
+            __syncthreads();
+            fence_after();
+            if (g + 2 < NG) {
+                if (tid == 0) issue_group(g + 2);
+                pend[1 + (g & 1)] = true;
+            }
+        }
+        if (!ok) break;
+        __syncthreads();  // h1, x0 and the A tiles are reused by the next tile
+    }
+    if (!ok && tid == 0) {
+        atomicExch(err, 1);
+        // MMAs may still be in flight: wait (bounded) for every outstanding
+        // commit before tensor memory is freed
+        for (int b = 0; b < 3; b++)
+            if (pend[b]) wait_bar(&s_bar[b], par[b]);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) tmem_free(tmem, kConvTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// FC3 + heads on tiles of 128 hits.
+constexpr uint32_t FC_W3 = 0, FC_A = FC_W3 + W3_BYTES, FC_ABUF = TF * KCH * 2,
+                   FC_PART = FC_A + 2 * FC_ABUF, FC_SMEM = FC_PART + 128 * 8 * 4;
+static_assert(FC_A % 128 == 0, "alignment");
+
+__global__ void __launch_bounds__(256, 1)
+    fc_kernel(const uint16_t* __restrict__ h2, int n, const float* __restrict__ w,
+              const uint8_t* __restrict__ img, float* __restrict__ out, int* err) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ float s_w4[NOUT * NH];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float* part = reinterpret_cast<float*>(sm + FC_PART);  // [128][8]
+    const uint32_t w3_addr = smem_u32(sm + FC_W3);
+
+    if (warp == 0) tmem_alloc(&s_tmem, 64);
+    if (tid == 0)
+        for (int b = 0; b < 2; b++) bar_init(&s_bar[b]);
+    for (uint32_t i = tid; i < W3_BYTES / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(sm + FC_W3)[i] = reinterpret_cast<const uint4*>(img + OFF_W3)[i];
+    for (int i = tid; i < NOUT * NH; i += blockDim.x) s_w4[i] = bf16_round(w[OW4 + i]);
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = s_tmem;
+    uint32_t par[2] = {0, 0};
+    bool pend[2] = {false, false};
+    bool ok = true;
+    auto waitp = [&](int b) -> bool {
+        const bool r = __syncthreads_and(wait_bar(&s_bar[b], par[b]));
+        if (r) {
+            par[b] ^= 1;
+            pend[b] = false;
+        }
+        return r;
+    };
+    const uint32_t id3 = idesc_bf16(128, NH);
+    const int n_tiles = (n + TF - 1) / TF;
+    const int half = warp >> 2;
+    const int erow = (warp & 3) * 32 + lane;
+
+    for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int hit0 = t * TF, nh = min(TF, n - hit0);
+        constexpr int NCH = K3 / KCH;  // 5 chunks of 10 MMAs
+        // chunk c of this tile into buffer c & 1 by asynchronous 16-byte
+        // copies (rows past the last hit are zero-filled)
+        auto load_chunk = [&](int c) {
+            const uint32_t abuf = smem_u32(sm + FC_A + (c & 1) * FC_ABUF);
+            for (int e = tid; e < TF * (KCH / 8); e += blockDim.x) {
+                const int r = e / (KCH / 8), kc = (e % (KCH / 8)) * 8;
+                const bool in = r < nh;
+                const uint16_t* src = h2 + (size_t)(hit0 + (in ? r : 0)) * K3 + c * KCH + kc;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(
+                                 abuf + cm_off(r, kc, TF)),
+                             "l"(src), "r"(in ? 16 : 0)
+                             : "memory");
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        };
+        load_chunk(0);
+        for (int c = 0; c < NCH && ok; c++) {
+            const int buf = c & 1;
+            if (c + 1 < NCH) {
+                if (c >= 1) {  // buffer (c + 1) & 1 was read by the MMAs of chunk c - 1
+                    ok = waitp((c + 1) & 1);
+                    if (!ok) break;
+                }
+                load_chunk(c + 1);
+                asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // chunk c landed
+            } else {
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            }
+            fence_async_smem();
+            fence_before();
+            __syncthreads();
+            fence_after();
+            if (tid == 0) {
+                const uint32_t a0 = smem_u32(sm + FC_A + buf * FC_ABUF);
+                for (int s = 0; s < KCH / 16; s++) {
+                    const int ks = c * (KCH / 16) + s;  // global K step
+                    mma(tmem, sdesc(a0 + s * 2 * (TF / 8) * 128, (TF / 8) * 128, 128),
+                        sdesc(w3_addr + ks * 2 * (NH / 8) * 128, (NH / 8) * 128, 128), id3,
+                        (c > 0 || s > 0) ? 1u : 0u);
+                }
+                commit(&s_bar[buf]);
+            }
+            pend[buf] = true;
+        }
+        if (!ok) {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            break;
+        }
+        // the last two chunks (buffers 1 and 0)
+        for (int c = NCH - 2; c < NCH && ok; c++) ok = waitp(c & 1);
+        if (!ok) break;
+        fence_after();
+        // epilogue: h3 = relu(acc + b3) rounded to bf16, heads on the CUDA
+        // cores; warps 4..7 take columns 32..63 and pass partial sums
+        uint32_t ra[16], rb[16];
+        const uint32_t tbase = tmem + ((uint32_t)((warp & 3) * 32) << 16) + half * 32;
+        tmem_ld16(tbase, ra);
+        tmem_ld16(tbase + 16, rb);
+        float acc[NOUT];
+#pragma unroll
+        for (int o = 0; o < NOUT; o++) acc[o] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 32; c++) {
+            const int ch = half * 32 + c;
+            const float z = __uint_as_float(c < 16 ? ra[c] : rb[c - 16]) + w[OB3 + ch];
+            const float h = bf16_round(fmaxf(z, 0.0f));
+#pragma unroll
+            for (int o = 0; o < NOUT; o++) acc[o] = __fmaf_rn(h, s_w4[o * NH + ch], acc[o]);
+        }
+        if (half == 1)
+#pragma unroll
+            for (int o = 0; o < NOUT; o++) part[erow * 8 + o] = acc[o];
+        fence_before();
+        __syncthreads();
+        if (half == 0 && erow < nh)
+#pragma unroll
+            for (int o = 0; o < NOUT; o++)
+                out[(size_t)(hit0 + erow) * NOUT + o] = acc[o] + part[erow * 8 + o] + w[OB4 + o];
+        __syncthreads();  // partial sums, A buffers and TMEM reused by the next tile
+    }
+    if (!ok && tid == 0) {
+        atomicExch(err, 1);
+        for (int b = 0; b < 2; b++)
+            if (pend[b]) wait_bar(&s_bar[b], par[b]);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) tmem_free(tmem, 64);
+}
+
+}  // namespace
+
+size_t weight_image_bytes() { return OFF_W3 + W3_BYTES; }
+size_t h2_bytes(uint32_t max_batch) { return (size_t)max_batch * K3 * 2; }
+
+cudaError_t forward(const float* w, const float* x, uint32_t n, uint8_t* img, uint16_t* h2,
+                    float* out, int* err, int sms, cudaStream_t s) {
+    if (!n) return cudaSuccess;
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(conv_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, CV_SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     FC_SMEM);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    prep_weights<<<(NH * K3 + 255) / 256, 256, 0, s>>>(w, img);
+    const int conv_tiles = (int)((n + TB - 1) / TB), fc_tiles = (int)((n + TF - 1) / TF);
+    conv_kernel<<<std::min(conv_tiles, sms), 256, CV_SMEM, s>>>(x, (int)n, w, img, h2, err);
+    fc_kernel<<<std::min(fc_tiles, sms), 256, FC_SMEM, s>>>(h2, (int)n, w, img, out, err);
+    return cudaGetLastError();
+}
+
+}  // namespace nettc
+}  // namespace pd

@@ -21,7 +21,7 @@ _INCLUDE = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_PKG, "libpd.so")
 SOURCES = ["pd_api.cu", "pd_chain.cu", "pd_fast.cu", "pd_fused.cu", "pd_noalloc.cu",
-           "pd_net.cu", "pd_serve.cu"]
+           "pd_net.cu", "pd_net_tc.cu", "pd_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
