@@ -79,13 +79,16 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 __device__ __forceinline__ uint32_t idesc_bf16(uint32_t m, uint32_t n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
 }
+// (volatile keeps tcgen05 operations in program order; shared-memory
+// operands are published before the issue by fences and a barrier, so no
+// memory clobber is needed and the issuing thread's table loads can run
+// ahead)
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                     uint32_t acc) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void commit(uint64_t* bar) {
     asm volatile(
@@ -177,22 +180,23 @@ __global__ void prep_weights(const float* __restrict__ w, uint8_t* __restrict__ 
 //   64-hit x 32-channel K-major block (4 KB), so the contribution of tap k to
 //   position p is two 64x32x16 MMAs of block nb(p, k) against the W2 slice of
 //   tap k; taps outside the patch are skipped (zero padding costs nothing).
-//   Positions go in groups of 4 with two groups in flight in TMEM, so the
-//   epilogue of one group runs while the next group's MMAs execute.
+//   Positions go in groups of 4 with three groups in flight in TMEM, so the
+//   epilogue of one group runs while the next two groups' MMAs execute.
 constexpr uint32_t CV_W2 = 0, CV_W1 = CV_W2 + W2_BYTES, CV_X0 = CV_W1 + W1_BYTES,
                    CV_H1 = CV_X0 + TB * NPOS * 4, CV_A = CV_H1 + TB * NPOS * C1 * 2,
                    CV_SMEM = CV_A + 13 * 4096;
 constexpr uint32_t kConvTmemCols = 512;  // 13 conv1 blocks of 32 columns
 constexpr int kGroup = 4;                // conv2 positions per TMEM group
+constexpr int kGroupBufs = 3;            // conv2 groups in flight
 static_assert(CV_H1 % 128 == 0 && CV_A % 128 == 0, "alignment");
-static_assert(2 * kGroup * 32 <= (int)kConvTmemCols, "conv2 groups fit TMEM");
+static_assert(kGroupBufs * kGroup * 32 <= (int)kConvTmemCols, "conv2 groups fit TMEM");
 
 __global__ void __launch_bounds__(256, 1)
     conv_kernel(const float* __restrict__ x, int n, const float* __restrict__ w,
                 const uint8_t* __restrict__ img, uint16_t* __restrict__ h2, int* err) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_bar[3];  // 0: conv1, 1-2: conv2 K halves
+    __shared__ __align__(8) uint64_t s_bar[1 + kGroupBufs];  // 0: conv1, then conv2 groups
     __shared__ int s_nb[NPOS * 9];
     // per position: its valid (tap, channel half) MMAs as descriptor address
     // offsets (16-byte units): A block of the neighbour | W2 slice << 16
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(256, 1)
 
     if (warp == 0) tmem_alloc(&s_tmem, kConvTmemCols);
     if (tid == 0)
-        for (int b = 0; b < 3; b++) bar_init(&s_bar[b]);
+        for (int b = 0; b < 1 + kGroupBufs; b++) bar_init(&s_bar[b]);
     for (int i = tid; i < NPOS * 9; i += blockDim.x) s_nb[i] = nb(i / 9, i % 9);
     if (tid < NPOS) {
         int m = 0;
@@ -228,8 +232,8 @@ __global__ void __launch_bounds__(256, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = s_tmem;
-    uint32_t par[3] = {0, 0, 0};
-    bool pend[3] = {false, false, false};
+    uint32_t par[1 + kGroupBufs] = {};
+    bool pend[1 + kGroupBufs] = {};
     bool ok = true;
     // every thread waits; __syncthreads_and makes the outcome uniform, and
     // the phase advances only on success
@@ -246,25 +250,26 @@ __global__ void __launch_bounds__(256, 1)
     const int half = warp >> 2;               // column half of the epilogue
     const int erow = (warp & 3) * 32 + lane;  // TMEM lane = tile row
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    // this thread's conv1 im2col row and half of its 16 taps
-    const int brow = tid >> 1, bpart = tid & 1;
 
     const uint32_t id64 = idesc_bf16(64, 32);
-    // conv2 MMAs of group g (positions kGroup*g ...) into TMEM half g & 1;
+    // conv2 MMAs of group g (positions kGroup*g ...) into TMEM group buffer
+    // g % kGroupBufs;
     // issued by thread 0
     const uint64_t a_desc0 = sdesc(h1_addr, 1024, 128), b_desc0 = sdesc(w2_addr, 512, 128);
     auto issue_group = [&](int g) {
         for (int i = 0; i < kGroup; i++) {
             const int p = g * kGroup + i;
             if (p >= NPOS) break;
-            const uint32_t d = tmem + (uint32_t)(((g & 1) * kGroup + i) * 32);
+            const uint32_t d = tmem + (uint32_t)(((g % kGroupBufs) * kGroup + i) * 32);
             const int nm = s_nmma[p];
-            for (int e = 0; e < nm; e++) {
-                const uint32_t o = s_mma[p * 18 + e];
-                mma(d, a_desc0 + (o & 0xFFFFu), b_desc0 + (o >> 16), id64, e > 0);
-            }
+            uint32_t o[18];
+#pragma unroll
+            for (int e = 0; e < 18; e++) o[e] = s_mma[p * 18 + e];  // table loads first
+#pragma unroll
+            for (int e = 0; e < 18; e++)
+                if (e < nm) mma(d, a_desc0 + (o[e] & 0xFFFFu), b_desc0 + (o[e] >> 16), id64, e > 0);
         }
-        commit(&s_bar[1 + (g & 1)]);
+        commit(&s_bar[1 + g % kGroupBufs]);
     };
     constexpr int NG = (NPOS + kGroup - 1) / kGroup;
     // M = 64 accumulators: row r in TMEM lane (r / 16) * 32 + r % 16
@@ -278,26 +283,24 @@ __global__ void __launch_bounds__(256, 1)
         }
         __syncthreads();
         // ---- conv1: all 13 tiles of 128 (position, hit) rows at once -------
-        for (int j = 0; j < 13; j++) {
-            const int gr = j * 128 + brow, p = gr / TB, hit = gr % TB;
-            const int k0 = bpart * 8;
-            uint32_t v[4];
+        // row p * 64 + hit of the im2col: the 9 taps of x0 around p (zero
+        // outside the patch), then 7 zero columns; rows 1600..1663 are zero
+        for (int e = tid; e < 13 * 128; e += blockDim.x) {
+            const int p = e >> 6, hit = e & 63;
+            uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (p < NPOS) {
+                const float* xr = sx0 + hit * NPOS;
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                uint16_t lo = 0, hi = 0;
-                const int ka = k0 + 2 * q, kb = ka + 1;
-                if (p < NPOS && ka < 9) {
-                    const int s2 = s_nb[p * 9 + ka];
-                    if (s2 >= 0) lo = bf16_bits(sx0[hit * NPOS + s2]);
+                for (int k = 0; k < 9; k++) {
+                    const int q = s_nb[p * 9 + k];
+                    const uint32_t b16 = q >= 0 ? (uint32_t)bf16_bits(xr[q]) : 0u;
+                    v[k >> 1] |= b16 << ((k & 1) * 16);
                 }
-                if (p < NPOS && kb < 9) {
-                    const int s2 = s_nb[p * 9 + kb];
-                    if (s2 >= 0) hi = bf16_bits(sx0[hit * NPOS + s2]);
-                }
-                v[q] = (uint32_t)lo | ((uint32_t)hi << 16);
             }
-            *reinterpret_cast<uint4*>(sm + CV_A + j * 4096 + cm_off(brow, k0, 128)) =
-                make_uint4(v[0], v[1], v[2], v[3]);
+            const int j = e >> 7, r = e & 127;
+            uint8_t* tile = sm + CV_A + j * 4096;
+            *reinterpret_cast<uint4*>(tile + cm_off(r, 0, 128)) = make_uint4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<uint4*>(tile + cm_off(r, 8, 128)) = make_uint4(v[4], v[5], v[6], v[7]);
         }
         fence_async_smem();
         fence_before();
@@ -341,21 +344,19 @@ __global__ void __launch_bounds__(256, 1)
         fence_before();
         __syncthreads();
         fence_after();
-        if (tid == 0) {
-            issue_group(0);
-            if (NG > 1) issue_group(1);
-        }
-        pend[1] = true;
-        pend[2] = NG > 1;
+        if (tid == 0)
+            for (int g = 0; g < kGroupBufs && g < NG; g++) issue_group(g);
+        for (int g = 0; g < kGroupBufs && g < NG; g++) pend[1 + g] = true;
         for (int g = 0; g < NG && ok; g++) {
-            ok = waitp(1 + (g & 1));
+            ok = waitp(1 + g % kGroupBufs);
             if (!ok) break;
             fence_after();
             for (int i = 0; i < kGroup; i++) {
                 const int p = g * kGroup + i;
                 if (p >= NPOS) break;
                 uint32_t r[16];
-                tmem_ld16(tmem + lane_base + (uint32_t)(((g & 1) * kGroup + i) * 32) + half * 16,
+                tmem_ld16(tmem + lane_base + (uint32_t)(((g % kGroupBufs) * kGroup + i) * 32) +
+                              half * 16,
                           r);
                 if (lane < 16 && qhit < nh) {
                     uint32_t pk[8];
@@ -375,9 +376,9 @@ __global__ void __launch_bounds__(256, 1)
             fence_before();
             __syncthreads();
             fence_after();
-            if (g + 2 < NG) {
-                if (tid == 0) issue_group(g + 2);
-                pend[1 + (g & 1)] = true;
+            if (g + kGroupBufs < NG) {
+                if (tid == 0) issue_group(g + kGroupBufs);
+                pend[1 + g % kGroupBufs] = true;
             }
         }
         if (!ok) break;
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(256, 1)
         atomicExch(err, 1);
         // MMAs may still be in flight: wait (bounded) for every outstanding
         // commit before tensor memory is freed
-        for (int b = 0; b < 3; b++)
+        for (int b = 0; b < 1 + kGroupBufs; b++)
             if (pend[b]) wait_bar(&s_bar[b], par[b]);
     }
     fence_before();
