@@ -244,13 +244,17 @@ int pd_set_tuning(pd_ctx* ctx, const pd_tuning* tuning);
 int pd_autotune(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frames,
                 pd_tuning* best, float* best_us_per_frame);
 
-/* Batched launches over contexts of different geometries.  One batch runs
- * the common mode of every (item, frame, unit) in one persistent kernel and
- * every stencil tile of every item in a second one, so frames of several
- * detectors share two launches.  Each item is processed exactly as
- * pd_process would (same results; summaries go to the item's context).
- * Items must use the band stencil (every geometry with at most 2048
- * columns per module); PD_ENOTSUP otherwise. */
+/* Batched launches over contexts of different geometries.  The frames of
+ * all items are split into chunks of about 96 MB of raw data (a chunk may
+ * hold frames of several items), so a chunk's second pass re-reads its raw
+ * frames from L2.  By default each chunk runs the kernels pd_process uses,
+ * item by item; with pd_batch_set_mixed(batch, 1) each chunk is one
+ * persistent common-mode launch over every (item, frame, unit) of the chunk
+ * and one persistent stencil launch over all its band tiles (items must
+ * then use the band stencil: every geometry with at most 2048 columns per
+ * module; PD_ENOTSUP otherwise).  Either way each item is processed exactly
+ * as pd_process would (same results; summaries go to the item's context),
+ * and a batch can be captured once as a CUDA graph and replayed. */
 typedef struct {
     pd_ctx* ctx;
     const uint16_t* frames;  /* device, 16-byte aligned                     */
@@ -265,6 +269,8 @@ typedef struct pd_batch pd_batch;
 /* Allocates the device item table (max_items) and a common-mode scratch of
  * max_cm_values floats for items that pass out.cm == NULL. */
 int pd_batch_create(uint32_t max_items, uint64_t max_cm_values, pd_batch** out);
+/* mixed != 0: the persistent mixed-geometry launches (see above). */
+int pd_batch_set_mixed(pd_batch* batch, int mixed);
 /* Enqueue a batch on `stream` (asynchronous). */
 int pd_batch_process(pd_batch* batch, const pd_batch_item* items, uint32_t n_items,
                      void* stream);

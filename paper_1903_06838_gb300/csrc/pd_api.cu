@@ -683,6 +683,8 @@ int pd_read_profile(pd_ctx* c, pd_profile* out) {
 struct pd_batch {
     uint32_t max_items = 0;
     uint64_t max_cm = 0;
+    uint32_t table_cap[2] = {0, 0};                  // entries of each table
+    uint32_t mixed = 0;  // 1: persistent kernels over all geometries of a chunk
     pd::BatchItem* d_table[2] = {nullptr, nullptr};  // [0] direct calls, [1] graph
     pd::BatchItem* h_table[2] = {nullptr, nullptr};  // page-locked staging
     cudaEvent_t copied = nullptr;                    // staging [0] free again
@@ -705,26 +707,119 @@ void free_batch(pd_batch* b) {
     delete b;
 }
 
+// The frames of a batch go in chunks of about this many raw bytes, one
+// common-mode + stencil launch pair each, so the stencil re-reads a chunk's
+// raw frames from L2 (the chunk interleaves the items' geometries).
+constexpr size_t kBatchChunkBytes = 96u << 20;
+
+struct Piece {
+    uint32_t item, first, count;
+};
+
+// Greedy split of the items' frames into chunks of about kBatchChunkBytes.
+std::vector<std::vector<Piece>> plan_chunks(const pd_batch_item* items, uint32_t n) {
+    std::vector<std::vector<Piece>> chunks;
+    std::vector<Piece> cur;
+    size_t cur_bytes = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        const size_t fb = (size_t)items[i].ctx->params.frame_px * 2;
+        uint32_t f = 0;
+        while (f < items[i].n_frames) {
+            size_t room = kBatchChunkBytes > cur_bytes ? kBatchChunkBytes - cur_bytes : 0;
+            uint32_t take = (uint32_t)std::min<size_t>(room / fb, items[i].n_frames - f);
+            if (take == 0) {
+                if (cur.empty()) {
+                    take = 1;  // a frame larger than a chunk
+                } else {
+                    chunks.push_back(cur);
+                    cur.clear();
+                    cur_bytes = 0;
+                    continue;
+                }
+            }
+            cur.push_back({i, f, take});
+            cur_bytes += take * fb;
+            f += take;
+            if (cur_bytes >= kBatchChunkBytes) {
+                chunks.push_back(cur);
+                cur.clear();
+                cur_bytes = 0;
+            }
+        }
+    }
+    if (!cur.empty()) chunks.push_back(cur);
+    return chunks;
+}
+
+size_t plan_entries(const std::vector<std::vector<Piece>>& chunks) {
+    size_t t = 0;
+    for (const auto& c : chunks) t += c.size();
+    return t;
+}
+
+// Table slot with room for `entries` sub-items (frees the old one; cudaFree
+// waits for work that may still read it).
+int ensure_table(pd_batch* b, int slot, size_t entries) {
+    if (entries <= b->table_cap[slot]) return PD_OK;
+    cudaFree(b->d_table[slot]);
+    cudaFreeHost(b->h_table[slot]);
+    b->d_table[slot] = nullptr;
+    b->h_table[slot] = nullptr;
+    b->table_cap[slot] = 0;
+    if (cudaMalloc(&b->d_table[slot], entries * sizeof(pd::BatchItem)) != cudaSuccess ||
+        cudaMallocHost(&b->h_table[slot], entries * sizeof(pd::BatchItem)) != cudaSuccess)
+        return fail(PD_ENOMEM, "batch table allocation failed");
+    b->table_cap[slot] = (uint32_t)entries;
+    return PD_OK;
+}
+
+int batch_check_items(const pd_batch* b, const pd_batch_item* items, uint32_t n) {
+    if (!items || n == 0 || n > b->max_items) return fail(PD_EINVAL, "batch: 1..max_items items");
+    for (uint32_t i = 0; i < n; i++) {
+        const pd_batch_item& it = items[i];
+        const char* why = nullptr;
+        int rc = pd::internal_check_process_args(it.ctx, it.frames, it.n_frames, &it.out, &why);
+        if (rc) return fail(rc, why);
+        if (b->mixed && !it.ctx->use_band)
+            return fail(PD_ENOTSUP, "batch: the mixed launch needs the band stencil");
+    }
+    return PD_OK;
+}
+
+// The launches pd_process makes for `nf` frames of one context (the
+// one-kernel chain, or the common-mode + stencil pair), without zeroing
+// the hit counter.
+cudaError_t launch_chain_piece(pd_ctx* c, const uint16_t* fr, uint32_t nf, uint32_t frame_base,
+                               const pd::CallOut& co, cudaStream_t s) {
+    if (c->use_fused && !c->two_pass)
+        return pd::launch_fused(c->params, c->fused_cfg, fr, nf, frame_base, co, s);
+    cudaError_t e = c->use_cm_big    ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, co.cm, s)
+                    : c->use_cm_rows ? pd::launch_cm_rows(c->params, fr, nf, co.cm, s)
+                                     : pd::launch_cm_select(c->params, fr, nf, co.cm, s);
+    if (e != cudaSuccess) return e;
+    return c->use_band ? pd::launch_stencil_band(c->params, c->band_cfg, fr, nf, frame_base, co, s)
+                       : pd::launch_stencil(c->params, fr, nf, frame_base, co, s);
+}
+
 int batch_enqueue(pd_batch* b, int slot, const pd_batch_item* items, uint32_t n,
                   cudaStream_t s) {
-    if (!items || n == 0 || n > b->max_items) return fail(PD_EINVAL, "batch: 1..max_items items");
+    int rc = batch_check_items(b, items, n);
+    if (rc) return rc;
     if (slot == 0 && b->copy_pending) {
         cudaError_t e = cudaEventSynchronize(b->copied);
         if (e != cudaSuccess) return fail_cuda(e, "batch staging wait");
         b->copy_pending = false;
     }
-    pd::BatchItem* h = b->h_table[slot];
-    unsigned long long cm_tasks = 0, tiles = 0;
+    // per item: kernel configuration and its common-mode destination
+    std::vector<pd::BatchItem> base(n);
+    std::vector<float*> item_cm(n);
     uint64_t cm_used = 0;
     size_t cm_smem = 0, band_smem = 0;
     for (uint32_t i = 0; i < n; i++) {
         const pd_batch_item& it = items[i];
         pd_ctx* c = it.ctx;
-        const char* why = nullptr;
-        int rc = pd::internal_check_process_args(c, it.frames, it.n_frames, &it.out, &why);
-        if (rc) return fail(rc, why);
-        if (!c->use_band) return fail(PD_ENOTSUP, "batch: geometry needs the band stencil");
-        pd::BatchItem& d = h[i];
+        pd::BatchItem& d = base[i];
+        d = pd::BatchItem{};
         d.p = c->params;
         d.cm_cfg = c->cm_cfg;
         d.band_cfg = c->band_cfg;
@@ -744,9 +839,6 @@ int batch_enqueue(pd_batch* b, int slot, const pd_batch_item* items, uint32_t n,
         d.band_vec = c->band_cfg.vec;
         band_smem = std::max(band_smem, pd::band_smem_bytes(c->params, c->band_cfg.rb,
                                                             c->band_cfg.pitch));
-        d.raw = it.frames;
-        d.n_frames = it.n_frames;
-        d.frame_base = it.frame_base;
         const uint64_t ncm = (uint64_t)it.n_frames * c->params.units_per_frame;
         float* cm = it.out.cm;
         if (!cm) {
@@ -754,25 +846,74 @@ int batch_enqueue(pd_batch* b, int slot, const pd_batch_item* items, uint32_t n,
             cm = b->d_cm + cm_used;
             cm_used += ncm;
         }
-        d.out = pd::CallOut{it.out.hits, it.out.hit_capacity, it.out.n_hits, it.out.corrected, cm};
-        d.cm_first = cm_tasks;
-        d.st_first = tiles;
-        d.st_tiles = (unsigned long long)it.n_frames * c->params.n_modules * c->band_cfg.n_bands;
-        cm_tasks += d.cm_kind == 4 ? (ncm + 15) / 16 : ncm;
-        tiles += d.st_tiles;
+        item_cm[i] = cm;
     }
-    cudaError_t e = cudaMemcpyAsync(b->d_table[slot], h, n * sizeof(pd::BatchItem),
-                                    cudaMemcpyHostToDevice, s);
+    const auto chunks = plan_chunks(items, n);
+    const size_t entries = plan_entries(chunks);
+    if (entries > b->table_cap[slot]) {
+        if (slot == 1) return fail(PD_EINVAL, "batch: table not sized before capture");
+        if ((rc = ensure_table(b, slot, entries))) return rc;
+    }
+    pd::BatchItem* h = b->h_table[slot];
+    struct Launch {
+        size_t first;
+        uint32_t count;
+        unsigned long long cm_tasks;
+    };
+    std::vector<Launch> launches;
+    size_t at = 0;
+    for (const auto& ch : chunks) {
+        Launch L{at, (uint32_t)ch.size(), 0};
+        unsigned long long tiles = 0;
+        for (const Piece& pc : ch) {
+            const pd_batch_item& it = items[pc.item];
+            const pd::ChainParams& cp = it.ctx->params;
+            pd::BatchItem& d = h[at++];
+            d = base[pc.item];
+            d.raw = it.frames + (size_t)pc.first * cp.frame_px;
+            d.n_frames = pc.count;
+            d.frame_base = it.frame_base + pc.first;
+            const uint64_t ncm = (uint64_t)pc.count * cp.units_per_frame;
+            d.out = pd::CallOut{it.out.hits, it.out.hit_capacity, it.out.n_hits,
+                                it.out.corrected ? it.out.corrected + (size_t)pc.first * cp.frame_px
+                                                 : nullptr,
+                                item_cm[pc.item] + (size_t)pc.first * cp.units_per_frame};
+            d.cm_first = L.cm_tasks;
+            d.st_first = tiles;
+            d.st_tiles = (unsigned long long)pc.count * cp.n_modules * d.band_cfg.n_bands;
+            L.cm_tasks += d.cm_kind == 4 ? (ncm + 15) / 16 : ncm;
+            tiles += d.st_tiles;
+        }
+        launches.push_back(L);
+    }
+    cudaError_t e;
+    for (uint32_t i = 0; i < n; i++)
+        if ((e = cudaMemsetAsync(items[i].out.n_hits, 0, sizeof(uint32_t), s)))
+            return fail_cuda(e, "zero n_hits");
+    if (!b->mixed) {
+        // per chunk, each piece through the kernels pd_process uses
+        size_t k = 0;
+        for (const auto& ch : chunks)
+            for (const Piece& pc : ch) {
+                const pd::BatchItem& d = h[k++];
+                if ((e = launch_chain_piece(items[pc.item].ctx, d.raw, d.n_frames, d.frame_base,
+                                            d.out, s)))
+                    return fail_cuda(e, "batch kernel launch");
+            }
+        return PD_OK;
+    }
+    e = cudaMemcpyAsync(b->d_table[slot], h, entries * sizeof(pd::BatchItem),
+                        cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail_cuda(e, "batch table upload");
     if (slot == 0) {
         if ((e = cudaEventRecord(b->copied, s))) return fail_cuda(e, "batch event");
         b->copy_pending = true;
     }
-    for (uint32_t i = 0; i < n; i++)
-        if ((e = cudaMemsetAsync(items[i].out.n_hits, 0, sizeof(uint32_t), s)))
-            return fail_cuda(e, "zero n_hits");
-    e = pd::launch_batch(b->d_table[slot], n, cm_tasks, cm_smem, band_smem, s);
-    if (e != cudaSuccess) return fail_cuda(e, "batch kernel launch");
+    for (const Launch& L : launches) {
+        e = pd::launch_batch(b->d_table[slot] + L.first, L.count, L.cm_tasks, cm_smem, band_smem,
+                             s);
+        if (e != cudaSuccess) return fail_cuda(e, "batch kernel launch");
+    }
     return PD_OK;
 }
 
@@ -786,13 +927,11 @@ int pd_batch_create(uint32_t max_items, uint64_t max_cm_values, pd_batch** out) 
     b->max_items = max_items;
     b->max_cm = max_cm_values;
     cudaError_t e;
-    for (int i = 0; i < 2; i++) {
-        if ((e = cudaMalloc(&b->d_table[i], max_items * sizeof(pd::BatchItem))) ||
-            (e = cudaMallocHost(&b->h_table[i], max_items * sizeof(pd::BatchItem)))) {
+    for (int i = 0; i < 2; i++)
+        if (ensure_table(b, i, max_items) != PD_OK) {
             free_batch(b);
-            return fail(PD_ENOMEM, "batch table allocation failed");
+            return PD_ENOMEM;
         }
-    }
     if (max_cm_values && (e = cudaMalloc(&b->d_cm, max_cm_values * sizeof(float)))) {
         free_batch(b);
         return fail(PD_ENOMEM, "batch scratch allocation failed");
@@ -811,6 +950,12 @@ int pd_batch_create(uint32_t max_items, uint64_t max_cm_values, pd_batch** out) 
     return PD_OK;
 }
 
+int pd_batch_set_mixed(pd_batch* b, int mixed) {
+    if (!b) return fail(PD_EINVAL, "NULL batch");
+    b->mixed = mixed ? 1u : 0u;
+    return PD_OK;
+}
+
 int pd_batch_process(pd_batch* b, const pd_batch_item* items, uint32_t n_items, void* stream) {
     if (!b) return fail(PD_EINVAL, "NULL batch");
     return batch_enqueue(b, 0, items, n_items, (cudaStream_t)stream);
@@ -825,6 +970,10 @@ int pd_batch_capture(pd_batch* b, const pd_batch_item* items, uint32_t n_items, 
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
     }
+    // the table is sized before the capture (no allocation while capturing)
+    int rc0 = batch_check_items(b, items, n_items);
+    if (rc0) return rc0;
+    if ((rc0 = ensure_table(b, 1, plan_entries(plan_chunks(items, n_items))))) return rc0;
     if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)))
         return fail_cuda(e, "begin capture");
     int rc = batch_enqueue(b, 1, items, n_items, s);

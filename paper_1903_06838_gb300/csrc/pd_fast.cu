@@ -43,6 +43,7 @@
 #define PD_BAND_UNROLL 2
 #endif
 
+
 namespace pd {
 
 namespace {

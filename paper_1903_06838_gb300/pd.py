@@ -170,6 +170,7 @@ def _declare(lib):
         "pd_batch_process": ([vp, ctypes.POINTER(PdBatchItem), u32, vp], i32),
         "pd_batch_capture": ([vp, ctypes.POINTER(PdBatchItem), u32, vp], i32),
         "pd_batch_replay": ([vp, vp], i32),
+        "pd_batch_set_mixed": ([vp, i32], i32),
         "pd_batch_destroy": ([vp], None),
         "pd_server_create": ([ctypes.POINTER(vp), u32, ctypes.POINTER(PdServeConfig),
                               ctypes.POINTER(vp)], i32),
@@ -474,6 +475,10 @@ def pd_batch_capture(batch: Batch, items, stream) -> None:
     batch._keep = arr
     _check(load().pd_batch_capture(batch.handle, arr, len(items), _stream_handle(stream)),
            "pd_batch_capture")
+
+
+def pd_batch_set_mixed(batch: Batch, mixed: bool) -> None:
+    _check(load().pd_batch_set_mixed(batch.handle, int(bool(mixed))), "pd_batch_set_mixed")
 
 
 def pd_batch_replay(batch: Batch, stream=None) -> None:

@@ -64,7 +64,8 @@ def _check(ctxs, outs, ref):
             np.testing.assert_array_equal(a, b)
 
 
-def test_batch_equals_single_context_processing_and_oracle():
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batch_equals_single_context_processing_and_oracle(mixed):
     data = _setup()
     ref = _individual(data)
     # the single-context path itself against the oracle on the mix
@@ -77,18 +78,21 @@ def test_batch_equals_single_context_processing_and_oracle():
     devs = [pd.frames_to_device(raw) for *_, raw in data]
     outs = _outputs(ctxs, data)
     batch = pd.pd_batch_create(8)
+    pd.pd_batch_set_mixed(batch, mixed)
     pd.pd_batch_process(batch, [(c, d.data_ptr(), len(r[3]), 0, o)
                                 for c, d, r, o in zip(ctxs, devs, data, outs)])
     torch.cuda.synchronize()
     _check(ctxs, outs, ref)
 
 
-def test_batch_graph_replays_on_new_frame_contents():
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batch_graph_replays_on_new_frame_contents(mixed):
     data = _setup()
     ctxs = _ctxs(data)
     devs = [pd.frames_to_device(raw) for *_, raw in data]
     outs = _outputs(ctxs, data)
     batch = pd.pd_batch_create(8)
+    pd.pd_batch_set_mixed(batch, mixed)
     stream = torch.cuda.Stream()
     items = [(c, d.data_ptr(), len(r[3]), 0, o) for c, d, r, o in zip(ctxs, devs, data, outs)]
     with torch.cuda.stream(stream):
