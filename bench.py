@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-net", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--only", choices=["serve", "batch", "net"], default=None,
+                    help="run one section alone (for profiling) and print its JSON")
     ap.add_argument("--serve-rate", type=float, default=100000.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     return ap.parse_args()
@@ -680,8 +682,27 @@ def batch_mix_run(args, dev, peak):
     return res
 
 
+def run_only(args):
+    import torch
+    from paper_1903_06838_gb300 import pd
+    pd.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    peak, _ = read_peaks()
+    if args.only == "serve":
+        res = serve_run(args, dev)
+    elif args.only == "batch":
+        res = {"single_asic_16": single_asic_run(args, dev),
+               "batch_mix_4096": batch_mix_run(args, dev, peak)}
+    else:
+        res = net_run(args, dev, read_peaks_all())
+    print(json.dumps({"only": args.only, **({"result": res})}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.only:
+        return run_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_pd(args)
