@@ -331,3 +331,21 @@ def test_results_independent_of_tuning(tuning):
     torch.cuda.synchronize()
     ref = _oracle(geom, thr, ped, gain, raw, want_corrected=True)
     _compare(ctx, out, ref, 11)
+
+
+@pytest.mark.parametrize("bins", [1, 4096])
+def test_histogram_bin_count_extremes(bins):
+    """One bin (every value clipped into it) and the maximum PD_MAX_HIST_BINS."""
+    det = synth.cspad_2p2m(n_modules=2, occupancy=0.02)
+    thr = dict(det.thresholds(), hist_bins=bins, hist_bin_kev=0.02 if bins > 1 else 1.0)
+    assert bins <= pd.PD_MAX_HIST_BINS
+    _run_case(det, 2, thr_over=thr)
+
+
+def test_widest_module_band_stencil():
+    """2048 columns per module (the widest the band stencil takes), row units
+    of 512 pixels (the largest the row kernel takes)."""
+    det = synth.Detector(n_modules=1, rows=12, cols=2048, unit_rows=1, unit_cols=512,
+                         occupancy=0.02)
+    ref = _run_case(det, 2)
+    assert ref.n_hits > 0
