@@ -466,7 +466,7 @@ def net_run(args, dev, peaks):
 
     det = synth.asic_352x384(occupancy=0.005, occupancy_hi=0.05, cloud_sigma=0.2,
                              cloud_sigma_hi=0.5, seed=31)
-    _, ptr, _, lab_tr = learn.make_set(det, 40, 0)
+    hits_tr, ptr, _, lab_tr = learn.make_set(det, 40, 0)
     hits_te, pte, (c_te, t_te, m_te), _ = learn.make_set(det, 12, 1000)
     batch = 4096
     net = pd.pd_net_create(1 << 16, seed=7)
@@ -530,6 +530,12 @@ def net_run(args, dev, peaks):
     e1.record()
     torch.cuda.synchronize(dev)
     step_s = e0.elapsed_time(e1) / 50 / 1e3
+    eta = {"cloud_0.2-0.5px": eta_run(dev, peaks, hits_tr, hits_te, t_te, single)}
+    # one fixed cloud width, where the centroid is one monotone map of the offset
+    det5 = synth.asic_352x384(occupancy=0.005, occupancy_hi=0.05, cloud_sigma=0.5, seed=37)
+    h5_tr, _, _, _ = learn.make_set(det5, 40, 0)
+    h5_te, _, (_, t5, m5), _ = learn.make_set(det5, 12, 1000)
+    eta["cloud_0.5px"] = eta_run(dev, peaks, h5_tr, h5_te, t5, m5 == 1, timing=False)
     bf16 = peaks.get("bf16_tflops")
     inf_tf = n_inf * NET_FWD_FLOP / inf_s / 1e12
     tr_tf = 3 * batch * NET_FWD_FLOP / step_s / 1e12
@@ -553,7 +559,57 @@ def net_run(args, dev, peaks):
                      "tflops": round(tr_tf, 1),
                      "frac_of_bf16_peak": round(tr_tf / bf16, 4) if bf16 else None},
         "flop_per_hit_forward": NET_FWD_FLOP,
+        "eta_linearisation": eta,
     }
+
+
+def eta_run(dev, peaks, hits_tr, hits_te, t_te, single, bins=255, timing=True):
+    """Centroid linearisation: the centroid CDF from the training frames'
+    single-photon hits, applied to the held-out hits (RMS against truth), and
+    the apply kernel's bandwidth over 2^24 hits (24 B read + 24 B written per
+    hit, 805 MB per launch, larger than L2)."""
+    import torch
+    from paper_1903_06838_gb300 import pd
+    e = pd.pd_eta_create(bins)
+    tr = torch.from_numpy(hits_tr.view(np.uint8).copy()).to(dev)
+    pd.pd_eta_accumulate(e, tr.data_ptr(), len(hits_tr))
+    pd.pd_eta_finalize(e)
+    te = torch.from_numpy(hits_te.view(np.uint8).copy()).to(dev)
+    out = torch.empty_like(te)
+    pd.pd_eta_apply(e, te.data_ptr(), len(hits_te), out.data_ptr())
+    torch.cuda.synchronize(dev)
+    lin = out.cpu().numpy().view(pd.HIT_DTYPE).reshape(-1)
+    rms = float(np.sqrt(((np.stack([lin["dx"], lin["dy"]], 1)[single] - t_te[single]) ** 2)
+                        .mean()))
+    rms_com = float(np.sqrt(((np.stack([hits_te["dx"], hits_te["dy"]], 1)[single] -
+                              t_te[single]) ** 2).mean()))
+    res = {"bins": bins, "calibration_hits": int(len(hits_tr)),
+           "rms_offset_px": {"centre_of_mass": round(rms_com, 4),
+                             "linearised": round(rms, 4)},
+           "linearised_fraction": round(float(
+               ((lin["flags"] & pd.PD_HIT_LINEARISED) != 0).mean()), 4)}
+    if not timing:
+        pd.pd_eta_destroy(e)
+        return res
+    n = 1 << 24
+    big = te.view(-1, 24).repeat((n + len(hits_te) - 1) // len(hits_te), 1)[:n].contiguous()
+    big_out = torch.empty_like(big)
+    for _ in range(3):
+        pd.pd_eta_apply(e, big.data_ptr(), n, big_out.data_ptr())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for _ in range(20):
+        pd.pd_eta_apply(e, big.data_ptr(), n, big_out.data_ptr())
+    e1.record()
+    torch.cuda.synchronize(dev)
+    s = e0.elapsed_time(e1) / 20 / 1e3
+    gbs = 48 * n / s / 1e9
+    hbm = peaks.get("hbm_gbs")
+    pd.pd_eta_destroy(e)
+    res["apply"] = {"hits_per_s": round(n / s), "gb_per_s": round(gbs, 1),
+                    "frac_of_hbm": round(gbs / hbm, 4) if hbm else None}
+    return res
 
 
 def flush_l2(dev, buf=[]):

@@ -68,6 +68,7 @@ extern "C" {
 #define PD_HIT_EDGE 1u      /* seed pixel lies on its module's border       */
 #define PD_HIT_SATURATED 2u /* rint(E / photon_kev) exceeded 255 and clipped */
 #define PD_HIT_LEARNED 4u   /* count and dx, dy come from the learned network */
+#define PD_HIT_LINEARISED 8u /* dx, dy linearised by pd_eta_apply            */
 
 /* Detector geometry.  Requirements (PD_EINVAL otherwise): all sizes > 0,
  * rows, cols <= 65535, fewer than 2^31 pixels per frame, rows % unit_rows
@@ -422,6 +423,43 @@ void pd_server_destroy(pd_server* server);
 int pd_compress_hits(const pd_hit* hits, uint32_t n, uint8_t* out, size_t cap, size_t* out_len);
 int pd_decompress_hits(const uint8_t* in, size_t len, uint32_t frame, pd_hit* out, uint32_t cap,
                        uint32_t* n_out);
+
+/* ---- Centroid linearisation ----------------------------------------------
+ * The centre-of-mass offset depends nonlinearly on where a photon landed,
+ * and centroids need linearising to give positions (section "Photon
+ * Subpixel Resolution", Fig. f and its caption).  With photons landing
+ * uniformly inside the seed pixel, the true offset is F(d) - 1/2 with F the
+ * cumulative distribution of the centroid d.  pd_eta estimates F per axis
+ * from single-photon hits (count == 1, finite dx and dy): a histogram of d
+ * over `bins` bins spanning [-1, 1] (centroids outside clip to the end
+ * bins).  `bins` is odd so that d = 0, an atom of the distribution (all
+ * neighbours below the zero threshold), lies in the middle of a bin and maps
+ * to the middle of its probability mass.  For a centroid d, in float32
+ * round-to-nearest in this order:
+ *   t = (d + 1) * (bins * 0.5);  k = clamp(floor(t), 0, bins - 1);
+ *   phi = clamp(t - k, 0, 1);  u = (C[k] + phi * h[k]) / N - 1/2
+ * with h the counts, C[k] the counts below bin k and N the total.  With no
+ * counts (N = 0) centroids are unchanged. */
+typedef struct pd_eta pd_eta;
+#define PD_MAX_ETA_BINS 4095u
+
+/* bins: odd, 1 <= bins <= PD_MAX_ETA_BINS.  Histograms start at zero. */
+int pd_eta_create(uint32_t bins, pd_eta** out);
+/* Add the single-photon hits among n device hits to the histograms
+ * (asynchronous on `stream`). */
+int pd_eta_accumulate(pd_eta* eta, const pd_hit* hits_dev, uint32_t n, void* stream);
+/* Cumulative counts of the current histograms; call before pd_eta_apply and
+ * again after more pd_eta_accumulate calls (asynchronous). */
+int pd_eta_finalize(pd_eta* eta, void* stream);
+/* hits_out[i] = hits_in[i] with dx, dy of single-photon hits replaced by
+ * their linearised values and PD_HIT_LINEARISED set; other hits are copied
+ * unchanged.  hits_out may equal hits_in (asynchronous). */
+int pd_eta_apply(const pd_eta* eta, const pd_hit* hits_in_dev, uint32_t n,
+                 pd_hit* hits_out_dev, void* stream);
+/* uint32 [2][bins]: the dx histogram, then the dy histogram (synchronous). */
+int pd_eta_get_histogram(const pd_eta* eta, uint32_t* hist_host);
+int pd_eta_reset(pd_eta* eta, void* stream);
+void pd_eta_destroy(pd_eta* eta);
 
 /* Kernel timing.  When enabled on a context, every kernel the context
  * launches is bracketed by CUDA events recorded on the launching stream;

@@ -20,8 +20,8 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_PKG, "libpd.so")
-SOURCES = ["pd_api.cu", "pd_chain.cu", "pd_fast.cu", "pd_fused.cu", "pd_noalloc.cu",
-           "pd_net.cu", "pd_net_tc.cu", "pd_serve.cu"]
+SOURCES = ["pd_api.cu", "pd_chain.cu", "pd_eta.cu", "pd_fast.cu", "pd_fused.cu",
+           "pd_noalloc.cu", "pd_net.cu", "pd_net_tc.cu", "pd_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
@@ -34,7 +34,8 @@ _lib = None
 PD_OK, PD_EINVAL, PD_EALIGN, PD_ENOMEM, PD_EOVERFLOW = 0, 1, 2, 3, 4
 PD_ETIMEDOUT, PD_ECUDA, PD_ENOTSUP, PD_EBUSY = 5, 6, 7, 8
 PD_CM_MEDIAN, PD_CM_NONE = 0, 1
-PD_HIT_EDGE, PD_HIT_SATURATED, PD_HIT_LEARNED = 1, 2, 4
+PD_HIT_EDGE, PD_HIT_SATURATED, PD_HIT_LEARNED, PD_HIT_LINEARISED = 1, 2, 4, 8
+PD_MAX_ETA_BINS = 4095
 PD_MAX_HIST_BINS = 4096
 
 HIT_DTYPE = np.dtype([("frame", "<u4"), ("pixel", "<u4"), ("energy_kev", "<f4"),
@@ -191,6 +192,13 @@ def _declare(lib):
         "pd_server_destroy": ([vp], None),
         "pd_compress_hits": ([vp, u32, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], i32),
         "pd_decompress_hits": ([vp, ctypes.c_size_t, u32, vp, u32, ctypes.POINTER(u32)], i32),
+        "pd_eta_create": ([u32, ctypes.POINTER(vp)], i32),
+        "pd_eta_accumulate": ([vp, vp, u32, vp], i32),
+        "pd_eta_finalize": ([vp, vp], i32),
+        "pd_eta_apply": ([vp, vp, u32, vp, vp], i32),
+        "pd_eta_get_histogram": ([vp, vp], i32),
+        "pd_eta_reset": ([vp, vp], i32),
+        "pd_eta_destroy": ([vp], None),
         "pd_net_num_params": ([], u32),
         "pd_net_create": ([u32, ctypes.c_uint64, ctypes.POINTER(vp)], i32),
         "pd_net_set_params": ([vp, vp, u32], i32),
@@ -681,6 +689,58 @@ def pd_decompress_hits(data: bytes, frame: int = 0) -> np.ndarray:
     _check(load().pd_decompress_hits(src, len(data), frame, out.ctypes.data, n.value,
                                      ctypes.byref(n)), "pd_decompress_hits")
     return out
+
+
+# ---- centroid linearisation -------------------------------------------------
+class Eta:
+    def __init__(self, bins: int = 255):
+        h = ctypes.c_void_p()
+        _check(load().pd_eta_create(bins, ctypes.byref(h)), "pd_eta_create")
+        self.handle = h.value
+        self.bins = bins
+
+    def close(self):
+        if self.handle:
+            load().pd_eta_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pd_eta_create(bins: int = 255) -> Eta:
+    return Eta(bins)
+
+
+def pd_eta_accumulate(eta: Eta, hits_ptr: int, n: int, stream=None) -> None:
+    _check(load().pd_eta_accumulate(eta.handle, hits_ptr, n, _stream_handle(stream)),
+           "pd_eta_accumulate")
+
+
+def pd_eta_finalize(eta: Eta, stream=None) -> None:
+    _check(load().pd_eta_finalize(eta.handle, _stream_handle(stream)), "pd_eta_finalize")
+
+
+def pd_eta_apply(eta: Eta, hits_in_ptr: int, n: int, hits_out_ptr: int, stream=None) -> None:
+    _check(load().pd_eta_apply(eta.handle, hits_in_ptr, n, hits_out_ptr, _stream_handle(stream)),
+           "pd_eta_apply")
+
+
+def pd_eta_get_histogram(eta: Eta) -> np.ndarray:
+    out = np.zeros((2, eta.bins), np.uint32)
+    _check(load().pd_eta_get_histogram(eta.handle, out.ctypes.data), "pd_eta_get_histogram")
+    return out
+
+
+def pd_eta_reset(eta: Eta, stream=None) -> None:
+    _check(load().pd_eta_reset(eta.handle, _stream_handle(stream)), "pd_eta_reset")
+
+
+def pd_eta_destroy(eta: Eta) -> None:
+    eta.close()
 
 
 def pd_strerror(code: int) -> str:

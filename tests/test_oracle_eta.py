@@ -9,7 +9,7 @@ import numpy as np
 from oracle import eta
 from paper_1903_06838_gb300 import pd
 
-B = 256
+B = 255
 
 
 def _hits(dx, dy, count=None):
@@ -72,3 +72,35 @@ def test_only_single_photon_hits_count_and_change():
 def test_empty_histogram_is_the_identity():
     d = np.float32([0.25, -0.5])
     assert np.array_equal(eta.linearise(np.zeros(B, np.uint32), d, B), d)
+
+
+def test_apply_flags_only_the_linearised_hits():
+    d = np.float32([0.1, 0.2, np.inf])
+    hits = _hits(d, d, np.uint8([1, 3, 1]))
+    hits["flags"] = [1, 2, 0]
+    hist = eta.accumulate(np.zeros((2, B), np.uint32), hits, B)
+    out = eta.apply(hist, hits, B)
+    assert list(out["flags"]) == [1 | eta.LINEARISED, 2, 0]
+    assert pd.PD_HIT_LINEARISED == eta.LINEARISED
+
+
+def test_atom_at_zero_maps_to_the_middle_of_its_mass():
+    # 40 % of the centroids exactly 0 (all charge in the seed pixel), the rest
+    # symmetric about 0: F jumps from 0.3 to 0.7 at d = 0, whose best
+    # estimate is the middle of the jump, u = 0
+    m = 30_000
+    side = np.linspace(0.01, 0.99, m).astype(np.float32)
+    d = np.concatenate([-side, side, np.zeros(40_000, np.float32)])
+    hist = eta.accumulate(np.zeros((2, B), np.uint32), _hits(d, d), B)
+    assert eta.linearise(hist[0], np.float32([0.0]), B)[0] == np.float32(0.0)
+    # just off the atom the map leaves the jump's ends (within one bin's mass)
+    lo, hi = eta.linearise(hist[0], np.float32([-0.01, 0.01]), B)
+    assert -0.22 < lo < -0.19 and 0.19 < hi < 0.22
+
+
+def test_one_bin_is_half_the_centroid():
+    # a single bin spanning [-1, 1] interpolates the whole range linearly
+    d = np.float32([-0.8, 0.0, 0.4, 1.0])
+    hist = eta.accumulate(np.zeros((2, 1), np.uint32), _hits(d, d), 1)
+    # (up to the float32 roundings of d + 1, the product by N and the quotient)
+    assert np.max(np.abs(eta.linearise(hist[0], d, 1) - d / 2)) <= 2.0 ** -23
