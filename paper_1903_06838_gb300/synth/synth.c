@@ -208,8 +208,11 @@ long long ps_frames(const ps_config* c, const float* ped, const float* gain,
                             }
                             double fx[3], fy[3], sx = 0, sy = 0;
                             for (int d = -1; d <= 1; d++) {
-                                fx[d + 1] = gmass(q + d, q + d + 1, x, s);
-                                fy[d + 1] = gmass(r + d, r + d + 1, y, s);
+                                /* signed pixel edges: q + d wraps in
+                                   unsigned arithmetic at column / row 0 */
+                                const double qe = (double)q + d, re = (double)r + d;
+                                fx[d + 1] = gmass(qe, qe + 1.0, x, s);
+                                fy[d + 1] = gmass(re, re + 1.0, y, s);
                                 sx += fx[d + 1];
                                 sy += fy[d + 1];
                             }

@@ -397,7 +397,8 @@ def test_seed_tie_properties(seed):
 
 def test_pileup_counts():
     """k photons landing together deposit k times the energy; with no noise
-    and a low zeroing threshold rint(E / E_ph) recovers k."""
+    and a low zeroing threshold rint(E / E_ph) recovers k (away from the
+    module border, where part of the 3x3 footprint falls outside)."""
     det = synth.asic_352x384(rows=64, cols=64, unit_rows=1, unit_cols=64,
                              noise_sigma=0.0, cm_sigma=0.0, occupancy=0.0005,
                              multi_frac=1.0, cloud_sigma=0.25, seed=5)
@@ -420,7 +421,8 @@ def test_pileup_counts():
                 if abs(s[0] - (col + 0.5)) < 1.5 and abs(s[1] - (row + 0.5)) < 1.5]
         far = [s for s in by_frame.get(f, [])
                if abs(s[0] - (col + 0.5)) < 4 and abs(s[1] - (row + 0.5)) < 4]
-        if len(near) == 1 and len(far) == 1:
+        inside = all(1 <= int(v) <= 62 for v in near[0][:2]) if near else False
+        if len(near) == 1 and len(far) == 1 and inside:
             assert h["count"] == near[0][2]
             checked += 1
     assert checked > 20
