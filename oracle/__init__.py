@@ -29,7 +29,7 @@ HIT_DTYPE = np.dtype([("frame", "<u4"), ("pixel", "<u4"), ("energy_kev", "<f4"),
                       ("npix", "u1"), ("flags", "<u2")])
 assert HIT_DTYPE.itemsize == 24
 
-CM_MEDIAN, CM_NONE = 0, 1
+CM_MEDIAN, CM_NONE, CM_MEAN, CM_MEAN_STACKED = 0, 1, 2, 3
 HIT_EDGE, HIT_SATURATED = 1, 2
 
 
@@ -74,6 +74,10 @@ def _load():
         lib.oracle_lower_median.restype = ctypes.c_float
         lib.oracle_default_min_count.argtypes = [ctypes.c_uint32]
         lib.oracle_default_min_count.restype = ctypes.c_uint32
+        lib.oracle_paper_mean.argtypes = [vp, ctypes.c_uint32, ctypes.c_float]
+        lib.oracle_paper_mean.restype = ctypes.c_float
+        lib.oracle_cm_values_per_frame.argtypes = [ctypes.POINTER(Geometry)]
+        lib.oracle_cm_values_per_frame.restype = ctypes.c_uint32
         _lib = lib
     return _lib
 
@@ -100,6 +104,18 @@ def default_min_count(unit_pixels: int) -> int:
     return int(_load().oracle_default_min_count(unit_pixels))
 
 
+def paper_mean(values, cut) -> np.float32:
+    """The paper's common-mode estimator (Fig. c) over one group of values."""
+    v = np.ascontiguousarray(values, np.float32)
+    return np.float32(_load().oracle_paper_mean(v.ctypes.data, v.size, np.float32(cut)))
+
+
+def cm_values_per_frame(geom: Geometry) -> int:
+    """Common-mode values per frame: units, then (stacked) module rows and
+    module columns."""
+    return int(_load().oracle_cm_values_per_frame(ctypes.byref(geom)))
+
+
 class Result:
     """Outputs of one oracle run (hits in frame, module, row, col order)."""
 
@@ -121,8 +137,7 @@ def process(geom: Geometry, thr: Thresholds, ped, gain, raw, *, frame_base=0,
     raw = np.ascontiguousarray(raw, np.uint16).reshape(-1)
     assert raw.size % fpx == 0 and ped.size == fpx and gain.size == fpx
     n = raw.size // fpx
-    upf = geom.n_modules * (geom.rows // geom.unit_rows) * \
-        (geom.cols // geom.unit_cols)
+    upf = cm_values_per_frame(geom)
     cap = hit_capacity if hit_capacity is not None else max(1024, n * fpx // 8)
     hits = np.zeros(cap, HIT_DTYPE)
     nh = ctypes.c_uint32(0)

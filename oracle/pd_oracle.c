@@ -26,7 +26,23 @@
  *     the role of the figure's sqrt(HW) guard against estimating from too
  *     few pixels.  n_min defaults to ceil(sqrt(unit pixels)).
  *     Ascending order is IEEE order refined so -0 sorts below +0.
- *  3. c = d - cm_u
+ *     The paper's own estimator (Fig. c) is available too, as
+ *     cm_mode = MEAN: per group of G pixels, N0 = number of values v with
+ *     v < cm_cut (and v > -inf), S = their sum, and
+ *     cm = S / max(N0, sqrt(G)); the sqrt(G) term keeps a group with few
+ *     background pixels from correcting by a noisy estimate.  The sum is
+ *     defined exactly, independent of order: with M the largest |v| of the
+ *     set and E = max(floor(log2 M), -60), every v is rounded to the grid
+ *     2^(E-38) (rint, ties to even), the integers are added exactly, and the
+ *     total is rounded once to binary32.  Values down to M * 2^-15 lie on
+ *     that grid, so for detector data the sum is the exactly rounded sum.
+ *     cm_mode = MEAN_STACKED stacks three such stages, as the paper's
+ *     benchmark model does (section "Performance"; the text of section
+ *     "Common Mode" names row, column and block groups): stage 1 over each
+ *     unit gives cm_u; stage 2 over each row of the module, on d - cm_u,
+ *     gives cm_r; stage 3 over each column of the module, on
+ *     (d - cm_u) - cm_r, gives cm_c.  G is the group's pixel count.
+ *  3. c = d - cm_u  (stacked: c = ((d - cm_u) - cm_r) - cm_c)
  *  4. Gain: e = c * inv_gain with inv_gain = 1.0f / gain computed once
  *     (Fig. b divides by the gain map; the reciprocal is taken once per
  *     pixel); gain <= 0 or non-finite masks the pixel (inv_gain = 0).
@@ -79,7 +95,7 @@ typedef struct {
     uint16_t flags;
 } og_hit;
 
-enum { OG_CM_MEDIAN = 0, OG_CM_NONE = 1 };
+enum { OG_CM_MEDIAN = 0, OG_CM_NONE = 1, OG_CM_MEAN = 2, OG_CM_MEAN_STACKED = 3 };
 enum { OG_EDGE = 1, OG_SATURATED = 2 };
 
 /* The 32-bit pattern of a float mapped so that unsigned comparison of the
@@ -119,13 +135,56 @@ float oracle_lower_median(float* set, uint32_t n) {
     return set[(n - 1) / 2];
 }
 
+/* A value enters the paper's mean iff it is below the cut and not -inf. */
+static int mean_selects(float v, float cut) { return v < cut && v > -INFINITY; }
+
+/* The paper's common-mode estimator (Fig. c) over the n values of one
+ * group, with the exactly defined sum of step 2 above. */
+float oracle_paper_mean(const float* v, uint32_t n, float cut) {
+    uint32_t n0 = 0;
+    float mx = 0.0f;
+    for (uint32_t i = 0; i < n; i++) {
+        if (!mean_selects(v[i], cut)) continue;
+        n0++;
+        if (fabsf(v[i]) > mx) mx = fabsf(v[i]);
+    }
+    float sum = 0.0f;
+    if (n0 > 0 && mx > 0.0f) {
+        int ex;
+        frexpf(mx, &ex); /* mx = f * 2^ex, f in [0.5, 1) */
+        int e = ex - 1;
+        if (e < -60) e = -60;
+        const int k = 38 - e;
+        long long total = 0;
+        for (uint32_t i = 0; i < n; i++)
+            if (mean_selects(v[i], cut)) total += llrintf(ldexpf(v[i], k));
+        sum = ldexpf((float)total, -k);
+    }
+    const float guard = sqrtf((float)n);
+    const float den = (float)n0 > guard ? (float)n0 : guard;
+    return sum / den;
+}
+
+/* Common-mode values per frame: units, then (stacked) module rows and
+ * module columns. */
+uint32_t oracle_cm_values_per_frame(const og_geometry* g) {
+    const uint32_t units = g->n_modules * (g->rows / g->unit_rows) * (g->cols / g->unit_cols);
+    if (g->cm_mode != OG_CM_MEAN_STACKED) return units;
+    return units + g->n_modules * (g->rows + g->cols);
+}
+
 int oracle_check(const og_geometry* g, const og_thresholds* t) {
     if (!g || !t) return 1;
     if (!g->n_modules || !g->rows || !g->cols || !g->unit_rows ||
         !g->unit_cols)
         return 1;
     if (g->rows % g->unit_rows || g->cols % g->unit_cols) return 1;
-    if (g->cm_mode != OG_CM_MEDIAN && g->cm_mode != OG_CM_NONE) return 1;
+    if (g->cm_mode > OG_CM_MEAN_STACKED) return 1;
+    /* the exact sum of the mean stays within 64 bits below 2^24 values */
+    if (g->cm_mode >= OG_CM_MEAN &&
+        ((uint64_t)g->unit_rows * g->unit_cols >= (1u << 24) || g->rows >= (1u << 24) ||
+         g->cols >= (1u << 24)))
+        return 1;
     if (!(t->zero_thr_kev >= 0.0f) || !(t->seed_thr_kev >= t->zero_thr_kev))
         return 1;
     if (!(t->photon_kev > 0.0f) || !(t->hist_bin_kev > 0.0f)) return 1;
@@ -146,7 +205,9 @@ int oracle_check(const og_geometry* g, const og_thresholds* t) {
  *   count_map:  u32 [pixels]   (accumulated, not cleared)
  *   hist_pix, hist_hit: u64 [hist_bins] (accumulated, not cleared)
  *   corrected:  float [n_frames][pixels] e values, or NULL
- *   cm_out:     float [n_frames][units] common mode, or NULL
+ *   cm_out:     float [n_frames][oracle_cm_values_per_frame] common mode
+ *               (units, then for MEAN_STACKED n_modules x rows row terms
+ *               and n_modules x cols column terms), or NULL
  *   n_seeds:    receives the number of seeds (hits plus seeds with n = 0),
  *               or NULL
  * Returns 0, or 1 on invalid input.
@@ -173,15 +234,25 @@ int oracle_process(const og_geometry* g, const og_thresholds* t,
     float* d = (float*)malloc(mpx * sizeof(float));
     float* e = (float*)malloc(mpx * sizeof(float));
     float* s = (float*)malloc(mpx * sizeof(float));
-    float* set = (float*)malloc((size_t)unit_px * sizeof(float));
+    const int stacked = g->cm_mode == OG_CM_MEAN_STACKED;
+    const uint32_t cpf = oracle_cm_values_per_frame(g);
+    const uint32_t upf = g->n_modules * upm;
+    size_t set_n = unit_px;
+    if (R > set_n) set_n = R;
+    if (C > set_n) set_n = C;
+    float* set = (float*)malloc(set_n * sizeof(float));
     float* cmu = (float*)malloc((size_t)upm * sizeof(float));
-    if (!inv_gain || !d || !e || !s || !set || !cmu) {
+    float* cmr = (float*)calloc(R, sizeof(float));
+    float* cmc = (float*)calloc(C, sizeof(float));
+    if (!inv_gain || !d || !e || !s || !set || !cmu || !cmr || !cmc) {
         free(inv_gain); free(d); free(e); free(s); free(set); free(cmu);
+        free(cmr); free(cmc);
         return 1;
     }
     for (size_t p = 0; p < fpx; p++) {
         if (!isfinite(ped[p])) {
             free(inv_gain); free(d); free(e); free(s); free(set); free(cmu);
+            free(cmr); free(cmc);
             return 1;
         }
         const float gp = gain[p];
@@ -211,11 +282,38 @@ int oracle_process(const og_geometry* g, const og_thresholds* t,
                             }
                         }
                         if (n >= n_min && n > 0) cm = oracle_lower_median(set, n);
+                    } else if (g->cm_mode != OG_CM_NONE) {
+                        uint32_t n = 0;
+                        for (uint32_t r = 0; r < g->unit_rows; r++)
+                            for (uint32_t c = 0; c < g->unit_cols; c++)
+                                set[n++] = d[(size_t)(ur * g->unit_rows + r) * C +
+                                             uc * g->unit_cols + c];
+                        cm = oracle_paper_mean(set, n, t->cm_cut_adu);
                     }
                     cmu[ur * ucols + uc] = cm;
                     if (cm_out)
-                        cm_out[(size_t)f * g->n_modules * upm + m * upm +
-                               ur * ucols + uc] = cm;
+                        cm_out[(size_t)f * cpf + m * upm + ur * ucols + uc] = cm;
+                }
+            }
+            if (stacked) {
+                /* stage 2: each module row, on d - cm_u */
+                for (uint32_t r = 0; r < R; r++) {
+                    for (uint32_t c = 0; c < C; c++)
+                        set[c] = d[(size_t)r * C + c] -
+                                 cmu[(r / g->unit_rows) * ucols + c / g->unit_cols];
+                    cmr[r] = oracle_paper_mean(set, C, t->cm_cut_adu);
+                    if (cm_out) cm_out[(size_t)f * cpf + upf + (size_t)m * R + r] = cmr[r];
+                }
+                /* stage 3: each module column, on (d - cm_u) - cm_r */
+                for (uint32_t c = 0; c < C; c++) {
+                    for (uint32_t r = 0; r < R; r++)
+                        set[r] = (d[(size_t)r * C + c] -
+                                  cmu[(r / g->unit_rows) * ucols + c / g->unit_cols]) -
+                                 cmr[r];
+                    cmc[c] = oracle_paper_mean(set, R, t->cm_cut_adu);
+                    if (cm_out)
+                        cm_out[(size_t)f * cpf + upf + (size_t)g->n_modules * R +
+                               (size_t)m * C + c] = cmc[c];
                 }
             }
             /* 3.-5. subtract common mode, gain, zero noise; pixel histogram */
@@ -224,7 +322,8 @@ int oracle_process(const og_geometry* g, const og_thresholds* t,
                     const size_t p = (size_t)r * C + c;
                     const float cm =
                         cmu[(r / g->unit_rows) * ucols + c / g->unit_cols];
-                    const float cc = d[p] - cm;
+                    float cc = d[p] - cm;
+                    if (stacked) cc = (cc - cmr[r]) - cmc[c];
                     const float ev = cc * inv_gain[base + p];
                     e[p] = ev;
                     s[p] = ev > t->zero_thr_kev ? ev : 0.0f;
@@ -301,5 +400,6 @@ int oracle_process(const og_geometry* g, const og_thresholds* t,
     *n_hits = nh;
     if (n_seeds) *n_seeds = ns;
     free(inv_gain); free(d); free(e); free(s); free(set); free(cmu);
+    free(cmr); free(cmc);
     return 0;
 }
