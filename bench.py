@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-net", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--only", choices=["serve", "batch", "net"], default=None,
+    ap.add_argument("--no-cm-variants", action="store_true")
+    ap.add_argument("--only", choices=["serve", "batch", "net", "cm"], default=None,
                     help="run one section alone (for profiling) and print its JSON")
     ap.add_argument("--serve-rate", type=float, default=100000.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
@@ -352,6 +353,8 @@ def run_pd(args):
         line["e2e"] = {"value": round(nf * ws / dt, 1), "unit": "frames/s",
                        "h2d_bytes_per_step": raw_b, "d2h_bytes_per_step": nh * HIT_BYTES + 4,
                        "api": "pd_process_host (page-locked host frames, hits back to host)"}
+    if rank == 0 and ws == 1 and not args.no_cm_variants:
+        line["cm_variants"] = cm_variants_run(args, dev, det, ped, gain, frames, nf, peak)
     if rank == 0 and ws == 1 and not args.no_serve:
         del frames, out
         torch.cuda.empty_cache()
@@ -370,6 +373,50 @@ def run_pd(args):
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return 0
+
+
+def cm_variants_run(args, dev, det, ped, gain, frames, nf, peak, steps=5):
+    """The same 2.2 Mpx batch with the paper's mean common mode (one stage per
+    bank, and three stacked stages: bank, module row, module column) in place
+    of the median: frames/s and the device time of each kernel group.  The
+    common-mode launches' algorithmic bytes are one read of raw and of the
+    pedestal map per stage plus the common-mode values written."""
+    import torch
+    from paper_1903_06838_gb300 import pd
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for name, mode in (("mean", pd.PD_CM_MEAN), ("mean_stacked", pd.PD_CM_MEAN_STACKED)):
+        ctx = pd.pd_create(dict(det.geometry(), cm_mode=mode), ped, gain, det.thresholds())
+        out = pd.Outputs(ctx, nf, nf * 16384, device=dev)
+        for _ in range(3):
+            pd.pd_process(ctx, frames.data_ptr(), nf, 0, stream=stream, **out.ptrs())
+        torch.cuda.synchronize(dev)
+        pd.pd_set_profiling(ctx, True)
+        pd.pd_read_profile(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            pd.pd_process(ctx, frames.data_ptr(), nf, 0, stream=stream, **out.ptrs())
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        prof = pd.pd_read_profile(ctx)
+        pd.pd_set_profiling(ctx, False)
+        ms = e0.elapsed_time(e1) / steps
+        stages = 3 if mode == pd.PD_CM_MEAN_STACKED else 1
+        fpx = det.pixels_per_frame
+        cm_bytes = nf * (stages * fpx * (2 + 4) + ctx.cm_values_per_frame * 4)
+        cm_ms = prof["common_mode"][1] / steps if "common_mode" in prof else None
+        res[name] = {
+            "frames_per_s": round(nf / (ms / 1e3), 1),
+            "ms_per_step": round(ms, 3),
+            "kernel_ms_per_step": {k: round(v[1] / steps, 3) for k, v in prof.items()},
+            "common_mode_gbs": round(cm_bytes / (cm_ms / 1e3) / 1e9, 1) if cm_ms else None,
+            "common_mode_frac_of_hbm": round(cm_bytes / (cm_ms / 1e3) / 1e9 / peak, 4)
+            if cm_ms else None,
+            "hits_per_frame": round(int(out.n_hits.item()) / nf, 1)}
+        del out
+        pd.pd_destroy(ctx)
+    return res
 
 
 def h2d_bandwidth(dev, nbytes=1 << 30, reps=5):
@@ -746,6 +793,13 @@ def run_only(args):
     peak, _ = read_peaks()
     if args.only == "serve":
         res = serve_run(args, dev)
+    elif args.only == "cm":
+        from paper_1903_06838_gb300 import synth
+        det = workload()
+        ped, gain = synth.maps(det)
+        raw, _ = synth.frames(det, ped, gain, 0, args.frames, truth=False)
+        frames = pd.frames_to_device(raw).to(dev)
+        res = cm_variants_run(args, dev, det, ped, gain, frames, args.frames, peak)
     elif args.only == "batch":
         res = {"single_asic_16": single_asic_run(args, dev),
                "batch_mix_4096": batch_mix_run(args, dev, peak)}

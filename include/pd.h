@@ -63,6 +63,19 @@ extern "C" {
 /* ---- common-mode estimators (paper Fig. c and its text) --------------- */
 #define PD_CM_MEDIAN 0 /* lower median of d = raw - pedestal over d < cut  */
 #define PD_CM_NONE 1   /* no common-mode correction (cm = 0)               */
+/* The paper's estimator (section "Common Mode", Fig. c): over a group of G
+ * pixels, N0 values v with v < cut (and v > -inf) summing to S give
+ * cm = S / max(N0, sqrt(G)).  S is exact and independent of order: with M
+ * the largest selected |v| and E = max(floor(log2 M), -60), each v is
+ * rounded (to nearest even) to the grid 2^(E-38), the integers are added
+ * exactly and the total is rounded once to float32; values down to
+ * M * 2^-15 lie on that grid.  cm_min_count is not used.  Units must hold
+ * fewer than 2^24 pixels. */
+#define PD_CM_MEAN 2         /* one stage over each unit (v = d)           */
+/* Three stacked stages (section "Performance"): units (v = d), then each
+ * module row (v = d - cm_u), then each module column
+ * (v = (d - cm_u) - cm_r); c = ((d - cm_u) - cm_r) - cm_c. */
+#define PD_CM_MEAN_STACKED 3
 
 /* ---- hit flags -------------------------------------------------------- */
 #define PD_HIT_EDGE 1u      /* seed pixel lies on its module's border       */
@@ -77,7 +90,7 @@ typedef struct {
     uint32_t n_modules;
     uint32_t rows, cols;           /* pixels of one module                  */
     uint32_t unit_rows, unit_cols; /* common-mode unit                      */
-    uint32_t cm_mode;              /* PD_CM_MEDIAN or PD_CM_NONE            */
+    uint32_t cm_mode;              /* PD_CM_MEDIAN, _NONE, _MEAN, _MEAN_STACKED */
 } pd_geometry;
 
 /* Thresholds and summary binning.  The paper exposes two noise thresholds
@@ -119,7 +132,11 @@ typedef struct {
     uint32_t hit_capacity;
     uint32_t* n_hits;      /* 1 x u32: set to the call's true hit count      */
     float* corrected;      /* [n_frames][pixels] e (keV) or NULL; 16-B aligned */
-    float* cm;             /* [n_frames][units]  common mode (ADU) or NULL   */
+    float* cm;             /* [n_frames][cm_values_per_frame] common mode
+                              (ADU) or NULL: the units' values (module-major,
+                              row-major units), then for PD_CM_MEAN_STACKED
+                              n_modules x rows row terms and n_modules x cols
+                              column terms                                   */
 } pd_outputs;
 
 typedef struct pd_ctx pd_ctx;
@@ -132,6 +149,7 @@ typedef struct {
     uint32_t cm_min_count;   /* resolved value (0 replaced by the default) */
     uint32_t hist_bins;
     uint32_t masked_pixels;  /* pixels whose gain was <= 0 or not finite   */
+    uint32_t cm_values_per_frame; /* common-mode values per frame (pd_outputs.cm) */
 } pd_info;
 
 /* pd_create — validate the geometry and thresholds, copy the pedestal and
@@ -171,7 +189,7 @@ int pd_process(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frames,
  * Its common-mode scratch is one fixed device array inside the library,
  * PD_NOALLOC_MAX_CM floats (4 MiB), present on every GPU that loads the
  * library until the process exits.  Limit: when out->cm is NULL,
- * n_frames * units_per_frame must not exceed PD_NOALLOC_MAX_CM, else the
+ * n_frames * cm_values_per_frame must not exceed PD_NOALLOC_MAX_CM, else the
  * call returns PD_EINVAL (split the call, or pass out->cm, which is then
  * used instead).  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress), so make that first call before any
@@ -217,8 +235,8 @@ void pd_destroy(pd_ctx* ctx);
  * of the next chunk on a second stream beside the stencil of the current
  * one; two_pass: 0 runs the whole chain as one kernel per (frame, module)
  * where the geometry allows it (common-mode units that are full-height
- * column banks, at most two per module, or common mode off; columns a
- * multiple of 4), 1 uses the common-mode + stencil kernel pair (the
+ * column banks, at most two per module, or common mode off, with the median
+ * or no common mode; columns a multiple of 4), 1 uses the common-mode + stencil kernel pair (the
  * default; pd_get_tuning reports 1 when the one-kernel form is not
  * available).
  * Results never depend on tuning. */
@@ -252,8 +270,8 @@ int pd_autotune(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frames,
  * item by item; with pd_batch_set_mixed(batch, 1) each chunk is one
  * persistent common-mode launch over every (item, frame, unit) of the chunk
  * and one persistent stencil launch over all its band tiles (items must
- * then use the band stencil: every geometry with at most 2048 columns per
- * module; PD_ENOTSUP otherwise).  Either way each item is processed exactly
+ * then use the band stencil, every geometry with at most 2048 columns per
+ * module, and the median or no common mode; PD_ENOTSUP otherwise).  Either way each item is processed exactly
  * as pd_process would (same results; summaries go to the item's context),
  * and a batch can be captured once as a CUDA graph and replayed. */
 typedef struct {

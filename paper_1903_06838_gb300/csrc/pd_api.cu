@@ -144,8 +144,9 @@ int check_geometry(const pd_geometry* g) {
         return fail(PD_EINVAL, "geometry sizes must be > 0");
     if (g->rows % g->unit_rows || g->cols % g->unit_cols)
         return fail(PD_EINVAL, "common-mode units must tile each module");
-    if (g->cm_mode != PD_CM_MEDIAN && g->cm_mode != PD_CM_NONE)
-        return fail(PD_EINVAL, "unknown cm_mode");
+    if (g->cm_mode > PD_CM_MEAN_STACKED) return fail(PD_EINVAL, "unknown cm_mode");
+    if (g->cm_mode >= PD_CM_MEAN && (uint64_t)g->unit_rows * g->unit_cols >= (1u << 24))
+        return fail(PD_EINVAL, "the mean common mode needs units of fewer than 2^24 pixels");
     const unsigned long long fpx =
         (unsigned long long)g->n_modules * g->rows * g->cols;
     if (fpx >= (1ull << 31)) return fail(PD_EINVAL, "frame too large");
@@ -207,8 +208,18 @@ void free_ctx(pd_ctx* c) {
     delete c;
 }
 
+// The common-mode launch(es) of a context for nf frames into cm.
+cudaError_t launch_cm(const pd_ctx* c, const uint16_t* fr, uint32_t nf, float* cm,
+                      cudaStream_t s) {
+    if (c->params.cm_mode == PD_CM_MEAN || c->params.cm_mode == PD_CM_MEAN_STACKED)
+        return pd::launch_cm_mean(c->params, fr, nf, cm, s);
+    return c->use_cm_big    ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, cm, s)
+           : c->use_cm_rows ? pd::launch_cm_rows(c->params, fr, nf, cm, s)
+                            : pd::launch_cm_select(c->params, fr, nf, cm, s);
+}
+
 int ensure_cm(pd_ctx* c, uint32_t n_frames) {
-    const size_t need = (size_t)n_frames * c->params.units_per_frame;
+    const size_t need = (size_t)n_frames * pd::cm_per_frame(c->params);
     if (need <= c->cm_cap) return PD_OK;
     // growth reallocates: any work on the old buffer must be finished
     cudaError_t e = cudaDeviceSynchronize();
@@ -256,14 +267,12 @@ int run_chain(pd_ctx* c, const uint16_t* frames, uint32_t n_frames, uint32_t fra
     for (uint32_t done = 0; done < n_frames; k++) {
         const uint32_t nf = std::min(c->chunk_frames, n_frames - done);
         const uint16_t* fr = frames + (size_t)done * c->params.frame_px;
-        float* cmc = cm + (size_t)done * c->params.units_per_frame;
+        float* cmc = cm + (size_t)done * pd::cm_per_frame(c->params);
         if (two && k >= 2 && (e = cudaStreamWaitEvent(sc, c->ev_st[k & 1], 0)))
             return fail_cuda(e, "chunk pipeline wait");
         {
             ProfileScope ps(c, 0, sc);
-            e = c->use_cm_big    ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, cmc, sc)
-                : c->use_cm_rows ? pd::launch_cm_rows(c->params, fr, nf, cmc, sc)
-                                 : pd::launch_cm_select(c->params, fr, nf, cmc, sc);
+            e = launch_cm(c, fr, nf, cmc, sc);
         }
         if (e != cudaSuccess) return fail_cuda(e, "common-mode kernel launch");
         if (two && ((e = cudaEventRecord(c->ev_cm[k & 1], sc)) ||
@@ -293,7 +302,7 @@ namespace pd {
 
 int internal_fail(int code, const char* why) { return fail(code, why ? why : "error"); }
 
-uint32_t internal_units_per_frame(const pd_ctx* c) { return c->params.units_per_frame; }
+uint32_t internal_cm_per_frame(const pd_ctx* c) { return pd::cm_per_frame(c->params); }
 
 int internal_check_process_args(const pd_ctx* c, const uint16_t* frames, uint32_t n_frames,
                                 const pd_outputs* out, const char** why) {
@@ -330,10 +339,8 @@ int internal_run_sequential(pd_ctx* c, const uint16_t* frames, uint32_t n_frames
     for (uint32_t done = 0; done < n_frames;) {
         const uint32_t nf = std::min(c->chunk_frames, n_frames - done);
         const uint16_t* fr = frames + (size_t)done * c->params.frame_px;
-        float* cmc = cm + (size_t)done * c->params.units_per_frame;
-        e = c->use_cm_big    ? launch_cm_big(c->params, c->cm_cfg, fr, nf, cmc, s)
-            : c->use_cm_rows ? launch_cm_rows(c->params, fr, nf, cmc, s)
-                             : launch_cm_select(c->params, fr, nf, cmc, s);
+        float* cmc = cm + (size_t)done * pd::cm_per_frame(c->params);
+        e = launch_cm(c, fr, nf, cmc, s);
         if (e != cudaSuccess) return fail_cuda(e, "common-mode kernel launch");
         CallOut co{out->hits, out->hit_capacity, out->n_hits,
                    out->corrected ? out->corrected + (size_t)done * c->params.frame_px
@@ -412,9 +419,11 @@ int pd_create(const pd_geometry* geometry, const float* pedestal_host,
     c->use_cm_big = g.cm_mode == PD_CM_MEDIAN && pd::cm_big_supported(p, c->cm_cfg);
     c->use_cm_rows = g.cm_mode == PD_CM_MEDIAN && !c->use_cm_big && pd::cm_rows_supported(p);
     c->band_cfg = pd::make_band_config(p);
-    c->use_band = c->band_cfg.ok;
+    // the band stencil reads one common-mode value per unit row segment
+    c->use_band = c->band_cfg.ok && g.cm_mode != PD_CM_MEAN_STACKED;
     c->fused_cfg = pd::make_fused_config(p);
-    c->use_fused = c->fused_cfg.ok;
+    // the one-kernel chain computes the median (or nothing) itself
+    c->use_fused = c->fused_cfg.ok && (g.cm_mode == PD_CM_MEDIAN || g.cm_mode == PD_CM_NONE);
     {
         const size_t fbytes = (size_t)p.frame_px * 2;
         const size_t target = 96u << 20;  // raw bytes per chunk (measured best)
@@ -483,6 +492,7 @@ int pd_query(const pd_ctx* c, pd_info* info) {
     if (!c || !info) return fail(PD_EINVAL, "NULL argument");
     info->pixels_per_frame = c->params.frame_px;
     info->units_per_frame = c->params.units_per_frame;
+    info->cm_values_per_frame = pd::cm_per_frame(c->params);
     info->unit_pixels = c->params.unit_px;
     info->cm_min_count = c->params.cm_min_count;
     info->hist_bins = c->params.hist_bins;
@@ -782,6 +792,8 @@ int batch_check_items(const pd_batch* b, const pd_batch_item* items, uint32_t n)
         if (rc) return fail(rc, why);
         if (b->mixed && !it.ctx->use_band)
             return fail(PD_ENOTSUP, "batch: the mixed launch needs the band stencil");
+        if (b->mixed && it.ctx->params.cm_mode >= PD_CM_MEAN)
+            return fail(PD_ENOTSUP, "batch: the mixed launch computes the median only");
     }
     return PD_OK;
 }
@@ -793,9 +805,7 @@ cudaError_t launch_chain_piece(pd_ctx* c, const uint16_t* fr, uint32_t nf, uint3
                                const pd::CallOut& co, cudaStream_t s) {
     if (c->use_fused && !c->two_pass)
         return pd::launch_fused(c->params, c->fused_cfg, fr, nf, frame_base, co, s);
-    cudaError_t e = c->use_cm_big    ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, co.cm, s)
-                    : c->use_cm_rows ? pd::launch_cm_rows(c->params, fr, nf, co.cm, s)
-                                     : pd::launch_cm_select(c->params, fr, nf, co.cm, s);
+    cudaError_t e = launch_cm(c, fr, nf, co.cm, s);
     if (e != cudaSuccess) return e;
     return c->use_band ? pd::launch_stencil_band(c->params, c->band_cfg, fr, nf, frame_base, co, s)
                        : pd::launch_stencil(c->params, fr, nf, frame_base, co, s);
@@ -839,7 +849,7 @@ int batch_enqueue(pd_batch* b, int slot, const pd_batch_item* items, uint32_t n,
         d.band_vec = c->band_cfg.vec;
         band_smem = std::max(band_smem, pd::band_smem_bytes(c->params, c->band_cfg.rb,
                                                             c->band_cfg.pitch));
-        const uint64_t ncm = (uint64_t)it.n_frames * c->params.units_per_frame;
+        const uint64_t ncm = (uint64_t)it.n_frames * pd::cm_per_frame(c->params);
         float* cm = it.out.cm;
         if (!cm) {
             if (cm_used + ncm > b->max_cm) return fail(PD_EINVAL, "batch: common-mode scratch too small");
@@ -873,11 +883,11 @@ int batch_enqueue(pd_batch* b, int slot, const pd_batch_item* items, uint32_t n,
             d.raw = it.frames + (size_t)pc.first * cp.frame_px;
             d.n_frames = pc.count;
             d.frame_base = it.frame_base + pc.first;
-            const uint64_t ncm = (uint64_t)pc.count * cp.units_per_frame;
+            const uint64_t ncm = (uint64_t)pc.count * pd::cm_per_frame(cp);
             d.out = pd::CallOut{it.out.hits, it.out.hit_capacity, it.out.n_hits,
                                 it.out.corrected ? it.out.corrected + (size_t)pc.first * cp.frame_px
                                                  : nullptr,
-                                item_cm[pc.item] + (size_t)pc.first * cp.units_per_frame};
+                                item_cm[pc.item] + (size_t)pc.first * pd::cm_per_frame(cp)};
             d.cm_first = L.cm_tasks;
             d.st_first = tiles;
             d.st_tiles = (unsigned long long)pc.count * cp.n_modules * d.band_cfg.n_bands;

@@ -4,7 +4,8 @@
 //                     Fig. c): exact lower median of d = raw - pedestal over
 //                     the unit's pixels with d < cut, found by a 4-pass
 //                     8-bit radix select (pd_cm_generic.cuh).
-//   stencil_kernel    dark, common mode and gain correction (Fig. b), noise
+//   stencil_kernel    dark, common mode (per unit; for the stacked mean also
+//                     per module row and column) and gain correction (Fig. b), noise
 //                     zeroing, 3x3 local maximum, charge sum, photon count
 //                     (Fig. e), centre-of-mass offset (Fig. f), warp-ballot
 //                     hit compaction and the summaries ("Summarization").
@@ -48,6 +49,7 @@ __global__ void __launch_bounds__(kCmThreads)
 constexpr int kTY = 16, kTX = 64, kStThreads = 256;
 constexpr int kHY = kTY + 2, kHX = kTX + 2;
 
+template <bool STACKED>
 __global__ void __launch_bounds__(kStThreads)
     stencil_kernel(ChainParams p, const uint16_t* __restrict__ raw,
                    uint32_t frame_base, CallOut out, uint32_t tiles_y,
@@ -72,8 +74,13 @@ __global__ void __launch_bounds__(kStThreads)
         const int r0 = ty * kTY, c0 = tx * kTX;
         const size_t mod_base = (size_t)m * p.module_px;
         const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
-        const float* cmf = out.cm + (size_t)f * p.units_per_frame +
+        const float* cmf = out.cm + (size_t)f * cm_per_frame(p) +
                            (size_t)m * p.units_per_module;
+        // stacked mean: module-row and module-column terms after the units'
+        const float* cmr = out.cm + (size_t)f * cm_per_frame(p) + p.units_per_frame +
+                           (size_t)m * p.rows;
+        const float* cmc = out.cm + (size_t)f * cm_per_frame(p) + p.units_per_frame +
+                           (size_t)p.n_modules * p.rows + (size_t)m * p.cols;
 
         // 1. corrected signal of the tile and its 1-pixel halo
         for (int j = threadIdx.x; j < kHY * kHX; j += kStThreads) {
@@ -85,7 +92,9 @@ __global__ void __launch_bounds__(kStThreads)
                 const float cm = cmf[((uint32_t)r / p.unit_rows) * p.units_per_row +
                                      (uint32_t)c / p.unit_cols];
                 const float d = __fsub_rn(__uint2float_rn(fr[off]), p.ped[mod_base + off]);
-                const float e = __fmul_rn(__fsub_rn(d, cm), p.inv_gain[mod_base + off]);
+                float cc = __fsub_rn(d, cm);
+                if (STACKED) cc = __fsub_rn(__fsub_rn(cc, cmr[r]), cmc[c]);
+                const float e = __fmul_rn(cc, p.inv_gain[mod_base + off]);
                 s = e > p.zero_thr ? e : 0.0f;
                 if (hr >= 1 && hr <= kTY && hc >= 1 && hc <= kTX) {
                     atomicAdd(&hpix[hist_bin(e, p.hist_neg_lo_s, p.hist_inv_w, p.hist_bins)], 1u);
@@ -219,16 +228,21 @@ cudaError_t launch_stencil(const ChainParams& p, const uint16_t* raw,
     const size_t smem = 2 * (size_t)p.hist_bins * sizeof(uint32_t);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(stencil_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(2 * PD_MAX_HIST_BINS * sizeof(uint32_t)));
-        if (e != cudaSuccess) return e;
+        for (auto k : {stencil_kernel<false>, stencil_kernel<true>}) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(2 * PD_MAX_HIST_BINS * sizeof(uint32_t)));
+            if (e != cudaSuccess) return e;
+        }
         attr_set = true;
     }
     unsigned long long grid = (unsigned long long)device_sm_count() * 4;
     if (grid > n_tiles) grid = n_tiles;
-    stencil_kernel<<<(unsigned)grid, kStThreads, smem, stream>>>(p, raw, frame_base, out,
-                                                                 tiles_y, tiles_x, n_tiles);
+    if (p.cm_mode == PD_CM_MEAN_STACKED)
+        stencil_kernel<true><<<(unsigned)grid, kStThreads, smem, stream>>>(
+            p, raw, frame_base, out, tiles_y, tiles_x, n_tiles);
+    else
+        stencil_kernel<false><<<(unsigned)grid, kStThreads, smem, stream>>>(
+            p, raw, frame_base, out, tiles_y, tiles_x, n_tiles);
     return cudaGetLastError();
 }
 

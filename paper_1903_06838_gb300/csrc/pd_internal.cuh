@@ -37,13 +37,20 @@ struct ChainParams {
     unsigned long long* hist_hit;  // [hist_bins]
 };
 
+// Common-mode values per frame: one per unit, then for the stacked mean one
+// per module row and one per module column.
+__host__ __device__ inline uint32_t cm_per_frame(const ChainParams& p) {
+    return p.units_per_frame +
+           (p.cm_mode == PD_CM_MEAN_STACKED ? p.n_modules * (p.rows + p.cols) : 0u);
+}
+
 // Per-call outputs (device pointers).
 struct CallOut {
     pd_hit* hits;
     uint32_t hit_capacity;
     uint32_t* n_hits;
     float* corrected;  // may be null
-    float* cm;         // [n_frames][units_per_frame]; never null here
+    float* cm;         // [n_frames][cm_per_frame]; never null here
 };
 
 // Launchers (pd_chain.cu).  All are asynchronous on `stream` and return the
@@ -54,6 +61,9 @@ cudaError_t launch_stencil(const ChainParams& p, const uint16_t* raw,
                            uint32_t n_frames, uint32_t frame_base,
                            const CallOut& out, cudaStream_t stream);
 size_t cm_select_smem_bytes(const ChainParams& p);
+// The paper's mean estimator, one stage or three stacked (pd_cm_mean.cu).
+cudaError_t launch_cm_mean(const ChainParams& p, const uint16_t* raw, uint32_t n_frames,
+                           float* cm, cudaStream_t stream);
 
 int device_sm_count();
 
@@ -66,9 +76,9 @@ cudaError_t launch_gather(const ChainParams& p, const uint16_t* raw, uint32_t fr
 int internal_fail(int code, const char* why);
 int internal_check_process_args(const pd_ctx* ctx, const uint16_t* frames, uint32_t n_frames,
                                 const pd_outputs* out, const char** why);
-uint32_t internal_units_per_frame(const pd_ctx* ctx);
+uint32_t internal_cm_per_frame(const pd_ctx* ctx);
 // The chain on `stream` only (no second stream), with caller-provided
-// common-mode storage of n_frames * units_per_frame floats.
+// common-mode storage of n_frames * cm_per_frame floats.
 int internal_run_sequential(pd_ctx* ctx, const uint16_t* frames, uint32_t n_frames,
                             uint32_t frame_base, const pd_outputs* out, float* cm,
                             cudaStream_t stream);

@@ -269,7 +269,8 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ gr,
 
 // 5x5 patch of e / photon_kev around each hit's seed (zero outside the
 // module): e recomputed exactly as the chain does, with the call's common
-// mode cm[frame - frame_base][unit].
+// mode of frame - frame_base (unit term, and for the stacked mean the module
+// row and column terms).
 __global__ void gather_kernel(pd::ChainParams p, const uint16_t* __restrict__ raw,
                               uint32_t frame_base, const float* __restrict__ cm,
                               const pd_hit* __restrict__ hits, uint32_t n,
@@ -287,8 +288,13 @@ __global__ void gather_kernel(pd::ChainParams p, const uint16_t* __restrict__ ra
         const uint32_t unit = m * p.units_per_module +
                               ((uint32_t)r / p.unit_rows) * p.units_per_row + (uint32_t)c / p.unit_cols;
         const float d = __fsub_rn(__uint2float_rn(raw[(size_t)f * p.frame_px + g]), p.ped[g]);
-        const float e = __fmul_rn(__fsub_rn(d, cm[(size_t)f * p.units_per_frame + unit]),
-                                  p.inv_gain[g]);
+        const float* cmf = cm + (size_t)f * cm_per_frame(p);
+        float cc = __fsub_rn(d, cmf[unit]);
+        if (p.cm_mode == PD_CM_MEAN_STACKED)
+            cc = __fsub_rn(__fsub_rn(cc, cmf[p.units_per_frame + (size_t)m * p.rows + r]),
+                           cmf[p.units_per_frame + (size_t)p.n_modules * p.rows +
+                               (size_t)m * p.cols + c]);
+        const float e = __fmul_rn(cc, p.inv_gain[g]);
         v = __fdiv_rn(e, p.photon_kev);
     }
     patches[(size_t)h * NPOS + lane] = v;

@@ -60,10 +60,10 @@ extern "C" int pd_process_noalloc(pd_ctx* ctx, const uint16_t* frames_dev, uint3
     if (rc) return pd::internal_fail(rc, why);
     float* cm = out->cm;
     if (!cm) {
-        const uint64_t need = (uint64_t)n_frames * pd::internal_units_per_frame(ctx);
+        const uint64_t need = (uint64_t)n_frames * pd::internal_cm_per_frame(ctx);
         if (need > kNoAllocMaxCm)
             return pd::internal_fail(PD_EINVAL,
-                                     "pd_process_noalloc: n_frames * units_per_frame exceeds "
+                                     "pd_process_noalloc: n_frames * cm_values_per_frame exceeds "
                                      "PD_NOALLOC_MAX_CM; split the call or pass out->cm");
         rc = scratch_address(&cm, &why);
         if (rc) return pd::internal_fail(rc, why);

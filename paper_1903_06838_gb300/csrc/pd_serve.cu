@@ -476,7 +476,7 @@ int pd_server_create(pd_ctx* const* ctxs, uint32_t n_geometries, const pd_serve_
         }
         slot_bytes += (size_t)cfg->max_batch_frames *
                       ((size_t)info.pixels_per_frame * 2 + (size_t)cfg->hits_per_frame * sizeof(pd_hit) +
-                       (size_t)info.units_per_frame * 4);
+                       (size_t)info.cm_values_per_frame * 4);
     }
     // device_budget = 0: the free device memory now, less 1 GiB of headroom
     uint64_t budget = cfg->device_budget;
@@ -533,7 +533,7 @@ int pd_server_create(pd_ctx* const* ctxs, uint32_t n_geometries, const pd_serve_
         for (uint32_t g = 0; g < n_geometries && ok; g++) {
             pd_info info{};
             pd_query(ctxs[g], &info);
-            cm_vals += (uint64_t)cfg->max_batch_frames * info.units_per_frame;
+            cm_vals += (uint64_t)cfg->max_batch_frames * info.cm_values_per_frame;
             uint16_t* f = nullptr;
             pd_hit* dh = nullptr;
             uint32_t* dn = nullptr;

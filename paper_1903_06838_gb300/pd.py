@@ -20,8 +20,8 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_PKG, "libpd.so")
-SOURCES = ["pd_api.cu", "pd_chain.cu", "pd_eta.cu", "pd_fast.cu", "pd_fused.cu",
-           "pd_noalloc.cu", "pd_net.cu", "pd_net_tc.cu", "pd_serve.cu"]
+SOURCES = ["pd_api.cu", "pd_chain.cu", "pd_cm_mean.cu", "pd_eta.cu", "pd_fast.cu",
+           "pd_fused.cu", "pd_noalloc.cu", "pd_net.cu", "pd_net_tc.cu", "pd_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
@@ -33,7 +33,7 @@ _lib = None
 # ---- public constants (mirror include/pd.h) -------------------------------
 PD_OK, PD_EINVAL, PD_EALIGN, PD_ENOMEM, PD_EOVERFLOW = 0, 1, 2, 3, 4
 PD_ETIMEDOUT, PD_ECUDA, PD_ENOTSUP, PD_EBUSY = 5, 6, 7, 8
-PD_CM_MEDIAN, PD_CM_NONE = 0, 1
+PD_CM_MEDIAN, PD_CM_NONE, PD_CM_MEAN, PD_CM_MEAN_STACKED = 0, 1, 2, 3
 PD_HIT_EDGE, PD_HIT_SATURATED, PD_HIT_LEARNED, PD_HIT_LINEARISED = 1, 2, 4, 8
 PD_MAX_ETA_BINS = 4095
 PD_MAX_HIST_BINS = 4096
@@ -67,7 +67,7 @@ class PdOutputs(ctypes.Structure):
 class PdInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
                 ("pixels_per_frame", "units_per_frame", "unit_pixels",
-                 "cm_min_count", "hist_bins", "masked_pixels")]
+                 "cm_min_count", "hist_bins", "masked_pixels", "cm_values_per_frame")]
 
 
 class PdProfile(ctypes.Structure):
@@ -276,6 +276,10 @@ class Context:
     @property
     def units_per_frame(self) -> int:
         return self.info.units_per_frame
+
+    @property
+    def cm_values_per_frame(self) -> int:
+        return self.info.cm_values_per_frame
 
     def close(self):
         if self.handle:
@@ -761,7 +765,7 @@ class Outputs:
         self.corrected = torch.empty((n_frames, ctx.pixels_per_frame),
                                      dtype=torch.float32, device=device) \
             if corrected else None
-        self.cm = torch.empty((n_frames, ctx.units_per_frame),
+        self.cm = torch.empty((n_frames, ctx.cm_values_per_frame),
                               dtype=torch.float32, device=device) if cm else None
 
     def ptrs(self):
