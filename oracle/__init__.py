@@ -33,6 +33,38 @@ CM_MEDIAN, CM_NONE, CM_MEAN, CM_MEAN_STACKED = 0, 1, 2, 3
 HIT_EDGE, HIT_SATURATED = 1, 2
 
 
+MAX_FEATURES = 8
+
+
+class Filters(ctypes.Structure):
+    """Matched-filter bank: per feature 4 x 5 filters F0, F1, F1dx, F1dy and
+    the threshold F1Nmin (Figs. d-f)."""
+    _fields_ = [("n_features", ctypes.c_uint32),
+                ("f0", ctypes.c_float * 20 * MAX_FEATURES),
+                ("f1", ctypes.c_float * 20 * MAX_FEATURES),
+                ("f1_dx", ctypes.c_float * 20 * MAX_FEATURES),
+                ("f1_dy", ctypes.c_float * 20 * MAX_FEATURES),
+                ("f1_nmin", ctypes.c_float * MAX_FEATURES)]
+
+
+def filters(f0, f1, f1_dx, f1_dy, f1_nmin) -> Filters:
+    """Bank from arrays [F][4][5] (and [F] thresholds)."""
+    f0, f1, fdx, fdy = (np.asarray(a, np.float32).reshape(-1, 4, 5)
+                        for a in (f0, f1, f1_dx, f1_dy))
+    nmin = np.asarray(f1_nmin, np.float32).reshape(-1)
+    nf = f1.shape[0]
+    fb = Filters()
+    fb.n_features = nf
+    for name, a in (("f0", f0), ("f1", f1), ("f1_dx", fdx), ("f1_dy", fdy)):
+        dst = np.zeros((MAX_FEATURES, 20), np.float32)
+        dst[:nf] = a.reshape(nf, 20)
+        ctypes.memmove(getattr(fb, name), dst.ctypes.data, dst.nbytes)
+    dst = np.zeros(MAX_FEATURES, np.float32)
+    dst[:nf] = nmin
+    ctypes.memmove(fb.f1_nmin, dst.ctypes.data, dst.nbytes)
+    return fb
+
+
 class Geometry(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
                 ("n_modules", "rows", "cols", "unit_rows", "unit_cols",
@@ -70,6 +102,11 @@ def _load():
             ctypes.c_uint32, ctypes.c_uint32, vp, ctypes.c_uint32, vp, vp, vp,
             vp, vp, vp, vp]
         lib.oracle_process.restype = ctypes.c_int
+        lib.oracle_process_matched.argtypes = [
+            ctypes.POINTER(Geometry), ctypes.POINTER(Thresholds), ctypes.POINTER(Filters),
+            vp, vp, vp, ctypes.c_uint32, ctypes.c_uint32, vp, ctypes.c_uint32, vp, vp, vp,
+            vp, vp, vp, vp]
+        lib.oracle_process_matched.restype = ctypes.c_int
         lib.oracle_lower_median.argtypes = [vp, ctypes.c_uint32]
         lib.oracle_lower_median.restype = ctypes.c_float
         lib.oracle_default_min_count.argtypes = [ctypes.c_uint32]
@@ -128,8 +165,9 @@ class Result:
 
 def process(geom: Geometry, thr: Thresholds, ped, gain, raw, *, frame_base=0,
             want_corrected=False, want_cm=True, hit_capacity=None,
-            count_map=None, hist_pix=None, hist_hit=None) -> Result:
-    """Run the oracle.  raw: uint16 [n, modules, rows, cols] (or flat)."""
+            count_map=None, hist_pix=None, hist_hit=None, filters=None) -> Result:
+    """Run the oracle.  raw: uint16 [n, modules, rows, cols] (or flat).
+    filters: a Filters bank selects the matched-filter charge summing."""
     lib = _load()
     ped = np.ascontiguousarray(ped, np.float32).reshape(-1)
     gain = np.ascontiguousarray(gain, np.float32).reshape(-1)
@@ -147,14 +185,15 @@ def process(geom: Geometry, thr: Thresholds, ped, gain, raw, *, frame_base=0,
     hh = hist_hit if hist_hit is not None else np.zeros(thr.hist_bins, np.uint64)
     corr = np.zeros((n, fpx), np.float32) if want_corrected else None
     cm = np.zeros((n, upf), np.float32) if want_cm else None
-    rc = lib.oracle_process(ctypes.byref(geom), ctypes.byref(thr),
-                            ped.ctypes.data, gain.ctypes.data, raw.ctypes.data,
-                            n, frame_base, hits.ctypes.data, cap,
-                            ctypes.byref(nh), cmap.ctypes.data, hp.ctypes.data,
-                            hh.ctypes.data,
-                            corr.ctypes.data if corr is not None else None,
-                            cm.ctypes.data if cm is not None else None,
-                            ctypes.byref(ns))
+    rest = (ped.ctypes.data, gain.ctypes.data, raw.ctypes.data, n, frame_base,
+            hits.ctypes.data, cap, ctypes.byref(nh), cmap.ctypes.data, hp.ctypes.data,
+            hh.ctypes.data, corr.ctypes.data if corr is not None else None,
+            cm.ctypes.data if cm is not None else None, ctypes.byref(ns))
+    if filters is None:
+        rc = lib.oracle_process(ctypes.byref(geom), ctypes.byref(thr), *rest)
+    else:
+        rc = lib.oracle_process_matched(ctypes.byref(geom), ctypes.byref(thr),
+                                        ctypes.byref(filters), *rest)
     if rc:
         raise ValueError("oracle rejected the geometry or thresholds")
     k = min(nh.value, cap)

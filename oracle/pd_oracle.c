@@ -70,6 +70,28 @@
  *     (each rounded to nearest once; fmaf rounds once), clipped to
  *     [0, bins-1].
  *
+ * Matched filters (oracle_process_matched; section "Photon Charge
+ * Summing", Figs. d and e; section "Photon Subpixel Resolution", Fig. f).
+ * Steps 6.-8. are replaced by the paper's filter model, with a filter bank
+ * supplied by the caller (the paper prints its values only as a picture).
+ * Each of the bank's F features has four 4 x 5 filters F0, F1, F1dx, F1dy
+ * and a threshold F1Nmin.  A filter is applied at pixel (r, c) as TF's
+ * conv2d with "SAME" padding does for a 4 x 5 kernel: tap (i, j) meets the
+ * pixel (r + i - 1, c + j - 2), zero outside the module; the taps are
+ * accumulated row-major from 0.0f, each term a product.  With T = (s > 0)
+ * (the "Signal?" mask; s > 0 iff e > zero_thr since zero_thr >= 0):
+ *     Size_f     = sum T * F1_f        Droplet_f = sum s * F1_f
+ *     Overflow_f = sum T * F0_f        Mx_f = sum s * F1dx_f,  My_f likewise
+ *     Valid_f    = (Overflow_f == 0) and (Size_f >= F1Nmin_f)
+ * and, over the valid features in order,
+ *     E  = sum Droplet_f                        (Frames3)
+ *     dx = sum Mx_f / Droplet_f,  dy = sum My_f / Droplet_f
+ * where a feature whose Droplet_f is 0 adds nothing to dx, dy.  A pixel
+ * with a valid feature and E != 0 counts as a seed (hist_hit[bin(E)]); its
+ * count is n = rint(E / photon_kev) as in 7., a hit iff n >= 1, with npix
+ * the number of signal pixels under the nonzero taps of the first valid
+ * feature's F1.
+ *
  * Inputs must be finite (pedestal finite; non-finite gains are masked).
  */
 #include <math.h>
@@ -97,6 +119,29 @@ typedef struct {
 
 enum { OG_CM_MEDIAN = 0, OG_CM_NONE = 1, OG_CM_MEAN = 2, OG_CM_MEAN_STACKED = 3 };
 enum { OG_EDGE = 1, OG_SATURATED = 2 };
+
+#define OG_MAX_FEATURES 8
+typedef struct {
+    uint32_t n_features;
+    float f0[OG_MAX_FEATURES][4][5];
+    float f1[OG_MAX_FEATURES][4][5];
+    float f1_dx[OG_MAX_FEATURES][4][5];
+    float f1_dy[OG_MAX_FEATURES][4][5];
+    float f1_nmin[OG_MAX_FEATURES];
+} og_filters;
+
+static int filters_ok(const og_filters* fb) {
+    if (fb->n_features < 1 || fb->n_features > OG_MAX_FEATURES) return 0;
+    for (uint32_t f = 0; f < fb->n_features; f++) {
+        if (isnan(fb->f1_nmin[f])) return 0;
+        for (int i = 0; i < 4; i++)
+            for (int j = 0; j < 5; j++)
+                if (!isfinite(fb->f0[f][i][j]) || !isfinite(fb->f1[f][i][j]) ||
+                    !isfinite(fb->f1_dx[f][i][j]) || !isfinite(fb->f1_dy[f][i][j]))
+                    return 0;
+    }
+    return 1;
+}
 
 /* The 32-bit pattern of a float mapped so that unsigned comparison of the
  * keys is the ascending IEEE order with -0 below +0. */
@@ -212,12 +257,83 @@ int oracle_check(const og_geometry* g, const og_thresholds* t) {
  *               or NULL
  * Returns 0, or 1 on invalid input.
  */
+static int process_impl(const og_geometry* g, const og_thresholds* t,
+                        const og_filters* fb, const float* ped, const float* gain,
+                        const uint16_t* raw, uint32_t n_frames, uint32_t frame_base,
+                        og_hit* hits, uint32_t cap, uint32_t* n_hits, uint32_t* count_map,
+                        uint64_t* hist_pix, uint64_t* hist_hit, float* corrected,
+                        float* cm_out, uint64_t* n_seeds);
+
 int oracle_process(const og_geometry* g, const og_thresholds* t,
                    const float* ped, const float* gain, const uint16_t* raw,
                    uint32_t n_frames, uint32_t frame_base, og_hit* hits,
                    uint32_t cap, uint32_t* n_hits, uint32_t* count_map,
                    uint64_t* hist_pix, uint64_t* hist_hit, float* corrected,
                    float* cm_out, uint64_t* n_seeds) {
+    return process_impl(g, t, NULL, ped, gain, raw, n_frames, frame_base, hits, cap, n_hits,
+                        count_map, hist_pix, hist_hit, corrected, cm_out, n_seeds);
+}
+
+/* The chain with the matched-filter charge summing of the bank fb. */
+int oracle_process_matched(const og_geometry* g, const og_thresholds* t,
+                           const og_filters* fb, const float* ped, const float* gain,
+                           const uint16_t* raw, uint32_t n_frames, uint32_t frame_base,
+                           og_hit* hits, uint32_t cap, uint32_t* n_hits,
+                           uint32_t* count_map, uint64_t* hist_pix, uint64_t* hist_hit,
+                           float* corrected, float* cm_out, uint64_t* n_seeds) {
+    if (!fb || !filters_ok(fb)) return 1;
+    return process_impl(g, t, fb, ped, gain, raw, n_frames, frame_base, hits, cap, n_hits,
+                        count_map, hist_pix, hist_hit, corrected, cm_out, n_seeds);
+}
+
+/* The matched-filter model at pixel (r, c) of a module's zeroed signal s
+ * (R x C).  Returns 1 when a feature is valid; fills E, dx, dy, npix. */
+static int matched_at(const og_filters* fb, const float* s, uint32_t R, uint32_t C,
+                      uint32_t r, uint32_t c, float* E_out, float* dx_out, float* dy_out,
+                      uint32_t* npix_out) {
+    float E = 0.0f, dx = 0.0f, dy = 0.0f;
+    uint32_t npix = 0;
+    int any = 0;
+    for (uint32_t f = 0; f < fb->n_features; f++) {
+        float size = 0.0f, over = 0.0f, drop = 0.0f, mx = 0.0f, my = 0.0f;
+        uint32_t under = 0;
+        for (int i = 0; i < 4; i++) {
+            for (int j = 0; j < 5; j++) {
+                const long rr = (long)r + i - 1, cc = (long)c + j - 2;
+                float sv = 0.0f;
+                if (rr >= 0 && rr < (long)R && cc >= 0 && cc < (long)C)
+                    sv = s[(size_t)rr * C + cc];
+                const float tv = sv > 0.0f ? 1.0f : 0.0f;
+                size = size + tv * fb->f1[f][i][j];
+                over = over + tv * fb->f0[f][i][j];
+                drop = drop + sv * fb->f1[f][i][j];
+                mx = mx + sv * fb->f1_dx[f][i][j];
+                my = my + sv * fb->f1_dy[f][i][j];
+                if (sv > 0.0f && fb->f1[f][i][j] != 0.0f) under++;
+            }
+        }
+        if (!(over == 0.0f && size >= fb->f1_nmin[f])) continue;
+        if (!any) npix = under;
+        any = 1;
+        E = E + drop;
+        if (drop != 0.0f) {
+            dx = dx + mx / drop;
+            dy = dy + my / drop;
+        }
+    }
+    *E_out = E;
+    *dx_out = dx;
+    *dy_out = dy;
+    *npix_out = npix;
+    return any;
+}
+
+static int process_impl(const og_geometry* g, const og_thresholds* t,
+                        const og_filters* fb, const float* ped, const float* gain,
+                        const uint16_t* raw, uint32_t n_frames, uint32_t frame_base,
+                        og_hit* hits, uint32_t cap, uint32_t* n_hits, uint32_t* count_map,
+                        uint64_t* hist_pix, uint64_t* hist_hit, float* corrected,
+                        float* cm_out, uint64_t* n_seeds) {
     if (oracle_check(g, t)) return 1;
     const uint32_t R = g->rows, C = g->cols;
     const size_t mpx = (size_t)R * C;
@@ -332,7 +448,39 @@ int oracle_process(const og_geometry* g, const og_thresholds* t,
                 }
             }
             /* 6.-9. seeds, charge sum, count, centroid, summaries */
-            for (uint32_t r = 0; r < R; r++) {
+            for (uint32_t r = 0; fb && r < R; r++) {
+                for (uint32_t c = 0; c < C; c++) {
+                    float E, dxm, dym;
+                    uint32_t npix;
+                    if (!matched_at(fb, s, R, C, r, c, &E, &dxm, &dym, &npix)) continue;
+                    if (E == 0.0f) continue;
+                    ns++;
+                    hist_hit[bin_of(E, lo_s, inv_w, t->hist_bins)]++;
+                    const float qr = nearbyintf(E / t->photon_kev);
+                    uint32_t n;
+                    uint16_t flags = 0;
+                    if (!(qr >= 0.0f)) n = 0;
+                    else if (qr > 255.0f) { n = 255; flags |= OG_SATURATED; }
+                    else n = (uint32_t)qr;
+                    if (n < 1) continue;
+                    if (r == 0 || c == 0 || r == R - 1 || c == C - 1) flags |= OG_EDGE;
+                    const uint32_t pix = (uint32_t)(base + (size_t)r * C + c);
+                    count_map[pix] += n;
+                    if (nh < cap) {
+                        og_hit* h = &hits[nh];
+                        h->frame = frame_base + f;
+                        h->pixel = pix;
+                        h->energy_kev = E;
+                        h->dx = dxm;
+                        h->dy = dym;
+                        h->count = (uint8_t)n;
+                        h->npix = (uint8_t)(npix > 255 ? 255 : npix);
+                        h->flags = flags;
+                    }
+                    nh++;
+                }
+            }
+            for (uint32_t r = 0; !fb && r < R; r++) {
                 for (uint32_t c = 0; c < C; c++) {
                     const size_t p = (size_t)r * C + c;
                     const float sp = s[p];
