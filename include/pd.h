@@ -111,6 +111,34 @@ typedef struct {
 
 #define PD_MAX_HIST_BINS 4096u
 
+/* Matched-filter charge summing (section "Photon Charge Summing", Figs. d
+ * and e; centroids: section "Photon Subpixel Resolution", Fig. f).  A bank
+ * of n_features features, each with four 4 x 5 filters and a threshold.
+ * Filter tap [i][j] applied at pixel (r, c) meets pixel (r + i - 1,
+ * c + j - 2) of the same module (zero outside): TF's conv2d "SAME"
+ * alignment of a 4 x 5 kernel.  With s the zeroed signal (Fig. e "Signal")
+ * and T = (s > 0), at every pixel and for each feature f:
+ *   Size = sum T * f1   Droplet = sum s * f1   Overflow = sum T * f0
+ *   Mx = sum s * f1_dx  My = sum s * f1_dy     (taps row-major from 0.0f)
+ *   Valid = Overflow == 0 && Size >= f1_nmin
+ * and over the valid features in order E = sum Droplet (Frames3),
+ * dx = sum Mx / Droplet, dy = sum My / Droplet (features whose Droplet is
+ * 0 add nothing to dx, dy).  A pixel with a valid feature and E != 0 is a
+ * seed (hist_hit[bin(E)]); n = rint(E / photon_kev) clamped to 255 as in
+ * the default chain, a hit iff n >= 1, npix = signal pixels under the
+ * nonzero f1 taps of the first valid feature, flags as in the default
+ * chain.  The paper gives its bank's values only as a picture; the bank is
+ * the caller's.  All values finite, f1_nmin not NaN. */
+#define PD_MAX_FEATURES 8u
+typedef struct {
+    uint32_t n_features;  /* 1 .. PD_MAX_FEATURES */
+    float f0[PD_MAX_FEATURES][4][5];    /* overflow ring: must see no signal */
+    float f1[PD_MAX_FEATURES][4][5];    /* footprint: size and droplet      */
+    float f1_dx[PD_MAX_FEATURES][4][5]; /* column offsets for the centroid  */
+    float f1_dy[PD_MAX_FEATURES][4][5]; /* row offsets for the centroid     */
+    float f1_nmin[PD_MAX_FEATURES];     /* minimum Size of a valid match    */
+} pd_filter_bank;
+
 /* One photon hit (24 bytes).  pixel = module*rows*cols + row*cols + col of
  * the seed; dx, dy are the charge centre of mass in pixel pitches relative
  * to the seed pixel centre (Fig. f), so the position is
@@ -201,6 +229,15 @@ int pd_process(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frames,
 #define PD_NOALLOC_MAX_CM (1u << 20)
 int pd_process_noalloc(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frames,
                        uint32_t frame_base, const pd_outputs* out, void* stream);
+
+/* pd_set_filter_bank — replace the 3x3 local-maximum charge summing of
+ * this context (steps of section "Photon Charge Summing" as the default
+ * chain reads them) by the matched filters of `bank` (copied; host memory),
+ * or restore the default with bank == NULL.  Synchronises the device; do
+ * not call while work of this context is in flight.  The one-kernel chain
+ * and the mixed batch launch are not used with a bank.  PD_EINVAL for a
+ * feature count out of range or a non-finite value. */
+int pd_set_filter_bank(pd_ctx* ctx, const pd_filter_bank* bank);
 
 /* pd_process_host — the same chain on host-resident frames.  Copies the
  * frames to the device in chunks (pipelined on two internal streams, so

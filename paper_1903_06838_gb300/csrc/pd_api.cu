@@ -48,6 +48,8 @@ struct pd_ctx {
     bool use_fused = false;     // the geometry allows the one-kernel chain
     uint32_t two_pass = 1;      // 1: common-mode and stencil kernels (measured
                                 // faster on GB300 so far); 0: the one-kernel chain
+    bool matched = false;       // matched-filter charge summing (pd_set_filter_bank)
+    pd::MatchedBank* d_bank = nullptr;
     uint32_t chunk_frames = 1;  // frames per common-mode/stencil launch pair
     uint32_t overlap = 1;       // common mode of chunk c+1 beside stencil of c
     cudaStream_t aux = nullptr; // second stream of the chunk pipeline
@@ -186,6 +188,7 @@ void free_ctx(pd_ctx* c) {
     cudaFree(c->d_hist_pix);
     cudaFree(c->d_hist_hit);
     cudaFree(c->d_cm);
+    cudaFree(c->d_bank);
     cudaFree(c->d_stage[0]);
     cudaFree(c->d_stage[1]);
     cudaFree(c->d_host_hits);
@@ -206,6 +209,17 @@ void free_ctx(pd_ctx* c) {
     }
     for (auto e : c->spare) cudaEventDestroy(e);
     delete c;
+}
+
+// The one-kernel chain replaces the kernel pair.
+bool fused_on(const pd_ctx* c) { return c->use_fused && !c->two_pass && !c->matched; }
+
+// The charge-summing launch of a context (after its common mode).
+cudaError_t launch_stencil_for(const pd_ctx* c, const uint16_t* fr, uint32_t nf,
+                               uint32_t frame_base, const pd::CallOut& co, cudaStream_t s) {
+    if (c->matched) return pd::launch_matched(c->params, c->d_bank, fr, nf, frame_base, co, s);
+    return c->use_band ? pd::launch_stencil_band(c->params, c->band_cfg, fr, nf, frame_base, co, s)
+                       : pd::launch_stencil(c->params, fr, nf, frame_base, co, s);
 }
 
 // The common-mode launch(es) of a context for nf frames into cm.
@@ -239,7 +253,7 @@ int run_chain(pd_ctx* c, const uint16_t* frames, uint32_t n_frames, uint32_t fra
     if (zero && (e = cudaMemsetAsync(out->n_hits, 0, sizeof(uint32_t), s)) != cudaSuccess)
         return fail_cuda(e, "zero n_hits");
     if (n_frames == 0) return PD_OK;
-    if (c->use_fused && !c->two_pass) {
+    if (fused_on(c)) {
         pd::CallOut co{out->hits, out->hit_capacity, out->n_hits, out->corrected, out->cm};
         ProfileScope ps(c, 2, s);
         e = pd::launch_fused(c->params, c->fused_cfg, frames, n_frames, frame_base, co, s);
@@ -284,9 +298,7 @@ int run_chain(pd_ctx* c, const uint16_t* frames, uint32_t n_frames, uint32_t fra
                        cmc};
         {
             ProfileScope ps(c, 1, s);
-            e = c->use_band ? pd::launch_stencil_band(c->params, c->band_cfg, fr, nf,
-                                                      frame_base + done, co, s)
-                            : pd::launch_stencil(c->params, fr, nf, frame_base + done, co, s);
+            e = launch_stencil_for(c, fr, nf, frame_base + done, co, s);
         }
         if (e != cudaSuccess) return fail_cuda(e, "stencil kernel launch");
         if (two && (e = cudaEventRecord(c->ev_st[k & 1], s)))
@@ -331,7 +343,7 @@ int internal_run_sequential(pd_ctx* c, const uint16_t* frames, uint32_t n_frames
                             cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(out->n_hits, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return fail_cuda(e, "zero n_hits");
-    if (c->use_fused && !c->two_pass) {
+    if (fused_on(c)) {
         CallOut co{out->hits, out->hit_capacity, out->n_hits, out->corrected, out->cm};
         e = launch_fused(c->params, c->fused_cfg, frames, n_frames, frame_base, co, s);
         return e == cudaSuccess ? PD_OK : fail_cuda(e, "chain kernel launch");
@@ -346,9 +358,7 @@ int internal_run_sequential(pd_ctx* c, const uint16_t* frames, uint32_t n_frames
                    out->corrected ? out->corrected + (size_t)done * c->params.frame_px
                                   : nullptr,
                    cmc};
-        e = c->use_band ? launch_stencil_band(c->params, c->band_cfg, fr, nf, frame_base + done,
-                                              co, s)
-                        : launch_stencil(c->params, fr, nf, frame_base + done, co, s);
+        e = launch_stencil_for(c, fr, nf, frame_base + done, co, s);
         if (e != cudaSuccess) return fail_cuda(e, "stencil kernel launch");
         done += nf;
     }
@@ -624,6 +634,27 @@ int pd_get_summary(pd_ctx* c, uint32_t* count_map_host, uint64_t* hist_pix_host,
     return PD_OK;
 }
 
+int pd_set_filter_bank(pd_ctx* c, const pd_filter_bank* bank) {
+    if (!c) return fail(PD_EINVAL, "NULL context");
+    pd::MatchedBank mb{};
+    if (bank && !pd::compile_bank(*bank, &mb))
+        return fail(PD_EINVAL, "filter bank: 1..PD_MAX_FEATURES features, finite values");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail_cuda(e, "synchronise before a bank change");
+    if (!bank) {
+        c->matched = false;
+        return PD_OK;
+    }
+    if (!c->d_bank && (e = cudaMalloc(&c->d_bank, sizeof(pd::MatchedBank))) != cudaSuccess) {
+        c->d_bank = nullptr;
+        return fail(PD_ENOMEM, "filter bank allocation failed");
+    }
+    if ((e = cudaMemcpy(c->d_bank, &mb, sizeof(mb), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail_cuda(e, "filter bank upload");
+    c->matched = true;
+    return PD_OK;
+}
+
 int pd_reset_summary(pd_ctx* c, void* stream) {
     if (!c) return fail(PD_EINVAL, "NULL context");
     cudaStream_t s = (cudaStream_t)stream;
@@ -640,7 +671,7 @@ int pd_get_tuning(const pd_ctx* c, pd_tuning* t) {
     t->chunk_frames = c->chunk_frames;
     t->band_rows = c->use_band ? c->band_cfg.rb : 0;
     t->overlap = c->overlap;
-    t->two_pass = c->use_fused ? c->two_pass : 1;
+    t->two_pass = c->use_fused && !c->matched ? c->two_pass : 1;
     return PD_OK;
 }
 
@@ -792,6 +823,8 @@ int batch_check_items(const pd_batch* b, const pd_batch_item* items, uint32_t n)
         if (rc) return fail(rc, why);
         if (b->mixed && !it.ctx->use_band)
             return fail(PD_ENOTSUP, "batch: the mixed launch needs the band stencil");
+        if (b->mixed && it.ctx->matched)
+            return fail(PD_ENOTSUP, "batch: the mixed launch has no matched filters");
         if (b->mixed && it.ctx->params.cm_mode >= PD_CM_MEAN)
             return fail(PD_ENOTSUP, "batch: the mixed launch computes the median only");
     }
@@ -803,12 +836,11 @@ int batch_check_items(const pd_batch* b, const pd_batch_item* items, uint32_t n)
 // the hit counter.
 cudaError_t launch_chain_piece(pd_ctx* c, const uint16_t* fr, uint32_t nf, uint32_t frame_base,
                                const pd::CallOut& co, cudaStream_t s) {
-    if (c->use_fused && !c->two_pass)
+    if (fused_on(c))
         return pd::launch_fused(c->params, c->fused_cfg, fr, nf, frame_base, co, s);
     cudaError_t e = launch_cm(c, fr, nf, co.cm, s);
     if (e != cudaSuccess) return e;
-    return c->use_band ? pd::launch_stencil_band(c->params, c->band_cfg, fr, nf, frame_base, co, s)
-                       : pd::launch_stencil(c->params, fr, nf, frame_base, co, s);
+    return launch_stencil_for(c, fr, nf, frame_base, co, s);
 }
 
 int batch_enqueue(pd_batch* b, int slot, const pd_batch_item* items, uint32_t n,
@@ -1055,7 +1087,7 @@ int pd_autotune(pd_ctx* c, const uint16_t* frames_dev, uint32_t n_frames, pd_tun
             if (std::find(chunks.begin(), chunks.end(), cf) == chunks.end()) chunks.push_back(cf);
         }
         std::vector<uint32_t> bands = {0};
-        if (c->use_band) {
+        if (c->use_band && !c->matched) {
             const uint32_t rb = c->band_cfg.rb;
             for (uint32_t v : {rb / 2, rb * 3 / 2, rb * 2})
                 if (v >= 2 && v != rb) bands.push_back(v);
@@ -1065,7 +1097,7 @@ int pd_autotune(pd_ctx* c, const uint16_t* frames_dev, uint32_t n_frames, pd_tun
         o.hit_capacity = cap;
         o.n_hits = nh;
         std::vector<pd_tuning> cands;
-        if (c->use_fused) cands.push_back(pd_tuning{orig.chunk_frames, orig.band_rows, 1, 0});
+        if (c->use_fused && !c->matched) cands.push_back(pd_tuning{orig.chunk_frames, orig.band_rows, 1, 0});
         for (uint32_t cf : chunks)
             for (uint32_t bd : bands)
                 for (uint32_t ov : {1u, 0u}) cands.push_back(pd_tuning{cf, bd ? bd : orig.band_rows, ov, 1});

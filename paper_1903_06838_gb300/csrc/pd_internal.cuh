@@ -44,6 +44,21 @@ __host__ __device__ inline uint32_t cm_per_frame(const ChainParams& p) {
            (p.cm_mode == PD_CM_MEAN_STACKED ? p.n_modules * (p.rows + p.cols) : 0u);
 }
 
+// A matched-filter bank compiled to lists of nonzero taps (pd_matched.cu).
+// `at` is the tap's offset in the kernel's shared tile: i * 68 + j.
+struct MatchedTap {
+    uint16_t at, pad;
+    float v;
+};
+struct MatchedBank {
+    uint32_t n_features;
+    float nmin[PD_MAX_FEATURES];
+    uint16_t off1[PD_MAX_FEATURES + 1], off0[PD_MAX_FEATURES + 1];
+    uint16_t offx[PD_MAX_FEATURES + 1], offy[PD_MAX_FEATURES + 1];
+    MatchedTap t1[PD_MAX_FEATURES * 20], t0[PD_MAX_FEATURES * 20];
+    MatchedTap tx[PD_MAX_FEATURES * 20], ty[PD_MAX_FEATURES * 20];
+};
+
 // Per-call outputs (device pointers).
 struct CallOut {
     pd_hit* hits;
@@ -61,6 +76,11 @@ cudaError_t launch_stencil(const ChainParams& p, const uint16_t* raw,
                            uint32_t n_frames, uint32_t frame_base,
                            const CallOut& out, cudaStream_t stream);
 size_t cm_select_smem_bytes(const ChainParams& p);
+// Matched-filter stencil (pd_matched.cu); compile_bank validates.
+bool compile_bank(const pd_filter_bank& bank, MatchedBank* out);
+cudaError_t launch_matched(const ChainParams& p, const MatchedBank* bank_dev,
+                           const uint16_t* raw, uint32_t n_frames, uint32_t frame_base,
+                           const CallOut& out, cudaStream_t stream);
 // The paper's mean estimator, one stage or three stacked (pd_cm_mean.cu).
 cudaError_t launch_cm_mean(const ChainParams& p, const uint16_t* raw, uint32_t n_frames,
                            float* cm, cudaStream_t stream);

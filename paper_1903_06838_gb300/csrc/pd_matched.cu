@@ -1,0 +1,282 @@
+// pd_matched.cu — charge summing with the paper's matched filters.
+//
+// Section "Photon Charge Summing" (Figs. d, e) and section "Photon Subpixel
+// Resolution" (Fig. f).  With T = (s > 0) the signal mask and s the zeroed
+// signal, each feature f of the bank has four 4 x 5 filters F0, F1, F1dx,
+// F1dy and a threshold F1Nmin:
+//     Size_f = T * F1     Droplet_f = s * F1     Overflow_f = T * F0
+//     Mx_f = s * F1dx     My_f = s * F1dy
+//     Valid_f = (Overflow_f == 0) and (Size_f >= F1Nmin_f)
+// and a pixel's energy is the sum of its valid droplets in feature order,
+// its centroid the sum of Mx_f / Droplet_f (My_f / Droplet_f) over the valid
+// features whose droplet is not 0.  A filter tap (i, j) applied at (r, c)
+// meets (r + i - 1, c + j - 2), zero outside the module (TF's "SAME"
+// alignment of a 4 x 5 kernel); each sum runs over the taps row-major from
+// 0.0f with products rounded once.
+//
+// The bank is compiled on the host into lists of the nonzero taps.  Skipping
+// a zero tap is exact: its term is +-0, and a sum that starts at +0.0f is
+// never -0 (x + (-x) rounds to +0), so adding +-0 never changes it.  For the
+// same reason a pixel whose 4 x 5 window holds no signal has every Size,
+// Overflow and Droplet equal to 0, so its energy is 0 and it is skipped.
+//
+// matched_kernel: grid-stride over 16 x 64 tiles of (frame, module); the
+// corrected signal of the tile and its halo (one row above, two below, two
+// columns each side) goes to shared memory together with, per halo row and
+// column, whether any of the five columns around carries signal; pixels
+// with a non-empty window evaluate the bank; hits are compacted with a warp
+// ballot and one atomic per warp.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <new>
+
+#include "pd_internal.cuh"
+
+namespace pd {
+
+namespace {
+
+constexpr int kTY = 16, kTX = 64, kThreads = 256;
+constexpr int kHY = kTY + 3, kHX = kTX + 4;
+
+__device__ __forceinline__ uint32_t hist_bin(float v, float neg_lo_s, float inv_w,
+                                             uint32_t bins) {
+    const float t = __fmaf_rn(v, inv_w, neg_lo_s);
+    if (!(t >= 0.0f)) return 0;
+    if (t >= (float)bins) return bins - 1;
+    return (uint32_t)t;
+}
+
+template <bool STACKED>
+__global__ void __launch_bounds__(kThreads)
+    matched_kernel(ChainParams p, const MatchedBank* __restrict__ bank,
+                   const uint16_t* __restrict__ raw, uint32_t frame_base, CallOut out,
+                   uint32_t tiles_y, uint32_t tiles_x, unsigned long long n_tiles) {
+    extern __shared__ uint32_t hsm[];  // [2][hist_bins]
+    __shared__ float tile[kHY][kHX];
+    __shared__ uint8_t rowany[kHY][kTX];  // signal within columns c-2 .. c+2
+    __shared__ MatchedBank sb;
+    uint32_t* hpix = hsm;
+    uint32_t* hhit = hsm + p.hist_bins;
+    for (uint32_t b = threadIdx.x; b < 2 * p.hist_bins; b += kThreads) hsm[b] = 0;
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(bank);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&sb);
+        for (uint32_t k = threadIdx.x; k < sizeof(MatchedBank) / 4; k += kThreads) dst[k] = src[k];
+    }
+    __syncthreads();
+
+    const int R = (int)p.rows, C = (int)p.cols;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nf = sb.n_features;
+    for (unsigned long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        unsigned long long q = t;
+        const int tx = (int)(q % tiles_x);
+        q /= tiles_x;
+        const int ty = (int)(q % tiles_y);
+        q /= tiles_y;
+        const uint32_t m = (uint32_t)(q % p.n_modules);
+        const uint32_t f = (uint32_t)(q / p.n_modules);
+        const int r0 = ty * kTY, c0 = tx * kTX;
+        const size_t mod_base = (size_t)m * p.module_px;
+        const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
+        const float* cmf = out.cm + (size_t)f * cm_per_frame(p) + (size_t)m * p.units_per_module;
+        const float* cmr = out.cm + (size_t)f * cm_per_frame(p) + p.units_per_frame +
+                           (size_t)m * p.rows;
+        const float* cmc = out.cm + (size_t)f * cm_per_frame(p) + p.units_per_frame +
+                           (size_t)p.n_modules * p.rows + (size_t)m * p.cols;
+
+        // 1. zeroed signal of the tile and its halo
+        for (int j = threadIdx.x; j < kHY * kHX; j += kThreads) {
+            const int hr = j / kHX, hc = j % kHX;
+            const int r = r0 + hr - 1, c = c0 + hc - 2;
+            float s = 0.0f;
+            if (r >= 0 && r < R && c >= 0 && c < C) {
+                const uint32_t off = (uint32_t)r * p.cols + (uint32_t)c;
+                const float cm = cmf[((uint32_t)r / p.unit_rows) * p.units_per_row +
+                                     (uint32_t)c / p.unit_cols];
+                const float d = __fsub_rn(__uint2float_rn(fr[off]), p.ped[mod_base + off]);
+                float cc = __fsub_rn(d, cm);
+                if (STACKED) cc = __fsub_rn(__fsub_rn(cc, cmr[r]), cmc[c]);
+                const float e = __fmul_rn(cc, p.inv_gain[mod_base + off]);
+                s = e > p.zero_thr ? e : 0.0f;
+                if (hr >= 1 && hr <= kTY && hc >= 2 && hc < kTX + 2) {
+                    atomicAdd(&hpix[hist_bin(e, p.hist_neg_lo_s, p.hist_inv_w, p.hist_bins)], 1u);
+                    if (out.corrected)
+                        out.corrected[(size_t)f * p.frame_px + mod_base + off] = e;
+                }
+            }
+            tile[hr][hc] = s;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < kHY * kTX; j += kThreads) {
+            const int hr = j / kTX, ic = j % kTX;
+            const float* row = &tile[hr][ic];
+            rowany[hr][ic] = (row[0] > 0.0f) | (row[1] > 0.0f) | (row[2] > 0.0f) |
+                             (row[3] > 0.0f) | (row[4] > 0.0f);
+        }
+        __syncthreads();
+
+        // 2. the bank at every pixel whose window holds signal
+        for (int base = 0; base < kTY * kTX; base += kThreads) {
+            const int j = base + threadIdx.x;
+            const int ir = j / kTX, ic = j % kTX;
+            const int r = r0 + ir, c = c0 + ic;
+            bool emit = false;
+            pd_hit h;
+            uint32_t n = 0, pix = 0;
+            if (r < R && c < C &&
+                (rowany[ir][ic] | rowany[ir + 1][ic] | rowany[ir + 2][ic] | rowany[ir + 3][ic])) {
+                // window tap (i, j) is tile[ir + i][ic + j]
+                const float* w = &tile[ir][ic];
+                float E = 0.0f, dx = 0.0f, dy = 0.0f;
+                uint32_t npix = 0;
+                bool any = false;
+                for (uint32_t ft = 0; ft < nf; ft++) {
+                    float size = 0.0f, over = 0.0f;
+                    for (uint32_t k = sb.off1[ft]; k < sb.off1[ft + 1]; k++)
+                        if (w[sb.t1[k].at] > 0.0f) size = __fadd_rn(size, sb.t1[k].v);
+                    for (uint32_t k = sb.off0[ft]; k < sb.off0[ft + 1]; k++)
+                        if (w[sb.t0[k].at] > 0.0f) over = __fadd_rn(over, sb.t0[k].v);
+                    if (!(over == 0.0f && size >= sb.nmin[ft])) continue;
+                    float drop = 0.0f, mx = 0.0f, my = 0.0f;
+                    uint32_t under = 0;
+                    for (uint32_t k = sb.off1[ft]; k < sb.off1[ft + 1]; k++) {
+                        const float sv = w[sb.t1[k].at];
+                        drop = __fadd_rn(drop, __fmul_rn(sv, sb.t1[k].v));
+                        under += sv > 0.0f;
+                    }
+                    for (uint32_t k = sb.offx[ft]; k < sb.offx[ft + 1]; k++)
+                        mx = __fadd_rn(mx, __fmul_rn(w[sb.tx[k].at], sb.tx[k].v));
+                    for (uint32_t k = sb.offy[ft]; k < sb.offy[ft + 1]; k++)
+                        my = __fadd_rn(my, __fmul_rn(w[sb.ty[k].at], sb.ty[k].v));
+                    if (!any) npix = under;
+                    any = true;
+                    E = __fadd_rn(E, drop);
+                    if (drop != 0.0f) {
+                        dx = __fadd_rn(dx, __fdiv_rn(mx, drop));
+                        dy = __fadd_rn(dy, __fdiv_rn(my, drop));
+                    }
+                }
+                if (any && E != 0.0f) {
+                    atomicAdd(&hhit[hist_bin(E, p.hist_neg_lo_s, p.hist_inv_w, p.hist_bins)], 1u);
+                    const float qr = rintf(__fdiv_rn(E, p.photon_kev));
+                    uint16_t flags = 0;
+                    if (!(qr >= 0.0f)) {
+                        n = 0;
+                    } else if (qr > 255.0f) {
+                        n = 255;
+                        flags |= PD_HIT_SATURATED;
+                    } else {
+                        n = (uint32_t)qr;
+                    }
+                    if (n >= 1) {
+                        if (r == 0 || c == 0 || r == R - 1 || c == C - 1) flags |= PD_HIT_EDGE;
+                        pix = (uint32_t)mod_base + (uint32_t)r * p.cols + (uint32_t)c;
+                        h.frame = frame_base + f;
+                        h.pixel = pix;
+                        h.energy_kev = E;
+                        h.dx = dx;
+                        h.dy = dy;
+                        h.count = (uint8_t)n;
+                        h.npix = (uint8_t)(npix > 255 ? 255 : npix);
+                        h.flags = flags;
+                        emit = true;
+                    }
+                }
+            }
+            const uint32_t mask = __ballot_sync(0xffffffffu, emit);
+            if (mask) {
+                uint32_t slot = 0;
+                if (lane == __ffs(mask) - 1) slot = atomicAdd(out.n_hits, __popc(mask));
+                slot = __shfl_sync(0xffffffffu, slot, __ffs(mask) - 1);
+                if (emit) {
+                    slot += __popc(mask & ((1u << lane) - 1u));
+                    atomicAdd(&p.count_map[pix], n);
+                    if (slot < out.hit_capacity) out.hits[slot] = h;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (uint32_t b = threadIdx.x; b < p.hist_bins; b += kThreads) {
+        if (hpix[b]) atomicAdd(&p.hist_pix[b], (unsigned long long)hpix[b]);
+        if (hhit[b]) atomicAdd(&p.hist_hit[b], (unsigned long long)hhit[b]);
+    }
+}
+
+// Nonzero taps of one 4 x 5 filter, row-major, appended to list.
+void compile_taps(const float (*flt)[5], MatchedTap* list, uint32_t* n) {
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 5; j++)
+            if (flt[i][j] != 0.0f) {
+                list[*n].at = (uint16_t)(i * kHX + j);
+                list[*n].v = flt[i][j];
+                (*n)++;
+            }
+}
+
+}  // namespace
+
+bool compile_bank(const pd_filter_bank& b, MatchedBank* out) {
+    if (b.n_features < 1 || b.n_features > PD_MAX_FEATURES) return false;
+    MatchedBank mb{};
+    mb.n_features = b.n_features;
+    uint32_t n1 = 0, n0 = 0, nx = 0, ny = 0;
+    for (uint32_t f = 0; f < b.n_features; f++) {
+        if (isnan(b.f1_nmin[f])) return false;
+        for (int i = 0; i < 4; i++)
+            for (int j = 0; j < 5; j++)
+                if (!isfinite(b.f0[f][i][j]) || !isfinite(b.f1[f][i][j]) ||
+                    !isfinite(b.f1_dx[f][i][j]) || !isfinite(b.f1_dy[f][i][j]))
+                    return false;
+        mb.nmin[f] = b.f1_nmin[f];
+        mb.off1[f] = (uint16_t)n1;
+        mb.off0[f] = (uint16_t)n0;
+        mb.offx[f] = (uint16_t)nx;
+        mb.offy[f] = (uint16_t)ny;
+        compile_taps(b.f1[f], mb.t1, &n1);
+        compile_taps(b.f0[f], mb.t0, &n0);
+        compile_taps(b.f1_dx[f], mb.tx, &nx);
+        compile_taps(b.f1_dy[f], mb.ty, &ny);
+    }
+    mb.off1[b.n_features] = (uint16_t)n1;
+    mb.off0[b.n_features] = (uint16_t)n0;
+    mb.offx[b.n_features] = (uint16_t)nx;
+    mb.offy[b.n_features] = (uint16_t)ny;
+    *out = mb;
+    return true;
+}
+
+cudaError_t launch_matched(const ChainParams& p, const MatchedBank* bank_dev,
+                           const uint16_t* raw, uint32_t n_frames, uint32_t frame_base,
+                           const CallOut& out, cudaStream_t stream) {
+    const uint32_t tiles_y = (p.rows + kTY - 1) / kTY;
+    const uint32_t tiles_x = (p.cols + kTX - 1) / kTX;
+    const unsigned long long n_tiles =
+        (unsigned long long)n_frames * p.n_modules * tiles_y * tiles_x;
+    if (n_tiles == 0) return cudaSuccess;
+    const size_t smem = 2 * (size_t)p.hist_bins * sizeof(uint32_t);
+    static bool attr_set = false;
+    if (!attr_set) {
+        for (auto k : {matched_kernel<false>, matched_kernel<true>}) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(2 * PD_MAX_HIST_BINS * sizeof(uint32_t)));
+            if (e != cudaSuccess) return e;
+        }
+        attr_set = true;
+    }
+    unsigned long long grid = (unsigned long long)device_sm_count() * 4;
+    if (grid > n_tiles) grid = n_tiles;
+    if (p.cm_mode == PD_CM_MEAN_STACKED)
+        matched_kernel<true><<<(unsigned)grid, kThreads, smem, stream>>>(
+            p, bank_dev, raw, frame_base, out, tiles_y, tiles_x, n_tiles);
+    else
+        matched_kernel<false><<<(unsigned)grid, kThreads, smem, stream>>>(
+            p, bank_dev, raw, frame_base, out, tiles_y, tiles_x, n_tiles);
+    return cudaGetLastError();
+}
+
+}  // namespace pd

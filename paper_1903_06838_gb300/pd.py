@@ -21,7 +21,8 @@ _INCLUDE = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_PKG, "libpd.so")
 SOURCES = ["pd_api.cu", "pd_chain.cu", "pd_cm_mean.cu", "pd_eta.cu", "pd_fast.cu",
-           "pd_fused.cu", "pd_noalloc.cu", "pd_net.cu", "pd_net_tc.cu", "pd_serve.cu"]
+           "pd_fused.cu", "pd_matched.cu", "pd_noalloc.cu", "pd_net.cu", "pd_net_tc.cu",
+           "pd_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
@@ -42,6 +43,18 @@ HIT_DTYPE = np.dtype([("frame", "<u4"), ("pixel", "<u4"), ("energy_kev", "<f4"),
                       ("dx", "<f4"), ("dy", "<f4"), ("count", "u1"),
                       ("npix", "u1"), ("flags", "<u2")])
 assert HIT_DTYPE.itemsize == 24
+
+
+PD_MAX_FEATURES = 8
+
+
+class PdFilterBank(ctypes.Structure):
+    _fields_ = [("n_features", ctypes.c_uint32),
+                ("f0", ctypes.c_float * 20 * PD_MAX_FEATURES),
+                ("f1", ctypes.c_float * 20 * PD_MAX_FEATURES),
+                ("f1_dx", ctypes.c_float * 20 * PD_MAX_FEATURES),
+                ("f1_dy", ctypes.c_float * 20 * PD_MAX_FEATURES),
+                ("f1_nmin", ctypes.c_float * PD_MAX_FEATURES)]
 
 
 class PdGeometry(ctypes.Structure):
@@ -163,6 +176,7 @@ def _declare(lib):
                              ctypes.POINTER(u32)], i32),
         "pd_get_summary": ([vp, vp, vp, vp, vp], i32),
         "pd_reset_summary": ([vp, vp], i32),
+        "pd_set_filter_bank": ([vp, vp], i32),
         "pd_destroy": ([vp], None),
         "pd_set_profiling": ([vp, i32], i32),
         "pd_autotune": ([vp, vp, u32, ctypes.POINTER(PdTuning),
@@ -384,6 +398,30 @@ def pd_get_summary(ctx: Context, stream=None):
                                  hh.ctypes.data, _stream_handle(stream)),
            "pd_get_summary")
     return cm, hp, hh
+
+
+def pd_set_filter_bank(ctx: Context, f0=None, f1=None, f1_dx=None, f1_dy=None,
+                       f1_nmin=None) -> None:
+    """Matched-filter charge summing with the bank of arrays [F][4][5] (and
+    [F] thresholds); with no arrays the default 3x3 local maximum."""
+    if f1 is None:
+        _check(load().pd_set_filter_bank(ctx.handle, None), "pd_set_filter_bank")
+        return
+    arrs = [np.asarray(a, np.float32).reshape(-1, 4, 5) for a in (f0, f1, f1_dx, f1_dy)]
+    nmin = np.asarray(f1_nmin, np.float32).reshape(-1)
+    nf = arrs[1].shape[0]
+    if nf > PD_MAX_FEATURES or any(a.shape[0] != nf for a in arrs) or nmin.size != nf:
+        raise ValueError("filter bank arrays disagree in their feature count")
+    fb = PdFilterBank()
+    fb.n_features = nf
+    for name, a in zip(("f0", "f1", "f1_dx", "f1_dy"), arrs):
+        dst = np.zeros((PD_MAX_FEATURES, 20), np.float32)
+        dst[:nf] = a.reshape(nf, 20)
+        ctypes.memmove(getattr(fb, name), dst.ctypes.data, dst.nbytes)
+    dst = np.zeros(PD_MAX_FEATURES, np.float32)
+    dst[:nf] = nmin
+    ctypes.memmove(fb.f1_nmin, dst.ctypes.data, dst.nbytes)
+    _check(load().pd_set_filter_bank(ctx.handle, ctypes.byref(fb)), "pd_set_filter_bank")
 
 
 def pd_reset_summary(ctx: Context, stream=None) -> None:

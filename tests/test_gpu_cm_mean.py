@@ -52,7 +52,7 @@ def _run(det, n, mode, ped=None, gain=None, raw=None, thr_over=None, tuning=None
 
 def _compare(ctx, out, ref, n):
     hits, nh = out.hits_host()
-    assert nh == ref.n_hits and len(hits) == nh
+    assert nh == ref.n_hits and len(hits) == nh and len(ref.hits) == nh
     assert sort_hits(hits).tobytes() == sort_hits(ref.hits).tobytes()
     assert out.cm.cpu().numpy().tobytes() == ref.cm.reshape(n, -1).tobytes()
     assert out.corrected.cpu().numpy().tobytes() == ref.corrected.reshape(n, -1).tobytes()

@@ -37,6 +37,7 @@ def _compare(ctx, out, ref, n_frames, check_corrected=True):
     hits, n = out.hits_host()
     assert n == ref.n_hits
     assert len(hits) == n, "hit capacity too small for a full comparison"
+    assert len(ref.hits) == n, "oracle hit capacity too small for a full comparison"
     assert sort_hits(hits).tobytes() == sort_hits(ref.hits).tobytes()
     got_cm = out.cm.cpu().numpy()
     assert got_cm.tobytes() == ref.cm.reshape(n_frames, -1).tobytes()
