@@ -378,15 +378,22 @@ def run_pd(args):
 def cm_variants_run(args, dev, det, ped, gain, frames, nf, peak, steps=5):
     """The same 2.2 Mpx batch with the paper's mean common mode (one stage per
     bank, and three stacked stages: bank, module row, module column) in place
-    of the median: frames/s and the device time of each kernel group.  The
-    common-mode launches' algorithmic bytes are one read of raw and of the
-    pedestal map per stage plus the common-mode values written."""
+    of the median, and with the matched-filter charge summing (the example
+    six-feature bank) in place of the 3x3 local maximum: frames/s and the
+    device time of each kernel group.  The common-mode launches' algorithmic
+    bytes are one read of raw and of the pedestal map per stage plus the
+    common-mode values written."""
     import torch
-    from paper_1903_06838_gb300 import pd
+    from paper_1903_06838_gb300 import filters, pd
     stream = torch.cuda.current_stream(dev)
     res = {}
-    for name, mode in (("mean", pd.PD_CM_MEAN), ("mean_stacked", pd.PD_CM_MEAN_STACKED)):
+    for name, mode, bank in (("mean", pd.PD_CM_MEAN, None),
+                             ("mean_stacked", pd.PD_CM_MEAN_STACKED, None),
+                             ("matched_filters_example_bank", pd.PD_CM_MEDIAN,
+                              filters.example_bank())):
         ctx = pd.pd_create(dict(det.geometry(), cm_mode=mode), ped, gain, det.thresholds())
+        if bank is not None:
+            pd.pd_set_filter_bank(ctx, **bank)
         out = pd.Outputs(ctx, nf, nf * 16384, device=dev)
         for _ in range(3):
             pd.pd_process(ctx, frames.data_ptr(), nf, 0, stream=stream, **out.ptrs())
@@ -402,7 +409,7 @@ def cm_variants_run(args, dev, det, ped, gain, frames, nf, peak, steps=5):
         prof = pd.pd_read_profile(ctx)
         pd.pd_set_profiling(ctx, False)
         ms = e0.elapsed_time(e1) / steps
-        stages = 3 if mode == pd.PD_CM_MEAN_STACKED else 1
+        stages = {pd.PD_CM_MEAN_STACKED: 3, pd.PD_CM_MEAN: 1}.get(mode, 0)
         fpx = det.pixels_per_frame
         cm_bytes = nf * (stages * fpx * (2 + 4) + ctx.cm_values_per_frame * 4)
         cm_ms = prof["common_mode"][1] / steps if "common_mode" in prof else None
@@ -410,9 +417,10 @@ def cm_variants_run(args, dev, det, ped, gain, frames, nf, peak, steps=5):
             "frames_per_s": round(nf / (ms / 1e3), 1),
             "ms_per_step": round(ms, 3),
             "kernel_ms_per_step": {k: round(v[1] / steps, 3) for k, v in prof.items()},
-            "common_mode_gbs": round(cm_bytes / (cm_ms / 1e3) / 1e9, 1) if cm_ms else None,
+            "common_mode_gbs": round(cm_bytes / (cm_ms / 1e3) / 1e9, 1)
+            if cm_ms and stages else None,
             "common_mode_frac_of_hbm": round(cm_bytes / (cm_ms / 1e3) / 1e9 / peak, 4)
-            if cm_ms else None,
+            if cm_ms and stages else None,
             "hits_per_frame": round(int(out.n_hits.item()) / nf, 1)}
         del out
         pd.pd_destroy(ctx)

@@ -53,6 +53,11 @@ struct MatchedTap {
 struct MatchedBank {
     uint32_t n_features;
     float nmin[PD_MAX_FEATURES];
+    // 20-bit masks of the nonzero F1 and F0 taps (bit 5 i + j), and whether
+    // every nonzero F1 tap is 1 (Size = popcount) and every nonzero F0 tap
+    // is positive (Overflow == 0 iff no signal under F0)
+    uint32_t m1[PD_MAX_FEATURES], m0[PD_MAX_FEATURES];
+    uint32_t f1_unit[PD_MAX_FEATURES], f0_pos[PD_MAX_FEATURES];
     uint16_t off1[PD_MAX_FEATURES + 1], off0[PD_MAX_FEATURES + 1];
     uint16_t offx[PD_MAX_FEATURES + 1], offy[PD_MAX_FEATURES + 1];
     MatchedTap t1[PD_MAX_FEATURES * 20], t0[PD_MAX_FEATURES * 20];

@@ -23,9 +23,14 @@
 // matched_kernel: grid-stride over 16 x 64 tiles of (frame, module); the
 // corrected signal of the tile and its halo (one row above, two below, two
 // columns each side) goes to shared memory together with, per halo row and
-// column, whether any of the five columns around carries signal; pixels
-// with a non-empty window evaluate the bank; hits are compacted with a warp
-// ballot and one atomic per warp.
+// column, the 5-bit signal mask of the five columns around; four of those
+// give a pixel's 20-bit window mask.  Pixels with a non-empty window
+// evaluate the bank: Size is a popcount for features whose F1 taps are all
+// 1, and Overflow == 0 a mask test for features whose F0 taps are all
+// positive (a sum of positive terms is positive, and of ones is exact);
+// other features, and the droplet and momenta of valid features, run over
+// the tap lists.  Hits are compacted with a warp ballot and one atomic per
+// warp.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -56,7 +61,7 @@ __global__ void __launch_bounds__(kThreads)
                    uint32_t tiles_y, uint32_t tiles_x, unsigned long long n_tiles) {
     extern __shared__ uint32_t hsm[];  // [2][hist_bins]
     __shared__ float tile[kHY][kHX];
-    __shared__ uint8_t rowany[kHY][kTX];  // signal within columns c-2 .. c+2
+    __shared__ uint8_t row5[kHY][kTX];  // signal bits of columns c-2 .. c+2
     __shared__ MatchedBank sb;
     uint32_t* hpix = hsm;
     uint32_t* hhit = hsm + p.hist_bins;
@@ -114,8 +119,9 @@ __global__ void __launch_bounds__(kThreads)
         for (int j = threadIdx.x; j < kHY * kTX; j += kThreads) {
             const int hr = j / kTX, ic = j % kTX;
             const float* row = &tile[hr][ic];
-            rowany[hr][ic] = (row[0] > 0.0f) | (row[1] > 0.0f) | (row[2] > 0.0f) |
-                             (row[3] > 0.0f) | (row[4] > 0.0f);
+            row5[hr][ic] = (uint8_t)((row[0] > 0.0f) | (row[1] > 0.0f) << 1 |
+                                     (row[2] > 0.0f) << 2 | (row[3] > 0.0f) << 3 |
+                                     (row[4] > 0.0f) << 4);
         }
         __syncthreads();
 
@@ -127,20 +133,35 @@ __global__ void __launch_bounds__(kThreads)
             bool emit = false;
             pd_hit h;
             uint32_t n = 0, pix = 0;
-            if (r < R && c < C &&
-                (rowany[ir][ic] | rowany[ir + 1][ic] | rowany[ir + 2][ic] | rowany[ir + 3][ic])) {
+            const uint32_t win = (uint32_t)row5[ir][ic] | (uint32_t)row5[ir + 1][ic] << 5 |
+                                 (uint32_t)row5[ir + 2][ic] << 10 |
+                                 (uint32_t)row5[ir + 3][ic] << 15;
+            if (r < R && c < C && win) {
                 // window tap (i, j) is tile[ir + i][ic + j]
                 const float* w = &tile[ir][ic];
                 float E = 0.0f, dx = 0.0f, dy = 0.0f;
                 uint32_t npix = 0;
                 bool any = false;
                 for (uint32_t ft = 0; ft < nf; ft++) {
-                    float size = 0.0f, over = 0.0f;
-                    for (uint32_t k = sb.off1[ft]; k < sb.off1[ft + 1]; k++)
-                        if (w[sb.t1[k].at] > 0.0f) size = __fadd_rn(size, sb.t1[k].v);
-                    for (uint32_t k = sb.off0[ft]; k < sb.off0[ft + 1]; k++)
-                        if (w[sb.t0[k].at] > 0.0f) over = __fadd_rn(over, sb.t0[k].v);
-                    if (!(over == 0.0f && size >= sb.nmin[ft])) continue;
+                    bool clear;
+                    if (sb.f0_pos[ft]) {
+                        clear = (win & sb.m0[ft]) == 0;
+                    } else {
+                        float over = 0.0f;
+                        for (uint32_t k = sb.off0[ft]; k < sb.off0[ft + 1]; k++)
+                            if (w[sb.t0[k].at] > 0.0f) over = __fadd_rn(over, sb.t0[k].v);
+                        clear = over == 0.0f;
+                    }
+                    if (!clear) continue;
+                    float size;
+                    if (sb.f1_unit[ft]) {
+                        size = (float)__popc(win & sb.m1[ft]);
+                    } else {
+                        size = 0.0f;
+                        for (uint32_t k = sb.off1[ft]; k < sb.off1[ft + 1]; k++)
+                            if (w[sb.t1[k].at] > 0.0f) size = __fadd_rn(size, sb.t1[k].v);
+                    }
+                    if (!(size >= sb.nmin[ft])) continue;
                     float drop = 0.0f, mx = 0.0f, my = 0.0f;
                     uint32_t under = 0;
                     for (uint32_t k = sb.off1[ft]; k < sb.off1[ft + 1]; k++) {
@@ -239,6 +260,18 @@ bool compile_bank(const pd_filter_bank& b, MatchedBank* out) {
         mb.offy[f] = (uint16_t)ny;
         compile_taps(b.f1[f], mb.t1, &n1);
         compile_taps(b.f0[f], mb.t0, &n0);
+        mb.f1_unit[f] = mb.f0_pos[f] = 1;
+        for (int i = 0; i < 4; i++)
+            for (int j = 0; j < 5; j++) {
+                if (b.f1[f][i][j] != 0.0f) {
+                    mb.m1[f] |= 1u << (5 * i + j);
+                    if (b.f1[f][i][j] != 1.0f) mb.f1_unit[f] = 0;
+                }
+                if (b.f0[f][i][j] != 0.0f) {
+                    mb.m0[f] |= 1u << (5 * i + j);
+                    if (!(b.f0[f][i][j] > 0.0f)) mb.f0_pos[f] = 0;
+                }
+            }
         compile_taps(b.f1_dx[f], mb.tx, &nx);
         compile_taps(b.f1_dy[f], mb.ty, &ny);
     }
