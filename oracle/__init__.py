@@ -107,6 +107,12 @@ def _load():
             vp, vp, vp, ctypes.c_uint32, ctypes.c_uint32, vp, ctypes.c_uint32, vp, vp, vp,
             vp, vp, vp, vp]
         lib.oracle_process_matched.restype = ctypes.c_int
+        lib.oracle_process_ext.argtypes = [
+            ctypes.POINTER(Geometry), ctypes.POINTER(Thresholds), ctypes.POINTER(Filters),
+            ctypes.c_uint32, ctypes.c_uint32,
+            vp, vp, vp, ctypes.c_uint32, ctypes.c_uint32, vp, ctypes.c_uint32, vp, vp, vp,
+            vp, vp, vp, vp]
+        lib.oracle_process_ext.restype = ctypes.c_int
         lib.oracle_lower_median.argtypes = [vp, ctypes.c_uint32]
         lib.oracle_lower_median.restype = ctypes.c_float
         lib.oracle_default_min_count.argtypes = [ctypes.c_uint32]
@@ -165,15 +171,19 @@ class Result:
 
 def process(geom: Geometry, thr: Thresholds, ped, gain, raw, *, frame_base=0,
             want_corrected=False, want_cm=True, hit_capacity=None,
-            count_map=None, hist_pix=None, hist_hit=None, filters=None) -> Result:
+            count_map=None, hist_pix=None, hist_hit=None, filters=None,
+            n_gains=0, gain_shift=0) -> Result:
     """Run the oracle.  raw: uint16 [n, modules, rows, cols] (or flat).
-    filters: a Filters bank selects the matched-filter charge summing."""
+    filters: a Filters bank selects the matched-filter charge summing.
+    n_gains > 0: auto-ranging words (stage = raw >> gain_shift) with ped and
+    gain holding one map per stage, [n_gains, modules, rows, cols]."""
     lib = _load()
     ped = np.ascontiguousarray(ped, np.float32).reshape(-1)
     gain = np.ascontiguousarray(gain, np.float32).reshape(-1)
     fpx = geom.n_modules * geom.rows * geom.cols
     raw = np.ascontiguousarray(raw, np.uint16).reshape(-1)
-    assert raw.size % fpx == 0 and ped.size == fpx and gain.size == fpx
+    stages = n_gains or 1
+    assert raw.size % fpx == 0 and ped.size == stages * fpx and gain.size == stages * fpx
     n = raw.size // fpx
     upf = cm_values_per_frame(geom)
     cap = hit_capacity if hit_capacity is not None else max(1024, n * fpx // 8)
@@ -189,7 +199,11 @@ def process(geom: Geometry, thr: Thresholds, ped, gain, raw, *, frame_base=0,
             hits.ctypes.data, cap, ctypes.byref(nh), cmap.ctypes.data, hp.ctypes.data,
             hh.ctypes.data, corr.ctypes.data if corr is not None else None,
             cm.ctypes.data if cm is not None else None, ctypes.byref(ns))
-    if filters is None:
+    if n_gains:
+        rc = lib.oracle_process_ext(ctypes.byref(geom), ctypes.byref(thr),
+                                    ctypes.byref(filters) if filters is not None else None,
+                                    n_gains, gain_shift, *rest)
+    elif filters is None:
         rc = lib.oracle_process(ctypes.byref(geom), ctypes.byref(thr), *rest)
     else:
         rc = lib.oracle_process_matched(ctypes.byref(geom), ctypes.byref(thr),

@@ -92,6 +92,19 @@
  * the number of signal pixels under the nonzero taps of the first valid
  * feature's F1.
  *
+ * Auto-ranging multi-gain (oracle_process_ext with n_gains > 0; the
+ * caption of Fig. b notes that several darks and gains per pixel are
+ * accommodated the same way and does not show how).  Each raw word carries
+ * its gain stage in its top bits: stage = raw >> gain_shift, value =
+ * raw & (2^gain_shift - 1), and the pedestal and gain maps hold one map per
+ * stage.  Step 1 becomes d = (float)value - pedestal[stage]; only stage-0
+ * pixels enter the common-mode set (step 2 adds stage == 0 to d < cut);
+ * step 3-4 become e = (d - cm_u) * inv_gain[0] for stage 0 and
+ * e = d * inv_gain[stage] for the other stages (a pixel switched to a lower
+ * gain carries a signal far above the common mode's scale); a stage
+ * >= n_gains marks the pixel bad: e = 0.  Only the median and no common
+ * mode are defined with several gains.
+ *
  * Inputs must be finite (pedestal finite; non-finite gains are masked).
  */
 #include <math.h>
@@ -258,7 +271,8 @@ int oracle_check(const og_geometry* g, const og_thresholds* t) {
  * Returns 0, or 1 on invalid input.
  */
 static int process_impl(const og_geometry* g, const og_thresholds* t,
-                        const og_filters* fb, const float* ped, const float* gain,
+                        const og_filters* fb, uint32_t n_gains, uint32_t gain_shift,
+                        const float* ped, const float* gain,
                         const uint16_t* raw, uint32_t n_frames, uint32_t frame_base,
                         og_hit* hits, uint32_t cap, uint32_t* n_hits, uint32_t* count_map,
                         uint64_t* hist_pix, uint64_t* hist_hit, float* corrected,
@@ -270,8 +284,8 @@ int oracle_process(const og_geometry* g, const og_thresholds* t,
                    uint32_t cap, uint32_t* n_hits, uint32_t* count_map,
                    uint64_t* hist_pix, uint64_t* hist_hit, float* corrected,
                    float* cm_out, uint64_t* n_seeds) {
-    return process_impl(g, t, NULL, ped, gain, raw, n_frames, frame_base, hits, cap, n_hits,
-                        count_map, hist_pix, hist_hit, corrected, cm_out, n_seeds);
+    return process_impl(g, t, NULL, 0, 0, ped, gain, raw, n_frames, frame_base, hits, cap,
+                        n_hits, count_map, hist_pix, hist_hit, corrected, cm_out, n_seeds);
 }
 
 /* The chain with the matched-filter charge summing of the bank fb. */
@@ -282,8 +296,25 @@ int oracle_process_matched(const og_geometry* g, const og_thresholds* t,
                            uint32_t* count_map, uint64_t* hist_pix, uint64_t* hist_hit,
                            float* corrected, float* cm_out, uint64_t* n_seeds) {
     if (!fb || !filters_ok(fb)) return 1;
-    return process_impl(g, t, fb, ped, gain, raw, n_frames, frame_base, hits, cap, n_hits,
-                        count_map, hist_pix, hist_hit, corrected, cm_out, n_seeds);
+    return process_impl(g, t, fb, 0, 0, ped, gain, raw, n_frames, frame_base, hits, cap,
+                        n_hits, count_map, hist_pix, hist_hit, corrected, cm_out, n_seeds);
+}
+
+/* The chain with an optional filter bank (NULL: 3x3 local maximum) and
+ * n_gains gain stages (0: plain single-gain data; 1..4: auto-ranging words
+ * with the stage in bits gain_shift.., pedestal and gain [n_gains][pixels]). */
+int oracle_process_ext(const og_geometry* g, const og_thresholds* t, const og_filters* fb,
+                       uint32_t n_gains, uint32_t gain_shift, const float* ped,
+                       const float* gain, const uint16_t* raw, uint32_t n_frames,
+                       uint32_t frame_base, og_hit* hits, uint32_t cap, uint32_t* n_hits,
+                       uint32_t* count_map, uint64_t* hist_pix, uint64_t* hist_hit,
+                       float* corrected, float* cm_out, uint64_t* n_seeds) {
+    if (fb && !filters_ok(fb)) return 1;
+    if (n_gains > 4 || (n_gains && (gain_shift < 1 || gain_shift > 15))) return 1;
+    if (n_gains && g->cm_mode != OG_CM_MEDIAN && g->cm_mode != OG_CM_NONE) return 1;
+    return process_impl(g, t, fb, n_gains, gain_shift, ped, gain, raw, n_frames, frame_base,
+                        hits, cap, n_hits, count_map, hist_pix, hist_hit, corrected, cm_out,
+                        n_seeds);
 }
 
 /* The matched-filter model at pixel (r, c) of a module's zeroed signal s
@@ -329,12 +360,17 @@ static int matched_at(const og_filters* fb, const float* s, uint32_t R, uint32_t
 }
 
 static int process_impl(const og_geometry* g, const og_thresholds* t,
-                        const og_filters* fb, const float* ped, const float* gain,
+                        const og_filters* fb, uint32_t n_gains, uint32_t gain_shift,
+                        const float* ped, const float* gain,
                         const uint16_t* raw, uint32_t n_frames, uint32_t frame_base,
                         og_hit* hits, uint32_t cap, uint32_t* n_hits, uint32_t* count_map,
                         uint64_t* hist_pix, uint64_t* hist_hit, float* corrected,
                         float* cm_out, uint64_t* n_seeds) {
     if (oracle_check(g, t)) return 1;
+    /* one pedestal and gain map per stage; plain data is one stage of raw words */
+    const uint32_t stages = n_gains ? n_gains : 1;
+    const uint32_t vmask = n_gains ? (1u << gain_shift) - 1u : 0xFFFFu;
+    const uint32_t sshift = n_gains ? gain_shift : 16;
     const uint32_t R = g->rows, C = g->cols;
     const size_t mpx = (size_t)R * C;
     const size_t fpx = mpx * g->n_modules;
@@ -346,7 +382,8 @@ static int process_impl(const og_geometry* g, const og_thresholds* t,
     const float inv_w = 1.0f / t->hist_bin_kev;
     const float lo_s = t->hist_lo_kev * inv_w;
 
-    float* inv_gain = (float*)malloc(fpx * sizeof(float));
+    float* inv_gain = (float*)malloc(stages * fpx * sizeof(float));
+    uint8_t* stage = (uint8_t*)malloc(mpx);
     float* d = (float*)malloc(mpx * sizeof(float));
     float* e = (float*)malloc(mpx * sizeof(float));
     float* s = (float*)malloc(mpx * sizeof(float));
@@ -360,14 +397,14 @@ static int process_impl(const og_geometry* g, const og_thresholds* t,
     float* cmu = (float*)malloc((size_t)upm * sizeof(float));
     float* cmr = (float*)calloc(R, sizeof(float));
     float* cmc = (float*)calloc(C, sizeof(float));
-    if (!inv_gain || !d || !e || !s || !set || !cmu || !cmr || !cmc) {
-        free(inv_gain); free(d); free(e); free(s); free(set); free(cmu);
+    if (!inv_gain || !stage || !d || !e || !s || !set || !cmu || !cmr || !cmc) {
+        free(inv_gain); free(stage); free(d); free(e); free(s); free(set); free(cmu);
         free(cmr); free(cmc);
         return 1;
     }
-    for (size_t p = 0; p < fpx; p++) {
+    for (size_t p = 0; p < stages * fpx; p++) {
         if (!isfinite(ped[p])) {
-            free(inv_gain); free(d); free(e); free(s); free(set); free(cmu);
+            free(inv_gain); free(stage); free(d); free(e); free(s); free(set); free(cmu);
             free(cmr); free(cmc);
             return 1;
         }
@@ -381,8 +418,13 @@ static int process_impl(const og_geometry* g, const og_thresholds* t,
         for (uint32_t m = 0; m < g->n_modules; m++) {
             const size_t base = m * mpx;
             const uint16_t* rw = raw + (size_t)f * fpx + base;
-            /* 1. dark */
-            for (size_t p = 0; p < mpx; p++) d[p] = (float)rw[p] - ped[base + p];
+            /* 1. dark (per gain stage) */
+            for (size_t p = 0; p < mpx; p++) {
+                const uint32_t st = (uint32_t)rw[p] >> sshift;
+                const uint32_t v = (uint32_t)rw[p] & vmask;
+                stage[p] = (uint8_t)(st < stages ? st : 255);
+                d[p] = st < stages ? (float)v - ped[(size_t)st * fpx + base + p] : 0.0f;
+            }
             /* 2. common mode per unit */
             for (uint32_t ur = 0; ur < urows; ur++) {
                 for (uint32_t uc = 0; uc < ucols; uc++) {
@@ -394,7 +436,7 @@ static int process_impl(const og_geometry* g, const og_thresholds* t,
                                 const size_t p =
                                     (size_t)(ur * g->unit_rows + r) * C +
                                     uc * g->unit_cols + c;
-                                if (d[p] < t->cm_cut_adu) set[n++] = d[p];
+                                if (stage[p] == 0 && d[p] < t->cm_cut_adu) set[n++] = d[p];
                             }
                         }
                         if (n >= n_min && n > 0) cm = oracle_lower_median(set, n);
@@ -438,9 +480,14 @@ static int process_impl(const og_geometry* g, const og_thresholds* t,
                     const size_t p = (size_t)r * C + c;
                     const float cm =
                         cmu[(r / g->unit_rows) * ucols + c / g->unit_cols];
-                    float cc = d[p] - cm;
-                    if (stacked) cc = (cc - cmr[r]) - cmc[c];
-                    const float ev = cc * inv_gain[base + p];
+                    float ev = 0.0f;
+                    if (stage[p] == 0) {
+                        float cc = d[p] - cm;
+                        if (stacked) cc = (cc - cmr[r]) - cmc[c];
+                        ev = cc * inv_gain[base + p];
+                    } else if (stage[p] != 255) {
+                        ev = d[p] * inv_gain[(size_t)stage[p] * fpx + base + p];
+                    }
                     e[p] = ev;
                     s[p] = ev > t->zero_thr_kev ? ev : 0.0f;
                     hist_pix[bin_of(ev, lo_s, inv_w, t->hist_bins)]++;
@@ -547,7 +594,7 @@ static int process_impl(const og_geometry* g, const og_thresholds* t,
     }
     *n_hits = nh;
     if (n_seeds) *n_seeds = ns;
-    free(inv_gain); free(d); free(e); free(s); free(set); free(cmu);
+    free(inv_gain); free(stage); free(d); free(e); free(s); free(set); free(cmu);
     free(cmr); free(cmc);
     return 0;
 }

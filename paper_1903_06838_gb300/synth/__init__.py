@@ -260,3 +260,69 @@ PRESETS = {
     "epix_704x768": epix_704x768,
     "asic16_352x384": asic16_352x384,
 }
+
+
+# ---- auto-ranging detectors ---------------------------------------------
+def multigain_maps(det: Detector, n_gains: int = 3,
+                   ratios=(1.0, 1.0 / 3.0, 1.0 / 100.0),
+                   ped_offsets=(0.0, -300.0, -700.0)):
+    """Pedestal and gain maps of each gain stage, float32 [n_gains, modules,
+    rows, cols]: stage 0 is ``maps(det)``; stage g has gain ratios[g] times
+    stage 0's and its pedestal shifted by ped_offsets[g] ADU."""
+    ped0, gain0 = maps(det)
+    ped = np.stack([ped0 + np.float32(ped_offsets[g]) for g in range(n_gains)])
+    gain = np.stack([gain0 * np.float32(ratios[g]) for g in range(n_gains)])
+    return ped.astype(np.float32), gain.astype(np.float32)
+
+
+def multigain_frames(det: Detector, ped: np.ndarray, gain: np.ndarray, first: int, n: int,
+                     gain_shift: int = 14, blobs: int = 3, blob_kev: float = 3000.0,
+                     bad_frac: float = 1e-4):
+    """Raw words of an auto-ranging detector, uint16 [n, modules, rows, cols]:
+    stage = word >> gain_shift, ADC value = word & (2^gain_shift - 1).
+
+    Each frame is ``frames`` (noise, common mode, photons) at stage 0 plus
+    ``blobs`` bright Gaussian spots per module of up to ``blob_kev`` keV per
+    pixel.  A pixel whose stage-0 reading would pass 90 % of the ADC range
+    switches to the next stage, which reads the same charge at its own gain
+    and pedestal, with its own noise and no common mode; a few pixels carry
+    an invalid stage (n_gains) to model corrupt words.  Returns (raw, the
+    bright spots' deposited energy in keV per pixel as float32)."""
+    n_gains = ped.shape[0]
+    full = (1 << gain_shift) - 1
+    raw0, _, cm = frames(det, ped[0], gain[0], first, n, truth=True, cm_truth=True)
+    rng = np.random.default_rng((det.seed, first, n, 7))
+    shape = raw0.shape
+    R, C = det.rows, det.cols
+    yy, xx = np.mgrid[0:R, 0:C]
+    blob = np.zeros(shape, np.float64)
+    for f in range(n):
+        for m in range(det.n_modules):
+            for _ in range(blobs):
+                cy, cx = rng.uniform(0, R), rng.uniform(0, C)
+                w = rng.uniform(1.5, 6.0)
+                amp = rng.uniform(0.05, 1.0) * blob_kev
+                blob[f, m] += amp * np.exp(-((yy - cy) ** 2 + (xx - cx) ** 2) / (2 * w * w))
+    # common mode per pixel from its unit
+    upr = C // det.unit_cols
+    cm_px = np.repeat(np.repeat(cm.reshape(n, det.n_modules, R // det.unit_rows, upr),
+                                det.unit_rows, 2), det.unit_cols, 3)
+    a0 = raw0.astype(np.float64) + blob * gain[0][None].astype(np.float64)
+    # stage-0 signal in ADU without pedestal and common mode (noise included)
+    sig0 = a0 - ped[0][None] - cm_px
+    stage = np.zeros(shape, np.int64)
+    val = a0
+    limit = 0.9 * full
+    for g in range(1, n_gains):
+        up = val > limit
+        if not up.any():
+            break
+        ag = ped[g][None] + sig0 * (gain[g] / gain[0])[None] + \
+            rng.normal(0.0, det.noise_sigma, shape)
+        stage = np.where(up, g, stage)
+        val = np.where(up, ag, val)
+    raw = (stage << gain_shift) | np.clip(np.rint(val), 0, full).astype(np.int64)
+    if (n_gains << gain_shift) <= 0xFFFF:
+        bad = rng.random(shape) < bad_frac
+        raw = np.where(bad, (n_gains << gain_shift) | (raw & full), raw)
+    return raw.astype(np.uint16), blob.astype(np.float32)
