@@ -192,6 +192,24 @@ int pd_create(const pd_geometry* geometry, const float* pedestal_host,
               const float* gain_host, const pd_thresholds* thresholds,
               pd_ctx** out);
 
+/* pd_create_multigain — a context for auto-ranging detectors (the caption
+ * of Fig. b: several darks and gains per pixel).  Each raw word carries its
+ * gain stage in bits gain_shift..15 and its ADC value below:
+ * stage = raw >> gain_shift, value = raw & (2^gain_shift - 1).
+ * pedestal_host and gain_host hold n_gains maps, [n_gains][n_modules][rows]
+ * [cols].  Then d = value - pedestal[stage]; the common mode (median, or
+ * none) is taken over stage-0 pixels only and subtracted from them only:
+ * e = (d - cm) * inv_gain[0] for stage 0, e = d * inv_gain[stage] for the
+ * others; a stage >= n_gains marks a bad pixel, e = 0.  Everything after
+ * the energy (zeroing, charge summing or matched filters, summaries) is
+ * unchanged.  1 <= n_gains <= PD_MAX_GAINS, 1 <= gain_shift <= 15, cm_mode
+ * PD_CM_MEDIAN or PD_CM_NONE; such contexts use the generic kernels (no
+ * one-kernel chain, no mixed batch launch).  masked_pixels counts stage 0. */
+#define PD_MAX_GAINS 4u
+int pd_create_multigain(const pd_geometry* geometry, uint32_t n_gains, uint32_t gain_shift,
+                        const float* pedestal_host, const float* gain_host,
+                        const pd_thresholds* thresholds, pd_ctx** out);
+
 int pd_query(const pd_ctx* ctx, pd_info* info);
 
 /* pd_process — run the whole chain on n_frames device-resident raw frames

@@ -48,6 +48,10 @@ struct pd_ctx {
     bool use_fused = false;     // the geometry allows the one-kernel chain
     uint32_t two_pass = 1;      // 1: common-mode and stencil kernels (measured
                                 // faster on GB300 so far); 0: the one-kernel chain
+    bool multigain = false;     // auto-ranging words (pd_create_multigain)
+    pd::MultiGain mg{};
+    float* d_mg_ped = nullptr;  // [n_gains][pixels]
+    float* d_mg_ig = nullptr;
     bool matched = false;       // matched-filter charge summing (pd_set_filter_bank)
     pd::MatchedBank* d_bank = nullptr;
     uint32_t chunk_frames = 1;  // frames per common-mode/stencil launch pair
@@ -189,6 +193,8 @@ void free_ctx(pd_ctx* c) {
     cudaFree(c->d_hist_hit);
     cudaFree(c->d_cm);
     cudaFree(c->d_bank);
+    cudaFree(c->d_mg_ped);
+    cudaFree(c->d_mg_ig);
     cudaFree(c->d_stage[0]);
     cudaFree(c->d_stage[1]);
     cudaFree(c->d_host_hits);
@@ -213,11 +219,16 @@ void free_ctx(pd_ctx* c) {
 
 // The one-kernel chain replaces the kernel pair.
 bool fused_on(const pd_ctx* c) { return c->use_fused && !c->two_pass && !c->matched; }
+// (use_fused, use_band, use_cm_big and use_cm_rows are off for multi-gain
+// contexts: those kernels read single-gain words)
 
 // The charge-summing launch of a context (after its common mode).
 cudaError_t launch_stencil_for(const pd_ctx* c, const uint16_t* fr, uint32_t nf,
                                uint32_t frame_base, const pd::CallOut& co, cudaStream_t s) {
-    if (c->matched) return pd::launch_matched(c->params, c->d_bank, fr, nf, frame_base, co, s);
+    const pd::MultiGain* mg = c->multigain ? &c->mg : nullptr;
+    if (c->matched)
+        return pd::launch_matched(c->params, c->d_bank, fr, nf, frame_base, co, s, mg);
+    if (mg) return pd::launch_stencil(c->params, fr, nf, frame_base, co, s, mg);
     return c->use_band ? pd::launch_stencil_band(c->params, c->band_cfg, fr, nf, frame_base, co, s)
                        : pd::launch_stencil(c->params, fr, nf, frame_base, co, s);
 }
@@ -227,6 +238,7 @@ cudaError_t launch_cm(const pd_ctx* c, const uint16_t* fr, uint32_t nf, float* c
                       cudaStream_t s) {
     if (c->params.cm_mode == PD_CM_MEAN || c->params.cm_mode == PD_CM_MEAN_STACKED)
         return pd::launch_cm_mean(c->params, fr, nf, cm, s);
+    if (c->multigain) return pd::launch_cm_select(c->params, fr, nf, cm, s, &c->mg);
     return c->use_cm_big    ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, cm, s)
            : c->use_cm_rows ? pd::launch_cm_rows(c->params, fr, nf, cm, s)
                             : pd::launch_cm_select(c->params, fr, nf, cm, s);
@@ -386,8 +398,32 @@ const char* pd_strerror(int code) {
 
 const char* pd_last_error(void) { return g_last_error.c_str(); }
 
+namespace {
+int create_impl(const pd_geometry* geometry, uint32_t n_gains, uint32_t gain_shift,
+                const float* pedestal_host, const float* gain_host,
+                const pd_thresholds* thresholds, pd_ctx** out);
+}
+
 int pd_create(const pd_geometry* geometry, const float* pedestal_host,
               const float* gain_host, const pd_thresholds* thresholds, pd_ctx** out) {
+    return create_impl(geometry, 0, 0, pedestal_host, gain_host, thresholds, out);
+}
+
+int pd_create_multigain(const pd_geometry* geometry, uint32_t n_gains, uint32_t gain_shift,
+                        const float* pedestal_host, const float* gain_host,
+                        const pd_thresholds* thresholds, pd_ctx** out) {
+    if (out) *out = nullptr;
+    if (n_gains < 1 || n_gains > PD_MAX_GAINS || gain_shift < 1 || gain_shift > 15)
+        return fail(PD_EINVAL, "multi-gain: 1..PD_MAX_GAINS stages, gain_shift in 1..15");
+    if (geometry && geometry->cm_mode != PD_CM_MEDIAN && geometry->cm_mode != PD_CM_NONE)
+        return fail(PD_EINVAL, "multi-gain: the median or no common mode");
+    return create_impl(geometry, n_gains, gain_shift, pedestal_host, gain_host, thresholds, out);
+}
+
+namespace {
+int create_impl(const pd_geometry* geometry, uint32_t n_gains, uint32_t gain_shift,
+                const float* pedestal_host, const float* gain_host,
+                const pd_thresholds* thresholds, pd_ctx** out) {
     if (!out) return fail(PD_EINVAL, "out is NULL");
     *out = nullptr;
     int rc = check_geometry(geometry);
@@ -441,7 +477,8 @@ int pd_create(const pd_geometry* geometry, const float* pedestal_host,
     }
 
     const size_t fpx = p.frame_px;
-    for (size_t i = 0; i < fpx; i++)
+    const size_t stages = n_gains ? n_gains : 1;
+    for (size_t i = 0; i < stages * fpx; i++)
         if (!isfinite(pedestal_host[i])) {
             free_ctx(c);
             return fail(PD_EINVAL, "pedestal values must be finite");
@@ -494,9 +531,33 @@ int pd_create(const pd_geometry* geometry, const float* pedestal_host,
     p.count_map = c->d_count_map;
     p.hist_pix = c->d_hist_pix;
     p.hist_hit = c->d_hist_hit;
+    if (n_gains) {
+        // all stages' maps; stage 0 is also the context's single-gain map above
+        std::vector<float> ig(stages * fpx);
+        for (size_t i = 0; i < stages * fpx; i++) {
+            const float gv = gain_host[i];
+            ig[i] = gv > 0.0f && isfinite(gv) ? 1.0f / gv : 0.0f;
+        }
+        if ((e = cudaMalloc(&c->d_mg_ped, stages * fpx * 4)) != cudaSuccess ||
+            (e = cudaMalloc(&c->d_mg_ig, stages * fpx * 4)) != cudaSuccess) {
+            free_ctx(c);
+            return fail(PD_ENOMEM, "device allocation failed in pd_create_multigain");
+        }
+        if ((e = cudaMemcpy(c->d_mg_ped, pedestal_host, stages * fpx * 4,
+                            cudaMemcpyHostToDevice)) ||
+            (e = cudaMemcpy(c->d_mg_ig, ig.data(), stages * fpx * 4, cudaMemcpyHostToDevice))) {
+            free_ctx(c);
+            return fail_cuda(e, "pd_create_multigain upload");
+        }
+        c->multigain = true;
+        c->mg = pd::MultiGain{n_gains, gain_shift, (1u << gain_shift) - 1u, c->d_mg_ped,
+                              c->d_mg_ig};
+        c->use_cm_big = c->use_cm_rows = c->use_band = c->use_fused = false;
+    }
     *out = c;
     return PD_OK;
 }
+}  // namespace
 
 int pd_query(const pd_ctx* c, pd_info* info) {
     if (!c || !info) return fail(PD_EINVAL, "NULL argument");
@@ -823,6 +884,8 @@ int batch_check_items(const pd_batch* b, const pd_batch_item* items, uint32_t n)
         if (rc) return fail(rc, why);
         if (b->mixed && !it.ctx->use_band)
             return fail(PD_ENOTSUP, "batch: the mixed launch needs the band stencil");
+        if (b->mixed && it.ctx->multigain)
+            return fail(PD_ENOTSUP, "batch: the mixed launch reads single-gain words");
         if (b->mixed && it.ctx->matched)
             return fail(PD_ENOTSUP, "batch: the mixed launch has no matched filters");
         if (b->mixed && it.ctx->params.cm_mode >= PD_CM_MEAN)
@@ -1141,7 +1204,8 @@ int pd_net_gather(pd_ctx* c, const uint16_t* frames_dev, uint32_t frame_base, co
     if (!c || (n_hits && (!frames_dev || !cm_dev || !hits_dev || !patches_dev)))
         return fail(PD_EINVAL, "pd_net_gather: NULL argument");
     cudaError_t e = pd::launch_gather(c->params, frames_dev, frame_base, cm_dev, hits_dev, n_hits,
-                                      patches_dev, (cudaStream_t)stream);
+                                      patches_dev, (cudaStream_t)stream,
+                                      c->multigain ? &c->mg : nullptr);
     return e == cudaSuccess ? PD_OK : fail_cuda(e, "pd_net_gather");
 }
 

@@ -35,13 +35,13 @@ __device__ __forceinline__ uint32_t hist_bin(float v, float neg_lo_s, float inv_
 // Common mode: one CTA per (frame, unit).
 constexpr int kCmThreads = 256;
 
-template <bool KEYS_IN_SMEM>
+template <bool KEYS_IN_SMEM, bool MG>
 __global__ void __launch_bounds__(kCmThreads)
     cm_select_kernel(ChainParams p, const uint16_t* __restrict__ raw,
-                     float* __restrict__ cm_out) {
+                     float* __restrict__ cm_out, MultiGain mg) {
     extern __shared__ uint32_t keys[];
     __shared__ generic_cm::Shared sh;
-    generic_cm::unit<KEYS_IN_SMEM>(p, raw, cm_out, blockIdx.x, keys, sh);
+    generic_cm::unit<KEYS_IN_SMEM, MG>(p, raw, cm_out, blockIdx.x, keys, sh, mg);
 }
 
 // ---------------------------------------------------------------------------
@@ -49,11 +49,11 @@ __global__ void __launch_bounds__(kCmThreads)
 constexpr int kTY = 16, kTX = 64, kStThreads = 256;
 constexpr int kHY = kTY + 2, kHX = kTX + 2;
 
-template <bool STACKED>
+template <bool STACKED, bool MG>
 __global__ void __launch_bounds__(kStThreads)
     stencil_kernel(ChainParams p, const uint16_t* __restrict__ raw,
                    uint32_t frame_base, CallOut out, uint32_t tiles_y,
-                   uint32_t tiles_x, unsigned long long n_tiles) {
+                   uint32_t tiles_x, unsigned long long n_tiles, MultiGain mg) {
     extern __shared__ uint32_t hsm[];
     __shared__ float tile[kHY][kHX];
     uint32_t* hpix = hsm;
@@ -91,10 +91,15 @@ __global__ void __launch_bounds__(kStThreads)
                 const uint32_t off = (uint32_t)r * p.cols + (uint32_t)c;
                 const float cm = cmf[((uint32_t)r / p.unit_rows) * p.units_per_row +
                                      (uint32_t)c / p.unit_cols];
-                const float d = __fsub_rn(__uint2float_rn(fr[off]), p.ped[mod_base + off]);
-                float cc = __fsub_rn(d, cm);
-                if (STACKED) cc = __fsub_rn(__fsub_rn(cc, cmr[r]), cmc[c]);
-                const float e = __fmul_rn(cc, p.inv_gain[mod_base + off]);
+                float e;
+                if (MG) {
+                    e = mg_energy(mg, p.frame_px, fr[off], mod_base + off, cm);
+                } else {
+                    const float d = __fsub_rn(__uint2float_rn(fr[off]), p.ped[mod_base + off]);
+                    float cc = __fsub_rn(d, cm);
+                    if (STACKED) cc = __fsub_rn(__fsub_rn(cc, cmr[r]), cmc[c]);
+                    e = __fmul_rn(cc, p.inv_gain[mod_base + off]);
+                }
                 s = e > p.zero_thr ? e : 0.0f;
                 if (hr >= 1 && hr <= kTY && hc >= 1 && hc <= kTX) {
                     atomicAdd(&hpix[hist_bin(e, p.hist_neg_lo_s, p.hist_inv_w, p.hist_bins)], 1u);
@@ -197,29 +202,37 @@ size_t cm_select_smem_bytes(const ChainParams& p) {
 static constexpr size_t kMaxDynSmem = 200 * 1024;
 
 cudaError_t launch_cm_select(const ChainParams& p, const uint16_t* raw,
-                             uint32_t n_frames, float* cm, cudaStream_t stream) {
+                             uint32_t n_frames, float* cm, cudaStream_t stream,
+                             const MultiGain* mg) {
     const unsigned long long items = (unsigned long long)n_frames * p.units_per_frame;
     if (items == 0) return cudaSuccess;
     const size_t smem = cm_select_smem_bytes(p);
+    const MultiGain m = mg ? *mg : MultiGain{};
     if (smem <= kMaxDynSmem) {
         static bool attr_set = false;
         if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(cm_select_kernel<true>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)kMaxDynSmem);
-            if (e != cudaSuccess) return e;
+            for (auto k : {cm_select_kernel<true, false>, cm_select_kernel<true, true>}) {
+                cudaError_t e = cudaFuncSetAttribute(
+                    k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
+                if (e != cudaSuccess) return e;
+            }
             attr_set = true;
         }
-        cm_select_kernel<true><<<(unsigned)items, kCmThreads, smem, stream>>>(p, raw, cm);
+        if (mg)
+            cm_select_kernel<true, true><<<(unsigned)items, kCmThreads, smem, stream>>>(p, raw, cm, m);
+        else
+            cm_select_kernel<true, false><<<(unsigned)items, kCmThreads, smem, stream>>>(p, raw, cm, m);
+    } else if (mg) {
+        cm_select_kernel<false, true><<<(unsigned)items, kCmThreads, 0, stream>>>(p, raw, cm, m);
     } else {
-        cm_select_kernel<false><<<(unsigned)items, kCmThreads, 0, stream>>>(p, raw, cm);
+        cm_select_kernel<false, false><<<(unsigned)items, kCmThreads, 0, stream>>>(p, raw, cm, m);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_stencil(const ChainParams& p, const uint16_t* raw,
                            uint32_t n_frames, uint32_t frame_base,
-                           const CallOut& out, cudaStream_t stream) {
+                           const CallOut& out, cudaStream_t stream, const MultiGain* mg) {
     const uint32_t tiles_y = (p.rows + kTY - 1) / kTY;
     const uint32_t tiles_x = (p.cols + kTX - 1) / kTX;
     const unsigned long long n_tiles =
@@ -228,7 +241,8 @@ cudaError_t launch_stencil(const ChainParams& p, const uint16_t* raw,
     const size_t smem = 2 * (size_t)p.hist_bins * sizeof(uint32_t);
     static bool attr_set = false;
     if (!attr_set) {
-        for (auto k : {stencil_kernel<false>, stencil_kernel<true>}) {
+        for (auto k : {stencil_kernel<false, false>, stencil_kernel<true, false>,
+                       stencil_kernel<false, true>}) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)(2 * PD_MAX_HIST_BINS * sizeof(uint32_t)));
             if (e != cudaSuccess) return e;
@@ -237,12 +251,16 @@ cudaError_t launch_stencil(const ChainParams& p, const uint16_t* raw,
     }
     unsigned long long grid = (unsigned long long)device_sm_count() * 4;
     if (grid > n_tiles) grid = n_tiles;
-    if (p.cm_mode == PD_CM_MEAN_STACKED)
-        stencil_kernel<true><<<(unsigned)grid, kStThreads, smem, stream>>>(
-            p, raw, frame_base, out, tiles_y, tiles_x, n_tiles);
+    const MultiGain m = mg ? *mg : MultiGain{};
+    if (mg)
+        stencil_kernel<false, true><<<(unsigned)grid, kStThreads, smem, stream>>>(
+            p, raw, frame_base, out, tiles_y, tiles_x, n_tiles, m);
+    else if (p.cm_mode == PD_CM_MEAN_STACKED)
+        stencil_kernel<true, false><<<(unsigned)grid, kStThreads, smem, stream>>>(
+            p, raw, frame_base, out, tiles_y, tiles_x, n_tiles, m);
     else
-        stencil_kernel<false><<<(unsigned)grid, kStThreads, smem, stream>>>(
-            p, raw, frame_base, out, tiles_y, tiles_x, n_tiles);
+        stencil_kernel<false, false><<<(unsigned)grid, kStThreads, smem, stream>>>(
+            p, raw, frame_base, out, tiles_y, tiles_x, n_tiles, m);
     return cudaGetLastError();
 }
 

@@ -34,9 +34,12 @@ struct Shared {
 
 // Common mode of unit `item` (= frame * units_per_frame + unit) into
 // cm_out[item].  keys: unit_px words of shared memory when KEYS_IN_SMEM.
-template <bool KEYS_IN_SMEM>
+// MG: auto-ranging words (only stage-0 pixels enter the set; mg describes
+// the stages).
+template <bool KEYS_IN_SMEM, bool MG = false>
 __device__ void unit(const ChainParams& p, const uint16_t* __restrict__ raw,
-                     float* __restrict__ cm_out, uint32_t item, uint32_t* keys, Shared& sh) {
+                     float* __restrict__ cm_out, uint32_t item, uint32_t* keys, Shared& sh,
+                     const MultiGain& mg = MultiGain{}) {
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
     const uint32_t f = item / p.units_per_frame;
     const uint32_t u = item % p.units_per_frame;
@@ -54,7 +57,12 @@ __device__ void unit(const ChainParams& p, const uint16_t* __restrict__ raw,
 
     auto key_at = [&](uint32_t i) -> uint32_t {
         const uint32_t off = (r0 + i / p.unit_cols) * p.cols + c0 + i % p.unit_cols;
-        const float d = __fsub_rn(__uint2float_rn(fr[off]), pm[off]);
+        uint32_t w = fr[off];
+        if (MG) {
+            if ((w >> mg.shift) != 0) return kSentinel;
+            w &= mg.vmask;
+        }
+        const float d = __fsub_rn(__uint2float_rn(w), pm[off]);
         return d < p.cm_cut ? order_key(d) : kSentinel;
     };
 

@@ -37,6 +37,27 @@ struct ChainParams {
     unsigned long long* hist_hit;  // [hist_bins]
 };
 
+// Auto-ranging multi-gain data: each raw word holds its gain stage in the
+// bits from `shift` up, the ADC value below; one pedestal and inverse-gain map
+// per stage.  Passed beside ChainParams to the kernels that support it.
+struct MultiGain {
+    uint32_t n_gains, shift, vmask;
+    const float* ped;       // [n_gains][frame_px]
+    const float* inv_gain;  // [n_gains][frame_px]
+};
+
+// Energy of a multi-gain pixel (frame-relative index px) whose unit's common
+// mode is cm: stage 0 subtracts the common mode, other stages do not, and a
+// stage beyond the maps is a bad pixel with energy 0.
+__device__ __forceinline__ float mg_energy(const MultiGain& mg, uint32_t frame_px, uint16_t w,
+                                           size_t px, float cm) {
+    const uint32_t st = (uint32_t)w >> mg.shift;
+    if (st >= mg.n_gains) return 0.0f;
+    const size_t at = (size_t)st * frame_px + px;
+    const float d = __fsub_rn(__uint2float_rn((uint32_t)w & mg.vmask), mg.ped[at]);
+    return __fmul_rn(st == 0 ? __fsub_rn(d, cm) : d, mg.inv_gain[at]);
+}
+
 // Common-mode values per frame: one per unit, then for the stacked mean one
 // per module row and one per module column.
 __host__ __device__ inline uint32_t cm_per_frame(const ChainParams& p) {
@@ -75,17 +96,21 @@ struct CallOut {
 
 // Launchers (pd_chain.cu).  All are asynchronous on `stream` and return the
 // CUDA launch status.
+// mg: NULL for single-gain data.
 cudaError_t launch_cm_select(const ChainParams& p, const uint16_t* raw,
-                             uint32_t n_frames, float* cm, cudaStream_t stream);
+                             uint32_t n_frames, float* cm, cudaStream_t stream,
+                             const MultiGain* mg = nullptr);
 cudaError_t launch_stencil(const ChainParams& p, const uint16_t* raw,
                            uint32_t n_frames, uint32_t frame_base,
-                           const CallOut& out, cudaStream_t stream);
+                           const CallOut& out, cudaStream_t stream,
+                           const MultiGain* mg = nullptr);
 size_t cm_select_smem_bytes(const ChainParams& p);
 // Matched-filter stencil (pd_matched.cu); compile_bank validates.
 bool compile_bank(const pd_filter_bank& bank, MatchedBank* out);
 cudaError_t launch_matched(const ChainParams& p, const MatchedBank* bank_dev,
                            const uint16_t* raw, uint32_t n_frames, uint32_t frame_base,
-                           const CallOut& out, cudaStream_t stream);
+                           const CallOut& out, cudaStream_t stream,
+                           const MultiGain* mg = nullptr);
 // The paper's mean estimator, one stage or three stacked (pd_cm_mean.cu).
 cudaError_t launch_cm_mean(const ChainParams& p, const uint16_t* raw, uint32_t n_frames,
                            float* cm, cudaStream_t stream);
@@ -95,7 +120,7 @@ int device_sm_count();
 // 5x5 patches of e / photon_kev around hits (pd_net.cu).
 cudaError_t launch_gather(const ChainParams& p, const uint16_t* raw, uint32_t frame_base,
                           const float* cm, const pd_hit* hits, uint32_t n, float* patches,
-                          cudaStream_t s);
+                          cudaStream_t s, const MultiGain* mg = nullptr);
 
 // Helpers of pd_process_noalloc (pd_api.cu).  None of them allocates.
 int internal_fail(int code, const char* why);

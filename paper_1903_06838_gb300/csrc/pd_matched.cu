@@ -54,11 +54,12 @@ __device__ __forceinline__ uint32_t hist_bin(float v, float neg_lo_s, float inv_
     return (uint32_t)t;
 }
 
-template <bool STACKED>
+template <bool STACKED, bool MG>
 __global__ void __launch_bounds__(kThreads)
     matched_kernel(ChainParams p, const MatchedBank* __restrict__ bank,
                    const uint16_t* __restrict__ raw, uint32_t frame_base, CallOut out,
-                   uint32_t tiles_y, uint32_t tiles_x, unsigned long long n_tiles) {
+                   uint32_t tiles_y, uint32_t tiles_x, unsigned long long n_tiles,
+                   MultiGain mg) {
     extern __shared__ uint32_t hsm[];  // [2][hist_bins]
     __shared__ float tile[kHY][kHX];
     __shared__ uint8_t row5[kHY][kTX];  // signal bits of columns c-2 .. c+2
@@ -102,10 +103,15 @@ __global__ void __launch_bounds__(kThreads)
                 const uint32_t off = (uint32_t)r * p.cols + (uint32_t)c;
                 const float cm = cmf[((uint32_t)r / p.unit_rows) * p.units_per_row +
                                      (uint32_t)c / p.unit_cols];
-                const float d = __fsub_rn(__uint2float_rn(fr[off]), p.ped[mod_base + off]);
-                float cc = __fsub_rn(d, cm);
-                if (STACKED) cc = __fsub_rn(__fsub_rn(cc, cmr[r]), cmc[c]);
-                const float e = __fmul_rn(cc, p.inv_gain[mod_base + off]);
+                float e;
+                if (MG) {
+                    e = mg_energy(mg, p.frame_px, fr[off], mod_base + off, cm);
+                } else {
+                    const float d = __fsub_rn(__uint2float_rn(fr[off]), p.ped[mod_base + off]);
+                    float cc = __fsub_rn(d, cm);
+                    if (STACKED) cc = __fsub_rn(__fsub_rn(cc, cmr[r]), cmc[c]);
+                    e = __fmul_rn(cc, p.inv_gain[mod_base + off]);
+                }
                 s = e > p.zero_thr ? e : 0.0f;
                 if (hr >= 1 && hr <= kTY && hc >= 2 && hc < kTX + 2) {
                     atomicAdd(&hpix[hist_bin(e, p.hist_neg_lo_s, p.hist_inv_w, p.hist_bins)], 1u);
@@ -285,7 +291,7 @@ bool compile_bank(const pd_filter_bank& b, MatchedBank* out) {
 
 cudaError_t launch_matched(const ChainParams& p, const MatchedBank* bank_dev,
                            const uint16_t* raw, uint32_t n_frames, uint32_t frame_base,
-                           const CallOut& out, cudaStream_t stream) {
+                           const CallOut& out, cudaStream_t stream, const MultiGain* mg) {
     const uint32_t tiles_y = (p.rows + kTY - 1) / kTY;
     const uint32_t tiles_x = (p.cols + kTX - 1) / kTX;
     const unsigned long long n_tiles =
@@ -294,7 +300,8 @@ cudaError_t launch_matched(const ChainParams& p, const MatchedBank* bank_dev,
     const size_t smem = 2 * (size_t)p.hist_bins * sizeof(uint32_t);
     static bool attr_set = false;
     if (!attr_set) {
-        for (auto k : {matched_kernel<false>, matched_kernel<true>}) {
+        for (auto k : {matched_kernel<false, false>, matched_kernel<true, false>,
+                       matched_kernel<false, true>}) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)(2 * PD_MAX_HIST_BINS * sizeof(uint32_t)));
             if (e != cudaSuccess) return e;
@@ -303,12 +310,16 @@ cudaError_t launch_matched(const ChainParams& p, const MatchedBank* bank_dev,
     }
     unsigned long long grid = (unsigned long long)device_sm_count() * 4;
     if (grid > n_tiles) grid = n_tiles;
-    if (p.cm_mode == PD_CM_MEAN_STACKED)
-        matched_kernel<true><<<(unsigned)grid, kThreads, smem, stream>>>(
-            p, bank_dev, raw, frame_base, out, tiles_y, tiles_x, n_tiles);
+    const MultiGain m = mg ? *mg : MultiGain{};
+    if (mg)
+        matched_kernel<false, true><<<(unsigned)grid, kThreads, smem, stream>>>(
+            p, bank_dev, raw, frame_base, out, tiles_y, tiles_x, n_tiles, m);
+    else if (p.cm_mode == PD_CM_MEAN_STACKED)
+        matched_kernel<true, false><<<(unsigned)grid, kThreads, smem, stream>>>(
+            p, bank_dev, raw, frame_base, out, tiles_y, tiles_x, n_tiles, m);
     else
-        matched_kernel<false><<<(unsigned)grid, kThreads, smem, stream>>>(
-            p, bank_dev, raw, frame_base, out, tiles_y, tiles_x, n_tiles);
+        matched_kernel<false, false><<<(unsigned)grid, kThreads, smem, stream>>>(
+            p, bank_dev, raw, frame_base, out, tiles_y, tiles_x, n_tiles, m);
     return cudaGetLastError();
 }
 

@@ -271,10 +271,11 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ gr,
 // module): e recomputed exactly as the chain does, with the call's common
 // mode of frame - frame_base (unit term, and for the stacked mean the module
 // row and column terms).
+template <bool MG>
 __global__ void gather_kernel(pd::ChainParams p, const uint16_t* __restrict__ raw,
                               uint32_t frame_base, const float* __restrict__ cm,
                               const pd_hit* __restrict__ hits, uint32_t n,
-                              float* __restrict__ patches) {
+                              float* __restrict__ patches, pd::MultiGain mg) {
     const uint32_t h = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (h >= n || lane >= NPOS) return;
@@ -287,14 +288,20 @@ __global__ void gather_kernel(pd::ChainParams p, const uint16_t* __restrict__ ra
         const size_t g = (size_t)m * p.module_px + (size_t)r * p.cols + c;
         const uint32_t unit = m * p.units_per_module +
                               ((uint32_t)r / p.unit_rows) * p.units_per_row + (uint32_t)c / p.unit_cols;
-        const float d = __fsub_rn(__uint2float_rn(raw[(size_t)f * p.frame_px + g]), p.ped[g]);
         const float* cmf = cm + (size_t)f * cm_per_frame(p);
-        float cc = __fsub_rn(d, cmf[unit]);
-        if (p.cm_mode == PD_CM_MEAN_STACKED)
-            cc = __fsub_rn(__fsub_rn(cc, cmf[p.units_per_frame + (size_t)m * p.rows + r]),
-                           cmf[p.units_per_frame + (size_t)p.n_modules * p.rows +
-                               (size_t)m * p.cols + c]);
-        const float e = __fmul_rn(cc, p.inv_gain[g]);
+        float e;
+        if (MG) {
+            e = pd::mg_energy(mg, p.frame_px, raw[(size_t)f * p.frame_px + g], g, cmf[unit]);
+        } else {
+            const float d =
+                __fsub_rn(__uint2float_rn(raw[(size_t)f * p.frame_px + g]), p.ped[g]);
+            float cc = __fsub_rn(d, cmf[unit]);
+            if (p.cm_mode == PD_CM_MEAN_STACKED)
+                cc = __fsub_rn(__fsub_rn(cc, cmf[p.units_per_frame + (size_t)m * p.rows + r]),
+                               cmf[p.units_per_frame + (size_t)p.n_modules * p.rows +
+                                   (size_t)m * p.cols + c]);
+            e = __fmul_rn(cc, p.inv_gain[g]);
+        }
         v = __fdiv_rn(e, p.photon_kev);
     }
     patches[(size_t)h * NPOS + lane] = v;
@@ -569,10 +576,16 @@ void pd_net_destroy(pd_net* n) {
 namespace pd {
 cudaError_t launch_gather(const ChainParams& p, const uint16_t* raw, uint32_t frame_base,
                           const float* cm, const pd_hit* hits, uint32_t n, float* patches,
-                          cudaStream_t s) {
+                          cudaStream_t s, const MultiGain* mg) {
     if (!n) return cudaSuccess;
     const uint32_t per = 8;  // hits per 256-thread block (one warp each)
-    gather_kernel<<<(n + per - 1) / per, 256, 0, s>>>(p, raw, frame_base, cm, hits, n, patches);
+    const MultiGain m = mg ? *mg : MultiGain{};
+    if (mg)
+        gather_kernel<true><<<(n + per - 1) / per, 256, 0, s>>>(p, raw, frame_base, cm, hits, n,
+                                                              patches, m);
+    else
+        gather_kernel<false><<<(n + per - 1) / per, 256, 0, s>>>(p, raw, frame_base, cm, hits, n,
+                                                               patches, m);
     return cudaGetLastError();
 }
 }  // namespace pd

@@ -46,6 +46,7 @@ assert HIT_DTYPE.itemsize == 24
 
 
 PD_MAX_FEATURES = 8
+PD_MAX_GAINS = 4
 
 
 class PdFilterBank(ctypes.Structure):
@@ -169,6 +170,8 @@ def _declare(lib):
     sig = {
         "pd_create": ([ctypes.POINTER(PdGeometry), vp, vp,
                        ctypes.POINTER(PdThresholds), ctypes.POINTER(vp)], i32),
+        "pd_create_multigain": ([ctypes.POINTER(PdGeometry), u32, u32, vp, vp,
+                                 ctypes.POINTER(PdThresholds), ctypes.POINTER(vp)], i32),
         "pd_query": ([vp, ctypes.POINTER(PdInfo)], i32),
         "pd_process": ([vp, vp, u32, u32, ctypes.POINTER(PdOutputs), vp], i32),
         "pd_process_noalloc": ([vp, vp, u32, u32, ctypes.POINTER(PdOutputs), vp], i32),
@@ -318,8 +321,11 @@ def make_thresholds(cm_cut_adu, zero_thr_kev, seed_thr_kev, photon_kev,
                         cm_min_count, hist_lo_kev, hist_bin_kev, hist_bins)
 
 
-def pd_create(geometry, pedestal, gain, thresholds) -> Context:
-    """geometry / thresholds: PdGeometry / PdThresholds or dicts of fields."""
+def pd_create(geometry, pedestal, gain, thresholds, n_gains: int = 0,
+              gain_shift: int = 0) -> Context:
+    """geometry / thresholds: PdGeometry / PdThresholds or dicts of fields.
+    n_gains > 0: an auto-ranging context (pd_create_multigain) whose
+    pedestal and gain hold one map per stage."""
     lib = load()
     if isinstance(geometry, dict):
         geometry = make_geometry(**geometry)
@@ -327,10 +333,16 @@ def pd_create(geometry, pedestal, gain, thresholds) -> Context:
         thresholds = make_thresholds(**thresholds)
     ped = np.ascontiguousarray(pedestal, np.float32).reshape(-1)
     gain = np.ascontiguousarray(gain, np.float32).reshape(-1)
-    npx = geometry.n_modules * geometry.rows * geometry.cols
+    npx = geometry.n_modules * geometry.rows * geometry.cols * max(1, n_gains)
     if ped.size != npx or gain.size != npx:
         raise ValueError("pedestal/gain size does not match the geometry")
     h = ctypes.c_void_p()
+    if n_gains:
+        _check(lib.pd_create_multigain(ctypes.byref(geometry), n_gains, gain_shift,
+                                       ped.ctypes.data, gain.ctypes.data,
+                                       ctypes.byref(thresholds), ctypes.byref(h)),
+               "pd_create_multigain")
+        return Context(h.value, geometry, thresholds)
     _check(lib.pd_create(ctypes.byref(geometry), ped.ctypes.data,
                          gain.ctypes.data, ctypes.byref(thresholds),
                          ctypes.byref(h)), "pd_create")
