@@ -424,6 +424,44 @@ def cm_variants_run(args, dev, det, ped, gain, frames, nf, peak, steps=5):
             "hits_per_frame": round(int(out.n_hits.item()) / nf, 1)}
         del out
         pd.pd_destroy(ctx)
+    res["multigain_3_stages"] = multigain_run(dev, det, nf, steps)
+    return res
+
+
+def multigain_run(dev, det, nf, steps, distinct=16):
+    """Auto-ranging words (3 gain stages, stage in bits 14-15) on the same
+    geometry: 16 distinct generated frames (noise, photons, three bright
+    spots per sensor switching pixels to stages 1 and 2) tiled to the batch
+    size; frames/s through pd_process."""
+    import torch
+    from paper_1903_06838_gb300 import pd, synth
+    ped, gain = synth.multigain_maps(det, 3)
+    raw, _ = synth.multigain_frames(det, ped, gain, 0, distinct, gain_shift=14)
+    stage = raw >> 14
+    frames = pd.frames_to_device(raw).to(dev).repeat((nf + distinct - 1) // distinct, 1, 1, 1)
+    frames = frames[:nf].contiguous()
+    ctx = pd.pd_create(det.geometry(), ped, gain, det.thresholds(), n_gains=3, gain_shift=14)
+    out = pd.Outputs(ctx, nf, nf * 16384, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        pd.pd_process(ctx, frames.data_ptr(), nf, 0, stream=stream, **out.ptrs())
+    torch.cuda.synchronize(dev)
+    pd.pd_set_profiling(ctx, True)
+    pd.pd_read_profile(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        pd.pd_process(ctx, frames.data_ptr(), nf, 0, stream=stream, **out.ptrs())
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    prof = pd.pd_read_profile(ctx)
+    ms = e0.elapsed_time(e1) / steps
+    res = {"frames_per_s": round(nf / (ms / 1e3), 1), "ms_per_step": round(ms, 3),
+           "kernel_ms_per_step": {k: round(v[1] / steps, 3) for k, v in prof.items()},
+           "stage_fractions": [round(float((stage == g).mean()), 5) for g in range(4)],
+           "hits_per_frame": round(int(out.n_hits.item()) / nf, 1)}
+    del out, frames
+    pd.pd_destroy(ctx)
     return res
 
 

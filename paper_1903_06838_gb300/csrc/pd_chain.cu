@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(kStThreads)
                    uint32_t tiles_x, unsigned long long n_tiles, MultiGain mg) {
     extern __shared__ uint32_t hsm[];
     __shared__ float tile[kHY][kHX];
+    __shared__ uint32_t s_ucol[kHX], s_urow[kHY];  // unit offsets of halo columns / rows
     uint32_t* hpix = hsm;
     uint32_t* hhit = hsm + p.hist_bins;
     for (uint32_t b = threadIdx.x; b < 2 * p.hist_bins; b += kStThreads) hsm[b] = 0;
@@ -82,6 +83,18 @@ __global__ void __launch_bounds__(kStThreads)
         const float* cmc = out.cm + (size_t)f * cm_per_frame(p) + p.units_per_frame +
                            (size_t)p.n_modules * p.rows + (size_t)m * p.cols;
 
+        // unit of each halo column and row (two divisions per column and row
+        // of the tile rather than per pixel)
+        for (int k = threadIdx.x; k < kHX + kHY; k += kStThreads) {
+            if (k < kHX) {
+                const int c = c0 + k - 1;
+                s_ucol[k] = c >= 0 && c < C ? (uint32_t)c / p.unit_cols : 0u;
+            } else {
+                const int r = r0 + (k - kHX) - 1;
+                s_urow[k - kHX] = r >= 0 && r < R ? ((uint32_t)r / p.unit_rows) * p.units_per_row : 0u;
+            }
+        }
+        __syncthreads();
         // 1. corrected signal of the tile and its 1-pixel halo
         for (int j = threadIdx.x; j < kHY * kHX; j += kStThreads) {
             const int hr = j / kHX, hc = j % kHX;
@@ -89,8 +102,7 @@ __global__ void __launch_bounds__(kStThreads)
             float s = 0.0f;
             if (r >= 0 && r < R && c >= 0 && c < C) {
                 const uint32_t off = (uint32_t)r * p.cols + (uint32_t)c;
-                const float cm = cmf[((uint32_t)r / p.unit_rows) * p.units_per_row +
-                                     (uint32_t)c / p.unit_cols];
+                const float cm = cmf[s_urow[hr] + s_ucol[hc]];
                 float e;
                 if (MG) {
                     e = mg_energy(mg, p.frame_px, fr[off], mod_base + off, cm);

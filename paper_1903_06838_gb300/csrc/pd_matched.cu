@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(kThreads)
     extern __shared__ uint32_t hsm[];  // [2][hist_bins]
     __shared__ float tile[kHY][kHX];
     __shared__ uint8_t row5[kHY][kTX];  // signal bits of columns c-2 .. c+2
+    __shared__ uint32_t s_ucol[kHX], s_urow[kHY];  // unit offsets of halo columns / rows
     __shared__ MatchedBank sb;
     uint32_t* hpix = hsm;
     uint32_t* hhit = hsm + p.hist_bins;
@@ -94,6 +95,18 @@ __global__ void __launch_bounds__(kThreads)
         const float* cmc = out.cm + (size_t)f * cm_per_frame(p) + p.units_per_frame +
                            (size_t)p.n_modules * p.rows + (size_t)m * p.cols;
 
+        // unit of each halo column and row (divisions per column and row, not
+        // per pixel)
+        for (int k = threadIdx.x; k < kHX + kHY; k += kThreads) {
+            if (k < kHX) {
+                const int c = c0 + k - 2;
+                s_ucol[k] = c >= 0 && c < C ? (uint32_t)c / p.unit_cols : 0u;
+            } else {
+                const int r = r0 + (k - kHX) - 1;
+                s_urow[k - kHX] = r >= 0 && r < R ? ((uint32_t)r / p.unit_rows) * p.units_per_row : 0u;
+            }
+        }
+        __syncthreads();
         // 1. zeroed signal of the tile and its halo
         for (int j = threadIdx.x; j < kHY * kHX; j += kThreads) {
             const int hr = j / kHX, hc = j % kHX;
@@ -101,8 +114,7 @@ __global__ void __launch_bounds__(kThreads)
             float s = 0.0f;
             if (r >= 0 && r < R && c >= 0 && c < C) {
                 const uint32_t off = (uint32_t)r * p.cols + (uint32_t)c;
-                const float cm = cmf[((uint32_t)r / p.unit_rows) * p.units_per_row +
-                                     (uint32_t)c / p.unit_cols];
+                const float cm = cmf[s_urow[hr] + s_ucol[hc]];
                 float e;
                 if (MG) {
                     e = mg_energy(mg, p.frame_px, fr[off], mod_base + off, cm);
