@@ -64,14 +64,26 @@ __global__ void __launch_bounds__(kStThreads)
 
     const int R = (int)p.rows, C = (int)p.cols;
     const int lane = threadIdx.x & 31;
+    __shared__ uint32_t s_at[4];  // the tile's column, row, module and frame
+    __shared__ uint16_t s_list[kTY * kTX];  // the tile's seed candidates
+    __shared__ uint32_t s_nc;
     for (unsigned long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        unsigned long long q = t;
-        const int tx = (int)(q % tiles_x);
-        q /= tiles_x;
-        const int ty = (int)(q % tiles_y);
-        q /= tiles_y;
-        const uint32_t m = (uint32_t)(q % p.n_modules);
-        const uint32_t f = (uint32_t)(q / p.n_modules);
+        // one thread splits the tile index (64-bit divisions are long
+        // instruction sequences; every thread doing them cost more than
+        // the tile's pixels)
+        if (threadIdx.x == 0) {
+            unsigned long long q = t;
+            s_at[0] = (uint32_t)(q % tiles_x);
+            q /= tiles_x;
+            s_at[1] = (uint32_t)(q % tiles_y);
+            q /= tiles_y;
+            s_at[2] = (uint32_t)(q % p.n_modules);
+            s_at[3] = (uint32_t)(q / p.n_modules);
+            s_nc = 0;
+        }
+        __syncthreads();
+        const int tx = (int)s_at[0], ty = (int)s_at[1];
+        const uint32_t m = s_at[2], f = s_at[3];
         const int r0 = ty * kTY, c0 = tx * kTX;
         const size_t mod_base = (size_t)m * p.module_px;
         const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
@@ -123,17 +135,36 @@ __global__ void __launch_bounds__(kStThreads)
         }
         __syncthreads();
 
-        // 2. seeds, sums, count, centroid; warp-aggregated emission
+        // 2. pixels above the seed threshold into a list (warp-aggregated), so
+        //    that the seed tests below run with every lane busy
         for (int base = 0; base < kTY * kTX; base += kStThreads) {
             const int j = base + threadIdx.x;
             const int ir = j / kTX, ic = j % kTX;
-            const int r = r0 + ir, c = c0 + ic;
+            const bool cand = r0 + ir < R && c0 + ic < C && tile[ir + 1][ic + 1] > p.seed_thr;
+            const uint32_t bal = __ballot_sync(0xffffffffu, cand);
+            if (bal) {
+                const int lead = __ffs(bal) - 1;
+                uint32_t at0 = 0;
+                if (lane == lead) at0 = atomicAdd(&s_nc, (uint32_t)__popc(bal));
+                at0 = __shfl_sync(0xffffffffu, at0, lead);
+                if (cand) s_list[at0 + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)j;
+            }
+        }
+        __syncthreads();
+        const uint32_t n_cand = s_nc;
+
+        // 3. seeds, sums, count, centroid; warp-aggregated emission
+        for (uint32_t base = 0; base < n_cand; base += kStThreads) {
+            const uint32_t k = base + threadIdx.x;
             bool emit = false;
             pd_hit h;
             uint32_t n = 0, pix = 0;
-            if (r < R && c < C) {
+            if (k < n_cand) {
+                const int j = s_list[k];
+                const int ir = j / kTX, ic = j % kTX;
+                const int r = r0 + ir, c = c0 + ic;
                 const float sp = tile[ir + 1][ic + 1];
-                if (sp > p.seed_thr) {
+                {
                     bool seed = true;
 #pragma unroll
                     for (int dy = -1; dy <= 1; dy++)

@@ -78,14 +78,26 @@ __global__ void __launch_bounds__(kThreads)
     const int R = (int)p.rows, C = (int)p.cols;
     const int lane = threadIdx.x & 31;
     const uint32_t nf = sb.n_features;
+    __shared__ uint32_t s_at[4];  // the tile's column, row, module and frame
+    __shared__ uint32_t s_list[kTY * kTX];  // pixel j | window mask << 10
+    __shared__ uint32_t s_nc;
     for (unsigned long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        unsigned long long q = t;
-        const int tx = (int)(q % tiles_x);
-        q /= tiles_x;
-        const int ty = (int)(q % tiles_y);
-        q /= tiles_y;
-        const uint32_t m = (uint32_t)(q % p.n_modules);
-        const uint32_t f = (uint32_t)(q / p.n_modules);
+        // one thread splits the tile index (64-bit divisions are long
+        // instruction sequences; every thread doing them cost more than
+        // the tile's pixels)
+        if (threadIdx.x == 0) {
+            unsigned long long q = t;
+            s_at[0] = (uint32_t)(q % tiles_x);
+            q /= tiles_x;
+            s_at[1] = (uint32_t)(q % tiles_y);
+            q /= tiles_y;
+            s_at[2] = (uint32_t)(q % p.n_modules);
+            s_at[3] = (uint32_t)(q / p.n_modules);
+            s_nc = 0;
+        }
+        __syncthreads();
+        const int tx = (int)s_at[0], ty = (int)s_at[1];
+        const uint32_t m = s_at[2], f = s_at[3];
         const int r0 = ty * kTY, c0 = tx * kTX;
         const size_t mod_base = (size_t)m * p.module_px;
         const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
@@ -143,18 +155,39 @@ __global__ void __launch_bounds__(kThreads)
         }
         __syncthreads();
 
-        // 2. the bank at every pixel whose window holds signal
+        // 2. pixels whose window holds signal into a list (warp-aggregated),
+        //    so that the bank runs with every lane busy
         for (int base = 0; base < kTY * kTX; base += kThreads) {
             const int j = base + threadIdx.x;
             const int ir = j / kTX, ic = j % kTX;
-            const int r = r0 + ir, c = c0 + ic;
-            bool emit = false;
-            pd_hit h;
-            uint32_t n = 0, pix = 0;
             const uint32_t win = (uint32_t)row5[ir][ic] | (uint32_t)row5[ir + 1][ic] << 5 |
                                  (uint32_t)row5[ir + 2][ic] << 10 |
                                  (uint32_t)row5[ir + 3][ic] << 15;
-            if (r < R && c < C && win) {
+            const bool cand = r0 + ir < R && c0 + ic < C && win;
+            const uint32_t bal = __ballot_sync(0xffffffffu, cand);
+            if (bal) {
+                const int lead = __ffs(bal) - 1;
+                uint32_t at0 = 0;
+                if (lane == lead) at0 = atomicAdd(&s_nc, (uint32_t)__popc(bal));
+                at0 = __shfl_sync(0xffffffffu, at0, lead);
+                if (cand) s_list[at0 + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)j | win << 10;
+            }
+        }
+        __syncthreads();
+        const uint32_t n_cand = s_nc;
+
+        // 3. the bank at the listed pixels
+        for (uint32_t base = 0; base < n_cand; base += kThreads) {
+            const uint32_t k = base + threadIdx.x;
+            bool emit = false;
+            pd_hit h;
+            uint32_t n = 0, pix = 0;
+            const uint32_t e_k = k < n_cand ? s_list[k] : 0u;
+            const int j = (int)(e_k & 1023u);
+            const uint32_t win = e_k >> 10;
+            const int ir = j / kTX, ic = j % kTX;
+            const int r = r0 + ir, c = c0 + ic;
+            if (k < n_cand) {
                 // window tap (i, j) is tile[ir + i][ic + j]
                 const float* w = &tile[ir][ic];
                 float E = 0.0f, dx = 0.0f, dy = 0.0f;
