@@ -173,43 +173,81 @@ __global__ void prep_weights(const float* __restrict__ w, uint8_t* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// conv1 + conv2 on tiles of 64 hits; h2 out as bf16 [n][800].
-//   conv1: the 13 im2col tiles (128 rows x 16 taps, 4 KB each) are built at
-//   once and their 13 MMAs issued back to back into 13 TMEM column blocks.
-//   conv2: an implicit GEMM read in place: h1 is kept per position as a
-//   64-hit x 32-channel K-major block (4 KB), so the contribution of tap k to
-//   position p is two 64x32x16 MMAs of block nb(p, k) against the W2 slice of
-//   tap k; taps outside the patch are skipped (zero padding costs nothing).
-//   Positions go in groups of 4 with three groups in flight in TMEM, so the
-//   epilogue of one group runs while the next two groups' MMAs execute.
-constexpr uint32_t CV_W2 = 0, CV_W1 = CV_W2 + W2_BYTES, CV_X0 = CV_W1 + W1_BYTES,
-                   CV_H1 = CV_X0 + TB * NPOS * 4, CV_A = CV_H1 + TB * NPOS * C1 * 2,
-                   CV_SMEM = CV_A + 13 * 4096;
-constexpr uint32_t kConvTmemCols = 512;  // 13 conv1 blocks of 32 columns
-constexpr int kGroup = 4;                // conv2 positions per TMEM group
-constexpr int kGroupBufs = 3;            // conv2 groups in flight
-static_assert(CV_H1 % 128 == 0 && CV_A % 128 == 0, "alignment");
-static_assert(kGroupBufs * kGroup * 32 <= (int)kConvTmemCols, "conv2 groups fit TMEM");
+// conv1 + conv2 on tiles of 64 hits, h2 out as bf16 [n][800]; one CTA of 512
+// threads per SM with specialised warps:
+//   warps 0-7   conv1 on the CUDA cores (bf16 operands, float32 fused
+//               multiply-adds) into one of two h1 stages: per position a
+//               64-hit x 32-channel K-major block (4 KB), 100 KB per stage
+//   warps 8-11  lane 0 of warp 8 + b issues the conv2 MMAs of the position
+//               groups that use TMEM buffer b (128 columns, 4 positions):
+//               an implicit GEMM read in place, the contribution of tap k to
+//               position p being two 64x32x16 MMAs of h1 block nb(p, k)
+//               against the W2 slice of tap k (taps outside the patch are not
+//               issued).  One thread issues a small MMA about every 60
+//               cycles; four issuing threads bring that to about 25.
+//   warps 12-15 the epilogue: TMEM -> bias, ReLU, bf16 -> h2 (warp 12 + q
+//               reads TMEM lanes 32q..32q+31)
+// mbarriers hand the stages and TMEM buffers around (h1 full / empty, TMEM
+// full / empty), so conv1 of the next tile, conv2 MMAs and the epilogue of
+// earlier groups overlap.  Every wait is bounded; a timeout sets *err, stops
+// every role, and the issuing lane waits (bounded) for its last commit
+// before TMEM is freed.
+constexpr int WS_PROD_WARPS = 8, WS_MMA_WARP0 = 8, WS_EPI_WARP0 = 12;
+constexpr int WS_PROD = WS_PROD_WARPS * 32, WS_THREADS = 512;
+constexpr uint32_t H1_STAGE = TB * NPOS * C1 * 2;  // 102 400 bytes
+constexpr uint32_t WS_W2 = 0, WS_H1 = WS_W2 + W2_BYTES, WS_X = WS_H1 + 2 * H1_STAGE,
+                   WS_W1 = WS_X + TB * NPOS * 2, WS_SMEM = WS_W1 + (9 * C1 + C1) * 4;
+constexpr uint32_t kConvTmemCols = 512;
+constexpr int kGroup = 4;     // conv2 positions per TMEM buffer
+constexpr int kTBufs = 4;     // TMEM buffers of kGroup * 32 columns
+constexpr int NG = (NPOS + kGroup - 1) / kGroup;
+static_assert(WS_H1 % 128 == 0 && H1_STAGE % 128 == 0 && WS_W1 % 16 == 0, "alignment");
+static_assert(kTBufs * kGroup * 32 <= (int)kConvTmemCols, "TMEM buffers");
 
-__global__ void __launch_bounds__(256, 1)
+__device__ __forceinline__ void bar_init_n(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void producers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(WS_PROD) : "memory");
+}
+
+__global__ void __launch_bounds__(WS_THREADS, 1)
     conv_kernel(const float* __restrict__ x, int n, const float* __restrict__ w,
                 const uint8_t* __restrict__ img, uint16_t* __restrict__ h2, int* err) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_bar[1 + kGroupBufs];  // 0: conv1, then conv2 groups
+    __shared__ volatile int s_abort;
+    __shared__ int s_prod_go;  // the producers' uniform decision for a tile
+    __shared__ __align__(8) uint64_t s_h1_full[2], s_h1_empty[2], s_t_full[kTBufs],
+        s_t_empty[kTBufs];
     __shared__ int s_nb[NPOS * 9];
     // per position: its valid (tap, channel half) MMAs as descriptor address
     // offsets (16-byte units): A block of the neighbour | W2 slice << 16
     __shared__ uint32_t s_mma[NPOS * 18];
     __shared__ int s_nmma[NPOS];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    float* sx0 = reinterpret_cast<float*>(sm + CV_X0);
-    const uint32_t a_addr = smem_u32(sm + CV_A), w1_addr = smem_u32(sm + CV_W1),
-                   w2_addr = smem_u32(sm + CV_W2), h1_addr = smem_u32(sm + CV_H1);
+    uint16_t* sx = reinterpret_cast<uint16_t*>(sm + WS_X);      // [64][25] bf16 patches
+    float* w1t = reinterpret_cast<float*>(sm + WS_W1);           // [9][32] bf16-valued
+    float* b1 = w1t + 9 * C1;                                    // [32]
+    const uint32_t w2_addr = smem_u32(sm + WS_W2), h1_addr = smem_u32(sm + WS_H1);
 
     if (warp == 0) tmem_alloc(&s_tmem, kConvTmemCols);
-    if (tid == 0)
-        for (int b = 0; b < 1 + kGroupBufs; b++) bar_init(&s_bar[b]);
+    if (tid == 0) {
+        for (int b = 0; b < 2; b++) {
+            bar_init_n(&s_h1_full[b], WS_PROD);
+            bar_init_n(&s_h1_empty[b], kTBufs);  // one commit per issuing thread
+        }
+        for (int b = 0; b < kTBufs; b++) {
+            bar_init_n(&s_t_full[b], 1);
+            bar_init_n(&s_t_empty[b], 4);
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     for (int i = tid; i < NPOS * 9; i += blockDim.x) s_nb[i] = nb(i / 9, i % 9);
     if (tid < NPOS) {
         int m = 0;
@@ -224,176 +262,200 @@ __global__ void __launch_bounds__(256, 1)
         s_nmma[tid] = m;
     }
     for (uint32_t i = tid; i < W2_BYTES / 16; i += blockDim.x)
-        reinterpret_cast<uint4*>(sm + CV_W2)[i] = reinterpret_cast<const uint4*>(img + OFF_W2)[i];
-    for (uint32_t i = tid; i < W1_BYTES / 16; i += blockDim.x)
-        reinterpret_cast<uint4*>(sm + CV_W1)[i] = reinterpret_cast<const uint4*>(img + OFF_W1)[i];
+        reinterpret_cast<uint4*>(sm + WS_W2)[i] = reinterpret_cast<const uint4*>(img + OFF_W2)[i];
+    for (int i = tid; i < 9 * C1; i += blockDim.x) {
+        const int k = i / C1, c = i % C1;
+        w1t[i] = bf16_round(w[OW1 + c * 9 + k]);
+    }
+    for (int i = tid; i < C1; i += blockDim.x) b1[i] = w[OB1 + i];
     fence_async_smem();
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = s_tmem;
-    uint32_t par[1 + kGroupBufs] = {};
-    bool pend[1 + kGroupBufs] = {};
-    bool ok = true;
-    // every thread waits; __syncthreads_and makes the outcome uniform, and
-    // the phase advances only on success
-    auto waitp = [&](int b) -> bool {
-        const bool r = __syncthreads_and(wait_bar(&s_bar[b], par[b]));
-        if (r) {
-            par[b] ^= 1;
-            pend[b] = false;
-        }
-        return r;
-    };
-    const uint32_t id = idesc_bf16(128, 32);
     const int n_tiles = (n + TB - 1) / TB;
-    const int half = warp >> 2;               // column half of the epilogue
-    const int erow = (warp & 3) * 32 + lane;  // TMEM lane = tile row
-    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-
-    const uint32_t id64 = idesc_bf16(64, 32);
-    // conv2 MMAs of group g (positions kGroup*g ...) into TMEM group buffer
-    // g % kGroupBufs;
-    // issued by thread 0
-    const uint64_t a_desc0 = sdesc(h1_addr, 1024, 128), b_desc0 = sdesc(w2_addr, 512, 128);
-    auto issue_group = [&](int g) {
-        for (int i = 0; i < kGroup; i++) {
-            const int p = g * kGroup + i;
-            if (p >= NPOS) break;
-            const uint32_t d = tmem + (uint32_t)(((g % kGroupBufs) * kGroup + i) * 32);
-            const int nm = s_nmma[p];
-            uint32_t o[18];
-#pragma unroll
-            for (int e = 0; e < 18; e++) o[e] = s_mma[p * 18 + e];  // table loads first
-#pragma unroll
-            for (int e = 0; e < 18; e++)
-                if (e < nm) mma(d, a_desc0 + (o[e] & 0xFFFFu), b_desc0 + (o[e] >> 16), id64, e > 0);
+    // bounded wait that also gives up once another role has aborted
+    auto wait_or_abort = [&](uint64_t* bar, uint32_t parity) -> bool {
+        const uint32_t a = smem_u32(bar);
+        for (uint32_t it = 0; it < kWaitLimit; it++) {
+            uint32_t ok;
+            asm volatile(
+                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                "selp.u32 %0, 1, 0, p;\n}"
+                : "=r"(ok)
+                : "r"(a), "r"(parity)
+                : "memory");
+            if (ok) return true;
+            if ((it & 255) == 255 && s_abort) return false;
         }
-        commit(&s_bar[1 + g % kGroupBufs]);
+        s_abort = 1;
+        return false;
     };
-    constexpr int NG = (NPOS + kGroup - 1) / kGroup;
-    // M = 64 accumulators: row r in TMEM lane (r / 16) * 32 + r % 16
-    const int qhit = (warp & 3) * 16 + lane;  // this lane's hit (lane < 16)
 
-    for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        const int hit0 = t * TB, nh = min(TB, n - hit0);
-        for (int e = tid; e < TB * NPOS; e += blockDim.x) {
-            const int hit = e / NPOS;
-            sx0[e] = hit < nh ? bf16_round(x[(size_t)hit0 * NPOS + e]) : 0.0f;
-        }
-        __syncthreads();
-        // ---- conv1: all 13 tiles of 128 (position, hit) rows at once -------
-        // row p * 64 + hit of the im2col: the 9 taps of x0 around p (zero
-        // outside the patch), then 7 zero columns; rows 1600..1663 are zero
-        for (int e = tid; e < 13 * 128; e += blockDim.x) {
-            const int p = e >> 6, hit = e & 63;
-            uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            if (p < NPOS) {
-                const float* xr = sx0 + hit * NPOS;
+    if (warp < WS_PROD_WARPS) {
+        // ---- conv1 producers ------------------------------------------------
+        const int ptid = tid;
+        int i = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, i++) {
+            const int stage = i & 1;
+            // one thread waits for the stage; every producer follows its
+            // decision, so the named barriers below stay uniform
+            if (ptid == 0)
+                s_prod_go = wait_or_abort(&s_h1_empty[stage], ((i >> 1) & 1) ^ 1) && !s_abort;
+            producers_sync();  // also: the previous tile's patches are no longer read
+            if (!s_prod_go) break;
+            const int hit0 = t * TB, nh = min(TB, n - hit0);
+            for (int e = ptid; e < TB * NPOS; e += WS_PROD) {
+                const int hit = e / NPOS;
+                sx[e] = hit < nh ? bf16_bits(x[(size_t)hit0 * NPOS + e]) : (uint16_t)0;
+            }
+            producers_sync();
+            uint8_t* h1 = sm + WS_H1 + stage * H1_STAGE;
+            for (int e = ptid; e < NPOS * TB; e += WS_PROD) {
+                const int p = e >> 6, hit = e & 63;
+                const uint16_t* xr = sx + hit * NPOS;
+                float acc[C1];
+#pragma unroll
+                for (int c = 0; c < C1; c++) acc[c] = 0.0f;
 #pragma unroll
                 for (int k = 0; k < 9; k++) {
                     const int q = s_nb[p * 9 + k];
-                    const uint32_t b16 = q >= 0 ? (uint32_t)bf16_bits(xr[q]) : 0u;
-                    v[k >> 1] |= b16 << ((k & 1) * 16);
-                }
-            }
-            const int j = e >> 7, r = e & 127;
-            uint8_t* tile = sm + CV_A + j * 4096;
-            *reinterpret_cast<uint4*>(tile + cm_off(r, 0, 128)) = make_uint4(v[0], v[1], v[2], v[3]);
-            *reinterpret_cast<uint4*>(tile + cm_off(r, 8, 128)) = make_uint4(v[4], v[5], v[6], v[7]);
-        }
-        fence_async_smem();
-        fence_before();
-        __syncthreads();
-        fence_after();
-        if (tid == 0) {
-            for (int j = 0; j < 13; j++)
-                mma(tmem + 32 * j, sdesc(a_addr + j * 4096, 16 * 128, 128),
-                    sdesc(w1_addr, 4 * 128, 128), id, 0);
-            commit(&s_bar[0]);
-        }
-        pend[0] = true;
-        ok = waitp(0);
-        if (!ok) break;
-        fence_after();
-        for (int j = 0; j < 13; j++) {
-            uint32_t r[16];
-            tmem_ld16(tmem + lane_base + 32 * j + half * 16, r);
-            const int gr = j * 128 + erow, p = gr / TB, hit = gr % TB;
-            if (p < NPOS) {
-                uint32_t pk[8];
+                    if (q < 0) continue;
+                    const float xv = __uint_as_float((uint32_t)xr[q] << 16);
+                    const float4* wk = reinterpret_cast<const float4*>(w1t + k * C1);
 #pragma unroll
-                for (int c = 0; c < 16; c += 2) {
-                    const int ch = half * 16 + c;
-                    const float a0 = fmaxf(__uint_as_float(r[c]) + w[OB1 + ch], 0.0f);
-                    const float a1 = fmaxf(__uint_as_float(r[c + 1]) + w[OB1 + ch + 1], 0.0f);
-                    pk[c / 2] = (uint32_t)bf16_bits(a0) | ((uint32_t)bf16_bits(a1) << 16);
+                    for (int j = 0; j < C1 / 4; j++) {
+                        const float4 wv = wk[j];
+                        acc[4 * j] = __fmaf_rn(wv.x, xv, acc[4 * j]);
+                        acc[4 * j + 1] = __fmaf_rn(wv.y, xv, acc[4 * j + 1]);
+                        acc[4 * j + 2] = __fmaf_rn(wv.z, xv, acc[4 * j + 2]);
+                        acc[4 * j + 3] = __fmaf_rn(wv.w, xv, acc[4 * j + 3]);
+                    }
                 }
-                // h1 block of position p, K-major over 32 channels
-                uint8_t* blk = sm + CV_H1 + p * 4096;
-                *reinterpret_cast<uint4*>(blk + cm_off(hit, half * 16, TB)) =
-                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                *reinterpret_cast<uint4*>(blk + cm_off(hit, half * 16 + 8, TB)) =
-                    make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            }
-        }
-        fence_before();
-        __syncthreads();
-        // ---- conv2: implicit GEMM on h1 in place, groups of positions ----
-        fence_async_smem();  // h1 is read by the tensor cores
-        fence_before();
-        __syncthreads();
-        fence_after();
-        if (tid == 0)
-            for (int g = 0; g < kGroupBufs && g < NG; g++) issue_group(g);
-        for (int g = 0; g < kGroupBufs && g < NG; g++) pend[1 + g] = true;
-        for (int g = 0; g < NG && ok; g++) {
-            ok = waitp(1 + g % kGroupBufs);
-            if (!ok) break;
-            fence_after();
-            for (int i = 0; i < kGroup; i++) {
-                const int p = g * kGroup + i;
-                if (p >= NPOS) break;
-                uint32_t r[16];
-                tmem_ld16(tmem + lane_base + (uint32_t)(((g % kGroupBufs) * kGroup + i) * 32) +
-                              half * 16,
-                          r);
-                if (lane < 16 && qhit < nh) {
-                    uint32_t pk[8];
+                uint8_t* blk = h1 + p * 4096;
 #pragma unroll
-                    for (int c = 0; c < 16; c += 2) {
-                        const int ch = half * 16 + c;
-                        const float a0 = fmaxf(__uint_as_float(r[c]) + w[OB2 + ch], 0.0f);
-                        const float a1 = fmaxf(__uint_as_float(r[c + 1]) + w[OB2 + ch + 1], 0.0f);
+                for (int j = 0; j < C1 / 8; j++) {
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int c = 0; c < 8; c += 2) {
+                        const int ch = 8 * j + c;
+                        const float a0 = fmaxf(acc[ch] + b1[ch], 0.0f);
+                        const float a1 = fmaxf(acc[ch + 1] + b1[ch + 1], 0.0f);
                         pk[c / 2] = (uint32_t)bf16_bits(a0) | ((uint32_t)bf16_bits(a1) << 16);
                     }
-                    uint4* dst = reinterpret_cast<uint4*>(h2 + (size_t)(hit0 + qhit) * K3 +
-                                                          p * C2 + half * 16);
-                    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    *reinterpret_cast<uint4*>(blk + cm_off(hit, 8 * j, TB)) =
+                        make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 }
             }
-            fence_before();
-            __syncthreads();
-            fence_after();
-            if (g + kGroupBufs < NG) {
-                if (tid == 0) issue_group(g + kGroupBufs);
-                pend[1 + g % kGroupBufs] = true;
+            fence_async_smem();  // h1 is read by the tensor cores
+            bar_arrive(&s_h1_full[stage]);
+        }
+    } else if (warp < WS_EPI_WARP0) {
+        // ---- conv2 MMA issue: lane 0 of warp 8 + b, TMEM buffer b -----------
+        const int ib = warp - WS_MMA_WARP0;
+        if (lane == 0) {
+            const uint32_t id64 = idesc_bf16(64, 32);
+            const uint64_t b_desc0 = sdesc(w2_addr, 512, 128);
+            int i = 0, gq = 0;  // local tile, global group sequence
+            bool issued = false;
+            uint64_t* last = nullptr;
+            uint32_t last_par = 0;
+            for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, i++) {
+                const int stage = i & 1;
+                if (!wait_or_abort(&s_h1_full[stage], (i >> 1) & 1)) break;
+                fence_after();
+                const uint64_t a_desc0 = sdesc(h1_addr + stage * H1_STAGE, 1024, 128);
+                bool ok = true;
+                for (int g = 0; g < NG; g++, gq++) {
+                    const int b = gq % kTBufs;
+                    if (b != ib) continue;  // another thread's buffer
+                    if (!wait_or_abort(&s_t_empty[b], ((gq / kTBufs) & 1) ^ 1)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    for (int pi = 0; pi < kGroup; pi++) {
+                        const int p = g * kGroup + pi;
+                        if (p >= NPOS) break;
+                        const uint32_t d = tmem + (uint32_t)((b * kGroup + pi) * 32);
+                        const int nm = s_nmma[p];
+                        const uint32_t* tab = s_mma + p * 18;
+                        for (int e = 0; e < nm; e++) {
+                            const uint32_t o = tab[e];
+                            mma(d, a_desc0 + (o & 0xFFFFu), b_desc0 + (o >> 16), id64, e);
+                        }
+                    }
+                    commit(&s_t_full[b]);
+                    issued = true;
+                    last = &s_t_full[b];
+                    last_par = (gq / kTBufs) & 1;
+                }
+                if (!ok) break;
+                commit(&s_h1_empty[stage]);  // stage free once these MMAs complete
+            }
+            if (s_abort) {
+                atomicExch(err, 1);
+                if (issued) wait_bar(last, last_par);  // bounded
             }
         }
-        if (!ok) break;
-        __syncthreads();  // h1, x0 and the A tiles are reused by the next tile
-    }
-    if (!ok && tid == 0) {
-        atomicExch(err, 1);
-        // MMAs may still be in flight: wait (bounded) for every outstanding
-        // commit before tensor memory is freed
-        for (int b = 0; b < 1 + kGroupBufs; b++)
-            if (pend[b]) wait_bar(&s_bar[b], par[b]);
+        __syncwarp();
+    } else if (warp >= WS_EPI_WARP0) {
+        // ---- conv2 epilogue (warps 8-11, TMEM lane quadrant q) ---------------
+        const int q = warp - WS_EPI_WARP0;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        const int qhit = q * 16 + lane;  // M = 64: row r in TMEM lane (r / 16) * 32 + r % 16
+        float b2[C2];
+#pragma unroll
+        for (int c = 0; c < C2; c++) b2[c] = w[OB2 + c];
+        int gq = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+            const int hit0 = t * TB, nh = min(TB, n - hit0);
+            bool ok = true;
+            for (int g = 0; g < NG; g++, gq++) {
+                const int b = gq % kTBufs;
+                // lane 0 waits and the warp follows it (tcgen05.ld is warp-wide)
+                const int got = __shfl_sync(
+                    0xffffffffu, lane == 0 ? (int)wait_or_abort(&s_t_full[b], (gq / kTBufs) & 1) : 0,
+                    0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                for (int pi = 0; pi < kGroup; pi++) {
+                    const int p = g * kGroup + pi;
+                    if (p >= NPOS) break;
+                    uint32_t r[32];
+                    const uint32_t ta = tmem + lane_base + (uint32_t)((b * kGroup + pi) * 32);
+                    tmem_ld16(ta, *reinterpret_cast<uint32_t(*)[16]>(&r[0]));
+                    tmem_ld16(ta + 16, *reinterpret_cast<uint32_t(*)[16]>(&r[16]));
+                    if (lane < 16 && qhit < nh) {
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int c = 0; c < 32; c += 2) {
+                            const float a0 = fmaxf(__uint_as_float(r[c]) + b2[c], 0.0f);
+                            const float a1 = fmaxf(__uint_as_float(r[c + 1]) + b2[c + 1], 0.0f);
+                            pk[c / 2] = (uint32_t)bf16_bits(a0) | ((uint32_t)bf16_bits(a1) << 16);
+                        }
+                        uint4* dst = reinterpret_cast<uint4*>(h2 + (size_t)(hit0 + qhit) * K3 +
+                                                              p * C2);
+#pragma unroll
+                        for (int j = 0; j < 4; j++)
+                            dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2],
+                                                pk[4 * j + 3]);
+                    }
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) bar_arrive(&s_t_empty[b]);
+            }
+            if (!ok) break;
+        }
     }
     fence_before();
     __syncthreads();
     fence_after();
+    if (s_abort && tid == 0) atomicExch(err, 1);
     if (warp == 0) tmem_free(tmem, kConvTmemCols);
 }
 
@@ -548,7 +610,7 @@ cudaError_t forward(const float* w, const float* x, uint32_t n, uint8_t* img, ui
     cudaGetDevice(&dev);
     if (attr_dev != dev) {
         cudaError_t e = cudaFuncSetAttribute(conv_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, CV_SMEM);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, WS_SMEM);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(fc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      FC_SMEM);
@@ -557,7 +619,7 @@ cudaError_t forward(const float* w, const float* x, uint32_t n, uint8_t* img, ui
     }
     prep_weights<<<(NH * K3 + 255) / 256, 256, 0, s>>>(w, img);
     const int conv_tiles = (int)((n + TB - 1) / TB), fc_tiles = (int)((n + TF - 1) / TF);
-    conv_kernel<<<std::min(conv_tiles, sms), 256, CV_SMEM, s>>>(x, (int)n, w, img, h2, err);
+    conv_kernel<<<std::min(conv_tiles, sms), WS_THREADS, WS_SMEM, s>>>(x, (int)n, w, img, h2, err);
     fc_kernel<<<std::min(fc_tiles, sms), 256, FC_SMEM, s>>>(h2, (int)n, w, img, out, err);
     return cudaGetLastError();
 }
