@@ -295,6 +295,24 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     if (warp < WS_PROD_WARPS) {
         // ---- conv1 producers ------------------------------------------------
         const int ptid = tid;
+        // B fragments of W1 (bf16, K = taps) and the biases of this lane's
+        // channel pairs, for n-blocks of 8 channels
+        uint32_t bw[4][2];
+        float bias[4][2];
+        {
+            const int g = lane >> 2, tq = lane & 3;
+            auto w1b = [&](int ch, int k) -> uint32_t {
+                return k < 9 ? (uint32_t)bf16_bits(w[OW1 + ch * 9 + k]) : 0u;
+            };
+#pragma unroll
+            for (int nb = 0; nb < 4; nb++) {
+                const int ch = nb * 8 + g;
+                bw[nb][0] = w1b(ch, 2 * tq) | (w1b(ch, 2 * tq + 1) << 16);
+                bw[nb][1] = w1b(ch, 2 * tq + 8) | (w1b(ch, 2 * tq + 9) << 16);
+                bias[nb][0] = w[OB1 + nb * 8 + 2 * tq];
+                bias[nb][1] = w[OB1 + nb * 8 + 2 * tq + 1];
+            }
+        }
         int i = 0;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, i++) {
             const int stage = i & 1;
@@ -311,40 +329,39 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             }
             producers_sync();
             uint8_t* h1 = sm + WS_H1 + stage * H1_STAGE;
-            for (int e = ptid; e < NPOS * TB; e += WS_PROD) {
-                const int p = e >> 6, hit = e & 63;
-                const uint16_t* xr = sx + hit * NPOS;
-                float acc[C1];
-#pragma unroll
-                for (int c = 0; c < C1; c++) acc[c] = 0.0f;
-#pragma unroll
-                for (int k = 0; k < 9; k++) {
-                    const int q = s_nb[p * 9 + k];
-                    if (q < 0) continue;
-                    const float xv = __uint_as_float((uint32_t)xr[q] << 16);
-                    const float4* wk = reinterpret_cast<const float4*>(w1t + k * C1);
-#pragma unroll
-                    for (int j = 0; j < C1 / 4; j++) {
-                        const float4 wv = wk[j];
-                        acc[4 * j] = __fmaf_rn(wv.x, xv, acc[4 * j]);
-                        acc[4 * j + 1] = __fmaf_rn(wv.y, xv, acc[4 * j + 1]);
-                        acc[4 * j + 2] = __fmaf_rn(wv.z, xv, acc[4 * j + 2]);
-                        acc[4 * j + 3] = __fmaf_rn(wv.w, xv, acc[4 * j + 3]);
-                    }
-                }
+            // conv1 as warp-level m16n8k16 MMAs: a 16-row block is 16 hits of
+            // one position, K the 9 taps (7 zero columns), N 4 x 8 channels;
+            // lane (g, t) gathers its A fragment from the patches: rows g and
+            // g + 8, taps 2t, 2t + 1 and 2t + 8 (only t = 0 has tap 8)
+            const int pwarp = warp, g = lane >> 2, tq = lane & 3;
+            for (int rb = pwarp; rb < NPOS * (TB / 16); rb += WS_PROD_WARPS) {
+                const int p = rb >> 2, h0 = (rb & 3) * 16;
+                const int q0 = s_nb[p * 9 + 2 * tq], q1 = s_nb[p * 9 + 2 * tq + 1];
+                const int q2 = tq == 0 ? s_nb[p * 9 + 8] : -1;
+                const uint16_t* x0 = sx + (h0 + g) * NPOS;
+                const uint16_t* x1 = x0 + 8 * NPOS;
+                uint32_t a[4];
+                a[0] = (q0 >= 0 ? (uint32_t)x0[q0] : 0u) | (q1 >= 0 ? (uint32_t)x0[q1] << 16 : 0u);
+                a[1] = (q0 >= 0 ? (uint32_t)x1[q0] : 0u) | (q1 >= 0 ? (uint32_t)x1[q1] << 16 : 0u);
+                a[2] = q2 >= 0 ? (uint32_t)x0[q2] : 0u;
+                a[3] = q2 >= 0 ? (uint32_t)x1[q2] : 0u;
                 uint8_t* blk = h1 + p * 4096;
 #pragma unroll
-                for (int j = 0; j < C1 / 8; j++) {
-                    uint32_t pk[4];
-#pragma unroll
-                    for (int c = 0; c < 8; c += 2) {
-                        const int ch = 8 * j + c;
-                        const float a0 = fmaxf(acc[ch] + b1[ch], 0.0f);
-                        const float a1 = fmaxf(acc[ch + 1] + b1[ch + 1], 0.0f);
-                        pk[c / 2] = (uint32_t)bf16_bits(a0) | ((uint32_t)bf16_bits(a1) << 16);
-                    }
-                    *reinterpret_cast<uint4*>(blk + cm_off(hit, 8 * j, TB)) =
-                        make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                for (int nb = 0; nb < 4; nb++) {
+                    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+                        "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(bw[nb][0]),
+                          "r"(bw[nb][1]));
+                    const int ch = nb * 8 + 2 * tq;
+                    const __nv_bfloat162 v0 = __float22bfloat162_rn(
+                        make_float2(fmaxf(c[0] + bias[nb][0], 0.0f), fmaxf(c[1] + bias[nb][1], 0.0f)));
+                    const __nv_bfloat162 v1 = __float22bfloat162_rn(
+                        make_float2(fmaxf(c[2] + bias[nb][0], 0.0f), fmaxf(c[3] + bias[nb][1], 0.0f)));
+                    *reinterpret_cast<__nv_bfloat162*>(blk + cm_off(h0 + g, ch, TB)) = v0;
+                    *reinterpret_cast<__nv_bfloat162*>(blk + cm_off(h0 + g + 8, ch, TB)) = v1;
                 }
             }
             fence_async_smem();  // h1 is read by the tensor cores
