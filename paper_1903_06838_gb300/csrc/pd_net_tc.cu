@@ -146,6 +146,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 32 consecutive columns of this warp's 32 TMEM lanes, one wait
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // neighbour of position p at 3x3 offset k (k = 3 (dy + 1) + dx + 1), or -1
 __device__ __forceinline__ int nb(int p, int k) {
     const int y = p / 5 + k / 3 - 1, x = p % 5 + k % 3 - 1;
@@ -313,6 +329,19 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                 bias[nb][1] = w[OB1 + nb * 8 + 2 * tq + 1];
             }
         }
+        // a tile's patches are loaded into registers one tile ahead, so the
+        // global loads run during the previous tile's conv1
+        constexpr int XPER = (TB * NPOS + WS_PROD - 1) / WS_PROD;
+        float xn[XPER];
+        auto load_x = [&](int t) {
+            const int hit0 = t * TB, nh = t < n_tiles ? min(TB, n - hit0) : 0;
+#pragma unroll
+            for (int u = 0; u < XPER; u++) {
+                const int e = ptid + u * WS_PROD;
+                xn[u] = (e < TB * NPOS && e / NPOS < nh) ? x[(size_t)hit0 * NPOS + e] : 0.0f;
+            }
+        };
+        load_x(blockIdx.x);
         int i = 0;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, i++) {
             const int stage = i & 1;
@@ -322,11 +351,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                 s_prod_go = wait_or_abort(&s_h1_empty[stage], ((i >> 1) & 1) ^ 1) && !s_abort;
             producers_sync();  // also: the previous tile's patches are no longer read
             if (!s_prod_go) break;
-            const int hit0 = t * TB, nh = min(TB, n - hit0);
-            for (int e = ptid; e < TB * NPOS; e += WS_PROD) {
-                const int hit = e / NPOS;
-                sx[e] = hit < nh ? bf16_bits(x[(size_t)hit0 * NPOS + e]) : (uint16_t)0;
+#pragma unroll
+            for (int u = 0; u < XPER; u++) {
+                const int e = ptid + u * WS_PROD;
+                if (e < TB * NPOS) sx[e] = bf16_bits(xn[u]);
             }
+            load_x(t + gridDim.x);
             producers_sync();
             uint8_t* h1 = sm + WS_H1 + stage * H1_STAGE;
             // conv1 as warp-level m16n8k16 MMAs: a 16-row block is 16 hits of
@@ -443,16 +473,17 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                     const int p = g * kGroup + pi;
                     if (p >= NPOS) break;
                     uint32_t r[32];
-                    const uint32_t ta = tmem + lane_base + (uint32_t)((b * kGroup + pi) * 32);
-                    tmem_ld16(ta, *reinterpret_cast<uint32_t(*)[16]>(&r[0]));
-                    tmem_ld16(ta + 16, *reinterpret_cast<uint32_t(*)[16]>(&r[16]));
+                    tmem_ld32(tmem + lane_base + (uint32_t)((b * kGroup + pi) * 32), r);
                     if (lane < 16 && qhit < nh) {
                         uint32_t pk[16];
 #pragma unroll
                         for (int c = 0; c < 32; c += 2) {
-                            const float a0 = fmaxf(__uint_as_float(r[c]) + b2[c], 0.0f);
-                            const float a1 = fmaxf(__uint_as_float(r[c + 1]) + b2[c + 1], 0.0f);
-                            pk[c / 2] = (uint32_t)bf16_bits(a0) | ((uint32_t)bf16_bits(a1) << 16);
+                            const float2 z = __fadd2_rn(
+                                make_float2(__uint_as_float(r[c]), __uint_as_float(r[c + 1])),
+                                make_float2(b2[c], b2[c + 1]));
+                            const __nv_bfloat162 v =
+                                __float22bfloat162_rn(make_float2(fmaxf(z.x, 0.0f), fmaxf(z.y, 0.0f)));
+                            pk[c / 2] = *reinterpret_cast<const uint32_t*>(&v);
                         }
                         uint4* dst = reinterpret_cast<uint4*>(h2 + (size_t)(hit0 + qhit) * K3 +
                                                               p * C2);
