@@ -465,8 +465,7 @@ int create_impl(const pd_geometry* geometry, uint32_t n_gains, uint32_t gain_shi
     c->use_cm_big = g.cm_mode == PD_CM_MEDIAN && pd::cm_big_supported(p, c->cm_cfg);
     c->use_cm_rows = g.cm_mode == PD_CM_MEDIAN && !c->use_cm_big && pd::cm_rows_supported(p);
     c->band_cfg = pd::make_band_config(p);
-    // the band stencil reads one common-mode value per unit row segment
-    c->use_band = c->band_cfg.ok && g.cm_mode != PD_CM_MEAN_STACKED;
+    c->use_band = c->band_cfg.ok;
     c->fused_cfg = pd::make_fused_config(p);
     // the one-kernel chain computes the median (or nothing) itself
     c->use_fused = c->fused_cfg.ok && (g.cm_mode == PD_CM_MEDIAN || g.cm_mode == PD_CM_NONE);

@@ -491,8 +491,10 @@ struct BandShared {
 // Tiles first, first + step, ... < n_tiles of one call: tile t is band
 // t % n_bands of module (t / n_bands) % n_modules of frame t / (n_bands *
 // n_modules).  Zeroes this CTA's shared tile and histograms first and adds
-// the histograms to the context's at the end.
-template <int VEC>
+// the histograms to the context's at the end.  STACKED: the stacked mean
+// common mode, whose module-row and module-column terms follow the units'
+// values of each frame and are subtracted after the unit's.
+template <int VEC, bool STACKED = false>
 __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restrict__ raw,
                                  uint32_t frame_base, const CallOut& out, const BandConfig& bc,
                                  unsigned long long first, unsigned long long n_tiles,
@@ -503,6 +505,7 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
     uint32_t* hhit = hpix + p.hist_bins + 4;                     // hist_bins
     uint32_t* list = hhit + p.hist_bins;                         // kSeedCap
     float* cmt = reinterpret_cast<float*>(list + kSeedCap);      // (rb+2) * upr
+    float* crt = cmt + (bc.rb + 2) * p.units_per_row;            // (rb+2) row terms
     uint32_t& s_list_n = bsh.s_list_n;
 
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
@@ -534,8 +537,13 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
         const uint32_t fm = tt / bc.n_bands;
         const int r = (int)(tt - fm * bc.n_bands) * (int)bc.rb - 1 + (int)(i / p.units_per_row);
         if (r < 0 || r >= R) return 0.0f;
-        return -out.cm[(size_t)fm * p.units_per_module +
-                       ((uint32_t)r / p.unit_rows) * p.units_per_row + i % p.units_per_row];
+        // (stacked: each frame's values also hold the row and column terms)
+        const size_t fbase = (size_t)fm * p.units_per_module +
+                             (STACKED ? (size_t)(fm / p.n_modules) *
+                                            (cm_per_frame(p) - p.units_per_frame)
+                                      : 0);
+        return -out.cm[fbase + ((uint32_t)r / p.unit_rows) * p.units_per_row +
+                       i % p.units_per_row];
     };
     float cmv = 0.0f;
     if (first < n_tiles && tid < ncmt) cmv = tile_cm((uint32_t)first, tid);
@@ -556,6 +564,21 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
         // negated common mode of every (tile row, unit column)
         if (tid < ncmt) cmt[tid] = cmv;
         for (uint32_t i = tid + nthr; i < ncmt; i += nthr) cmt[i] = tile_cm((uint32_t)t, i);
+        // stacked: negated module-row terms of the tile's rows, and this
+        // thread's negated module-column terms
+        float ncc[VEC];
+        if (STACKED) {
+            const float* cmf = out.cm + (size_t)f * cm_per_frame(p) + p.units_per_frame;
+            for (uint32_t i = tid; i < bc.rb + 2; i += nthr) {
+                const int r = r0 - 1 + (int)i;
+                crt[i] = r >= 0 && r < R ? -cmf[(size_t)m * p.rows + r] : 0.0f;
+            }
+#pragma unroll
+            for (int i = 0; i < VEC; i++)
+                ncc[i] = active && col + i < C
+                             ? -cmf[(size_t)p.n_modules * p.rows + (size_t)m * p.cols + col + i]
+                             : 0.0f;
+        }
         if (tid == 0) s_list_n = 0;
         __syncthreads();
 
@@ -615,8 +638,16 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
                         const float2 d23 = __fadd2_rn(raw_pair(rr[j].y), make_float2(pp[j].z, pp[j].w));
                         const float2 n01 = make_float2(split > 0 ? ncma : ncmb, split > 1 ? ncma : ncmb);
                         const float2 n23 = make_float2(split > 2 ? ncma : ncmb, split > 3 ? ncma : ncmb);
-                        const float2 e01 = __fmul2_rn(__fadd2_rn(d01, n01), make_float2(gg[j].x, gg[j].y));
-                        const float2 e23 = __fmul2_rn(__fadd2_rn(d23, n23), make_float2(gg[j].z, gg[j].w));
+                        float2 c01 = __fadd2_rn(d01, n01), c23 = __fadd2_rn(d23, n23);
+                        if (STACKED) {
+                            const float ncr = crt[rl];
+                            c01 = __fadd2_rn(__fadd2_rn(c01, make_float2(ncr, ncr)),
+                                             make_float2(ncc[0], ncc[1]));
+                            c23 = __fadd2_rn(__fadd2_rn(c23, make_float2(ncr, ncr)),
+                                             make_float2(ncc[VEC > 2 ? 2 : 0], ncc[VEC > 3 ? 3 : 0]));
+                        }
+                        const float2 e01 = __fmul2_rn(c01, make_float2(gg[j].x, gg[j].y));
+                        const float2 e23 = __fmul2_rn(c23, make_float2(gg[j].z, gg[j].w));
                         e[0] = e01.x;
                         e[1] = e01.y;
                         e[2] = e23.x;
@@ -632,8 +663,9 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
                         atomicAdd(&hpix[(uint32_t)min(max(__float_as_int(u23.x), blo), bhi) - kMagicBits], 1u);
                         atomicAdd(&hpix[(uint32_t)min(max(__float_as_int(u23.y), blo), bhi) - kMagicBits], 1u);
                     } else {
-                        e[0] = __fmul_rn(__fadd_rn(__fadd_rn(__uint2float_rn(r1[j]), p1[j]), ncma),
-                                         g1[j]);
+                        float c0 = __fadd_rn(__fadd_rn(__uint2float_rn(r1[j]), p1[j]), ncma);
+                        if (STACKED) c0 = __fadd_rn(__fadd_rn(c0, crt[rl]), ncc[0]);
+                        e[0] = __fmul_rn(c0, g1[j]);
                         const float u = __fadd_rd(__fmaf_rn(e[0], p.hist_inv_w, p.hist_neg_lo_s),
                                                   kMagic);
                         atomicAdd(&hpix[(uint32_t)min(max(__float_as_int(u), blo), bhi) - kMagicBits], 1u);
@@ -783,15 +815,15 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
     }
 }
 
-template <int VEC>
+template <int VEC, bool STACKED>
 __global__ void __launch_bounds__(kBandThreads, 2)
     stencil_band_kernel(ChainParams p, const uint16_t* __restrict__ raw,
                         uint32_t frame_base, CallOut out, BandConfig bc,
                         unsigned long long n_tiles) {
     extern __shared__ __align__(16) uint32_t band_smem[];
     __shared__ BandShared bsh;
-    stencil_band_run<VEC>(p, raw, frame_base, out, bc, blockIdx.x, n_tiles, gridDim.x,
-                          band_smem, bsh);
+    stencil_band_run<VEC, STACKED>(p, raw, frame_base, out, bc, blockIdx.x, n_tiles, gridDim.x,
+                                   band_smem, bsh);
 }
 
 // ---------------------------------------------------------------------------
@@ -997,7 +1029,8 @@ BandConfig make_band_config(const ChainParams& p) {
 
 size_t band_smem_bytes(const ChainParams& p, uint32_t rb, uint32_t pitch) {
     return (size_t)(rb + 2) * pitch * 4 + (2 * (size_t)p.hist_bins + 4) * 4 +
-           (size_t)kSeedCap * 4 + (size_t)(rb + 2) * p.units_per_row * 4;
+           (size_t)kSeedCap * 4 + (size_t)(rb + 2) * p.units_per_row * 4 +
+           (size_t)(rb + 2) * 4;  // row terms of the stacked mean
 }
 
 cudaError_t launch_stencil_band(const ChainParams& p, const BandConfig& bc, const uint16_t* raw,
@@ -1008,13 +1041,12 @@ cudaError_t launch_stencil_band(const ChainParams& p, const BandConfig& bc, cons
     int dev = 0;
     cudaGetDevice(&dev);
     if (g_attr_dev_band != dev) {
-        cudaError_t e = cudaFuncSetAttribute(stencil_band_kernel<4>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(stencil_band_kernel<1>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
+        for (auto k : {stencil_band_kernel<4, false>, stencil_band_kernel<1, false>,
+                       stencil_band_kernel<4, true>, stencil_band_kernel<1, true>}) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 200 * 1024);
+            if (e != cudaSuccess) return e;
+        }
         g_attr_dev_band = dev;
     }
     const size_t smem = band_smem_bytes(p, bc.rb, bc.pitch);
@@ -1023,12 +1055,19 @@ cudaError_t launch_stencil_band(const ChainParams& p, const BandConfig& bc, cons
     per_sm = std::max(1, std::min(per_sm, 4));
     unsigned long long grid = (unsigned long long)device_sm_count() * per_sm;
     if (grid > n_tiles) grid = n_tiles;
-    if (bc.vec == 4)
-        stencil_band_kernel<4><<<(unsigned)grid, threads, smem, stream>>>(p, raw, frame_base, out,
-                                                                           bc, n_tiles);
+    const bool st = p.cm_mode == PD_CM_MEAN_STACKED;
+    if (bc.vec == 4 && st)
+        stencil_band_kernel<4, true><<<(unsigned)grid, threads, smem, stream>>>(
+            p, raw, frame_base, out, bc, n_tiles);
+    else if (bc.vec == 4)
+        stencil_band_kernel<4, false><<<(unsigned)grid, threads, smem, stream>>>(
+            p, raw, frame_base, out, bc, n_tiles);
+    else if (st)
+        stencil_band_kernel<1, true><<<(unsigned)grid, threads, smem, stream>>>(
+            p, raw, frame_base, out, bc, n_tiles);
     else
-        stencil_band_kernel<1><<<(unsigned)grid, threads, smem, stream>>>(p, raw, frame_base, out,
-                                                                           bc, n_tiles);
+        stencil_band_kernel<1, false><<<(unsigned)grid, threads, smem, stream>>>(
+            p, raw, frame_base, out, bc, n_tiles);
     return cudaGetLastError();
 }
 
