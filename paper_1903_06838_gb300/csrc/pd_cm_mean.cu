@@ -31,6 +31,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "pd_internal.cuh"
 
 namespace pd {
@@ -152,13 +154,12 @@ __global__ void __launch_bounds__(kMeanThreads)
 // stage 1, units of fewer than 8 rows: one warp per unit
 __global__ void __launch_bounds__(kMeanThreads)
     mean_units_warp_kernel(ChainParams p, const uint16_t* __restrict__ raw,
-                           float* __restrict__ cm, unsigned long long n_units) {
-    const unsigned long long item =
-        (unsigned long long)blockIdx.x * kMeanWarps + (threadIdx.x >> 5);
+                           float* __restrict__ cm, uint32_t n_units) {
+    const uint32_t item = blockIdx.x * kMeanWarps + (threadIdx.x >> 5);
     if (item >= n_units) return;  // whole warps leave together
     const int lane = threadIdx.x & 31;
-    const uint32_t f = (uint32_t)(item / p.units_per_frame);
-    const uint32_t u = (uint32_t)(item % p.units_per_frame);
+    const uint32_t f = item / p.units_per_frame;
+    const uint32_t u = item % p.units_per_frame;
     const UnitAt at = unit_at(p, f, u);
     const uint16_t* rw = raw + at.raw_off;
     const float* np_ = p.nped + at.map_off;
@@ -185,13 +186,12 @@ __global__ void __launch_bounds__(kMeanThreads)
 // stage 2: one warp per (frame, module, row), on d - cm_u
 __global__ void __launch_bounds__(kMeanThreads)
     mean_rows_kernel(ChainParams p, const uint16_t* __restrict__ raw, float* __restrict__ cm,
-                     unsigned long long n_rows) {
-    const unsigned long long item =
-        (unsigned long long)blockIdx.x * kMeanWarps + (threadIdx.x >> 5);
+                     uint32_t n_rows) {
+    const uint32_t item = blockIdx.x * kMeanWarps + (threadIdx.x >> 5);
     if (item >= n_rows) return;
     const int lane = threadIdx.x & 31;
-    const uint32_t r = (uint32_t)(item % p.rows);
-    const uint32_t fm = (uint32_t)(item / p.rows);
+    const uint32_t r = item % p.rows;
+    const uint32_t fm = item / p.rows;
     const uint32_t m = fm % p.n_modules, f = fm / p.n_modules;
     const size_t map = (size_t)m * p.module_px + (size_t)r * p.cols;
     const uint16_t* rw = raw + (size_t)f * p.frame_px + map;
@@ -225,13 +225,12 @@ __global__ void __launch_bounds__(kMeanThreads)
 // column, on (d - cm_u) - cm_r
 __global__ void __launch_bounds__(kMeanThreads)
     mean_cols_kernel(ChainParams p, const uint16_t* __restrict__ raw, float* __restrict__ cm,
-                     uint32_t col_blocks, unsigned long long n_items) {
-    const unsigned long long item =
-        (unsigned long long)blockIdx.x * kMeanWarps + (threadIdx.x >> 5);
+                     uint32_t col_blocks, uint32_t n_items) {
+    const uint32_t item = blockIdx.x * kMeanWarps + (threadIdx.x >> 5);
     if (item >= n_items) return;
     const int lane = threadIdx.x & 31;
-    const uint32_t cb = (uint32_t)(item % col_blocks);
-    const uint32_t fm = (uint32_t)(item / col_blocks);
+    const uint32_t cb = item % col_blocks;
+    const uint32_t fm = item / col_blocks;
     const uint32_t m = fm % p.n_modules, f = fm / p.n_modules;
     const uint32_t c = cb * 32 + lane;
     if (c >= p.cols) return;  // lanes stay independent from here on
@@ -271,18 +270,30 @@ unsigned warps_grid(unsigned long long items) {
 cudaError_t launch_cm_mean(const ChainParams& p, const uint16_t* raw, uint32_t n_frames,
                            float* cm, cudaStream_t stream) {
     if (n_frames == 0) return cudaSuccess;
-    const unsigned long long units = (unsigned long long)n_frames * p.units_per_frame;
-    if (p.unit_rows >= kMeanWarps)
-        mean_units_block_kernel<<<(unsigned)units, kMeanThreads, 0, stream>>>(p, raw, cm);
-    else
-        mean_units_warp_kernel<<<warps_grid(units), kMeanThreads, 0, stream>>>(p, raw, cm, units);
-    if (p.cm_mode != PD_CM_MEAN_STACKED) return cudaGetLastError();
-    const unsigned long long fm = (unsigned long long)n_frames * p.n_modules;
-    const unsigned long long rows = fm * p.rows;
-    mean_rows_kernel<<<warps_grid(rows), kMeanThreads, 0, stream>>>(p, raw, cm, rows);
+    // frames in groups whose work items (units, module rows, column blocks)
+    // stay below 2^31, so the kernels index them in 32 bits
+    const uint64_t per_frame = std::max<uint64_t>(
+        {(uint64_t)p.units_per_frame, (uint64_t)p.n_modules * p.rows,
+         (uint64_t)p.n_modules * ((p.cols + 31) / 32), 1});
+    const uint32_t group = (uint32_t)std::max<uint64_t>(1, ((1ull << 31) - 1) / per_frame);
     const uint32_t col_blocks = (p.cols + 31) / 32;
-    const unsigned long long cols = fm * col_blocks;
-    mean_cols_kernel<<<warps_grid(cols), kMeanThreads, 0, stream>>>(p, raw, cm, col_blocks, cols);
+    for (uint32_t f0 = 0; f0 < n_frames; f0 += group) {
+        const uint32_t nf = std::min(group, n_frames - f0);
+        const uint16_t* fr = raw + (size_t)f0 * p.frame_px;
+        float* cmf = cm + (size_t)f0 * cm_per_frame(p);
+        const uint32_t units = nf * p.units_per_frame;
+        if (p.unit_rows >= kMeanWarps)
+            mean_units_block_kernel<<<units, kMeanThreads, 0, stream>>>(p, fr, cmf);
+        else
+            mean_units_warp_kernel<<<warps_grid(units), kMeanThreads, 0, stream>>>(p, fr, cmf,
+                                                                                  units);
+        if (p.cm_mode != PD_CM_MEAN_STACKED) continue;
+        const uint32_t rows = nf * p.n_modules * p.rows;
+        mean_rows_kernel<<<warps_grid(rows), kMeanThreads, 0, stream>>>(p, fr, cmf, rows);
+        const uint32_t cols = nf * p.n_modules * col_blocks;
+        mean_cols_kernel<<<warps_grid(cols), kMeanThreads, 0, stream>>>(p, fr, cmf, col_blocks,
+                                                                        cols);
+    }
     return cudaGetLastError();
 }
 
