@@ -68,7 +68,7 @@ def filters(f0, f1, f1_dx, f1_dy, f1_nmin) -> Filters:
 class Geometry(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
                 ("n_modules", "rows", "cols", "unit_rows", "unit_cols",
-                 "cm_mode")]
+                 "cm_mode", "cm_after_gain")]
 
 
 class Thresholds(ctypes.Structure):
@@ -76,7 +76,7 @@ class Thresholds(ctypes.Structure):
                 ("seed_thr_kev", ctypes.c_float), ("photon_kev", ctypes.c_float),
                 ("cm_min_count", ctypes.c_uint32),
                 ("hist_lo_kev", ctypes.c_float), ("hist_bin_kev", ctypes.c_float),
-                ("hist_bins", ctypes.c_uint32)]
+                ("hist_bins", ctypes.c_uint32), ("cm_cut_kev", ctypes.c_float)]
 
 
 def build(force: bool = False) -> str:
@@ -125,15 +125,20 @@ def _load():
     return _lib
 
 
-def geometry(n_modules, rows, cols, unit_rows, unit_cols, cm_mode=CM_MEDIAN):
-    return Geometry(n_modules, rows, cols, unit_rows, unit_cols, cm_mode)
+def geometry(n_modules, rows, cols, unit_rows, unit_cols, cm_mode=CM_MEDIAN,
+             cm_after_gain=0):
+    """cm_after_gain = 1: the paper's order, gain before common mode."""
+    return Geometry(n_modules, rows, cols, unit_rows, unit_cols, cm_mode, cm_after_gain)
 
 
 def thresholds(cm_cut_adu, zero_thr_kev, seed_thr_kev, photon_kev,
                cm_min_count=0, hist_lo_kev=-4.0, hist_bin_kev=0.05,
-               hist_bins=1296):
+               hist_bins=1296, cm_cut_kev=None):
+    """cm_cut_kev: the common-mode cut in the paper's order (default: the
+    photon energy, as cm_cut_adu defaults to it in ADU)."""
     return Thresholds(cm_cut_adu, zero_thr_kev, seed_thr_kev, photon_kev,
-                      cm_min_count, hist_lo_kev, hist_bin_kev, hist_bins)
+                      cm_min_count, hist_lo_kev, hist_bin_kev, hist_bins,
+                      photon_kev if cm_cut_kev is None else cm_cut_kev)
 
 
 def lower_median(values) -> np.float32:

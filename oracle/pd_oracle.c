@@ -105,6 +105,14 @@
  * >= n_gains marks the pixel bad: e = 0.  Only the median and no common
  * mode are defined with several gains.
  *
+ * The paper's order (cm_after_gain = 1; Fig. a lists gain before common
+ * mode, and Fig. c takes the gain-corrected Frames1): step 4 comes first,
+ * e0 = d * inv_gain, the common-mode set is {e0 < cm_cut_kev} over the
+ * unit's unmasked pixels (inv_gain != 0), the estimators (median, mean,
+ * stacked stages) work on e0 in keV exactly as on d, and e = e0 - cm_u
+ * (stacked: ((e0 - cm_u) - cm_r) - cm_c); a masked pixel reads e = 0.  Not
+ * defined with several gains.
+ *
  * Inputs must be finite (pedestal finite; non-finite gains are masked).
  */
 #include <math.h>
@@ -113,7 +121,7 @@
 #include <string.h>
 
 typedef struct {
-    uint32_t n_modules, rows, cols, unit_rows, unit_cols, cm_mode;
+    uint32_t n_modules, rows, cols, unit_rows, unit_cols, cm_mode, cm_after_gain;
 } og_geometry;
 
 typedef struct {
@@ -121,6 +129,7 @@ typedef struct {
     uint32_t cm_min_count;
     float hist_lo_kev, hist_bin_kev;
     uint32_t hist_bins;
+    float cm_cut_kev;
 } og_thresholds;
 
 typedef struct {
@@ -197,7 +206,9 @@ float oracle_lower_median(float* set, uint32_t n) {
 static int mean_selects(float v, float cut) { return v < cut && v > -INFINITY; }
 
 /* The paper's common-mode estimator (Fig. c) over the n values of one
- * group, with the exactly defined sum of step 2 above. */
+ * group, with the exactly defined sum of step 2 above.  Values that must
+ * not enter the set (masked pixels in the paper's order) are passed as NaN,
+ * which no comparison selects. */
 float oracle_paper_mean(const float* v, uint32_t n, float cut) {
     uint32_t n0 = 0;
     float mx = 0.0f;
@@ -237,7 +248,8 @@ int oracle_check(const og_geometry* g, const og_thresholds* t) {
         !g->unit_cols)
         return 1;
     if (g->rows % g->unit_rows || g->cols % g->unit_cols) return 1;
-    if (g->cm_mode > OG_CM_MEAN_STACKED) return 1;
+    if (g->cm_mode > OG_CM_MEAN_STACKED || g->cm_after_gain > 1) return 1;
+    if (g->cm_after_gain && isnan(t->cm_cut_kev)) return 1;
     /* the exact sum of the mean stays within 64 bits below 2^24 values */
     if (g->cm_mode >= OG_CM_MEAN &&
         ((uint64_t)g->unit_rows * g->unit_cols >= (1u << 24) || g->rows >= (1u << 24) ||
@@ -312,6 +324,7 @@ int oracle_process_ext(const og_geometry* g, const og_thresholds* t, const og_fi
     if (fb && !filters_ok(fb)) return 1;
     if (n_gains > 4 || (n_gains && (gain_shift < 1 || gain_shift > 15))) return 1;
     if (n_gains && g->cm_mode != OG_CM_MEDIAN && g->cm_mode != OG_CM_NONE) return 1;
+    if (n_gains && g->cm_after_gain) return 1;
     return process_impl(g, t, fb, n_gains, gain_shift, ped, gain, raw, n_frames, frame_base,
                         hits, cap, n_hits, count_map, hist_pix, hist_hit, corrected, cm_out,
                         n_seeds);
@@ -371,6 +384,8 @@ static int process_impl(const og_geometry* g, const og_thresholds* t,
     const uint32_t stages = n_gains ? n_gains : 1;
     const uint32_t vmask = n_gains ? (1u << gain_shift) - 1u : 0xFFFFu;
     const uint32_t sshift = n_gains ? gain_shift : 16;
+    const int ag = g->cm_after_gain != 0;
+    const float cut = ag ? t->cm_cut_kev : t->cm_cut_adu;
     const uint32_t R = g->rows, C = g->cols;
     const size_t mpx = (size_t)R * C;
     const size_t fpx = mpx * g->n_modules;
@@ -418,12 +433,15 @@ static int process_impl(const og_geometry* g, const og_thresholds* t,
         for (uint32_t m = 0; m < g->n_modules; m++) {
             const size_t base = m * mpx;
             const uint16_t* rw = raw + (size_t)f * fpx + base;
-            /* 1. dark (per gain stage) */
+            /* 1. dark (per gain stage); in the paper's order 4. gain first:
+             * d then holds e0 = d * inv_gain, NaN for masked pixels so that
+             * no common-mode set takes them */
             for (size_t p = 0; p < mpx; p++) {
                 const uint32_t st = (uint32_t)rw[p] >> sshift;
                 const uint32_t v = (uint32_t)rw[p] & vmask;
                 stage[p] = (uint8_t)(st < stages ? st : 255);
                 d[p] = st < stages ? (float)v - ped[(size_t)st * fpx + base + p] : 0.0f;
+                if (ag) d[p] = inv_gain[base + p] != 0.0f ? d[p] * inv_gain[base + p] : NAN;
             }
             /* 2. common mode per unit */
             for (uint32_t ur = 0; ur < urows; ur++) {
@@ -436,7 +454,7 @@ static int process_impl(const og_geometry* g, const og_thresholds* t,
                                 const size_t p =
                                     (size_t)(ur * g->unit_rows + r) * C +
                                     uc * g->unit_cols + c;
-                                if (stage[p] == 0 && d[p] < t->cm_cut_adu) set[n++] = d[p];
+                                if (stage[p] == 0 && d[p] < cut) set[n++] = d[p];
                             }
                         }
                         if (n >= n_min && n > 0) cm = oracle_lower_median(set, n);
@@ -446,7 +464,7 @@ static int process_impl(const og_geometry* g, const og_thresholds* t,
                             for (uint32_t c = 0; c < g->unit_cols; c++)
                                 set[n++] = d[(size_t)(ur * g->unit_rows + r) * C +
                                              uc * g->unit_cols + c];
-                        cm = oracle_paper_mean(set, n, t->cm_cut_adu);
+                        cm = oracle_paper_mean(set, n, cut);
                     }
                     cmu[ur * ucols + uc] = cm;
                     if (cm_out)
@@ -459,7 +477,7 @@ static int process_impl(const og_geometry* g, const og_thresholds* t,
                     for (uint32_t c = 0; c < C; c++)
                         set[c] = d[(size_t)r * C + c] -
                                  cmu[(r / g->unit_rows) * ucols + c / g->unit_cols];
-                    cmr[r] = oracle_paper_mean(set, C, t->cm_cut_adu);
+                    cmr[r] = oracle_paper_mean(set, C, cut);
                     if (cm_out) cm_out[(size_t)f * cpf + upf + (size_t)m * R + r] = cmr[r];
                 }
                 /* stage 3: each module column, on (d - cm_u) - cm_r */
@@ -468,7 +486,7 @@ static int process_impl(const og_geometry* g, const og_thresholds* t,
                         set[r] = (d[(size_t)r * C + c] -
                                   cmu[(r / g->unit_rows) * ucols + c / g->unit_cols]) -
                                  cmr[r];
-                    cmc[c] = oracle_paper_mean(set, R, t->cm_cut_adu);
+                    cmc[c] = oracle_paper_mean(set, R, cut);
                     if (cm_out)
                         cm_out[(size_t)f * cpf + upf + (size_t)g->n_modules * R +
                                (size_t)m * C + c] = cmc[c];
@@ -481,7 +499,12 @@ static int process_impl(const og_geometry* g, const og_thresholds* t,
                     const float cm =
                         cmu[(r / g->unit_rows) * ucols + c / g->unit_cols];
                     float ev = 0.0f;
-                    if (stage[p] == 0) {
+                    if (ag) {
+                        if (inv_gain[base + p] != 0.0f) {
+                            ev = d[p] - cm;
+                            if (stacked) ev = (ev - cmr[r]) - cmc[c];
+                        }
+                    } else if (stage[p] == 0) {
                         float cc = d[p] - cm;
                         if (stacked) cc = (cc - cmr[r]) - cmc[c];
                         ev = cc * inv_gain[base + p];

@@ -141,12 +141,13 @@ class Detector:
         return dict(cm_cut_adu=self.photon_kev * self.adu_per_kev,
                     zero_thr_kev=thr, seed_thr_kev=thr,
                     photon_kev=self.photon_kev, cm_min_count=0,
-                    hist_lo_kev=-4.0, hist_bin_kev=0.05, hist_bins=1296)
+                    hist_lo_kev=-4.0, hist_bin_kev=0.05, hist_bins=1296,
+                    cm_cut_kev=self.photon_kev)
 
     def geometry(self) -> dict:
         return dict(n_modules=self.n_modules, rows=self.rows, cols=self.cols,
                     unit_rows=self.unit_rows, unit_cols=self.unit_cols,
-                    cm_mode=0)
+                    cm_mode=0, cm_after_gain=0)
 
 
 def maps(det: Detector):
