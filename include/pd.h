@@ -91,6 +91,13 @@ typedef struct {
     uint32_t rows, cols;           /* pixels of one module                  */
     uint32_t unit_rows, unit_cols; /* common-mode unit                      */
     uint32_t cm_mode;              /* PD_CM_MEDIAN, _NONE, _MEAN, _MEAN_STACKED */
+    /* 0 (default): common mode on d = raw - pedestal in ADU, then gain.
+     * 1: the paper's order (Fig. a lists gain first; Fig. c takes the
+     * gain-corrected Frames1): e0 = d * inv_gain, the common-mode set is
+     * {e0 < cm_cut_kev} over unmasked pixels, the estimators work on e0,
+     * e = e0 - cm (stacked: ((e0 - cm_u) - cm_r) - cm_c), masked pixels read
+     * 0.  Not with pd_create_multigain. */
+    uint32_t cm_after_gain;
 } pd_geometry;
 
 /* Thresholds and summary binning.  The paper exposes two noise thresholds
@@ -107,6 +114,7 @@ typedef struct {
     float hist_lo_kev;      /* histogram bin b covers lo + [b, b+1) * width  */
     float hist_bin_kev;     /*   (computed as floor((v - lo) * (1/width)))   */
     uint32_t hist_bins;     /* end bins are clamped                          */
+    float cm_cut_kev;       /* common-mode cut when cm_after_gain = 1 (keV)  */
 } pd_thresholds;
 
 #define PD_MAX_HIST_BINS 4096u

@@ -151,6 +151,7 @@ int check_geometry(const pd_geometry* g) {
     if (g->rows % g->unit_rows || g->cols % g->unit_cols)
         return fail(PD_EINVAL, "common-mode units must tile each module");
     if (g->cm_mode > PD_CM_MEAN_STACKED) return fail(PD_EINVAL, "unknown cm_mode");
+    if (g->cm_after_gain > 1) return fail(PD_EINVAL, "cm_after_gain is 0 or 1");
     if (g->cm_mode >= PD_CM_MEAN && (uint64_t)g->unit_rows * g->unit_cols >= (1u << 24))
         return fail(PD_EINVAL, "the mean common mode needs units of fewer than 2^24 pixels");
     const unsigned long long fpx =
@@ -236,7 +237,7 @@ cudaError_t launch_stencil_for(const pd_ctx* c, const uint16_t* fr, uint32_t nf,
 // The common-mode launch(es) of a context for nf frames into cm.
 cudaError_t launch_cm(const pd_ctx* c, const uint16_t* fr, uint32_t nf, float* cm,
                       cudaStream_t s) {
-    if (c->params.cm_mode == PD_CM_MEAN || c->params.cm_mode == PD_CM_MEAN_STACKED)
+    if (pd::cm_kind(c->params) == PD_CM_MEAN || pd::cm_kind(c->params) == PD_CM_MEAN_STACKED)
         return pd::launch_cm_mean(c->params, fr, nf, cm, s);
     if (c->multigain) return pd::launch_cm_select(c->params, fr, nf, cm, s, &c->mg);
     return c->use_cm_big    ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, cm, s)
@@ -417,6 +418,8 @@ int pd_create_multigain(const pd_geometry* geometry, uint32_t n_gains, uint32_t 
         return fail(PD_EINVAL, "multi-gain: 1..PD_MAX_GAINS stages, gain_shift in 1..15");
     if (geometry && geometry->cm_mode != PD_CM_MEDIAN && geometry->cm_mode != PD_CM_NONE)
         return fail(PD_EINVAL, "multi-gain: the median or no common mode");
+    if (geometry && geometry->cm_after_gain)
+        return fail(PD_EINVAL, "multi-gain: common mode before gain only");
     return create_impl(geometry, n_gains, gain_shift, pedestal_host, gain_host, thresholds, out);
 }
 
@@ -430,6 +433,8 @@ int create_impl(const pd_geometry* geometry, uint32_t n_gains, uint32_t gain_shi
     if (rc) return rc;
     rc = check_thresholds(thresholds);
     if (rc) return rc;
+    if (geometry->cm_after_gain && isnan(thresholds->cm_cut_kev))
+        return fail(PD_EINVAL, "cm_cut_kev is NaN");
     if (!pedestal_host || !gain_host) return fail(PD_EINVAL, "maps are NULL");
 
     pd_ctx* c = new (std::nothrow) pd_ctx();
@@ -450,10 +455,10 @@ int create_impl(const pd_geometry* geometry, uint32_t n_gains, uint32_t gain_shi
     p.module_px = g.rows * g.cols;
     p.frame_px = g.n_modules * p.module_px;
     p.units_per_frame = g.n_modules * p.units_per_module;
-    p.cm_mode = g.cm_mode;
+    p.cm_mode = g.cm_mode | (g.cm_after_gain ? pd::kCmAfterGain : 0u);
     p.cm_min_count = thresholds->cm_min_count ? thresholds->cm_min_count
                                               : ceil_sqrt_u32(p.unit_px);
-    p.cm_cut = thresholds->cm_cut_adu;
+    p.cm_cut = g.cm_after_gain ? thresholds->cm_cut_kev : thresholds->cm_cut_adu;
     p.zero_thr = thresholds->zero_thr_kev;
     p.seed_thr = thresholds->seed_thr_kev;
     p.photon_kev = thresholds->photon_kev;
@@ -462,13 +467,16 @@ int create_impl(const pd_geometry* geometry, uint32_t n_gains, uint32_t gain_shi
     p.hist_bins = thresholds->hist_bins;
 
     c->cm_cfg = pd::make_cm_big_config(p);
-    c->use_cm_big = g.cm_mode == PD_CM_MEDIAN && pd::cm_big_supported(p, c->cm_cfg);
-    c->use_cm_rows = g.cm_mode == PD_CM_MEDIAN && !c->use_cm_big && pd::cm_rows_supported(p);
+    // the bank and row median kernels, the band stencil and the one-kernel
+    // chain work on d in ADU: the paper's order uses the generic kernels
+    const bool ag = g.cm_after_gain != 0;
+    c->use_cm_big = !ag && g.cm_mode == PD_CM_MEDIAN && pd::cm_big_supported(p, c->cm_cfg);
+    c->use_cm_rows = !ag && g.cm_mode == PD_CM_MEDIAN && !c->use_cm_big && pd::cm_rows_supported(p);
     c->band_cfg = pd::make_band_config(p);
-    c->use_band = c->band_cfg.ok;
+    c->use_band = c->band_cfg.ok && !ag;
     c->fused_cfg = pd::make_fused_config(p);
     // the one-kernel chain computes the median (or nothing) itself
-    c->use_fused = c->fused_cfg.ok && (g.cm_mode == PD_CM_MEDIAN || g.cm_mode == PD_CM_NONE);
+    c->use_fused = c->fused_cfg.ok && !ag && (g.cm_mode == PD_CM_MEDIAN || g.cm_mode == PD_CM_NONE);
     {
         const size_t fbytes = (size_t)p.frame_px * 2;
         const size_t target = 96u << 20;  // raw bytes per chunk (measured best)
@@ -887,7 +895,7 @@ int batch_check_items(const pd_batch* b, const pd_batch_item* items, uint32_t n)
             return fail(PD_ENOTSUP, "batch: the mixed launch reads single-gain words");
         if (b->mixed && it.ctx->matched)
             return fail(PD_ENOTSUP, "batch: the mixed launch has no matched filters");
-        if (b->mixed && it.ctx->params.cm_mode >= PD_CM_MEAN)
+        if (b->mixed && pd::cm_kind(it.ctx->params) >= PD_CM_MEAN)
             return fail(PD_ENOTSUP, "batch: the mixed launch computes the median only");
     }
     return PD_OK;

@@ -43,7 +43,7 @@ __device__ void unit(const ChainParams& p, const uint16_t* __restrict__ raw,
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
     const uint32_t f = item / p.units_per_frame;
     const uint32_t u = item % p.units_per_frame;
-    if (p.cm_mode == PD_CM_NONE) {
+    if (cm_kind(p) == PD_CM_NONE) {
         if (tid == 0) cm_out[item] = 0.0f;
         return;
     }
@@ -54,6 +54,8 @@ __device__ void unit(const ChainParams& p, const uint16_t* __restrict__ raw,
     const size_t mod_base = (size_t)m * p.module_px;
     const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
     const float* pm = p.ped + mod_base;
+    const float* gm = p.inv_gain + mod_base;
+    const bool ag = cm_after_gain(p);
 
     auto key_at = [&](uint32_t i) -> uint32_t {
         const uint32_t off = (r0 + i / p.unit_cols) * p.cols + c0 + i % p.unit_cols;
@@ -62,8 +64,9 @@ __device__ void unit(const ChainParams& p, const uint16_t* __restrict__ raw,
             if ((w >> mg.shift) != 0) return kSentinel;
             w &= mg.vmask;
         }
-        const float d = __fsub_rn(__uint2float_rn(w), pm[off]);
-        return d < p.cm_cut ? order_key(d) : kSentinel;
+        const float v =
+            cm_input(ag, __fsub_rn(__uint2float_rn(w), pm[off]), ag ? gm[off] : 1.0f);
+        return v < p.cm_cut ? order_key(v) : kSentinel;
     };
 
     uint32_t cnt = 0;

@@ -90,6 +90,14 @@ __device__ __forceinline__ float dark(const uint16_t* raw, const float* nped, si
     return __fadd_rn(__uint2float_rn(raw[off]), nped[off]);
 }
 
+// A pixel's common-mode input: d, or in the paper's order d * inv_gain (NaN
+// for masked pixels, which no selection takes).
+__device__ __forceinline__ float cmv(bool ag, const uint16_t* raw, const float* nped,
+                                     const float* ig, size_t off) {
+    const float d = dark(raw, nped, off);
+    return ag ? cm_input(true, d, ig[off]) : d;
+}
+
 // Offsets of frame f, unit u in the pixel arrays and its rectangle origin.
 struct UnitAt {
     size_t raw_off, map_off;
@@ -114,6 +122,8 @@ __global__ void __launch_bounds__(kMeanThreads)
     const UnitAt at = unit_at(p, f, u);
     const uint16_t* rw = raw + at.raw_off;
     const float* np_ = p.nped + at.map_off;
+    const float* ig_ = p.inv_gain + at.map_off;
+    const bool ag = cm_after_gain(p);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         s_n0 = 0;
@@ -125,7 +135,7 @@ __global__ void __launch_bounds__(kMeanThreads)
     for (uint32_t r = warp; r < p.unit_rows; r += kMeanWarps)
         for (uint32_t c = lane; c < p.unit_cols; c += 32) {
             const size_t off = (size_t)r * p.cols + c;
-            a.first(dark(rw, np_, off), p.cm_cut);
+            a.first(cmv(ag, rw, np_, ig_, off), p.cm_cut);
         }
     const uint32_t wn = __reduce_add_sync(0xffffffffu, a.n0);
     const uint32_t wm = __reduce_max_sync(0xffffffffu, a.max_bits);
@@ -140,7 +150,7 @@ __global__ void __launch_bounds__(kMeanThreads)
         for (uint32_t r = warp; r < p.unit_rows; r += kMeanWarps)
             for (uint32_t c = lane; c < p.unit_cols; c += 32) {
                 const size_t off = (size_t)r * p.cols + c;
-                a.second(dark(rw, np_, off), p.cm_cut, scale);
+                a.second(cmv(ag, rw, np_, ig_, off), p.cm_cut, scale);
             }
         const long long wt = warp_sum64(a.total);
         if (lane == 0) atomicAdd(&s_total, (unsigned long long)wt);
@@ -163,10 +173,12 @@ __global__ void __launch_bounds__(kMeanThreads)
     const UnitAt at = unit_at(p, f, u);
     const uint16_t* rw = raw + at.raw_off;
     const float* np_ = p.nped + at.map_off;
+    const float* ig_ = p.inv_gain + at.map_off;
+    const bool ag = cm_after_gain(p);
     Acc a;
     for (uint32_t r = 0; r < p.unit_rows; r++)
         for (uint32_t c = lane; c < p.unit_cols; c += 32)
-            a.first(dark(rw, np_, (size_t)r * p.cols + c), p.cm_cut);
+            a.first(cmv(ag, rw, np_, ig_, (size_t)r * p.cols + c), p.cm_cut);
     const uint32_t n0 = __reduce_add_sync(0xffffffffu, a.n0);
     const uint32_t mb = __reduce_max_sync(0xffffffffu, a.max_bits);
     long long total = 0;
@@ -174,7 +186,7 @@ __global__ void __launch_bounds__(kMeanThreads)
         const float scale = pow2f(grid_k(mb));
         for (uint32_t r = 0; r < p.unit_rows; r++)
             for (uint32_t c = lane; c < p.unit_cols; c += 32)
-                a.second(dark(rw, np_, (size_t)r * p.cols + c), p.cm_cut, scale);
+                a.second(cmv(ag, rw, np_, ig_, (size_t)r * p.cols + c), p.cm_cut, scale);
         total = warp_sum64(a.total);
     }
     if (lane == 0)
@@ -196,13 +208,15 @@ __global__ void __launch_bounds__(kMeanThreads)
     const size_t map = (size_t)m * p.module_px + (size_t)r * p.cols;
     const uint16_t* rw = raw + (size_t)f * p.frame_px + map;
     const float* np_ = p.nped + map;
+    const float* ig_ = p.inv_gain + map;
+    const bool ag = cm_after_gain(p);
     const float* cmf = cm + (size_t)f * cm_per_frame(p);
     const float* cmu = cmf + (size_t)m * p.units_per_module + (r / p.unit_rows) * p.units_per_row;
     Acc a;
     for (uint32_t j = 0; j < p.units_per_row; j++) {
         const float cu = cmu[j];
         for (uint32_t c = j * p.unit_cols + lane; c < (j + 1) * p.unit_cols; c += 32)
-            a.first(__fsub_rn(dark(rw, np_, c), cu), p.cm_cut);
+            a.first(__fsub_rn(cmv(ag, rw, np_, ig_, c), cu), p.cm_cut);
     }
     const uint32_t n0 = __reduce_add_sync(0xffffffffu, a.n0);
     const uint32_t mb = __reduce_max_sync(0xffffffffu, a.max_bits);
@@ -212,7 +226,7 @@ __global__ void __launch_bounds__(kMeanThreads)
         for (uint32_t j = 0; j < p.units_per_row; j++) {
             const float cu = cmu[j];
             for (uint32_t c = j * p.unit_cols + lane; c < (j + 1) * p.unit_cols; c += 32)
-                a.second(__fsub_rn(dark(rw, np_, c), cu), p.cm_cut, scale);
+                a.second(__fsub_rn(cmv(ag, rw, np_, ig_, c), cu), p.cm_cut, scale);
         }
         total = warp_sum64(a.total);
     }
@@ -237,6 +251,8 @@ __global__ void __launch_bounds__(kMeanThreads)
     const size_t map = (size_t)m * p.module_px + c;
     const uint16_t* rw = raw + (size_t)f * p.frame_px + map;
     const float* np_ = p.nped + map;
+    const float* ig_ = p.inv_gain + map;
+    const bool ag = cm_after_gain(p);
     const float* cmf = cm + (size_t)f * cm_per_frame(p);
     const float* cmu = cmf + (size_t)m * p.units_per_module + c / p.unit_cols;
     const float* cmr = cmf + p.units_per_frame + (size_t)m * p.rows;
@@ -245,7 +261,7 @@ __global__ void __launch_bounds__(kMeanThreads)
     for (uint32_t b = 0; b < unit_blocks; b++) {
         const float cu = cmu[(size_t)b * p.units_per_row];
         for (uint32_t r = b * p.unit_rows; r < (b + 1) * p.unit_rows; r++)
-            a.first(__fsub_rn(__fsub_rn(dark(rw, np_, (size_t)r * p.cols), cu), cmr[r]),
+            a.first(__fsub_rn(__fsub_rn(cmv(ag, rw, np_, ig_, (size_t)r * p.cols), cu), cmr[r]),
                     p.cm_cut);
     }
     if (a.n0 > 0 && a.max_bits != 0) {
@@ -253,7 +269,7 @@ __global__ void __launch_bounds__(kMeanThreads)
         for (uint32_t b = 0; b < unit_blocks; b++) {
             const float cu = cmu[(size_t)b * p.units_per_row];
             for (uint32_t r = b * p.unit_rows; r < (b + 1) * p.unit_rows; r++)
-                a.second(__fsub_rn(__fsub_rn(dark(rw, np_, (size_t)r * p.cols), cu), cmr[r]),
+                a.second(__fsub_rn(__fsub_rn(cmv(ag, rw, np_, ig_, (size_t)r * p.cols), cu), cmr[r]),
                          p.cm_cut, scale);
         }
     }
@@ -287,7 +303,7 @@ cudaError_t launch_cm_mean(const ChainParams& p, const uint16_t* raw, uint32_t n
         else
             mean_units_warp_kernel<<<warps_grid(units), kMeanThreads, 0, stream>>>(p, fr, cmf,
                                                                                   units);
-        if (p.cm_mode != PD_CM_MEAN_STACKED) continue;
+        if (cm_kind(p) != PD_CM_MEAN_STACKED) continue;
         const uint32_t rows = nf * p.n_modules * p.rows;
         mean_rows_kernel<<<warps_grid(rows), kMeanThreads, 0, stream>>>(p, fr, cmf, rows);
         const uint32_t cols = nf * p.n_modules * col_blocks;

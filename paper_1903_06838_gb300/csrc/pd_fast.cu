@@ -73,7 +73,7 @@ __device__ void cm_big_unit(const ChainParams& p, const uint16_t* __restrict__ r
     const uint32_t f = item / p.units_per_frame;
     const uint32_t u = item % p.units_per_frame;
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
-    if (p.cm_mode == PD_CM_NONE) {
+    if (cm_kind(p) == PD_CM_NONE) {
         if (tid == 0) cm_out[item] = 0.0f;
         return;
     }
@@ -356,7 +356,7 @@ __device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ 
     const int lane = threadIdx.x & 31;
     const uint32_t f = (uint32_t)(item / p.units_per_frame);
     const uint32_t u = (uint32_t)(item % p.units_per_frame);
-    if (p.cm_mode == PD_CM_NONE) {
+    if (cm_kind(p) == PD_CM_NONE) {
         if (lane == 0) cm_out[item] = 0.0f;
         return;
     }
@@ -1055,7 +1055,7 @@ cudaError_t launch_stencil_band(const ChainParams& p, const BandConfig& bc, cons
     per_sm = std::max(1, std::min(per_sm, 4));
     unsigned long long grid = (unsigned long long)device_sm_count() * per_sm;
     if (grid > n_tiles) grid = n_tiles;
-    const bool st = p.cm_mode == PD_CM_MEAN_STACKED;
+    const bool st = cm_kind(p) == PD_CM_MEAN_STACKED;
     if (bc.vec == 4 && st)
         stencil_band_kernel<4, true><<<(unsigned)grid, threads, smem, stream>>>(
             p, raw, frame_base, out, bc, n_tiles);

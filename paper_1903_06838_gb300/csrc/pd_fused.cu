@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(MAXT, 2)
     const int R = (int)p.rows, C = (int)p.cols;
     const uint32_t c4 = 4 * tx;
     const uint32_t U = p.units_per_row;
-    const bool median = p.cm_mode == PD_CM_MEDIAN;
+    const bool median = cm_kind(p) == PD_CM_MEDIAN;
 
     uint32_t* codes32 = smem;                                    // region A
     float* ring = reinterpret_cast<float*>(smem);                // region A (pass C)
@@ -593,7 +593,7 @@ FusedConfig make_fused_config(const ChainParams& p) {
     FusedConfig fc{};
     fc.ok = false;
     if (p.cols % 4 != 0 || p.cols / 4 > 512 || p.cols >= 65536 || p.rows >= 65536) return fc;
-    const bool median = p.cm_mode == PD_CM_MEDIAN;
+    const bool median = cm_kind(p) == PD_CM_MEDIAN;
     if (median) {
         if (p.unit_rows != p.rows || p.units_per_row > kFusedMaxUnits) return fc;
         const double cut = p.cm_cut;

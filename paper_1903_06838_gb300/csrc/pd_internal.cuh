@@ -58,11 +58,43 @@ __device__ __forceinline__ float mg_energy(const MultiGain& mg, uint32_t frame_p
     return __fmul_rn(st == 0 ? __fsub_rn(d, cm) : d, mg.inv_gain[at]);
 }
 
+// ChainParams.cm_mode holds the estimator (PD_CM_*) in its low byte and the
+// paper's order (gain before common mode) as flag kCmAfterGain.
+constexpr uint32_t kCmAfterGain = 0x100u;
+__host__ __device__ inline uint32_t cm_kind(const ChainParams& p) { return p.cm_mode & 0xFFu; }
+__host__ __device__ inline bool cm_after_gain(const ChainParams& p) {
+    return (p.cm_mode & kCmAfterGain) != 0;
+}
+
+// The value a pixel brings to the common mode: d = raw - pedestal, or in
+// the paper's order d * inv_gain (NaN, which no cut selects, for masked
+// pixels).
+__device__ __forceinline__ float cm_input(bool after_gain, float d, float inv_gain) {
+    if (!after_gain) return d;
+    return inv_gain != 0.0f ? __fmul_rn(d, inv_gain) : __int_as_float(0x7fc00000);
+}
+
+// Energy of a single-gain pixel from d, its unit's common mode and (stacked)
+// the row and column terms, in the context's order.
+template <bool STACKED>
+__device__ __forceinline__ float energy(bool after_gain, float d, float inv_gain, float cm,
+                                        float cmr, float cmc) {
+    if (after_gain) {
+        if (inv_gain == 0.0f) return 0.0f;
+        float e = __fsub_rn(__fmul_rn(d, inv_gain), cm);
+        if (STACKED) e = __fsub_rn(__fsub_rn(e, cmr), cmc);
+        return e;
+    }
+    float c = __fsub_rn(d, cm);
+    if (STACKED) c = __fsub_rn(__fsub_rn(c, cmr), cmc);
+    return __fmul_rn(c, inv_gain);
+}
+
 // Common-mode values per frame: one per unit, then for the stacked mean one
 // per module row and one per module column.
 __host__ __device__ inline uint32_t cm_per_frame(const ChainParams& p) {
     return p.units_per_frame +
-           (p.cm_mode == PD_CM_MEAN_STACKED ? p.n_modules * (p.rows + p.cols) : 0u);
+           (cm_kind(p) == PD_CM_MEAN_STACKED ? p.n_modules * (p.rows + p.cols) : 0u);
 }
 
 // A matched-filter bank compiled to lists of nonzero taps (pd_matched.cu).

@@ -132,9 +132,8 @@ __global__ void __launch_bounds__(kThreads)
                     e = mg_energy(mg, p.frame_px, fr[off], mod_base + off, cm);
                 } else {
                     const float d = __fsub_rn(__uint2float_rn(fr[off]), p.ped[mod_base + off]);
-                    float cc = __fsub_rn(d, cm);
-                    if (STACKED) cc = __fsub_rn(__fsub_rn(cc, cmr[r]), cmc[c]);
-                    e = __fmul_rn(cc, p.inv_gain[mod_base + off]);
+                    e = energy<STACKED>(cm_after_gain(p), d, p.inv_gain[mod_base + off], cm,
+                                        STACKED ? cmr[r] : 0.0f, STACKED ? cmc[c] : 0.0f);
                 }
                 s = e > p.zero_thr ? e : 0.0f;
                 if (hr >= 1 && hr <= kTY && hc >= 2 && hc < kTX + 2) {
@@ -359,7 +358,7 @@ cudaError_t launch_matched(const ChainParams& p, const MatchedBank* bank_dev,
     if (mg)
         matched_kernel<false, true><<<(unsigned)grid, kThreads, smem, stream>>>(
             p, bank_dev, raw, frame_base, out, tiles_y, tiles_x, n_tiles, m);
-    else if (p.cm_mode == PD_CM_MEAN_STACKED)
+    else if (cm_kind(p) == PD_CM_MEAN_STACKED)
         matched_kernel<true, false><<<(unsigned)grid, kThreads, smem, stream>>>(
             p, bank_dev, raw, frame_base, out, tiles_y, tiles_x, n_tiles, m);
     else

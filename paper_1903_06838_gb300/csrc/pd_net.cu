@@ -295,12 +295,13 @@ __global__ void gather_kernel(pd::ChainParams p, const uint16_t* __restrict__ ra
         } else {
             const float d =
                 __fsub_rn(__uint2float_rn(raw[(size_t)f * p.frame_px + g]), p.ped[g]);
-            float cc = __fsub_rn(d, cmf[unit]);
-            if (p.cm_mode == PD_CM_MEAN_STACKED)
-                cc = __fsub_rn(__fsub_rn(cc, cmf[p.units_per_frame + (size_t)m * p.rows + r]),
-                               cmf[p.units_per_frame + (size_t)p.n_modules * p.rows +
-                                   (size_t)m * p.cols + c]);
-            e = __fmul_rn(cc, p.inv_gain[g]);
+            if (cm_kind(p) == PD_CM_MEAN_STACKED)
+                e = pd::energy<true>(cm_after_gain(p), d, p.inv_gain[g], cmf[unit],
+                                     cmf[p.units_per_frame + (size_t)m * p.rows + r],
+                                     cmf[p.units_per_frame + (size_t)p.n_modules * p.rows +
+                                         (size_t)m * p.cols + c]);
+            else
+                e = pd::energy<false>(cm_after_gain(p), d, p.inv_gain[g], cmf[unit], 0.0f, 0.0f);
         }
         v = __fdiv_rn(e, p.photon_kev);
     }

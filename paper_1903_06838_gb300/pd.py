@@ -61,7 +61,7 @@ class PdFilterBank(ctypes.Structure):
 class PdGeometry(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
                 ("n_modules", "rows", "cols", "unit_rows", "unit_cols",
-                 "cm_mode")]
+                 "cm_mode", "cm_after_gain")]
 
 
 class PdThresholds(ctypes.Structure):
@@ -69,7 +69,7 @@ class PdThresholds(ctypes.Structure):
                 ("seed_thr_kev", ctypes.c_float), ("photon_kev", ctypes.c_float),
                 ("cm_min_count", ctypes.c_uint32),
                 ("hist_lo_kev", ctypes.c_float), ("hist_bin_kev", ctypes.c_float),
-                ("hist_bins", ctypes.c_uint32)]
+                ("hist_bins", ctypes.c_uint32), ("cm_cut_kev", ctypes.c_float)]
 
 
 class PdOutputs(ctypes.Structure):
@@ -310,15 +310,19 @@ class Context:
 
 
 def make_geometry(n_modules, rows, cols, unit_rows, unit_cols,
-                  cm_mode=PD_CM_MEDIAN) -> PdGeometry:
-    return PdGeometry(n_modules, rows, cols, unit_rows, unit_cols, cm_mode)
+                  cm_mode=PD_CM_MEDIAN, cm_after_gain=0) -> PdGeometry:
+    """cm_after_gain = 1: the paper's order, gain before common mode."""
+    return PdGeometry(n_modules, rows, cols, unit_rows, unit_cols, cm_mode, cm_after_gain)
 
 
 def make_thresholds(cm_cut_adu, zero_thr_kev, seed_thr_kev, photon_kev,
                     cm_min_count=0, hist_lo_kev=-4.0, hist_bin_kev=0.05,
-                    hist_bins=1296) -> PdThresholds:
+                    hist_bins=1296, cm_cut_kev=None) -> PdThresholds:
+    """cm_cut_kev: the common-mode cut in the paper's order (default: the
+    photon energy)."""
     return PdThresholds(cm_cut_adu, zero_thr_kev, seed_thr_kev, photon_kev,
-                        cm_min_count, hist_lo_kev, hist_bin_kev, hist_bins)
+                        cm_min_count, hist_lo_kev, hist_bin_kev, hist_bins,
+                        photon_kev if cm_cut_kev is None else cm_cut_kev)
 
 
 def pd_create(geometry, pedestal, gain, thresholds, n_gains: int = 0,
