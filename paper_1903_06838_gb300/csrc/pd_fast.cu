@@ -374,23 +374,57 @@ __device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ 
     if (lane == 0) S.n_few = 0;
     __syncwarp();
 
-    // d of this lane's pixels (pixel i of the unit = lane + 32 * j)
+    // d of this lane's pixels: pixel i of the unit = lane + 32 * j, or for
+    // aligned single-row units 4 consecutive pixels per load (chunk
+    // lane + 32 * (j / 4), pixel 4 * chunk + j % 4)
     float d[kRowPerLane];
     uint32_t code[kRowPerLane];
+    const bool vec4 = p.unit_rows == 1 && npx % 4 == 0 && c0 % 4 == 0 && p.cols % 4 == 0;
+    if (vec4) {
+        const uint16_t* rrow = fr + r0 * p.cols + c0;
+        const float* prow = npm + r0 * p.cols + c0;
 #pragma unroll
-    for (int j = 0; j < kRowPerLane; j++) {
-        const uint32_t i = lane + 32 * j;
-        d[j] = 0.0f;
-        code[j] = 256;
-        if (i < npx) {
-            const uint32_t off = p.unit_rows == 1
-                                     ? r0 * p.cols + c0 + i
-                                     : (r0 + i / p.unit_cols) * p.cols + c0 + i % p.unit_cols;
-            d[j] = __fadd_rn(__uint2float_rn(fr[off]), npm[off]);
-            int b = __float_as_int(__fmaf_rd(d[j], 1.0f, magic_1));
-            b = min(max(b, (int)kMagicBits), (int)(kMagicBits + 256));
-            code[j] = (uint32_t)b - kMagicBits;
-            atomicAdd(&S.hist[code[j]], 1u);
+        for (int jc = 0; jc < kRowPerLane / 4; jc++) {
+            const uint32_t ch = lane + 32 * jc;
+            uint2 rw = make_uint2(0, 0);
+            float4 pp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (4 * ch < npx) {
+                rw = *reinterpret_cast<const uint2*>(rrow + 4 * ch);
+                pp = *reinterpret_cast<const float4*>(prow + 4 * ch);
+            }
+            const float2 d01 = __fadd2_rn(raw_pair(rw.x), make_float2(pp.x, pp.y));
+            const float2 d23 = __fadd2_rn(raw_pair(rw.y), make_float2(pp.z, pp.w));
+            const float dv[4] = {d01.x, d01.y, d23.x, d23.y};
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int j = 4 * jc + q;
+                d[j] = 0.0f;
+                code[j] = 256;
+                if (4 * ch < npx) {
+                    d[j] = dv[q];
+                    int b = __float_as_int(__fmaf_rd(d[j], 1.0f, magic_1));
+                    b = min(max(b, (int)kMagicBits), (int)(kMagicBits + 256));
+                    code[j] = (uint32_t)b - kMagicBits;
+                    atomicAdd(&S.hist[code[j]], 1u);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kRowPerLane; j++) {
+            const uint32_t i = lane + 32 * j;
+            d[j] = 0.0f;
+            code[j] = 256;
+            if (i < npx) {
+                const uint32_t off = p.unit_rows == 1
+                                         ? r0 * p.cols + c0 + i
+                                         : (r0 + i / p.unit_cols) * p.cols + c0 + i % p.unit_cols;
+                d[j] = __fadd_rn(__uint2float_rn(fr[off]), npm[off]);
+                int b = __float_as_int(__fmaf_rd(d[j], 1.0f, magic_1));
+                b = min(max(b, (int)kMagicBits), (int)(kMagicBits + 256));
+                code[j] = (uint32_t)b - kMagicBits;
+                atomicAdd(&S.hist[code[j]], 1u);
+            }
         }
     }
     __syncwarp();
