@@ -1021,9 +1021,17 @@ int batch_enqueue(pd_batch* b, int slot, const pd_batch_item* items, uint32_t n,
         if ((e = cudaEventRecord(b->copied, s))) return fail_cuda(e, "batch event");
         b->copy_pending = true;
     }
+    // kernels specialised to the kinds this batch holds
+    bool all_kinds = false;
+    int vec = -1;
+    for (uint32_t i = 0; i < n; i++) {
+        if (base[i].cm_kind != 0 && base[i].cm_kind != 4) all_kinds = true;
+        const int v = (int)base[i].band_vec;
+        vec = vec < 0 ? v : (vec == v ? v : 0);
+    }
     for (const Launch& L : launches) {
         e = pd::launch_batch(b->d_table[slot] + L.first, L.count, L.cm_tasks, cm_smem, band_smem,
-                             s);
+                             s, all_kinds, vec < 0 ? 0 : vec);
         if (e != cudaSuccess) return fail_cuda(e, "batch kernel launch");
     }
     return PD_OK;

@@ -876,6 +876,10 @@ __device__ __forceinline__ uint32_t find_item(const BatchItem* items, uint32_t n
     return lo;
 }
 
+// ALL_KINDS false: every item's common mode is a bank with pairs of
+// pixels (kind 0) or rows (kind 4), the usual mix; the kernel then carries
+// only those two paths (fewer registers).
+template <bool ALL_KINDS>
 __global__ void __launch_bounds__(512, 2)
     batch_cm_kernel(const BatchItem* __restrict__ items, uint32_t n_items,
                     unsigned long long n_tasks) {
@@ -894,27 +898,44 @@ __global__ void __launch_bounds__(512, 2)
             __syncthreads();
             continue;
         }
-        switch (it.cm_kind) {
-            case 0: cm_big_unit<2>(it.p, it.raw, it.out.cm, it.cm_cfg, local, smem, big); break;
-            case 1: cm_big_unit<1>(it.p, it.raw, it.out.cm, it.cm_cfg, local, smem, big); break;
-            case 2: generic_cm::unit<true>(it.p, it.raw, it.out.cm, local, smem, gen); break;
-            default: generic_cm::unit<false>(it.p, it.raw, it.out.cm, local, smem, gen); break;
+        if (!ALL_KINDS) {
+            cm_big_unit<2>(it.p, it.raw, it.out.cm, it.cm_cfg, local, smem, big);
+        } else {
+            switch (it.cm_kind) {
+                case 0: cm_big_unit<2>(it.p, it.raw, it.out.cm, it.cm_cfg, local, smem, big); break;
+                case 1: cm_big_unit<1>(it.p, it.raw, it.out.cm, it.cm_cfg, local, smem, big); break;
+                case 2: generic_cm::unit<true>(it.p, it.raw, it.out.cm, local, smem, gen); break;
+                default: generic_cm::unit<false>(it.p, it.raw, it.out.cm, local, smem, gen); break;
+            }
         }
         __syncthreads();  // shared memory is reused by the next task
     }
 }
 
+// VEC 4 or 1: every item uses that width; 0: each item its own.
+template <int VEC>
 __global__ void __launch_bounds__(kBandThreads, 2)
     batch_stencil_kernel(const BatchItem* __restrict__ items, uint32_t n_items) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ BandShared bsh;
+    // the current item in shared memory: its parameters are read from there
+    // rather than held in registers
+    __shared__ __align__(16) BatchItem s_item;
     const unsigned long long G = gridDim.x, b = blockIdx.x;
     for (uint32_t i = 0; i < n_items; i++) {
-        const BatchItem& it = items[i];
+        __syncthreads();  // the previous item is no longer read
+        {
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(items + i);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&s_item);
+            for (uint32_t k = threadIdx.x; k < sizeof(BatchItem) / 4; k += blockDim.x)
+                dst[k] = src[k];
+        }
+        __syncthreads();
+        const BatchItem& it = s_item;
         const unsigned long long n = it.st_tiles;
         const unsigned long long first = (b + G - it.st_first % G) % G;
         if (first >= n) continue;
-        if (it.band_vec == 4)
+        if (VEC == 4 || (VEC == 0 && it.band_vec == 4))
             stencil_band_run<4>(it.p, it.raw, it.frame_base, it.out, it.band_cfg, first, n, G,
                                 smem, bsh);
         else
@@ -928,18 +949,21 @@ __global__ void __launch_bounds__(kBandThreads, 2)
 
 cudaError_t launch_batch(const BatchItem* items_dev, uint32_t n_items,
                          unsigned long long cm_tasks, size_t cm_smem, size_t band_smem,
-                         cudaStream_t stream) {
+                         cudaStream_t stream, bool all_kinds, int vec) {
     int dev = 0;
     cudaGetDevice(&dev);
     static int attr_dev = -1;
     if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(batch_cm_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kCmBigMaxSmem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(batch_stencil_kernel,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
+        for (auto k : {batch_cm_kernel<true>, batch_cm_kernel<false>}) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kCmBigMaxSmem);
+            if (e != cudaSuccess) return e;
+        }
+        for (auto k : {batch_stencil_kernel<0>, batch_stencil_kernel<4>, batch_stencil_kernel<1>}) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 200 * 1024);
+            if (e != cudaSuccess) return e;
+        }
         attr_dev = dev;
     }
     if (!items_dev) return cudaSuccess;  // attribute set-up only
@@ -947,14 +971,24 @@ cudaError_t launch_batch(const BatchItem* items_dev, uint32_t n_items,
     if (cm_tasks) {
         unsigned long long grid = 2ull * sms;
         if (grid > cm_tasks) grid = cm_tasks;
-        batch_cm_kernel<<<(unsigned)grid, 512, cm_smem, stream>>>(items_dev, n_items, cm_tasks);
+        if (all_kinds)
+            batch_cm_kernel<true><<<(unsigned)grid, 512, cm_smem, stream>>>(items_dev, n_items,
+                                                                             cm_tasks);
+        else
+            batch_cm_kernel<false><<<(unsigned)grid, 512, cm_smem, stream>>>(items_dev, n_items,
+                                                                              cm_tasks);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     int per_sm = (int)((200 * 1024) / std::max<size_t>(band_smem, 1));
     per_sm = std::max(1, std::min(per_sm, 2));
-    batch_stencil_kernel<<<(unsigned)(sms * per_sm), kBandThreads, band_smem, stream>>>(items_dev,
-                                                                                       n_items);
+    const unsigned grid_st = sms * (unsigned)per_sm;
+    if (vec == 4)
+        batch_stencil_kernel<4><<<grid_st, kBandThreads, band_smem, stream>>>(items_dev, n_items);
+    else if (vec == 1)
+        batch_stencil_kernel<1><<<grid_st, kBandThreads, band_smem, stream>>>(items_dev, n_items);
+    else
+        batch_stencil_kernel<0><<<grid_st, kBandThreads, band_smem, stream>>>(items_dev, n_items);
     return cudaGetLastError();
 }
 

@@ -54,10 +54,12 @@ struct BatchItem {
 };
 
 // Common mode of every item in one launch, then every stencil tile in one
-// launch (both persistent), on `stream`.
+// launch (both persistent), on `stream`.  all_kinds false: every item's
+// common-mode kind is 0 or 4; vec: the band width all items share (4 or 1),
+// or 0.
 cudaError_t launch_batch(const BatchItem* items_dev, uint32_t n_items,
                          unsigned long long cm_tasks, size_t cm_smem, size_t band_smem,
-                         cudaStream_t stream);
+                         cudaStream_t stream, bool all_kinds = true, int vec = 0);
 
 CmBigConfig make_cm_big_config(const ChainParams& p);
 bool cm_big_supported(const ChainParams& p, const CmBigConfig& cfg);
