@@ -1076,7 +1076,10 @@ cudaError_t launch_cm_big(const ChainParams& p, const CmBigConfig& cfg, const ui
 
 BandConfig make_band_config(const ChainParams& p) {
     BandConfig bc{};
-    const bool vec4 = p.cols % 4 == 0 && p.module_px % 4 == 0 && p.frame_px % 4 == 0;
+    // a four-pixel chunk starts at a multiple of 4 and takes the common mode
+    // of at most two units, which needs units at least two columns wide
+    const bool vec4 = p.cols % 4 == 0 && p.module_px % 4 == 0 && p.frame_px % 4 == 0 &&
+                      p.unit_cols >= 2;
     bc.vec = vec4 ? 4 : 1;
     bc.tx = p.cols / bc.vec;
     bc.ok = bc.tx <= kBandThreads;

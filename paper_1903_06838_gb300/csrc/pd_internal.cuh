@@ -98,9 +98,12 @@ __host__ __device__ inline uint32_t cm_per_frame(const ChainParams& p) {
 }
 
 // A matched-filter bank compiled to lists of nonzero taps (pd_matched.cu).
-// `at` is the tap's offset in the kernel's shared tile: i * 68 + j.
+// (i, j) is the tap's place in the 4 x 5 filter and `at` its offset in a
+// kernel's shared tile, i * pitch + j (set for the tile kernel's pitch of 68;
+// the band kernel rewrites it in its shared copy of the bank).
 struct MatchedTap {
-    uint16_t at, pad;
+    uint8_t i, j;
+    uint16_t at;
     float v;
 };
 struct MatchedBank {

@@ -31,12 +31,22 @@
 // other features, and the droplet and momenta of valid features, run over
 // the tap lists.  Hits are compacted with a warp ballot and one atomic per
 // warp.
+//
+// matched_band_kernel: the same per pixel on full-width bands of module rows
+// (single gain, raw - pedestal before the common mode), with the band
+// stencil's four-pixel vector loads and packed correction.  Each thread
+// stores the signal bits of its four pixels as one nibble; a pixel's window
+// mask is read from the nibbles of four rows, and each thread tests a run of
+// consecutive rows with the masks of the rows above and below in registers.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <new>
 
+#include "pd_dev.cuh"
+#include "pd_fast.cuh"
 #include "pd_internal.cuh"
 
 namespace pd {
@@ -52,6 +62,106 @@ __device__ __forceinline__ uint32_t hist_bin(float v, float neg_lo_s, float inv_
     if (!(t >= 0.0f)) return 0;
     if (t >= (float)bins) return bins - 1;
     return (uint32_t)t;
+}
+
+// The bank at one pixel: w points at its window's tap (0, 0) in a shared
+// tile (tap (i, j) at w[i * pitch + j], the pitch folded into the taps'
+// offsets), win is its 20-bit signal mask.  Returns whether some feature is
+// valid; E, dx, dy and npix (the signal pixels under the first valid
+// feature's F1) as described above.
+__device__ __forceinline__ bool evaluate_bank(const MatchedBank& sb, const float* w,
+                                              uint32_t win, float& E, float& dx, float& dy,
+                                              uint32_t& npix) {
+    E = dx = dy = 0.0f;
+    npix = 0;
+    bool any = false;
+    for (uint32_t ft = 0; ft < sb.n_features; ft++) {
+        bool clear;
+        if (sb.f0_pos[ft]) {
+            clear = (win & sb.m0[ft]) == 0;
+        } else {
+            float over = 0.0f;
+            for (uint32_t k = sb.off0[ft]; k < sb.off0[ft + 1]; k++)
+                if (w[sb.t0[k].at] > 0.0f) over = __fadd_rn(over, sb.t0[k].v);
+            clear = over == 0.0f;
+        }
+        if (!clear) continue;
+        float size;
+        if (sb.f1_unit[ft]) {
+            size = (float)__popc(win & sb.m1[ft]);
+        } else {
+            size = 0.0f;
+            for (uint32_t k = sb.off1[ft]; k < sb.off1[ft + 1]; k++)
+                if (w[sb.t1[k].at] > 0.0f) size = __fadd_rn(size, sb.t1[k].v);
+        }
+        if (!(size >= sb.nmin[ft])) continue;
+        float drop = 0.0f, mx = 0.0f, my = 0.0f;
+        uint32_t under = 0;
+        for (uint32_t k = sb.off1[ft]; k < sb.off1[ft + 1]; k++) {
+            const float sv = w[sb.t1[k].at];
+            drop = __fadd_rn(drop, __fmul_rn(sv, sb.t1[k].v));
+            under += sv > 0.0f;
+        }
+        for (uint32_t k = sb.offx[ft]; k < sb.offx[ft + 1]; k++)
+            mx = __fadd_rn(mx, __fmul_rn(w[sb.tx[k].at], sb.tx[k].v));
+        for (uint32_t k = sb.offy[ft]; k < sb.offy[ft + 1]; k++)
+            my = __fadd_rn(my, __fmul_rn(w[sb.ty[k].at], sb.ty[k].v));
+        if (!any) npix = under;
+        any = true;
+        E = __fadd_rn(E, drop);
+        if (drop != 0.0f) {
+            dx = __fadd_rn(dx, __fdiv_rn(mx, drop));
+            dy = __fadd_rn(dy, __fdiv_rn(my, drop));
+        }
+    }
+    return any;
+}
+
+// Count, flags and record of a pixel whose bank gave energy E (E != 0);
+// returns whether it is a hit (count >= 1) and adds E to the hit histogram.
+__device__ __forceinline__ bool make_hit(const ChainParams& p, uint32_t* hhit, float E, float dx,
+                                         float dy, uint32_t npix, int r, int c, uint32_t frame,
+                                         size_t mod_base, pd_hit& h, uint32_t& n, uint32_t& pix) {
+    atomicAdd(&hhit[hist_bin(E, p.hist_neg_lo_s, p.hist_inv_w, p.hist_bins)], 1u);
+    const float qr = rintf(__fdiv_rn(E, p.photon_kev));
+    uint16_t flags = 0;
+    if (!(qr >= 0.0f)) {
+        n = 0;
+    } else if (qr > 255.0f) {
+        n = 255;
+        flags |= PD_HIT_SATURATED;
+    } else {
+        n = (uint32_t)qr;
+    }
+    if (n < 1) return false;
+    const int R = (int)p.rows, C = (int)p.cols;
+    if (r == 0 || c == 0 || r == R - 1 || c == C - 1) flags |= PD_HIT_EDGE;
+    pix = (uint32_t)mod_base + (uint32_t)r * p.cols + (uint32_t)c;
+    h.frame = frame;
+    h.pixel = pix;
+    h.energy_kev = E;
+    h.dx = dx;
+    h.dy = dy;
+    h.count = (uint8_t)n;
+    h.npix = (uint8_t)(npix > 255 ? 255 : npix);
+    h.flags = flags;
+    return true;
+}
+
+// Warp-aggregated emission: one atomic on the hit counter per warp.
+__device__ __forceinline__ void emit_hits(const ChainParams& p, const CallOut& out, bool emit,
+                                          const pd_hit& h, uint32_t n, uint32_t pix, int lane) {
+    const uint32_t mask = __ballot_sync(0xffffffffu, emit);
+    if (mask) {
+        uint32_t slot = 0;
+        if (lane == __ffs(mask) - 1) slot = atomicAdd(out.n_hits, __popc(mask));
+        slot = __shfl_sync(0xffffffffu, slot, __ffs(mask) - 1);
+        if (emit) {
+            slot += __popc(mask & ((1u << lane) - 1u));
+            atomicAdd(&p.count_map[pix], n);
+            if (slot < out.hit_capacity) out.hits[slot] = h;
+        }
+    }
 }
 
 template <bool STACKED, bool MG>
@@ -77,7 +187,6 @@ __global__ void __launch_bounds__(kThreads)
 
     const int R = (int)p.rows, C = (int)p.cols;
     const int lane = threadIdx.x & 31;
-    const uint32_t nf = sb.n_features;
     __shared__ uint32_t s_at[4];  // the tile's column, row, module and frame
     __shared__ uint32_t s_list[kTY * kTX];  // pixel j | window mask << 10
     __shared__ uint32_t s_nc;
@@ -188,91 +297,310 @@ __global__ void __launch_bounds__(kThreads)
             const int r = r0 + ir, c = c0 + ic;
             if (k < n_cand) {
                 // window tap (i, j) is tile[ir + i][ic + j]
-                const float* w = &tile[ir][ic];
-                float E = 0.0f, dx = 0.0f, dy = 0.0f;
-                uint32_t npix = 0;
-                bool any = false;
-                for (uint32_t ft = 0; ft < nf; ft++) {
-                    bool clear;
-                    if (sb.f0_pos[ft]) {
-                        clear = (win & sb.m0[ft]) == 0;
-                    } else {
-                        float over = 0.0f;
-                        for (uint32_t k = sb.off0[ft]; k < sb.off0[ft + 1]; k++)
-                            if (w[sb.t0[k].at] > 0.0f) over = __fadd_rn(over, sb.t0[k].v);
-                        clear = over == 0.0f;
-                    }
-                    if (!clear) continue;
-                    float size;
-                    if (sb.f1_unit[ft]) {
-                        size = (float)__popc(win & sb.m1[ft]);
-                    } else {
-                        size = 0.0f;
-                        for (uint32_t k = sb.off1[ft]; k < sb.off1[ft + 1]; k++)
-                            if (w[sb.t1[k].at] > 0.0f) size = __fadd_rn(size, sb.t1[k].v);
-                    }
-                    if (!(size >= sb.nmin[ft])) continue;
-                    float drop = 0.0f, mx = 0.0f, my = 0.0f;
-                    uint32_t under = 0;
-                    for (uint32_t k = sb.off1[ft]; k < sb.off1[ft + 1]; k++) {
-                        const float sv = w[sb.t1[k].at];
-                        drop = __fadd_rn(drop, __fmul_rn(sv, sb.t1[k].v));
-                        under += sv > 0.0f;
-                    }
-                    for (uint32_t k = sb.offx[ft]; k < sb.offx[ft + 1]; k++)
-                        mx = __fadd_rn(mx, __fmul_rn(w[sb.tx[k].at], sb.tx[k].v));
-                    for (uint32_t k = sb.offy[ft]; k < sb.offy[ft + 1]; k++)
-                        my = __fadd_rn(my, __fmul_rn(w[sb.ty[k].at], sb.ty[k].v));
-                    if (!any) npix = under;
-                    any = true;
-                    E = __fadd_rn(E, drop);
-                    if (drop != 0.0f) {
-                        dx = __fadd_rn(dx, __fdiv_rn(mx, drop));
-                        dy = __fadd_rn(dy, __fdiv_rn(my, drop));
-                    }
-                }
-                if (any && E != 0.0f) {
-                    atomicAdd(&hhit[hist_bin(E, p.hist_neg_lo_s, p.hist_inv_w, p.hist_bins)], 1u);
-                    const float qr = rintf(__fdiv_rn(E, p.photon_kev));
-                    uint16_t flags = 0;
-                    if (!(qr >= 0.0f)) {
-                        n = 0;
-                    } else if (qr > 255.0f) {
-                        n = 255;
-                        flags |= PD_HIT_SATURATED;
-                    } else {
-                        n = (uint32_t)qr;
-                    }
-                    if (n >= 1) {
-                        if (r == 0 || c == 0 || r == R - 1 || c == C - 1) flags |= PD_HIT_EDGE;
-                        pix = (uint32_t)mod_base + (uint32_t)r * p.cols + (uint32_t)c;
-                        h.frame = frame_base + f;
-                        h.pixel = pix;
-                        h.energy_kev = E;
-                        h.dx = dx;
-                        h.dy = dy;
-                        h.count = (uint8_t)n;
-                        h.npix = (uint8_t)(npix > 255 ? 255 : npix);
-                        h.flags = flags;
-                        emit = true;
-                    }
-                }
+                float E, dx, dy;
+                uint32_t npix;
+                if (evaluate_bank(sb, &tile[ir][ic], win, E, dx, dy, npix) && E != 0.0f)
+                    emit = make_hit(p, hhit, E, dx, dy, npix, r, c, frame_base + f, mod_base, h,
+                                    n, pix);
             }
-            const uint32_t mask = __ballot_sync(0xffffffffu, emit);
-            if (mask) {
-                uint32_t slot = 0;
-                if (lane == __ffs(mask) - 1) slot = atomicAdd(out.n_hits, __popc(mask));
-                slot = __shfl_sync(0xffffffffu, slot, __ffs(mask) - 1);
-                if (emit) {
-                    slot += __popc(mask & ((1u << lane) - 1u));
-                    atomicAdd(&p.count_map[pix], n);
-                    if (slot < out.hit_capacity) out.hits[slot] = h;
-                }
-            }
+            emit_hits(p, out, emit, h, n, pix, lane);
         }
         __syncthreads();
     }
     for (uint32_t b = threadIdx.x; b < p.hist_bins; b += kThreads) {
+        if (hpix[b]) atomicAdd(&p.hist_pix[b], (unsigned long long)hpix[b]);
+        if (hhit[b]) atomicAdd(&p.hist_hit[b], (unsigned long long)hhit[b]);
+    }
+}
+
+// Shared memory of the band kernel for bands of rb rows: the s-tile of
+// rb + 3 rows (one above, two below) at the given pitch, both histograms
+// (plus a spare bin), the candidate list, the negated common mode of every
+// (tile row, unit column), the stacked row terms and the signal nibbles.
+size_t band_smem(const ChainParams& p, uint32_t rb, uint32_t pitch) {
+    const size_t nr = rb + 3;
+    return 4 * (nr * pitch + 2 * (size_t)p.hist_bins + 4 + kSeedCap + nr * p.units_per_row + nr) +
+           nr * (pitch / 4);
+}
+
+constexpr uint32_t kMaxTaps = PD_MAX_FEATURES * 20;
+
+// Bands of rb rows of (frame, module): tile t is band t % n_bands of module
+// (t / n_bands) % n_modules of frame t / (n_bands * n_modules).
+template <bool STACKED>
+__global__ void __launch_bounds__(kBandThreads, 2)
+    matched_band_kernel(ChainParams p, const MatchedBank* __restrict__ bank,
+                        const uint16_t* __restrict__ raw, uint32_t frame_base, CallOut out,
+                        BandConfig bc, unsigned long long n_tiles) {
+    extern __shared__ __align__(16) uint32_t msm[];
+    __shared__ MatchedBank sb;
+    __shared__ uint32_t s_nc;
+    const uint32_t P = bc.pitch, NQ = P / 4, NR = bc.rb + 3;
+    float* stile = reinterpret_cast<float*>(msm);  // NR x P; real column c at 4 + c
+    uint32_t* hpix = msm + NR * P;                 // hist_bins + spare
+    uint32_t* hhit = hpix + p.hist_bins + 4;       // hist_bins
+    uint32_t* list = hhit + p.hist_bins;           // kSeedCap
+    float* cmt = reinterpret_cast<float*>(list + kSeedCap);  // NR x units_per_row
+    float* crt = cmt + NR * p.units_per_row;                  // NR row terms
+    // nibble q of a row: signal bits of s-tile columns 4q .. 4q + 3 (real
+    // columns 4q - 4 .. 4q - 1); the first and last nibble stay 0
+    uint8_t* nib = reinterpret_cast<uint8_t*>(crt + NR);
+
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31;
+    const int R = (int)p.rows, C = (int)p.cols;
+    const uint32_t TX = bc.tx, TY = bc.ty;
+    const uint32_t tx = tid % TX, ty = tid / TX;
+    const bool active = ty < TY;
+    const int col = (int)(tx * 4);  // first column of this thread's chunk
+    const uint32_t uca = (uint32_t)col / p.unit_cols;
+    const uint32_t ucb = (uint32_t)(col + 3) / p.unit_cols;
+    const int split = (int)(ucb * p.unit_cols) - col;  // pixels i >= split use ucb
+    const int max_bits = (int)(kMagicBits + p.hist_bins - 1);
+    const int trash_bits = (int)(kMagicBits + p.hist_bins);
+
+    for (uint32_t i = tid; i < NR * P; i += nthr) stile[i] = 0.0f;
+    for (uint32_t i = tid; i < NR * NQ; i += nthr) nib[i] = 0;
+    for (uint32_t i = tid; i < 2 * p.hist_bins + 4; i += nthr) hpix[i] = 0;
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(bank);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&sb);
+        for (uint32_t k = tid; k < sizeof(MatchedBank) / 4; k += nthr) dst[k] = src[k];
+    }
+    __syncthreads();
+    // tap offsets at this pitch
+    for (uint32_t k = tid; k < 4 * kMaxTaps; k += nthr) {
+        MatchedTap* lst = k < kMaxTaps ? sb.t1 : k < 2 * kMaxTaps ? sb.t0
+                                             : k < 3 * kMaxTaps ? sb.tx : sb.ty;
+        MatchedTap& tp = lst[k % kMaxTaps];
+        tp.at = (uint16_t)(tp.i * P + tp.j);
+    }
+
+    // negated common mode of entry i (tile row, unit column) of tile tt; each
+    // thread holds its entry of the next tile in a register
+    const uint32_t ncmt = NR * p.units_per_row;
+    auto tile_cm = [&](unsigned long long tt, uint32_t i) -> float {
+        const unsigned long long fm = tt / bc.n_bands;
+        const int r = (int)(tt - fm * bc.n_bands) * (int)bc.rb - 1 + (int)(i / p.units_per_row);
+        if (r < 0 || r >= R) return 0.0f;
+        const size_t fbase = (size_t)fm * p.units_per_module +
+                             (STACKED ? (size_t)(fm / p.n_modules) *
+                                            (cm_per_frame(p) - p.units_per_frame)
+                                      : 0);
+        return -out.cm[fbase + ((uint32_t)r / p.unit_rows) * p.units_per_row +
+                       i % p.units_per_row];
+    };
+    float cmv = 0.0f;
+    if (blockIdx.x < n_tiles && tid < ncmt) cmv = tile_cm(blockIdx.x, tid);
+
+    for (unsigned long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        unsigned long long q = t;
+        const int band = (int)(q % bc.n_bands);
+        q /= bc.n_bands;
+        const uint32_t m = (uint32_t)(q % p.n_modules);
+        const uint32_t f = (uint32_t)(q / p.n_modules);
+        const int r0 = band * (int)bc.rb;
+        const int rows_here = min((int)bc.rb, R - r0);
+        const size_t mod_base = (size_t)m * p.module_px;
+        const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
+        const float* npm = p.nped + mod_base;
+        const float* gm = p.inv_gain + mod_base;
+
+        if (tid < ncmt) cmt[tid] = cmv;
+        for (uint32_t i = tid + nthr; i < ncmt; i += nthr) cmt[i] = tile_cm(t, i);
+        float ncc[4];
+        if (STACKED) {
+            const float* cmf = out.cm + (size_t)f * cm_per_frame(p) + p.units_per_frame;
+            for (uint32_t i = tid; i < NR; i += nthr) {
+                const int r = r0 - 1 + (int)i;
+                crt[i] = r >= 0 && r < R ? -cmf[(size_t)m * p.rows + r] : 0.0f;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                ncc[i] = active ? -cmf[(size_t)p.n_modules * p.rows + (size_t)m * p.cols + col + i]
+                                : 0.0f;
+        }
+        if (tid == 0) s_nc = 0;
+        __syncthreads();
+
+        // 1. zeroed signal and its nibbles of rows r0-1 .. r0+rows_here+1;
+        //    halo rows are not histogrammed (their bins go to the spare bin)
+        if (active) {
+            const int nrows = rows_here + 3;
+            constexpr int U = 1;
+            for (int rl0 = (int)ty; rl0 < nrows; rl0 += U * (int)TY) {
+                uint2 rr[U];
+                float4 pp[U], gg[U];
+                bool in[U];
+#pragma unroll
+                for (int j = 0; j < U; j++) {
+                    const int rl = rl0 + j * (int)TY;
+                    const int r = r0 - 1 + rl;
+                    in[j] = rl < nrows && r >= 0 && r < R;
+                    if (in[j]) {
+                        const uint32_t off = (uint32_t)r * p.cols + (uint32_t)col;
+                        rr[j] = *reinterpret_cast<const uint2*>(fr + off);
+                        pp[j] = *reinterpret_cast<const float4*>(npm + off);
+                        gg[j] = *reinterpret_cast<const float4*>(gm + off);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < U; j++) {
+                    const int rl = rl0 + j * (int)TY;
+                    if (rl >= nrows) continue;
+                    float* srow = stile + rl * P + 4 + col;
+                    uint8_t* nq = nib + rl * NQ + tx + 1;
+                    if (!in[j]) {
+                        *reinterpret_cast<float4*>(srow) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        *nq = 0;
+                        continue;
+                    }
+                    const int r = r0 - 1 + rl;
+                    const bool own = rl >= 1 && rl <= rows_here;
+                    const int blo = own ? (int)kMagicBits : trash_bits;
+                    const int bhi = own ? max_bits : trash_bits;
+                    const float ncma = cmt[rl * p.units_per_row + uca];
+                    const float ncmb = cmt[rl * p.units_per_row + ucb];
+                    const float2 d01 = __fadd2_rn(raw_pair(rr[j].x), make_float2(pp[j].x, pp[j].y));
+                    const float2 d23 = __fadd2_rn(raw_pair(rr[j].y), make_float2(pp[j].z, pp[j].w));
+                    const float2 n01 = make_float2(split > 0 ? ncma : ncmb, split > 1 ? ncma : ncmb);
+                    const float2 n23 = make_float2(split > 2 ? ncma : ncmb, split > 3 ? ncma : ncmb);
+                    float2 c01 = __fadd2_rn(d01, n01), c23 = __fadd2_rn(d23, n23);
+                    if (STACKED) {
+                        const float ncr = crt[rl];
+                        c01 = __fadd2_rn(__fadd2_rn(c01, make_float2(ncr, ncr)),
+                                         make_float2(ncc[0], ncc[1]));
+                        c23 = __fadd2_rn(__fadd2_rn(c23, make_float2(ncr, ncr)),
+                                         make_float2(ncc[2], ncc[3]));
+                    }
+                    const float2 e01 = __fmul2_rn(c01, make_float2(gg[j].x, gg[j].y));
+                    const float2 e23 = __fmul2_rn(c23, make_float2(gg[j].z, gg[j].w));
+                    const float2 iw = make_float2(p.hist_inv_w, p.hist_inv_w);
+                    const float2 nl = make_float2(p.hist_neg_lo_s, p.hist_neg_lo_s);
+                    const float2 mgc = make_float2(kMagic, kMagic);
+                    const float2 u01 = __fadd2_rd(__ffma2_rn(e01, iw, nl), mgc);
+                    const float2 u23 = __fadd2_rd(__ffma2_rn(e23, iw, nl), mgc);
+                    atomicAdd(&hpix[(uint32_t)min(max(__float_as_int(u01.x), blo), bhi) - kMagicBits], 1u);
+                    atomicAdd(&hpix[(uint32_t)min(max(__float_as_int(u01.y), blo), bhi) - kMagicBits], 1u);
+                    atomicAdd(&hpix[(uint32_t)min(max(__float_as_int(u23.x), blo), bhi) - kMagicBits], 1u);
+                    atomicAdd(&hpix[(uint32_t)min(max(__float_as_int(u23.y), blo), bhi) - kMagicBits], 1u);
+                    const float e[4] = {e01.x, e01.y, e23.x, e23.y};
+                    float sv[4];
+                    uint32_t bits = 0;
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        sv[i] = e[i] > p.zero_thr ? e[i] : 0.0f;
+                        bits |= (uint32_t)(sv[i] > 0.0f) << i;
+                    }
+                    *reinterpret_cast<float4*>(srow) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+                    *nq = (uint8_t)bits;
+                    if (own && out.corrected) {
+                        const uint32_t off = (uint32_t)r * p.cols + (uint32_t)col;
+                        float* dst = out.corrected + (size_t)f * p.frame_px + mod_base + off;
+                        *reinterpret_cast<float4*>(dst) = make_float4(e[0], e[1], e[2], e[3]);
+                    }
+                }
+            }
+        }
+        // the next tile's common mode, in flight during the rest of this one
+        if (t + gridDim.x < n_tiles && tid < ncmt) cmv = tile_cm(t + gridDim.x, tid);
+        __syncthreads();
+
+        // 2. pixels whose window holds signal: each thread walks a run of
+        //    own rows of its chunk; g holds the nibbles q-1 .. q+1 of a row
+        //    (s-tile columns col .. col + 11), and pixel col + i's window
+        //    columns are its bits i + 2 .. i + 6
+        uint64_t cmask = 0;  // bit 4 k + i: row a + k, pixel col + i
+        const int seg = (rows_here + (int)TY - 1) / (int)TY;
+        const int a = 1 + (int)ty * seg;
+        const int b = min(rows_here, a + seg - 1);
+        if (active && a <= b) {
+            const uint8_t* nb = nib + tx;
+            auto g_of = [&](int rl) -> uint32_t {
+                const uint8_t* g = nb + rl * NQ;
+                return (uint32_t)g[0] | (uint32_t)g[1] << 4 | (uint32_t)g[2] << 8;
+            };
+            uint32_t g0 = g_of(a - 1), g1 = g_of(a), g2 = g_of(a + 1);
+            for (int rl = a; rl <= b; rl++) {
+                const uint32_t g3 = g_of(rl + 2);
+                const uint32_t o = (g0 | g1 | g2 | g3) >> 2;
+                const uint32_t c4 = (uint32_t)((o & 0x1Fu) != 0) | (uint32_t)((o & 0x3Eu) != 0) << 1 |
+                                    (uint32_t)((o & 0x7Cu) != 0) << 2 |
+                                    (uint32_t)((o & 0xF8u) != 0) << 3;
+                cmask |= (uint64_t)c4 << (4 * (rl - a));
+                g0 = g1;
+                g1 = g2;
+                g2 = g3;
+            }
+        }
+        // compaction: a warp scan and one shared atomic per warp (the last
+        // warp of the block may be partial)
+        {
+            const unsigned wm = __activemask();
+            const uint32_t cnt = (uint32_t)__popcll(cmask);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(wm, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int wl = 31 - __clz((int)wm);
+            const uint32_t tot = __shfl_sync(wm, incl, wl);
+            uint32_t base = 0;
+            if (lane == wl && tot) base = atomicAdd(&s_nc, tot);
+            base = __shfl_sync(wm, base, wl);
+            uint32_t at = base + incl - cnt;
+            while (cmask && at < kSeedCap) {
+                const int bit = __ffsll((long long)cmask) - 1;
+                cmask &= cmask - 1;
+                list[at++] = ((uint32_t)(a + bit / 4) << 16) | (uint32_t)(col + bit % 4);
+            }
+        }
+        __syncthreads();
+
+        // 3. the bank at the listed pixels (every own pixel if the list
+        //    overflowed)
+        const uint32_t n_list = s_nc;
+        const bool scan = n_list > kSeedCap;
+        const uint32_t n_work = scan ? (uint32_t)rows_here * (uint32_t)C : n_list;
+        for (uint32_t base = 0; base < n_work; base += nthr) {
+            const uint32_t j = base + tid;
+            bool emit = false;
+            pd_hit h;
+            uint32_t n = 0, pix = 0;
+            if (j < n_work) {
+                int rl, c;
+                if (scan) {
+                    rl = 1 + (int)(j / (uint32_t)C);
+                    c = (int)(j % (uint32_t)C);
+                } else {
+                    const uint32_t e = list[j];
+                    rl = (int)(e >> 16);
+                    c = (int)(e & 0xFFFFu);
+                }
+                // window rows rl-1 .. rl+2, columns c-2 .. c+2: bits
+                // 2 + c % 4 .. 6 + c % 4 of nibbles c / 4 .. c / 4 + 2
+                const uint8_t* nw = nib + (rl - 1) * NQ + c / 4;
+                const int sh = 2 + (c & 3);
+                uint32_t win = 0;
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const uint8_t* g = nw + i * NQ;
+                    const uint32_t gr = (uint32_t)g[0] | (uint32_t)g[1] << 4 | (uint32_t)g[2] << 8;
+                    win |= ((gr >> sh) & 0x1Fu) << (5 * i);
+                }
+                float E, dx, dy;
+                uint32_t npix;
+                if (win && evaluate_bank(sb, stile + (rl - 1) * P + c + 2, win, E, dx, dy, npix) &&
+                    E != 0.0f)
+                    emit = make_hit(p, hhit, E, dx, dy, npix, r0 - 1 + rl, c, frame_base + f,
+                                    mod_base, h, n, pix);
+            }
+            emit_hits(p, out, emit, h, n, pix, lane);
+        }
+        __syncthreads();
+    }
+    for (uint32_t b = tid; b < p.hist_bins; b += nthr) {
         if (hpix[b]) atomicAdd(&p.hist_pix[b], (unsigned long long)hpix[b]);
         if (hhit[b]) atomicAdd(&p.hist_hit[b], (unsigned long long)hhit[b]);
     }
@@ -283,6 +611,8 @@ void compile_taps(const float (*flt)[5], MatchedTap* list, uint32_t* n) {
     for (int i = 0; i < 4; i++)
         for (int j = 0; j < 5; j++)
             if (flt[i][j] != 0.0f) {
+                list[*n].i = (uint8_t)i;
+                list[*n].j = (uint8_t)j;
                 list[*n].at = (uint16_t)(i * kHX + j);
                 list[*n].v = flt[i][j];
                 (*n)++;
@@ -333,9 +663,59 @@ bool compile_bank(const pd_filter_bank& b, MatchedBank* out) {
     return true;
 }
 
+// Band form of the matched stencil: single gain, raw - pedestal before the
+// common mode, four-pixel chunks (as the band stencil's), and bands of at
+// least one row within about 100 KB of shared memory.
+static bool matched_band_config(const ChainParams& p, BandConfig* out) {
+    if (cm_after_gain(p)) return false;
+    BandConfig bc = make_band_config(p);
+    if (!bc.ok || bc.vec != 4) return false;
+    uint32_t rb = std::min<uint32_t>(std::max<uint32_t>(4, 12288 / p.cols), p.rows);
+    // a thread's run of rows (4 pixels each) fits its 64-bit candidate mask
+    while (rb > 1 && ((rb + bc.ty - 1) / bc.ty) * 4 > 64) rb--;
+    while (rb > 1 && band_smem(p, rb, bc.pitch) > 100 * 1024) rb--;
+    if (band_smem(p, rb, bc.pitch) > 100 * 1024) return false;
+    bc.rb = rb;
+    bc.n_bands = (p.rows + rb - 1) / rb;
+    *out = bc;
+    return true;
+}
+
+static int g_attr_dev_mband = -1;
+
 cudaError_t launch_matched(const ChainParams& p, const MatchedBank* bank_dev,
                            const uint16_t* raw, uint32_t n_frames, uint32_t frame_base,
                            const CallOut& out, cudaStream_t stream, const MultiGain* mg) {
+    BandConfig bc;
+    if (!mg && matched_band_config(p, &bc)) {
+        const unsigned long long n_tiles =
+            (unsigned long long)n_frames * p.n_modules * bc.n_bands;
+        if (n_tiles == 0) return cudaSuccess;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (g_attr_dev_mband != dev) {
+            for (auto k : {matched_band_kernel<false>, matched_band_kernel<true>}) {
+                cudaError_t e = cudaFuncSetAttribute(
+                    k, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+                if (e != cudaSuccess) return e;
+            }
+            g_attr_dev_mband = dev;
+        }
+        const size_t smem = band_smem(p, bc.rb, bc.pitch);
+        const size_t per_cta = smem + sizeof(MatchedBank) + 1024;
+        int per_sm = (int)((228 * 1024) / per_cta);
+        per_sm = std::max(1, std::min(per_sm, 2));
+        unsigned long long grid = (unsigned long long)device_sm_count() * per_sm;
+        if (grid > n_tiles) grid = n_tiles;
+        const unsigned threads = bc.tx * bc.ty;
+        if (cm_kind(p) == PD_CM_MEAN_STACKED)
+            matched_band_kernel<true><<<(unsigned)grid, threads, smem, stream>>>(
+                p, bank_dev, raw, frame_base, out, bc, n_tiles);
+        else
+            matched_band_kernel<false><<<(unsigned)grid, threads, smem, stream>>>(
+                p, bank_dev, raw, frame_base, out, bc, n_tiles);
+        return cudaGetLastError();
+    }
     const uint32_t tiles_y = (p.rows + kTY - 1) / kTY;
     const uint32_t tiles_x = (p.cols + kTX - 1) / kTX;
     const unsigned long long n_tiles =

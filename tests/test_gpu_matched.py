@@ -84,6 +84,47 @@ def test_workloads_bit_exact(name, bank):
     _compare(ctx, out, ref, n)
 
 
+# Shapes of the band form (columns a multiple of 4, single gain): ragged last
+# bands, modules of one and two rows, the widest and narrowest rows, units
+# two columns wide (a four-pixel chunk meets two units), and signal dense
+# enough that a band's candidate list overflows and every pixel is tested.
+D = synth.Detector
+BAND_SHAPES = {
+    "one_row_modules": (D(n_modules=3, rows=1, cols=96, unit_rows=1, unit_cols=48,
+                          occupancy=0.1), 4),
+    "two_row_modules": (D(n_modules=2, rows=2, cols=388, unit_rows=2, unit_cols=194,
+                          occupancy=0.05), 3),
+    "ragged_bands_100x128": (D(n_modules=2, rows=100, cols=128, unit_rows=25, unit_cols=64,
+                               occupancy=0.03), 3),
+    "wide_2048": (D(n_modules=1, rows=20, cols=2048, unit_rows=20, unit_cols=512,
+                    occupancy=0.01), 2),
+    "narrow_4": (D(n_modules=2, rows=700, cols=4, unit_rows=100, unit_cols=4,
+                   occupancy=0.05), 2),
+    "two_column_units": (D(n_modules=1, rows=24, cols=64, unit_rows=24, unit_cols=2,
+                           occupancy=0.03), 3),
+    "dense_overflow": (D(n_modules=2, rows=40, cols=388, unit_rows=40, unit_cols=194,
+                         occupancy=0.5, cloud_sigma=0.5), 2),
+}
+
+
+@pytest.mark.parametrize("bank", ["example", "random1"])
+@pytest.mark.parametrize("name", list(BAND_SHAPES))
+def test_band_shapes_bit_exact(name, bank):
+    det, n = BAND_SHAPES[name]
+    ctx, out, ref = _run(det, n, BANKS[bank])
+    if bank == "example":
+        assert ref.n_hits > 0
+    _compare(ctx, out, ref, n)
+
+
+@pytest.mark.parametrize("name", ["ragged_bands_100x128", "dense_overflow"])
+def test_band_shapes_stacked_mean(name):
+    det, n = BAND_SHAPES[name]
+    ctx, out, ref = _run(det, n, filters.example_bank(), cm_mode=pd.PD_CM_MEAN_STACKED)
+    assert ref.n_hits > 0
+    _compare(ctx, out, ref, n)
+
+
 def test_with_stacked_mean_common_mode():
     det = synth.cspad_2p2m(n_modules=2, occupancy=0.01)
     ctx, out, ref = _run(det, 3, filters.example_bank(), cm_mode=pd.PD_CM_MEAN_STACKED)

@@ -90,6 +90,17 @@ WORKLOADS = {
     "high_occupancy_pileup": (synth.asic_352x384(rows=64, occupancy=0.1,
                                                  cloud_sigma_hi=0.5,
                                                  cloud_sigma=0.2), 3),
+    # narrow units: a four-pixel chunk of the band stencil meets up to four
+    # units of one column, two of two or three columns
+    "column_units_48x64": (synth.Detector(n_modules=2, rows=48, cols=64,
+                                          unit_rows=48, unit_cols=1,
+                                          occupancy=0.02), 3),
+    "two_column_units_40x96": (synth.Detector(n_modules=1, rows=40, cols=96,
+                                              unit_rows=20, unit_cols=2,
+                                              occupancy=0.02), 3),
+    "three_column_units_33x72": (synth.Detector(n_modules=2, rows=33, cols=72,
+                                                unit_rows=11, unit_cols=3,
+                                                occupancy=0.02), 3),
 }
 
 
