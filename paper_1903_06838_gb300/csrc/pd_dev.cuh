@@ -23,6 +23,37 @@ __device__ __forceinline__ float key_value(uint32_t k) {
 }
 
 
+// Band, module and frame of tiles t, t + step, t + 2 step, ... of a band
+// stencil (tile t is band t % nb of module (t / nb) % nm of frame
+// t / (nb nm)), split once and then advanced with carries instead of 64-bit
+// divisions per tile.
+struct TileWalk {
+    uint32_t band, m, f;     // of the current tile
+    uint32_t sb, sm, sf;     // the step split the same way
+    uint32_t nb, nm;
+    __device__ __forceinline__ TileWalk(unsigned long long t, unsigned long long step,
+                                        uint32_t n_bands, uint32_t n_modules)
+        : nb(n_bands), nm(n_modules) {
+        band = (uint32_t)(t % nb);
+        t /= nb;
+        m = (uint32_t)(t % nm);
+        f = (uint32_t)(t / nm);
+        sb = (uint32_t)(step % nb);
+        step /= nb;
+        sm = (uint32_t)(step % nm);
+        sf = (uint32_t)(step / nm);
+    }
+    __device__ __forceinline__ void next() {
+        band += sb;
+        const uint32_t cb = band >= nb;
+        if (cb) band -= nb;
+        m += sm + cb;  // below 2 nm
+        const uint32_t cm = m >= nm;
+        if (cm) m -= nm;
+        f += sf + cm;
+    }
+};
+
 // Histogram bin of the summaries: floor(fma(v, inv_w, -lo_s)) clipped to
 // [0, bins-1], as the code of an element of a 32-bit histogram array.
 __device__ __forceinline__ uint32_t summary_bin(float v, float inv_w, float neg_lo_s,

@@ -194,34 +194,45 @@ __device__ void cm_big_unit(const ChainParams& p, const uint16_t* __restrict__ r
 
     if (bin != 0) {
         // pass B: positions of the winning bin's pixels (shared memory only),
-        // then one parallel fetch of their raw value and pedestal
+        // then one parallel fetch of their raw value and pedestal.  The codes
+        // are a row-major array of one 16-bit code per pixel of the unit (in
+        // both layouts), read eight at a time; a halfword h of y = word ^
+        // (bin, bin) is zero iff bit 15 of ((h & 0x7FFF) + 0x7FFF) | h is
+        // clear.  About one pixel in a hundred matches: each takes a slot
+        // with a shared atomic (list order is free; s_cand counts every
+        // match, so an overflow is seen).
         uint32_t* cidx = reinterpret_cast<uint32_t*>(cand);
         const uint32_t both = bin | (bin << 16);
-        uint32_t mine = 0;  // this thread's candidates (no atomics in the loop)
-        if (active) {
-            for (uint32_t r = ty; r < p.unit_rows; r += TY) {
-                const uint32_t w = r * TX + tx;
-                if (VEC == 2) {
-                    const uint32_t y = codes[w] ^ both;
-                    mine += ((y & 0xFFFFu) == 0) + ((y >> 16) == 0);
-                } else {
-                    mine += reinterpret_cast<const uint16_t*>(codes)[w] == bin;
-                }
+        auto take = [&](uint32_t y, uint32_t px0) {
+            uint32_t z = ~((((y & 0x7FFF7FFFu) + 0x7FFF7FFFu) | y)) & 0x80008000u;
+            while (z) {
+                const uint32_t at = atomicAdd(&s_cand, 1u);
+                if (at < kCandCap) cidx[at] = px0 + ((z & 0x8000u) ? 0u : 1u);
+                z &= z - 1;
+            }
+        };
+        const uint32_t n8 = p.unit_px / 8;
+        const uint4* c8 = reinterpret_cast<const uint4*>(codes);
+        for (uint32_t q = tid; q < n8; q += nthr) {
+            const uint4 v = c8[q];
+            const uint32_t y0 = v.x ^ both, y1 = v.y ^ both, y2 = v.z ^ both, y3 = v.w ^ both;
+            const uint32_t t0 = ((y0 & 0x7FFF7FFFu) + 0x7FFF7FFFu) | y0;
+            const uint32_t t1 = ((y1 & 0x7FFF7FFFu) + 0x7FFF7FFFu) | y1;
+            const uint32_t t2 = ((y2 & 0x7FFF7FFFu) + 0x7FFF7FFFu) | y2;
+            const uint32_t t3 = ((y3 & 0x7FFF7FFFu) + 0x7FFF7FFFu) | y3;
+            if ((t0 & t1 & t2 & t3 & 0x80008000u) != 0x80008000u) {
+                take(y0, 8 * q);
+                take(y1, 8 * q + 2);
+                take(y2, 8 * q + 4);
+                take(y3, 8 * q + 6);
             }
         }
-        uint32_t at = block_excl_scan(mine, swarp, &s_cand);
-        if (active && mine) {
-            for (uint32_t r = ty; r < p.unit_rows && at < kCandCap; r += TY) {
-                const uint32_t w = r * TX + tx;
-                if (VEC == 2) {
-                    const uint32_t y = codes[w] ^ both;
-                    if ((y & 0xFFFFu) == 0 && at < kCandCap) cidx[at++] = 2 * w;
-                    if ((y >> 16) == 0 && at < kCandCap) cidx[at++] = 2 * w + 1;
-                } else if (reinterpret_cast<const uint16_t*>(codes)[w] == bin) {
-                    cidx[at++] = w;
-                }
+        const uint16_t* c16 = reinterpret_cast<const uint16_t*>(codes);
+        for (uint32_t i = 8 * n8 + tid; i < p.unit_px; i += nthr)
+            if (c16[i] == bin) {
+                const uint32_t at = atomicAdd(&s_cand, 1u);
+                if (at < kCandCap) cidx[at] = i;
             }
-        }
         __syncthreads();
         const uint32_t mc = s_cand;
         if (mc <= kCandCap) {
@@ -582,12 +593,10 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
     float cmv = 0.0f;
     if (first < n_tiles && tid < ncmt) cmv = tile_cm((uint32_t)first, tid);
 
-    for (unsigned long long t = first; t < n_tiles; t += step) {
-        unsigned long long q = t;
-        const int band = (int)(q % bc.n_bands);
-        q /= bc.n_bands;
-        const uint32_t m = (uint32_t)(q % p.n_modules);
-        const uint32_t f = (uint32_t)(q / p.n_modules);
+    TileWalk walk(first, step, bc.n_bands, p.n_modules);
+    for (unsigned long long t = first; t < n_tiles; t += step, walk.next()) {
+        const int band = (int)walk.band;
+        const uint32_t m = walk.m, f = walk.f;
         const int r0 = band * (int)bc.rb;
         const int rows_here = min((int)bc.rb, R - r0);
         const size_t mod_base = (size_t)m * p.module_px;

@@ -393,12 +393,10 @@ __global__ void __launch_bounds__(kBandThreads, 2)
     float cmv = 0.0f;
     if (blockIdx.x < n_tiles && tid < ncmt) cmv = tile_cm(blockIdx.x, tid);
 
-    for (unsigned long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        unsigned long long q = t;
-        const int band = (int)(q % bc.n_bands);
-        q /= bc.n_bands;
-        const uint32_t m = (uint32_t)(q % p.n_modules);
-        const uint32_t f = (uint32_t)(q / p.n_modules);
+    TileWalk walk(blockIdx.x, gridDim.x, bc.n_bands, p.n_modules);
+    for (unsigned long long t = blockIdx.x; t < n_tiles; t += gridDim.x, walk.next()) {
+        const int band = (int)walk.band;
+        const uint32_t m = walk.m, f = walk.f;
         const int r0 = band * (int)bc.rb;
         const int rows_here = min((int)bc.rb, R - r0);
         const size_t mod_base = (size_t)m * p.module_px;
