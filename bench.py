@@ -35,8 +35,7 @@ HIT_BYTES = 24
 # DRAM bytes (read + write) per frame of each kernel, from the ncu capture
 # summarised in profiles/cspad_2p2m_chain.md; set an entry to None when its
 # kernel changes until it is captured again.
-NCU_TRAFFIC_PER_FRAME = {"stencil": 129.202944e6 / 21, "common_mode": 108.918016e6 / 21,
-                         "fused_chain": None}
+NCU_TRAFFIC_PER_FRAME = {"stencil": None, "common_mode": None, "fused_chain": None}
 
 
 def parse():

@@ -54,6 +54,7 @@ struct pd_ctx {
     float* d_mg_ig = nullptr;
     bool matched = false;       // matched-filter charge summing (pd_set_filter_bank)
     pd::MatchedBank* d_bank = nullptr;
+    uint8_t* d_vtab = nullptr;  // valid-feature table of an all-binary bank
     uint32_t chunk_frames = 1;  // frames per common-mode/stencil launch pair
     uint32_t overlap = 1;       // common mode of chunk c+1 beside stencil of c
     cudaStream_t aux = nullptr; // second stream of the chunk pipeline
@@ -194,6 +195,7 @@ void free_ctx(pd_ctx* c) {
     cudaFree(c->d_hist_hit);
     cudaFree(c->d_cm);
     cudaFree(c->d_bank);
+    cudaFree(c->d_vtab);
     cudaFree(c->d_mg_ped);
     cudaFree(c->d_mg_ig);
     cudaFree(c->d_stage[0]);
@@ -719,6 +721,18 @@ int pd_set_filter_bank(pd_ctx* c, const pd_filter_bank* bank) {
     }
     if ((e = cudaMemcpy(c->d_bank, &mb, sizeof(mb), cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail_cuda(e, "filter bank upload");
+    if (mb.all_binary) {
+        // the table is built from the uploaded bank, then the bank points at it
+        if (!c->d_vtab && (e = cudaMalloc(&c->d_vtab, 1u << 20)) != cudaSuccess) {
+            c->d_vtab = nullptr;
+            return fail(PD_ENOMEM, "filter bank table allocation failed");
+        }
+        if ((e = pd::build_vtab(c->d_bank, c->d_vtab)) != cudaSuccess)
+            return fail_cuda(e, "filter bank table");
+        mb.vtab = c->d_vtab;
+        if ((e = cudaMemcpy(c->d_bank, &mb, sizeof(mb), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail_cuda(e, "filter bank upload");
+    }
     c->matched = true;
     return PD_OK;
 }

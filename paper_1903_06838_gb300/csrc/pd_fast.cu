@@ -566,7 +566,6 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
     const int split = (int)(ucb * p.unit_cols) - col;  // pixels i >= split use ucb
     const int max_bits = (int)(kMagicBits + p.hist_bins - 1);
     const int trash_bits = (int)(kMagicBits + p.hist_bins);  // spare bin of hpix
-    const bool seed_eq = p.seed_thr == p.zero_thr;
 
     // zero the whole s-tile once (pad columns stay zero), and the histograms
     for (uint32_t i = tid; i < (bc.rb + 2) * P; i += nthr) stile[i] = 0.0f;
@@ -714,12 +713,11 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
                         atomicAdd(&hpix[(uint32_t)min(max(__float_as_int(u), blo), bhi) - kMagicBits], 1u);
                     }
                     float sv[VEC];
-                    bool cand = false;
+                    uint32_t seeds = 0;  // bit i: pixel i passes the seed threshold
 #pragma unroll
                     for (int i = 0; i < VEC; i++) {
-                        const bool sig = e[i] > p.zero_thr;
-                        sv[i] = sig ? e[i] : 0.0f;
-                        cand = cand || (seed_eq ? sig : (sv[i] > p.seed_thr));
+                        sv[i] = e[i] > p.zero_thr ? e[i] : 0.0f;
+                        seeds |= (uint32_t)(sv[i] > p.seed_thr) << i;
                     }
                     if (VEC == 4)
                         *reinterpret_cast<float4*>(srow) = make_float4(sv[0], sv[1], sv[2], sv[3]);
@@ -733,11 +731,7 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
                         else
                             dst[0] = e[0];
                     }
-                    if (own && cand) {
-#pragma unroll
-                        for (int i = 0; i < VEC; i++)
-                            if (sv[i] > p.seed_thr) cmask |= 1ull << ((kk + j) * VEC + i);
-                    }
+                    if (own) cmask |= (uint64_t)seeds << ((kk + j) * VEC);
                 }
             }
         }

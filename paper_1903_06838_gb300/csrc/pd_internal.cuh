@@ -118,6 +118,11 @@ struct MatchedBank {
     uint16_t offx[PD_MAX_FEATURES + 1], offy[PD_MAX_FEATURES + 1];
     MatchedTap t1[PD_MAX_FEATURES * 20], t0[PD_MAX_FEATURES * 20];
     MatchedTap tx[PD_MAX_FEATURES * 20], ty[PD_MAX_FEATURES * 20];
+    // every feature binary (f1_unit and f0_pos): the valid features of a
+    // pixel depend on its window mask alone, and vtab (device, 2^20 bytes,
+    // or null) holds them for every mask
+    uint32_t all_binary;
+    const uint8_t* vtab;
 };
 
 // Per-call outputs (device pointers).
@@ -142,6 +147,9 @@ cudaError_t launch_stencil(const ChainParams& p, const uint16_t* raw,
 size_t cm_select_smem_bytes(const ChainParams& p);
 // Matched-filter stencil (pd_matched.cu); compile_bank validates.
 bool compile_bank(const pd_filter_bank& bank, MatchedBank* out);
+// The valid-feature table of a bank whose features are all binary: 2^20
+// bytes at vtab (synchronous).
+cudaError_t build_vtab(const MatchedBank* bank_dev, uint8_t* vtab);
 cudaError_t launch_matched(const ChainParams& p, const MatchedBank* bank_dev,
                            const uint16_t* raw, uint32_t n_frames, uint32_t frame_base,
                            const CallOut& out, cudaStream_t stream,

@@ -35,9 +35,13 @@
 // matched_band_kernel: the same per pixel on full-width bands of module rows
 // (single gain, raw - pedestal before the common mode), with the band
 // stencil's four-pixel vector loads and packed correction.  Each thread
-// stores the signal bits of its four pixels as one nibble; a pixel's window
-// mask is read from the nibbles of four rows, and each thread tests a run of
-// consecutive rows with the masks of the rows above and below in registers.
+// stores the signal bits of its four pixels as one nibble (a pixel's window
+// mask is read from the nibbles of four rows), and a chunk with signal marks
+// the pixels whose windows it lies in on a bitmap of the band, from which
+// the candidate list is built.  The valid features of every candidate come
+// first (for a bank of binary features, from a table indexed by the window
+// mask); the sums then run over a second list of the candidates with a valid
+// feature, so that they keep every lane busy.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -66,15 +70,14 @@ __device__ __forceinline__ uint32_t hist_bin(float v, float neg_lo_s, float inv_
 
 // The bank at one pixel: w points at its window's tap (0, 0) in a shared
 // tile (tap (i, j) at w[i * pitch + j], the pitch folded into the taps'
-// offsets), win is its 20-bit signal mask.  Returns whether some feature is
-// valid; E, dx, dy and npix (the signal pixels under the first valid
-// feature's F1) as described above.
-__device__ __forceinline__ bool evaluate_bank(const MatchedBank& sb, const float* w,
-                                              uint32_t win, float& E, float& dx, float& dy,
-                                              uint32_t& npix) {
-    E = dx = dy = 0.0f;
-    npix = 0;
-    bool any = false;
+// offsets), win is its 20-bit signal mask.  valid_features gives the mask
+// of the valid features; sum_features their energy E, centroid sums dx, dy
+// and npix (the signal pixels under the first valid feature's F1), as
+// described above.
+__device__ __forceinline__ uint32_t valid_features(const MatchedBank& sb, const float* w,
+                                                   uint32_t win) {
+    if (sb.vtab) return sb.vtab[win];
+    uint32_t valid = 0;
     for (uint32_t ft = 0; ft < sb.n_features; ft++) {
         bool clear;
         if (sb.f0_pos[ft]) {
@@ -94,7 +97,20 @@ __device__ __forceinline__ bool evaluate_bank(const MatchedBank& sb, const float
             for (uint32_t k = sb.off1[ft]; k < sb.off1[ft + 1]; k++)
                 if (w[sb.t1[k].at] > 0.0f) size = __fadd_rn(size, sb.t1[k].v);
         }
-        if (!(size >= sb.nmin[ft])) continue;
+        if (size >= sb.nmin[ft]) valid |= 1u << ft;
+    }
+    return valid;
+}
+
+__device__ __forceinline__ void sum_features(const MatchedBank& sb, const float* w,
+                                             uint32_t valid, float& E, float& dx, float& dy,
+                                             uint32_t& npix) {
+    E = dx = dy = 0.0f;
+    npix = 0;
+    bool any = false;
+    while (valid) {
+        const uint32_t ft = (uint32_t)(__ffs(valid) - 1);
+        valid &= valid - 1;
         float drop = 0.0f, mx = 0.0f, my = 0.0f;
         uint32_t under = 0;
         for (uint32_t k = sb.off1[ft]; k < sb.off1[ft + 1]; k++) {
@@ -114,7 +130,6 @@ __device__ __forceinline__ bool evaluate_bank(const MatchedBank& sb, const float
             dy = __fadd_rn(dy, __fdiv_rn(my, drop));
         }
     }
-    return any;
 }
 
 // Count, flags and record of a pixel whose bank gave energy E (E != 0);
@@ -148,14 +163,16 @@ __device__ __forceinline__ bool make_hit(const ChainParams& p, uint32_t* hhit, f
     return true;
 }
 
-// Warp-aggregated emission: one atomic on the hit counter per warp.
+// Warp-aggregated emission: one atomic on the hit counter per warp.  wm:
+// the warp's lanes (all of them must call).
 __device__ __forceinline__ void emit_hits(const ChainParams& p, const CallOut& out, bool emit,
-                                          const pd_hit& h, uint32_t n, uint32_t pix, int lane) {
-    const uint32_t mask = __ballot_sync(0xffffffffu, emit);
+                                          const pd_hit& h, uint32_t n, uint32_t pix, int lane,
+                                          unsigned wm = 0xffffffffu) {
+    const uint32_t mask = __ballot_sync(wm, emit);
     if (mask) {
         uint32_t slot = 0;
         if (lane == __ffs(mask) - 1) slot = atomicAdd(out.n_hits, __popc(mask));
-        slot = __shfl_sync(0xffffffffu, slot, __ffs(mask) - 1);
+        slot = __shfl_sync(wm, slot, __ffs(mask) - 1);
         if (emit) {
             slot += __popc(mask & ((1u << lane) - 1u));
             atomicAdd(&p.count_map[pix], n);
@@ -297,11 +314,15 @@ __global__ void __launch_bounds__(kThreads)
             const int r = r0 + ir, c = c0 + ic;
             if (k < n_cand) {
                 // window tap (i, j) is tile[ir + i][ic + j]
-                float E, dx, dy;
-                uint32_t npix;
-                if (evaluate_bank(sb, &tile[ir][ic], win, E, dx, dy, npix) && E != 0.0f)
-                    emit = make_hit(p, hhit, E, dx, dy, npix, r, c, frame_base + f, mod_base, h,
-                                    n, pix);
+                const uint32_t valid = valid_features(sb, &tile[ir][ic], win);
+                if (valid) {
+                    float E, dx, dy;
+                    uint32_t npix;
+                    sum_features(sb, &tile[ir][ic], valid, E, dx, dy, npix);
+                    if (E != 0.0f)
+                        emit = make_hit(p, hhit, E, dx, dy, npix, r, c, frame_base + f, mod_base,
+                                        h, n, pix);
+                }
             }
             emit_hits(p, out, emit, h, n, pix, lane);
         }
@@ -313,13 +334,19 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// Candidates per band tile (a larger count tests every own pixel).
+constexpr uint32_t kMbCap = 3072;
+
 // Shared memory of the band kernel for bands of rb rows: the s-tile of
 // rb + 3 rows (one above, two below) at the given pitch, both histograms
-// (plus a spare bin), the candidate list, the negated common mode of every
-// (tile row, unit column), the stacked row terms and the signal nibbles.
+// (plus a spare bin), the candidate list and the list of those with a valid
+// feature, the negated common mode of every (tile row, unit column), the
+// stacked row terms, the candidate bitmap of the own rows and the signal
+// nibbles.
 size_t band_smem(const ChainParams& p, uint32_t rb, uint32_t pitch) {
     const size_t nr = rb + 3;
-    return 4 * (nr * pitch + 2 * (size_t)p.hist_bins + 4 + kSeedCap + nr * p.units_per_row + nr) +
+    return 4 * (nr * pitch + 2 * (size_t)p.hist_bins + 4 + 2 * kMbCap + nr * p.units_per_row +
+                nr + (size_t)(rb + 1) * ((pitch + 31) / 32)) +
            nr * (pitch / 4);
 }
 
@@ -334,17 +361,23 @@ __global__ void __launch_bounds__(kBandThreads, 2)
                         BandConfig bc, unsigned long long n_tiles) {
     extern __shared__ __align__(16) uint32_t msm[];
     __shared__ MatchedBank sb;
-    __shared__ uint32_t s_nc;
+    __shared__ uint32_t s_nc, s_nv;
     const uint32_t P = bc.pitch, NQ = P / 4, NR = bc.rb + 3;
     float* stile = reinterpret_cast<float*>(msm);  // NR x P; real column c at 4 + c
     uint32_t* hpix = msm + NR * P;                 // hist_bins + spare
     uint32_t* hhit = hpix + p.hist_bins + 4;       // hist_bins
-    uint32_t* list = hhit + p.hist_bins;           // kSeedCap
-    float* cmt = reinterpret_cast<float*>(list + kSeedCap);  // NR x units_per_row
+    uint32_t* list = hhit + p.hist_bins;           // kMbCap: row << 16 | column
+    uint32_t* vlist = list + kMbCap;               // kMbCap: list index | valid << 24
+    float* cmt = reinterpret_cast<float*>(vlist + kMbCap);  // NR x units_per_row
     float* crt = cmt + NR * p.units_per_row;                  // NR row terms
+    // candidate bitmap: bit x of row rl (words of WPR per row, rows 1 ..
+    // rows_here used) marks s-tile column x of own row rl as a pixel whose
+    // window holds signal; zero between tiles
+    const uint32_t WPR = (P + 31) / 32;
+    uint32_t* cbits = reinterpret_cast<uint32_t*>(crt + NR);  // (rb + 1) x WPR
     // nibble q of a row: signal bits of s-tile columns 4q .. 4q + 3 (real
     // columns 4q - 4 .. 4q - 1); the first and last nibble stay 0
-    uint8_t* nib = reinterpret_cast<uint8_t*>(crt + NR);
+    uint8_t* nib = reinterpret_cast<uint8_t*>(cbits + (bc.rb + 1) * WPR);
 
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31;
@@ -361,6 +394,7 @@ __global__ void __launch_bounds__(kBandThreads, 2)
 
     for (uint32_t i = tid; i < NR * P; i += nthr) stile[i] = 0.0f;
     for (uint32_t i = tid; i < NR * NQ; i += nthr) nib[i] = 0;
+    for (uint32_t i = tid; i < (bc.rb + 1) * WPR; i += nthr) cbits[i] = 0;
     for (uint32_t i = tid; i < 2 * p.hist_bins + 4; i += nthr) hpix[i] = 0;
     {
         const uint32_t* src = reinterpret_cast<const uint32_t*>(bank);
@@ -418,7 +452,7 @@ __global__ void __launch_bounds__(kBandThreads, 2)
                 ncc[i] = active ? -cmf[(size_t)p.n_modules * p.rows + (size_t)m * p.cols + col + i]
                                 : 0.0f;
         }
-        if (tid == 0) s_nc = 0;
+        if (tid == 0) s_nc = s_nv = 0;
         __syncthreads();
 
         // 1. zeroed signal and its nibbles of rows r0-1 .. r0+rows_here+1;
@@ -492,6 +526,18 @@ __global__ void __launch_bounds__(kBandThreads, 2)
                     }
                     *reinterpret_cast<float4*>(srow) = make_float4(sv[0], sv[1], sv[2], sv[3]);
                     *nq = (uint8_t)bits;
+                    if (bits) {
+                        // signal at row rl, s-tile column x lies in the
+                        // windows of own rows rl-2 .. rl+1, columns x-2 ..
+                        // x+2: an 8-bit run from column col + 2
+                        const uint32_t run = bits | bits << 1 | bits << 2 | bits << 3 | bits << 4;
+                        const uint32_t x0 = (uint32_t)col + 2, w = x0 >> 5, sh = x0 & 31;
+                        const uint32_t lo = run << sh, hi = sh > 24 ? run >> (32 - sh) : 0u;
+                        for (int rr = max(1, rl - 2); rr <= min(rows_here, rl + 1); rr++) {
+                            atomicOr(&cbits[rr * WPR + w], lo);
+                            if (hi) atomicOr(&cbits[rr * WPR + w + 1], hi);
+                        }
+                    }
                     if (own && out.corrected) {
                         const uint32_t off = (uint32_t)r * p.cols + (uint32_t)col;
                         float* dst = out.corrected + (size_t)f * p.frame_px + mod_base + off;
@@ -504,38 +550,27 @@ __global__ void __launch_bounds__(kBandThreads, 2)
         if (t + gridDim.x < n_tiles && tid < ncmt) cmv = tile_cm(t + gridDim.x, tid);
         __syncthreads();
 
-        // 2. pixels whose window holds signal: each thread walks a run of
-        //    own rows of its chunk; g holds the nibbles q-1 .. q+1 of a row
-        //    (s-tile columns col .. col + 11), and pixel col + i's window
-        //    columns are its bits i + 2 .. i + 6
-        uint64_t cmask = 0;  // bit 4 k + i: row a + k, pixel col + i
-        const int seg = (rows_here + (int)TY - 1) / (int)TY;
-        const int a = 1 + (int)ty * seg;
-        const int b = min(rows_here, a + seg - 1);
-        if (active && a <= b) {
-            const uint8_t* nb = nib + tx;
-            auto g_of = [&](int rl) -> uint32_t {
-                const uint8_t* g = nb + rl * NQ;
-                return (uint32_t)g[0] | (uint32_t)g[1] << 4 | (uint32_t)g[2] << 8;
-            };
-            uint32_t g0 = g_of(a - 1), g1 = g_of(a), g2 = g_of(a + 1);
-            for (int rl = a; rl <= b; rl++) {
-                const uint32_t g3 = g_of(rl + 2);
-                const uint32_t o = (g0 | g1 | g2 | g3) >> 2;
-                const uint32_t c4 = (uint32_t)((o & 0x1Fu) != 0) | (uint32_t)((o & 0x3Eu) != 0) << 1 |
-                                    (uint32_t)((o & 0x7Cu) != 0) << 2 |
-                                    (uint32_t)((o & 0xF8u) != 0) << 3;
-                cmask |= (uint64_t)c4 << (4 * (rl - a));
-                g0 = g1;
-                g1 = g2;
-                g2 = g3;
+        // 2. the marked pixels into a list (a warp scan and one shared
+        //    atomic per warp reserve each thread's slots; list order is
+        //    free), clearing the bitmap for the next tile
+        const uint32_t n_words = (uint32_t)rows_here * WPR;
+        for (uint32_t base = 0; base < n_words; base += nthr) {
+            const uint32_t q = base + tid;
+            uint32_t word = 0;
+            int rl = 0, x0 = 0;
+            if (q < n_words) {
+                rl = 1 + (int)(q / WPR);
+                x0 = 32 * (int)(q % WPR);
+                uint32_t* cw = cbits + rl * WPR + (q % WPR);
+                word = *cw;
+                *cw = 0;
+                // keep s-tile columns 4 .. C + 3 (real columns 0 .. C - 1)
+                if (x0 < 4) word &= 0xFFFFFFFFu << (4 - x0);
+                const int xe = C + 4 - x0;
+                if (xe < 32) word &= xe > 0 ? 0xFFFFFFFFu >> (32 - xe) : 0u;
             }
-        }
-        // compaction: a warp scan and one shared atomic per warp (the last
-        // warp of the block may be partial)
-        {
             const unsigned wm = __activemask();
-            const uint32_t cnt = (uint32_t)__popcll(cmask);
+            const uint32_t cnt = (uint32_t)__popc(word);
             uint32_t incl = cnt;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -544,57 +579,113 @@ __global__ void __launch_bounds__(kBandThreads, 2)
             }
             const int wl = 31 - __clz((int)wm);
             const uint32_t tot = __shfl_sync(wm, incl, wl);
-            uint32_t base = 0;
-            if (lane == wl && tot) base = atomicAdd(&s_nc, tot);
-            base = __shfl_sync(wm, base, wl);
-            uint32_t at = base + incl - cnt;
-            while (cmask && at < kSeedCap) {
-                const int bit = __ffsll((long long)cmask) - 1;
-                cmask &= cmask - 1;
-                list[at++] = ((uint32_t)(a + bit / 4) << 16) | (uint32_t)(col + bit % 4);
+            uint32_t at0 = 0;
+            if (lane == wl && tot) at0 = atomicAdd(&s_nc, tot);
+            at0 = __shfl_sync(wm, at0, wl);
+            uint32_t at = at0 + incl - cnt;
+            while (word && at < kMbCap) {
+                const int bit = __ffs(word) - 1;
+                word &= word - 1;
+                list[at++] = ((uint32_t)rl << 16) | (uint32_t)(x0 + bit - 4);
             }
         }
         __syncthreads();
 
         // 3. the bank at the listed pixels (every own pixel if the list
-        //    overflowed)
+        //    overflowed): first the valid features of each, then, for the
+        //    few with some valid feature (a second list), the sums and the
+        //    hit, so that the sums run with every lane on such a pixel
         const uint32_t n_list = s_nc;
-        const bool scan = n_list > kSeedCap;
+        const bool scan = n_list > kMbCap;
         const uint32_t n_work = scan ? (uint32_t)rows_here * (uint32_t)C : n_list;
-        for (uint32_t base = 0; base < n_work; base += nthr) {
-            const uint32_t j = base + tid;
-            bool emit = false;
-            pd_hit h;
-            uint32_t n = 0, pix = 0;
-            if (j < n_work) {
-                int rl, c;
-                if (scan) {
-                    rl = 1 + (int)(j / (uint32_t)C);
-                    c = (int)(j % (uint32_t)C);
-                } else {
-                    const uint32_t e = list[j];
-                    rl = (int)(e >> 16);
-                    c = (int)(e & 0xFFFFu);
-                }
-                // window rows rl-1 .. rl+2, columns c-2 .. c+2: bits
-                // 2 + c % 4 .. 6 + c % 4 of nibbles c / 4 .. c / 4 + 2
-                const uint8_t* nw = nib + (rl - 1) * NQ + c / 4;
-                const int sh = 2 + (c & 3);
-                uint32_t win = 0;
-#pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const uint8_t* g = nw + i * NQ;
-                    const uint32_t gr = (uint32_t)g[0] | (uint32_t)g[1] << 4 | (uint32_t)g[2] << 8;
-                    win |= ((gr >> sh) & 0x1Fu) << (5 * i);
-                }
-                float E, dx, dy;
-                uint32_t npix;
-                if (win && evaluate_bank(sb, stile + (rl - 1) * P + c + 2, win, E, dx, dy, npix) &&
-                    E != 0.0f)
-                    emit = make_hit(p, hhit, E, dx, dy, npix, r0 - 1 + rl, c, frame_base + f,
-                                    mod_base, h, n, pix);
+        // (row, column) of work item j, and its window mask: rows rl-1 ..
+        // rl+2, columns c-2 .. c+2 are bits 2 + c % 4 .. 6 + c % 4 of
+        // nibbles c / 4 .. c / 4 + 2
+        auto item_at = [&](uint32_t j, int& rl, int& c) {
+            if (scan) {
+                rl = 1 + (int)(j / (uint32_t)C);
+                c = (int)(j % (uint32_t)C);
+            } else {
+                const uint32_t e = list[j];
+                rl = (int)(e >> 16);
+                c = (int)(e & 0xFFFFu);
             }
-            emit_hits(p, out, emit, h, n, pix, lane);
+        };
+        auto window = [&](int rl, int c) -> uint32_t {
+            const uint8_t* nw = nib + (rl - 1) * NQ + c / 4;
+            const int sh = 2 + (c & 3);
+            uint32_t win = 0;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const uint8_t* g = nw + i * NQ;
+                const uint32_t gr = (uint32_t)g[0] | (uint32_t)g[1] << 4 | (uint32_t)g[2] << 8;
+                win |= ((gr >> sh) & 0x1Fu) << (5 * i);
+            }
+            return win;
+        };
+        if (!scan) {
+            for (uint32_t base = 0; base < n_work; base += nthr) {
+                const uint32_t j = base + tid;
+                uint32_t valid = 0;
+                if (j < n_work) {
+                    int rl, c;
+                    item_at(j, rl, c);
+                    const uint32_t win = window(rl, c);
+                    if (win) valid = valid_features(sb, stile + (rl - 1) * P + c + 2, win);
+                }
+                const unsigned wm = __activemask();
+                const uint32_t bal = __ballot_sync(wm, valid != 0);
+                if (bal) {
+                    const int lead = __ffs(bal) - 1;
+                    uint32_t at0 = 0;
+                    if (lane == lead) at0 = atomicAdd(&s_nv, (uint32_t)__popc(bal));
+                    at0 = __shfl_sync(wm, at0, lead);
+                    if (valid) vlist[at0 + __popc(bal & ((1u << lane) - 1u))] = j | valid << 24;
+                }
+            }
+            __syncthreads();
+            const uint32_t n_valid = s_nv;
+            for (uint32_t base = 0; base < n_valid; base += nthr) {
+                const uint32_t k = base + tid;
+                bool emit = false;
+                pd_hit h;
+                uint32_t n = 0, pix = 0;
+                if (k < n_valid) {
+                    const uint32_t e = vlist[k];
+                    int rl, c;
+                    item_at(e & 0xFFFFFFu, rl, c);
+                    float E, dx, dy;
+                    uint32_t npix;
+                    sum_features(sb, stile + (rl - 1) * P + c + 2, e >> 24, E, dx, dy, npix);
+                    if (E != 0.0f)
+                        emit = make_hit(p, hhit, E, dx, dy, npix, r0 - 1 + rl, c, frame_base + f,
+                                        mod_base, h, n, pix);
+                }
+                emit_hits(p, out, emit, h, n, pix, lane, __activemask());
+            }
+        } else {
+            for (uint32_t base = 0; base < n_work; base += nthr) {
+                const uint32_t j = base + tid;
+                bool emit = false;
+                pd_hit h;
+                uint32_t n = 0, pix = 0;
+                if (j < n_work) {
+                    int rl, c;
+                    item_at(j, rl, c);
+                    const uint32_t win = window(rl, c);
+                    const float* w = stile + (rl - 1) * P + c + 2;
+                    const uint32_t valid = win ? valid_features(sb, w, win) : 0u;
+                    if (valid) {
+                        float E, dx, dy;
+                        uint32_t npix;
+                        sum_features(sb, w, valid, E, dx, dy, npix);
+                        if (E != 0.0f)
+                            emit = make_hit(p, hhit, E, dx, dy, npix, r0 - 1 + rl, c,
+                                            frame_base + f, mod_base, h, n, pix);
+                    }
+                }
+                emit_hits(p, out, emit, h, n, pix, lane, __activemask());
+            }
         }
         __syncthreads();
     }
@@ -602,6 +693,18 @@ __global__ void __launch_bounds__(kBandThreads, 2)
         if (hpix[b]) atomicAdd(&p.hist_pix[b], (unsigned long long)hpix[b]);
         if (hhit[b]) atomicAdd(&p.hist_hit[b], (unsigned long long)hhit[b]);
     }
+}
+
+// Valid features of every window mask of an all-binary bank (no tap is
+// read: the tests are mask tests and popcounts).
+__global__ void vtab_kernel(const MatchedBank* __restrict__ bank, uint8_t* __restrict__ vtab) {
+    const uint32_t win = blockIdx.x * blockDim.x + threadIdx.x;
+    if (win >= (1u << 20)) return;
+    uint32_t valid = 0;
+    for (uint32_t ft = 0; ft < bank->n_features; ft++)
+        if ((win & bank->m0[ft]) == 0 && (float)__popc(win & bank->m1[ft]) >= bank->nmin[ft])
+            valid |= 1u << ft;
+    vtab[win] = (uint8_t)valid;
 }
 
 // Nonzero taps of one 4 x 5 filter, row-major, appended to list.
@@ -653,12 +756,22 @@ bool compile_bank(const pd_filter_bank& b, MatchedBank* out) {
         compile_taps(b.f1_dx[f], mb.tx, &nx);
         compile_taps(b.f1_dy[f], mb.ty, &ny);
     }
+    mb.all_binary = 1;
+    for (uint32_t f = 0; f < b.n_features; f++)
+        if (!mb.f1_unit[f] || !mb.f0_pos[f]) mb.all_binary = 0;
+    mb.vtab = nullptr;
     mb.off1[b.n_features] = (uint16_t)n1;
     mb.off0[b.n_features] = (uint16_t)n0;
     mb.offx[b.n_features] = (uint16_t)nx;
     mb.offy[b.n_features] = (uint16_t)ny;
     *out = mb;
     return true;
+}
+
+cudaError_t build_vtab(const MatchedBank* bank_dev, uint8_t* vtab) {
+    vtab_kernel<<<(1u << 20) / 256, 256>>>(bank_dev, vtab);
+    cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : cudaDeviceSynchronize();
 }
 
 // Band form of the matched stencil: single gain, raw - pedestal before the
@@ -669,8 +782,6 @@ static bool matched_band_config(const ChainParams& p, BandConfig* out) {
     BandConfig bc = make_band_config(p);
     if (!bc.ok || bc.vec != 4) return false;
     uint32_t rb = std::min<uint32_t>(std::max<uint32_t>(4, 12288 / p.cols), p.rows);
-    // a thread's run of rows (4 pixels each) fits its 64-bit candidate mask
-    while (rb > 1 && ((rb + bc.ty - 1) / bc.ty) * 4 > 64) rb--;
     while (rb > 1 && band_smem(p, rb, bc.pitch) > 100 * 1024) rb--;
     if (band_smem(p, rb, bc.pitch) > 100 * 1024) return false;
     bc.rb = rb;

@@ -29,8 +29,22 @@ def random_bank(seed, n_features=6):
     return dict(f0=f0, f1=f1, f1_dx=fdx, f1_dy=fdy, f1_nmin=nmin)
 
 
+def binary_bank(seed, n_features=7):
+    """Footprints of ones and positive rings (the table path: validity is a
+    function of the window mask), thresholds fractional, never or always met."""
+    rng = np.random.default_rng(seed)
+    shape = (n_features, 4, 5)
+    f1 = np.where(rng.random(shape) < 0.3, 1.0, 0.0)
+    f0 = np.where((f1 == 0) & (rng.random(shape) < 0.3), rng.choice([0.3, 1.0, 2.0], shape), 0.0)
+    fdx = np.where(f1 != 0, rng.uniform(-2, 2, shape), 0.0)
+    fdy = np.where(f1 != 0, rng.uniform(-2, 2, shape), 0.0)
+    nmin = np.resize(np.array([1.0, -1.0, 0.0, 2.5, 1e9, 3.0, 2.0]), n_features)
+    return dict(f0=f0, f1=f1, f1_dx=fdx, f1_dy=fdy, f1_nmin=nmin)
+
+
 BANKS = {"example": filters.example_bank(), "random1": random_bank(1),
-         "random2_3f": random_bank(2, 3), "random3_8f": random_bank(3, 8)}
+         "random2_3f": random_bank(2, 3), "random3_8f": random_bank(3, 8),
+         "binary4_7f": binary_bank(4)}
 
 WORKLOADS = {
     "asic_rows_x8": (synth.asic_352x384(cloud_sigma=0.35), 8),
