@@ -222,8 +222,8 @@ void free_ctx(pd_ctx* c) {
 
 // The one-kernel chain replaces the kernel pair.
 bool fused_on(const pd_ctx* c) { return c->use_fused && !c->two_pass && !c->matched; }
-// (use_fused, use_band, use_cm_big and use_cm_rows are off for multi-gain
-// contexts: those kernels read single-gain words)
+// (use_fused and use_cm_rows are off for multi-gain contexts: those
+// kernels read single-gain words)
 
 // The charge-summing launch of a context (after its common mode).
 cudaError_t launch_stencil_for(const pd_ctx* c, const uint16_t* fr, uint32_t nf,
@@ -231,9 +231,9 @@ cudaError_t launch_stencil_for(const pd_ctx* c, const uint16_t* fr, uint32_t nf,
     const pd::MultiGain* mg = c->multigain ? &c->mg : nullptr;
     if (c->matched)
         return pd::launch_matched(c->params, c->d_bank, fr, nf, frame_base, co, s, mg);
-    if (mg) return pd::launch_stencil(c->params, fr, nf, frame_base, co, s, mg);
-    return c->use_band ? pd::launch_stencil_band(c->params, c->band_cfg, fr, nf, frame_base, co, s)
-                       : pd::launch_stencil(c->params, fr, nf, frame_base, co, s);
+    return c->use_band
+               ? pd::launch_stencil_band(c->params, c->band_cfg, fr, nf, frame_base, co, s, mg)
+               : pd::launch_stencil(c->params, fr, nf, frame_base, co, s, mg);
 }
 
 // The common-mode launch(es) of a context for nf frames into cm.
@@ -241,7 +241,10 @@ cudaError_t launch_cm(const pd_ctx* c, const uint16_t* fr, uint32_t nf, float* c
                       cudaStream_t s) {
     if (pd::cm_kind(c->params) == PD_CM_MEAN || pd::cm_kind(c->params) == PD_CM_MEAN_STACKED)
         return pd::launch_cm_mean(c->params, fr, nf, cm, s);
-    if (c->multigain) return pd::launch_cm_select(c->params, fr, nf, cm, s, &c->mg);
+    if (c->multigain)
+        return c->use_cm_big ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, cm, s,
+                                                 ~c->mg.vmask & 0xFFFFu)
+                             : pd::launch_cm_select(c->params, fr, nf, cm, s, &c->mg);
     return c->use_cm_big    ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, cm, s)
            : c->use_cm_rows ? pd::launch_cm_rows(c->params, fr, nf, cm, s)
                             : pd::launch_cm_select(c->params, fr, nf, cm, s);
@@ -561,7 +564,11 @@ int create_impl(const pd_geometry* geometry, uint32_t n_gains, uint32_t gain_shi
         c->multigain = true;
         c->mg = pd::MultiGain{n_gains, gain_shift, (1u << gain_shift) - 1u, c->d_mg_ped,
                               c->d_mg_ig};
-        c->use_cm_big = c->use_cm_rows = c->use_band = c->use_fused = false;
+        // the bank median and the band stencil decode the stages (the
+        // band stencil with four-pixel chunks only); the row-unit median
+        // and the one-kernel chain read single-gain words
+        c->use_cm_rows = c->use_fused = false;
+        c->use_band = c->use_band && c->band_cfg.vec == 4;
     }
     *out = c;
     return PD_OK;

@@ -58,10 +58,12 @@ struct CmBigShared {
 
 // Common mode of unit `item` (= frame * units_per_frame + unit) into
 // cm_out[item]; cm_smem: cm_big_smem_bytes(p) of dynamic shared memory.
-template <int VEC>
+// MG: auto-ranging words; a word with a bit of stage_mask set is not in
+// stage 0 and stays out of the set (a stage-0 word is its own ADC value).
+template <int VEC, bool MG = false>
 __device__ void cm_big_unit(const ChainParams& p, const uint16_t* __restrict__ raw,
                             float* __restrict__ cm_out, const CmBigConfig& cfg, uint32_t item,
-                            uint32_t* cm_smem, CmBigShared& sh) {
+                            uint32_t* cm_smem, CmBigShared& sh, uint32_t stage_mask = 0) {
     uint32_t* hist = cm_smem;                            // kCmBins + spare + pad
     float* cand = reinterpret_cast<float*>(hist + kCmBins + 4);  // kCandCap
     uint32_t* codes = reinterpret_cast<uint32_t*>(cand + kCandCap);  // VEC=2: pairs
@@ -131,12 +133,17 @@ __device__ void cm_big_unit(const ChainParams& p, const uint16_t* __restrict__ r
                 for (int j = 0; j < U; j++) pp[j] = prow[j * stride];
 #pragma unroll
                 for (int j = 0; j < U; j++) {
-                    const float2 d = __fadd2_rn(raw_pair(cptr[j * cstride]), pp[j]);
+                    const uint32_t x = cptr[j * cstride];
+                    const float2 d = __fadd2_rn(raw_pair(x), pp[j]);
                     const float2 u = __ffma2_rd(d, eight, mw);
-                    const int b0 = min(max(__float_as_int(u.x), (int)kMagicBits),
-                                       (int)(kMagicBits + kCmBins));
-                    const int b1 = min(max(__float_as_int(u.y), (int)kMagicBits),
-                                       (int)(kMagicBits + kCmBins));
+                    int b0 = min(max(__float_as_int(u.x), (int)kMagicBits),
+                                 (int)(kMagicBits + kCmBins));
+                    int b1 = min(max(__float_as_int(u.y), (int)kMagicBits),
+                                 (int)(kMagicBits + kCmBins));
+                    if (MG) {
+                        if (x & stage_mask) b0 = (int)(kMagicBits + kCmBins);
+                        if ((x >> 16) & stage_mask) b1 = (int)(kMagicBits + kCmBins);
+                    }
                     atomicAdd(&hist[(uint32_t)b0 - kMagicBits], 1u);
                     atomicAdd(&hist[(uint32_t)b1 - kMagicBits], 1u);
                     cptr[j * cstride] = __byte_perm((uint32_t)b0, (uint32_t)b1, 0x5410u);
@@ -145,12 +152,17 @@ __device__ void cm_big_unit(const ChainParams& p, const uint16_t* __restrict__ r
                 cptr += U * cstride;
             }
             for (; r < p.unit_rows; r += TY) {
-                const float2 d = __fadd2_rn(raw_pair(*cptr), *prow);
+                const uint32_t x = *cptr;
+                const float2 d = __fadd2_rn(raw_pair(x), *prow);
                 const float2 u = __ffma2_rd(d, eight, mw);
-                const int b0 = min(max(__float_as_int(u.x), (int)kMagicBits),
-                                   (int)(kMagicBits + kCmBins));
-                const int b1 = min(max(__float_as_int(u.y), (int)kMagicBits),
-                                   (int)(kMagicBits + kCmBins));
+                int b0 = min(max(__float_as_int(u.x), (int)kMagicBits),
+                             (int)(kMagicBits + kCmBins));
+                int b1 = min(max(__float_as_int(u.y), (int)kMagicBits),
+                             (int)(kMagicBits + kCmBins));
+                if (MG) {
+                    if (x & stage_mask) b0 = (int)(kMagicBits + kCmBins);
+                    if ((x >> 16) & stage_mask) b1 = (int)(kMagicBits + kCmBins);
+                }
                 atomicAdd(&hist[(uint32_t)b0 - kMagicBits], 1u);
                 atomicAdd(&hist[(uint32_t)b1 - kMagicBits], 1u);
                 *cptr = __byte_perm((uint32_t)b0, (uint32_t)b1, 0x5410u);
@@ -160,9 +172,11 @@ __device__ void cm_big_unit(const ChainParams& p, const uint16_t* __restrict__ r
         } else {
             uint32_t off = (r0 + ty) * p.cols + c0 + tx;
             for (uint32_t r = ty; r < p.unit_rows; r += TY, off += TY * p.cols) {
-                const float d = __fadd_rn(__uint2float_rn(fr[off]), npm[off]);
+                const uint32_t w = fr[off];
+                const float d = __fadd_rn(__uint2float_rn(w), npm[off]);
                 uint32_t k = cm_code(d, cfg.magic_w);
                 k = min(k, kCmBins);
+                if (MG && (w & stage_mask)) k = kCmBins;
                 atomicAdd(&hist[k], 1u);
                 reinterpret_cast<uint16_t*>(codes)[r * TX + tx] = (uint16_t)k;
             }
@@ -188,7 +202,9 @@ __device__ void cm_big_unit(const ChainParams& p, const uint16_t* __restrict__ r
     // the key of pixel i of the unit (kSent when d >= cut)
     auto unit_key = [&](uint32_t i) -> uint32_t {
         const uint32_t off = (r0 + i / p.unit_cols) * p.cols + c0 + i % p.unit_cols;
-        const float d = __fadd_rn(__uint2float_rn(fr[off]), npm[off]);
+        const uint32_t w = fr[off];
+        if (MG && (w & stage_mask)) return kSent;
+        const float d = __fadd_rn(__uint2float_rn(w), npm[off]);
         return d < p.cm_cut ? order_key(d) : kSent;
     };
 
@@ -288,13 +304,13 @@ __device__ void cm_big_unit(const ChainParams& p, const uint16_t* __restrict__ r
     if (tid == 0) cm_out[item] = key_value(key);
 }
 
-template <int VEC>
+template <int VEC, bool MG>
 __global__ void __launch_bounds__(512, 2)
     cm_big_kernel(ChainParams p, const uint16_t* __restrict__ raw,
-                  float* __restrict__ cm_out, CmBigConfig cfg) {
+                  float* __restrict__ cm_out, CmBigConfig cfg, uint32_t stage_mask) {
     extern __shared__ __align__(16) uint32_t cm_smem[];
     __shared__ CmBigShared sh;
-    cm_big_unit<VEC>(p, raw, cm_out, cfg, blockIdx.x, cm_smem, sh);
+    cm_big_unit<VEC, MG>(p, raw, cm_out, cfg, blockIdx.x, cm_smem, sh, stage_mask);
 }
 
 // ---------------------------------------------------------------------------
@@ -539,11 +555,12 @@ struct BandShared {
 // the histograms to the context's at the end.  STACKED: the stacked mean
 // common mode, whose module-row and module-column terms follow the units'
 // values of each frame and are subtracted after the unit's.
-template <int VEC, bool STACKED = false>
+template <int VEC, bool STACKED = false, bool MG = false>
 __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restrict__ raw,
                                  uint32_t frame_base, const CallOut& out, const BandConfig& bc,
                                  unsigned long long first, unsigned long long n_tiles,
-                                 unsigned long long step, uint32_t* band_smem, BandShared& bsh) {
+                                 unsigned long long step, uint32_t* band_smem, BandShared& bsh,
+                                 const MultiGain& mg = MultiGain{}) {
     const uint32_t P = bc.pitch;                 // floats per s-tile row
     float* stile = reinterpret_cast<float*>(band_smem);          // (rb+2) * P
     uint32_t* hpix = band_smem + (bc.rb + 2) * P;               // hist_bins + spare
@@ -688,8 +705,31 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
                             c23 = __fadd2_rn(__fadd2_rn(c23, make_float2(ncr, ncr)),
                                              make_float2(ncc[VEC > 2 ? 2 : 0], ncc[VEC > 3 ? 3 : 0]));
                         }
-                        const float2 e01 = __fmul2_rn(c01, make_float2(gg[j].x, gg[j].y));
-                        const float2 e23 = __fmul2_rn(c23, make_float2(gg[j].z, gg[j].w));
+                        float2 e01 = __fmul2_rn(c01, make_float2(gg[j].x, gg[j].y));
+                        float2 e23 = __fmul2_rn(c23, make_float2(gg[j].z, gg[j].w));
+                        if (MG && ((rr[j].x | rr[j].y) & (~mg.vmask << 16 | (~mg.vmask & 0xFFFFu)))) {
+                            // words of a higher gain stage: that stage's pedestal
+                            // and gain, no common mode; beyond the maps, 0
+                            float ev[4] = {e01.x, e01.y, e23.x, e23.y};
+                            const uint32_t wv[4] = {rr[j].x & 0xFFFFu, rr[j].x >> 16,
+                                                    rr[j].y & 0xFFFFu, rr[j].y >> 16};
+                            const size_t px = mod_base + (size_t)r * p.cols + (size_t)col;
+#pragma unroll
+                            for (int i = 0; i < 4; i++) {
+                                const uint32_t st = wv[i] >> mg.shift;
+                                if (st == 0) continue;
+                                if (st >= mg.n_gains) {
+                                    ev[i] = 0.0f;
+                                    continue;
+                                }
+                                const size_t at = (size_t)st * p.frame_px + px + i;
+                                ev[i] = __fmul_rn(
+                                    __fsub_rn(__uint2float_rn(wv[i] & mg.vmask), mg.ped[at]),
+                                    mg.inv_gain[at]);
+                            }
+                            e01 = make_float2(ev[0], ev[1]);
+                            e23 = make_float2(ev[2], ev[3]);
+                        }
                         e[0] = e01.x;
                         e[1] = e01.y;
                         e[2] = e23.x;
@@ -852,15 +892,15 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
     }
 }
 
-template <int VEC, bool STACKED>
+template <int VEC, bool STACKED, bool MG = false>
 __global__ void __launch_bounds__(kBandThreads, 2)
     stencil_band_kernel(ChainParams p, const uint16_t* __restrict__ raw,
                         uint32_t frame_base, CallOut out, BandConfig bc,
-                        unsigned long long n_tiles) {
+                        unsigned long long n_tiles, MultiGain mg) {
     extern __shared__ __align__(16) uint32_t band_smem[];
     __shared__ BandShared bsh;
-    stencil_band_run<VEC, STACKED>(p, raw, frame_base, out, bc, blockIdx.x, n_tiles, gridDim.x,
-                                   band_smem, bsh);
+    stencil_band_run<VEC, STACKED, MG>(p, raw, frame_base, out, bc, blockIdx.x, n_tiles, gridDim.x,
+                                       band_smem, bsh, mg);
 }
 
 // ---------------------------------------------------------------------------
@@ -1052,28 +1092,26 @@ CmBigConfig make_cm_big_config(const ChainParams& p) {
 static int g_attr_dev_cm = -1, g_attr_dev_band = -1;
 
 cudaError_t launch_cm_big(const ChainParams& p, const CmBigConfig& cfg, const uint16_t* raw,
-                          uint32_t n_frames, float* cm, cudaStream_t stream) {
+                          uint32_t n_frames, float* cm, cudaStream_t stream,
+                          uint32_t stage_mask) {
     const unsigned long long items = (unsigned long long)n_frames * p.units_per_frame;
     if (items == 0) return cudaSuccess;
     int dev = 0;
     cudaGetDevice(&dev);
     if (g_attr_dev_cm != dev) {
-        cudaError_t e = cudaFuncSetAttribute(cm_big_kernel<2>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kCmBigMaxSmem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(cm_big_kernel<1>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kCmBigMaxSmem);
-        if (e != cudaSuccess) return e;
+        for (auto k : {cm_big_kernel<2, false>, cm_big_kernel<1, false>, cm_big_kernel<2, true>,
+                       cm_big_kernel<1, true>}) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kCmBigMaxSmem);
+            if (e != cudaSuccess) return e;
+        }
         g_attr_dev_cm = dev;
     }
     const size_t smem = cm_big_smem_bytes(p);
     const unsigned threads = cfg.tx * cfg.ty;
-    if (cfg.vec == 2)
-        cm_big_kernel<2><<<(unsigned)items, threads, smem, stream>>>(p, raw, cm, cfg);
-    else
-        cm_big_kernel<1><<<(unsigned)items, threads, smem, stream>>>(p, raw, cm, cfg);
+    auto k = cfg.vec == 2 ? (stage_mask ? cm_big_kernel<2, true> : cm_big_kernel<2, false>)
+                          : (stage_mask ? cm_big_kernel<1, true> : cm_big_kernel<1, false>);
+    k<<<(unsigned)items, threads, smem, stream>>>(p, raw, cm, cfg, stage_mask);
     return cudaGetLastError();
 }
 
@@ -1109,14 +1147,16 @@ size_t band_smem_bytes(const ChainParams& p, uint32_t rb, uint32_t pitch) {
 
 cudaError_t launch_stencil_band(const ChainParams& p, const BandConfig& bc, const uint16_t* raw,
                                 uint32_t n_frames, uint32_t frame_base, const CallOut& out,
-                                cudaStream_t stream) {
+                                cudaStream_t stream, const MultiGain* mg) {
     const unsigned long long n_tiles = (unsigned long long)n_frames * p.n_modules * bc.n_bands;
     if (n_tiles == 0) return cudaSuccess;
+    if (mg && bc.vec != 4) return cudaErrorInvalidValue;
     int dev = 0;
     cudaGetDevice(&dev);
     if (g_attr_dev_band != dev) {
         for (auto k : {stencil_band_kernel<4, false>, stencil_band_kernel<1, false>,
-                       stencil_band_kernel<4, true>, stencil_band_kernel<1, true>}) {
+                       stencil_band_kernel<4, true>, stencil_band_kernel<1, true>,
+                       stencil_band_kernel<4, false, true>}) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  200 * 1024);
             if (e != cudaSuccess) return e;
@@ -1130,18 +1170,13 @@ cudaError_t launch_stencil_band(const ChainParams& p, const BandConfig& bc, cons
     unsigned long long grid = (unsigned long long)device_sm_count() * per_sm;
     if (grid > n_tiles) grid = n_tiles;
     const bool st = cm_kind(p) == PD_CM_MEAN_STACKED;
-    if (bc.vec == 4 && st)
-        stencil_band_kernel<4, true><<<(unsigned)grid, threads, smem, stream>>>(
-            p, raw, frame_base, out, bc, n_tiles);
-    else if (bc.vec == 4)
-        stencil_band_kernel<4, false><<<(unsigned)grid, threads, smem, stream>>>(
-            p, raw, frame_base, out, bc, n_tiles);
-    else if (st)
-        stencil_band_kernel<1, true><<<(unsigned)grid, threads, smem, stream>>>(
-            p, raw, frame_base, out, bc, n_tiles);
-    else
-        stencil_band_kernel<1, false><<<(unsigned)grid, threads, smem, stream>>>(
-            p, raw, frame_base, out, bc, n_tiles);
+    const MultiGain m = mg ? *mg : MultiGain{};
+    auto k = mg              ? stencil_band_kernel<4, false, true>
+             : bc.vec == 4 && st ? stencil_band_kernel<4, true>
+             : bc.vec == 4       ? stencil_band_kernel<4, false>
+             : st                ? stencil_band_kernel<1, true>
+                                 : stencil_band_kernel<1, false>;
+    k<<<(unsigned)grid, threads, smem, stream>>>(p, raw, frame_base, out, bc, n_tiles, m);
     return cudaGetLastError();
 }
 

@@ -64,8 +64,11 @@ cudaError_t launch_batch(const BatchItem* items_dev, uint32_t n_items,
 CmBigConfig make_cm_big_config(const ChainParams& p);
 bool cm_big_supported(const ChainParams& p, const CmBigConfig& cfg);
 size_t cm_big_smem_bytes(const ChainParams& p);
+// stage_mask: 0 for single-gain words; for auto-ranging words the stage bits
+// (~value mask), whose pixels are not in stage 0 and stay out of the set.
 cudaError_t launch_cm_big(const ChainParams& p, const CmBigConfig& cfg, const uint16_t* raw,
-                          uint32_t n_frames, float* cm, cudaStream_t stream);
+                          uint32_t n_frames, float* cm, cudaStream_t stream,
+                          uint32_t stage_mask = 0);
 
 // Units of at most 512 pixels (one warp each), cut an integer in (-1e6, 1e6).
 float cm_rows_magic(const ChainParams& p);
@@ -75,9 +78,11 @@ cudaError_t launch_cm_rows(const ChainParams& p, const uint16_t* raw, uint32_t n
 
 BandConfig make_band_config(const ChainParams& p);
 size_t band_smem_bytes(const ChainParams& p, uint32_t rb, uint32_t pitch);
+// mg: auto-ranging words (four-pixel chunks and the median or no common
+// mode only), or NULL.
 cudaError_t launch_stencil_band(const ChainParams& p, const BandConfig& bc, const uint16_t* raw,
                                 uint32_t n_frames, uint32_t frame_base, const CallOut& out,
-                                cudaStream_t stream);
+                                cudaStream_t stream, const MultiGain* mg = nullptr);
 
 // Whole chain in one persistent kernel per (frame, module) for modules whose
 // common-mode units are full-height column banks (at most kFusedMaxUnits per

@@ -24,6 +24,12 @@ WORKLOADS = {
                                        unit_cols=15, occupancy=0.03), 3, 4, 13),
     "big_unit_256x256_3g": (synth.Detector(n_modules=1, rows=256, cols=256, unit_rows=256,
                                            unit_cols=256, occupancy=0.01), 2, 3, 14),
+    # banks of odd width (one pixel per load in the bank median), and units
+    # two columns wide (a four-pixel chunk of the band stencil meets two)
+    "odd_banks_64x198_3g": (synth.Detector(n_modules=2, rows=64, cols=198, unit_rows=64,
+                                           unit_cols=99, occupancy=0.02), 2, 3, 14),
+    "two_column_units_2g": (synth.Detector(n_modules=1, rows=24, cols=64, unit_rows=24,
+                                           unit_cols=2, occupancy=0.03), 3, 2, 15),
 }
 
 
@@ -73,6 +79,19 @@ def test_workloads_bit_exact(name, mode):
     ctx, out, ref = _run(det, n, n_gains, shift, ped, gain, raw, mode=m)
     assert ref.n_hits > 0
     _compare(ctx, out, ref, n)
+
+
+def test_bank_median_below_window_uses_whole_unit_select():
+    # stage-0 d about -400 ADU, below the bank median's window [cut - 512,
+    # cut) = [-312, 200): the whole-unit selection, which must skip the words
+    # of the other stages too
+    det = synth.cspad_2p2m(n_modules=2)
+    ped, gain, raw = _data(det, 2, 3, 14)
+    ped_ctx = ped.copy()
+    ped_ctx[0] += np.float32(400.0)
+    ctx, out, ref = _run(det, 2, 3, 14, ped_ctx, gain, raw)
+    assert float(ref.cm.max()) < -312.0
+    _compare(ctx, out, ref, 2)
 
 
 def test_with_matched_filters():
