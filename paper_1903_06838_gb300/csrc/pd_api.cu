@@ -771,8 +771,6 @@ int pd_set_tuning(pd_ctx* c, const pd_tuning* t) {
         const uint32_t rb = std::min(t->band_rows, c->params.rows);
         if (pd::band_smem_bytes(c->params, rb, c->band_cfg.pitch) > 200 * 1024)
             return fail(PD_EINVAL, "band too tall for shared memory");
-        if (((rb + 2 + c->band_cfg.ty - 1) / c->band_cfg.ty) * c->band_cfg.vec > 64)
-            return fail(PD_EINVAL, "band too tall for the per-thread candidate mask");
         c->band_cfg.rb = rb;
         c->band_cfg.n_bands = (c->params.rows + rb - 1) / rb;
     }

@@ -68,7 +68,6 @@ __device__ void cm_big_unit(const ChainParams& p, const uint16_t* __restrict__ r
     float* cand = reinterpret_cast<float*>(hist + kCmBins + 4);  // kCandCap
     uint32_t* codes = reinterpret_cast<uint32_t*>(cand + kCandCap);  // VEC=2: pairs
     uint32_t* gsum = sh.gsum;
-    uint32_t* swarp = sh.swarp;
     uint32_t &s_bin = sh.s_bin, &s_rank = sh.s_rank, &s_n = sh.s_n, &s_cand = sh.s_cand;
     uint32_t &s_prefix = sh.s_prefix, &s_rrank = sh.s_rrank;
 
@@ -568,6 +567,10 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
     uint32_t* list = hhit + p.hist_bins;                         // kSeedCap
     float* cmt = reinterpret_cast<float*>(list + kSeedCap);      // (rb+2) * upr
     float* crt = cmt + (bc.rb + 2) * p.units_per_row;            // (rb+2) row terms
+    // seed bitmap: bit c of word row rl marks own pixel (rl, c) above the
+    // seed threshold; rows 1 .. rows_here used, zero between tiles
+    const uint32_t WPR = (uint32_t)(p.cols + 31) / 32;
+    uint32_t* sbits = reinterpret_cast<uint32_t*>(crt + bc.rb + 2);  // (rb+1) x WPR
     uint32_t& s_list_n = bsh.s_list_n;
 
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
@@ -587,6 +590,7 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
     // zero the whole s-tile once (pad columns stay zero), and the histograms
     for (uint32_t i = tid; i < (bc.rb + 2) * P; i += nthr) stile[i] = 0.0f;
     for (uint32_t i = tid; i < 2 * p.hist_bins + 4; i += nthr) hpix[i] = 0;
+    for (uint32_t i = tid; i < (bc.rb + 1) * WPR; i += nthr) sbits[i] = 0;
     __syncthreads();
 
     // negated common mode of (tile row, unit column) entry i of tile tt;
@@ -644,12 +648,10 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
         // 1. zeroed signal of rows r0-1 .. r0+rows_here (halo rows included);
         //    loads of U rows are issued before any is used.  Halo rows
         //    are not histogrammed: their bins are clamped to the spare bin.
-        uint64_t cmask = 0;  // seed candidates of this thread: bit k*VEC + i
         if (active) {
             const int nrows = rows_here + 2;
-            int kk = 0;
             constexpr int U = PD_BAND_UNROLL;
-            for (int rl0 = (int)ty; rl0 < nrows; rl0 += U * (int)TY, kk += U) {
+            for (int rl0 = (int)ty; rl0 < nrows; rl0 += U * (int)TY) {
                 uint2 rr[U];
                 float4 pp[U], gg[U];
                 uint16_t r1[U];
@@ -771,18 +773,31 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
                         else
                             dst[0] = e[0];
                     }
-                    if (own) cmask |= (uint64_t)seeds << ((kk + j) * VEC);
+                    // (a chunk's pixels share one word: col % 4 == 0 when VEC == 4)
+                    if (own && seeds) atomicOr(&sbits[rl * WPR + (col >> 5)], seeds << (col & 31));
                 }
             }
         }
         // the next tile's common mode, in flight during compaction and seeds
         if (t + step < n_tiles && tid < ncmt) cmv = tile_cm((uint32_t)(t + step), tid);
 
-        // compaction of the candidates: a warp scan and one shared atomic
-        // per warp reserve each thread's slots (list order is free)
-        {
+        __syncthreads();
+
+        // compaction of the candidates: one bitmap word per thread, a warp
+        // scan and one shared atomic per warp reserve each thread's slots
+        // (list order is free); the words are cleared for the next tile
+        const uint32_t n_words = (uint32_t)rows_here * WPR;
+        for (uint32_t base = 0; base < n_words; base += nthr) {
+            const uint32_t q = base + tid;
+            uint32_t word = 0, rc = 0;  // rc: row << 16 | first column of the word
+            if (q < n_words) {
+                const uint32_t rl = 1 + q / WPR, w = q - (rl - 1) * WPR;
+                word = sbits[rl * WPR + w];
+                if (word) sbits[rl * WPR + w] = 0;
+                rc = rl << 16 | 32 * w;
+            }
             const unsigned wm = __activemask();
-            const uint32_t cnt = (uint32_t)__popcll(cmask);
+            const uint32_t cnt = (uint32_t)__popc(word);
             uint32_t incl = cnt;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -791,15 +806,14 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
             }
             const int wl = 31 - __clz((int)wm);
             const uint32_t tot = __shfl_sync(wm, incl, wl);
-            uint32_t base = 0;
-            if (lane == wl && tot) base = atomicAdd(&s_list_n, tot);
-            base = __shfl_sync(wm, base, wl);
-            uint32_t at = base + incl - cnt;
-            while (cmask && at < kSeedCap) {
-                const int b = __ffsll((long long)cmask) - 1;
-                cmask &= cmask - 1;
-                const int rl = (int)ty + (b / VEC) * (int)TY;
-                list[at++] = ((uint32_t)rl << 16) | (uint32_t)(col + b % VEC);
+            uint32_t at0 = 0;
+            if (lane == wl && tot) at0 = atomicAdd(&s_list_n, tot);
+            at0 = __shfl_sync(wm, at0, wl);
+            uint32_t at = at0 + incl - cnt;
+            while (word && at < kSeedCap) {
+                const int b = __ffs(word) - 1;
+                word &= word - 1;
+                list[at++] = rc + (uint32_t)b;
             }
         }
         __syncthreads();
@@ -1130,10 +1144,8 @@ BandConfig make_band_config(const ChainParams& p) {
     // about 12k pixels per band, at least 4 rows
     uint32_t rb = std::max<uint32_t>(4, 12288 / p.cols);
     rb = std::min<uint32_t>(rb, p.rows);
-    // keep the shared memory of one CTA under about 100 KB, and the rows a
-    // thread visits (times pixels per chunk) within its 64-bit candidate mask
+    // keep the shared memory of one CTA under about 100 KB
     while (rb > 1 && band_smem_bytes(p, rb, bc.pitch) > 100 * 1024) rb--;
-    while (rb > 1 && ((rb + 2 + bc.ty - 1) / bc.ty) * bc.vec > 64) rb--;
     bc.rb = rb;
     bc.n_bands = (p.rows + rb - 1) / rb;
     return bc;
@@ -1142,7 +1154,8 @@ BandConfig make_band_config(const ChainParams& p) {
 size_t band_smem_bytes(const ChainParams& p, uint32_t rb, uint32_t pitch) {
     return (size_t)(rb + 2) * pitch * 4 + (2 * (size_t)p.hist_bins + 4) * 4 +
            (size_t)kSeedCap * 4 + (size_t)(rb + 2) * p.units_per_row * 4 +
-           (size_t)(rb + 2) * 4;  // row terms of the stacked mean
+           (size_t)(rb + 2) * 4 +                           // row terms of the stacked mean
+           (size_t)(rb + 1) * ((p.cols + 31) / 32) * 4;     // seed bitmap
 }
 
 cudaError_t launch_stencil_band(const ChainParams& p, const BandConfig& bc, const uint16_t* raw,
