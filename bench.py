@@ -35,7 +35,9 @@ HIT_BYTES = 24
 # DRAM bytes (read + write) per frame of each kernel, from the ncu capture
 # summarised in profiles/cspad_2p2m_chain.md; set an entry to None when its
 # kernel changes until it is captured again.
-NCU_TRAFFIC_PER_FRAME = {"stencil": None, "common_mode": None, "fused_chain": None}
+NCU_TRAFFIC_PER_FRAME = {"stencil": (123.118336e6 + 6.723328e6) / 21,
+                         "common_mode": (105.737984e6 + 3.624704e6) / 21,
+                         "fused_chain": None}
 
 
 def parse():
