@@ -326,7 +326,10 @@ def test_full_size_cspad_batch_sampled():
                                     dict(chunk_frames=1, overlap=1, two_pass=1),
                                     dict(chunk_frames=3, overlap=0, two_pass=1),
                                     dict(chunk_frames=2, band_rows=4, overlap=1, two_pass=1),
-                                    dict(chunk_frames=5, band_rows=17, overlap=1, two_pass=1)])
+                                    dict(chunk_frames=5, band_rows=17, overlap=1, two_pass=1),
+                                    # 82 loaded rows over 5 row lanes: more than 64 seed
+                                    # candidates per thread, one CTA per SM
+                                    dict(chunk_frames=4, band_rows=80, overlap=0, two_pass=1)])
 def test_results_independent_of_tuning(tuning):
     """Chunking, band height, the two-stream overlap and the choice between
     the one-kernel chain and the kernel pair change only the launch schedule:
