@@ -261,8 +261,12 @@ int pd_process_noalloc(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frame
  * chain reads them) by the matched filters of `bank` (copied; host memory),
  * or restore the default with bank == NULL.  Synchronises the device; do
  * not call while work of this context is in flight.  The one-kernel chain
- * and the mixed batch launch are not used with a bank.  PD_EINVAL for a
- * feature count out of range or a non-finite value. */
+ * and the mixed batch launch are not used with a bank.  When every feature
+ * is binary (F1 taps 1 or 0, F0 taps positive or 0), the valid features
+ * depend on a pixel's 4 x 5 signal mask alone: the context then allocates
+ * a 2^20-byte device table (once; freed by pd_destroy) and fills it on the
+ * device before returning.  PD_EINVAL for a feature count out of range or a
+ * non-finite value, PD_ENOMEM when the table cannot be allocated. */
 int pd_set_filter_bank(pd_ctx* ctx, const pd_filter_bank* bank);
 
 /* pd_process_host — the same chain on host-resident frames.  Copies the
