@@ -318,7 +318,9 @@ def run_pd(args):
     maps_b = fpx * 4           # one FP32 map, read once per launch
     cmap_b = fpx * 4 * 2       # photon-count map, read and written once
     cm_b = nf * ctx.units_per_frame * 4
-    # algorithmic bytes of one launch of each kernel
+    # algorithmic bytes of one launch of each kernel: its frames' raw words and
+    # each map it reads once, the common-mode values, the hit records and the
+    # count map read and written once
     kernel_bytes = {
         "common_mode": raw_b + maps_b + cm_b,
         "stencil": raw_b + 2 * maps_b + cm_b + hits_b + cmap_b,
