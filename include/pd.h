@@ -57,7 +57,7 @@ extern "C" {
 #define PD_EOVERFLOW 4  /* more hits than hit_capacity (count still exact)  */
 #define PD_ETIMEDOUT 5  /* a bounded device-side or host-side wait gave up  */
 #define PD_ECUDA 6      /* a CUDA runtime call failed                       */
-#define PD_ENOTSUP 7    /* valid request this build does not support        */
+#define PD_ENOTSUP 7    /* valid request the library does not support       */
 #define PD_EBUSY 8      /* admission refused: no slot or memory budget free */
 
 /* ---- common-mode estimators (paper Fig. c and its text) --------------- */
