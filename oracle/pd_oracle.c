@@ -90,7 +90,9 @@
  * with a valid feature and E != 0 counts as a seed (hist_hit[bin(E)]); its
  * count is n = rint(E / photon_kev) as in 7., a hit iff n >= 1, with npix
  * the number of signal pixels under the nonzero taps of the first valid
- * feature's F1.
+ * feature's F1.  The model is pinned (correlation against a library routine,
+ * the alignment, hand-worked cloud shapes); the paper's own filter values are
+ * not in its text, so parity with the paper's bank is unpinned.
  *
  * Auto-ranging multi-gain (oracle_process_ext with n_gains > 0; the
  * caption of Fig. b notes that several darks and gains per pixel are
