@@ -29,8 +29,9 @@
 // 1, and Overflow == 0 a mask test for features whose F0 taps are all
 // positive (a sum of positive terms is positive, and of ones is exact);
 // other features, and the droplet and momenta of valid features, run over
-// the tap lists.  Hits are compacted with a warp ballot and one atomic per
-// warp.
+// the tap lists (a bank of binary features reads its valid features from the
+// table described below).  Hits are compacted with a warp ballot and one
+// atomic per warp.
 //
 // matched_band_kernel: the same per pixel on full-width bands of module rows
 // (single gain, raw - pedestal before the common mode), with the band
