@@ -466,6 +466,60 @@ def test_histogram_bins_and_clipping():
     assert list(r.hist_pix[[0, 4, 5, 8, 9]]) == [3, 1, 1, 1, 2]
 
 
+def _rn32(x: Fraction) -> Fraction:
+    """x rounded to the nearest binary32 value (ties to even), exactly."""
+    if x == 0:
+        return Fraction(0)
+    sign, a = (-1 if x < 0 else 1), abs(x)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    while a >= Fraction(2) ** (e + 1):
+        e += 1
+    while a < Fraction(2) ** e:
+        e -= 1
+    m = a / Fraction(2) ** (e - 23)  # in [2^23, 2^24)
+    q = math.floor(m)
+    r = m - q
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and q % 2):
+        q += 1
+    return sign * q * Fraction(2) ** (e - 23)
+
+
+# e values next to bin edges of 0.05 keV bins from -4 keV, with the bin the
+# fused form gives and the bin the division form would give
+NON_DYADIC = [(0.20000001788139343, 84, 83), (-0.9000000953674316, 62, 61),
+              (0.44999998807907104, 89, 88), (0.5499998927116394, 91, 90),
+              (-1.0000001192092896, 59, 60), (-0.9500001072883606, 60, 61)]
+
+
+def test_histogram_bins_non_dyadic_width():
+    """The summaries' bin with a width that is not dyadic (0.05 keV, lo = -4
+    keV): bin(v) = floor(fma(v, 1/w, -lo * (1/w))), 1/w and lo * (1/w) each
+    rounded to binary32 once and the fused product-sum rounded once.  Worked
+    in exact rationals here: w rounds to 0.05000000074505806, 1/w to 20
+    exactly and -lo/w to 80, so bin(v) = floor(RN(20 v + 80)).  At each value
+    below the division form floor(RN(RN(v - lo) / w)) gives the neighbouring
+    bin, so the pin tells the two readings apart."""
+    w = Fraction(float(np.float32(0.05)))
+    lo = Fraction(-4)
+    inv_w = _rn32(1 / w)
+    lo_s = _rn32(lo * inv_w)
+    assert inv_w == 20 and lo_s == -80
+    for v, fused, division in NON_DYADIC:
+        vf = Fraction(float(np.float32(v)))
+        assert math.floor(_rn32(vf * inv_w - lo_s)) == fused
+        assert math.floor(_rn32(_rn32(vf - lo) / w)) == division
+    C = len(NON_DYADIC)
+    g = _geom(n_modules=1, rows=1, cols=C, unit_rows=1, unit_cols=C, cm_mode=oracle.CM_NONE)
+    t = _thr(0.5, 100.0, 100.0, 1.0, hist_lo_kev=-4.0, hist_bin_kev=0.05, hist_bins=1296)
+    # raw 0, unit gain: e = -pedestal exactly
+    ped = np.array([-v for v, _, _ in NON_DYADIC], np.float32).reshape(1, 1, C)
+    r = oracle.process(g, t, ped, np.ones((1, 1, C), np.float32), np.zeros((1, 1, 1, C), np.uint16))
+    exp = np.zeros(1296, np.uint64)
+    for _, fused, _ in NON_DYADIC:
+        exp[fused] += 1
+    np.testing.assert_array_equal(r.hist_pix, exp)
+
+
 def test_split_calls_accumulate_like_one():
     det = SMALL["asic"].replace(seed=9)
     ped, gain = synth.maps(det)
