@@ -242,16 +242,22 @@ int pd_process(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frames,
  *
  * Its common-mode scratch is one fixed device array inside the library,
  * PD_NOALLOC_MAX_CM floats (4 MiB), present on every GPU that loads the
- * library until the process exits.  Limit: when out->cm is NULL,
- * n_frames * cm_values_per_frame must not exceed PD_NOALLOC_MAX_CM, else the
- * call returns PD_EINVAL (split the call, or pass out->cm, which is then
- * used instead).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress), so make that first call before any
- * stream capture.  The array is shared by all calls and keeps the last
- * call's values; nothing in it needs clearing (every value is written
- * before it is read), but calls whose work overlaps on the GPU (different
- * streams, no ordering between them) race on it: order them.  Runs on
- * `stream` alone.  Arguments, outputs and errors as pd_process. */
+ * library until the process exits.  Limit: when out->cm is NULL and the
+ * context runs the common-mode + stencil kernel pair, n_frames *
+ * cm_values_per_frame must not exceed PD_NOALLOC_MAX_CM, else the call
+ * returns PD_EINVAL (split the call, or pass out->cm, which is then used
+ * instead); the one-kernel chain (pd_tuning.two_pass = 0) uses no scratch
+ * and has no limit.  The array's device address is looked up by pd_create
+ * on the context's device; under CUDA's lazy module loading that lookup is
+ * what loads the module holding the array, so this entry point itself loads
+ * nothing on a context's device (should pd_create's lookup have failed, the
+ * first call here looks it up again: make that first call before any stream
+ * capture).  The context's device must be current (PD_EINVAL otherwise).
+ * The array is shared by all calls and keeps the last call's values;
+ * nothing in it needs clearing (every value is written before it is read),
+ * but calls whose work overlaps on the GPU (different streams, no ordering
+ * between them) race on it: order them.  Runs on `stream` alone.
+ * Arguments, outputs and errors as pd_process. */
 #define PD_NOALLOC_MAX_CM (1u << 20)
 int pd_process_noalloc(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frames,
                        uint32_t frame_base, const pd_outputs* out, void* stream);
@@ -306,12 +312,20 @@ void pd_destroy(pd_ctx* ctx);
  * or no common mode; columns a multiple of 4), 1 uses the common-mode + stencil kernel pair (the
  * default; pd_get_tuning reports 1 when the one-kernel form is not
  * available).
+ * kernels: 1 runs the lean pair where the context allows it (the default:
+ * the integer-coded bank median for units of 4096+ pixels whose pedestals
+ * keep d = raw - pedestal exact inside the common-mode window, and the lean
+ * band stencil for columns a multiple of 4, single-gain words, the median,
+ * no or the one-stage mean common mode, subtracted before gain); 2 runs the
+ * earlier kernel pair (pd_get_tuning reports 2 when the lean pair is not
+ * available).
  * Results never depend on tuning. */
 typedef struct {
     uint32_t chunk_frames;
     uint32_t band_rows;
     uint32_t overlap;
     uint32_t two_pass;
+    uint32_t kernels;
 } pd_tuning;
 
 int pd_get_tuning(const pd_ctx* ctx, pd_tuning* tuning);

@@ -18,6 +18,7 @@
 #include "pd.h"
 #include "pd_fast.cuh"
 #include "pd_internal.cuh"
+#include "pd_lean.cuh"
 
 namespace {
 
@@ -46,6 +47,14 @@ struct pd_ctx {
     pd::FusedConfig fused_cfg;
     bool use_cm_big = false, use_cm_rows = false, use_band = false;
     bool use_fused = false;     // the geometry allows the one-kernel chain
+    // the lean pair (pd_lean.cu): the integer-coded bank median and the
+    // lean band stencil, where the context allows them
+    bool use_bank = false, use_lean = false;
+    pd::CodeMap cmap{};
+    uint4* d_kmap = nullptr;
+    pd::LeanConfig lean_cfg{};
+    uint32_t kernels = 1;       // 1: the lean pair where available; 2: the earlier pair
+    uint32_t* d_err = nullptr;  // bit 0: a bounded wait for staged copies gave up
     uint32_t two_pass = 1;      // 1: common-mode and stencil kernels (measured
                                 // faster on GB300 so far); 0: the one-kernel chain
     bool multigain = false;     // auto-ranging words (pd_create_multigain)
@@ -198,6 +207,8 @@ void free_ctx(pd_ctx* c) {
     cudaFree(c->d_vtab);
     cudaFree(c->d_mg_ped);
     cudaFree(c->d_mg_ig);
+    cudaFree(c->d_kmap);
+    cudaFree(c->d_err);
     cudaFree(c->d_stage[0]);
     cudaFree(c->d_stage[1]);
     cudaFree(c->d_host_hits);
@@ -231,6 +242,8 @@ cudaError_t launch_stencil_for(const pd_ctx* c, const uint16_t* fr, uint32_t nf,
     const pd::MultiGain* mg = c->multigain ? &c->mg : nullptr;
     if (c->matched)
         return pd::launch_matched(c->params, c->d_bank, fr, nf, frame_base, co, s, mg);
+    if (c->use_lean && c->kernels == 1)
+        return pd::launch_stencil_lean(c->params, c->lean_cfg, fr, nf, frame_base, co, s);
     return c->use_band
                ? pd::launch_stencil_band(c->params, c->band_cfg, fr, nf, frame_base, co, s, mg)
                : pd::launch_stencil(c->params, fr, nf, frame_base, co, s, mg);
@@ -245,6 +258,8 @@ cudaError_t launch_cm(const pd_ctx* c, const uint16_t* fr, uint32_t nf, float* c
         return c->use_cm_big ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, cm, s,
                                                  ~c->mg.vmask & 0xFFFFu)
                              : pd::launch_cm_select(c->params, fr, nf, cm, s, &c->mg);
+    if (c->use_bank && c->kernels == 1)
+        return pd::launch_cm_bank(c->params, c->cm_cfg, c->cmap, fr, nf, cm, c->d_err, s);
     return c->use_cm_big    ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, cm, s)
            : c->use_cm_rows ? pd::launch_cm_rows(c->params, fr, nf, cm, s)
                             : pd::launch_cm_select(c->params, fr, nf, cm, s);
@@ -333,6 +348,10 @@ namespace pd {
 int internal_fail(int code, const char* why) { return fail(code, why ? why : "error"); }
 
 uint32_t internal_cm_per_frame(const pd_ctx* c) { return pd::cm_per_frame(c->params); }
+
+int internal_ctx_device(const pd_ctx* c) { return c->device; }
+
+bool internal_uses_cm_scratch(const pd_ctx* c) { return !fused_on(c); }
 
 int internal_check_process_args(const pd_ctx* c, const uint16_t* frames, uint32_t n_frames,
                                 const pd_outputs* out, const char** why) {
@@ -515,7 +534,8 @@ int create_impl(const pd_geometry* geometry, uint32_t n_gains, uint32_t gain_shi
         (e = cudaMalloc(&c->d_inv_gain, fpx * 4)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_count_map, fpx * 4)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_hist_pix, p.hist_bins * 8)) != cudaSuccess ||
-        (e = cudaMalloc(&c->d_hist_hit, p.hist_bins * 8)) != cudaSuccess) {
+        (e = cudaMalloc(&c->d_hist_hit, p.hist_bins * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_err, 4)) != cudaSuccess) {
         free_ctx(c);
         return fail(PD_ENOMEM, "device allocation failed in pd_create");
     }
@@ -524,7 +544,8 @@ int create_impl(const pd_geometry* geometry, uint32_t n_gains, uint32_t gain_shi
         (e = cudaMemcpy(c->d_inv_gain, inv.data(), fpx * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemset(c->d_count_map, 0, fpx * 4)) ||
         (e = cudaMemset(c->d_hist_pix, 0, p.hist_bins * 8)) ||
-        (e = cudaMemset(c->d_hist_hit, 0, p.hist_bins * 8))) {
+        (e = cudaMemset(c->d_hist_hit, 0, p.hist_bins * 8)) ||
+        (e = cudaMemset(c->d_err, 0, 4))) {
         free_ctx(c);
         return fail_cuda(e, "pd_create upload");
     }
@@ -569,7 +590,29 @@ int create_impl(const pd_geometry* geometry, uint32_t n_gains, uint32_t gain_shi
         // and the one-kernel chain read single-gain words
         c->use_cm_rows = c->use_fused = false;
         c->use_band = c->use_band && c->band_cfg.vec == 4;
+    } else if (!ag) {
+        // the lean pair: single-gain words, common mode before gain
+        c->lean_cfg = pd::make_lean_config(p);
+        c->use_lean = c->lean_cfg.ok &&
+                      (g.cm_mode == PD_CM_MEDIAN || g.cm_mode == PD_CM_NONE || g.cm_mode == PD_CM_MEAN);
+        std::vector<uint16_t> km;
+        pd::CodeMap cmap{};
+        if (c->use_cm_big && pd::build_code_map(p, pedestal_host, &km, &cmap) &&
+            pd::cm_bank_supported(p, cmap)) {
+            if ((e = cudaMalloc(&c->d_kmap, km.size() * 2)) != cudaSuccess) {
+                free_ctx(c);
+                return fail(PD_ENOMEM, "device allocation failed in pd_create");
+            }
+            if ((e = cudaMemcpy(c->d_kmap, km.data(), km.size() * 2, cudaMemcpyHostToDevice))) {
+                free_ctx(c);
+                return fail_cuda(e, "pd_create upload");
+            }
+            cmap.kmap = c->d_kmap;
+            c->cmap = cmap;
+            c->use_bank = true;
+        }
     }
+    pd::noalloc_prepare(c->device);
     *out = c;
     return PD_OK;
 }
@@ -708,6 +751,10 @@ int pd_get_summary(pd_ctx* c, uint32_t* count_map_host, uint64_t* hist_pix_host,
                                               cudaMemcpyDeviceToHost, s)))
         return fail_cuda(e, "histogram download");
     if ((e = cudaStreamSynchronize(s))) return fail_cuda(e, "summary synchronise");
+    uint32_t err = 0;
+    if ((e = cudaMemcpy(&err, c->d_err, 4, cudaMemcpyDeviceToHost)))
+        return fail_cuda(e, "error word download");
+    if (err) return fail(PD_ETIMEDOUT, "a bounded wait for staged raw copies gave up");
     return PD_OK;
 }
 
@@ -758,15 +805,25 @@ int pd_reset_summary(pd_ctx* c, void* stream) {
 int pd_get_tuning(const pd_ctx* c, pd_tuning* t) {
     if (!c || !t) return fail(PD_EINVAL, "NULL argument");
     t->chunk_frames = c->chunk_frames;
-    t->band_rows = c->use_band ? c->band_cfg.rb : 0;
+    const bool lean = c->use_lean && c->kernels == 1 && !c->matched;
+    t->band_rows = lean ? c->lean_cfg.rb : c->use_band ? c->band_cfg.rb : 0;
     t->overlap = c->overlap;
     t->two_pass = c->use_fused && !c->matched ? c->two_pass : 1;
+    t->kernels = c->use_lean || c->use_bank ? c->kernels : 2;
     return PD_OK;
 }
 
 int pd_set_tuning(pd_ctx* c, const pd_tuning* t) {
     if (!c || !t) return fail(PD_EINVAL, "NULL argument");
     if (t->chunk_frames) c->chunk_frames = t->chunk_frames;
+    if (t->kernels > 2) return fail(PD_EINVAL, "kernels is 0, 1 or 2");
+    if (t->kernels) c->kernels = t->kernels;
+    if (t->band_rows && c->use_lean) {
+        const pd::LeanConfig lc = pd::make_lean_config(c->params, t->band_rows);
+        if (!lc.ok || lc.rb != std::min(t->band_rows, c->params.rows))
+            return fail(PD_EINVAL, "band too tall for shared memory");
+        c->lean_cfg = lc;
+    }
     if (t->band_rows && c->use_band) {
         const uint32_t rb = std::min(t->band_rows, c->params.rows);
         if (pd::band_smem_bytes(c->params, rb, c->band_cfg.pitch) > 200 * 1024)
@@ -1183,21 +1240,32 @@ int pd_autotune(pd_ctx* c, const uint16_t* frames_dev, uint32_t n_frames, pd_tun
             const uint32_t cf = (uint32_t)std::max<size_t>(1, ((size_t)mb << 20) / fbytes);
             if (std::find(chunks.begin(), chunks.end(), cf) == chunks.end()) chunks.push_back(cf);
         }
-        std::vector<uint32_t> bands = {0};
-        if (c->use_band && !c->matched) {
-            const uint32_t rb = c->band_cfg.rb;
-            for (uint32_t v : {rb / 2, rb * 3 / 2, rb * 2})
-                if (v >= 2 && v != rb) bands.push_back(v);
-        }
+        // band heights around each stencil's default (explicit values, since
+        // one band_rows setting applies to both stencils)
+        auto band_set = [](uint32_t rb) {
+            std::vector<uint32_t> v = {rb};
+            for (uint32_t x : {rb / 2, rb * 3 / 2, rb * 2})
+                if (x >= 2 && x != rb) v.push_back(x);
+            return v;
+        };
+        const uint32_t lean_rb0 = c->lean_cfg.rb, band_rb0 = c->band_cfg.rb;
         pd_outputs o{};
         o.hits = hits;
         o.hit_capacity = cap;
         o.n_hits = nh;
         std::vector<pd_tuning> cands;
-        if (c->use_fused && !c->matched) cands.push_back(pd_tuning{orig.chunk_frames, orig.band_rows, 1, 0});
-        for (uint32_t cf : chunks)
-            for (uint32_t bd : bands)
-                for (uint32_t ov : {1u, 0u}) cands.push_back(pd_tuning{cf, bd ? bd : orig.band_rows, ov, 1});
+        if (c->use_fused && !c->matched)
+            cands.push_back(pd_tuning{orig.chunk_frames, orig.band_rows, 1, 0, orig.kernels});
+        std::vector<uint32_t> kopts = {orig.kernels};
+        if ((c->use_lean || c->use_bank) && !c->matched) kopts = {1u, 2u};
+        for (uint32_t k : kopts) {
+            std::vector<uint32_t> bands = {0};
+            if (!c->matched && k == 1 && c->use_lean) bands = band_set(lean_rb0);
+            else if (!c->matched && c->use_band) bands = band_set(band_rb0);
+            for (uint32_t cf : chunks)
+                for (uint32_t bd : bands)
+                    for (uint32_t ov : {1u, 0u}) cands.push_back(pd_tuning{cf, bd, ov, 1, k});
+        }
         for (const pd_tuning& t : cands) {
                     if (pd_set_tuning(c, &t) != PD_OK) continue;
                     if (run_chain(c, frames_dev, n_frames, 0, &o, nullptr) != PD_OK) continue;

@@ -1,0 +1,1024 @@
+// pd_lean.cu — the lean kernel pair of the chain.
+//
+//   cm_bank_kernel     common mode of one large unit per CTA (paper section
+//                      "Common Mode", Fig. c; the estimator is the lower
+//                      median over d < cut).  Pass A reads eight raw words per
+//                      16-byte load (three rows in flight per thread) and
+//                      turns them into histogram bins with 16-bit SIMD
+//                      integer arithmetic (CodeMap in pd_lean.cuh): clamp,
+//                      shift-add of the per-pixel offset, clamp; the codes
+//                      stay in shared memory.  The bin of rank floor((n-1)/2)
+//                      is found by a scan; pass B finds that bin's pixels
+//                      among the thread's own codes (eight per 16-byte read,
+//                      one shared atomic per warp to reserve their slots) and
+//                      an exact selection over their binary32 d gives the
+//                      median.  A median in the window's open bottom bin, or
+//                      more candidates than the buffer holds, selects over
+//                      the whole unit instead (same result).
+//   stencil_lean_kernel dark, common mode, gain (Fig. b), the pixel
+//                      histogram, zeroing, 3x3 local maximum, charge sum,
+//                      count (Fig. e), centroid (Fig. f), hits and summaries
+//                      for bands of full-width rows of a module; persistent
+//                      over band tiles.  Each thread owns one four-pixel
+//                      column chunk of the band and walks its rows; the
+//                      corrected energies e of the band and its halo rows go
+//                      to shared memory as they are, and only pixels with
+//                      e above the seed threshold become candidates (a
+//                      register bit per row, then a shared list).  The
+//                      zeroing s = e > zero_thr ? e : 0 is applied where the
+//                      3x3 sums read the neighbourhood.
+//
+// All arithmetic on values that reach an output is round-to-nearest in the
+// chain's order (compiled with --fmad=false), as in pd_fast.cu.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "pd_dev.cuh"
+#include "pd_lean.cuh"
+
+namespace pd {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Bulk copies and mbarriers (inline PTX).
+constexpr uint32_t kCopyWaitLimit = 1u << 20;  // try_wait rounds before giving up
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// global -> shared bulk copy of `bytes` (a multiple of 16; both addresses
+// 16-byte aligned), counted against the mbarrier's transaction bytes
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(saddr(dst)),
+        "l"(src), "r"(bytes), "r"(saddr(bar))
+        : "memory");
+}
+// bounded wait for phase `parity` of the mbarrier; false when it gave up
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = saddr(bar);
+    for (uint32_t it = 0; it < kCopyWaitLimit; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// 16-bit SIMD min / max of two lanes per word (sm_90 and later)
+__device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t vmax_u16x2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// biased bin codes of two raw words: clamp(8 min(x, cap) + k, lo, hi) per lane
+// (8 cap + k < 2^16 in each lane, so the shift-add carries nothing across)
+__device__ __forceinline__ uint32_t code2(uint32_t x, uint32_t k, uint32_t cap2, uint32_t lo2,
+                                          uint32_t hi2) {
+    const uint32_t xm = vmin_u16x2(x, cap2);
+    return vmin_u16x2(vmax_u16x2((xm << 3) + k, lo2), hi2);
+}
+
+// ---------------------------------------------------------------------------
+// Common mode of one large unit, integer-coded.
+struct BankShared {
+    uint64_t bar;
+    uint32_t gsum[kCmBins / 32];
+    uint32_t swarp[32];
+    uint32_t s_bin, s_rank, s_n, s_cand, s_prefix, s_rrank;
+};
+
+constexpr int kBankThreads = 512;
+constexpr uint32_t kThreadGroups = 8;  // groups with a winning-bin code per thread (pass B)
+
+// Block-wide location of rank k = target_of(total) in hist[0 .. PER * 512):
+// each of the 512 threads sums PER bins, warp scans and the sixteen warp
+// totals give every thread its prefix, and the thread whose bins hold rank k
+// finds the bin.  *s_total, *s_bin (PER * 512 when no bin holds k) and
+// *s_rank (rank within the bin).  All threads must call it.
+template <int PER, class TargetFn>
+__device__ __forceinline__ void rank_in_bins(const uint32_t* hist, TargetFn target_of,
+                                             uint32_t* swarp, uint32_t* s_total, uint32_t* s_bin,
+                                             uint32_t* s_rank) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t v[PER], sum = 0;
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        v[j] = hist[PER * tid + j];
+        sum += v[j];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += x;
+    }
+    if (lane == 31) swarp[warp] = incl;
+    if (tid == 0) *s_bin = PER * kBankThreads;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+#pragma unroll
+    for (uint32_t w = 0; w < kBankThreads / 32; w++) {
+        const uint32_t t = swarp[w];
+        before += w < warp ? t : 0u;
+        total += t;
+    }
+    const uint32_t k = target_of(total);
+    uint32_t lo = before + incl - sum;
+    if (k < total && lo <= k && k < lo + sum) {
+#pragma unroll
+        for (int j = 0; j < PER; j++) {
+            if (k < lo + v[j]) {
+                *s_bin = PER * tid + j;
+                *s_rank = k - lo;
+                break;
+            }
+            lo += v[j];
+        }
+    }
+    if (tid == 0) *s_total = total;
+    __syncthreads();
+}
+
+// Exact element of rank `brank` among the mc binary32 values cand[0..mc)
+// that all lie in the histogram bin [lo_b, lo_b + 1/8): 1024 sub-bins of
+// 1/8192 ADU (d - lo_b rounded to nearest is monotone in d, so sub-bins stay
+// ordered), then the few values of the target sub-bin are ranked by
+// counting.  sub: 1024 words; scratch: mc words; few: up to mc floats.
+// Thread 0 .. writes the result to *out.  All threads must call it.
+__device__ void select_in_bin(const float* cand, uint32_t mc, float lo_b, uint32_t brank,
+                              uint32_t* sub, uint32_t* scratch, float* few, uint32_t* swarp,
+                              uint32_t* s_prefix, uint32_t* s_bin, uint32_t* s_rank,
+                              uint32_t* s_nf, float* out) {
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    for (uint32_t i = tid; i < 1024 / 4; i += nthr)
+        reinterpret_cast<uint4*>(sub)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) *s_nf = 0;
+    __syncthreads();
+    for (uint32_t t = tid; t < mc; t += nthr) {
+        const float x = __fmul_rn(__fsub_rn(cand[t], lo_b), 8192.0f);
+        const uint32_t sb = min((uint32_t)max(__float2int_rd(x), 0), 1023u);
+        scratch[t] = sb;
+        atomicAdd(&sub[sb], 1u);
+    }
+    __syncthreads();
+    rank_in_bins<1024 / kBankThreads>(
+        sub, [brank](uint32_t) { return brank; }, swarp, s_prefix, s_bin, s_rank);
+    const uint32_t sbin = *s_bin, srank = *s_rank;
+    for (uint32_t t = tid; t < mc; t += nthr)
+        if (scratch[t] == sbin) few[atomicAdd(s_nf, 1u)] = cand[t];
+    __syncthreads();
+    const uint32_t nf = *s_nf;
+    for (uint32_t t = tid; t < nf; t += nthr) {
+        const uint32_t kt = order_key(few[t]);
+        uint32_t less = 0, leq = 0;
+        for (uint32_t j = 0; j < nf; j++) {
+            const uint32_t kj = order_key(few[j]);
+            less += kj < kt;
+            leq += kj <= kt;
+        }
+        if (less <= srank && srank < leq) *out = few[t];
+    }
+}
+
+// Pass A on one group of eight words: biased codes back to the group and one
+// histogram increment per word (hb[code'] is hist[code' - bias]).
+__device__ __forceinline__ void bank_codes(uint4* g, const uint4& k, uint32_t cap2, uint32_t lo2,
+                                           uint32_t hi2, uint32_t* hb) {
+    const uint4 x = *g;
+    const uint4 y = make_uint4(code2(x.x, k.x, cap2, lo2, hi2), code2(x.y, k.y, cap2, lo2, hi2),
+                               code2(x.z, k.z, cap2, lo2, hi2), code2(x.w, k.w, cap2, lo2, hi2));
+    atomicAdd(hb + (y.x & 0xFFFFu), 1u);
+    atomicAdd(hb + (y.x >> 16), 1u);
+    atomicAdd(hb + (y.y & 0xFFFFu), 1u);
+    atomicAdd(hb + (y.y >> 16), 1u);
+    atomicAdd(hb + (y.z & 0xFFFFu), 1u);
+    atomicAdd(hb + (y.z >> 16), 1u);
+    atomicAdd(hb + (y.w & 0xFFFFu), 1u);
+    atomicAdd(hb + (y.w >> 16), 1u);
+    *g = y;
+}
+
+// 4-D tiled bulk tensor copy global -> shared (box at coordinates c0..c3 of
+// the tensor map), counted against the mbarrier's transaction bytes
+__device__ __forceinline__ void tensor_copy_4d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                               int c2, int c3, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(saddr(bar))
+        : "memory");
+}
+
+// The frames as the tensor [frame][period][group][8 words]: a period is
+// cmap.t consecutive rows (t * cols a multiple of 8 words), a group 16 bytes.
+// Unit u's rows of phase phi (global row = phi mod t) lie in one box of
+// cmap.bp periods x cmap.w8 groups from (group g_lo(phi), period q_lo); the
+// unit's staged buffer holds the t boxes one after the other, each padded to
+// cmap.ne_box groups (a multiple of 8, so every box starts 128-byte aligned).
+// Persistent: CTA b takes items b, b + grid, ...; the next item's copies are
+// issued as soon as pass B has finished reading the stage, so they land
+// while the current item's candidates are ranked.
+__global__ void __launch_bounds__(kBankThreads, 2)
+    cm_bank_kernel(ChainParams p, float* __restrict__ cm_out, CmBigConfig cfg, CodeMap cmap,
+                   const __grid_constant__ CUtensorMap frames, const uint16_t* __restrict__ raw,
+                   uint32_t n_items, uint32_t* __restrict__ err) {
+    extern __shared__ __align__(128) uint4 stage[];  // t * ne_box groups of 8 words
+    __shared__ BankShared sh;
+    const uint32_t W8 = cmap.w8, T = cmap.t;
+    const uint32_t ne = T * cmap.ne_box;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(stage + ne);       // kCmBins + 4 (spare at kCmBins)
+    float* cand = reinterpret_cast<float*>(hist + kCmBins + 4);      // kCandCap
+    uint32_t* cidx = reinterpret_cast<uint32_t*>(cand + kCandCap);   // kCandCap
+    const uint32_t tid = threadIdx.x, lane = tid & 31;
+    const uint32_t cap2 = cmap.rcap * 0x10001u;
+    const uint32_t lo2 = cmap.bias * 0x10001u;
+    const uint32_t hi2 = (cmap.bias + kCmBins) * 0x10001u;
+    uint32_t* hb = hist - cmap.bias;  // hb[code'] is hist[code' - bias]
+
+    // global first row and first column of item `it`'s unit, its frame
+    auto unit_of = [&](uint32_t it, uint32_t* R0, uint32_t* c0, uint32_t* f) {
+        *f = it / p.units_per_frame;
+        const uint32_t u = it - *f * p.units_per_frame;
+        const uint32_t m = u / p.units_per_module, um = u - m * p.units_per_module;
+        *R0 = m * p.rows + (um / p.units_per_row) * p.unit_rows;
+        *c0 = (um % p.units_per_row) * p.unit_cols;
+    };
+    // one tensor copy per row phase of item `it` (thread 0)
+    auto issue = [&](uint32_t it) {
+        uint32_t R0, c0, f;
+        unit_of(it, &R0, &c0, &f);
+        mbar_expect_tx(&sh.bar, T * cmap.bp * W8 * 16u);
+        for (uint32_t ph = 0; ph < T; ph++)
+            tensor_copy_4d(stage + ph * cmap.ne_box, &frames, 0, (int)((ph * p.cols + c0) >> 3),
+                           (int)(R0 / T), (int)f, &sh.bar);
+    };
+
+    if (tid == 0) {
+        mbar_init(&sh.bar, 1);
+        fence_mbar_init();
+        if (blockIdx.x < n_items) issue(blockIdx.x);
+    }
+    for (uint32_t i = tid; i < (kCmBins + 4) / 4; i += kBankThreads)
+        reinterpret_cast<uint4*>(hist)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) sh.s_cand = 0;
+    __syncthreads();  // mbarrier initialised, histogram zero
+
+    uint32_t parity = 0;
+    for (uint32_t item = blockIdx.x; item < n_items; item += gridDim.x, parity ^= 1u) {
+        const uint32_t next = item + gridDim.x;
+        uint32_t R0, c0, f;
+        unit_of(item, &R0, &c0, &f);
+        const uint32_t u = item - f * p.units_per_frame;
+        const uint32_t q_lo = R0 / T;
+        const uint16_t* fr = raw + (size_t)f * p.frame_px;
+        // the first per-pixel offsets K' of pass A (from the unit's map in
+        // the staged layout) are loaded while the copies land
+        const uint4* km = cmap.kmap + (size_t)u * ne;
+        const uint4 zero4 = make_uint4(0, 0, 0, 0);
+        uint4 k0 = tid < ne ? __ldg(km + tid) : zero4;
+        uint4 k1 = tid + kBankThreads < ne ? __ldg(km + tid + kBankThreads) : zero4;
+        uint4 k2 = tid + 2 * kBankThreads < ne ? __ldg(km + tid + 2 * kBankThreads) : zero4;
+        // one thread waits for the copies; the others wait at the barrier
+        // (which orders the copied data before their reads)
+        const bool ok = tid != 0 || mbar_wait(&sh.bar, parity);
+        if (__syncthreads_or(!ok)) {
+            // the copies did not complete in time: report, give them a second
+            // bounded wait (they write this CTA's shared memory), stop
+            if (tid == 0) {
+                atomicOr(err, 1u);
+                mbar_wait(&sh.bar, parity);
+            }
+            return;
+        }
+
+        // 1. pass A over the staged groups, three groups per round, the next
+        //    round's offsets in flight
+        for (uint32_t e = tid; e < ne; e += 3 * kBankThreads) {
+            const uint32_t e3 = e + 3 * kBankThreads;
+            const uint4 n0 = e3 < ne ? __ldg(km + e3) : zero4;
+            const uint4 n1 = e3 + kBankThreads < ne ? __ldg(km + e3 + kBankThreads) : zero4;
+            const uint4 n2 = e3 + 2 * kBankThreads < ne ? __ldg(km + e3 + 2 * kBankThreads) : zero4;
+            bank_codes(stage + e, k0, cap2, lo2, hi2, hb);
+            if (e + kBankThreads < ne) bank_codes(stage + e + kBankThreads, k1, cap2, lo2, hi2, hb);
+            if (e + 2 * kBankThreads < ne)
+                bank_codes(stage + e + 2 * kBankThreads, k2, cap2, lo2, hi2, hb);
+            k0 = n0;
+            k1 = n1;
+            k2 = n2;
+        }
+        __syncthreads();
+
+        // 2. the bin of rank floor((n-1)/2) among the values below the cut
+        const uint32_t min_count = p.cm_min_count;
+        rank_in_bins<kCmBins / kBankThreads>(
+            hist,
+            [min_count](uint32_t total) {
+                return (total > 0 && total >= min_count) ? (total - 1) / 2 : total;
+            },
+            sh.swarp, &sh.s_n, &sh.s_bin, &sh.s_rank);
+        const uint32_t n = sh.s_n;
+        const uint32_t bin = sh.s_bin, brank = sh.s_rank;
+        const bool none = n == 0 || n < min_count;
+        // frame pixel of staged group e, word l
+        auto staged_px = [&](uint32_t e, uint32_t l) -> uint32_t {
+            const uint32_t ph = e / cmap.ne_box, g = e - ph * cmap.ne_box;
+            const uint32_t pp = g / W8, k = g - pp * W8;
+            return (q_lo + pp) * T * p.cols + 8 * (((ph * p.cols + c0) >> 3) + k) + l;
+        };
+        const uint32_t warp = tid >> 5;
+        const uint32_t tgt = (bin + cmap.bias) * 0x10001u;
+        uint32_t n_grp = 0;  // this thread's groups holding the winning bin
+        if (!none && bin != 0) {
+            // 3. pass B: the thread's groups that hold a code of the winning
+            //    bin go to its own slots of the candidate buffer (no shared
+            //    atomics, no warp coordination).  A halfword h of
+            //    y = word ^ (target, target) is zero only if the word has a
+            //    zero halfword when (y - 0x00010001) & ~y & 0x80008000 != 0
+            //    (a borrow from a zero low half can flag the high half, but
+            //    then the group matches anyway); the exact lanes are found
+            //    after the barrier.
+            uint16_t* slots = reinterpret_cast<uint16_t*>(cidx) + tid * kThreadGroups;
+            for (uint32_t e = tid; e < ne; e += kBankThreads) {
+                const uint4 v = stage[e];
+                const uint32_t y0 = v.x ^ tgt, y1 = v.y ^ tgt, y2 = v.z ^ tgt, y3 = v.w ^ tgt;
+                const uint32_t h = ((y0 - 0x00010001u) & ~y0) | ((y1 - 0x00010001u) & ~y1) |
+                                   ((y2 - 0x00010001u) & ~y2) | ((y3 - 0x00010001u) & ~y3);
+                if (h & 0x80008000u) {
+                    if (n_grp < kThreadGroups) slots[n_grp] = (uint16_t)e;
+                    n_grp++;
+                }
+            }
+        }
+        // exact matching pixels of the thread's groups, and a block scan of
+        // their counts for the compact candidate array
+        uint32_t n_px = 0;
+        if (!none && bin != 0) {
+            const uint16_t* slots = reinterpret_cast<const uint16_t*>(cidx) + tid * kThreadGroups;
+            for (uint32_t i = 0; i < min(n_grp, kThreadGroups); i++) {
+                const uint4 v = stage[slots[i]];
+                const uint32_t w[4] = {v.x ^ tgt, v.y ^ tgt, v.z ^ tgt, v.w ^ tgt};
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    n_px += ((w[j] & 0xFFFFu) == 0) + ((w[j] >> 16) == 0);
+            }
+        }
+        uint32_t incl = n_px;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += x;
+        }
+        const bool ovf = n_grp > kThreadGroups;
+        if (lane == 31) sh.swarp[warp] = incl;
+        if (tid == 0) sh.s_cand = 0;
+        __syncthreads();
+        if (ovf) sh.s_cand = 1;  // a thread's slots overflowed
+        uint32_t before = incl - n_px, mc = 0;
+        for (uint32_t w = 0; w < kBankThreads / 32; w++) {
+            const uint32_t c = sh.swarp[w];
+            before += w < warp ? c : 0u;
+            mc += c;
+        }
+        // 4. the staged position of each matching pixel at its place in a
+        //    compact list (in the histogram's words, free now), then one
+        //    thread per candidate loads its raw word and pedestal
+        uint32_t* qlist = hist;
+        if (!none && bin != 0 && mc <= kCandCap) {
+            const uint16_t* slots = reinterpret_cast<const uint16_t*>(cidx) + tid * kThreadGroups;
+            uint32_t at = before;
+            for (uint32_t i = 0; i < min(n_grp, kThreadGroups); i++) {
+                const uint32_t e = slots[i];
+                const uint4 v = stage[e];
+                const uint32_t w[4] = {v.x ^ tgt, v.y ^ tgt, v.z ^ tgt, v.w ^ tgt};
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (((w[j >> 1] >> (16 * (j & 1))) & 0xFFFFu) == 0) qlist[at++] = e * 8 + j;
+            }
+        }
+        __syncthreads();  // the stage is no longer read
+        if (!none && bin != 0 && mc <= kCandCap) {
+            const float* npf = p.nped;
+            for (uint32_t t = tid; t < mc; t += kBankThreads) {
+                const uint32_t q = qlist[t];
+                const uint32_t px = staged_px(q >> 3, q & 7u);
+                cand[t] = __fadd_rn(__uint2float_rn(fr[px]), npf[px]);
+            }
+        }
+        __syncthreads();
+        // the next item's copies (after the candidates' loads, which would
+        // otherwise queue behind them) land while this item is ranked
+        if (tid == 0 && next < n_items) {
+            fence_async_smem();  // order this item's generic stage accesses before the copy
+            issue(next);
+        }
+        const bool over = sh.s_cand != 0 || mc > kCandCap;
+        if (none) {
+            if (tid == 0) cm_out[item] = 0.0f;
+        } else if (bin != 0 && !over) {
+            // the exact rank inside the bin
+            const float lo_b = __fadd_rn(cfg.w_lo, __fmul_rn((float)bin, 0.125f));
+            select_in_bin(cand, mc, lo_b, brank, hist, cidx, reinterpret_cast<float*>(hist + 1024),
+                          sh.swarp, &sh.s_prefix, &sh.s_bin, &sh.s_rank, &sh.s_rrank,
+                          cm_out + item);
+        } else {
+            // whole-unit exact selection (bottom bin or candidate overflow)
+            const uint32_t P0 = R0 * p.cols + c0;
+            const float* npf = p.nped;
+            auto unit_key = [&](uint32_t i) -> uint32_t {
+                const uint32_t px = P0 + (i / p.unit_cols) * p.cols + i % p.unit_cols;
+                const float d = __fadd_rn(__uint2float_rn(fr[px]), npf[px]);
+                return d < p.cm_cut ? order_key(d) : kSent;
+            };
+            const uint32_t key = block_radix_select(unit_key, p.unit_px, (n - 1) / 2, hist,
+                                                    &sh.s_prefix, &sh.s_rrank);
+            if (tid == 0) cm_out[item] = key_value(key);
+        }
+        __syncthreads();  // the histogram and candidates are no longer read
+        for (uint32_t i = tid; i < (kCmBins + 4) / 4; i += kBankThreads)
+            reinterpret_cast<uint4*>(hist)[i] = make_uint4(0, 0, 0, 0);
+        if (tid == 0) sh.s_cand = 0;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Lean stencil over bands of full-width rows.
+constexpr uint32_t kLeanThreads = 512;
+
+struct LeanRow {
+    uint2 rw;   // four raw words
+    float4 np;  // their negated pedestals
+    float4 g;   // their inverse gains
+};
+
+// Tiles first, first + step, ... < n_tiles (tile t: band t % n_bands of module
+// (t / n_bands) % n_modules of frame t / (n_bands n_modules)).  COLBANK: the
+// common-mode units span the module's full height, so a thread's four pixels
+// take the same two values on every row of a tile.  CORR: write corrected
+// frames.
+template <bool COLBANK, bool CORR>
+__global__ void __launch_bounds__(kLeanThreads, 2)
+    stencil_lean_kernel(ChainParams p, const uint16_t* __restrict__ raw, uint32_t frame_base,
+                        CallOut out, LeanConfig lc, unsigned long long n_tiles) {
+    extern __shared__ __align__(16) float lean_smem[];
+    __shared__ uint32_t list_n[2];
+    const uint32_t P = lc.pitch, RB = lc.rb;
+    float* tile = lean_smem;                                            // (RB + 2) x P
+    uint32_t* hpix = reinterpret_cast<uint32_t*>(tile + (RB + 2) * P);  // hist_bins
+    uint32_t* hhit = hpix + p.hist_bins;                                // hist_bins
+    uint32_t* list = hhit + p.hist_bins;                                // list_cap
+    float* cmt = reinterpret_cast<float*>(list + lc.list_cap);          // (RB + 2) x upr
+
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    const uint32_t TX = lc.tx, TY = lc.ty;
+    const uint32_t cx = tid % TX, ty = tid / TX;
+    const int R = (int)p.rows, C = (int)p.cols;
+    const int col = 4 * (int)cx;
+    const uint32_t uca = (uint32_t)col / p.unit_cols;
+    const uint32_t ucb = (uint32_t)(col + 3) / p.unit_cols;
+    const int split = (int)(ucb * p.unit_cols) - col;  // pixels i >= split take unit ucb
+    const int last_bin = (int)p.hist_bins - 1;
+    const float2 iw2 = make_float2(p.hist_inv_w, p.hist_inv_w);
+    const float2 nl2 = make_float2(p.hist_neg_lo_s, p.hist_neg_lo_s);
+    const float2 mg2 = make_float2(kMagic, kMagic);
+    // every pixel with e > seed_thr has a histogram bin >= seed_bin (the bin
+    // is monotone in e); rows holding such a bin are scanned for candidates
+    const int seed_bin = (int)summary_bin(p.seed_thr, p.hist_inv_w, p.hist_neg_lo_s,
+                                          (int)(kMagicBits + p.hist_bins - 1));
+
+    for (uint32_t i = tid; i < (RB + 2) * P; i += nthr) tile[i] = 0.0f;
+    for (uint32_t i = tid; i < 2 * p.hist_bins; i += nthr) hpix[i] = 0;
+    if (tid < 2) list_n[tid] = 0;
+    __syncthreads();
+
+    const int n_own_full = RB > ty ? ((int)RB - 1 - (int)ty) / (int)TY + 1 : 0;
+    const unsigned long long first = blockIdx.x, step = gridDim.x;
+    TileWalk walk(first, step, lc.n_bands, p.n_modules);
+    uint32_t par = 0;
+    for (unsigned long long t = first; t < n_tiles; t += step, walk.next(), par ^= 1u) {
+        const uint32_t m = walk.m, f = walk.f;
+        const int r0 = (int)walk.band * (int)RB;
+        const int rows_here = min((int)RB, R - r0);
+        const size_t mod_base = (size_t)m * p.module_px;
+        const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
+        const float* npm = p.nped + mod_base;
+        const float* gm = p.inv_gain + mod_base;
+        const float* cmf = out.cm + (size_t)f * p.units_per_frame + (size_t)m * p.units_per_module;
+
+        // negated common mode of the chunk's pixels (COLBANK), or of every
+        // (tile row, unit column) in shared memory
+        float2 n01 = make_float2(0.0f, 0.0f), n23 = n01;
+        if (COLBANK) {
+            const float a = -cmf[uca], b = -cmf[ucb];
+            n01 = make_float2(split > 0 ? a : b, split > 1 ? a : b);
+            n23 = make_float2(split > 2 ? a : b, split > 3 ? a : b);
+        } else {
+            const uint32_t upr = p.units_per_row;
+            for (uint32_t i = tid; i < (uint32_t)(rows_here + 2) * upr; i += nthr) {
+                const int r = r0 - 1 + (int)(i / upr);
+                cmt[i] = r >= 0 && r < R ? -cmf[((uint32_t)r / p.unit_rows) * upr + i % upr] : 0.0f;
+            }
+            __syncthreads();
+        }
+
+        // e of four pixels of module row r, from a row of loads
+        auto correct = [&](const LeanRow& x, int rl, float2& e01, float2& e23) {
+            const float2 d01 = __fadd2_rn(raw_pair(x.rw.x), make_float2(x.np.x, x.np.y));
+            const float2 d23 = __fadd2_rn(raw_pair(x.rw.y), make_float2(x.np.z, x.np.w));
+            float2 m01 = n01, m23 = n23;
+            if (!COLBANK) {
+                const float a = cmt[rl * p.units_per_row + uca];
+                const float b = cmt[rl * p.units_per_row + ucb];
+                m01 = make_float2(split > 0 ? a : b, split > 1 ? a : b);
+                m23 = make_float2(split > 2 ? a : b, split > 3 ? a : b);
+            }
+            e01 = __fmul2_rn(__fadd2_rn(d01, m01), make_float2(x.g.x, x.g.y));
+            e23 = __fmul2_rn(__fadd2_rn(d23, m23), make_float2(x.g.z, x.g.w));
+        };
+        auto load = [&](int r) -> LeanRow {
+            const uint32_t off = (uint32_t)r * p.cols + (uint32_t)col;
+            LeanRow x;
+            x.rw = __ldg(reinterpret_cast<const uint2*>(fr + off));
+            x.np = __ldg(reinterpret_cast<const float4*>(npm + off));
+            x.g = __ldg(reinterpret_cast<const float4*>(gm + off));
+            return x;
+        };
+
+        // 1. halo rows (tile rows 0 and rows_here + 1): e only, zero outside
+        //    the module; done by the last two row lanes, which own the
+        //    fewest rows
+        auto halo = [&](int rl) {
+            const int r = r0 - 1 + rl;
+            float4 ev = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (r >= 0 && r < R) {
+                float2 e01, e23;
+                correct(load(r), rl, e01, e23);
+                ev = make_float4(e01.x, e01.y, e23.x, e23.y);
+            }
+            *reinterpret_cast<float4*>(tile + rl * P + 4 + col) = ev;
+        };
+        if (TY == 1) {
+            halo(0);
+            halo(rows_here + 1);
+        } else if (ty == TY - 1) {
+            halo(0);
+        } else if (ty == TY - 2) {
+            halo(rows_here + 1);
+        }
+
+        // 2. own rows r0 + ty + i TY (tile row 1 + ty + i TY): e to the tile,
+        //    the pixel histogram, a bit per row whose largest bin reaches the
+        //    seed threshold's; rows are processed in pairs from two register
+        //    sets, so the next row's loads are in flight while a row is
+        //    processed
+        const int n_own = rows_here == (int)RB ? n_own_full
+                          : rows_here > (int)ty ? (rows_here - 1 - (int)ty) / (int)TY + 1 : 0;
+        uint32_t cmask = 0;  // bit i: own row i may hold a candidate
+        auto own_row = [&](const LeanRow& x, int i) {
+            const int rl = 1 + (int)ty + i * (int)TY;
+            float2 e01, e23;
+            correct(x, rl, e01, e23);
+            const float2 u01 = __fadd2_rd(__ffma2_rn(e01, iw2, nl2), mg2);
+            const float2 u23 = __fadd2_rd(__ffma2_rn(e23, iw2, nl2), mg2);
+            const int b0 = min(__viaddmax_s32(__float_as_int(u01.x), -(int)kMagicBits, 0), last_bin);
+            const int b1 = min(__viaddmax_s32(__float_as_int(u01.y), -(int)kMagicBits, 0), last_bin);
+            const int b2 = min(__viaddmax_s32(__float_as_int(u23.x), -(int)kMagicBits, 0), last_bin);
+            const int b3 = min(__viaddmax_s32(__float_as_int(u23.y), -(int)kMagicBits, 0), last_bin);
+            atomicAdd(&hpix[b0], 1u);
+            atomicAdd(&hpix[b1], 1u);
+            atomicAdd(&hpix[b2], 1u);
+            atomicAdd(&hpix[b3], 1u);
+            *reinterpret_cast<float4*>(tile + rl * P + 4 + col) =
+                make_float4(e01.x, e01.y, e23.x, e23.y);
+            if (CORR) {
+                float* dst = out.corrected + (size_t)f * p.frame_px + mod_base +
+                             (size_t)(r0 + rl - 1) * p.cols + col;
+                *reinterpret_cast<float4*>(dst) = make_float4(e01.x, e01.y, e23.x, e23.y);
+            }
+            if (max(__vimax3_s32(b0, b1, b2), b3) >= seed_bin) cmask |= 1u << i;
+        };
+        if (n_own > 0) {
+            const int rs = (int)TY;  // rows between a thread's own rows
+            LeanRow a = load(r0 + (int)ty), b;
+            for (int i = 0; i < n_own; i += 2) {
+                if (i + 1 < n_own) b = load(r0 + (int)ty + (i + 1) * rs);
+                own_row(a, i);
+                if (i + 1 >= n_own) break;
+                if (i + 2 < n_own) a = load(r0 + (int)ty + (i + 2) * rs);
+                own_row(b, i + 1);
+            }
+        }
+        // candidate pixels (e > seed_thr) of the marked rows into the tile's
+        // list, one reservation per thread (rare: the thread reads its own
+        // rows back from the tile)
+        if (cmask) {
+            auto bits4 = [&](int i) -> uint32_t {
+                const int rl = 1 + (int)ty + i * (int)TY;
+                const float4 ev = *reinterpret_cast<const float4*>(tile + rl * P + 4 + col);
+                return (uint32_t)(ev.x > p.seed_thr) | (uint32_t)(ev.y > p.seed_thr) << 1 |
+                       (uint32_t)(ev.z > p.seed_thr) << 2 | (uint32_t)(ev.w > p.seed_thr) << 3;
+            };
+            uint32_t n_px = 0;
+            for (uint32_t mm = cmask; mm; mm &= mm - 1) n_px += __popc(bits4(__ffs(mm) - 1));
+            if (n_px) {
+                uint32_t at = atomicAdd(&list_n[par], n_px);
+                for (uint32_t mm = cmask; mm; mm &= mm - 1) {
+                    const int i = __ffs(mm) - 1;
+                    const uint32_t rl = 1 + ty + (uint32_t)i * TY;
+                    for (uint32_t bb = bits4(i); bb; bb &= bb - 1, at++)
+                        if (at < lc.list_cap)
+                            list[at] = rl << 16 | ((uint32_t)col + (uint32_t)(__ffs(bb) - 1));
+                }
+            }
+        }
+        __syncthreads();
+
+        // 3. seeds: local maximum on s = e > zero_thr ? e : 0 with the raster
+        //    tie rule, 3x3 sums, count, centroid, emission
+        const uint32_t n_list = list_n[par];
+        if (tid == 0) list_n[par ^ 1u] = 0;  // the next tile's counter (read last tile)
+        const bool scan = n_list > lc.list_cap;  // overflow: test every own pixel
+        const uint32_t n_work = scan ? (uint32_t)rows_here * (uint32_t)C : n_list;
+        const float z = p.zero_thr;
+        for (uint32_t base = 0; base < n_work; base += nthr) {
+            if (base + (tid & ~31u) >= n_work) break;  // the whole warp is past the list
+            const uint32_t j = base + tid;
+            bool emit = false;
+            pd_hit h;
+            uint32_t n = 0, pix = 0;
+            if (j < n_work) {
+                int rl, c;
+                if (scan) {
+                    rl = 1 + (int)(j / (uint32_t)C);
+                    c = (int)(j % (uint32_t)C);
+                } else {
+                    const uint32_t e = list[j];
+                    rl = (int)(e >> 16);
+                    c = (int)(e & 0xFFFFu);
+                }
+                const float* sc = tile + rl * P + 4 + c;
+                const float sp = sc[0];
+                if (sp > p.seed_thr) {
+                    float nb[9] = {sc[-(int)P - 1], sc[-(int)P], sc[-(int)P + 1],
+                                   sc[-1],          sp,          sc[1],
+                                   sc[P - 1],       sc[P],       sc[P + 1]};
+#pragma unroll
+                    for (int k = 0; k < 9; k++) nb[k] = nb[k] > z ? nb[k] : 0.0f;
+                    const bool seed = sp > nb[0] && sp > nb[1] && sp > nb[2] && sp > nb[3] &&
+                                      sp >= nb[5] && sp >= nb[6] && sp >= nb[7] && sp >= nb[8];
+                    if (seed) {
+                        float E = 0.0f, Mx = 0.0f, My = 0.0f;
+                        uint32_t npix = 0;
+#pragma unroll
+                        for (int k = 0; k < 9; k++) {
+                            const float ox = (float)(k % 3 - 1), oy = (float)(k / 3 - 1);
+                            E = __fadd_rn(E, nb[k]);
+                            Mx = __fadd_rn(Mx, __fmul_rn(nb[k], ox));
+                            My = __fadd_rn(My, __fmul_rn(nb[k], oy));
+                            npix += nb[k] > 0.0f;
+                        }
+                        atomicAdd(&hhit[summary_bin(E, p.hist_inv_w, p.hist_neg_lo_s,
+                                                    (int)(kMagicBits + p.hist_bins - 1))],
+                                  1u);
+                        const float qr = rintf(__fdiv_rn(E, p.photon_kev));
+                        uint16_t flags = 0;
+                        if (!(qr >= 0.0f)) {
+                            n = 0;
+                        } else if (qr > 255.0f) {
+                            n = 255;
+                            flags |= PD_HIT_SATURATED;
+                        } else {
+                            n = (uint32_t)qr;
+                        }
+                        if (n >= 1) {
+                            const int r = r0 - 1 + rl;
+                            if (r == 0 || c == 0 || r == R - 1 || c == C - 1) flags |= PD_HIT_EDGE;
+                            pix = (uint32_t)mod_base + (uint32_t)r * p.cols + (uint32_t)c;
+                            h.frame = frame_base + f;
+                            h.pixel = pix;
+                            h.energy_kev = E;
+                            h.dx = __fdiv_rn(Mx, E);
+                            h.dy = __fdiv_rn(My, E);
+                            h.count = (uint8_t)n;
+                            h.npix = (uint8_t)npix;
+                            h.flags = flags;
+                            emit = true;
+                        }
+                    }
+                }
+            }
+            const uint32_t mask = __ballot_sync(0xffffffffu, emit);
+            if (mask) {
+                const int lane = tid & 31;
+                const int leader = __ffs(mask) - 1;
+                uint32_t slot = 0;
+                if (lane == leader) slot = atomicAdd(out.n_hits, __popc(mask));
+                slot = __shfl_sync(0xffffffffu, slot, leader);
+                if (emit) {
+                    slot += __popc(mask & ((1u << lane) - 1u));
+                    atomicAdd(&p.count_map[pix], n);
+                    if (slot < out.hit_capacity) out.hits[slot] = h;
+                }
+            }
+        }
+        __syncthreads();  // the tile is rewritten by the next band
+    }
+    for (uint32_t b = tid; b < p.hist_bins; b += nthr) {
+        if (hpix[b]) atomicAdd(&p.hist_pix[b], (unsigned long long)hpix[b]);
+        if (hhit[b]) atomicAdd(&p.hist_hit[b], (unsigned long long)hhit[b]);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side of the integer codes.
+namespace {
+
+// floor(a + b) of two doubles, exactly (TwoSum keeps the rounding error)
+long long floor_sum(double a, double b) {
+    const double s = a + b;
+    const double bb = s - a;
+    const double err = (a - (s - bb)) + (b - bb);
+    const double fs = std::floor(s);
+    if (s == fs) return (long long)fs - (err < 0.0 ? 1 : 0);
+    return (long long)fs;
+}
+
+}  // namespace
+
+bool build_code_map(const ChainParams& p, const float* pedestal, std::vector<uint16_t>* kmap,
+                    CodeMap* out) {
+    if (p.frame_px % 8) return false;
+    if (!(p.cm_cut > -1e6f && p.cm_cut < 1e6f)) return false;
+    // periods of t rows whose length is a multiple of 8 words tile the frame
+    uint32_t gcd = 8;
+    while (p.cols % gcd) gcd >>= 1;
+    const uint32_t T = 8 / gcd;
+    if (((size_t)p.n_modules * p.rows) % T) return false;
+    const double cut = p.cm_cut;
+    const double lo = cut - 512.0;
+    const double D = std::max(std::fabs(lo), std::fabs(cut));
+    const size_t fpx = p.frame_px;
+    long long fmin = 0, fmax = 0, rcap = 0;
+    std::vector<int32_t> F(fpx);
+    for (size_t i = 0; i < fpx; i++) {
+        const float ped = pedestal[i];
+        if (!std::isfinite(ped)) return false;
+        if (ped != 0.0f) {
+            // d = x - ped is exact in binary32 while |d| < 2^24 ulp-units of ped
+            int ex = 0;
+            std::frexp((double)ped, &ex);  // |ped| in [2^(ex-1), 2^ex)
+            const int q = std::max(ex - 24, -149);
+            if (!(D < std::ldexp(1.0, 24 + q))) return false;
+        }
+        const long long fv = floor_sum(-8.0 * (double)ped, -8.0 * lo);
+        if (fv < -(1LL << 30) || fv > (1LL << 30)) return false;
+        F[i] = (int32_t)fv;
+        // raw words at or above ceil((4096 - F) / 8) are in the spare bin
+        const long long need = 4096 - fv;
+        const long long rc = need <= 0 ? 0 : (need + 7) / 8;
+        fmin = i ? std::min(fmin, fv) : fv;
+        fmax = i ? std::max(fmax, fv) : fv;
+        rcap = i ? std::max(rcap, rc) : rc;
+    }
+    const long long bias = fmin < 0 ? -fmin : 0;
+    const long long kmax = std::max(fmax + bias, bias + 4096);
+    if (rcap > 65535 || 8 * rcap + kmax > 65535) return false;
+    // box of a unit's rows of one phase: periods q_lo .. q_hi, groups
+    // g_lo(phase) .. g_hi(phase) of a period
+    auto unit_pos = [&](uint32_t u, uint32_t* R0, uint32_t* c0) {
+        const uint32_t m = u / p.units_per_module, um = u % p.units_per_module;
+        *R0 = m * p.rows + (um / p.units_per_row) * p.unit_rows;
+        *c0 = (um % p.units_per_row) * p.unit_cols;
+    };
+    uint32_t w8 = 0, bp = 0;
+    for (uint32_t u = 0; u < p.units_per_frame; u++) {
+        uint32_t R0, c0;
+        unit_pos(u, &R0, &c0);
+        bp = std::max(bp, (R0 + p.unit_rows - 1) / T - R0 / T + 1);
+        for (uint32_t ph = 0; ph < T; ph++)
+            w8 = std::max(w8, (ph * p.cols + c0 + p.unit_cols - 1) / 8 - (ph * p.cols + c0) / 8 + 1);
+    }
+    if (w8 > 256 || bp > 256) return false;
+    const uint32_t ne_box = (bp * w8 + 7) / 8 * 8;
+    const size_t per_unit = (size_t)T * ne_box * 8;
+    const uint16_t junk = (uint16_t)(bias + 4096);
+    kmap->assign((size_t)p.units_per_frame * per_unit, junk);
+    const size_t tpx = (size_t)T * p.cols;  // words per period
+    for (uint32_t u = 0; u < p.units_per_frame; u++) {
+        uint32_t R0, c0;
+        unit_pos(u, &R0, &c0);
+        const uint32_t q_lo = R0 / T;
+        for (uint32_t ph = 0; ph < T; ph++) {
+            uint16_t* dst = kmap->data() + (size_t)u * per_unit + (size_t)ph * ne_box * 8;
+            const uint32_t g_lo = (ph * p.cols + c0) / 8;
+            for (uint32_t pp = 0; pp < bp; pp++)
+                for (uint32_t k = 0; k < w8; k++)
+                    for (uint32_t l = 0; l < 8; l++) {
+                        const size_t ppx = 8 * ((size_t)g_lo + k) + l;  // word of the period
+                        if (ppx >= tpx) continue;
+                        const uint32_t rp = (uint32_t)(ppx / p.cols);
+                        const uint32_t col = (uint32_t)(ppx % p.cols);
+                        const size_t R = (size_t)(q_lo + pp) * T + rp;
+                        if (rp != ph || R < R0 || R >= (size_t)R0 + p.unit_rows || col < c0 ||
+                            col >= c0 + p.unit_cols)
+                            continue;
+                        dst[((size_t)pp * w8 + k) * 8 + l] = (uint16_t)(F[R * p.cols + col] + bias);
+                    }
+        }
+    }
+    *out = CodeMap{nullptr, w8, (uint32_t)bias, (uint32_t)rcap, T, bp, ne_box, 2};
+    return true;
+}
+
+size_t cm_bank_smem_bytes(const ChainParams& p, const CodeMap& cmap) {
+    (void)p;
+    return (size_t)cmap.t * cmap.ne_box * 16 + (size_t)(kCmBins + 4) * 4 + (size_t)kCandCap * 8;
+}
+
+bool cm_bank_supported(const ChainParams& p, const CodeMap& cmap) {
+    return p.unit_rows * p.unit_cols >= kCmBigMinPx && cm_bank_smem_bytes(p, cmap) <= 110 * 1024;
+}
+
+static int g_attr_dev_bank = -1;
+
+// cuTensorMapEncodeTiled from the driver, looked up once
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+cudaError_t launch_cm_bank(const ChainParams& p, const CmBigConfig& cfg, const CodeMap& cmap,
+                           const uint16_t* raw, uint32_t n_frames, float* cm, uint32_t* err,
+                           cudaStream_t stream) {
+    const unsigned long long items = (unsigned long long)n_frames * p.units_per_frame;
+    if (items == 0) return cudaSuccess;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (g_attr_dev_bank != dev) {
+        cudaError_t e = cudaFuncSetAttribute(cm_bank_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             110 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(cm_bank_kernel,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+        g_attr_dev_bank = dev;
+    }
+    // the call's frames as [frame][period][group][8 words] of uint16
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const uint64_t G = (uint64_t)cmap.t * p.cols / 8;
+    const cuuint64_t dims[4] = {8, G, (cuuint64_t)p.frame_px / ((cuuint64_t)cmap.t * p.cols),
+                                n_frames};
+    const cuuint64_t strides[3] = {16, G * 16, (cuuint64_t)p.frame_px * 2};
+    const cuuint32_t box[4] = {8, cmap.w8, cmap.bp, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUtensorMap map;
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<uint16_t*>(raw), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    const size_t smem = cm_bank_smem_bytes(p, cmap);
+    const unsigned long long grid = std::min<unsigned long long>(
+        items, (unsigned long long)std::max<uint32_t>(cmap.ctas_per_sm, 1) * device_sm_count());
+    cm_bank_kernel<<<(unsigned)grid, kBankThreads, smem, stream>>>(p, cm, cfg, cmap, map, raw,
+                                                                   (uint32_t)items, err);
+    return cudaGetLastError();
+}
+
+}  // namespace pd
+
+// ---------------------------------------------------------------------------
+// Host side of the lean stencil.
+namespace pd {
+
+constexpr size_t kLeanSmemTwo = 100 * 1024;  // two CTAs per SM
+constexpr size_t kLeanSmemMax = 200 * 1024;
+
+LeanConfig make_lean_config(const ChainParams& p, uint32_t rb) {
+    LeanConfig lc{};
+    lc.ok = false;
+    // four-pixel chunks start 8-byte aligned in every frame and module, and a
+    // chunk takes the common mode of at most two units
+    if (p.cols % 4 || p.module_px % 4 || p.frame_px % 4 || p.unit_cols < 2) return lc;
+    if (p.cols / 4 > kLeanThreads || p.cols > 65535) return lc;
+    if (cm_kind(p) == PD_CM_MEAN_STACKED || cm_after_gain(p)) return lc;
+    lc.tx = p.cols / 4;
+    lc.ty = std::max<uint32_t>(1, kLeanThreads / lc.tx);
+    lc.pitch = p.cols + 8;
+    lc.colbank = p.unit_rows == p.rows ? 1u : 0u;
+    lc.list_cap = 4096;
+    const bool dflt = rb == 0;
+    if (dflt) {
+        // the tallest band two CTAs per SM hold (at most 16 rows per row
+        // lane), then split evenly over the module's rows
+        LeanConfig t = lc;
+        t.rb = 1;
+        while (t.rb < p.rows && (t.rb + lc.ty) / lc.ty <= 16) {
+            t.rb++;
+            if (lean_smem_bytes(p, t) > kLeanSmemTwo) {
+                t.rb--;
+                break;
+            }
+        }
+        const uint32_t nb = (p.rows + t.rb - 1) / t.rb;
+        rb = (p.rows + nb - 1) / nb;
+    }
+    rb = std::min(rb, p.rows);
+    // own rows per thread fit a 64-bit candidate mask (4 bits per row)
+    while (rb > 1 && (rb + lc.ty - 1) / lc.ty > 16) rb--;
+    lc.rb = rb;
+    // the default keeps two CTAs per SM; a requested height may take one
+    const size_t limit = dflt ? kLeanSmemTwo : kLeanSmemMax;
+    while (lc.rb > 1 && lean_smem_bytes(p, lc) > limit) lc.rb--;
+    lc.n_bands = (p.rows + lc.rb - 1) / lc.rb;
+    lc.ok = lean_smem_bytes(p, lc) <= limit;
+    return lc;
+}
+
+size_t lean_smem_bytes(const ChainParams& p, const LeanConfig& lc) {
+    return (size_t)(lc.rb + 2) * lc.pitch * 4 + 2 * (size_t)p.hist_bins * 4 +
+           (size_t)lc.list_cap * 4 + (lc.colbank ? 0 : (size_t)(lc.rb + 2) * p.units_per_row * 4);
+}
+
+static int g_attr_dev_lean = -1;
+
+cudaError_t launch_stencil_lean(const ChainParams& p, const LeanConfig& lc, const uint16_t* raw,
+                                uint32_t n_frames, uint32_t frame_base, const CallOut& out,
+                                cudaStream_t stream) {
+    const unsigned long long n_tiles = (unsigned long long)n_frames * p.n_modules * lc.n_bands;
+    if (n_tiles == 0) return cudaSuccess;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (g_attr_dev_lean != dev) {
+        for (auto k : {stencil_lean_kernel<true, false>, stencil_lean_kernel<true, true>,
+                       stencil_lean_kernel<false, false>, stencil_lean_kernel<false, true>}) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kLeanSmemMax);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            if (e != cudaSuccess) return e;
+        }
+        g_attr_dev_lean = dev;
+    }
+    const size_t smem = lean_smem_bytes(p, lc);
+    const unsigned threads = lc.tx * lc.ty;
+    const uint32_t per_sm = lc.ctas_per_sm ? lc.ctas_per_sm : (smem <= kLeanSmemTwo ? 2u : 1u);
+    unsigned long long grid = (unsigned long long)device_sm_count() * per_sm;
+    if (grid > n_tiles) grid = n_tiles;
+    const bool corr = out.corrected != nullptr;
+    auto k = lc.colbank ? (corr ? stencil_lean_kernel<true, true> : stencil_lean_kernel<true, false>)
+                        : (corr ? stencil_lean_kernel<false, true> : stencil_lean_kernel<false, false>);
+    k<<<(unsigned)grid, threads, smem, stream>>>(p, raw, frame_base, out, lc, n_tiles);
+    return cudaGetLastError();
+}
+
+}  // namespace pd

@@ -21,7 +21,7 @@ _INCLUDE = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_PKG, "libpd.so")
 SOURCES = ["pd_api.cu", "pd_chain.cu", "pd_cm_mean.cu", "pd_eta.cu", "pd_fast.cu",
-           "pd_fused.cu", "pd_matched.cu", "pd_noalloc.cu", "pd_net.cu", "pd_net_tc.cu",
+           "pd_fused.cu", "pd_lean.cu", "pd_matched.cu", "pd_noalloc.cu", "pd_net.cu", "pd_net_tc.cu",
            "pd_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false",
@@ -93,7 +93,7 @@ class PdProfile(ctypes.Structure):
 
 class PdTuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
-                ("chunk_frames", "band_rows", "overlap", "two_pass")]
+                ("chunk_frames", "band_rows", "overlap", "two_pass", "kernels")]
 
 
 class PdBatchItem(ctypes.Structure):
@@ -455,16 +455,16 @@ def pd_get_tuning(ctx: Context) -> dict:
     t = PdTuning()
     _check(load().pd_get_tuning(ctx.handle, ctypes.byref(t)), "pd_get_tuning")
     return dict(chunk_frames=t.chunk_frames, band_rows=t.band_rows,
-                overlap=t.overlap, two_pass=t.two_pass)
+                overlap=t.overlap, two_pass=t.two_pass, kernels=t.kernels)
 
 
 def pd_set_tuning(ctx: Context, chunk_frames=0, band_rows=0, overlap=None,
-                  two_pass=None) -> None:
-    """Zero chunk_frames / band_rows and None overlap / two_pass keep the
-    context's current values."""
+                  two_pass=None, kernels=0) -> None:
+    """Zero chunk_frames / band_rows / kernels and None overlap / two_pass
+    keep the context's current values."""
     cur = pd_get_tuning(ctx)
     t = PdTuning(chunk_frames, band_rows, cur["overlap"] if overlap is None else overlap,
-                 cur["two_pass"] if two_pass is None else two_pass)
+                 cur["two_pass"] if two_pass is None else two_pass, kernels)
     _check(load().pd_set_tuning(ctx.handle, ctypes.byref(t)), "pd_set_tuning")
 
 
@@ -490,7 +490,8 @@ def pd_autotune(ctx: Context, frames_ptr: int, n_frames: int):
     _check(load().pd_autotune(ctx.handle, frames_ptr, n_frames, ctypes.byref(t),
                               ctypes.byref(us)), "pd_autotune")
     return (dict(chunk_frames=t.chunk_frames, band_rows=t.band_rows,
-                 overlap=t.overlap, two_pass=t.two_pass), float(us.value))
+                 overlap=t.overlap, two_pass=t.two_pass, kernels=t.kernels),
+            float(us.value))
 
 
 class Batch:

@@ -104,13 +104,15 @@ WORKLOADS = {
 }
 
 
+@pytest.mark.parametrize("kernels", [1, 2], ids=["lean_pair", "earlier_pair"])
 @pytest.mark.parametrize("name", list(WORKLOADS))
-def test_generated_workloads_bit_exact(name):
+def test_generated_workloads_bit_exact(name, kernels):
     det, n = WORKLOADS[name]
     ped, gain = synth.maps(det)
     raw, _ = synth.frames(det, ped, gain, 0, n)
     geom, thr = det.geometry(), det.thresholds()
     ctx = _ctx(geom, thr, ped, gain)
+    pd.pd_set_tuning(ctx, kernels=kernels)
     out = pd.process(ctx, pd.frames_to_device(raw), corrected=True, cm=True)
     torch.cuda.synchronize()
     ref = _oracle(geom, thr, ped, gain, raw, want_corrected=True)
@@ -159,6 +161,44 @@ def test_bank_flat_frames_overflow_candidates():
 def test_bank_unanchored_cut_generic_path():
     det = synth.cspad_2p2m(n_modules=2)
     _run_case(det, 2, thr_over=dict(cm_cut_adu=200.3))
+
+
+def test_bank_low_pedestals_keep_float_codes():
+    # pedestals near 100 ADU: d = raw - ped is not exact in binary32 over the
+    # whole window, so the bank median keeps its floating-point bin codes
+    det = synth.cspad_2p2m(n_modules=2, ped_mean=120.0, ped_sigma=30.0)
+    ref = _run_case(det, 2)
+    assert ref.n_hits > 0 and ref.cm.any()
+
+
+def test_bank_wide_pedestal_spread():
+    # pedestals spread over thousands of ADU: the integer codes do not fit
+    # 16-bit lanes and the context keeps the floating-point bank median
+    det = synth.cspad_2p2m(n_modules=2)
+    ped, gain = synth.maps(det)
+    ped = (ped + np.linspace(0.0, 6000.0, ped.size).reshape(ped.shape)).astype(np.float32)
+    raw, _ = synth.frames(det, ped, gain, 0, 2)
+    geom, thr = det.geometry(), det.thresholds()
+    ctx = _ctx(geom, thr, ped, gain)
+    out = pd.process(ctx, pd.frames_to_device(raw), corrected=True, cm=True)
+    torch.cuda.synchronize()
+    _compare(ctx, out, _oracle(geom, thr, ped, gain, raw, want_corrected=True), 2)
+
+
+def test_lean_stencil_candidate_list_overflow():
+    # a bright flat region: every pixel of it passes the seed threshold, more
+    # candidates than a tile's list holds, so the tile tests every own pixel
+    det = synth.cspad_2p2m(n_modules=1)
+    ped, gain = synth.maps(det)
+    raw, _ = synth.frames(det, ped, gain, 0, 2)
+    raw = raw.reshape(2, det.rows, det.cols)
+    raw[0, 10:60, 20:300] = np.minimum(raw[0, 10:60, 20:300].astype(np.int64) + 60, 65535)
+    geom, thr = det.geometry(), det.thresholds()
+    ctx = _ctx(geom, thr, ped, gain)
+    out = pd.process(ctx, pd.frames_to_device(raw), corrected=True, cm=True)
+    torch.cuda.synchronize()
+    ref = _oracle(geom, thr, ped, gain, raw, want_corrected=True)
+    _compare(ctx, out, ref, 2)
 
 
 def test_bank_min_count_not_reached():
@@ -329,7 +369,14 @@ def test_full_size_cspad_batch_sampled():
                                     dict(chunk_frames=5, band_rows=17, overlap=1, two_pass=1),
                                     # 82 loaded rows over 5 row lanes: more than 64 seed
                                     # candidates per thread, one CTA per SM
-                                    dict(chunk_frames=4, band_rows=80, overlap=0, two_pass=1)])
+                                    dict(chunk_frames=4, band_rows=80, overlap=0, two_pass=1),
+                                    # the lean stencil with 1- and 2-row bands (halo rows
+                                    # by the last row lanes), and the earlier pair
+                                    dict(chunk_frames=2, band_rows=1, overlap=1, two_pass=1),
+                                    dict(chunk_frames=3, band_rows=2, overlap=0, two_pass=1),
+                                    dict(chunk_frames=4, overlap=1, two_pass=1, kernels=2),
+                                    dict(chunk_frames=1, band_rows=9, overlap=0, two_pass=1,
+                                         kernels=2)])
 def test_results_independent_of_tuning(tuning):
     """Chunking, band height, the two-stream overlap and the choice between
     the one-kernel chain and the kernel pair change only the launch schedule:
@@ -364,3 +411,31 @@ def test_widest_module_band_stencil():
                          occupancy=0.02)
     ref = _run_case(det, 2)
     assert ref.n_hits > 0
+
+
+@pytest.mark.parametrize("kernels", [1, 2], ids=["lean_pair", "earlier_pair"])
+def test_histogram_bins_non_dyadic_width_on_gpu(kernels):
+    """e values next to the edges of 0.05 keV bins from -4 keV (not dyadic):
+    the pixel histogram holds them in the bins of the fused form
+    floor(fma(e, 1/w, -lo/w)) worked out in exact rationals by the oracle's
+    pin (the division form would put each in the neighbouring bin)."""
+    vals = [(0.20000001788139343, 84), (-0.9000000953674316, 62), (0.44999998807907104, 89),
+            (0.5499998927116394, 91), (-1.0000001192092896, 59), (-0.9500001072883606, 60),
+            (0.0, 80), (0.0, 80)]
+    C = len(vals)
+    geom = dict(n_modules=1, rows=1, cols=C, unit_rows=1, unit_cols=C, cm_mode=pd.PD_CM_NONE)
+    thr = dict(cm_cut_adu=100.0, zero_thr_kev=100.0, seed_thr_kev=100.0, photon_kev=1.0,
+               hist_lo_kev=-4.0, hist_bin_kev=0.05, hist_bins=1296)
+    ped = np.array([-v for v, _ in vals], np.float32).reshape(1, 1, C)
+    gain = np.ones((1, 1, C), np.float32)
+    raw = np.zeros((1, 1, 1, C), np.uint16)
+    ctx = _ctx(geom, thr, ped, gain)
+    pd.pd_set_tuning(ctx, kernels=kernels)
+    out = pd.process(ctx, pd.frames_to_device(raw), corrected=True, cm=True)
+    torch.cuda.synchronize()
+    ref = _oracle(geom, thr, ped, gain, raw, want_corrected=True)
+    _compare(ctx, out, ref, 1)
+    exp = np.zeros(1296, np.uint64)
+    for _, b in vals:
+        exp[b] += 1
+    np.testing.assert_array_equal(pd.pd_get_summary(ctx)[1], exp)
