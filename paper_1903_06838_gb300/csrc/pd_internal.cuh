@@ -170,6 +170,11 @@ int internal_fail(int code, const char* why);
 int internal_check_process_args(const pd_ctx* ctx, const uint16_t* frames, uint32_t n_frames,
                                 const pd_outputs* out, const char** why);
 uint32_t internal_cm_per_frame(const pd_ctx* ctx);
+int internal_ctx_device(const pd_ctx* ctx);
+// false when the context runs the one-kernel chain (common mode on chip)
+bool internal_uses_cm_scratch(const pd_ctx* ctx);
+// pd_create: resolve the no-allocation scratch on device `dev` (current)
+void noalloc_prepare(int dev);
 // The chain on `stream` only (no second stream), with caller-provided
 // common-mode storage of n_frames * cm_per_frame floats.
 int internal_run_sequential(pd_ctx* ctx, const uint16_t* frames, uint32_t n_frames,

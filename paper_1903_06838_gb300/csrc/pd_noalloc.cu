@@ -6,7 +6,11 @@
 // it with cudaMalloc when a call needs more.  Here the scratch is the
 // file-scope array g_cm_scratch instead, sized for kNoAllocMaxCm floats and
 // present on every device that loads this library, for the life of the
-// process.
+// process.  Its device address is resolved by pd_create on the context's
+// device (which allocates anyway); with CUDA's lazy module loading that
+// lookup is also what loads this file's module and commits the array, so a
+// no-allocation call made on a context's device finds the address cached and
+// loads nothing.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,15 +32,14 @@ static __device__ __align__(256) float g_cm_scratch[kNoAllocMaxCm];
 std::mutex g_mu;
 float* g_ptr[kMaxDevices] = {};
 
-// Device address of g_cm_scratch on the current device (first use on a
-// device resolves and caches it).
-int scratch_address(float** out, const char** why) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        *why = "no usable current device";
+// Device address of g_cm_scratch on device `dev`, which must be current
+// (the first use on a device resolves and caches it).
+int scratch_address(int dev, float** out, const char** why) {
+    if (dev < 0 || dev >= kMaxDevices) {
+        *why = "device index beyond the no-allocation table";
         return PD_ECUDA;
     }
+    cudaError_t e = cudaSuccess;
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_ptr[dev]) {
         void* p = nullptr;
@@ -53,19 +56,38 @@ int scratch_address(float** out, const char** why) {
 
 }  // namespace
 
+namespace pd {
+
+// Called by pd_create with the context's device current: resolves (and so,
+// under lazy loading, loads) the scratch there.  A failure is not fatal to
+// pd_create; the no-allocation call then tries again itself.
+void noalloc_prepare(int dev) {
+    float* p = nullptr;
+    const char* why = nullptr;
+    if (scratch_address(dev, &p, &why) != PD_OK) cudaGetLastError();
+}
+
+}  // namespace pd
+
 extern "C" int pd_process_noalloc(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frames,
                                   uint32_t frame_base, const pd_outputs* out, void* stream) {
     const char* why = nullptr;
     int rc = pd::internal_check_process_args(ctx, frames_dev, n_frames, out, &why);
     if (rc) return pd::internal_fail(rc, why);
+    // the scratch belongs to one device: the context's must be current
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != pd::internal_ctx_device(ctx))
+        return pd::internal_fail(PD_EINVAL,
+                                 "pd_process_noalloc: the context's device must be current");
     float* cm = out->cm;
-    if (!cm) {
+    // (the one-kernel chain keeps its common mode on chip: no scratch, no limit)
+    if (!cm && pd::internal_uses_cm_scratch(ctx)) {
         const uint64_t need = (uint64_t)n_frames * pd::internal_cm_per_frame(ctx);
         if (need > kNoAllocMaxCm)
             return pd::internal_fail(PD_EINVAL,
                                      "pd_process_noalloc: n_frames * cm_values_per_frame exceeds "
                                      "PD_NOALLOC_MAX_CM; split the call or pass out->cm");
-        rc = scratch_address(&cm, &why);
+        rc = scratch_address(dev, &cm, &why);
         if (rc) return pd::internal_fail(rc, why);
     }
     // g_cm_scratch needs no clearing: each common-mode value is written by
