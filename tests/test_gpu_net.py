@@ -43,6 +43,27 @@ def test_forward_matches_oracle_with_bf16_operands():
     assert np.abs(got - exact).max() < 0.05  # bfloat16 operands stay close
 
 
+def test_forward_full_size_sampled_against_oracle():
+    """2^17 + 1000 patches through chunks of 65 536 (each CTA runs several
+    conv and FC tiles, the TMEM buffers and mbarrier phases wrap, the next
+    tile's patches are prefetched, and the call crosses a chunk boundary with
+    a ragged tail): every 61st hit, which covers every CTA's later tiles,
+    equals the float64 oracle with the same bf16 operand rounding.  The
+    forward pass is per hit, so the oracle on the sample is exact."""
+    rng = np.random.default_rng(5)
+    P, flat = _params(4)
+    net = pd.pd_net_create(65536, seed=0)
+    pd.pd_net_set_params(net, flat)
+    n = (1 << 17) + 1000
+    x, *_ = _random_batch(rng, n)
+    got = learn.predict(net, torch.from_numpy(x).cuda()).cpu().numpy()
+    idx = np.arange(0, n, 61)
+    idx = np.union1d(idx, np.arange(n - 64, n))  # the ragged tail in full
+    ref, _ = onet.forward(P, x[idx].astype(np.float64), operand=onet.bf16)
+    np.testing.assert_allclose(got[idx], ref, rtol=2e-3, atol=2e-3)
+    assert np.isfinite(got).all()
+
+
 def test_gradients_match_float64_oracle():
     rng = np.random.default_rng(2)
     P, flat = _params(3)
