@@ -33,10 +33,12 @@ METRIC = ("frames/s and HBM GB/s (fraction of peak) on 2.2 Mpx frames; "
 FRAMES_PER_STEP = 1024
 HIT_BYTES = 24
 # DRAM bytes (read + write) per frame of each kernel, from the ncu capture
-# summarised in profiles/cspad_2p2m_chain.md; set an entry to None when its
-# kernel changes until it is captured again.
-NCU_TRAFFIC_PER_FRAME = {"stencil": None,
-                         "common_mode": None,
+# summarised in profiles/cspad_2p2m_chain.md (the kernel pair run back to
+# back on 21-frame chunks, caches not flushed between kernels, so the
+# stencil's re-read of raw is counted where it misses L2); set an entry to
+# None when its kernel changes until it is captured again.
+NCU_TRAFFIC_PER_FRAME = {"stencil": (106.228736e6 + 18.52544e6) / 21,
+                         "common_mode": (86.923264e6 + 3.517696e6) / 21,
                          "fused_chain": None}
 
 
@@ -58,10 +60,17 @@ def parse():
     ap.add_argument("--no-net", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cm-variants", action="store_true")
-    ap.add_argument("--only", choices=["serve", "batch", "net", "cm"], default=None,
+    ap.add_argument("--only", choices=["serve", "batch", "net", "cm", "link"], default=None,
                     help="run one section alone (for profiling) and print its JSON")
     ap.add_argument("--serve-rate", type=float, default=100000.0)
-    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--net-train-hits", type=int, default=1 << 22)
+    ap.add_argument("--net-steps", type=int, default=4096)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--link-seconds", type=float, default=75.0,
+                    help="--only link: seconds of back-to-back host -> device copies")
+    ap.add_argument("--serve-repeats", type=int, default=3)
+    ap.add_argument("--serve-pin", type=int, default=0,
+                    help="k > 0: the server's host threads pinned from the k-th allowed CPU on")
     return ap.parse_args()
 
 
@@ -390,10 +399,22 @@ def run_pd(args):
                        "api": "pd_process_host (page-locked host frames, hits back to host)"}
     if rank == 0 and ws == 1 and not args.no_cm_variants:
         line["cm_variants"] = cm_variants_run(args, dev, det, ped, gain, frames, nf, peak)
+    serve_summary = None
     if rank == 0 and ws == 1 and not args.no_serve:
         del frames, out
         torch.cuda.empty_cache()
         line["serve"] = serve_run(args, dev)
+        # the 80/20 mix in a few keys near the front of the line
+        m = line["serve"]["mix"]
+        summary = {"workload": "Poisson 100 kHz offered, 80% 704x768 / 20% 2.2 Mpx, "
+                               f"{args.serve_repeats} x {args.serve_seconds:g} s",
+                   "p50_us": [r["p50_us"] for r in m["repeats"]],
+                   "p99_us": [r["p99_us"] for r in m["repeats"]],
+                   "sustained_hz": [r["sustained_hz"] for r in m["repeats"]],
+                   "rejected": [r["frames_rejected"] for r in m["repeats"]],
+                   "h2d_link_gbs_after": [r["h2d_link_gbs_after"] for r in m["repeats"]],
+                   "h2d_offered_gbs": m["h2d_offered_gbs"]}
+        serve_summary = summary
     if rank == 0 and ws == 1 and not args.no_batch:
         line["single_asic_16"] = single_asic_run(args, dev)
         line["batch_mix_4096"] = batch_mix_run(args, dev, peak)
@@ -402,6 +423,9 @@ def run_pd(args):
         line["net"] = net_run(args, dev, read_peaks_all())
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(det, ped, gain, raw[:512])
+    if serve_summary is not None:
+        # last, so the line's tail (which a log keeps) holds the 80/20 mix
+        line["serve_mix_100khz"] = serve_summary
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -517,6 +541,37 @@ def h2d_bandwidth(dev, nbytes=1 << 30, reps=5):
     return nbytes * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
 
 
+def link_run(args, dev, chunk=32 << 20, host_bytes=2 << 30):
+    """Host -> device bandwidth over time under back-to-back copies of 32 MiB
+    from a 2 GiB page-locked buffer (the serving path's traffic), one figure
+    per second (CUDA events around groups of 16 copies)."""
+    import torch
+    src = torch.empty(host_bytes, dtype=torch.uint8, pin_memory=True)
+    src.fill_(1)
+    dst = torch.empty(chunk, dtype=torch.uint8, device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n = host_bytes // chunk
+    clocks = Clocks(dev.index or 0)
+    clocks.start()
+    k, t0, series = 0, time.time(), []
+    while time.time() - t0 < args.link_seconds:
+        t_sec, moved, ms = time.time(), 0, 0.0
+        while time.time() - t_sec < 1.0:
+            e0.record()
+            for _ in range(16):
+                off = (k % n) * chunk
+                dst.copy_(src[off:off + chunk], non_blocking=True)
+                k += 1
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms += e0.elapsed_time(e1)
+            moved += 16 * chunk
+        series.append([round(t_sec - t0, 1), round(moved / (ms / 1e3) / 1e9, 1)])
+    return {"workload": "back-to-back 32 MiB host -> device copies from a 2 GiB "
+                        "page-locked buffer", "seconds_gbs": series, "clocks": clocks.stop()}
+
+
 def serve_run(args, dev):
     """Streaming serve: Poisson arrivals at the target rate from page-locked
     rings, 80 % ePix100-sized 704x768 frames and 20 % 2.2 Mpx CSPAD frames,
@@ -527,7 +582,9 @@ def serve_run(args, dev):
 
     dets = [synth.epix_704x768(occupancy=0.001, occupancy_hi=0.02, seed=41),
             synth.cspad_2p2m(occupancy=0.001, occupancy_hi=0.02, seed=42)]
-    distinct, ring = 64, 512
+    # 128 frames per geometry: a larger page-locked ring (2.9 GB at 512) lowered
+    # the host -> device rate of sustained uploads on this platform
+    distinct, ring = 64, 128
     ctxs, frames = [], []
     for d in dets:
         ped, gain = synth.maps(d)
@@ -535,7 +592,7 @@ def serve_run(args, dev):
         frames.append(raw.reshape(distinct, -1))
         ctxs.append(pd.pd_create(d.geometry(), ped, gain, d.thresholds()))
     sv = pd.Server(ctxs, n_slots=8, max_batch_frames=32, ring_frames=ring,
-                   hits_per_frame=49152, max_uploading=1)
+                   hits_per_frame=49152, max_uploading=1, cpu_pin=args.serve_pin)
     for g in range(len(dets)):
         for k in range(ring):
             sv.ring_frame(g, k)[:] = frames[g][k % distinct]
@@ -545,13 +602,26 @@ def serve_run(args, dev):
         sv.replay(args.serve_rate, 0.3, mix=mix, seed=1)       # warm-up
         sv.drain(60.0)
         sv.reset_stats()
-        clocks = Clocks(dev.index or 0)
-        clocks.start()
-        sv.replay(args.serve_rate, args.serve_seconds, mix=mix, seed=2, first_id=1 << 32)
-        sv.drain(120.0)
-        clk = clocks.stop()
-        out[name] = _serve_line(sv.stats(), args, mix, link, clk)
-        sv.reset_stats()
+        runs = []
+        for rep in range(max(args.serve_repeats, 1)):
+            clocks = Clocks(dev.index or 0)
+            clocks.start()
+            sv.replay(args.serve_rate, args.serve_seconds, mix=mix, seed=2 + rep,
+                      first_id=(1 << 32) * (rep + 1))
+            sv.drain(120.0)
+            clk = clocks.stop()
+            offered = args.serve_rate * sum(w * f.shape[1] * 2 for w, f in zip(mix, frames)) / 1e9
+            runs.append(_serve_line(sv.stats(), args, mix, link, clk))
+            runs[-1]["h2d_offered_gbs"] = round(offered, 1)
+            # the link's bandwidth right after the run: under sustained copies
+            # the host -> device rate of this platform falls within a minute
+            runs[-1]["h2d_link_gbs_after"] = round(h2d_bandwidth(dev, 256 << 20, 8), 1)
+            sv.reset_stats()
+        out[name] = dict(runs[0], repeats=[{k: r[k] for k in ("sustained_hz", "p50_us", "p99_us",
+                                                               "max_us", "frames_rejected",
+                                                               "mean_batch_frames", "split_us",
+                                                               "replay_late", "h2d_link_gbs_after")}
+                                           for r in runs])
     sv.close()
     return out
 
@@ -560,9 +630,10 @@ def _serve_line(st, args, mix, link, clk):
     el = max(st["elapsed_s"], 1e-9)
     return {
         "workload": f"Poisson arrivals, {mix[0]:.0%} 704x768 / {mix[1]:.0%} 32x185x388, "
-                    "occupancy log-uniform 0.1-2%, page-locked rings pre-filled with 64 "
-                    "distinct frames per geometry; 8 slots, <= 32 frames per geometry per "
-                    "batch, 1 batch uploading at a time",
+                    "occupancy log-uniform 0.1-2%, page-locked rings of 128 frames per geometry "
+                    "pre-filled with 64 distinct frames; 8 slots, <= 32 frames per geometry per "
+                    "batch, 1 batch uploading at a time; host threads "
+                    + ("pinned to their own cores" if args.serve_pin else "not pinned"),
         "offered_hz": args.serve_rate, "seconds": args.serve_seconds,
         "frames_done": st["frames_done"], "frames_rejected": st["frames_rejected"],
         "sustained_hz": round(st["frames_done"] / el, 1),
@@ -575,6 +646,16 @@ def _serve_line(st, args, mix, link, clk):
         "compression_ratio": round(st["raw_bytes"] / max(st["compressed_bytes"], 1), 1),
         "hits_per_frame": round(st["hits"] / max(st["frames_done"], 1), 1),
         "latency": "arrival (scheduled Poisson time) to hits on the host",
+        "split_us": {"ring_wait_mean": round(st["wait_mean_us"], 1),
+                     "ring_wait_p99": round(st["wait_p99_us"], 1),
+                     "device_mean": round(st["device_mean_us"], 1),
+                     "device_p99": round(st["device_p99_us"], 1),
+                     "hit_copy_mean": round(st["fetch_mean_us"], 1),
+                     "batch_upload_mean": round(st["upload_mean_us"], 1),
+                     "batch_kernels_mean": round(st["run_mean_us"], 1),
+                     "encode_per_batch_mean": round(st["encode_mean_us"], 1)},
+        "replay_late": st["replay_late"],
+        "replay_late_max_us": round(st["replay_late_max_us"], 1),
         "clocks": clk,
     }
 
@@ -594,12 +675,22 @@ def net_run(args, dev, peaks):
 
     det = synth.asic_352x384(occupancy=0.005, occupancy_hi=0.05, cloud_sigma=0.2,
                              cloud_sigma_hi=0.5, seed=31)
-    hits_tr, ptr, _, lab_tr = learn.make_set(det, 40, 0)
-    hits_te, pte, (c_te, t_te, m_te), _ = learn.make_set(det, 12, 1000)
+    # training set of at least 2^22 generated hits, in chunks of frames
+    parts, first = [], 0
+    while sum(len(p[0]) for p in parts) < args.net_train_hits:
+        parts.append(learn.make_set(det, 300, first))
+        first += 300
+    hits_tr = np.concatenate([p[0] for p in parts])
+    ptr = torch.cat([p[1] for p in parts])
+    host_tr = tuple(np.concatenate([p[2][k] for p in parts]) for k in range(3))
+    lab_tr = tuple(torch.cat([p[3][k] for p in parts]) for k in range(3))
+    del parts
+    hits_te, pte, (c_te, t_te, m_te), _ = learn.make_set(det, 12, 1 << 20)
     batch = 4096
     net = pd.pd_net_create(1 << 16, seed=7)
     t0 = time.perf_counter()
-    learn.train(net, ptr, lab_tr, steps=800, batch=2048, lr=2e-3)
+    learn.train(net, ptr, lab_tr, steps=args.net_steps, batch=2048, lr=2e-3,
+                host_mask=host_tr[2])
     train_wall = time.perf_counter() - t0
     out = learn.predict(net, pte).cpu().numpy()
     single = m_te == 1
@@ -644,8 +735,8 @@ def net_run(args, dev, peaks):
             "disagreement_vs_classical": round(float((r["count"] != hits_te["count"]).mean()), 5),
             "agreement_with_truth": round(float((r["count"] == c_te).mean()), 4)}
         for cc, r in gates.items()}
-    # throughput: inference over 2^20 patches, training steps of 4096
-    n_inf = 1 << 20
+    # throughput: inference over 2^24 patches, training steps of 4096
+    n_inf = 1 << 24
     reps = (n_inf + pte.shape[0] - 1) // pte.shape[0]
     big = pte.repeat(reps, 1)[:n_inf].contiguous()
     o_big = torch.empty((n_inf, 7), dtype=torch.float32, device=dev)
@@ -686,8 +777,9 @@ def net_run(args, dev, peaks):
     tr_tf = 3 * batch * NET_FWD_FLOP / step_s / 1e12
     return {
         "workload": "352x384 ASIC, 8 keV, occupancy 0.5-5 %, cloud sigma 0.2-0.5 px; "
-                    "train 800 Adam steps of 2048 hits from 40 frames, test on 12 other "
-                    "frames",
+                    f"train {args.net_steps} Adam steps of 2048 hits drawn from "
+                    f"{first} frames, test on 12 other frames; inference timed on "
+                    "2^24 patches",
         "train_hits": int(ptr.shape[0]), "test_hits": int(len(hits_te)),
         "train_wall_s": round(train_wall, 2),
         "rms_offset_px": {"centre_of_mass": round(rms_com, 4), "network": round(rms_net, 4),
@@ -900,6 +992,8 @@ def run_only(args):
         raw, _ = synth.frames(det, ped, gain, 0, args.frames, truth=False)
         frames = pd.frames_to_device(raw).to(dev)
         res = cm_variants_run(args, dev, det, ped, gain, frames, args.frames, peak)
+    elif args.only == "link":
+        res = link_run(args, dev)
     elif args.only == "batch":
         res = {"single_asic_16": single_asic_run(args, dev),
                "batch_mix_4096": batch_mix_run(args, dev, peak)}

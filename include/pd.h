@@ -426,6 +426,16 @@ int pd_net_gradients(pd_net* net, const float* patches_dev, const uint8_t* count
                      const float* targets_dev, const uint8_t* mask_dev, uint32_t n,
                      float n_reg, float lambda, float* grads_dev, float* loss_dev,
                      void* stream);
+/* Rows idx_dev[0..n) (device, each < the set's size) of a training set
+ * (patches float [][25], counts u8, targets float [][2], mask u8, all
+ * device) into the batch arrays *_out (device, n rows each), for
+ * pd_net_train_step without host work between steps.  Asynchronous on
+ * `stream`.  Training batches are this implementation's (the paper trains
+ * nothing). */
+int pd_net_take(const float* patches_dev, const uint8_t* counts_dev, const float* targets_dev,
+                const uint8_t* mask_dev, const uint32_t* idx_dev, uint32_t n,
+                float* patches_out, uint8_t* counts_out, float* targets_out,
+                uint8_t* mask_out, void* stream);
 /* pd_net_gradients followed by one Adam step (beta 0.9 / 0.999, eps 1e-8). */
 int pd_net_train_step(pd_net* net, const float* patches_dev, const uint8_t* counts_dev,
                       const float* targets_dev, const uint8_t* mask_dev, uint32_t n,
@@ -470,7 +480,14 @@ typedef struct {
     uint32_t max_uploading;     /* batches still uploading frames at most;  *
                                  * 0 = 1 (admission holds frames in the    *
                                  * ring while the link is this busy)       */
-    uint32_t reserved;          /* 0 */
+    uint32_t cpu_pin;           /* 0: host threads unpinned; c > 0: the     *
+                                 * dispatcher runs on the (c-1)-th CPU the   *
+                                 * process may use, encoder i on the         *
+                                 * (c+i)-th, and the thread inside           *
+                                 * pd_server_replay on the (c+encoders)-th   *
+                                 * (modulo their number; Linux affinity,     *
+                                 * the replaying thread's own mask is put    *
+                                 * back when it returns)                     */
 } pd_serve_config;
 
 typedef struct {
@@ -479,6 +496,17 @@ typedef struct {
     uint64_t raw_bytes, compressed_bytes, hits;
     double elapsed_s;            /* first arrival to last completion        */
     double p50_us, p99_us, max_us, mean_us;
+    /* latency split per frame: queued in the ring (arrival to batch issue),
+     * issue to hit counts on the host (upload, kernels, count copy), then
+     * to hits on the host (hit copy) */
+    double wait_mean_us, wait_p99_us, device_mean_us, device_p99_us, fetch_mean_us;
+    double encode_mean_us;       /* per batch and geometry: hits on the host
+                                  * to all its frames encoded               */
+    uint64_t replay_late;        /* replayed arrivals reached > 20 us late  */
+    double replay_late_max_us;
+    /* per batch on the device clock: the frames' upload, then the kernels
+     * and the hit-count copy */
+    double upload_mean_us, run_mean_us;
 } pd_serve_stats;
 
 int pd_server_create(pd_ctx* const* ctxs, uint32_t n_geometries, const pd_serve_config* cfg,

@@ -254,6 +254,26 @@ __global__ void loss_kernel(const float* __restrict__ out, const uint8_t* __rest
     if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, l);
 }
 
+// rows idx[i] of a training set into batch row i (one thread per float of a
+// patch row, the labels by the row's first thread)
+__global__ void take_kernel(const float* __restrict__ patches, const uint8_t* __restrict__ counts,
+                            const float* __restrict__ targets, const uint8_t* __restrict__ mask,
+                            const uint32_t* __restrict__ idx, uint32_t n,
+                            float* __restrict__ p_out, uint8_t* __restrict__ c_out,
+                            float* __restrict__ t_out, uint8_t* __restrict__ m_out) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (uint64_t)n * NPOS) return;
+    const uint32_t i = (uint32_t)(t / NPOS), k = (uint32_t)(t % NPOS);
+    const uint32_t j = idx[i];
+    p_out[t] = patches[(size_t)j * NPOS + k];
+    if (k == 0) {
+        c_out[i] = counts[j];
+        m_out[i] = mask[j];
+        t_out[2 * (size_t)i] = targets[2 * (size_t)j];
+        t_out[2 * (size_t)i + 1] = targets[2 * (size_t)j + 1];
+    }
+}
+
 __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ gr,
                             float* __restrict__ m, float* __restrict__ v, int n, float lr,
                             float b1, float b2, float c1, float c2, float eps) {
@@ -537,6 +557,19 @@ int pd_net_gradients(pd_net* n, const float* patches, const uint8_t* counts, con
     if (!e && grads_dev)
         e = cudaMemcpyAsync(grads_dev, n->gw, NPARAM * 4, cudaMemcpyDeviceToDevice, s);
     return e == cudaSuccess ? PD_OK : net_cuda(e, "pd_net_gradients");
+}
+
+int pd_net_take(const float* patches, const uint8_t* counts, const float* targets,
+                const uint8_t* mask, const uint32_t* idx, uint32_t count, float* p_out,
+                uint8_t* c_out, float* t_out, uint8_t* m_out, void* stream) {
+    if (!count) return PD_OK;
+    if (!patches || !counts || !targets || !mask || !idx || !p_out || !c_out || !t_out || !m_out)
+        return net_fail(PD_EINVAL, "pd_net_take: NULL argument");
+    const uint64_t threads = (uint64_t)count * NPOS;
+    take_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        patches, counts, targets, mask, idx, count, p_out, c_out, t_out, m_out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PD_OK : net_cuda(e, "pd_net_take");
 }
 
 int pd_net_train_step(pd_net* n, const float* patches, const uint8_t* counts, const float* targets,

@@ -16,6 +16,8 @@
 // frame, encoded compactly, and timed from arrival to hits on the host.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <pthread.h>
+#include <sched.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -42,6 +44,27 @@ int64_t now_ns() {
         .count();
 }
 
+// Pin a thread to the k-th CPU (modulo their number) of the CPUs this
+// process may run on (a container's CPU set is often a subset of the online
+// CPUs); false if the system refuses (the thread then keeps its mask).
+bool pin_to_cpu(pthread_t th, uint32_t k) {
+    cpu_set_t allowed;
+    if (sched_getaffinity(0, sizeof(allowed), &allowed) != 0) return false;
+    const int n = CPU_COUNT(&allowed);
+    if (n <= 0) return false;
+    int want = (int)(k % (uint32_t)n), cpu = -1;
+    for (int c = 0; c < CPU_SETSIZE; c++)
+        if (CPU_ISSET(c, &allowed) && want-- == 0) {
+            cpu = c;
+            break;
+        }
+    if (cpu < 0) return false;
+    cpu_set_t set;
+    CPU_ZERO(&set);
+    CPU_SET(cpu, &set);
+    return pthread_setaffinity_np(th, sizeof(set), &set) == 0;
+}
+
 enum : uint8_t { kFree = 0, kCommitted = 1, kInFlight = 2, kAcquired = 3 };
 
 struct Ring {
@@ -66,7 +89,7 @@ enum : int { kSlotFree = 0, kSlotRunning = 1, kSlotHits = 2, kSlotEncoding = 3 }
 
 struct DevSlot {
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev_up = nullptr, ev_counts = nullptr, ev_hits = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_up = nullptr, ev_counts = nullptr, ev_hits = nullptr;
     bool uploaded = false;            // the batch's frames are on the device
     pd_batch* batch = nullptr;
     std::vector<uint16_t*> d_frames;  // per geometry
@@ -76,19 +99,31 @@ struct DevSlot {
     std::vector<pd_hit*> h_hits;      // page-locked
     std::atomic<int> state{kSlotFree};
     std::atomic<uint32_t> tasks_left{0};
-    int64_t t_done = 0;                         // hits on the host
+    int64_t t_issue = 0, t_counts = 0, t_done = 0;  // issued, counts seen, hits on the host
     std::vector<std::vector<Pending>> frames;   // per geometry, batch order
-    std::vector<std::vector<pd_hit>> grouped;   // per geometry, hits by frame
-    std::vector<std::vector<uint32_t>> offset;  // per geometry, frames + 1
 };
 
-// Encoder work: group a geometry's hits by frame (frame < 0), or sort and
-// encode one frame.
-struct Task {
-    DevSlot* slot;
-    uint32_t geom;
-    int32_t frame;
+// One geometry's hits of a finished batch, grouped by frame.  The encoders
+// own it once it is built, so that the device slot is free again before
+// the frames are encoded.
+struct Job {
+    uint32_t geom = 0;
+    int64_t t_done = 0;                 // hits on the host
+    std::vector<Pending> frames;        // batch order
+    std::vector<pd_hit> grouped;        // hits by frame
+    std::vector<uint32_t> offset;       // frames + 1
+    std::atomic<uint32_t> ranges_left{0};
 };
+
+// Encoder work: group a slot's hits of one geometry (slot set), or sort and
+// encode frames [first, last) of a job.
+struct Task {
+    DevSlot* slot = nullptr;
+    std::shared_ptr<Job> job;
+    uint32_t geom = 0, first = 0, last = 0;
+};
+
+constexpr uint32_t kEncodeRange = 8;  // frames per encode task
 
 struct FrameResult {
     uint32_t geom = 0;
@@ -182,6 +217,10 @@ struct pd_server {
     std::atomic<int> error{PD_OK};
     std::unordered_map<uint64_t, FrameResult> results;
     std::vector<double> latencies;
+    std::vector<double> lat_wait, lat_device;  // per frame: ring queue, issue to counts
+    double sum_fetch_us = 0, sum_encode_us = 0, replay_late_max_us = 0;
+    double sum_upload_us = 0, sum_run_us = 0;  // per batch, device clock
+    uint64_t encoded_batches = 0, replay_late = 0, timed_batches = 0;
     uint64_t committed = 0, done = 0, rejected = 0, raw_bytes = 0, comp_bytes = 0, hits = 0;
     uint64_t batches = 0, max_batch_seen = 0;
     int64_t t_first = 0, t_last = 0;
@@ -197,6 +236,7 @@ void destroy_slot(DevSlot& s) {
     for (auto p : s.h_hits) cudaFreeHost(p);
     cudaFreeHost(s.h_nhits);
     if (s.batch) pd_batch_destroy(s.batch);
+    if (s.ev_start) cudaEventDestroy(s.ev_start);
     if (s.ev_up) cudaEventDestroy(s.ev_up);
     if (s.ev_counts) cudaEventDestroy(s.ev_counts);
     if (s.ev_hits) cudaEventDestroy(s.ev_hits);
@@ -209,6 +249,7 @@ bool issue(pd_server* sv, DevSlot& s) {
     const uint32_t G = (uint32_t)sv->rings.size();
     std::vector<std::pair<uint32_t, uint32_t>> take(G);  // (first ring slot, count)
     uint32_t total = 0;
+    int64_t t_issue = 0;
     {
         std::lock_guard<std::mutex> lock(sv->mu);
         for (uint32_t g = 0; g < G; g++) {
@@ -225,6 +266,7 @@ bool issue(pd_server* sv, DevSlot& s) {
             total += n;
         }
         if (!total) return false;
+        t_issue = now_ns();
         for (uint32_t g = 0; g < G; g++) {
             s.frames[g].clear();
             Ring& r = sv->rings[g];
@@ -237,6 +279,7 @@ bool issue(pd_server* sv, DevSlot& s) {
         sv->batches++;
     }
     std::vector<pd_batch_item> items;
+    if (cudaEventRecord(s.ev_start, s.stream) != cudaSuccess) sv->error.store(PD_ECUDA);
     for (uint32_t g = 0; g < G; g++) {
         const uint32_t n = take[g].second;
         if (!n) continue;
@@ -266,6 +309,7 @@ bool issue(pd_server* sv, DevSlot& s) {
             sv->error.store(PD_ECUDA);
     }
     if (cudaEventRecord(s.ev_counts, s.stream) != cudaSuccess) sv->error.store(PD_ECUDA);
+    s.t_issue = t_issue;
     s.state.store(kSlotRunning);
     return true;
 }
@@ -274,8 +318,15 @@ bool issue(pd_server* sv, DevSlot& s) {
 // ring slots are released; download exactly the hits.
 void fetch_hits(pd_server* sv, DevSlot& s) {
     const uint32_t cap = sv->cfg.max_batch_frames * sv->cfg.hits_per_frame;
+    s.t_counts = now_ns();
+    float up_ms = 0, run_ms = 0;
+    cudaEventElapsedTime(&up_ms, s.ev_start, s.ev_up);
+    cudaEventElapsedTime(&run_ms, s.ev_up, s.ev_counts);
     {
         std::lock_guard<std::mutex> lock(sv->mu);
+        sv->sum_upload_us += up_ms * 1e3;
+        sv->sum_run_us += run_ms * 1e3;
+        sv->timed_batches++;
         for (uint32_t g = 0; g < (uint32_t)sv->rings.size(); g++)
             for (const Pending& p : s.frames[g]) sv->rings[g].state[p.ring_slot] = kFree;
     }
@@ -311,9 +362,16 @@ void hits_arrived(pd_server* sv, DevSlot& s) {
         std::lock_guard<std::mutex> lock(sv->mu);
         for (uint32_t g = 0; g < G; g++) {
             if (s.frames[g].empty()) continue;
-            for (const Pending& p : s.frames[g])
+            for (const Pending& p : s.frames[g]) {
                 sv->latencies.push_back((t_done - p.t_arrival) / 1e3);
-            tasks.push_back({&s, g, -1});
+                sv->lat_wait.push_back((s.t_issue - p.t_arrival) / 1e3);
+                sv->lat_device.push_back((s.t_counts - s.t_issue) / 1e3);
+                sv->sum_fetch_us += (t_done - s.t_counts) / 1e3;
+            }
+            Task t;
+            t.slot = &s;
+            t.geom = g;
+            tasks.push_back(t);
         }
         sv->t_last = t_done;
     }
@@ -323,68 +381,85 @@ void hits_arrived(pd_server* sv, DevSlot& s) {
     push_tasks(sv, tasks);
 }
 
-void task_done(DevSlot& s, uint32_t n = 1) {
-    if (s.tasks_left.fetch_sub(n) == n) s.state.store(kSlotFree);
+// The last group task of a batch frees its slot.
+void task_done(DevSlot& s) {
+    if (s.tasks_left.fetch_sub(1) == 1) s.state.store(kSlotFree);
 }
 
 void group_task(pd_server* sv, DevSlot& s, uint32_t g) {
     const uint32_t cap = sv->cfg.max_batch_frames * sv->cfg.hits_per_frame;
     if (s.h_nhits[g] > cap) sv->error.store(PD_EOVERFLOW);
     const uint32_t n = std::min(s.h_nhits[g], cap);
-    const uint32_t F = (uint32_t)s.frames[g].size();
+    auto job = std::make_shared<Job>();
+    job->geom = g;
+    job->t_done = s.t_done;
+    job->frames = s.frames[g];
+    const uint32_t F = (uint32_t)job->frames.size();
     const pd_hit* h = s.h_hits[g];
-    std::vector<uint32_t>& off = s.offset[g];
+    std::vector<uint32_t>& off = job->offset;
     off.assign(F + 1, 0);
     for (uint32_t i = 0; i < n; i++)
         if (h[i].frame < F) off[h[i].frame + 1]++;
     for (uint32_t k = 0; k < F; k++) off[k + 1] += off[k];
-    std::vector<pd_hit>& out = s.grouped[g];
+    std::vector<pd_hit>& out = job->grouped;
     out.resize(off[F]);
     std::vector<uint32_t> at(off.begin(), off.end() - 1);
     for (uint32_t i = 0; i < n; i++)
         if (h[i].frame < F) out[at[h[i].frame]++] = h[i];
+    task_done(s);  // the slot's buffers are no longer read
     std::vector<Task> t;
-    for (uint32_t k = 0; k < F; k++) t.push_back({&s, g, (int32_t)k});
-    s.tasks_left.fetch_add(F);
+    for (uint32_t k = 0; k < F; k += kEncodeRange) {
+        Task x;
+        x.job = job;
+        x.geom = g;
+        x.first = k;
+        x.last = std::min(F, k + kEncodeRange);
+        t.push_back(x);
+    }
+    job->ranges_left.store((uint32_t)t.size());
     push_tasks(sv, t);
-    task_done(s);
 }
 
-void frame_task(pd_server* sv, DevSlot& s, uint32_t g, uint32_t k) {
+void encode_task(pd_server* sv, Job& job, uint32_t first, uint32_t last) {
     thread_local std::vector<uint64_t> order, tmp;
-    const std::vector<uint32_t>& off = s.offset[g];
-    const pd_hit* h = s.grouped[g].data() + off[k];
-    const uint32_t n = off[k + 1] - off[k];
-    sort_by_pixel(h, n, order, tmp);
-    FrameResult res;
-    res.geom = g;
-    res.n_hits = n;
-    size_t cb;
-    if (sv->cfg.keep_hits) {
-        cb = encode_sorted(h, order.data(), n, nullptr, 0);
-        res.stream.resize(cb);
-        encode_sorted(h, order.data(), n, res.stream.data(), cb);
-        res.hits.resize(n);
-        for (uint32_t i = 0; i < n; i++) {
-            res.hits[i] = h[(uint32_t)order[i]];
-            res.hits[i].frame = (uint32_t)s.frames[g][k].id;
-        }
-    } else {
-        cb = encode_sorted(h, order.data(), n, nullptr, 0);
-    }
-    const Pending& p = s.frames[g][k];
-    {
-        std::lock_guard<std::mutex> lock(sv->mu);
-        sv->comp_bytes += cb;
-        sv->raw_bytes += (size_t)sv->rings[g].frame_px * 2;
-        sv->hits += n;
-        sv->done++;
+    const uint32_t g = job.geom;
+    size_t comp = 0;
+    uint64_t hits = 0;
+    std::vector<std::pair<uint64_t, FrameResult>> kept;
+    for (uint32_t k = first; k < last; k++) {
+        const pd_hit* h = job.grouped.data() + job.offset[k];
+        const uint32_t n = job.offset[k + 1] - job.offset[k];
+        sort_by_pixel(h, n, order, tmp);
+        const size_t cb = encode_sorted(h, order.data(), n, nullptr, 0);
+        comp += cb;
+        hits += n;
         if (sv->cfg.keep_hits) {
-            res.latency_us = (s.t_done - p.t_arrival) / 1e3;
-            sv->results[p.id] = std::move(res);
+            const Pending& p = job.frames[k];
+            FrameResult res;
+            res.geom = g;
+            res.n_hits = n;
+            res.stream.resize(cb);
+            encode_sorted(h, order.data(), n, res.stream.data(), cb);
+            res.hits.resize(n);
+            for (uint32_t i = 0; i < n; i++) {
+                res.hits[i] = h[(uint32_t)order[i]];
+                res.hits[i].frame = (uint32_t)p.id;
+            }
+            res.latency_us = (job.t_done - p.t_arrival) / 1e3;
+            kept.emplace_back(p.id, std::move(res));
         }
     }
-    task_done(s);
+    const bool last_range = job.ranges_left.fetch_sub(1) == 1;
+    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->comp_bytes += comp;
+    sv->raw_bytes += (uint64_t)(last - first) * sv->rings[g].frame_px * 2;
+    sv->hits += hits;
+    sv->done += last - first;
+    for (auto& kv : kept) sv->results[kv.first] = std::move(kv.second);
+    if (last_range) {
+        sv->sum_encode_us += (now_ns() - job.t_done) / 1e3;
+        sv->encoded_batches++;
+    }
 }
 
 void encoder_loop(pd_server* sv) {
@@ -397,10 +472,10 @@ void encoder_loop(pd_server* sv) {
             t = sv->queue.front();
             sv->queue.pop_front();
         }
-        if (t.frame < 0)
+        if (t.slot)
             group_task(sv, *t.slot, t.geom);
         else
-            frame_task(sv, *t.slot, t.geom, (uint32_t)t.frame);
+            encode_task(sv, *t.job, t.first, t.last);
     }
 }
 
@@ -522,11 +597,10 @@ int pd_server_create(pd_ctx* const* ctxs, uint32_t n_geometries, const pd_serve_
         if (rc) break;
         DevSlot& s = *sp;
         s.frames.resize(n_geometries);
-        s.grouped.resize(n_geometries);
-        s.offset.resize(n_geometries);
         bool ok = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess &&
-                  cudaEventCreateWithFlags(&s.ev_up, cudaEventDisableTiming) == cudaSuccess &&
-                  cudaEventCreateWithFlags(&s.ev_counts, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreate(&s.ev_start) == cudaSuccess &&
+                  cudaEventCreate(&s.ev_up) == cudaSuccess &&
+                  cudaEventCreate(&s.ev_counts) == cudaSuccess &&
                   cudaEventCreateWithFlags(&s.ev_hits, cudaEventDisableTiming) == cudaSuccess &&
                   cudaMallocHost(&s.h_nhits, n_geometries * 4) == cudaSuccess;
         uint64_t cm_vals = 0;
@@ -560,6 +634,13 @@ int pd_server_create(pd_ctx* const* ctxs, uint32_t n_geometries, const pd_serve_
     if (!n_enc) n_enc = std::max(1u, std::min(8u, std::thread::hardware_concurrency() / 2));
     for (uint32_t i = 0; i < n_enc; i++) sv->encoders.emplace_back(encoder_loop, sv);
     sv->dispatcher = std::thread(dispatch_loop, sv);
+    if (cfg->cpu_pin) {
+        // dedicated cores keep the dispatcher and encoders off the cores other
+        // work of the host uses (latency tails came from sharing them)
+        pin_to_cpu(sv->dispatcher.native_handle(), cfg->cpu_pin - 1);
+        for (uint32_t i = 0; i < n_enc; i++)
+            pin_to_cpu(sv->encoders[i].native_handle(), cfg->cpu_pin + i);
+    }
     *out = sv;
     return PD_OK;
 }
@@ -633,12 +714,25 @@ int pd_server_replay(pd_server* sv, double rate_hz, double duration_s, const flo
         acc += (mix ? std::max(0.0f, mix[g]) : 1.0) / tot;
         cdf[g] = acc;
     }
+    // the replaying thread on its own core while it runs (mask put back after)
+    cpu_set_t old_mask;
+    const bool pinned = sv->cfg.cpu_pin &&
+                        pthread_getaffinity_np(pthread_self(), sizeof(old_mask), &old_mask) == 0 &&
+                        pin_to_cpu(pthread_self(),
+                                   sv->cfg.cpu_pin + (uint32_t)sv->encoders.size());
+    struct Restore {
+        bool on;
+        cpu_set_t* m;
+        ~Restore() {
+            if (on) pthread_setaffinity_np(pthread_self(), sizeof(*m), m);
+        }
+    } restore{pinned, &old_mask};
     std::mt19937_64 rng(seed);
     std::exponential_distribution<double> gap(rate_hz);
     std::uniform_real_distribution<double> pick(0.0, 1.0);
     const int64_t t0 = now_ns(), t_end = t0 + (int64_t)(duration_s * 1e9);
-    double t = 0;
-    uint64_t id = first_id;
+    double t = 0, late_max = 0;
+    uint64_t id = first_id, n_late = 0;
     while (true) {
         t += gap(rng);
         const int64_t ta = t0 + (int64_t)(t * 1e9);
@@ -646,12 +740,22 @@ int pd_server_replay(pd_server* sv, double rate_hz, double duration_s, const flo
         const double u = pick(rng);
         uint32_t g = 0;
         while (g + 1 < G && u > cdf[g]) g++;
-        while (now_ns() < ta) {
+        int64_t tn;
+        while ((tn = now_ns()) < ta) {
         }
+        // arrivals the producer reached late (it was descheduled or held up)
+        const double late_us = (tn - ta) / 1e3;
+        if (late_us > 20.0) n_late++;
+        late_max = std::max(late_max, late_us);
         uint16_t* ptr = nullptr;
         uint32_t slot = 0;
         if (pd_server_acquire(sv, g, &ptr, &slot) != PD_OK) continue;  // ring full: dropped
         commit_at(sv, g, slot, id++, ta);
+    }
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->replay_late += n_late;
+        sv->replay_late_max_us = std::max(sv->replay_late_max_us, late_max);
     }
     return sv->error.load();
 }
@@ -694,7 +798,24 @@ int pd_server_stats(pd_server* sv, pd_serve_stats* st) {
         double s = 0;
         for (double x : l) s += x;
         st->mean_us = s / l.size();
+        for (int k = 0; k < 2; k++) {
+            std::vector<double> v = k ? sv->lat_device : sv->lat_wait;
+            std::sort(v.begin(), v.end());
+            double m = 0;
+            for (double x : v) m += x;
+            const double p99 = v[std::min(v.size() - 1, (size_t)(0.99 * (v.size() - 1) + 0.5))];
+            (k ? st->device_mean_us : st->wait_mean_us) = m / v.size();
+            (k ? st->device_p99_us : st->wait_p99_us) = p99;
+        }
+        st->fetch_mean_us = sv->sum_fetch_us / l.size();
     }
+    st->encode_mean_us = sv->encoded_batches ? sv->sum_encode_us / sv->encoded_batches : 0.0;
+    if (sv->timed_batches) {
+        st->upload_mean_us = sv->sum_upload_us / sv->timed_batches;
+        st->run_mean_us = sv->sum_run_us / sv->timed_batches;
+    }
+    st->replay_late = sv->replay_late;
+    st->replay_late_max_us = sv->replay_late_max_us;
     return PD_OK;
 }
 
@@ -702,6 +823,11 @@ int pd_server_reset_stats(pd_server* sv) {
     if (!sv) return pd::internal_fail(PD_EINVAL, "NULL server");
     std::lock_guard<std::mutex> lock(sv->mu);
     sv->latencies.clear();
+    sv->lat_wait.clear();
+    sv->lat_device.clear();
+    sv->sum_fetch_us = sv->sum_encode_us = sv->replay_late_max_us = 0;
+    sv->sum_upload_us = sv->sum_run_us = 0;
+    sv->encoded_batches = sv->replay_late = sv->timed_batches = 0;
     sv->results.clear();
     sv->committed -= sv->done;
     sv->done = 0;

@@ -16,29 +16,39 @@ from . import pd, synth
 
 def label_hits(det: synth.Detector, hits: np.ndarray, photons: np.ndarray):
     """(counts u8, targets float32 [n, 2], mask u8) for each hit."""
-    C = det.cols
-    mpx = det.rows * det.cols
-    # photons indexed by (frame, module, landing row, landing col)
-    key = {}
-    for i, ph in enumerate(photons):
-        r, c = int(ph["y"]), int(ph["x"])
-        key.setdefault((int(ph["frame"]), int(ph["module"]), r, c), []).append(i)
+    C, R, M = det.cols, det.rows, det.n_modules
+    mpx = R * C
+    # photons keyed by (frame, module, landing row, landing col), sorted
+    px = np.floor(photons["x"]).astype(np.int64)
+    py = np.floor(photons["y"]).astype(np.int64)
+    pkey = ((photons["frame"].astype(np.int64) * M + photons["module"].astype(np.int64)) * R
+            + py) * C + px
+    order = np.argsort(pkey, kind="stable")
+    skey = pkey[order]
     n = len(hits)
-    counts = np.zeros(n, np.uint8)
+    m, within = np.divmod(hits["pixel"].astype(np.int64), mpx)
+    r0, c0 = np.divmod(within, C)
+    base = hits["frame"].astype(np.int64) * M + m
+    total = np.zeros(n, np.int64)
+    first = np.full(n, -1, np.int64)  # a photon of the window (for single ones)
+    for dr in (-1, 0, 1):
+        for dc in (-1, 0, 1):
+            r, c = r0 + dr, c0 + dc
+            ok = (r >= 0) & (r < R) & (c >= 0) & (c < C)
+            k = (base * R + r) * C + c
+            lo = np.searchsorted(skey, k, "left")
+            hi = np.searchsorted(skey, k, "right")
+            cnt = np.where(ok, hi - lo, 0)
+            take = (cnt > 0) & (first < 0)
+            first[take] = order[lo[take]]
+            total += cnt
+    counts = np.minimum(total, 4).astype(np.uint8)
+    single = total == 1
     tgt = np.zeros((n, 2), np.float32)
-    mask = np.zeros(n, np.uint8)
-    for j, h in enumerate(hits):
-        m, within = divmod(int(h["pixel"]), mpx)
-        r0, c0 = divmod(within, C)
-        sel = []
-        for dr in (-1, 0, 1):
-            for dc in (-1, 0, 1):
-                sel += key.get((int(h["frame"]), m, r0 + dr, c0 + dc), [])
-        counts[j] = min(len(sel), 4)
-        if len(sel) == 1:
-            ph = photons[sel[0]]
-            tgt[j] = (ph["x"] - (c0 + 0.5), ph["y"] - (r0 + 0.5))
-            mask[j] = 1
+    ph = photons[first[single]]
+    tgt[single, 0] = ph["x"] - (c0[single] + 0.5)
+    tgt[single, 1] = ph["y"] - (r0[single] + 0.5)
+    mask = single.astype(np.uint8)
     return counts, tgt, mask
 
 
@@ -59,13 +69,14 @@ def hits_and_patches(ctx, det, frames_dev, frame_base=0):
 
 
 def make_set(det: synth.Detector, n_frames: int, first_frame: int = 0):
-    """Generated frames -> (hits, patches on device, labels)."""
+    """Generated frames -> (hits, patches on device, host labels, device labels)."""
     import torch
     ped, gain = synth.maps(det)
     raw, photons = synth.frames(det, ped, gain, first_frame, n_frames)
     ctx = pd.pd_create(det.geometry(), ped, gain, det.thresholds())
     dev = pd.frames_to_device(raw)
     hits, patches, _ = hits_and_patches(ctx, det, dev, first_frame)
+    del dev
     counts, tgt, mask = label_hits(det, hits, photons)
     dev_labels = (torch.from_numpy(counts).cuda(), torch.from_numpy(tgt).cuda(),
                   torch.from_numpy(mask).cuda())
@@ -73,26 +84,35 @@ def make_set(det: synth.Detector, n_frames: int, first_frame: int = 0):
 
 
 def train(net, patches, dev_labels, steps: int, batch: int = 2048, lr: float = 2e-3,
-          lam: float = 10.0, seed: int = 0):
-    """Adam steps over shuffled mini-batches; returns the loss per step."""
+          lam: float = 10.0, seed: int = 0, host_mask=None):
+    """Adam steps over random mini-batches; returns the loss per step.  Every
+    step's batch indices are drawn up front and uploaded once; each step's
+    rows are gathered on the device (pd_net_take) and the losses stay on the
+    device until the end, so the steps run back to back with no host work
+    between them."""
     import torch
     counts, tgt, mask = dev_labels
     n = patches.shape[0]
-    g = torch.Generator(device="cpu").manual_seed(seed)
-    loss = torch.zeros(1, dtype=torch.float32, device=patches.device)
-    losses = []
+    dev = patches.device
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, n, (steps, batch), dtype=np.int64).astype(np.uint32)
+    m_host = host_mask if host_mask is not None else mask.cpu().numpy()
+    n_reg = m_host[idx].astype(np.int64).sum(axis=1)
+    idx_dev = torch.from_numpy(idx.view(np.int32)).to(dev)
+    x = torch.empty((batch, 25), dtype=torch.float32, device=dev)
+    c = torch.empty(batch, dtype=torch.uint8, device=dev)
+    t = torch.empty((batch, 2), dtype=torch.float32, device=dev)
+    m = torch.empty(batch, dtype=torch.uint8, device=dev)
+    losses = torch.zeros(max(steps, 1), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
     for s in range(steps):
-        idx = torch.randint(0, n, (batch,), generator=g).to(patches.device)
-        x = patches[idx].contiguous()
-        c = counts[idx].contiguous()
-        t = tgt[idx].contiguous()
-        m = mask[idx].contiguous()
-        nreg = float(m.sum().item())
-        loss.zero_()
+        pd.pd_net_take(patches.data_ptr(), counts.data_ptr(), tgt.data_ptr(), mask.data_ptr(),
+                       idx_dev[s].data_ptr(), batch, x.data_ptr(), c.data_ptr(), t.data_ptr(),
+                       m.data_ptr(), stream=stream)
         pd.pd_net_train_step(net, x.data_ptr(), c.data_ptr(), t.data_ptr(), m.data_ptr(),
-                             batch, nreg, lam, lr, loss.data_ptr())
-        losses.append(float(loss.item()))
-    return losses
+                             batch, float(n_reg[s]), lam, lr, losses[s].data_ptr(),
+                             stream=stream)
+    return [float(v) for v in losses[:steps].cpu().numpy()]
 
 
 def predict(net, patches):

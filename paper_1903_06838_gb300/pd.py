@@ -107,7 +107,7 @@ class PdServeConfig(ctypes.Structure):
                 ("ring_frames", ctypes.c_uint32), ("hits_per_frame", ctypes.c_uint32),
                 ("device_budget", ctypes.c_uint64), ("keep_hits", ctypes.c_uint32),
                 ("encode_threads", ctypes.c_uint32), ("max_uploading", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("cpu_pin", ctypes.c_uint32)]
 
 
 class PdServeStats(ctypes.Structure):
@@ -115,7 +115,12 @@ class PdServeStats(ctypes.Structure):
                 ("frames_committed", "frames_done", "frames_rejected", "batches",
                  "max_batch_frames", "raw_bytes", "compressed_bytes", "hits")] + \
                [(n, ctypes.c_double) for n in
-                ("elapsed_s", "p50_us", "p99_us", "max_us", "mean_us")]
+                ("elapsed_s", "p50_us", "p99_us", "max_us", "mean_us", "wait_mean_us",
+                 "wait_p99_us", "device_mean_us", "device_p99_us", "fetch_mean_us",
+                 "encode_mean_us")] + \
+               [("replay_late", ctypes.c_uint64)] + \
+               [(n, ctypes.c_double) for n in
+                ("replay_late_max_us", "upload_mean_us", "run_mean_us")]
 
 
 class PdError(RuntimeError):
@@ -224,6 +229,7 @@ def _declare(lib):
         "pd_net_forward": ([vp, vp, u32, vp, vp], i32),
         "pd_net_gradients": ([vp, vp, vp, vp, vp, u32, ctypes.c_float, ctypes.c_float, vp, vp,
                               vp], i32),
+        "pd_net_take": ([vp, vp, vp, vp, vp, u32, vp, vp, vp, vp, vp], i32),
         "pd_net_train_step": ([vp, vp, vp, vp, vp, u32, ctypes.c_float, ctypes.c_float,
                                ctypes.c_float, vp, vp], i32),
         "pd_net_refine": ([vp, vp, u32, ctypes.c_float, ctypes.c_float, vp, vp], i32),
@@ -606,6 +612,13 @@ def pd_net_forward(net: Net, patches_ptr: int, n: int, out_ptr: int, stream=None
            "pd_net_forward")
 
 
+def pd_net_take(patches_ptr, counts_ptr, targets_ptr, mask_ptr, idx_ptr, n, p_out, c_out,
+                t_out, m_out, stream=None) -> None:
+    _check(load().pd_net_take(patches_ptr, counts_ptr, targets_ptr, mask_ptr, idx_ptr, n,
+                              p_out, c_out, t_out, m_out, _stream_handle(stream)),
+           "pd_net_take")
+
+
 def pd_net_gradients(net: Net, patches_ptr, counts_ptr, targets_ptr, mask_ptr, n, n_reg,
                      lam, grads_ptr, loss_ptr, stream=None) -> None:
     _check(load().pd_net_gradients(net.handle, patches_ptr, counts_ptr, targets_ptr, mask_ptr,
@@ -634,10 +647,11 @@ def pd_net_destroy(net: Net) -> None:
 class Server:
     def __init__(self, ctxs, n_slots=4, max_batch_frames=32, ring_frames=256,
                  hits_per_frame=16384, device_budget=0, keep_hits=False, encode_threads=0,
-                 max_uploading=0):
+                 max_uploading=0, cpu_pin=0):
         arr = (ctypes.c_void_p * len(ctxs))(*[c.handle for c in ctxs])
         cfg = PdServeConfig(n_slots, max_batch_frames, ring_frames, hits_per_frame,
-                            device_budget, int(keep_hits), encode_threads, max_uploading, 0)
+                            device_budget, int(keep_hits), encode_threads, max_uploading,
+                            cpu_pin)
         h = ctypes.c_void_p()
         _check(load().pd_server_create(arr, len(ctxs), ctypes.byref(cfg), ctypes.byref(h)),
                "pd_server_create")
