@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 #include <cmath>
@@ -492,15 +493,22 @@ struct LeanRow {
 // (t / n_bands) % n_modules of frame t / (n_bands n_modules)).  COLBANK: the
 // common-mode units span the module's full height, so a thread's four pixels
 // take the same two values on every row of a tile.  CORR: write corrected
-// frames.
-template <bool COLBANK, bool CORR>
+// frames.  STAGE: the tile's raw rows come by one tensor copy (the frames as
+// [frame][period][group][8 words]) into shared memory; the next tile's copy
+// is issued once the rows are read and lands while the seeds are tested.
+template <bool COLBANK, bool CORR, bool STAGE>
 __global__ void __launch_bounds__(kLeanThreads, 2)
     stencil_lean_kernel(ChainParams p, const uint16_t* __restrict__ raw, uint32_t frame_base,
-                        CallOut out, LeanConfig lc, unsigned long long n_tiles) {
-    extern __shared__ __align__(16) float lean_smem[];
+                        CallOut out, LeanConfig lc, unsigned long long n_tiles,
+                        const __grid_constant__ CUtensorMap frames, uint32_t* __restrict__ err) {
+    extern __shared__ __align__(128) float lean_smem[];
     __shared__ uint32_t list_n[2];
+    __shared__ uint64_t stage_bar;
     const uint32_t P = lc.pitch, RB = lc.rb;
-    float* tile = lean_smem;                                            // (RB + 2) x P
+    // staged raw rows (STAGE), 128-byte aligned, then the float tile
+    const uint32_t stage_words = STAGE ? lc.stage_bp * lc.stage_g * 8u : 0u;
+    const uint16_t* stg = reinterpret_cast<const uint16_t*>(lean_smem);
+    float* tile = lean_smem + ((stage_words / 2 + 31u) & ~31u);         // (RB + 2) x P
     uint32_t* hpix = reinterpret_cast<uint32_t*>(tile + (RB + 2) * P);  // hist_bins
     uint32_t* hhit = hpix + p.hist_bins;                                // hist_bins
     uint32_t* list = hhit + p.hist_bins;                                // list_cap
@@ -523,6 +531,24 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
     const int seed_bin = (int)summary_bin(p.seed_thr, p.hist_inv_w, p.hist_neg_lo_s,
                                           (int)(kMagicBits + p.hist_bins - 1));
 
+    // first frame row held by the stage for tile tt (the period holding the
+    // row above the band), and the copy of its rows (thread 0)
+    const uint32_t T = STAGE ? lc.stage_t : 1u;
+    // (T is a power of two, so & ~(T - 1) floors to a period, -1 included)
+    auto issue = [&](unsigned long long tt) {
+        const unsigned long long mb = tt / lc.n_bands;
+        const uint32_t band = (uint32_t)(tt - mb * lc.n_bands);
+        const uint32_t f = (uint32_t)(mb / p.n_modules);
+        const uint32_t m = (uint32_t)(mb - (unsigned long long)f * p.n_modules);
+        const int first = ((int)(m * p.rows + band * RB) - 1) & ~(int)(T - 1);
+        mbar_expect_tx(&stage_bar, lc.stage_bp * lc.stage_g * 16u);
+        tensor_copy_4d(lean_smem, &frames, 0, 0, first / (int)T, (int)f, &stage_bar);
+    };
+    if (STAGE && tid == 0) {
+        mbar_init(&stage_bar, 1);
+        fence_mbar_init();
+        if (blockIdx.x < n_tiles) issue(blockIdx.x);
+    }
     for (uint32_t i = tid; i < (RB + 2) * P; i += nthr) tile[i] = 0.0f;
     for (uint32_t i = tid; i < 2 * p.hist_bins; i += nthr) hpix[i] = 0;
     if (tid < 2) list_n[tid] = 0;
@@ -541,12 +567,35 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
         const float* npm = p.nped + mod_base;
         const float* gm = p.inv_gain + mod_base;
         const float* cmf = out.cm + (size_t)f * p.units_per_frame + (size_t)m * p.units_per_module;
+        // stage row of module row r: r + srow0
+        const int srow0 =
+            STAGE ? (int)(m * p.rows) - (((int)(m * p.rows) + r0 - 1) & ~(int)(T - 1)) : 0;
+        const uint32_t soff = (uint32_t)srow0 * p.cols;  // stage word of frame word off: off + soff
+        // the chunk's two common-mode values (COLBANK), loaded before the
+        // wait for the stage so that their latency overlaps it
+        float ca = 0.0f, cb = 0.0f;
+        if (COLBANK) {
+            ca = -cmf[uca];
+            cb = -cmf[ucb];
+        }
+        if (STAGE) {
+            // one thread waits for the copy; the barrier orders its data
+            // before every thread's reads
+            const bool ok = tid != 0 || mbar_wait(&stage_bar, par);
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    atomicOr(err, 2u);
+                    mbar_wait(&stage_bar, par);  // the copy still writes this CTA's memory
+                }
+                return;
+            }
+        }
 
         // negated common mode of the chunk's pixels (COLBANK), or of every
         // (tile row, unit column) in shared memory
         float2 n01 = make_float2(0.0f, 0.0f), n23 = n01;
         if (COLBANK) {
-            const float a = -cmf[uca], b = -cmf[ucb];
+            const float a = ca, b = cb;
             n01 = make_float2(split > 0 ? a : b, split > 1 ? a : b);
             n23 = make_float2(split > 2 ? a : b, split > 3 ? a : b);
         } else {
@@ -575,7 +624,10 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
         auto load = [&](int r) -> LeanRow {
             const uint32_t off = (uint32_t)r * p.cols + (uint32_t)col;
             LeanRow x;
-            x.rw = __ldg(reinterpret_cast<const uint2*>(fr + off));
+            if (STAGE)
+                x.rw = *reinterpret_cast<const uint2*>(stg + off + soff);
+            else
+                x.rw = __ldg(reinterpret_cast<const uint2*>(fr + off));
             x.np = __ldg(reinterpret_cast<const float4*>(npm + off));
             x.g = __ldg(reinterpret_cast<const float4*>(gm + off));
             return x;
@@ -669,6 +721,11 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
             }
         }
         __syncthreads();
+        // the stage is read: the next tile's rows land during the seeds
+        if (STAGE && tid == 0 && t + step < n_tiles) {
+            fence_async_smem();  // order the generic reads of the stage before the copy
+            issue(t + step);
+        }
 
         // 3. seeds: local maximum on s = e > zero_thr ? e : 0 with the raster
         //    tie rule, 3x3 sums, count, centroid, emission
@@ -734,8 +791,8 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
                             h.frame = frame_base + f;
                             h.pixel = pix;
                             h.energy_kev = E;
-                            h.dx = __fdiv_rn(Mx, E);
-                            h.dy = __fdiv_rn(My, E);
+                            h.dx = Mx == 0.0f && E > 0.0f ? Mx : __fdiv_rn(Mx, E);
+                            h.dy = My == 0.0f && E > 0.0f ? My : __fdiv_rn(My, E);
                             h.count = (uint8_t)n;
                             h.npix = (uint8_t)npix;
                             h.flags = flags;
@@ -940,8 +997,15 @@ cudaError_t launch_cm_bank(const ChainParams& p, const CmBigConfig& cfg, const C
 // Host side of the lean stencil.
 namespace pd {
 
-constexpr size_t kLeanSmemTwo = 100 * 1024;  // two CTAs per SM
+constexpr size_t kLeanSmemTwo = 108 * 1024;  // two CTAs per SM
 constexpr size_t kLeanSmemMax = 200 * 1024;
+
+// periods the stage holds: the band's rows, the rows above and below it,
+// and up to stage_t - 1 rows before them (the copy starts on a period)
+void set_stage_periods(LeanConfig& lc) {
+    if (lc.stage_t) lc.stage_bp = (lc.rb + 1 + 2 * lc.stage_t - 1) / lc.stage_t;
+}
+bool staged(const LeanConfig& lc) { return lc.stage_t != 0 && lc.stage_bp <= 256; }
 
 LeanConfig make_lean_config(const ChainParams& p, uint32_t rb) {
     LeanConfig lc{};
@@ -956,6 +1020,7 @@ LeanConfig make_lean_config(const ChainParams& p, uint32_t rb) {
     lc.pitch = p.cols + 8;
     lc.colbank = p.unit_rows == p.rows ? 1u : 0u;
     lc.list_cap = 4096;
+    lc.stage_t = 0;  // the band height is chosen without the stage
     const bool dflt = rb == 0;
     if (dflt) {
         // the tallest band two CTAs per SM hold (at most 16 rows per row
@@ -964,6 +1029,7 @@ LeanConfig make_lean_config(const ChainParams& p, uint32_t rb) {
         t.rb = 1;
         while (t.rb < p.rows && (t.rb + lc.ty) / lc.ty <= 16) {
             t.rb++;
+            set_stage_periods(t);
             if (lean_smem_bytes(p, t) > kLeanSmemTwo) {
                 t.rb--;
                 break;
@@ -976,16 +1042,38 @@ LeanConfig make_lean_config(const ChainParams& p, uint32_t rb) {
     // own rows per thread fit a 64-bit candidate mask (4 bits per row)
     while (rb > 1 && (rb + lc.ty - 1) / lc.ty > 16) rb--;
     lc.rb = rb;
+    set_stage_periods(lc);
     // the default keeps two CTAs per SM; a requested height may take one
     const size_t limit = dflt ? kLeanSmemTwo : kLeanSmemMax;
-    while (lc.rb > 1 && lean_smem_bytes(p, lc) > limit) lc.rb--;
+    while (lc.rb > 1 && lean_smem_bytes(p, lc) > limit) {
+        lc.rb--;
+        set_stage_periods(lc);
+    }
     lc.n_bands = (p.rows + lc.rb - 1) / lc.rb;
     lc.ok = lean_smem_bytes(p, lc) <= limit;
+    // staged raw where it costs no band height: the fewest rows per period
+    // whose words fill 16-byte groups (at most 256 groups, the tensor copy's
+    // box limit), frames a whole number of periods and of 16-byte groups.
+    // On the 2.2 Mpx sensor the stage would cut the band from 47 to 31 rows,
+    // and the shorter bands' per-tile costs outweigh the faster rows
+    // (measured 117.7 k against 122.1 k frames/s), so it stays off there.
+    for (uint32_t t = 1; t <= 8 && lc.ok; t *= 2)
+        if ((t * p.cols) % 8 == 0) {
+            if (t * p.cols / 8 <= 256 && (p.frame_px / p.cols) % t == 0 && p.frame_px % 8 == 0 &&
+                encode_fn() != nullptr) {
+                lc.stage_t = t;
+                lc.stage_g = t * p.cols / 8;
+                set_stage_periods(lc);
+                if (!staged(lc) || lean_smem_bytes(p, lc) > limit) lc.stage_t = 0;
+            }
+            break;
+        }
     return lc;
 }
 
 size_t lean_smem_bytes(const ChainParams& p, const LeanConfig& lc) {
-    return (size_t)(lc.rb + 2) * lc.pitch * 4 + 2 * (size_t)p.hist_bins * 4 +
+    const size_t stage = staged(lc) ? ((size_t)lc.stage_bp * lc.stage_g * 16 + 127) / 128 * 128 : 0;
+    return stage + (size_t)(lc.rb + 2) * lc.pitch * 4 + 2 * (size_t)p.hist_bins * 4 +
            (size_t)lc.list_cap * 4 + (lc.colbank ? 0 : (size_t)(lc.rb + 2) * p.units_per_row * 4);
 }
 
@@ -993,14 +1081,16 @@ static int g_attr_dev_lean = -1;
 
 cudaError_t launch_stencil_lean(const ChainParams& p, const LeanConfig& lc, const uint16_t* raw,
                                 uint32_t n_frames, uint32_t frame_base, const CallOut& out,
-                                cudaStream_t stream) {
+                                uint32_t* err, cudaStream_t stream) {
     const unsigned long long n_tiles = (unsigned long long)n_frames * p.n_modules * lc.n_bands;
     if (n_tiles == 0) return cudaSuccess;
     int dev = 0;
     cudaGetDevice(&dev);
     if (g_attr_dev_lean != dev) {
-        for (auto k : {stencil_lean_kernel<true, false>, stencil_lean_kernel<true, true>,
-                       stencil_lean_kernel<false, false>, stencil_lean_kernel<false, true>}) {
+        for (auto k : {stencil_lean_kernel<true, false, false>, stencil_lean_kernel<true, true, false>,
+                       stencil_lean_kernel<false, false, false>, stencil_lean_kernel<false, true, false>,
+                       stencil_lean_kernel<true, false, true>, stencil_lean_kernel<true, true, true>,
+                       stencil_lean_kernel<false, false, true>, stencil_lean_kernel<false, true, true>}) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kLeanSmemMax);
             if (e == cudaSuccess)
@@ -1009,15 +1099,39 @@ cudaError_t launch_stencil_lean(const ChainParams& p, const LeanConfig& lc, cons
         }
         g_attr_dev_lean = dev;
     }
+    const bool stage = staged(lc);
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    if (stage) {
+        // the call's frames as [frame][period][group][8 words] of uint16
+        PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+        if (!enc || !err) return cudaErrorNotSupported;
+        const uint64_t G = lc.stage_g;
+        const cuuint64_t dims[4] = {8, G, (cuuint64_t)p.frame_px / ((cuuint64_t)lc.stage_t * p.cols),
+                                    n_frames};
+        const cuuint64_t strides[3] = {16, G * 16, (cuuint64_t)p.frame_px * 2};
+        const cuuint32_t box[4] = {8, lc.stage_g, lc.stage_bp, 1};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<uint16_t*>(raw), dims, strides,
+                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
     const size_t smem = lean_smem_bytes(p, lc);
     const unsigned threads = lc.tx * lc.ty;
     const uint32_t per_sm = lc.ctas_per_sm ? lc.ctas_per_sm : (smem <= kLeanSmemTwo ? 2u : 1u);
     unsigned long long grid = (unsigned long long)device_sm_count() * per_sm;
     if (grid > n_tiles) grid = n_tiles;
     const bool corr = out.corrected != nullptr;
-    auto k = lc.colbank ? (corr ? stencil_lean_kernel<true, true> : stencil_lean_kernel<true, false>)
-                        : (corr ? stencil_lean_kernel<false, true> : stencil_lean_kernel<false, false>);
-    k<<<(unsigned)grid, threads, smem, stream>>>(p, raw, frame_base, out, lc, n_tiles);
+    auto k = stage ? (lc.colbank ? (corr ? stencil_lean_kernel<true, true, true>
+                                         : stencil_lean_kernel<true, false, true>)
+                                 : (corr ? stencil_lean_kernel<false, true, true>
+                                         : stencil_lean_kernel<false, false, true>))
+                   : (lc.colbank ? (corr ? stencil_lean_kernel<true, true, false>
+                                         : stencil_lean_kernel<true, false, false>)
+                                 : (corr ? stencil_lean_kernel<false, true, false>
+                                         : stencil_lean_kernel<false, false, false>));
+    k<<<(unsigned)grid, threads, smem, stream>>>(p, raw, frame_base, out, lc, n_tiles, map, err);
     return cudaGetLastError();
 }
 

@@ -63,13 +63,21 @@ struct LeanConfig {
     uint32_t colbank;    // 1: units span the module's full height
     uint32_t list_cap;   // seed candidates per tile
     uint32_t ctas_per_sm;  // persistent CTAs per SM of a launch (0: as shared memory allows)
+    // staged raw (stage_t > 0): each tile's rows, halo rows included, come
+    // to shared memory as one tensor copy of stage_bp periods of stage_t
+    // rows (frames read as [frame][period][16-byte group][8 words], stage_g
+    // groups per period); the next tile's copy is in flight while a tile's
+    // seeds are tested
+    uint32_t stage_t, stage_g, stage_bp;
     bool ok;
 };
 
 LeanConfig make_lean_config(const ChainParams& p, uint32_t rb = 0);
 size_t lean_smem_bytes(const ChainParams& p, const LeanConfig& lc);
+// raw: 16-byte aligned.  err: context error word (bit 1: a bounded wait
+// for a staged copy gave up).
 cudaError_t launch_stencil_lean(const ChainParams& p, const LeanConfig& lc, const uint16_t* raw,
                                 uint32_t n_frames, uint32_t frame_base, const CallOut& out,
-                                cudaStream_t stream);
+                                uint32_t* err, cudaStream_t stream);
 
 }  // namespace pd
