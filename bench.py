@@ -34,12 +34,12 @@ FRAMES_PER_STEP = 1024
 HIT_BYTES = 24
 # DRAM bytes (read + write) per frame of each kernel, from the ncu capture
 # summarised in profiles/cspad_2p2m_chain.md (the kernel pair run back to
-# back on 21-frame chunks, caches not flushed between kernels, so the
+# back on one 64-frame chunk, caches not flushed between kernels, so the
 # stencil's re-read of raw is counted where it misses L2); set an entry to
 # None when its kernel changes until it is captured again.
-NCU_TRAFFIC_PER_FRAME = {"stencil": (106.228736e6 + 18.52544e6) / 21,
-                         "common_mode": (86.923264e6 + 3.517696e6) / 21,
-                         "fused_chain": None}
+NCU_TRAFFIC_PER_FRAME = {"stencil": (316.297472e6 + 51.442432e6) / 64,
+                         "common_mode": (302.14272e6 + 3.378688e6) / 64,
+                         "fused_chain": None, "chain_queue": None}
 
 
 def parse():
@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--band-rows", type=int, default=0)
     ap.add_argument("--no-overlap", action="store_true")
+    ap.add_argument("--kernels", type=int, default=0,
+                    help="pd_tuning.kernels: 1 the lean pair, 2 the earlier pair, 3 the lean "
+                         "pair as one work-queue launch (0: the context's default)")
     ap.add_argument("--fused", action="store_true",
                     help="one-kernel chain instead of the common-mode + stencil pair")
     ap.add_argument("--no-serve", action="store_true")
@@ -269,9 +272,9 @@ def run_pd(args):
     synth.frames(det, ped, gain, rank * nf, nf, truth=False, out=raw)
     frames = host.to(dev, non_blocking=False)
     ctx = pd.pd_create(det.geometry(), ped, gain, det.thresholds())
-    if args.chunk or args.band_rows or args.no_overlap or args.fused:
+    if args.chunk or args.band_rows or args.no_overlap or args.fused or args.kernels:
         pd.pd_set_tuning(ctx, args.chunk, args.band_rows, 0 if args.no_overlap else 1,
-                         0 if args.fused else 1)
+                         0 if args.fused else 1, args.kernels)
     cap = nf * 16384
     out = pd.Outputs(ctx, nf, cap, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -340,6 +343,7 @@ def run_pd(args):
         "common_mode": raw_b + maps_b + cm_b,
         "stencil": raw_b + 2 * maps_b + cm_b + hits_b + cmap_b,
         "fused_chain": raw_b + 2 * maps_b + hits_b + cmap_b,
+        "chain_queue": raw_b + 2 * maps_b + cm_b + hits_b + cmap_b,
     }
     dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
     roof = None

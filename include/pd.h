@@ -318,7 +318,11 @@ void pd_destroy(pd_ctx* ctx);
  * band stencil for columns a multiple of 4, single-gain words, the median,
  * no or the one-stage mean common mode, subtracted before gain); 2 runs the
  * earlier kernel pair (pd_get_tuning reports 2 when the lean pair is not
- * available).
+ * available); 3 runs the lean pair as one persistent launch per call over a
+ * work queue (bank medians of a few frames, then the stencil tiles of the
+ * frames before them, so raw is re-read from L2; column-bank units, no
+ * corrected frames, no matched filters; pd_get_tuning reports 1 where it
+ * does not apply).
  * Results never depend on tuning. */
 typedef struct {
     uint32_t chunk_frames;

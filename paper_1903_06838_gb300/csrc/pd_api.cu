@@ -53,7 +53,11 @@ struct pd_ctx {
     pd::CodeMap cmap{};
     uint4* d_kmap = nullptr;
     pd::LeanConfig lean_cfg{};
-    uint32_t kernels = 1;       // 1: the lean pair where available; 2: the earlier pair
+    uint32_t kernels = 1;       // 1: the lean pair where available; 2: the earlier pair;
+                                // 3: the lean pair as one work-queue launch
+    bool use_queue = false;     // the lean pair can run as the work-queue launch
+    uint32_t* d_qsync = nullptr;  // its queue counter and per-(frame, module) counts
+    size_t qsync_cap = 0;         // words
     uint32_t* d_err = nullptr;  // bit 0: a bounded wait for staged copies gave up
     uint32_t two_pass = 1;      // 1: common-mode and stencil kernels (measured
                                 // faster on GB300 so far); 0: the one-kernel chain
@@ -98,8 +102,8 @@ struct pd_ctx {
 
 namespace {
 
-const char* const kKernelNames[] = {"common_mode", "stencil", "fused_chain"};
-constexpr int kNumKernelNames = 3;
+const char* const kKernelNames[] = {"common_mode", "stencil", "fused_chain", "chain_queue"};
+constexpr int kNumKernelNames = 4;
 
 cudaEvent_t take_event(pd_ctx* c) {
     if (!c->spare.empty()) {
@@ -208,6 +212,7 @@ void free_ctx(pd_ctx* c) {
     cudaFree(c->d_mg_ped);
     cudaFree(c->d_mg_ig);
     cudaFree(c->d_kmap);
+    cudaFree(c->d_qsync);
     cudaFree(c->d_err);
     cudaFree(c->d_stage[0]);
     cudaFree(c->d_stage[1]);
@@ -280,6 +285,28 @@ int ensure_cm(pd_ctx* c, uint32_t n_frames) {
     return PD_OK;
 }
 
+// The work-queue launch applies (lean pair, column banks, no matched
+// filters, no corrected frames).
+bool queue_on(const pd_ctx* c, const pd_outputs* out) {
+    return c->use_queue && c->kernels == 3 && !c->matched && !out->corrected &&
+           pd::queue_supported(c->params, c->cmap, c->lean_cfg);
+}
+
+int ensure_qsync(pd_ctx* c, uint32_t n_frames) {
+    const size_t need = pd::queue_sync_words(c->params, n_frames);
+    if (need <= c->qsync_cap) return PD_OK;
+    // growth reallocates: any work on the old buffer must be finished
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail_cuda(e, "synchronise before queue scratch growth");
+    cudaFree(c->d_qsync);
+    c->d_qsync = nullptr;
+    c->qsync_cap = 0;
+    if (cudaMalloc(&c->d_qsync, need * 4) != cudaSuccess)
+        return fail(PD_ENOMEM, "queue scratch allocation failed");
+    c->qsync_cap = need;
+    return PD_OK;
+}
+
 int run_chain(pd_ctx* c, const uint16_t* frames, uint32_t n_frames, uint32_t frame_base,
               const pd_outputs* out, cudaStream_t s, bool zero = true) {
     cudaError_t e = cudaSuccess;
@@ -297,6 +324,16 @@ int run_chain(pd_ctx* c, const uint16_t* frames, uint32_t n_frames, uint32_t fra
         int rc = ensure_cm(c, n_frames);
         if (rc) return rc;
         cm = c->d_cm;
+    }
+    if (queue_on(c, out)) {
+        // every frame of the call in one work-queue launch
+        int rc = ensure_qsync(c, n_frames);
+        if (rc) return rc;
+        pd::CallOut co{out->hits, out->hit_capacity, out->n_hits, nullptr, cm};
+        ProfileScope ps(c, 3, s);
+        e = pd::launch_chain_queue(c->params, c->cm_cfg, c->cmap, c->lean_cfg, frames, n_frames,
+                                   frame_base, co, c->d_qsync, c->d_err, s);
+        return e == cudaSuccess ? PD_OK : fail_cuda(e, "queue kernel launch");
     }
     // Frames go in chunks sized so raw stays resident in L2 between the
     // common-mode pass and the stencil pass that re-reads it.  With overlap,
@@ -612,6 +649,7 @@ int create_impl(const pd_geometry* geometry, uint32_t n_gains, uint32_t gain_shi
             cmap.kmap = c->d_kmap;
             c->cmap = cmap;
             c->use_bank = true;
+            c->use_queue = c->use_lean && pd::queue_supported(p, cmap, c->lean_cfg);
         }
     }
     pd::noalloc_prepare(c->device);
@@ -807,18 +845,19 @@ int pd_reset_summary(pd_ctx* c, void* stream) {
 int pd_get_tuning(const pd_ctx* c, pd_tuning* t) {
     if (!c || !t) return fail(PD_EINVAL, "NULL argument");
     t->chunk_frames = c->chunk_frames;
-    const bool lean = c->use_lean && c->kernels == 1 && !c->matched;
+    const bool lean = c->use_lean && (c->kernels == 1 || c->kernels == 3) && !c->matched;
     t->band_rows = lean ? c->lean_cfg.rb : c->use_band ? c->band_cfg.rb : 0;
     t->overlap = c->overlap;
     t->two_pass = c->use_fused && !c->matched ? c->two_pass : 1;
-    t->kernels = c->use_lean || c->use_bank ? c->kernels : 2;
+    t->kernels = c->use_lean || c->use_bank ? (c->kernels == 3 && !c->use_queue ? 1u : c->kernels)
+                                            : 2;
     return PD_OK;
 }
 
 int pd_set_tuning(pd_ctx* c, const pd_tuning* t) {
     if (!c || !t) return fail(PD_EINVAL, "NULL argument");
     if (t->chunk_frames) c->chunk_frames = t->chunk_frames;
-    if (t->kernels > 2) return fail(PD_EINVAL, "kernels is 0, 1 or 2");
+    if (t->kernels > 3) return fail(PD_EINVAL, "kernels is 0, 1, 2 or 3");
     if (t->kernels) c->kernels = t->kernels;
     if (t->band_rows && c->use_lean) {
         const pd::LeanConfig lc = pd::make_lean_config(c->params, t->band_rows);
@@ -1260,6 +1299,9 @@ int pd_autotune(pd_ctx* c, const uint16_t* frames_dev, uint32_t n_frames, pd_tun
             cands.push_back(pd_tuning{orig.chunk_frames, orig.band_rows, 1, 0, orig.kernels});
         std::vector<uint32_t> kopts = {orig.kernels};
         if ((c->use_lean || c->use_bank) && !c->matched) kopts = {1u, 2u};
+        // the work-queue launch: one launch per call, so chunking, band
+        // height and overlap are not varied
+        if (c->use_queue && !c->matched) cands.push_back(pd_tuning{orig.chunk_frames, 0, 1, 1, 3});
         for (uint32_t k : kopts) {
             std::vector<uint32_t> bands = {0};
             if (!c->matched && k == 1 && c->use_lean) bands = band_set(lean_rb0);

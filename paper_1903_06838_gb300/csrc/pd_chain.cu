@@ -17,6 +17,7 @@
 #include <stdint.h>
 
 #include "pd_cm_generic.cuh"
+#include "pd_dev.cuh"
 #include "pd_internal.cuh"
 
 namespace pd {
@@ -205,8 +206,8 @@ __global__ void __launch_bounds__(kStThreads)
                             h.frame = frame_base + f;
                             h.pixel = pix;
                             h.energy_kev = E;
-                            h.dx = __fdiv_rn(Mx, E);
-                            h.dy = __fdiv_rn(My, E);
+                            h.dx = moment_over_energy(Mx, E);
+                            h.dy = moment_over_energy(My, E);
                             h.count = (uint8_t)n;
                             h.npix = (uint8_t)npix;
                             h.flags = flags;

@@ -65,6 +65,14 @@ __device__ __forceinline__ uint32_t summary_bin(float v, float inv_w, float neg_
     return (uint32_t)(b - (int)kMagicBits);
 }
 
+// Centroid offset m / e rounded to nearest (section "Photon Subpixel
+// Resolution").  A zero moment over a positive energy is that zero, sign
+// included, exactly as the division gives it; testing for it first keeps
+// single-pixel hits (both moments zero) off the division's slow path.
+__device__ __forceinline__ float moment_over_energy(float m, float e) {
+    return m == 0.0f && e > 0.0f ? m : __fdiv_rn(m, e);
+}
+
 // Two raw values of a packed pair as exact floats: 2^23 + raw has the raw
 // value as its low mantissa bits, and subtracting 2^23 is exact.
 __device__ __forceinline__ float2 raw_pair(uint32_t x) {

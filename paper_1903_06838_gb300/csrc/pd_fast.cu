@@ -875,8 +875,8 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
                             h.frame = frame_base + f;
                             h.pixel = pix;
                             h.energy_kev = E;
-                            h.dx = __fdiv_rn(Mx, E);
-                            h.dy = __fdiv_rn(My, E);
+                            h.dx = moment_over_energy(Mx, E);
+                            h.dy = moment_over_energy(My, E);
                             h.count = (uint8_t)n;
                             h.npix = (uint8_t)npix;
                             h.flags = flags;

@@ -66,20 +66,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  "r"(bytes)
                  : "memory");
 }
-// global -> shared bulk copy of `bytes` (a multiple of 16; both addresses
-// 16-byte aligned), counted against the mbarrier's transaction bytes
-__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes,
-                                          uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-        "[%3];" ::"r"(saddr(dst)),
-        "l"(src), "r"(bytes), "r"(saddr(bar))
-        : "memory");
-}
-// bounded wait for phase `parity` of the mbarrier; false when it gave up
+// orders this thread's generic-proxy shared-memory accesses before later
+// asynchronous-proxy ones (a tensor copy into the same memory)
 __device__ __forceinline__ void fence_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// bounded wait for phase `parity` of the mbarrier; false when it gave up
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     const uint32_t a = saddr(bar);
     for (uint32_t it = 0; it < kCopyWaitLimit; it++) {
@@ -253,59 +245,61 @@ __device__ __forceinline__ void tensor_copy_4d(void* dst, const CUtensorMap* map
 // cmap.bp periods x cmap.w8 groups from (group g_lo(phi), period q_lo); the
 // unit's staged buffer holds the t boxes one after the other, each padded to
 // cmap.ne_box groups (a multiple of 8, so every box starts 128-byte aligned).
-// Persistent: CTA b takes items b, b + grid, ...; the next item's copies are
-// issued as soon as pass B has finished reading the stage, so they land
-// while the current item's candidates are ranked.
-__global__ void __launch_bounds__(kBankThreads, 2)
-    cm_bank_kernel(ChainParams p, float* __restrict__ cm_out, CmBigConfig cfg, CodeMap cmap,
-                   const __grid_constant__ CUtensorMap frames, const uint16_t* __restrict__ raw,
-                   uint32_t n_items, uint32_t* __restrict__ err) {
-    extern __shared__ __align__(128) uint4 stage[];  // t * ne_box groups of 8 words
-    __shared__ BankShared sh;
+// The shared-memory regions of one bank item.
+struct BankSmem {
+    uint4* stage;    // t * ne_box groups of 8 words
+    uint32_t* hist;  // kCmBins + 4 (spare at kCmBins)
+    float* cand;     // candidate capacity
+    uint32_t* cidx;  // candidate capacity
+};
+
+// Global first row and first column of item `it`'s unit, and its frame.
+__device__ __forceinline__ void bank_unit_of(const ChainParams& p, uint32_t it, uint32_t* R0,
+                                             uint32_t* c0, uint32_t* f) {
+    *f = it / p.units_per_frame;
+    const uint32_t u = it - *f * p.units_per_frame;
+    const uint32_t m = u / p.units_per_module, um = u - m * p.units_per_module;
+    *R0 = m * p.rows + (um / p.units_per_row) * p.unit_rows;
+    *c0 = (um % p.units_per_row) * p.unit_cols;
+}
+
+// One tensor copy per row phase of item `it` into the stage (thread 0).
+__device__ __forceinline__ void bank_issue(const ChainParams& p, const CodeMap& cmap,
+                                           const CUtensorMap* frames, uint4* stage, uint64_t* bar,
+                                           uint32_t it) {
+    uint32_t R0, c0, f;
+    bank_unit_of(p, it, &R0, &c0, &f);
+    mbar_expect_tx(bar, cmap.t * cmap.bp * cmap.w8 * 16u);
+    for (uint32_t ph = 0; ph < cmap.t; ph++)
+        tensor_copy_4d(stage + ph * cmap.ne_box, frames, 0, (int)((ph * p.cols + c0) >> 3),
+                       (int)(R0 / cmap.t), (int)f, bar);
+}
+
+// One bank item whose copy has been issued (its completion is phase `parity`
+// of sh.bar); the histogram must be zero on entry and is zero again on
+// return.  issue_next() runs on thread 0 once the stage is read (the next
+// item's copy may start then).  False if the copy wait gave up.
+template <class NextFn>
+__device__ __forceinline__ bool cm_bank_item(const ChainParams& p, float* __restrict__ cm_out,
+                                             const CmBigConfig& cfg, const CodeMap& cmap,
+                                             const uint16_t* __restrict__ raw, uint32_t item,
+                                             uint32_t parity, const BankSmem& sm,
+                                             uint32_t cand_cap, BankShared& sh,
+                                             uint32_t* __restrict__ err, NextFn issue_next) {
+    uint4* stage = sm.stage;
+    uint32_t* hist = sm.hist;
+    float* cand = sm.cand;
+    uint32_t* cidx = sm.cidx;
     const uint32_t W8 = cmap.w8, T = cmap.t;
     const uint32_t ne = T * cmap.ne_box;
-    uint32_t* hist = reinterpret_cast<uint32_t*>(stage + ne);       // kCmBins + 4 (spare at kCmBins)
-    float* cand = reinterpret_cast<float*>(hist + kCmBins + 4);      // kCandCap
-    uint32_t* cidx = reinterpret_cast<uint32_t*>(cand + kCandCap);   // kCandCap
     const uint32_t tid = threadIdx.x, lane = tid & 31;
     const uint32_t cap2 = cmap.rcap * 0x10001u;
     const uint32_t lo2 = cmap.bias * 0x10001u;
     const uint32_t hi2 = (cmap.bias + kCmBins) * 0x10001u;
     uint32_t* hb = hist - cmap.bias;  // hb[code'] is hist[code' - bias]
-
-    // global first row and first column of item `it`'s unit, its frame
-    auto unit_of = [&](uint32_t it, uint32_t* R0, uint32_t* c0, uint32_t* f) {
-        *f = it / p.units_per_frame;
-        const uint32_t u = it - *f * p.units_per_frame;
-        const uint32_t m = u / p.units_per_module, um = u - m * p.units_per_module;
-        *R0 = m * p.rows + (um / p.units_per_row) * p.unit_rows;
-        *c0 = (um % p.units_per_row) * p.unit_cols;
-    };
-    // one tensor copy per row phase of item `it` (thread 0)
-    auto issue = [&](uint32_t it) {
+    {
         uint32_t R0, c0, f;
-        unit_of(it, &R0, &c0, &f);
-        mbar_expect_tx(&sh.bar, T * cmap.bp * W8 * 16u);
-        for (uint32_t ph = 0; ph < T; ph++)
-            tensor_copy_4d(stage + ph * cmap.ne_box, &frames, 0, (int)((ph * p.cols + c0) >> 3),
-                           (int)(R0 / T), (int)f, &sh.bar);
-    };
-
-    if (tid == 0) {
-        mbar_init(&sh.bar, 1);
-        fence_mbar_init();
-        if (blockIdx.x < n_items) issue(blockIdx.x);
-    }
-    for (uint32_t i = tid; i < (kCmBins + 4) / 4; i += kBankThreads)
-        reinterpret_cast<uint4*>(hist)[i] = make_uint4(0, 0, 0, 0);
-    if (tid == 0) sh.s_cand = 0;
-    __syncthreads();  // mbarrier initialised, histogram zero
-
-    uint32_t parity = 0;
-    for (uint32_t item = blockIdx.x; item < n_items; item += gridDim.x, parity ^= 1u) {
-        const uint32_t next = item + gridDim.x;
-        uint32_t R0, c0, f;
-        unit_of(item, &R0, &c0, &f);
+        bank_unit_of(p, item, &R0, &c0, &f);
         const uint32_t u = item - f * p.units_per_frame;
         const uint32_t q_lo = R0 / T;
         const uint16_t* fr = raw + (size_t)f * p.frame_px;
@@ -326,7 +320,7 @@ __global__ void __launch_bounds__(kBankThreads, 2)
                 atomicOr(err, 1u);
                 mbar_wait(&sh.bar, parity);
             }
-            return;
+            return false;
         }
 
         // 1. pass A over the staged groups, three groups per round, the next
@@ -421,7 +415,7 @@ __global__ void __launch_bounds__(kBankThreads, 2)
         //    compact list (in the histogram's words, free now), then one
         //    thread per candidate loads its raw word and pedestal
         uint32_t* qlist = hist;
-        if (!none && bin != 0 && mc <= kCandCap) {
+        if (!none && bin != 0 && mc <= cand_cap) {
             const uint16_t* slots = reinterpret_cast<const uint16_t*>(cidx) + tid * kThreadGroups;
             uint32_t at = before;
             for (uint32_t i = 0; i < min(n_grp, kThreadGroups); i++) {
@@ -434,7 +428,7 @@ __global__ void __launch_bounds__(kBankThreads, 2)
             }
         }
         __syncthreads();  // the stage is no longer read
-        if (!none && bin != 0 && mc <= kCandCap) {
+        if (!none && bin != 0 && mc <= cand_cap) {
             const float* npf = p.nped;
             for (uint32_t t = tid; t < mc; t += kBankThreads) {
                 const uint32_t q = qlist[t];
@@ -445,11 +439,8 @@ __global__ void __launch_bounds__(kBankThreads, 2)
         __syncthreads();
         // the next item's copies (after the candidates' loads, which would
         // otherwise queue behind them) land while this item is ranked
-        if (tid == 0 && next < n_items) {
-            fence_async_smem();  // order this item's generic stage accesses before the copy
-            issue(next);
-        }
-        const bool over = sh.s_cand != 0 || mc > kCandCap;
+        if (tid == 0) issue_next();
+        const bool over = sh.s_cand != 0 || mc > cand_cap;
         if (none) {
             if (tid == 0) cm_out[item] = 0.0f;
         } else if (bin != 0 && !over) {
@@ -477,6 +468,49 @@ __global__ void __launch_bounds__(kBankThreads, 2)
         if (tid == 0) sh.s_cand = 0;
         __syncthreads();
     }
+    return true;
+}
+
+// Persistent: CTA b takes items b, b + grid, ...; the next item's copies are
+// issued as soon as pass B has finished reading the stage, so they land
+// while the current item's candidates are ranked.
+__global__ void __launch_bounds__(kBankThreads, 2)
+    cm_bank_kernel(ChainParams p, float* __restrict__ cm_out, CmBigConfig cfg, CodeMap cmap,
+                   const __grid_constant__ CUtensorMap frames, const uint16_t* __restrict__ raw,
+                   uint32_t n_items, uint32_t* __restrict__ err) {
+    extern __shared__ __align__(128) uint4 stage[];  // t * ne_box groups of 8 words
+    __shared__ BankShared sh;
+    const uint32_t ne = cmap.t * cmap.ne_box;
+    BankSmem sm;
+    sm.stage = stage;
+    sm.hist = reinterpret_cast<uint32_t*>(stage + ne);
+    sm.cand = reinterpret_cast<float*>(sm.hist + kCmBins + 4);
+    sm.cidx = reinterpret_cast<uint32_t*>(sm.cand + kCandCap);
+    const uint32_t tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&sh.bar, 1);
+        fence_mbar_init();
+        if (blockIdx.x < n_items) bank_issue(p, cmap, &frames, stage, &sh.bar, blockIdx.x);
+    }
+    for (uint32_t i = tid; i < (kCmBins + 4) / 4; i += kBankThreads)
+        reinterpret_cast<uint4*>(sm.hist)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) sh.s_cand = 0;
+    __syncthreads();  // mbarrier initialised, histogram zero
+
+    uint32_t parity = 0;
+    for (uint32_t item = blockIdx.x; item < n_items; item += gridDim.x, parity ^= 1u) {
+        const uint32_t next = item + gridDim.x;
+        const bool ok = cm_bank_item(p, cm_out, cfg, cmap, raw, item, parity, sm, kCandCap, sh,
+                                     err, [&] {
+                                         if (next < n_items) {
+                                             // order this item's generic stage accesses
+                                             // before the copy
+                                             fence_async_smem();
+                                             bank_issue(p, cmap, &frames, stage, &sh.bar, next);
+                                         }
+                                     });
+        if (!ok) return;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -489,31 +523,41 @@ struct LeanRow {
     float4 g;   // their inverse gains
 };
 
-// Tiles first, first + step, ... < n_tiles (tile t: band t % n_bands of module
-// (t / n_bands) % n_modules of frame t / (n_bands n_modules)).  COLBANK: the
-// common-mode units span the module's full height, so a thread's four pixels
-// take the same two values on every row of a tile.  CORR: write corrected
-// frames.  STAGE: the tile's raw rows come by one tensor copy (the frames as
-// [frame][period][group][8 words]) into shared memory; the next tile's copy
-// is issued once the rows are read and lands while the seeds are tested.
-template <bool COLBANK, bool CORR, bool STAGE>
-__global__ void __launch_bounds__(kLeanThreads, 2)
-    stencil_lean_kernel(ChainParams p, const uint16_t* __restrict__ raw, uint32_t frame_base,
-                        CallOut out, LeanConfig lc, unsigned long long n_tiles,
-                        const __grid_constant__ CUtensorMap frames, uint32_t* __restrict__ err) {
-    extern __shared__ __align__(128) float lean_smem[];
-    __shared__ uint32_t list_n[2];
-    __shared__ uint64_t stage_bar;
-    const uint32_t P = lc.pitch, RB = lc.rb;
-    // staged raw rows (STAGE), 128-byte aligned, then the float tile
-    const uint32_t stage_words = STAGE ? lc.stage_bp * lc.stage_g * 8u : 0u;
-    const uint16_t* stg = reinterpret_cast<const uint16_t*>(lean_smem);
-    float* tile = lean_smem + ((stage_words / 2 + 31u) & ~31u);         // (RB + 2) x P
-    uint32_t* hpix = reinterpret_cast<uint32_t*>(tile + (RB + 2) * P);  // hist_bins
-    uint32_t* hhit = hpix + p.hist_bins;                                // hist_bins
-    uint32_t* list = hhit + p.hist_bins;                                // list_cap
-    float* cmt = reinterpret_cast<float*>(list + lc.list_cap);          // (RB + 2) x upr
+// Shared memory of the lean stencil: the staged raw rows (STAGE), the tile
+// of corrected energies, the two summary histograms, the candidate list,
+// the common mode per tile row (not COLBANK), the list counters and the
+// stage's mbarrier.
+struct LeanSmem {
+    const uint16_t* stg;
+    float* tile;       // (rb + 2) x pitch
+    uint32_t* hpix;    // hist_bins
+    uint32_t* hhit;    // hist_bins
+    uint32_t* list;    // list_cap
+    float* cmt;        // (rb + 2) x units_per_row
+    uint32_t* list_n;  // 2
+    uint64_t* stage_bar;
+};
 
+// One tile (band `band` of module m of frame f, list counter `par`).  The
+// tile's pad columns must be zero and list_n[par] zero on entry.  Threads
+// with rowlane false own no rows (blocks larger than tx * ty).
+// issue_next() runs on thread 0 once the stage is read.  False if a staged
+// copy's wait gave up.
+template <bool COLBANK, bool CORR, bool STAGE, class NextFn>
+__device__ __forceinline__ bool lean_tile(const ChainParams& p, const uint16_t* __restrict__ raw,
+                                          uint32_t frame_base, const CallOut& out,
+                                          const LeanConfig& lc, const LeanSmem& sm, uint32_t f,
+                                          uint32_t m, uint32_t band, uint32_t par, bool rowlane,
+                                          uint32_t* __restrict__ err, NextFn issue_next) {
+    const uint32_t P = lc.pitch, RB = lc.rb;
+    const uint16_t* stg = sm.stg;
+    float* tile = sm.tile;
+    uint32_t* hpix = sm.hpix;
+    uint32_t* hhit = sm.hhit;
+    uint32_t* list = sm.list;
+    float* cmt = sm.cmt;
+    uint32_t* list_n = sm.list_n;
+    uint64_t* stage_bar = sm.stage_bar;
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
     const uint32_t TX = lc.tx, TY = lc.ty;
     const uint32_t cx = tid % TX, ty = tid / TX;
@@ -530,37 +574,10 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
     // is monotone in e); rows holding such a bin are scanned for candidates
     const int seed_bin = (int)summary_bin(p.seed_thr, p.hist_inv_w, p.hist_neg_lo_s,
                                           (int)(kMagicBits + p.hist_bins - 1));
-
-    // first frame row held by the stage for tile tt (the period holding the
-    // row above the band), and the copy of its rows (thread 0)
     const uint32_t T = STAGE ? lc.stage_t : 1u;
-    // (T is a power of two, so & ~(T - 1) floors to a period, -1 included)
-    auto issue = [&](unsigned long long tt) {
-        const unsigned long long mb = tt / lc.n_bands;
-        const uint32_t band = (uint32_t)(tt - mb * lc.n_bands);
-        const uint32_t f = (uint32_t)(mb / p.n_modules);
-        const uint32_t m = (uint32_t)(mb - (unsigned long long)f * p.n_modules);
-        const int first = ((int)(m * p.rows + band * RB) - 1) & ~(int)(T - 1);
-        mbar_expect_tx(&stage_bar, lc.stage_bp * lc.stage_g * 16u);
-        tensor_copy_4d(lean_smem, &frames, 0, 0, first / (int)T, (int)f, &stage_bar);
-    };
-    if (STAGE && tid == 0) {
-        mbar_init(&stage_bar, 1);
-        fence_mbar_init();
-        if (blockIdx.x < n_tiles) issue(blockIdx.x);
-    }
-    for (uint32_t i = tid; i < (RB + 2) * P; i += nthr) tile[i] = 0.0f;
-    for (uint32_t i = tid; i < 2 * p.hist_bins; i += nthr) hpix[i] = 0;
-    if (tid < 2) list_n[tid] = 0;
-    __syncthreads();
-
     const int n_own_full = RB > ty ? ((int)RB - 1 - (int)ty) / (int)TY + 1 : 0;
-    const unsigned long long first = blockIdx.x, step = gridDim.x;
-    TileWalk walk(first, step, lc.n_bands, p.n_modules);
-    uint32_t par = 0;
-    for (unsigned long long t = first; t < n_tiles; t += step, walk.next(), par ^= 1u) {
-        const uint32_t m = walk.m, f = walk.f;
-        const int r0 = (int)walk.band * (int)RB;
+    {
+        const int r0 = (int)band * (int)RB;
         const int rows_here = min((int)RB, R - r0);
         const size_t mod_base = (size_t)m * p.module_px;
         const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
@@ -575,19 +592,19 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
         // wait for the stage so that their latency overlaps it
         float ca = 0.0f, cb = 0.0f;
         if (COLBANK) {
-            ca = -cmf[uca];
-            cb = -cmf[ucb];
+            ca = -__ldcg(cmf + uca);
+            cb = -__ldcg(cmf + ucb);
         }
         if (STAGE) {
             // one thread waits for the copy; the barrier orders its data
             // before every thread's reads
-            const bool ok = tid != 0 || mbar_wait(&stage_bar, par);
+            const bool ok = tid != 0 || mbar_wait(stage_bar, par);
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) {
                     atomicOr(err, 2u);
-                    mbar_wait(&stage_bar, par);  // the copy still writes this CTA's memory
+                    mbar_wait(stage_bar, par);  // the copy still writes this CTA's memory
                 }
-                return;
+                return false;
             }
         }
 
@@ -602,7 +619,8 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
             const uint32_t upr = p.units_per_row;
             for (uint32_t i = tid; i < (uint32_t)(rows_here + 2) * upr; i += nthr) {
                 const int r = r0 - 1 + (int)(i / upr);
-                cmt[i] = r >= 0 && r < R ? -cmf[((uint32_t)r / p.unit_rows) * upr + i % upr] : 0.0f;
+                cmt[i] = r >= 0 && r < R ? -__ldcg(cmf + ((uint32_t)r / p.unit_rows) * upr + i % upr)
+                                          : 0.0f;
             }
             __syncthreads();
         }
@@ -660,8 +678,10 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
         //    seed threshold's; rows are processed in pairs from two register
         //    sets, so the next row's loads are in flight while a row is
         //    processed
-        const int n_own = rows_here == (int)RB ? n_own_full
-                          : rows_here > (int)ty ? (rows_here - 1 - (int)ty) / (int)TY + 1 : 0;
+        const int n_own = !rowlane               ? 0
+                          : rows_here == (int)RB ? n_own_full
+                          : rows_here > (int)ty  ? (rows_here - 1 - (int)ty) / (int)TY + 1
+                                                 : 0;
         uint32_t cmask = 0;  // bit i: own row i may hold a candidate
         auto own_row = [&](const LeanRow& x, int i) {
             const int rl = 1 + (int)ty + i * (int)TY;
@@ -722,10 +742,7 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
         }
         __syncthreads();
         // the stage is read: the next tile's rows land during the seeds
-        if (STAGE && tid == 0 && t + step < n_tiles) {
-            fence_async_smem();  // order the generic reads of the stage before the copy
-            issue(t + step);
-        }
+        if (tid == 0) issue_next();
 
         // 3. seeds: local maximum on s = e > zero_thr ? e : 0 with the raster
         //    tie rule, 3x3 sums, count, centroid, emission
@@ -791,8 +808,8 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
                             h.frame = frame_base + f;
                             h.pixel = pix;
                             h.energy_kev = E;
-                            h.dx = Mx == 0.0f && E > 0.0f ? Mx : __fdiv_rn(Mx, E);
-                            h.dy = My == 0.0f && E > 0.0f ? My : __fdiv_rn(My, E);
+                            h.dx = moment_over_energy(Mx, E);
+                            h.dy = moment_over_energy(My, E);
                             h.count = (uint8_t)n;
                             h.npix = (uint8_t)npix;
                             h.flags = flags;
@@ -817,10 +834,262 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
         }
         __syncthreads();  // the tile is rewritten by the next band
     }
-    for (uint32_t b = tid; b < p.hist_bins; b += nthr) {
-        if (hpix[b]) atomicAdd(&p.hist_pix[b], (unsigned long long)hpix[b]);
-        if (hhit[b]) atomicAdd(&p.hist_hit[b], (unsigned long long)hhit[b]);
+    return true;
+}
+
+// Tiles first, first + step, ... < n_tiles (tile t: band t % n_bands of module
+// (t / n_bands) % n_modules of frame t / (n_bands n_modules)).  COLBANK: the
+// common-mode units span the module's full height, so a thread's four pixels
+// take the same two values on every row of a tile.  CORR: write corrected
+// frames.  STAGE: the tile's raw rows come by one tensor copy (the frames as
+// [frame][period][group][8 words]) into shared memory; the next tile's copy
+// is issued once the rows are read and lands while the seeds are tested.
+template <bool COLBANK, bool CORR, bool STAGE>
+__global__ void __launch_bounds__(kLeanThreads, 2)
+    stencil_lean_kernel(ChainParams p, const uint16_t* __restrict__ raw, uint32_t frame_base,
+                        CallOut out, LeanConfig lc, unsigned long long n_tiles,
+                        const __grid_constant__ CUtensorMap frames, uint32_t* __restrict__ err) {
+    extern __shared__ __align__(128) float lean_smem[];
+    __shared__ uint32_t list_n[2];
+    __shared__ uint64_t stage_bar;
+    const uint32_t P = lc.pitch, RB = lc.rb;
+    // staged raw rows (STAGE), 128-byte aligned, then the float tile
+    const uint32_t stage_words = STAGE ? lc.stage_bp * lc.stage_g * 8u : 0u;
+    LeanSmem sm;
+    sm.stg = reinterpret_cast<const uint16_t*>(lean_smem);
+    sm.tile = lean_smem + ((stage_words / 2 + 31u) & ~31u);
+    sm.hpix = reinterpret_cast<uint32_t*>(sm.tile + (RB + 2) * P);
+    sm.hhit = sm.hpix + p.hist_bins;
+    sm.list = sm.hhit + p.hist_bins;
+    sm.cmt = reinterpret_cast<float*>(sm.list + lc.list_cap);
+    sm.list_n = list_n;
+    sm.stage_bar = &stage_bar;
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+
+    // the copy of tile tt's raw rows (thread 0): from the period holding the
+    // row above the band (T is a power of two, so & ~(T - 1) floors to a
+    // period, -1 included)
+    auto issue = [&](unsigned long long tt) {
+        const uint32_t T = lc.stage_t;
+        const unsigned long long mb = tt / lc.n_bands;
+        const uint32_t band = (uint32_t)(tt - mb * lc.n_bands);
+        const uint32_t f = (uint32_t)(mb / p.n_modules);
+        const uint32_t m = (uint32_t)(mb - (unsigned long long)f * p.n_modules);
+        const int first = ((int)(m * p.rows + band * RB) - 1) & ~(int)(T - 1);
+        mbar_expect_tx(&stage_bar, lc.stage_bp * lc.stage_g * 16u);
+        tensor_copy_4d(lean_smem, &frames, 0, 0, first / (int)T, (int)f, &stage_bar);
+    };
+    if (STAGE && tid == 0) {
+        mbar_init(&stage_bar, 1);
+        fence_mbar_init();
+        if (blockIdx.x < n_tiles) issue(blockIdx.x);
     }
+    for (uint32_t i = tid; i < (RB + 2) * P; i += nthr) sm.tile[i] = 0.0f;
+    for (uint32_t i = tid; i < 2 * p.hist_bins; i += nthr) sm.hpix[i] = 0;
+    if (tid < 2) list_n[tid] = 0;
+    __syncthreads();
+
+    const unsigned long long first = blockIdx.x, step = gridDim.x;
+    TileWalk walk(first, step, lc.n_bands, p.n_modules);
+    uint32_t par = 0;
+    for (unsigned long long t = first; t < n_tiles; t += step, walk.next(), par ^= 1u) {
+        const bool ok = lean_tile<COLBANK, CORR, STAGE>(
+            p, raw, frame_base, out, lc, sm, walk.f, walk.m, walk.band, par, true, err, [&] {
+                if (STAGE && t + step < n_tiles) {
+                    fence_async_smem();  // order the generic reads of the stage before the copy
+                    issue(t + step);
+                }
+            });
+        if (!ok) return;
+    }
+    for (uint32_t b = tid; b < p.hist_bins; b += nthr) {
+        if (sm.hpix[b]) atomicAdd(&p.hist_pix[b], (unsigned long long)sm.hpix[b]);
+        if (sm.hhit[b]) atomicAdd(&p.hist_hit[b], (unsigned long long)sm.hhit[b]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The lean pair as one persistent launch over a work queue.  Items are
+// claimed in order from a global counter; superstep s holds the bank items
+// of frames [sK, sK + K) and then the stencil tiles of frames
+// [(s-1)K, sK), so a tile's raw rows were read by its bank items one
+// superstep earlier (K frames of raw, a few tens of MB, stay in L2) and no
+// kernel boundary separates the two kinds.  A tile waits (bounded) until
+// both banks of its module have published their common mode.  A tile only
+// waits on items earlier in the queue, and a CTA only ever waits on such
+// items while it holds a later one, so the waits cannot form a cycle
+// whichever CTAs are resident.
+
+struct QueuePlan {
+    uint32_t n_frames, K;     // frames of the launch, frames per superstep
+    uint32_t U, TPF;          // bank items and tiles per frame
+    uint32_t n_items;         // n_frames (U + TPF)
+};
+
+constexpr uint32_t kDepWaitLimit = 1u << 22;  // polls of a tile's dependency
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* a) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+// First queue index of superstep s.
+__device__ __forceinline__ uint32_t queue_start(const QueuePlan& q, uint32_t s) {
+    const uint32_t cm_frames = min(s * q.K, q.n_frames);
+    const uint32_t st_frames = s ? min((s - 1) * q.K, q.n_frames) : 0u;
+    return cm_frames * q.U + st_frames * q.TPF;
+}
+
+// Queue index i as a bank item (*cm true, *item) or a tile (*cm false, tile
+// index *item = f * TPF + m * n_bands + band).
+__device__ __forceinline__ void queue_decode(const QueuePlan& q, uint32_t i, bool* cm,
+                                             uint32_t* item) {
+    const uint32_t first = min(q.K, q.n_frames) * q.U;
+    uint32_t s = i < first ? 0u : 1u + (i - first) / (q.K * (q.U + q.TPF));
+    while (s > 0 && queue_start(q, s) > i) s--;
+    while (queue_start(q, s + 1) <= i) s++;
+    const uint32_t j = i - queue_start(q, s);
+    const uint32_t cm_here = s * q.K < q.n_frames ? min(q.K, q.n_frames - s * q.K) * q.U : 0u;
+    *cm = j < cm_here;
+    *item = *cm ? s * q.K * q.U + j : (s - 1) * q.K * q.TPF + (j - cm_here);
+}
+
+__global__ void __launch_bounds__(kBankThreads, 2)
+    chain_queue_kernel(ChainParams p, const uint16_t* __restrict__ raw, uint32_t frame_base,
+                       CallOut out, CmBigConfig cfg, CodeMap cmap, LeanConfig lc, QueuePlan q,
+                       const __grid_constant__ CUtensorMap frames, uint32_t* __restrict__ qsync,
+                       uint32_t* __restrict__ err) {
+    extern __shared__ __align__(128) uint4 qsmem[];
+    __shared__ BankShared sh;
+    __shared__ uint32_t list_n[2];
+    __shared__ uint32_t s_kind, s_item;  // the claimed item, decoded by thread 0
+    const uint32_t tid = threadIdx.x;
+    uint32_t* counter = qsync;  // the queue
+    uint32_t* done = qsync + 1;  // per (frame, module): banks published
+    // bank item view of the shared memory
+    BankSmem bs;
+    bs.stage = qsmem;
+    bs.hist = reinterpret_cast<uint32_t*>(qsmem + cmap.t * cmap.ne_box);
+    bs.cand = reinterpret_cast<float*>(bs.hist + kCmBins + 4);
+    bs.cidx = reinterpret_cast<uint32_t*>(bs.cand + kCandCap);
+    // tile view of the same memory (the summary histograms are flushed to
+    // global memory before a bank item reuses it)
+    LeanSmem ts;
+    ts.stg = nullptr;
+    ts.tile = reinterpret_cast<float*>(qsmem);
+    ts.hpix = reinterpret_cast<uint32_t*>(ts.tile + (lc.rb + 2) * lc.pitch);
+    ts.hhit = ts.hpix + p.hist_bins;
+    ts.list = ts.hhit + p.hist_bins;
+    ts.cmt = nullptr;
+    ts.list_n = list_n;
+    ts.stage_bar = nullptr;
+    const bool rowlane = tid < lc.tx * lc.ty;
+
+    // thread 0 decodes a claimed index for the block (kind 2: past the end)
+    auto publish = [&](uint32_t i) {
+        bool cm = false;
+        uint32_t it = 0;
+        if (i < q.n_items) queue_decode(q, i, &cm, &it);
+        s_kind = i >= q.n_items ? 2u : cm ? 0u : 1u;
+        s_item = it;
+    };
+    if (tid == 0) {
+        mbar_init(&sh.bar, 1);
+        fence_mbar_init();
+        publish(atomicAdd(counter, 1u));
+    }
+    __syncthreads();
+    uint32_t parity = 0, par = 0;
+    int prev = -1;             // kind of the previous item: 0 bank, 1 tile
+    bool staged = false;       // thread 0: this bank item's copy was issued
+    auto flush_hists = [&] {
+        for (uint32_t b = tid; b < p.hist_bins; b += blockDim.x) {
+            if (ts.hpix[b]) atomicAdd(&p.hist_pix[b], (unsigned long long)ts.hpix[b]);
+            if (ts.hhit[b]) atomicAdd(&p.hist_hit[b], (unsigned long long)ts.hhit[b]);
+        }
+    };
+    while (true) {
+        const uint32_t kind = s_kind, item = s_item;
+        if (kind == 2) break;
+        uint32_t nxt = 0;
+        if (tid == 0) nxt = atomicAdd(counter, 1u);  // claimed now, read at the item's end
+        if (kind == 0) {
+            if (prev == 1) {
+                flush_hists();
+                __syncthreads();  // the histograms are read before the bank item overwrites them
+            }
+            if (tid == 0 && !staged) {
+                fence_async_smem();  // the tile's generic accesses before the copy
+                bank_issue(p, cmap, &frames, bs.stage, &sh.bar, item);
+            }
+            if (prev != 0) {
+                for (uint32_t k = tid; k < (kCmBins + 4) / 4; k += blockDim.x)
+                    reinterpret_cast<uint4*>(bs.hist)[k] = make_uint4(0, 0, 0, 0);
+                if (tid == 0) sh.s_cand = 0;
+                // (the item's first barrier orders these stores before its passes)
+            }
+            bool next_staged = false;
+            const bool ok = cm_bank_item(p, out.cm, cfg, cmap, raw, item, parity, bs, kCandCap, sh,
+                                         err, [&] {
+                                             if (nxt >= q.n_items) return;
+                                             bool ncm;
+                                             uint32_t nitem;
+                                             queue_decode(q, nxt, &ncm, &nitem);
+                                             if (ncm) {
+                                                 fence_async_smem();
+                                                 bank_issue(p, cmap, &frames, bs.stage, &sh.bar,
+                                                            nitem);
+                                                 next_staged = true;
+                                             }
+                                         });
+            parity ^= 1u;
+            if (!ok) return;
+            staged = next_staged;
+            // publish the bank's common mode: every thread's stores (the
+            // winning thread's included) are fenced before the count
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                const uint32_t f = item / p.units_per_frame;
+                const uint32_t m = (item - f * p.units_per_frame) / p.units_per_module;
+                atomicAdd(done + f * p.n_modules + m, 1u);
+            }
+            prev = 0;
+        } else {
+            const uint32_t f = item / q.TPF;
+            const uint32_t rem = item - f * q.TPF;
+            const uint32_t m = rem / lc.n_bands, band = rem - m * lc.n_bands;
+            if (prev != 1) {
+                // zero summaries, zero pad columns, fresh list counters
+                for (uint32_t k = tid; k < 2 * p.hist_bins; k += blockDim.x) ts.hpix[k] = 0;
+                for (uint32_t k = tid; k < (lc.rb + 2) * 8; k += blockDim.x) {
+                    const uint32_t r = k >> 3, c = k & 7u;
+                    ts.tile[r * lc.pitch + (c < 4 ? c : p.cols + c)] = 0.0f;
+                }
+                if (tid < 2) list_n[tid] = 0;
+                par = 0;
+            }
+            // both banks of the module have published their common mode
+            bool ok = true;
+            if (tid == 0) {
+                const uint32_t* d = done + f * p.n_modules + m;
+                uint32_t it = 0;
+                while (ld_acquire_gpu(d) < p.units_per_module && ++it < kDepWaitLimit)
+                    __nanosleep(64);
+                ok = it < kDepWaitLimit;
+                if (!ok) atomicOr(err, 4u);
+            }
+            if (__syncthreads_or(!ok)) return;
+            lean_tile<true, false, false>(p, raw, frame_base, out, lc, ts, f, m, band, par,
+                                          rowlane, err, [] {});
+            par ^= 1u;
+            prev = 1;
+        }
+        if (tid == 0) publish(nxt);
+        __syncthreads();
+    }
+    if (prev == 1) flush_hists();
 }
 
 }  // namespace
@@ -952,6 +1221,25 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+// The call's frames as the tensor [frame][period][group][8 words] of uint16
+// with the bank item's box.
+static cudaError_t encode_bank_map(const ChainParams& p, const CodeMap& cmap,
+                                   const uint16_t* raw, uint32_t n_frames, CUtensorMap* map) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const uint64_t G = (uint64_t)cmap.t * p.cols / 8;
+    const cuuint64_t dims[4] = {8, G, (cuuint64_t)p.frame_px / ((cuuint64_t)cmap.t * p.cols),
+                                n_frames};
+    const cuuint64_t strides[3] = {16, G * 16, (cuuint64_t)p.frame_px * 2};
+    const cuuint32_t box[4] = {8, cmap.w8, cmap.bp, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<uint16_t*>(raw), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
 cudaError_t launch_cm_bank(const ChainParams& p, const CmBigConfig& cfg, const CodeMap& cmap,
                            const uint16_t* raw, uint32_t n_frames, float* cm, uint32_t* err,
                            cudaStream_t stream) {
@@ -969,20 +1257,9 @@ cudaError_t launch_cm_bank(const ChainParams& p, const CmBigConfig& cfg, const C
         if (e != cudaSuccess) return e;
         g_attr_dev_bank = dev;
     }
-    // the call's frames as [frame][period][group][8 words] of uint16
-    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
-    const uint64_t G = (uint64_t)cmap.t * p.cols / 8;
-    const cuuint64_t dims[4] = {8, G, (cuuint64_t)p.frame_px / ((cuuint64_t)cmap.t * p.cols),
-                                n_frames};
-    const cuuint64_t strides[3] = {16, G * 16, (cuuint64_t)p.frame_px * 2};
-    const cuuint32_t box[4] = {8, cmap.w8, cmap.bp, 1};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUtensorMap map;
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<uint16_t*>(raw), dims, strides,
-            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
+    cudaError_t me = encode_bank_map(p, cmap, raw, n_frames, &map);
+    if (me != cudaSuccess) return me;
     const size_t smem = cm_bank_smem_bytes(p, cmap);
     const unsigned long long grid = std::min<unsigned long long>(
         items, (unsigned long long)std::max<uint32_t>(cmap.ctas_per_sm, 1) * device_sm_count());
@@ -1132,6 +1409,63 @@ cudaError_t launch_stencil_lean(const ChainParams& p, const LeanConfig& lc, cons
                                  : (corr ? stencil_lean_kernel<false, true, false>
                                          : stencil_lean_kernel<false, false, false>));
     k<<<(unsigned)grid, threads, smem, stream>>>(p, raw, frame_base, out, lc, n_tiles, map, err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Host side of the work-queue launch.
+
+constexpr size_t kQueueSuperstepBytes = 20u << 20;  // raw per superstep (stays in L2)
+
+size_t queue_smem_bytes(const ChainParams& p, const CodeMap& cmap, const LeanConfig& lc) {
+    return std::max(cm_bank_smem_bytes(p, cmap), lean_smem_bytes(p, lc));
+}
+
+bool queue_supported(const ChainParams& p, const CodeMap& cmap, const LeanConfig& lc) {
+    return lc.ok && lc.colbank && !staged(lc) && lc.tx * lc.ty <= kBankThreads &&
+           cm_bank_supported(p, cmap) && queue_smem_bytes(p, cmap, lc) <= 110 * 1024 &&
+           p.cols >= 8;
+}
+
+size_t queue_sync_words(const ChainParams& p, uint32_t n_frames) {
+    return 1 + (size_t)n_frames * p.n_modules;
+}
+
+static int g_attr_dev_queue = -1;
+
+cudaError_t launch_chain_queue(const ChainParams& p, const CmBigConfig& cfg, const CodeMap& cmap,
+                               const LeanConfig& lc, const uint16_t* raw, uint32_t n_frames,
+                               uint32_t frame_base, const CallOut& out, uint32_t* qsync,
+                               uint32_t* err, cudaStream_t stream) {
+    if (n_frames == 0) return cudaSuccess;
+    const uint64_t per_frame = (uint64_t)p.units_per_frame + (uint64_t)p.n_modules * lc.n_bands;
+    if ((uint64_t)n_frames * per_frame >= (1ull << 31)) return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (g_attr_dev_queue != dev) {
+        cudaError_t e = cudaFuncSetAttribute(chain_queue_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             110 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(chain_queue_kernel,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+        g_attr_dev_queue = dev;
+    }
+    CUtensorMap map;
+    cudaError_t e = encode_bank_map(p, cmap, raw, n_frames, &map);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(qsync, 0, queue_sync_words(p, n_frames) * 4, stream))) return e;
+    QueuePlan q;
+    q.n_frames = n_frames;
+    q.K = (uint32_t)std::max<size_t>(1, kQueueSuperstepBytes / ((size_t)p.frame_px * 2));
+    q.U = p.units_per_frame;
+    q.TPF = p.n_modules * lc.n_bands;
+    q.n_items = (uint32_t)(n_frames * per_frame);
+    const size_t smem = queue_smem_bytes(p, cmap, lc);
+    const unsigned grid = (unsigned)std::min<uint64_t>(q.n_items, 2ull * device_sm_count());
+    chain_queue_kernel<<<grid, kBankThreads, smem, stream>>>(p, raw, frame_base, out, cfg, cmap,
+                                                             lc, q, map, qsync, err);
     return cudaGetLastError();
 }
 

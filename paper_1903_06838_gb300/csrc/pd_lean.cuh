@@ -80,4 +80,19 @@ cudaError_t launch_stencil_lean(const ChainParams& p, const LeanConfig& lc, cons
                                 uint32_t n_frames, uint32_t frame_base, const CallOut& out,
                                 uint32_t* err, cudaStream_t stream);
 
+// The lean pair as one persistent launch over a work queue (bank items of
+// frames [sK, sK + K) then the stencil tiles of the K frames before them, K
+// frames of raw staying in L2 between the two), for column-bank units and
+// the unstaged stencil without corrected frames.  out.cm receives the common
+// mode of all n_frames.  qsync: queue_sync_words(p, n_frames) words of
+// device scratch (cleared by the launch).  err bits: 1 a staged copy's wait,
+// 4 a tile's wait for its banks gave up.
+size_t queue_smem_bytes(const ChainParams& p, const CodeMap& cmap, const LeanConfig& lc);
+bool queue_supported(const ChainParams& p, const CodeMap& cmap, const LeanConfig& lc);
+size_t queue_sync_words(const ChainParams& p, uint32_t n_frames);
+cudaError_t launch_chain_queue(const ChainParams& p, const CmBigConfig& cfg, const CodeMap& cmap,
+                               const LeanConfig& lc, const uint16_t* raw, uint32_t n_frames,
+                               uint32_t frame_base, const CallOut& out, uint32_t* qsync,
+                               uint32_t* err, cudaStream_t stream);
+
 }  // namespace pd
