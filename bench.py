@@ -968,7 +968,8 @@ def batch_mix_run(args, dev, peak):
     gbs = raw_bytes / s_step / 1e9
     res = {"workload": "4096 frames: 1366 ePix 704x768 (6 keV) + 1365 CSPAD 32x185x388 (8 keV) "
                        "+ 1365 16x352x384 (12 keV), occupancy log-uniform 0.1-10 % per frame; "
-                       "96 MB chunks, each item's kernels per chunk, captured once and "
+                       "each item through its context's schedule (600 MB chunks, two streams), "
+                       "captured once and "
                        "replayed as a CUDA graph; inputs far larger than L2",
            "frames_per_s": round(n_frames / s_step), "ms_per_batch": round(s_step * 1e3, 2),
            "raw_gb": round(raw_bytes / 1e9, 2), "raw_gbs": round(gbs, 1),

@@ -348,11 +348,12 @@ int pd_set_tuning(pd_ctx* ctx, const pd_tuning* tuning);
 int pd_autotune(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frames,
                 pd_tuning* best, float* best_us_per_frame);
 
-/* Batched launches over contexts of different geometries.  The frames of
- * all items are split into chunks of about 96 MB of raw data (a chunk may
- * hold frames of several items), so a chunk's second pass re-reads its raw
- * frames from L2.  By default each chunk runs the kernels pd_process uses,
- * item by item; with pd_batch_set_mixed(batch, 1) each chunk is one
+/* Batched launches over contexts of different geometries.  By default each
+ * item runs as pd_process runs it (its context's chunks, band height and
+ * two-stream overlap), item after item on the batch's stream, its common
+ * mode in the batch's scratch.  With pd_batch_set_mixed(batch, 1) the
+ * frames of all items are split into chunks of about 96 MB of raw data (a
+ * chunk may hold frames of several items) and each chunk is one
  * persistent common-mode launch over every (item, frame, unit) of the chunk
  * and one persistent stencil launch over all its band tiles (items must
  * then use the band stencil, every geometry with at most 2048 columns per

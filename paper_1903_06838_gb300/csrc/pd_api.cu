@@ -1018,18 +1018,6 @@ int batch_check_items(const pd_batch* b, const pd_batch_item* items, uint32_t n)
     return PD_OK;
 }
 
-// The launches pd_process makes for `nf` frames of one context (the
-// one-kernel chain, or the common-mode + stencil pair), without zeroing
-// the hit counter.
-cudaError_t launch_chain_piece(pd_ctx* c, const uint16_t* fr, uint32_t nf, uint32_t frame_base,
-                               const pd::CallOut& co, cudaStream_t s) {
-    if (fused_on(c))
-        return pd::launch_fused(c->params, c->fused_cfg, fr, nf, frame_base, co, s);
-    cudaError_t e = launch_cm(c, fr, nf, co.cm, s);
-    if (e != cudaSuccess) return e;
-    return launch_stencil_for(c, fr, nf, frame_base, co, s);
-}
-
 int batch_enqueue(pd_batch* b, int slot, const pd_batch_item* items, uint32_t n,
                   cudaStream_t s) {
     int rc = batch_check_items(b, items, n);
@@ -1077,6 +1065,22 @@ int batch_enqueue(pd_batch* b, int slot, const pd_batch_item* items, uint32_t n,
         }
         item_cm[i] = cm;
     }
+    cudaError_t e;
+    for (uint32_t i = 0; i < n; i++)
+        if ((e = cudaMemsetAsync(items[i].out.n_hits, 0, sizeof(uint32_t), s)))
+            return fail_cuda(e, "zero n_hits");
+    if (!b->mixed) {
+        // each item as pd_process runs it (its context's chunks, band height
+        // and two-stream overlap), its common mode in the batch's scratch
+        for (uint32_t i = 0; i < n; i++) {
+            pd_outputs o = items[i].out;
+            o.cm = item_cm[i];
+            const int r = run_chain(items[i].ctx, items[i].frames, items[i].n_frames,
+                                    items[i].frame_base, &o, s, false);
+            if (r) return r;
+        }
+        return PD_OK;
+    }
     const auto chunks = plan_chunks(items, n);
     const size_t entries = plan_entries(chunks);
     if (entries > b->table_cap[slot]) {
@@ -1114,22 +1118,6 @@ int batch_enqueue(pd_batch* b, int slot, const pd_batch_item* items, uint32_t n,
             tiles += d.st_tiles;
         }
         launches.push_back(L);
-    }
-    cudaError_t e;
-    for (uint32_t i = 0; i < n; i++)
-        if ((e = cudaMemsetAsync(items[i].out.n_hits, 0, sizeof(uint32_t), s)))
-            return fail_cuda(e, "zero n_hits");
-    if (!b->mixed) {
-        // per chunk, each piece through the kernels pd_process uses
-        size_t k = 0;
-        for (const auto& ch : chunks)
-            for (const Piece& pc : ch) {
-                const pd::BatchItem& d = h[k++];
-                if ((e = launch_chain_piece(items[pc.item].ctx, d.raw, d.n_frames, d.frame_base,
-                                            d.out, s)))
-                    return fail_cuda(e, "batch kernel launch");
-            }
-        return PD_OK;
     }
     e = cudaMemcpyAsync(b->d_table[slot], h, entries * sizeof(pd::BatchItem),
                         cudaMemcpyHostToDevice, s);
