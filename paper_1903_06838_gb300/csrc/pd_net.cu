@@ -206,20 +206,31 @@ struct AtomicAcc {  // out[i][j] += acc
 };
 
 // ---- small kernels --------------------------------------------------------
-__global__ void colsum_kernel(const float* __restrict__ a, int M, int N, float* __restrict__ out) {
-    // out[j] += sum_i a[i][j]
-    const int j = blockIdx.x;
+// out[j] += sum_i a[i][j] for j < N <= 256: each block sums a slice of rows
+// (thread t adds column t % N of rows t / N, t / N + 256 / N, ...; the rows
+// are contiguous, so the loads coalesce), then one atomic per column.
+__global__ void colsum_kernel(const float* __restrict__ a, int M, int N, int rows_per_block,
+                              float* __restrict__ out) {
+    __shared__ float part[256];
+    const int t = threadIdx.x, lanes = blockDim.x / N * N;
+    const int j = t % N, r0 = blockIdx.x * rows_per_block;
+    const int r1 = min(M, r0 + rows_per_block);
     float s = 0.0f;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) s += a[(size_t)i * N + j];
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __shared__ float ws[32];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    if (t < lanes)
+        for (int i = r0 + t / N; i < r1; i += lanes / N) s += a[(size_t)i * N + j];
+    part[t] = t < lanes ? s : 0.0f;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.0f;
-        for (int w = 0; w < (int)(blockDim.x + 31) / 32; w++) t += ws[w];
-        atomicAdd(&out[j], t);
+    if (t < N) {
+        float tot = 0.0f;
+        for (int k = t; k < lanes; k += N) tot += part[k];
+        atomicAdd(&out[t], tot);
     }
+}
+
+void colsum(const float* a, int M, int N, float* out, cudaStream_t s) {
+    if (M <= 0) return;
+    const int rows = 512;
+    colsum_kernel<<<(M + rows - 1) / rows, 256, 0, s>>>(a, M, N, rows, out);
 }
 
 // Softmax cross-entropy over out[:, 0:5] and masked squared error of
@@ -419,12 +430,15 @@ cudaError_t backward(pd_net* net, const float* x, int n, const uint8_t* counts, 
     loss_kernel<<<(n + 255) / 256, 256, 0, s>>>(net->out, counts, tgt, mask, n,
                                                 std::max(1.0f, nreg), lam, net->dout, loss);
     if ((e = cudaGetLastError())) return e;
+    // split-K of the weight gradients (K = hits, or hits x 25 positions for
+    // the convolutions): enough CTAs to fill the GPU, about 1024 rows each
     const int sp = std::max(1, std::min(64, n * NPOS / 4096));
+    const int sp_conv = std::max(1, std::min(512, n * NPOS / 1024));
     // heads
     if ((e = gemm(NOUT, NH, n, ColMajor{net->dout, NOUT}, RowMajor{net->h3, NH},
                   AtomicAcc{gw + OW4, NH}, s, sp)))
         return e;
-    colsum_kernel<<<NOUT, 256, 0, s>>>(net->dout, n, NOUT, gw + OB4);
+    colsum(net->dout, n, NOUT, gw + OB4, s);
     if ((e = gemm(n, NH, NOUT, RowMajor{net->dout, NOUT}, RowMajor{w + OW4, NH},
                   ReluGrad{net->dz3, net->h3, NH}, s)))
         return e;
@@ -432,23 +446,23 @@ cudaError_t backward(pd_net* net, const float* x, int n, const uint8_t* counts, 
     if ((e = gemm(NH, NPOS * C2, n, ColMajor{net->dz3, NH}, RowMajor{net->h2, NPOS * C2},
                   AtomicAcc{gw + OW3, NPOS * C2}, s, sp)))
         return e;
-    colsum_kernel<<<NH, 256, 0, s>>>(net->dz3, n, NH, gw + OB3);
+    colsum(net->dz3, n, NH, gw + OB3, s);
     if ((e = gemm(n, NPOS * C2, NH, RowMajor{net->dz3, NH}, RowMajor{w + OW3, NPOS * C2},
                   ReluGrad{net->dz2, net->h2, NPOS * C2}, s)))
         return e;
     // conv2: weights, bias, input
     if ((e = gemm(C2, 9 * C1, n * NPOS, ColMajor{net->dz2, C2}, Im2col{net->h1, C1},
-                  AtomicAcc{gw + OW2, 9 * C1}, s, sp)))
+                  AtomicAcc{gw + OW2, 9 * C1}, s, sp_conv)))
         return e;
-    colsum_kernel<<<C2, 256, 0, s>>>(net->dz2, n * NPOS, C2, gw + OB2);
+    colsum(net->dz2, n * NPOS, C2, gw + OB2, s);
     if ((e = gemm(n * NPOS, C1, 9 * C2, ConvTransposeA{net->dz2}, ConvTransposeB{w + OW2},
                   ReluGrad{net->dz1, net->h1, C1}, s)))
         return e;
     // conv1: weights, bias
     if ((e = gemm(C1, 9, n * NPOS, ColMajor{net->dz1, C1}, Im2col{x, 1}, AtomicAcc{gw + OW1, 9},
-                  s, sp)))
+                  s, sp_conv)))
         return e;
-    colsum_kernel<<<C1, 256, 0, s>>>(net->dz1, n * NPOS, C1, gw + OB1);
+    colsum(net->dz1, n * NPOS, C1, gw + OB1, s);
     return cudaGetLastError();
 }
 
