@@ -161,24 +161,6 @@ struct Im2col {  // element ((hit, p), k*C + c) of the im2col of act [hit][25][C
         return q < 0 ? 0.0f : act[((size_t)hit * NPOS + q) * C + c];
     }
 };
-// Gradient of conv2's input: element ((hit, q), k*32 + c) = dz2[hit][q - off k][c]
-// (the position whose offset-k neighbour is q), zero outside the grid.
-struct ConvTransposeA {
-    const float* dz;
-    __device__ float operator()(int row, int col) const {
-        const int hit = row / NPOS, q = row % NPOS, k = col / C2, c = col % C2;
-        const int p = nbr(q, 8 - k);  // the mirrored offset
-        return p < 0 ? 0.0f : dz[((size_t)hit * NPOS + p) * C2 + c];
-    }
-};
-struct ConvTransposeB {  // element (k*32 + c, c_in) = W2[c][k*32 + c_in]
-    const float* w2;
-    __device__ float operator()(int kk, int cin) const {
-        const int k = kk / C2, c = kk % C2;
-        return w2[(size_t)c * (9 * C1) + k * C1 + cin];
-    }
-};
-
 // ---- epilogues -----------------------------------------------------------
 struct BiasAct {  // out[i][j] = act(acc + bias[j])
     float* out;
@@ -231,6 +213,222 @@ void colsum(const float* a, int M, int N, float* out, cudaStream_t s) {
     if (M <= 0) return;
     const int rows = 512;
     colsum_kernel<<<(M + rows - 1) / rows, 256, 0, s>>>(a, M, N, rows, out);
+}
+
+// ---- convolution weight gradients ------------------------------------------
+// dW[c_out][tap][c_in] = sum over hits and positions p of
+// bf16(dz[hit][p][c_out]) * bf16(act[hit][nbr(p, tap)][c_in]) (zero where the
+// neighbour is outside the 5x5 grid), the operand rounding of the GEMMs.
+
+// Position p of the 5x5 grid in the zero-bordered 7x7 grid; the neighbour at
+// tap k is then a constant offset (k / 3 - 1) * 7 + k % 3 - 1.
+__device__ __forceinline__ int pad7(int p) { return (p / 5 + 1) * 7 + p % 5 + 1; }
+
+constexpr int WG_HB = 8;                        // hits per staged chunk
+constexpr int WG_ROWS = WG_HB * 49;             // 392 padded positions
+constexpr int WG_K = (WG_ROWS + 15) / 16 * 16;  // 400: whole k-steps
+constexpr int WG_PAD = 8;                       // zero rows before and after (offsets -8..8)
+constexpr int WG_LD = WG_PAD + WG_K + WG_PAD;   // 416 bf16 per channel row
+
+// conv2: one warp per tap (9 warps), a 32 x 32 block of c_out x c_in each,
+// on mma.sync m16n8k16; CTAs stride over chunks of WG_HB hits and add their
+// sums to gw once.  Shared memory: dz and act transposed to
+// [channel][padded position], bf16.
+__global__ void __launch_bounds__(288) conv2_wgrad_kernel(const float* __restrict__ dz,
+                                                          const float* __restrict__ act, int n,
+                                                          float* __restrict__ gw) {
+    extern __shared__ __align__(16) uint16_t wg_smem[];
+    uint16_t* dzT = wg_smem;              // [C2][WG_LD]
+    uint16_t* acT = wg_smem + C2 * WG_LD;  // [C1][WG_LD]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    const int tap = warp;
+    const int off = (tap / 3 - 1) * 7 + tap % 3 - 1;
+    float acc[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[a][b][c] = 0.0f;
+    for (int i = tid; i < (C2 + C1) * WG_LD / 2; i += blockDim.x)
+        reinterpret_cast<uint32_t*>(wg_smem)[i] = 0u;  // borders and padding stay zero
+    for (int h0 = blockIdx.x * WG_HB; h0 < n; h0 += gridDim.x * WG_HB) {
+        __syncthreads();  // the previous chunk is read
+        const int nh = min(WG_HB, n - h0);
+        for (int e = tid; e < WG_HB * NPOS * 32; e += blockDim.x) {
+            const int h = e / (NPOS * 32), pc = e - h * (NPOS * 32);
+            const int pos = pc / 32, c = pc - pos * 32;
+            const int row = WG_PAD + h * 49 + pad7(pos);
+            const size_t src = ((size_t)(h0 + h) * NPOS + pos) * 32 + c;
+            dzT[c * WG_LD + row] = h < nh ? bf16_bits(dz[src]) : (uint16_t)0;
+            acT[c * WG_LD + row] = h < nh ? bf16_bits(act[src]) : (uint16_t)0;
+        }
+        __syncthreads();
+        if (warp < 9) {
+            for (int k0 = 0; k0 < WG_K; k0 += 16) {
+                const int ka = WG_PAD + k0 + 2 * tq;
+                uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+                for (int mi = 0; mi < 2; mi++) {
+                    const uint16_t* r0 = dzT + (mi * 16 + g) * WG_LD;
+                    const uint16_t* r8 = r0 + 8 * WG_LD;
+                    af[mi][0] = *reinterpret_cast<const uint32_t*>(r0 + ka);
+                    af[mi][1] = *reinterpret_cast<const uint32_t*>(r8 + ka);
+                    af[mi][2] = *reinterpret_cast<const uint32_t*>(r0 + ka + 8);
+                    af[mi][3] = *reinterpret_cast<const uint32_t*>(r8 + ka + 8);
+                }
+#pragma unroll
+                for (int ni = 0; ni < 4; ni++) {
+                    const uint16_t* rb = acT + (ni * 8 + g) * WG_LD + ka + off;
+                    bfr[ni][0] = (uint32_t)rb[0] | (uint32_t)rb[1] << 16;
+                    bfr[ni][1] = (uint32_t)rb[8] | (uint32_t)rb[9] << 16;
+                }
+#pragma unroll
+                for (int mi = 0; mi < 2; mi++)
+#pragma unroll
+                    for (int ni = 0; ni < 4; ni++) mma_bf16(acc[mi][ni], af[mi], bfr[ni]);
+            }
+        }
+    }
+    if (warp < 9) {
+#pragma unroll
+        for (int mi = 0; mi < 2; mi++)
+#pragma unroll
+            for (int ni = 0; ni < 4; ni++) {
+                const int co = mi * 16 + g, ci = ni * 8 + 2 * tq;
+                float* w0 = gw + (size_t)co * (9 * C1) + tap * C1 + ci;
+                float* w8 = w0 + 8 * (9 * C1);
+                atomicAdd(w0, acc[mi][ni][0]);
+                atomicAdd(w0 + 1, acc[mi][ni][1]);
+                atomicAdd(w8, acc[mi][ni][2]);
+                atomicAdd(w8 + 1, acc[mi][ni][3]);
+            }
+    }
+}
+
+// conv1 (one input channel): thread t owns output (c_out = t / 9, tap = t % 9)
+// and sums over its CTA's hits in float32 (bf16-rounded operands).
+__global__ void __launch_bounds__(288) conv1_wgrad_kernel(const float* __restrict__ dz,
+                                                          const float* __restrict__ x, int n,
+                                                          float* __restrict__ gw) {
+    __shared__ float sdz[WG_HB][NPOS][C1];
+    __shared__ float sx[WG_HB][49];
+    const int tid = threadIdx.x;
+    const int co = tid / 9, tap = tid % 9;
+    const int off = (tap / 3 - 1) * 7 + tap % 3 - 1;
+    for (int i = tid; i < WG_HB * 49; i += blockDim.x) (&sx[0][0])[i] = 0.0f;
+    float acc = 0.0f;
+    for (int h0 = blockIdx.x * WG_HB; h0 < n; h0 += gridDim.x * WG_HB) {
+        __syncthreads();
+        const int nh = min(WG_HB, n - h0);
+        for (int e = tid; e < WG_HB * NPOS * C1; e += blockDim.x) {
+            const int h = e / (NPOS * C1);
+            (&sdz[0][0][0])[e] =
+                h < nh ? __bfloat162float(__float2bfloat16_rn(dz[(size_t)h0 * NPOS * C1 + e])) : 0.0f;
+        }
+        for (int e = tid; e < WG_HB * NPOS; e += blockDim.x) {
+            const int h = e / NPOS, pos = e - h * NPOS;
+            sx[h][pad7(pos)] =
+                h < nh ? __bfloat162float(__float2bfloat16_rn(x[(size_t)h0 * NPOS + e])) : 0.0f;
+        }
+        __syncthreads();
+        if (tid < C1 * 9)
+            for (int h = 0; h < nh; h++)
+#pragma unroll 5
+                for (int pos = 0; pos < NPOS; pos++)
+                    acc = __fmaf_rn(sdz[h][pos][co], sx[h][pad7(pos) + off], acc);
+    }
+    if (tid < C1 * 9) atomicAdd(&gw[co * 9 + tap], acc);
+}
+
+// conv2 forward (h2 = relu(conv(h1) + b2)) and the gradient of its input
+// (dz1 = conv_transpose(dz2) where h1 > 0) on mma.sync m16n8k16: for tap k
+// the input rows are the padded rows shifted by +off(k) (forward) or -off(k)
+// (the transpose), so each is a GEMM over K = 9 taps x 32 channels from a
+// zero-bordered [row][channel] tile of WG_HB hits.  8 warps; warp w computes
+// the 16-row tiles w, w + 8, ... of the 400 padded rows, all 32 outputs.
+template <bool DGRAD>
+__global__ void __launch_bounds__(256) conv2_mma_kernel(const float* __restrict__ in,
+                                                        const float* __restrict__ w2,
+                                                        const float* __restrict__ aux, int n,
+                                                        float* __restrict__ out) {
+    __shared__ __align__(16) uint16_t ap[WG_LD][32];    // input, padded rows
+    __shared__ __align__(16) uint16_t ws[32][9 * 32];   // [n][tap * 32 + k channel]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    // weights: forward ws[c_out][tap][c_in] = W2; transpose ws[c_in][tap][c_out]
+    for (int e = tid; e < 32 * 9 * 32; e += blockDim.x) {
+        const int a = e / (9 * 32), rest = e - a * (9 * 32), tap = rest / 32, b = rest % 32;
+        ws[a][rest] = bf16_bits(DGRAD ? w2[(size_t)b * (9 * C1) + tap * C1 + a] : w2[e]);
+    }
+    for (int i = tid; i < WG_LD * 32 / 2; i += blockDim.x) reinterpret_cast<uint32_t*>(ap)[i] = 0u;
+    for (int h0 = blockIdx.x * WG_HB; h0 < n; h0 += gridDim.x * WG_HB) {
+        __syncthreads();  // the previous chunk is read
+        const int nh = min(WG_HB, n - h0);
+        for (int e = tid; e < WG_HB * NPOS * 32; e += blockDim.x) {
+            const int h = e / (NPOS * 32), pc = e - h * (NPOS * 32);
+            const int pos = pc / 32, c = pc - pos * 32;
+            ap[WG_PAD + h * 49 + pad7(pos)][c] =
+                h < nh ? bf16_bits(in[(size_t)h0 * NPOS * 32 + e]) : (uint16_t)0;
+        }
+        __syncthreads();
+        for (int mt = warp; mt < WG_K / 16; mt += 8) {
+            float acc[4][4];
+#pragma unroll
+            for (int b = 0; b < 4; b++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[b][c] = 0.0f;
+            const int r0 = mt * 16 + g;  // padded row of a0 / a2 (a1 / a3: r0 + 8)
+#pragma unroll 3
+            for (int tap = 0; tap < 9; tap++) {
+                const int off = (tap / 3 - 1) * 7 + tap % 3 - 1;
+                const int ra = WG_PAD + r0 + (DGRAD ? -off : off);
+#pragma unroll
+                for (int kc = 0; kc < 32; kc += 16) {
+                    uint32_t af[4], bfr[4][2];
+                    af[0] = *reinterpret_cast<const uint32_t*>(&ap[ra][kc + 2 * tq]);
+                    af[1] = *reinterpret_cast<const uint32_t*>(&ap[ra + 8][kc + 2 * tq]);
+                    af[2] = *reinterpret_cast<const uint32_t*>(&ap[ra][kc + 8 + 2 * tq]);
+                    af[3] = *reinterpret_cast<const uint32_t*>(&ap[ra + 8][kc + 8 + 2 * tq]);
+#pragma unroll
+                    for (int ni = 0; ni < 4; ni++) {
+                        const uint16_t* wb = &ws[ni * 8 + g][tap * 32 + kc + 2 * tq];
+                        bfr[ni][0] = *reinterpret_cast<const uint32_t*>(wb);
+                        bfr[ni][1] = *reinterpret_cast<const uint32_t*>(wb + 8);
+                    }
+#pragma unroll
+                    for (int ni = 0; ni < 4; ni++) mma_bf16(acc[ni], af, bfr[ni]);
+                }
+            }
+            // rows r0 and r0 + 8: outputs of interior positions of real hits
+#pragma unroll
+            for (int half = 0; half < 2; half++) {
+                const int R = r0 + 8 * half, h = R / 49, pp = R - h * 49;
+                const int y = pp / 7, x = pp - y * 7;
+                if (h >= nh || y < 1 || y > 5 || x < 1 || x > 5) continue;
+                const size_t o = ((size_t)(h0 + h) * NPOS + (y - 1) * 5 + (x - 1)) * 32;
+#pragma unroll
+                for (int ni = 0; ni < 4; ni++)
+#pragma unroll
+                    for (int j = 0; j < 2; j++) {
+                        const int c = ni * 8 + 2 * tq + j;
+                        const float v = acc[ni][2 * half + j];
+                        if (DGRAD)
+                            out[o + c] = aux[o + c] > 0.0f ? v : 0.0f;
+                        else
+                            out[o + c] = fmaxf(v + aux[c], 0.0f);
+                    }
+            }
+        }
+    }
+}
+
+// a[i] = relu(a[i] + bias[i % N])
+__global__ void bias_act_kernel(float* __restrict__ a, int total, int N,
+                                const float* __restrict__ bias) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) a[i] = fmaxf(a[i] + bias[i % N], 0.0f);
 }
 
 // Softmax cross-entropy over out[:, 0:5] and masked squared error of
@@ -408,13 +606,17 @@ cudaError_t forward(pd_net* net, const float* x, int n, cudaStream_t s) {
                   BiasAct{net->h1, C1, w + OB1, true}, s)))
         return e;
     // conv2: [n*25, 288] x W2^T -> h2
-    if ((e = gemm(n * NPOS, C2, 9 * C1, Im2col{net->h1, C1}, ColMajor{w + OW2, 9 * C1},
-                  BiasAct{net->h2, C2, w + OB2, true}, s)))
-        return e;
-    // fc: [n, 800] x W3^T -> h3
+    conv2_mma_kernel<false><<<std::max(1, std::min(2 * 152, (n + WG_HB - 1) / WG_HB)), 256, 0, s>>>(
+        net->h1, w + OW2, w + OB2, n, net->h2);
+    if ((e = cudaGetLastError())) return e;
+    // fc: [n, 800] x W3^T -> h3, split over K (8 slices summed atomically),
+    // then the bias and ReLU
+    if ((e = cudaMemsetAsync(net->h3, 0, (size_t)n * NH * sizeof(float), s))) return e;
     if ((e = gemm(n, NH, NPOS * C2, RowMajor{net->h2, NPOS * C2}, ColMajor{w + OW3, NPOS * C2},
-                  BiasAct{net->h3, NH, w + OB3, true}, s)))
+                  AtomicAcc{net->h3, NH}, s, 8)))
         return e;
+    bias_act_kernel<<<(n * NH + 255) / 256, 256, 0, s>>>(net->h3, n * NH, NH, w + OB3);
+    if ((e = cudaGetLastError())) return e;
     // heads: [n, 64] x W4^T -> out
     return gemm(n, NOUT, NH, RowMajor{net->h3, NH}, ColMajor{w + OW4, NH},
                 BiasAct{net->out, NOUT, w + OB4, false}, s);
@@ -430,10 +632,8 @@ cudaError_t backward(pd_net* net, const float* x, int n, const uint8_t* counts, 
     loss_kernel<<<(n + 255) / 256, 256, 0, s>>>(net->out, counts, tgt, mask, n,
                                                 std::max(1.0f, nreg), lam, net->dout, loss);
     if ((e = cudaGetLastError())) return e;
-    // split-K of the weight gradients (K = hits, or hits x 25 positions for
-    // the convolutions): enough CTAs to fill the GPU, about 1024 rows each
+    // split-K of the fully connected layers' weight gradients (K = hits)
     const int sp = std::max(1, std::min(64, n * NPOS / 4096));
-    const int sp_conv = std::max(1, std::min(512, n * NPOS / 1024));
     // heads
     if ((e = gemm(NOUT, NH, n, ColMajor{net->dout, NOUT}, RowMajor{net->h3, NH},
                   AtomicAcc{gw + OW4, NH}, s, sp)))
@@ -451,17 +651,31 @@ cudaError_t backward(pd_net* net, const float* x, int n, const uint8_t* counts, 
                   ReluGrad{net->dz2, net->h2, NPOS * C2}, s)))
         return e;
     // conv2: weights, bias, input
-    if ((e = gemm(C2, 9 * C1, n * NPOS, ColMajor{net->dz2, C2}, Im2col{net->h1, C1},
-                  AtomicAcc{gw + OW2, 9 * C1}, s, sp_conv)))
-        return e;
+    {
+        const int smem = (C2 + C1) * WG_LD * 2;
+        static int attr_dev = -1;  // the shared-memory opt-in, once per device
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (attr_dev != dev) {
+            if ((e = cudaFuncSetAttribute(conv2_wgrad_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+                return e;
+            attr_dev = dev;
+        }
+        const int grid = std::max(1, std::min(2 * 152, (n + WG_HB - 1) / WG_HB));
+        conv2_wgrad_kernel<<<grid, 288, smem, s>>>(net->dz2, net->h1, n, gw + OW2);
+        if ((e = cudaGetLastError())) return e;
+    }
     colsum(net->dz2, n * NPOS, C2, gw + OB2, s);
-    if ((e = gemm(n * NPOS, C1, 9 * C2, ConvTransposeA{net->dz2}, ConvTransposeB{w + OW2},
-                  ReluGrad{net->dz1, net->h1, C1}, s)))
-        return e;
+    conv2_mma_kernel<true><<<std::max(1, std::min(2 * 152, (n + WG_HB - 1) / WG_HB)), 256, 0, s>>>(
+        net->dz2, w + OW2, net->h1, n, net->dz1);
+    if ((e = cudaGetLastError())) return e;
     // conv1: weights, bias
-    if ((e = gemm(C1, 9, n * NPOS, ColMajor{net->dz1, C1}, Im2col{x, 1}, AtomicAcc{gw + OW1, 9},
-                  s, sp_conv)))
-        return e;
+    {
+        const int grid = std::max(1, std::min(2 * 152, (n + WG_HB - 1) / WG_HB));
+        conv1_wgrad_kernel<<<grid, 288, 0, s>>>(net->dz1, x, n, gw + OW1);
+        if ((e = cudaGetLastError())) return e;
+    }
     colsum(net->dz1, n * NPOS, C1, gw + OB1, s);
     return cudaGetLastError();
 }
