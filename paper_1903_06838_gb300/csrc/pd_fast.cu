@@ -376,6 +376,8 @@ __device__ __forceinline__ bool warp_find_rank(const uint32_t* hist, uint32_t k,
 }
 
 // Common mode of unit `item` by one whole warp (lane = lane index).
+// PER: pixels per lane the unit can hold (PER * 32 >= unit_px; a multiple of 4).
+template <int PER = kRowPerLane>
 __device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ raw,
                              float* __restrict__ cm_out, unsigned long long item,
                              float magic_1, RowWarpShared& S) {
@@ -403,14 +405,14 @@ __device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ 
     // d of this lane's pixels: pixel i of the unit = lane + 32 * j, or for
     // aligned single-row units 4 consecutive pixels per load (chunk
     // lane + 32 * (j / 4), pixel 4 * chunk + j % 4)
-    float d[kRowPerLane];
-    uint32_t code[kRowPerLane];
+    float d[PER];
+    uint32_t code[PER];
     const bool vec4 = p.unit_rows == 1 && npx % 4 == 0 && c0 % 4 == 0 && p.cols % 4 == 0;
     if (vec4) {
         const uint16_t* rrow = fr + r0 * p.cols + c0;
         const float* prow = npm + r0 * p.cols + c0;
 #pragma unroll
-        for (int jc = 0; jc < kRowPerLane / 4; jc++) {
+        for (int jc = 0; jc < PER / 4; jc++) {
             const uint32_t ch = lane + 32 * jc;
             uint2 rw = make_uint2(0, 0);
             float4 pp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -437,7 +439,7 @@ __device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ 
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < kRowPerLane; j++) {
+        for (int j = 0; j < PER; j++) {
             const uint32_t i = lane + 32 * j;
             d[j] = 0.0f;
             code[j] = 256;
@@ -471,9 +473,9 @@ __device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ 
     if (bin != 0) {
         // level 2: sub-bins of the winning 1-ADU bin [lo, lo + 1)
         const float lo = __fadd_rn(p.cm_cut, (float)((int)bin - 256));
-        uint32_t sb[kRowPerLane];
+        uint32_t sb[PER];
 #pragma unroll
-        for (int j = 0; j < kRowPerLane; j++) {
+        for (int j = 0; j < PER; j++) {
             sb[j] = 64;
             if (code[j] == bin) {
                 const float x = __fmul_rn(__fsub_rn(d[j], lo), 64.0f);
@@ -486,7 +488,7 @@ __device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ 
         warp_find_rank<2>(S.sub, kb, lane, &sbin, &ks);
         // level 3: values of the winning sub-bin, ranked by counting
 #pragma unroll
-        for (int j = 0; j < kRowPerLane; j++)
+        for (int j = 0; j < PER; j++)
             if (sb[j] == sbin) {
                 const uint32_t slot = atomicAdd(&S.n_few, 1u);
                 if (slot < 64) S.few[slot] = d[j];
@@ -515,7 +517,7 @@ __device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ 
         for (int i = lane; i < 256; i += 32) S.hist[i] = 0;
         __syncwarp();
 #pragma unroll
-        for (int j = 0; j < kRowPerLane; j++) {
+        for (int j = 0; j < PER; j++) {
             if (code[j] >= 256) continue;  // outside the unit or d >= cut
             const uint32_t key = order_key(d[j]);
             if (pass > 0 && (key >> (shift + 8)) != prefix) continue;
@@ -531,6 +533,7 @@ __device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ 
     if (lane == 0) cm_out[item] = key_value(prefix);
 }
 
+template <int PER>
 __global__ void __launch_bounds__(32 * kRowWarps)
     cm_rows_kernel(ChainParams p, const uint16_t* __restrict__ raw, float* __restrict__ cm_out,
                    unsigned long long n_items, float magic_1) {
@@ -538,7 +541,7 @@ __global__ void __launch_bounds__(32 * kRowWarps)
     const int w = threadIdx.x >> 5;
     const unsigned long long item = (unsigned long long)blockIdx.x * kRowWarps + w;
     if (item >= n_items) return;  // whole warps only; no block-level barrier follows
-    cm_rows_unit(p, raw, cm_out, item, magic_1, ws[w]);
+    cm_rows_unit<PER>(p, raw, cm_out, item, magic_1, ws[w]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1066,7 +1069,12 @@ cudaError_t launch_cm_rows(const ChainParams& p, const uint16_t* raw, uint32_t n
     // floor(d - (cut - 256)) by a rounded-down fma with a magic addend
     const float magic_1 = cm_rows_magic(p);
     const unsigned long long blocks = (items + kRowWarps - 1) / kRowWarps;
-    cm_rows_kernel<<<(unsigned)blocks, 32 * kRowWarps, 0, stream>>>(p, raw, cm, items, magic_1);
+    // units of up to 384 pixels (ASIC rows) hold 12 pixels a lane
+    if (p.unit_px <= 384)
+        cm_rows_kernel<12><<<(unsigned)blocks, 32 * kRowWarps, 0, stream>>>(p, raw, cm, items, magic_1);
+    else
+        cm_rows_kernel<kRowPerLane><<<(unsigned)blocks, 32 * kRowWarps, 0, stream>>>(p, raw, cm, items,
+                                                                                  magic_1);
     return cudaGetLastError();
 }
 
