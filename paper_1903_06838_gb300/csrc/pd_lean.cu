@@ -538,6 +538,33 @@ struct LeanSmem {
     uint64_t* stage_bar;
 };
 
+// A thread's fixed part in every tile: its four-pixel chunk (column col of
+// chunk column cx), its row lane ty, the common-mode units of its chunk, and
+// the seed threshold's histogram bin; computed once per kernel.
+struct LeanLane {
+    uint32_t cx, ty;
+    int col;
+    uint32_t uca, ucb;  // units of the chunk's first and last pixel
+    int split;          // pixels i >= split take unit ucb
+    int seed_bin;       // every e > seed_thr has a bin >= seed_bin
+    int n_own_full;     // own rows of a full band
+};
+
+__device__ __forceinline__ LeanLane lean_lane(const ChainParams& p, const LeanConfig& lc) {
+    LeanLane L;
+    const uint32_t tid = threadIdx.x;
+    L.cx = tid % lc.tx;
+    L.ty = tid / lc.tx;
+    L.col = 4 * (int)L.cx;
+    L.uca = (uint32_t)L.col / p.unit_cols;
+    L.ucb = (uint32_t)(L.col + 3) / p.unit_cols;
+    L.split = (int)(L.ucb * p.unit_cols) - L.col;
+    L.seed_bin = (int)summary_bin(p.seed_thr, p.hist_inv_w, p.hist_neg_lo_s,
+                                  (int)(kMagicBits + p.hist_bins - 1));
+    L.n_own_full = lc.rb > L.ty ? ((int)lc.rb - 1 - (int)L.ty) / (int)lc.ty + 1 : 0;
+    return L;
+}
+
 // One tile (band `band` of module m of frame f, list counter `par`).  The
 // tile's pad columns must be zero and list_n[par] zero on entry.  Threads
 // with rowlane false own no rows (blocks larger than tx * ty).
@@ -546,9 +573,10 @@ struct LeanSmem {
 template <bool COLBANK, bool CORR, bool STAGE, class NextFn>
 __device__ __forceinline__ bool lean_tile(const ChainParams& p, const uint16_t* __restrict__ raw,
                                           uint32_t frame_base, const CallOut& out,
-                                          const LeanConfig& lc, const LeanSmem& sm, uint32_t f,
-                                          uint32_t m, uint32_t band, uint32_t par, bool rowlane,
-                                          uint32_t* __restrict__ err, NextFn issue_next) {
+                                          const LeanConfig& lc, const LeanSmem& sm,
+                                          const LeanLane& L, uint32_t f, uint32_t m, uint32_t band,
+                                          uint32_t par, bool rowlane, uint32_t* __restrict__ err,
+                                          NextFn issue_next) {
     const uint32_t P = lc.pitch, RB = lc.rb;
     const uint16_t* stg = sm.stg;
     float* tile = sm.tile;
@@ -559,23 +587,20 @@ __device__ __forceinline__ bool lean_tile(const ChainParams& p, const uint16_t* 
     uint32_t* list_n = sm.list_n;
     uint64_t* stage_bar = sm.stage_bar;
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
-    const uint32_t TX = lc.tx, TY = lc.ty;
-    const uint32_t cx = tid % TX, ty = tid / TX;
+    const uint32_t TY = lc.ty;
+    const uint32_t ty = L.ty;
     const int R = (int)p.rows, C = (int)p.cols;
-    const int col = 4 * (int)cx;
-    const uint32_t uca = (uint32_t)col / p.unit_cols;
-    const uint32_t ucb = (uint32_t)(col + 3) / p.unit_cols;
-    const int split = (int)(ucb * p.unit_cols) - col;  // pixels i >= split take unit ucb
+    const int col = L.col;
+    const uint32_t uca = L.uca, ucb = L.ucb;
+    const int split = L.split;
     const int last_bin = (int)p.hist_bins - 1;
     const float2 iw2 = make_float2(p.hist_inv_w, p.hist_inv_w);
     const float2 nl2 = make_float2(p.hist_neg_lo_s, p.hist_neg_lo_s);
     const float2 mg2 = make_float2(kMagic, kMagic);
-    // every pixel with e > seed_thr has a histogram bin >= seed_bin (the bin
-    // is monotone in e); rows holding such a bin are scanned for candidates
-    const int seed_bin = (int)summary_bin(p.seed_thr, p.hist_inv_w, p.hist_neg_lo_s,
-                                          (int)(kMagicBits + p.hist_bins - 1));
+    // rows holding a histogram bin >= seed_bin are scanned for candidates
+    const int seed_bin = L.seed_bin;
     const uint32_t T = STAGE ? lc.stage_t : 1u;
-    const int n_own_full = RB > ty ? ((int)RB - 1 - (int)ty) / (int)TY + 1 : 0;
+    const int n_own_full = L.n_own_full;
     {
         const int r0 = (int)band * (int)RB;
         const int rows_here = min((int)RB, R - r0);
@@ -889,12 +914,13 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
     if (tid < 2) list_n[tid] = 0;
     __syncthreads();
 
+    const LeanLane lane = lean_lane(p, lc);
     const unsigned long long first = blockIdx.x, step = gridDim.x;
     TileWalk walk(first, step, lc.n_bands, p.n_modules);
     uint32_t par = 0;
     for (unsigned long long t = first; t < n_tiles; t += step, walk.next(), par ^= 1u) {
         const bool ok = lean_tile<COLBANK, CORR, STAGE>(
-            p, raw, frame_base, out, lc, sm, walk.f, walk.m, walk.band, par, true, err, [&] {
+            p, raw, frame_base, out, lc, sm, lane, walk.f, walk.m, walk.band, par, true, err, [&] {
                 if (STAGE && t + step < n_tiles) {
                     fence_async_smem();  // order the generic reads of the stage before the copy
                     issue(t + step);
@@ -985,6 +1011,7 @@ __global__ void __launch_bounds__(kBankThreads, 2)
     ts.list_n = list_n;
     ts.stage_bar = nullptr;
     const bool rowlane = tid < lc.tx * lc.ty;
+    const LeanLane lane = lean_lane(p, lc);
 
     // thread 0 decodes a claimed index for the block (kind 2: past the end)
     auto publish = [&](uint32_t i) {
@@ -1081,7 +1108,7 @@ __global__ void __launch_bounds__(kBankThreads, 2)
                 if (!ok) atomicOr(err, 4u);
             }
             if (__syncthreads_or(!ok)) return;
-            lean_tile<true, false, false>(p, raw, frame_base, out, lc, ts, f, m, band, par,
+            lean_tile<true, false, false>(p, raw, frame_base, out, lc, ts, lane, f, m, band, par,
                                           rowlane, err, [] {});
             par ^= 1u;
             prev = 1;

@@ -64,12 +64,15 @@ def test_forward_full_size_sampled_against_oracle():
     assert np.isfinite(got).all()
 
 
-def test_gradients_match_float64_oracle():
+# 1024 hits: one 8-hit tile per CTA of the convolution kernels; 3001: CTAs
+# loop over several tiles and the last tile holds one hit
+@pytest.mark.parametrize("n_hits", [1024, 3001])
+def test_gradients_match_float64_oracle(n_hits):
     rng = np.random.default_rng(2)
     P, flat = _params(3)
-    net = pd.pd_net_create(2048, seed=0)
+    net = pd.pd_net_create(4096, seed=0)
     pd.pd_net_set_params(net, flat)
-    x, counts, tgt, mask = _random_batch(rng, 1024)
+    x, counts, tgt, mask = _random_batch(rng, n_hits)
     dev = [torch.from_numpy(a).cuda() for a in (x, counts, tgt, mask)]
     grads = torch.zeros(pd.pd_net_num_params(), dtype=torch.float32, device="cuda")
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
