@@ -294,8 +294,20 @@ int pd_get_summary(pd_ctx* ctx, uint32_t* count_map_host,
                    uint64_t* hist_pix_host, uint64_t* hist_hit_host,
                    void* stream);
 
-/* pd_reset_summary — zero the count map and histograms (async on stream). */
+/* pd_reset_summary — zero the count map and histograms (async on stream),
+ * and clear the context's record of a timed-out device wait. */
 int pd_reset_summary(pd_ctx* ctx, void* stream);
+
+/* Bounded device waits.  The kernels that wait on a staged copy (the bank
+ * median, the staged stencil) or on another CTA's result (the work-queue
+ * launch) poll a bounded number of times; when a wait gives up, the kernel
+ * waits out its copies in flight with the default bound, stops, and the
+ * context records it: pd_get_summary then returns PD_ETIMEDOUT (results of
+ * that call are not valid) until pd_reset_summary.  polls sets the bound of
+ * the first wait (0: the kernels' defaults, about 2^20 polls of a copy and
+ * 2^22 of a dependency); a small bound makes the timeout path run, which is
+ * what it is for (tests).  Launches already queued keep their bound. */
+int pd_set_wait_limit(pd_ctx* ctx, uint32_t polls);
 
 /* pd_destroy — free the context's device state (NULL is a no-op).  Waits
  * for the device to finish work that may use it. */

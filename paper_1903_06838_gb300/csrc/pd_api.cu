@@ -59,6 +59,7 @@ struct pd_ctx {
     uint32_t* d_qsync = nullptr;  // its queue counter and per-(frame, module) counts
     size_t qsync_cap = 0;         // words
     uint32_t* d_err = nullptr;  // bit 0: a bounded wait for staged copies gave up
+    uint32_t wait_polls = 0;    // polls of a bounded device wait (0: the kernels' default)
     uint32_t two_pass = 1;      // 1: common-mode and stencil kernels (measured
                                 // faster on GB300 so far); 0: the one-kernel chain
     bool multigain = false;     // auto-ranging words (pd_create_multigain)
@@ -247,8 +248,11 @@ cudaError_t launch_stencil_for(const pd_ctx* c, const uint16_t* fr, uint32_t nf,
     const pd::MultiGain* mg = c->multigain ? &c->mg : nullptr;
     if (c->matched)
         return pd::launch_matched(c->params, c->d_bank, fr, nf, frame_base, co, s, mg);
-    if (c->use_lean && c->kernels == 1)
-        return pd::launch_stencil_lean(c->params, c->lean_cfg, fr, nf, frame_base, co, c->d_err, s);
+    if (c->use_lean && c->kernels == 1) {
+        pd::LeanConfig lc = c->lean_cfg;
+        lc.wait_polls = c->wait_polls;
+        return pd::launch_stencil_lean(c->params, lc, fr, nf, frame_base, co, c->d_err, s);
+    }
     return c->use_band
                ? pd::launch_stencil_band(c->params, c->band_cfg, fr, nf, frame_base, co, s, mg)
                : pd::launch_stencil(c->params, fr, nf, frame_base, co, s, mg);
@@ -263,8 +267,11 @@ cudaError_t launch_cm(const pd_ctx* c, const uint16_t* fr, uint32_t nf, float* c
         return c->use_cm_big ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, cm, s,
                                                  ~c->mg.vmask & 0xFFFFu)
                              : pd::launch_cm_select(c->params, fr, nf, cm, s, &c->mg);
-    if (c->use_bank && c->kernels == 1)
-        return pd::launch_cm_bank(c->params, c->cm_cfg, c->cmap, fr, nf, cm, c->d_err, s);
+    if (c->use_bank && c->kernels == 1) {
+        pd::CodeMap cmap = c->cmap;
+        cmap.wait_polls = c->wait_polls;
+        return pd::launch_cm_bank(c->params, c->cm_cfg, cmap, fr, nf, cm, c->d_err, s);
+    }
     return c->use_cm_big    ? pd::launch_cm_big(c->params, c->cm_cfg, fr, nf, cm, s)
            : c->use_cm_rows ? pd::launch_cm_rows(c->params, fr, nf, cm, s)
                             : pd::launch_cm_select(c->params, fr, nf, cm, s);
@@ -331,8 +338,11 @@ int run_chain(pd_ctx* c, const uint16_t* frames, uint32_t n_frames, uint32_t fra
         if (rc) return rc;
         pd::CallOut co{out->hits, out->hit_capacity, out->n_hits, nullptr, cm};
         ProfileScope ps(c, 3, s);
-        e = pd::launch_chain_queue(c->params, c->cm_cfg, c->cmap, c->lean_cfg, frames, n_frames,
-                                   frame_base, co, c->d_qsync, c->d_err, s);
+        pd::CodeMap cmap = c->cmap;
+        pd::LeanConfig lc = c->lean_cfg;
+        cmap.wait_polls = lc.wait_polls = c->wait_polls;
+        e = pd::launch_chain_queue(c->params, c->cm_cfg, cmap, lc, frames, n_frames, frame_base, co,
+                                   c->d_qsync, c->d_err, s);
         return e == cudaSuccess ? PD_OK : fail_cuda(e, "queue kernel launch");
     }
     // Frames go in chunks sized so raw stays resident in L2 between the
@@ -837,8 +847,15 @@ int pd_reset_summary(pd_ctx* c, void* stream) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(c->d_count_map, 0, (size_t)c->params.frame_px * 4, s)) ||
         (e = cudaMemsetAsync(c->d_hist_pix, 0, (size_t)c->params.hist_bins * 8, s)) ||
-        (e = cudaMemsetAsync(c->d_hist_hit, 0, (size_t)c->params.hist_bins * 8, s)))
+        (e = cudaMemsetAsync(c->d_hist_hit, 0, (size_t)c->params.hist_bins * 8, s)) ||
+        (e = cudaMemsetAsync(c->d_err, 0, 4, s)))
         return fail_cuda(e, "summary reset");
+    return PD_OK;
+}
+
+int pd_set_wait_limit(pd_ctx* c, uint32_t polls) {
+    if (!c) return fail(PD_EINVAL, "NULL context");
+    c->wait_polls = polls;
     return PD_OK;
 }
 

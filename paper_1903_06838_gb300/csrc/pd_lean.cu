@@ -72,9 +72,10 @@ __device__ __forceinline__ void fence_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 // bounded wait for phase `parity` of the mbarrier; false when it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          uint32_t limit = kCopyWaitLimit) {
     const uint32_t a = saddr(bar);
-    for (uint32_t it = 0; it < kCopyWaitLimit; it++) {
+    for (uint32_t it = 0; it < limit; it++) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -312,7 +313,8 @@ __device__ __forceinline__ bool cm_bank_item(const ChainParams& p, float* __rest
         uint4 k2 = tid + 2 * kBankThreads < ne ? __ldg(km + tid + 2 * kBankThreads) : zero4;
         // one thread waits for the copies; the others wait at the barrier
         // (which orders the copied data before their reads)
-        const bool ok = tid != 0 || mbar_wait(&sh.bar, parity);
+        const bool ok = tid != 0 ||
+                        mbar_wait(&sh.bar, parity, cmap.wait_polls ? cmap.wait_polls : kCopyWaitLimit);
         if (__syncthreads_or(!ok)) {
             // the copies did not complete in time: report, give them a second
             // bounded wait (they write this CTA's shared memory), stop
@@ -623,7 +625,8 @@ __device__ __forceinline__ bool lean_tile(const ChainParams& p, const uint16_t* 
         if (STAGE) {
             // one thread waits for the copy; the barrier orders its data
             // before every thread's reads
-            const bool ok = tid != 0 || mbar_wait(stage_bar, par);
+            const bool ok = tid != 0 ||
+                            mbar_wait(stage_bar, par, lc.wait_polls ? lc.wait_polls : kCopyWaitLimit);
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) {
                     atomicOr(err, 2u);
@@ -1101,10 +1104,10 @@ __global__ void __launch_bounds__(kBankThreads, 2)
             bool ok = true;
             if (tid == 0) {
                 const uint32_t* d = done + f * p.n_modules + m;
+                const uint32_t limit = lc.wait_polls ? lc.wait_polls : kDepWaitLimit;
                 uint32_t it = 0;
-                while (ld_acquire_gpu(d) < p.units_per_module && ++it < kDepWaitLimit)
-                    __nanosleep(64);
-                ok = it < kDepWaitLimit;
+                while (ld_acquire_gpu(d) < p.units_per_module && ++it < limit) __nanosleep(64);
+                ok = it < limit;
                 if (!ok) atomicOr(err, 4u);
             }
             if (__syncthreads_or(!ok)) return;

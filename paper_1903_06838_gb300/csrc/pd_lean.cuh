@@ -37,6 +37,7 @@ struct CodeMap {
     uint32_t bp;        // periods per box
     uint32_t ne_box;    // groups per staged box (bp * w8 rounded up to 8)
     uint32_t ctas_per_sm;  // persistent CTAs per SM of a launch
+    uint32_t wait_polls;   // polls of a copy's mbarrier before giving up (0: default)
 };
 
 // Host side: the map of a geometry and pedestal (out->kmap left null), or
@@ -69,6 +70,7 @@ struct LeanConfig {
     // groups per period); the next tile's copy is in flight while a tile's
     // seeds are tested
     uint32_t stage_t, stage_g, stage_bp;
+    uint32_t wait_polls;  // polls of a staged copy or a tile's dependency (0: default)
     bool ok;
 };
 

@@ -236,6 +236,7 @@ def _declare(lib):
         "pd_net_destroy": ([vp], None),
         "pd_get_tuning": ([vp, ctypes.POINTER(PdTuning)], i32),
         "pd_set_tuning": ([vp, ctypes.POINTER(PdTuning)], i32),
+        "pd_set_wait_limit": ([vp, u32], i32),
         "pd_read_profile": ([vp, ctypes.POINTER(PdProfile)], i32),
         "pd_strerror": ([i32], ctypes.c_char_p),
         "pd_last_error": ([], ctypes.c_char_p),
@@ -462,6 +463,11 @@ def pd_get_tuning(ctx: Context) -> dict:
     _check(load().pd_get_tuning(ctx.handle, ctypes.byref(t)), "pd_get_tuning")
     return dict(chunk_frames=t.chunk_frames, band_rows=t.band_rows,
                 overlap=t.overlap, two_pass=t.two_pass, kernels=t.kernels)
+
+
+def pd_set_wait_limit(ctx: Context, polls: int) -> None:
+    """Polls of a bounded device wait before it gives up (0: the default)."""
+    _check(load().pd_set_wait_limit(ctx.handle, polls), "pd_set_wait_limit")
 
 
 def pd_set_tuning(ctx: Context, chunk_frames=0, band_rows=0, overlap=None,
