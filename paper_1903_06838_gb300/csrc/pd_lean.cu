@@ -1364,6 +1364,8 @@ LeanConfig make_lean_config(const ChainParams& p, uint32_t rb) {
     // On the 2.2 Mpx sensor the stage would cut the band from 47 to 31 rows,
     // and the shorter bands' per-tile costs outweigh the faster rows
     // (measured 117.7 k against 122.1 k frames/s), so it stays off there.
+    // (nor a CTA per SM: a band that fits two CTAs per SM unstaged keeps them)
+    const size_t stage_limit = lean_smem_bytes(p, lc) <= kLeanSmemTwo ? kLeanSmemTwo : limit;
     for (uint32_t t = 1; t <= 8 && lc.ok; t *= 2)
         if ((t * p.cols) % 8 == 0) {
             if (t * p.cols / 8 <= 256 && (p.frame_px / p.cols) % t == 0 && p.frame_px % 8 == 0 &&
@@ -1371,7 +1373,7 @@ LeanConfig make_lean_config(const ChainParams& p, uint32_t rb) {
                 lc.stage_t = t;
                 lc.stage_g = t * p.cols / 8;
                 set_stage_periods(lc);
-                if (!staged(lc) || lean_smem_bytes(p, lc) > limit) lc.stage_t = 0;
+                if (!staged(lc) || lean_smem_bytes(p, lc) > stage_limit) lc.stage_t = 0;
             }
             break;
         }
