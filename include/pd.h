@@ -493,7 +493,8 @@ typedef struct {
     uint64_t device_budget;     /* bytes of slot buffers; 0 = free device  *
                                  * memory at creation less 1 GiB            */
     uint32_t keep_hits;         /* 1: keep each frame's hits and stream    */
-    uint32_t encode_threads;    /* host encoder threads; 0 = min(8, cores/2) */
+    uint32_t encode_threads;    /* host encoder threads; 0 = min(8, cores/2);
+                                 * they run at nice +5, below the dispatcher */
     uint32_t max_uploading;     /* batches still uploading frames at most;  *
                                  * 0 = 1 (admission holds frames in the    *
                                  * ring while the link is this busy)       */

@@ -18,6 +18,7 @@
 #include <math.h>
 #include <pthread.h>
 #include <sched.h>
+#include <sys/resource.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -463,6 +464,10 @@ void encode_task(pd_server* sv, Job& job, uint32_t first, uint32_t last) {
 }
 
 void encoder_loop(pd_server* sv) {
+    // encoding is off the latency path (a batch's slot frees before its
+    // frames are encoded): on busy host cores the dispatcher and the
+    // producer come first (Linux nice values are per thread)
+    setpriority(PRIO_PROCESS, 0, 5);
     while (true) {
         Task t;
         {
