@@ -1212,10 +1212,15 @@ int pd_batch_capture(pd_batch* b, const pd_batch_item* items, uint32_t n_items, 
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
     }
-    // the table is sized before the capture (no allocation while capturing)
+    // the table and the contexts' queue scratch are sized before the capture
+    // (no allocation while capturing)
     int rc0 = batch_check_items(b, items, n_items);
     if (rc0) return rc0;
     if ((rc0 = ensure_table(b, 1, plan_entries(plan_chunks(items, n_items))))) return rc0;
+    for (uint32_t i = 0; i < n_items; i++)
+        if (queue_on(items[i].ctx, &items[i].out) &&
+            (rc0 = ensure_qsync(items[i].ctx, items[i].n_frames)))
+            return rc0;
     if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)))
         return fail_cuda(e, "begin capture");
     int rc = batch_enqueue(b, 1, items, n_items, s);

@@ -85,10 +85,16 @@ def test_batch_equals_single_context_processing_and_oracle(mixed):
     _check(ctxs, outs, ref)
 
 
-@pytest.mark.parametrize("mixed", [False, True])
-def test_batch_graph_replays_on_new_frame_contents(mixed):
+@pytest.mark.parametrize("mixed,kernels", [(False, 0), (True, 0), (False, 3)],
+                         ids=["per_item", "mixed", "per_item_work_queue"])
+def test_batch_graph_replays_on_new_frame_contents(mixed, kernels):
     data = _setup()
     ctxs = _ctxs(data)
+    if kernels:
+        # the CSPAD-like context runs the work-queue launch inside the graph
+        for c in ctxs:
+            pd.pd_set_tuning(c, kernels=kernels)
+        assert pd.pd_get_tuning(ctxs[1])["kernels"] == kernels
     devs = [pd.frames_to_device(raw) for *_, raw in data]
     outs = _outputs(ctxs, data)
     batch = pd.pd_batch_create(8)
