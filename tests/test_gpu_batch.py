@@ -25,9 +25,15 @@ MIX = [synth.epix_704x768(rows=96, occupancy=0.001, occupancy_hi=0.1, seed=21),
 FRAMES = [5, 4, 6]
 
 
-def _setup():
+# the same with four CSPAD-like sensors: frames of a whole number of 16-byte
+# groups, so the bank median's tensor copies and the work-queue launch apply
+MIX_BANK = [MIX[0], synth.cspad_2p2m(n_modules=4, occupancy=0.001, occupancy_hi=0.1, seed=22),
+            MIX[2]]
+
+
+def _setup(mix=MIX):
     data = []
-    for det, n in zip(MIX, FRAMES):
+    for det, n in zip(mix, FRAMES):
         ped, gain = synth.maps(det)
         raw, _ = synth.frames(det, ped, gain, 0, n)
         data.append((det, ped, gain, raw))
@@ -88,7 +94,7 @@ def test_batch_equals_single_context_processing_and_oracle(mixed):
 @pytest.mark.parametrize("mixed,kernels", [(False, 0), (True, 0), (False, 3)],
                          ids=["per_item", "mixed", "per_item_work_queue"])
 def test_batch_graph_replays_on_new_frame_contents(mixed, kernels):
-    data = _setup()
+    data = _setup(MIX_BANK if kernels == 3 else MIX)
     ctxs = _ctxs(data)
     if kernels:
         # the CSPAD-like context runs the work-queue launch inside the graph
