@@ -211,7 +211,7 @@ __global__ void colsum_kernel(const float* __restrict__ a, int M, int N, int row
 
 void colsum(const float* a, int M, int N, float* out, cudaStream_t s) {
     if (M <= 0) return;
-    const int rows = 512;
+    const int rows = 64;  // short dependent-load chains per thread
     colsum_kernel<<<(M + rows - 1) / rows, 256, 0, s>>>(a, M, N, rows, out);
 }
 
