@@ -632,8 +632,10 @@ cudaError_t backward(pd_net* net, const float* x, int n, const uint8_t* counts, 
     loss_kernel<<<(n + 255) / 256, 256, 0, s>>>(net->out, counts, tgt, mask, n,
                                                 std::max(1.0f, nreg), lam, net->dout, loss);
     if ((e = cudaGetLastError())) return e;
-    // split-K of the fully connected layers' weight gradients (K = hits)
-    const int sp = std::max(1, std::min(64, n * NPOS / 4096));
+    // split-K of the fully connected layers' weight gradients (K = hits):
+    // slices of about 64 hits, so each CTA runs two k-steps (these GEMMs
+    // are small and bound by their load latency, not by the atomics)
+    const int sp = std::max(1, std::min(64, n / 64));
     // heads
     if ((e = gemm(NOUT, NH, n, ColMajor{net->dout, NOUT}, RowMajor{net->h3, NH},
                   AtomicAcc{gw + OW4, NH}, s, sp)))
