@@ -228,7 +228,9 @@ constexpr int WG_HB = 8;                        // hits per staged chunk
 constexpr int WG_ROWS = WG_HB * 49;             // 392 padded positions
 constexpr int WG_K = (WG_ROWS + 15) / 16 * 16;  // 400: whole k-steps
 constexpr int WG_PAD = 8;                       // zero rows before and after (offsets -8..8)
-constexpr int WG_LD = WG_PAD + WG_K + WG_PAD;   // 416 bf16 per channel row
+constexpr int WG_ROW = WG_PAD + WG_K + WG_PAD;  // 416 bf16 of padded rows
+constexpr int WG_LD = WG_ROW + 2;  // channel row pitch: 209 words (odd), so the 32
+                                   // channels of one position land in 32 banks
 
 // conv2: one warp per tap (9 warps), a 32 x 32 block of c_out x c_in each,
 // on mma.sync m16n8k16; CTAs stride over chunks of WG_HB hits and add their
@@ -342,6 +344,10 @@ __global__ void __launch_bounds__(288) conv1_wgrad_kernel(const float* __restric
     if (tid < C1 * 9) atomicAdd(&gw[co * 9 + tap], acc);
 }
 
+constexpr int C2_AP = 40;       // bf16 per input row in shared memory (32 used)
+constexpr int C2_WS = 9 * 32 + 8;  // bf16 per weight row (288 used)
+constexpr int C2_SMEM = (WG_ROW * C2_AP + 32 * C2_WS) * 2;
+
 // conv2 forward (h2 = relu(conv(h1) + b2)) and the gradient of its input
 // (dz1 = conv_transpose(dz2) where h1 > 0) on mma.sync m16n8k16: for tap k
 // the input rows are the padded rows shifted by +off(k) (forward) or -off(k)
@@ -353,8 +359,12 @@ __global__ void __launch_bounds__(256) conv2_mma_kernel(const float* __restrict_
                                                         const float* __restrict__ w2,
                                                         const float* __restrict__ aux, int n,
                                                         float* __restrict__ out) {
-    __shared__ __align__(16) uint16_t ap[WG_LD][32];    // input, padded rows
-    __shared__ __align__(16) uint16_t ws[32][9 * 32];   // [n][tap * 32 + k channel]
+    // input [padded row][channel] and weights [n][tap * 32 + k channel], rows
+    // padded to 20 and 148 words so the fragment loads of 8 rows x 4 column
+    // pairs fall in 32 distinct banks
+    extern __shared__ __align__(16) uint16_t cm_smem[];
+    uint16_t (*ap)[C2_AP] = reinterpret_cast<uint16_t (*)[C2_AP]>(cm_smem);
+    uint16_t (*ws)[C2_WS] = reinterpret_cast<uint16_t (*)[C2_WS]>(cm_smem + WG_ROW * C2_AP);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, tq = lane & 3;
     // weights: forward ws[c_out][tap][c_in] = W2; transpose ws[c_in][tap][c_out]
@@ -362,7 +372,8 @@ __global__ void __launch_bounds__(256) conv2_mma_kernel(const float* __restrict_
         const int a = e / (9 * 32), rest = e - a * (9 * 32), tap = rest / 32, b = rest % 32;
         ws[a][rest] = bf16_bits(DGRAD ? w2[(size_t)b * (9 * C1) + tap * C1 + a] : w2[e]);
     }
-    for (int i = tid; i < WG_LD * 32 / 2; i += blockDim.x) reinterpret_cast<uint32_t*>(ap)[i] = 0u;
+    for (int i = tid; i < WG_ROW * C2_AP / 2; i += blockDim.x)
+        reinterpret_cast<uint32_t*>(cm_smem)[i] = 0u;
     for (int h0 = blockIdx.x * WG_HB; h0 < n; h0 += gridDim.x * WG_HB) {
         __syncthreads();  // the previous chunk is read
         const int nh = min(WG_HB, n - h0);
@@ -422,6 +433,23 @@ __global__ void __launch_bounds__(256) conv2_mma_kernel(const float* __restrict_
             }
         }
     }
+}
+
+template <bool DGRAD>
+cudaError_t launch_conv2_mma(const float* in, const float* w2, const float* aux, int n, float* out,
+                             cudaStream_t s) {
+    static int attr_dev = -1;  // the shared-memory opt-in, once per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(conv2_mma_kernel<DGRAD>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C2_SMEM);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    const int grid = std::max(1, std::min(2 * 152, (n + WG_HB - 1) / WG_HB));
+    conv2_mma_kernel<DGRAD><<<grid, 256, C2_SMEM, s>>>(in, w2, aux, n, out);
+    return cudaGetLastError();
 }
 
 // a[i] = relu(a[i] + bias[i % N])
@@ -606,9 +634,7 @@ cudaError_t forward(pd_net* net, const float* x, int n, cudaStream_t s) {
                   BiasAct{net->h1, C1, w + OB1, true}, s)))
         return e;
     // conv2: [n*25, 288] x W2^T -> h2
-    conv2_mma_kernel<false><<<std::max(1, std::min(2 * 152, (n + WG_HB - 1) / WG_HB)), 256, 0, s>>>(
-        net->h1, w + OW2, w + OB2, n, net->h2);
-    if ((e = cudaGetLastError())) return e;
+    if ((e = launch_conv2_mma<false>(net->h1, w + OW2, w + OB2, n, net->h2, s))) return e;
     // fc: [n, 800] x W3^T -> h3, split over K (8 slices summed atomically),
     // then the bias and ReLU
     if ((e = cudaMemsetAsync(net->h3, 0, (size_t)n * NH * sizeof(float), s))) return e;
@@ -669,9 +695,7 @@ cudaError_t backward(pd_net* net, const float* x, int n, const uint8_t* counts, 
         if ((e = cudaGetLastError())) return e;
     }
     colsum(net->dz2, n * NPOS, C2, gw + OB2, s);
-    conv2_mma_kernel<true><<<std::max(1, std::min(2 * 152, (n + WG_HB - 1) / WG_HB)), 256, 0, s>>>(
-        net->dz2, w + OW2, net->h1, n, net->dz1);
-    if ((e = cudaGetLastError())) return e;
+    if ((e = launch_conv2_mma<true>(net->dz2, w + OW2, net->h1, n, net->dz1, s))) return e;
     // conv1: weights, bias
     {
         const int grid = std::max(1, std::min(2 * 152, (n + WG_HB - 1) / WG_HB));
