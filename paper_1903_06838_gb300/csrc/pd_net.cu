@@ -356,7 +356,7 @@ constexpr int C2_SMEM = (WG_ROW * C2_AP + 32 * C2_WS) * 2;
 // the 16-row tiles w, w + 8, ... of the 400 padded rows, all 32 outputs.
 template <bool DGRAD>
 __global__ void __launch_bounds__(256) conv2_mma_kernel(const float* __restrict__ in,
-                                                        const float* __restrict__ w2,
+                                                        const uint4* __restrict__ w2img,
                                                         const float* __restrict__ aux, int n,
                                                         float* __restrict__ out) {
     // input [padded row][channel] and weights [n][tap * 32 + k channel], rows
@@ -367,10 +367,10 @@ __global__ void __launch_bounds__(256) conv2_mma_kernel(const float* __restrict_
     uint16_t (*ws)[C2_WS] = reinterpret_cast<uint16_t (*)[C2_WS]>(cm_smem + WG_ROW * C2_AP);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, tq = lane & 3;
-    // weights: forward ws[c_out][tap][c_in] = W2; transpose ws[c_in][tap][c_out]
-    for (int e = tid; e < 32 * 9 * 32; e += blockDim.x) {
-        const int a = e / (9 * 32), rest = e - a * (9 * 32), tap = rest / 32, b = rest % 32;
-        ws[a][rest] = bf16_bits(DGRAD ? w2[(size_t)b * (9 * C1) + tap * C1 + a] : w2[e]);
+    // weights, bf16 in this kernel's layout (w2_image_kernel), 16 bytes a load
+    for (int e = tid; e < 32 * 9 * 32 / 8; e += blockDim.x) {
+        const int a = e / (9 * 32 / 8), q = e - a * (9 * 32 / 8);
+        *reinterpret_cast<uint4*>(&ws[a][8 * q]) = w2img[e];
     }
     for (int i = tid; i < WG_ROW * C2_AP / 2; i += blockDim.x)
         reinterpret_cast<uint32_t*>(cm_smem)[i] = 0u;
@@ -435,9 +435,19 @@ __global__ void __launch_bounds__(256) conv2_mma_kernel(const float* __restrict_
     }
 }
 
+// bf16 images of W2 for conv2_mma_kernel: [0, 9216) the forward layout
+// [c_out][tap][c_in] (W2's own), [9216, 18432) the transpose [c_in][tap][c_out].
+__global__ void w2_image_kernel(const float* __restrict__ w2, uint16_t* __restrict__ img) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 32 * 9 * 32) return;
+    img[e] = bf16_bits(w2[e]);
+    const int a = e / (9 * 32), rest = e - a * (9 * 32), tap = rest / 32, b = rest % 32;
+    img[32 * 9 * 32 + e] = bf16_bits(w2[(size_t)b * (9 * C1) + tap * C1 + a]);
+}
+
 template <bool DGRAD>
-cudaError_t launch_conv2_mma(const float* in, const float* w2, const float* aux, int n, float* out,
-                             cudaStream_t s) {
+cudaError_t launch_conv2_mma(const float* in, const uint16_t* w2img, const float* aux, int n,
+                             float* out, cudaStream_t s) {
     static int attr_dev = -1;  // the shared-memory opt-in, once per device
     int dev = 0;
     cudaGetDevice(&dev);
@@ -448,7 +458,8 @@ cudaError_t launch_conv2_mma(const float* in, const float* w2, const float* aux,
         attr_dev = dev;
     }
     const int grid = std::max(1, std::min(2 * 152, (n + WG_HB - 1) / WG_HB));
-    conv2_mma_kernel<DGRAD><<<grid, 256, C2_SMEM, s>>>(in, w2, aux, n, out);
+    conv2_mma_kernel<DGRAD><<<grid, 256, C2_SMEM, s>>>(in, reinterpret_cast<const uint4*>(w2img),
+                                                        aux, n, out);
     return cudaGetLastError();
 }
 
@@ -609,6 +620,7 @@ struct pd_net {
     // tensor-core inference: bf16 weight image, bf16 h2, timeout flag
     uint8_t* tc_img = nullptr;
     uint16_t* tc_h2 = nullptr;
+    uint16_t* w2img = nullptr;  // bf16 W2, forward and transposed (training)
     int* tc_err = nullptr;
 };
 
@@ -621,6 +633,7 @@ void free_net(pd_net* n) {
         cudaFree(p);
     cudaFree(n->tc_img);
     cudaFree(n->tc_h2);
+    cudaFree(n->w2img);
     cudaFree(n->tc_err);
     delete n;
 }
@@ -634,7 +647,9 @@ cudaError_t forward(pd_net* net, const float* x, int n, cudaStream_t s) {
                   BiasAct{net->h1, C1, w + OB1, true}, s)))
         return e;
     // conv2: [n*25, 288] x W2^T -> h2
-    if ((e = launch_conv2_mma<false>(net->h1, w + OW2, w + OB2, n, net->h2, s))) return e;
+    w2_image_kernel<<<(32 * 9 * 32 + 255) / 256, 256, 0, s>>>(w + OW2, net->w2img);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = launch_conv2_mma<false>(net->h1, net->w2img, w + OB2, n, net->h2, s))) return e;
     // fc: [n, 800] x W3^T -> h3, split over K (8 slices summed atomically),
     // then the bias and ReLU
     if ((e = cudaMemsetAsync(net->h3, 0, (size_t)n * NH * sizeof(float), s))) return e;
@@ -695,7 +710,9 @@ cudaError_t backward(pd_net* net, const float* x, int n, const uint8_t* counts, 
         if ((e = cudaGetLastError())) return e;
     }
     colsum(net->dz2, n * NPOS, C2, gw + OB2, s);
-    if ((e = launch_conv2_mma<true>(net->dz2, w + OW2, net->h1, n, net->dz1, s))) return e;
+    // (W2's images were built by the forward pass of the same step)
+    if ((e = launch_conv2_mma<true>(net->dz2, net->w2img + 32 * 9 * 32, net->h1, n, net->dz1, s)))
+        return e;
     // conv1: weights, bias
     {
         const int grid = std::max(1, std::min(2 * 152, (n + WG_HB - 1) / WG_HB));
@@ -732,6 +749,7 @@ int pd_net_create(uint32_t max_batch, uint64_t seed, pd_net** out) {
     if (cudaMalloc(&n->tc_img, pd::nettc::weight_image_bytes()) != cudaSuccess ||
         cudaMalloc(&n->tc_h2, pd::nettc::h2_bytes(max_batch)) != cudaSuccess ||
         cudaMalloc(&n->tc_err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&n->w2img, 2 * 32 * 9 * 32 * sizeof(uint16_t)) != cudaSuccess ||
         cudaMemset(n->tc_err, 0, sizeof(int)) != cudaSuccess) {
         free_net(n);
         return net_fail(PD_ENOMEM, "pd_net_create: device allocation failed");
