@@ -54,6 +54,28 @@ struct TileWalk {
     }
 };
 
+// Bulk prefetch into L2 of the whole 16-byte units inside [a, b) (global
+// addresses; nothing outside the range is touched, nothing to wait for).
+__device__ __forceinline__ void prefetch_l2_range(const void* a, const void* b) {
+    const uint64_t s = ((uint64_t)a + 15ull) & ~15ull, e = (uint64_t)b & ~15ull;
+    if (e > s)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((uint32_t)(e - s))
+                     : "memory");
+}
+
+// The raw rows of a band stencil's tile asked of L2: band w.band (rb rows)
+// of module w.m of frame w.f, with the halo row above and `below` halo rows
+// below where the module has them; mod_rows x cols words per module,
+// frame_px per frame.
+__device__ __forceinline__ void prefetch_tile_rows(const uint16_t* raw, const TileWalk& w,
+                                                   uint32_t rb, uint32_t mod_rows, uint32_t cols,
+                                                   size_t frame_px, int below = 1) {
+    const int r0 = (int)(w.band * rb);
+    const int ra = max(r0 - 1, 0), re = min(r0 + (int)rb + below, (int)mod_rows);
+    const uint16_t* mod = raw + (size_t)w.f * frame_px + (size_t)w.m * mod_rows * cols;
+    prefetch_l2_range(mod + (size_t)ra * cols, mod + (size_t)re * cols);
+}
+
 // Histogram bin of the summaries: floor(fma(v, inv_w, -lo_s)) clipped to
 // [0, bins-1], as the code of an element of a 32-bit histogram array.
 __device__ __forceinline__ uint32_t summary_bin(float v, float inv_w, float neg_lo_s,

@@ -556,8 +556,11 @@ struct BandShared {
 // n_modules).  Zeroes this CTA's shared tile and histograms first and adds
 // the histograms to the context's at the end.  STACKED: the stacked mean
 // common mode, whose module-row and module-column terms follow the units'
-// values of each frame and are subtracted after the unit's.
-template <int VEC, bool STACKED = false, bool MG = false>
+// values of each frame and are subtracted after the unit's.  PREFETCH: the
+// raw rows of later tiles are asked of L2 ahead of their loads (the
+// single-context kernel; the batched one keeps its registers for the items'
+// parameters).
+template <int VEC, bool STACKED = false, bool MG = false, bool PREFETCH = false>
 __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restrict__ raw,
                                  uint32_t frame_base, const CallOut& out, const BandConfig& bc,
                                  unsigned long long first, unsigned long long n_tiles,
@@ -617,6 +620,15 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
     if (first < n_tiles && tid < ncmt) cmv = tile_cm((uint32_t)first, tid);
 
     TileWalk walk(first, step, bc.n_bands, p.n_modules);
+    // the last thread asks L2 for the raw rows (halo rows included) of the
+    // next tile now and of the tile after next once a tile is done, so that
+    // their loads find them there
+    const bool prefetcher = PREFETCH && tid == nthr - 1;
+    if (prefetcher && first + step < n_tiles) {
+        TileWalk nx = walk;
+        nx.next();
+        prefetch_tile_rows(raw, nx, bc.rb, p.rows, p.cols, p.frame_px);
+    }
     for (unsigned long long t = first; t < n_tiles; t += step, walk.next()) {
         const int band = (int)walk.band;
         const uint32_t m = walk.m, f = walk.f;
@@ -902,6 +914,12 @@ __device__ void stencil_band_run(const ChainParams& p, const uint16_t* __restric
             }
         }
         __syncthreads();
+        if (prefetcher && t + 2 * step < n_tiles) {
+            TileWalk nx = walk;
+            nx.next();
+            nx.next();
+            prefetch_tile_rows(raw, nx, bc.rb, p.rows, p.cols, p.frame_px);
+        }
     }
     for (uint32_t b = tid; b < p.hist_bins; b += nthr) {
         if (hpix[b]) atomicAdd(&p.hist_pix[b], (unsigned long long)hpix[b]);
@@ -916,8 +934,8 @@ __global__ void __launch_bounds__(kBandThreads, 2)
                         unsigned long long n_tiles, MultiGain mg) {
     extern __shared__ __align__(16) uint32_t band_smem[];
     __shared__ BandShared bsh;
-    stencil_band_run<VEC, STACKED, MG>(p, raw, frame_base, out, bc, blockIdx.x, n_tiles, gridDim.x,
-                                       band_smem, bsh, mg);
+    stencil_band_run<VEC, STACKED, MG, true>(p, raw, frame_base, out, bc, blockIdx.x, n_tiles,
+                                             gridDim.x, band_smem, bsh, mg);
 }
 
 // ---------------------------------------------------------------------------

@@ -88,15 +88,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
     return false;
 }
 
-// Bulk prefetch into L2 of the whole 16-byte units inside [a, b) (global
-// addresses; nothing outside the range is touched, nothing to wait for).
-__device__ __forceinline__ void prefetch_l2_range(const void* a, const void* b) {
-    const uint64_t s = ((uint64_t)a + 15ull) & ~15ull, e = (uint64_t)b & ~15ull;
-    if (e > s)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((uint32_t)(e - s))
-                     : "memory");
-}
-
 // 16-bit SIMD min / max of two lanes per word (sm_90 and later)
 __device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
     uint32_t d;
@@ -934,10 +925,7 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
     // once a tile is done, so that their loads find them there
     const bool prefetcher = !STAGE && tid == nthr - 1;
     auto prefetch = [&](const TileWalk& w) {
-        const int r0 = (int)(w.band * RB);
-        const int ra = max(r0 - 1, 0), rb = min(r0 + (int)RB + 1, (int)p.rows);
-        const uint16_t* mod = raw + (size_t)w.f * p.frame_px + (size_t)w.m * p.module_px;
-        prefetch_l2_range(mod + (size_t)ra * p.cols, mod + (size_t)rb * p.cols);
+        prefetch_tile_rows(raw, w, RB, p.rows, p.cols, p.frame_px);
     };
     if (prefetcher && first + step < n_tiles) {
         TileWalk nx = walk;

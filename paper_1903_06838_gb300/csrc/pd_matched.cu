@@ -429,6 +429,16 @@ __global__ void __launch_bounds__(kBandThreads, 2)
     if (blockIdx.x < n_tiles && tid < ncmt) cmv = tile_cm(blockIdx.x, tid);
 
     TileWalk walk(blockIdx.x, gridDim.x, bc.n_bands, p.n_modules);
+    // the last thread asks L2 for the raw rows (the halo row above, two
+    // below) of the next tile now and of the tile after next once a tile is
+    // done, so that their loads find them there
+    const unsigned long long step = gridDim.x;
+    const bool prefetcher = tid == nthr - 1;
+    if (prefetcher && blockIdx.x + step < n_tiles) {
+        TileWalk nx = walk;
+        nx.next();
+        prefetch_tile_rows(raw, nx, bc.rb, p.rows, p.cols, p.frame_px, 2);
+    }
     for (unsigned long long t = blockIdx.x; t < n_tiles; t += gridDim.x, walk.next()) {
         const int band = (int)walk.band;
         const uint32_t m = walk.m, f = walk.f;
@@ -689,6 +699,12 @@ __global__ void __launch_bounds__(kBandThreads, 2)
             }
         }
         __syncthreads();
+        if (prefetcher && t + 2 * step < n_tiles) {
+            TileWalk nx = walk;
+            nx.next();
+            nx.next();
+            prefetch_tile_rows(raw, nx, bc.rb, p.rows, p.cols, p.frame_px, 2);
+        }
     }
     for (uint32_t b = tid; b < p.hist_bins; b += nthr) {
         if (hpix[b]) atomicAdd(&p.hist_pix[b], (unsigned long long)hpix[b]);
