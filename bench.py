@@ -37,8 +37,8 @@ HIT_BYTES = 24
 # back on one 64-frame chunk, caches not flushed between kernels, so the
 # stencil's re-read of raw is counted where it misses L2); set an entry to
 # None when its kernel changes until it is captured again.
-NCU_TRAFFIC_PER_FRAME = {"stencil": (317.185536e6 + 51.442432e6) / 64,
-                         "common_mode": (302.498304e6 + 3.33312e6) / 64,
+NCU_TRAFFIC_PER_FRAME = {"stencil": (323.414528e6 + 54.440704e6) / 64,
+                         "common_mode": (302.125568e6 + 3.40608e6) / 64,
                          "fused_chain": None, "chain_queue": None}
 
 
