@@ -385,7 +385,10 @@ def run_pd(args):
 
     # end to end through the host-buffer entry point (pinned host frames)
     if not args.no_e2e:
-        hits_host = np.empty(cap, pd.HIT_DTYPE)
+        # the hit list lands in page-locked memory too, so its download can
+        # run while later chunks upload
+        hits_host = torch.empty(cap * pd.HIT_DTYPE.itemsize, dtype=torch.uint8,
+                                pin_memory=True).numpy().view(pd.HIT_DTYPE)
         pd.pd_process_host(ctx, raw, 0, out=hits_host)
         torch.cuda.synchronize(dev)
         e_steps = max(1, min(args.steps, 5))
@@ -400,7 +403,8 @@ def run_pd(args):
             dt = float(t.item())
         line["e2e"] = {"value": round(nf * ws / dt, 1), "unit": "frames/s",
                        "h2d_bytes_per_step": raw_b, "d2h_bytes_per_step": nh * HIT_BYTES + 4,
-                       "api": "pd_process_host (page-locked host frames, hits back to host)"}
+                       "api": "pd_process_host (page-locked host frames, hits back to page-locked "
+                              "host memory)"}
     if rank == 0 and ws == 1 and not args.no_cm_variants:
         line["cm_variants"] = cm_variants_run(args, dev, det, ped, gain, frames, nf, peak)
     serve_summary = None

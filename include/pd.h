@@ -276,10 +276,12 @@ int pd_process_noalloc(pd_ctx* ctx, const uint16_t* frames_dev, uint32_t n_frame
 int pd_set_filter_bank(pd_ctx* ctx, const pd_filter_bank* bank);
 
 /* pd_process_host — the same chain on host-resident frames.  Copies the
- * frames to the device in chunks (pipelined on two internal streams, so
- * page-locked host memory gives full link speed), processes them, and
- * copies the hit list and its count back.  Synchronous: returns after the
- * hits are in hits_host.  Returns PD_EOVERFLOW if more than hit_capacity
+ * frames to the device in chunks of about 64 MB (pipelined on internal
+ * streams, so page-locked host memory gives full link speed), processes
+ * them, and copies the hit list and its count back: the hits of a chunk are
+ * downloaded two chunks later, while later chunks upload (a page-locked
+ * hits_host lets that download run asynchronously).  Synchronous: returns
+ * after all hits are in hits_host.  Returns PD_EOVERFLOW if more than hit_capacity
  * hits occurred (*n_hits_host is then the true count, hits_host holds the
  * first hit_capacity records in unspecified order). */
 int pd_process_host(pd_ctx* ctx, const uint16_t* frames_host,

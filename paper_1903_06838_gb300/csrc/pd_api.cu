@@ -36,6 +36,11 @@ int fail_cuda(cudaError_t e, const char* what) {
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
+// pd_process_host: chunks between a chunk's processing and the download of
+// its hits (the host waits for chunk k - kHitLag's count while chunks up to k
+// are queued, so the device never runs dry)
+constexpr uint32_t kHitLag = 2;
+
 }  // namespace
 
 struct pd_ctx {
@@ -92,8 +97,11 @@ struct pd_ctx {
     pd_hit* d_host_hits = nullptr;
     uint32_t host_hit_cap = 0;
     uint32_t* d_host_nhits = nullptr;
-    cudaStream_t hstream[2] = {nullptr, nullptr};
+    cudaStream_t hstream[3] = {nullptr, nullptr, nullptr};  // process, upload, hit download
     cudaEvent_t hevent[4] = {nullptr, nullptr, nullptr, nullptr};
+    // hit counts after each chunk, read back to page-locked slots
+    uint32_t* h_counts = nullptr;
+    cudaEvent_t hcount_ev[kHitLag + 1] = {};
     // kernel timing (pd_set_profiling)
     bool profiling = false;
     struct Mark { int kernel; cudaEvent_t a, b; };
@@ -219,10 +227,13 @@ void free_ctx(pd_ctx* c) {
     cudaFree(c->d_stage[1]);
     cudaFree(c->d_host_hits);
     cudaFree(c->d_host_nhits);
-    for (int i = 0; i < 2; i++)
+    for (int i = 0; i < 3; i++)
         if (c->hstream[i]) cudaStreamDestroy(c->hstream[i]);
     for (int i = 0; i < 4; i++)
         if (c->hevent[i]) cudaEventDestroy(c->hevent[i]);
+    for (uint32_t i = 0; i <= kHitLag; i++)
+        if (c->hcount_ev[i]) cudaEventDestroy(c->hcount_ev[i]);
+    if (c->h_counts) cudaFreeHost(c->h_counts);
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     for (int i = 0; i < 2; i++) {
@@ -716,7 +727,7 @@ int pd_process_host(pd_ctx* c, const uint16_t* frames_host, uint32_t n_frames,
                 return fail(PD_ENOMEM, "staging allocation failed");
         c->stage_frames = chunk;
     }
-    for (int i = 0; i < 2; i++)
+    for (int i = 0; i < 3; i++)
         if (!c->hstream[i] &&
             (e = cudaStreamCreateWithFlags(&c->hstream[i], cudaStreamNonBlocking)))
             return fail_cuda(e, "stream create");
@@ -724,6 +735,14 @@ int pd_process_host(pd_ctx* c, const uint16_t* frames_host, uint32_t n_frames,
         if (!c->hevent[i] &&
             (e = cudaEventCreateWithFlags(&c->hevent[i], cudaEventDisableTiming)))
             return fail_cuda(e, "event create");
+    for (uint32_t i = 0; i <= kHitLag; i++)
+        if (!c->hcount_ev[i] &&
+            (e = cudaEventCreateWithFlags(&c->hcount_ev[i], cudaEventDisableTiming)))
+            return fail_cuda(e, "event create");
+    if (!c->h_counts &&
+        (e = cudaHostAlloc(reinterpret_cast<void**>(&c->h_counts), (kHitLag + 1) * sizeof(uint32_t),
+                           cudaHostAllocDefault)))
+        return fail_cuda(e, "page-locked count slots");
     const uint32_t cap = std::max<uint32_t>(hit_capacity, 1);
     if (c->host_hit_cap < cap) {
         cudaDeviceSynchronize();
@@ -743,8 +762,22 @@ int pd_process_host(pd_ctx* c, const uint16_t* frames_host, uint32_t n_frames,
     // staging buffer k%2.  copy(k) waits for process(k-2) (same buffer),
     // process(k) waits for copy(k), so the upload of chunk k+1 overlaps the
     // processing of chunk k.  One device counter spans all chunks, so the
-    // hit list is contiguous and read back once at the end.
-    cudaStream_t s0 = c->hstream[0], s1 = c->hstream[1];
+    // hit list is contiguous.  After each chunk the counter is copied to a
+    // page-locked slot; once chunk k is queued the host waits for chunk
+    // k - kHitLag's count and downloads the hits added up to it on
+    // hstream[2], so the hit list comes back during the uploads (the link
+    // carries both directions at once) instead of after the last chunk.
+    cudaStream_t s0 = c->hstream[0], s1 = c->hstream[1], s2 = c->hstream[2];
+    uint32_t downloaded = 0;
+    auto download_upto = [&](uint32_t count) -> cudaError_t {
+        const uint32_t upto = std::min(count, hit_capacity);
+        if (upto <= downloaded) return cudaSuccess;
+        const cudaError_t de =
+            cudaMemcpyAsync(hits_host + downloaded, c->d_host_hits + downloaded,
+                            (size_t)(upto - downloaded) * sizeof(pd_hit), cudaMemcpyDeviceToHost, s2);
+        downloaded = upto;
+        return de;
+    };
     if ((e = cudaMemsetAsync(c->d_host_nhits, 0, sizeof(uint32_t), s0)))
         return fail_cuda(e, "zero counter");
     cudaEvent_t copied[2] = {c->hevent[0], c->hevent[1]};
@@ -766,17 +799,28 @@ int pd_process_host(pd_ctx* c, const uint16_t* frames_host, uint32_t n_frames,
         rc = run_chain(c, c->d_stage[b], nf, frame_base + done, &o, s0, /*zero=*/false);
         if (rc) return rc;
         cudaEventRecord(processed[b], s0);
+        const uint32_t slot = k % (kHitLag + 1);
+        if ((e = cudaMemcpyAsync(c->h_counts + slot, c->d_host_nhits, 4, cudaMemcpyDeviceToHost,
+                                 s0)) ||
+            (e = cudaEventRecord(c->hcount_ev[slot], s0)))
+            return fail_cuda(e, "hit count readback");
+        if (k >= kHitLag) {
+            // chunk j = k - kHitLag is done once its count has arrived; its
+            // slot is next written by chunk k + 1, queued after this read
+            const uint32_t js = (k - kHitLag) % (kHitLag + 1);
+            if ((e = cudaEventSynchronize(c->hcount_ev[js])) ||
+                (e = download_upto(c->h_counts[js])))
+                return fail_cuda(e, "hit download");
+        }
         done += nf;
         k++;
     }
     uint32_t total = 0;
-    if ((e = cudaMemcpyAsync(&total, c->d_host_nhits, 4, cudaMemcpyDeviceToHost, s0)) ||
+    if ((e = cudaMemcpyAsync(c->h_counts, c->d_host_nhits, 4, cudaMemcpyDeviceToHost, s0)) ||
         (e = cudaStreamSynchronize(s0)))
         return fail_cuda(e, "hit count readback");
-    const uint32_t keep = std::min(total, hit_capacity);
-    if (keep && ((e = cudaMemcpyAsync(hits_host, c->d_host_hits, (size_t)keep * sizeof(pd_hit),
-                                      cudaMemcpyDeviceToHost, s0)) ||
-                 (e = cudaStreamSynchronize(s0))))
+    total = c->h_counts[0];
+    if ((e = download_upto(total)) || (e = cudaStreamSynchronize(s2)))
         return fail_cuda(e, "hit download");
     if ((e = cudaStreamSynchronize(s1))) return fail_cuda(e, "host path synchronise");
     *n_hits_host = total;

@@ -316,6 +316,37 @@ def test_host_buffer_entry_point():
     assert len(small) == 10 and n2 > 10
 
 
+@pytest.mark.parametrize("pinned", [False, True], ids=["pageable_hits", "page_locked_hits"])
+def test_host_path_hits_downloaded_during_uploads(pinned):
+    """Five 64 MB chunks of 2.2 Mpx frames: the hits that come back chunk by
+    chunk while later chunks upload are exactly the device path's, and a
+    capacity that ends inside one chunk's download returns that many distinct
+    records of the full list with the true count."""
+    det = synth.cspad_2p2m(occupancy=0.01)
+    ped, gain = synth.maps(det)
+    n = 70  # 14 frames per chunk
+    raw, _ = synth.frames(det, ped, gain, 0, n, truth=False)
+    geom, thr = det.geometry(), det.thresholds()
+    dev_ctx = _ctx(geom, thr, ped, gain)
+    out = pd.process(dev_ctx, pd.frames_to_device(raw), hit_capacity=n * 65536)
+    torch.cuda.synchronize()
+    ref, n_ref = out.hits_host()
+    assert n_ref == len(ref) > 0
+    ctx = _ctx(geom, thr, ped, gain)
+    cap = n * 65536
+    buf = (torch.empty(cap * pd.HIT_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True).numpy()
+           if pinned else np.empty(cap * pd.HIT_DTYPE.itemsize, np.uint8)).view(pd.HIT_DTYPE)
+    hits, nh = pd.pd_process_host(ctx, raw, out=buf)
+    assert nh == n_ref == len(hits)
+    assert sort_hits(hits).tobytes() == sort_hits(ref).tobytes()
+    part = n_ref // 3 + 7
+    some, n2 = pd.pd_process_host(ctx, raw, hit_capacity=part)
+    assert n2 == n_ref and len(some) == part
+    keys = set(zip(ref["frame"].tolist(), ref["pixel"].tolist()))
+    got = list(zip(some["frame"].tolist(), some["pixel"].tolist()))
+    assert len(set(got)) == part and set(got) <= keys
+
+
 def test_invalid_arguments_rejected():
     det = synth.asic_352x384(rows=16)
     ped, gain = synth.maps(det)
