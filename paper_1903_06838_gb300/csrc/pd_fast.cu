@@ -315,12 +315,15 @@ __global__ void __launch_bounds__(512, 2)
 // ---------------------------------------------------------------------------
 // Common mode of small units (at most kRowMaxPx pixels, e.g. 384-pixel ASIC
 // rows): one warp per unit, every pixel of the unit in the lanes' registers.
-// Level 1: 256 bins of 1 ADU over [cut - 256, cut) in warp-private shared
-// memory (d < cut - 256 in bin 0; d >= cut in the spare bin 256), a warp scan
-// finds the bin of rank floor((n-1)/2).  Level 2: the bin's values into 64
-// sub-bins of 1/64 ADU (RN(d - lo) is monotone in d), scan again.  Level 3:
-// the few values of that sub-bin, ranked by counting.  A median in bin 0
-// (open below) goes to a warp-level 4-pass radix select over the unit.
+// Level 1: 256 bins of 1 ADU from w0 = min(cut - 256, -128) in warp-private
+// shared memory (d < w0 in bin 0, d in [w0 + 255, cut) in bin 255, d >= cut
+// in the spare bin 256), a warp scan finds the bin of rank floor((n-1)/2).
+// The window stays around zero, where dark-subtracted values and their
+// median lie, also when the cut is far above 128 ADU.  Level 2: the bin's
+// values into 64 sub-bins of 1/64 ADU (RN(d - lo) is monotone in d), scan
+// again.  Level 3: the few values of that sub-bin, ranked by counting.  A
+// median in bin 0 (open below) or in an open bin 255 goes to a warp-level
+// 4-pass radix select over the unit.
 constexpr int kRowMaxPx = 512;      // pixels per unit handled by one warp
 constexpr int kRowPerLane = kRowMaxPx / 32;
 constexpr int kRowWarps = 8;        // units per CTA
@@ -431,8 +434,8 @@ __device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ 
                 if (4 * ch < npx) {
                     d[j] = dv[q];
                     int b = __float_as_int(__fmaf_rd(d[j], 1.0f, magic_1));
-                    b = min(max(b, (int)kMagicBits), (int)(kMagicBits + 256));
-                    code[j] = (uint32_t)b - kMagicBits;
+                    b = min(max(b, (int)kMagicBits), (int)(kMagicBits + 255));
+                    code[j] = d[j] < p.cm_cut ? (uint32_t)b - kMagicBits : 256u;
                     atomicAdd(&S.hist[code[j]], 1u);
                 }
             }
@@ -449,8 +452,8 @@ __device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ 
                                          : (r0 + i / p.unit_cols) * p.cols + c0 + i % p.unit_cols;
                 d[j] = __fadd_rn(__uint2float_rn(fr[off]), npm[off]);
                 int b = __float_as_int(__fmaf_rd(d[j], 1.0f, magic_1));
-                b = min(max(b, (int)kMagicBits), (int)(kMagicBits + 256));
-                code[j] = (uint32_t)b - kMagicBits;
+                b = min(max(b, (int)kMagicBits), (int)(kMagicBits + 255));
+                code[j] = d[j] < p.cm_cut ? (uint32_t)b - kMagicBits : 256u;
                 atomicAdd(&S.hist[code[j]], 1u);
             }
         }
@@ -470,9 +473,13 @@ __device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ 
     const uint32_t k = (n - 1) / 2;
     uint32_t bin = 0, kb = 0;
     warp_find_rank<8>(S.hist, k, lane, &bin, &kb);
-    if (bin != 0) {
+    // the window's base (magic_1 = 1.5 * 2^23 - w0, both exact) and whether
+    // bin 255 is a whole 1-ADU bin (the window ends at the cut)
+    const float w0 = __fsub_rn(kMagic, magic_1);
+    const bool top_closed = __fadd_rn(w0, 256.0f) == p.cm_cut;
+    if (bin != 0 && (bin != 255 || top_closed)) {
         // level 2: sub-bins of the winning 1-ADU bin [lo, lo + 1)
-        const float lo = __fadd_rn(p.cm_cut, (float)((int)bin - 256));
+        const float lo = __fadd_rn(w0, (float)bin);
         uint32_t sb[PER];
 #pragma unroll
         for (int j = 0; j < PER; j++) {
@@ -1070,8 +1077,9 @@ cudaError_t launch_batch(const BatchItem* items_dev, uint32_t n_items,
     return cudaGetLastError();
 }
 
+// 1.5 * 2^23 - w0 for the window base w0 = min(cut - 256, -128) (an integer)
 float cm_rows_magic(const ChainParams& p) {
-    return (float)(12582912.0 - ((double)p.cm_cut - 256.0));
+    return (float)(12582912.0 - std::min((double)p.cm_cut - 256.0, -128.0));
 }
 
 bool cm_rows_supported(const ChainParams& p) {
@@ -1084,7 +1092,7 @@ cudaError_t launch_cm_rows(const ChainParams& p, const uint16_t* raw, uint32_t n
                            float* cm, cudaStream_t stream) {
     const unsigned long long items = (unsigned long long)n_frames * p.units_per_frame;
     if (items == 0) return cudaSuccess;
-    // floor(d - (cut - 256)) by a rounded-down fma with a magic addend
+    // floor(d - w0) by a rounded-down fma with a magic addend
     const float magic_1 = cm_rows_magic(p);
     const unsigned long long blocks = (items + kRowWarps - 1) / kRowWarps;
     // units of up to 384 pixels (ASIC rows) hold 12 pixels a lane

@@ -208,10 +208,30 @@ def test_bank_min_count_not_reached():
 
 
 def test_rows_median_below_window_uses_radix_fallback():
-    # row units: window [cut - 256, cut) = [-56, 200); d is about -300 ADU
+    # row units: 1-ADU bins over [-128, 128), [128, cut = 200) open bin 255;
+    # d is about -300 ADU
     det = synth.asic_352x384(rows=24)
     ref = _run_case(det, 2, ped_shift=300.0)
-    assert ref.n_hits > 0 and float(ref.cm.max()) < -56.0
+    assert ref.n_hits > 0 and float(ref.cm.max()) < -128.0
+
+
+def test_rows_median_in_open_top_bin_uses_radix_fallback():
+    # d is about +170 ADU: below the cut (200) but above the window's 1-ADU
+    # bins [-128, 128), so the median lies in the open bin [127, 200)
+    det = synth.asic_352x384(rows=24)
+    ref = _run_case(det, 2, ped_shift=-170.0)
+    assert ref.n_hits > 0 and float(ref.cm.max()) < 200.0
+    assert np.mean(ref.cm > 128.0) > 0.9
+
+
+@pytest.mark.parametrize("shift", [0.0, -97.5], ids=["median_near_zero", "median_at_the_cut"])
+def test_rows_window_closed_at_a_low_cut(shift):
+    # cut 100 ADU <= 128: the bins span [cut - 256, cut) and bin 255 is the
+    # whole 1-ADU bin [99, 100); with d about 97.5 ADU half the values lie
+    # above the cut and the median of the rest sits just below it
+    det = synth.asic_352x384(rows=24)
+    ref = _run_case(det, 2, ped_shift=shift, thr_over=dict(cm_cut_adu=100.0))
+    assert float(ref.cm.max()) < 100.0
 
 
 def test_rows_flat_frames_many_equal_values():
