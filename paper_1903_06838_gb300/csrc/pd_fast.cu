@@ -327,12 +327,13 @@ __global__ void __launch_bounds__(512, 2)
 constexpr int kRowMaxPx = 512;      // pixels per unit handled by one warp
 constexpr int kRowPerLane = kRowMaxPx / 32;
 constexpr int kRowWarps = 8;        // units per CTA
-struct RowWarpShared {
-    uint32_t hist[256 + 4];
+struct __align__(16) RowWarpShared {
+    uint32_t hist[256 + 4];  // then sub: both zeroed as one run of 16-byte words
     uint32_t sub[64];
     float few[64];
     uint32_t n_few;
 };
+static_assert(sizeof(uint32_t) * (256 + 4) % 16 == 0, "sub follows hist on a 16-byte boundary");
 
 // warp inclusive scan of one value per lane
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
@@ -344,18 +345,13 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
     return v;
 }
 
-// Locate rank k among bins hist[0..nb) (nb = 32 * per): *bin and the rank
-// within it; returns false when k >= total.
+// Locate rank k among the bins of a warp, lane l holding bins l * PER ..
+// l * PER + PER - 1 in loc with the exclusive and inclusive warp prefix of
+// their counts: *bin and the rank within it; false when k >= total.
 template <int PER>
-__device__ __forceinline__ bool warp_find_rank(const uint32_t* hist, uint32_t k, int lane,
-                                               uint32_t* bin, uint32_t* krem) {
-    uint32_t loc[PER], sum = 0;
-#pragma unroll
-    for (int j = 0; j < PER; j++) {
-        loc[j] = hist[lane * PER + j];
-        sum += loc[j];
-    }
-    const uint32_t incl = warp_incl_scan(sum, lane), excl = incl - sum;
+__device__ __forceinline__ bool warp_locate(const uint32_t (&loc)[PER], uint32_t excl,
+                                            uint32_t incl, uint32_t k, int lane, uint32_t* bin,
+                                            uint32_t* krem) {
     const bool mine = excl <= k && k < incl;
     uint32_t b = 0, r = 0;
     if (mine) {
@@ -378,6 +374,21 @@ __device__ __forceinline__ bool warp_find_rank(const uint32_t* hist, uint32_t k,
     return true;
 }
 
+// Locate rank k among bins hist[0..nb) (nb = 32 * per): *bin and the rank
+// within it; returns false when k >= total.
+template <int PER>
+__device__ __forceinline__ bool warp_find_rank(const uint32_t* hist, uint32_t k, int lane,
+                                               uint32_t* bin, uint32_t* krem) {
+    uint32_t loc[PER], sum = 0;
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        loc[j] = hist[lane * PER + j];
+        sum += loc[j];
+    }
+    const uint32_t incl = warp_incl_scan(sum, lane);
+    return warp_locate<PER>(loc, incl - sum, incl, k, lane, bin, krem);
+}
+
 // Common mode of unit `item` by one whole warp (lane = lane index).
 // PER: pixels per lane the unit can hold (PER * 32 >= unit_px; a multiple of 4).
 template <int PER = kRowPerLane>
@@ -385,23 +396,32 @@ __device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ 
                              float* __restrict__ cm_out, unsigned long long item,
                              float magic_1, RowWarpShared& S) {
     const int lane = threadIdx.x & 31;
-    const uint32_t f = (uint32_t)(item / p.units_per_frame);
-    const uint32_t u = (uint32_t)(item % p.units_per_frame);
+    // (32-bit division where the item index allows it: the 64-bit one is a
+    // long instruction sequence, paid once per 384-pixel unit)
+    uint32_t f, u;
+    if (item < (1ull << 32)) {
+        f = (uint32_t)item / p.units_per_frame;
+        u = (uint32_t)item - f * p.units_per_frame;
+    } else {
+        f = (uint32_t)(item / p.units_per_frame);
+        u = (uint32_t)(item - (unsigned long long)f * p.units_per_frame);
+    }
     if (cm_kind(p) == PD_CM_NONE) {
         if (lane == 0) cm_out[item] = 0.0f;
         return;
     }
     const uint32_t m = u / p.units_per_module;
-    const uint32_t um = u % p.units_per_module;
-    const uint32_t r0 = (um / p.units_per_row) * p.unit_rows;
-    const uint32_t c0 = (um % p.units_per_row) * p.unit_cols;
+    const uint32_t um = u - m * p.units_per_module;
+    const uint32_t ur = p.units_per_row == 1 ? um : um / p.units_per_row;
+    const uint32_t r0 = ur * p.unit_rows;
+    const uint32_t c0 = (um - ur * p.units_per_row) * p.unit_cols;
     const size_t mod_base = (size_t)m * p.module_px;
     const uint16_t* fr = raw + (size_t)f * p.frame_px + mod_base;
     const float* npm = p.nped + mod_base;
     const uint32_t npx = p.unit_px;
 
-    for (int i = lane; i < 256 + 4; i += 32) S.hist[i] = 0;
-    for (int i = lane; i < 64; i += 32) S.sub[i] = 0;
+    for (int i = lane; i < (256 + 4 + 64) / 4; i += 32)
+        reinterpret_cast<uint4*>(S.hist)[i] = make_uint4(0, 0, 0, 0);
     if (lane == 0) S.n_few = 0;
     __syncwarp();
 
@@ -459,20 +479,28 @@ __device__ void cm_rows_unit(const ChainParams& p, const uint16_t* __restrict__ 
         }
     }
     __syncwarp();
-    // n = values below the cut (every bin but the spare one)
-    uint32_t cnt = 0;
+    // the lane's eight bins (two 16-byte reads) and their warp scan: n =
+    // values below the cut (every bin but the spare one), then the bin of
+    // rank floor((n-1)/2)
+    uint32_t loc[8];
+    {
+        const uint4 lo4 = reinterpret_cast<const uint4*>(S.hist)[2 * lane];
+        const uint4 hi4 = reinterpret_cast<const uint4*>(S.hist)[2 * lane + 1];
+        loc[0] = lo4.x; loc[1] = lo4.y; loc[2] = lo4.z; loc[3] = lo4.w;
+        loc[4] = hi4.x; loc[5] = hi4.y; loc[6] = hi4.z; loc[7] = hi4.w;
+    }
+    uint32_t lsum = 0;
 #pragma unroll
-    for (int j = 0; j < 8; j++) cnt += S.hist[lane * 8 + j];
-#pragma unroll
-    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    const uint32_t n = cnt;
+    for (int j = 0; j < 8; j++) lsum += loc[j];
+    const uint32_t incl = warp_incl_scan(lsum, lane);
+    const uint32_t n = __shfl_sync(0xffffffffu, incl, 31);
     if (n == 0 || n < p.cm_min_count) {
         if (lane == 0) cm_out[item] = 0.0f;
         return;
     }
     const uint32_t k = (n - 1) / 2;
     uint32_t bin = 0, kb = 0;
-    warp_find_rank<8>(S.hist, k, lane, &bin, &kb);
+    warp_locate<8>(loc, incl - lsum, incl, k, lane, &bin, &kb);
     // the window's base (magic_1 = 1.5 * 2^23 - w0, both exact) and whether
     // bin 255 is a whole 1-ADU bin (the window ends at the cut)
     const float w0 = __fsub_rn(kMagic, magic_1);
