@@ -571,8 +571,9 @@ __device__ __forceinline__ LeanLane lean_lane(const ChainParams& p, const LeanCo
 // tile's pad columns must be zero and list_n[par] zero on entry.  Threads
 // with rowlane false own no rows (blocks larger than tx * ty).
 // issue_next() runs on thread 0 once the stage is read.  False if a staged
-// copy's wait gave up.
-template <bool COLBANK, bool CORR, bool STAGE, class NextFn>
+// copy's wait gave up.  ONEUNIT (per-row table only): every four-pixel chunk
+// lies inside one common-mode unit (unit_cols a multiple of 4).
+template <bool COLBANK, bool CORR, bool STAGE, bool ONEUNIT, class NextFn>
 __device__ __forceinline__ bool lean_tile(const ChainParams& p, const uint16_t* __restrict__ raw,
                                           uint32_t frame_base, const CallOut& out,
                                           const LeanConfig& lc, const LeanSmem& sm,
@@ -644,11 +645,14 @@ __device__ __forceinline__ bool lean_tile(const ChainParams& p, const uint16_t* 
             n01 = make_float2(split > 0 ? a : b, split > 1 ? a : b);
             n23 = make_float2(split > 2 ? a : b, split > 3 ? a : b);
         } else {
+            // (entry i: tile row i / upr, unit column i % upr; the divisions
+            // are skipped for one unit per row and for one-row units)
             const uint32_t upr = p.units_per_row;
             for (uint32_t i = tid; i < (uint32_t)(rows_here + 2) * upr; i += nthr) {
-                const int r = r0 - 1 + (int)(i / upr);
-                cmt[i] = r >= 0 && r < R ? -__ldcg(cmf + ((uint32_t)r / p.unit_rows) * upr + i % upr)
-                                          : 0.0f;
+                const uint32_t ri = upr == 1 ? i : i / upr;
+                const int r = r0 - 1 + (int)ri;
+                const uint32_t ur = p.unit_rows == 1 ? (uint32_t)r : (uint32_t)r / p.unit_rows;
+                cmt[i] = r >= 0 && r < R ? -__ldcg(cmf + ur * upr + (i - ri * upr)) : 0.0f;
             }
             __syncthreads();
         }
@@ -658,7 +662,11 @@ __device__ __forceinline__ bool lean_tile(const ChainParams& p, const uint16_t* 
             const float2 d01 = __fadd2_rn(raw_pair(x.rw.x), make_float2(x.np.x, x.np.y));
             const float2 d23 = __fadd2_rn(raw_pair(x.rw.y), make_float2(x.np.z, x.np.w));
             float2 m01 = n01, m23 = n23;
-            if (!COLBANK) {
+            if (!COLBANK && ONEUNIT) {
+                const float a = cmt[rl * p.units_per_row + uca];
+                m01 = make_float2(a, a);
+                m23 = m01;
+            } else if (!COLBANK) {
                 const float a = cmt[rl * p.units_per_row + uca];
                 const float b = cmt[rl * p.units_per_row + ucb];
                 m01 = make_float2(split > 0 ? a : b, split > 1 ? a : b);
@@ -872,7 +880,8 @@ __device__ __forceinline__ bool lean_tile(const ChainParams& p, const uint16_t* 
 // frames.  STAGE: the tile's raw rows come by one tensor copy (the frames as
 // [frame][period][group][8 words]) into shared memory; the next tile's copy
 // is issued once the rows are read and lands while the seeds are tested.
-template <bool COLBANK, bool CORR, bool STAGE>
+// ONEUNIT: as in lean_tile.
+template <bool COLBANK, bool CORR, bool STAGE, bool ONEUNIT = false>
 __global__ void __launch_bounds__(kLeanThreads, 2)
     stencil_lean_kernel(ChainParams p, const uint16_t* __restrict__ raw, uint32_t frame_base,
                         CallOut out, LeanConfig lc, unsigned long long n_tiles,
@@ -934,7 +943,7 @@ __global__ void __launch_bounds__(kLeanThreads, 2)
     }
     uint32_t par = 0;
     for (unsigned long long t = first; t < n_tiles; t += step, walk.next(), par ^= 1u) {
-        const bool ok = lean_tile<COLBANK, CORR, STAGE>(
+        const bool ok = lean_tile<COLBANK, CORR, STAGE, ONEUNIT>(
             p, raw, frame_base, out, lc, sm, lane, walk.f, walk.m, walk.band, par, true, err, [&] {
                 if (STAGE && t + step < n_tiles) {
                     fence_async_smem();  // order the generic reads of the stage before the copy
@@ -1129,7 +1138,7 @@ __global__ void __launch_bounds__(kBankThreads, 2)
                 if (!ok) atomicOr(err, 4u);
             }
             if (__syncthreads_or(!ok)) return;
-            lean_tile<true, false, false>(p, raw, frame_base, out, lc, ts, lane, f, m, band, par,
+            lean_tile<true, false, false, false>(p, raw, frame_base, out, lc, ts, lane, f, m, band, par,
                                           rowlane, err, [] {});
             par ^= 1u;
             prev = 1;
@@ -1406,6 +1415,17 @@ size_t lean_smem_bytes(const ChainParams& p, const LeanConfig& lc) {
 
 static int g_attr_dev_lean = -1;
 
+namespace {
+// the stencil instance for a common-mode layout: column banks, a per-row
+// table, or a per-row table whose chunks each lie in one unit
+template <bool CORR, bool STAGE>
+auto lean_pick(bool colbank, bool oneunit) {
+    return colbank   ? stencil_lean_kernel<true, CORR, STAGE, false>
+           : oneunit ? stencil_lean_kernel<false, CORR, STAGE, true>
+                     : stencil_lean_kernel<false, CORR, STAGE, false>;
+}
+}  // namespace
+
 cudaError_t launch_stencil_lean(const ChainParams& p, const LeanConfig& lc, const uint16_t* raw,
                                 uint32_t n_frames, uint32_t frame_base, const CallOut& out,
                                 uint32_t* err, cudaStream_t stream) {
@@ -1417,7 +1437,11 @@ cudaError_t launch_stencil_lean(const ChainParams& p, const LeanConfig& lc, cons
         for (auto k : {stencil_lean_kernel<true, false, false>, stencil_lean_kernel<true, true, false>,
                        stencil_lean_kernel<false, false, false>, stencil_lean_kernel<false, true, false>,
                        stencil_lean_kernel<true, false, true>, stencil_lean_kernel<true, true, true>,
-                       stencil_lean_kernel<false, false, true>, stencil_lean_kernel<false, true, true>}) {
+                       stencil_lean_kernel<false, false, true>, stencil_lean_kernel<false, true, true>,
+                       stencil_lean_kernel<false, false, false, true>,
+                       stencil_lean_kernel<false, true, false, true>,
+                       stencil_lean_kernel<false, false, true, true>,
+                       stencil_lean_kernel<false, true, true, true>}) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kLeanSmemMax);
             if (e == cudaSuccess)
@@ -1450,14 +1474,13 @@ cudaError_t launch_stencil_lean(const ChainParams& p, const LeanConfig& lc, cons
     unsigned long long grid = (unsigned long long)device_sm_count() * per_sm;
     if (grid > n_tiles) grid = n_tiles;
     const bool corr = out.corrected != nullptr;
-    auto k = stage ? (lc.colbank ? (corr ? stencil_lean_kernel<true, true, true>
-                                         : stencil_lean_kernel<true, false, true>)
-                                 : (corr ? stencil_lean_kernel<false, true, true>
-                                         : stencil_lean_kernel<false, false, true>))
-                   : (lc.colbank ? (corr ? stencil_lean_kernel<true, true, false>
-                                         : stencil_lean_kernel<true, false, false>)
-                                 : (corr ? stencil_lean_kernel<false, true, false>
-                                         : stencil_lean_kernel<false, false, false>));
+    // per-row tables with every four-pixel chunk inside one unit take one
+    // table read per row
+    const bool one = !lc.colbank && p.unit_cols % 4 == 0;
+    auto k = stage ? (corr ? lean_pick<true, true>(lc.colbank, one)
+                           : lean_pick<false, true>(lc.colbank, one))
+                   : (corr ? lean_pick<true, false>(lc.colbank, one)
+                           : lean_pick<false, false>(lc.colbank, one));
     k<<<(unsigned)grid, threads, smem, stream>>>(p, raw, frame_base, out, lc, n_tiles, map, err);
     return cudaGetLastError();
 }
