@@ -783,13 +783,19 @@ int pd_process_host(pd_ctx* c, const uint16_t* frames_host, uint32_t n_frames,
     cudaEvent_t copied[2] = {c->hevent[0], c->hevent[1]};
     cudaEvent_t processed[2] = {c->hevent[2], c->hevent[3]};
     uint32_t done = 0, k = 0;
+    // on a failure, the work already queued (uploads that read frames_host,
+    // downloads that write hits_host) finishes before the call returns
+    auto stop = [&](int code) -> int {
+        for (cudaStream_t q : {s0, s1, s2}) cudaStreamSynchronize(q);
+        return code;
+    };
     while (done < n_frames) {
         const uint32_t nf = std::min(chunk, n_frames - done);
         const int b = k & 1;
         if (k >= 2) cudaStreamWaitEvent(s1, processed[b], 0);
         if ((e = cudaMemcpyAsync(c->d_stage[b], frames_host + (size_t)done * c->params.frame_px,
                                  nf * fbytes, cudaMemcpyHostToDevice, s1)))
-            return fail_cuda(e, "frame upload");
+            return stop(fail_cuda(e, "frame upload"));
         cudaEventRecord(copied[b], s1);
         cudaStreamWaitEvent(s0, copied[b], 0);
         pd_outputs o{};
@@ -797,20 +803,20 @@ int pd_process_host(pd_ctx* c, const uint16_t* frames_host, uint32_t n_frames,
         o.hits = c->d_host_hits;
         o.n_hits = c->d_host_nhits;
         rc = run_chain(c, c->d_stage[b], nf, frame_base + done, &o, s0, /*zero=*/false);
-        if (rc) return rc;
+        if (rc) return stop(rc);
         cudaEventRecord(processed[b], s0);
         const uint32_t slot = k % (kHitLag + 1);
         if ((e = cudaMemcpyAsync(c->h_counts + slot, c->d_host_nhits, 4, cudaMemcpyDeviceToHost,
                                  s0)) ||
             (e = cudaEventRecord(c->hcount_ev[slot], s0)))
-            return fail_cuda(e, "hit count readback");
+            return stop(fail_cuda(e, "hit count readback"));
         if (k >= kHitLag) {
             // chunk j = k - kHitLag is done once its count has arrived; its
             // slot is next written by chunk k + 1, queued after this read
             const uint32_t js = (k - kHitLag) % (kHitLag + 1);
             if ((e = cudaEventSynchronize(c->hcount_ev[js])) ||
                 (e = download_upto(c->h_counts[js])))
-                return fail_cuda(e, "hit download");
+                return stop(fail_cuda(e, "hit download"));
         }
         done += nf;
         k++;
@@ -818,10 +824,10 @@ int pd_process_host(pd_ctx* c, const uint16_t* frames_host, uint32_t n_frames,
     uint32_t total = 0;
     if ((e = cudaMemcpyAsync(c->h_counts, c->d_host_nhits, 4, cudaMemcpyDeviceToHost, s0)) ||
         (e = cudaStreamSynchronize(s0)))
-        return fail_cuda(e, "hit count readback");
+        return stop(fail_cuda(e, "hit count readback"));
     total = c->h_counts[0];
     if ((e = download_upto(total)) || (e = cudaStreamSynchronize(s2)))
-        return fail_cuda(e, "hit download");
+        return stop(fail_cuda(e, "hit download"));
     if ((e = cudaStreamSynchronize(s1))) return fail_cuda(e, "host path synchronise");
     *n_hits_host = total;
     return total > hit_capacity ? fail(PD_EOVERFLOW, "hit capacity exceeded") : PD_OK;
