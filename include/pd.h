@@ -479,7 +479,8 @@ void pd_net_destroy(pd_net* net);
  * keeps up to n_slots batches in flight, each on its own stream: when a
  * slot frees it takes every committed frame (up to max_batch_frames per
  * geometry), uploads, runs one pd_batch launch over all geometries and
- * downloads the hit counts and then the hits.  Latency = arrival to hits on
+ * downloads the hit counts and then the hits.  A frame's ring slot is free
+ * again as soon as its upload has completed.  Latency = arrival to hits on
  * the host.  Host encoder threads then group the hits per frame, sort them
  * by pixel and encode them (pd_compress_hits format); a frame is done when
  * encoded.  Summaries accumulate in each context (running count map).

@@ -91,7 +91,7 @@ enum : int { kSlotFree = 0, kSlotRunning = 1, kSlotHits = 2, kSlotEncoding = 3 }
 struct DevSlot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_start = nullptr, ev_up = nullptr, ev_counts = nullptr, ev_hits = nullptr;
-    bool uploaded = false;            // the batch's frames are on the device
+    bool uploaded = false;            // the batch's frames are on the device (ring slots freed)
     pd_batch* batch = nullptr;
     std::vector<uint16_t*> d_frames;  // per geometry
     std::vector<pd_hit*> d_hits;
@@ -315,9 +315,22 @@ bool issue(pd_server* sv, DevSlot& s) {
     return true;
 }
 
-// After the counts are on the host: the frames are on the device, so their
-// ring slots are released; download exactly the hits.
+// Once the batch's upload has completed its frames are on the device, and
+// their ring slots go back to the producer (the batch keeps their ids and
+// arrival times); once only, so that a slot the producer has taken again is
+// never released twice.
+void frames_uploaded(pd_server* sv, DevSlot& s) {
+    if (s.uploaded) return;
+    s.uploaded = true;
+    std::lock_guard<std::mutex> lock(sv->mu);
+    for (uint32_t g = 0; g < (uint32_t)sv->rings.size(); g++)
+        for (const Pending& p : s.frames[g]) sv->rings[g].state[p.ring_slot] = kFree;
+}
+
+// After the counts are on the host (the upload before them is complete):
+// download exactly the hits.
 void fetch_hits(pd_server* sv, DevSlot& s) {
+    frames_uploaded(sv, s);
     const uint32_t cap = sv->cfg.max_batch_frames * sv->cfg.hits_per_frame;
     s.t_counts = now_ns();
     float up_ms = 0, run_ms = 0;
@@ -328,8 +341,6 @@ void fetch_hits(pd_server* sv, DevSlot& s) {
         sv->sum_upload_us += up_ms * 1e3;
         sv->sum_run_us += run_ms * 1e3;
         sv->timed_batches++;
-        for (uint32_t g = 0; g < (uint32_t)sv->rings.size(); g++)
-            for (const Pending& p : s.frames[g]) sv->rings[g].state[p.ring_slot] = kFree;
     }
     for (uint32_t g = 0; g < (uint32_t)sv->rings.size(); g++) {
         if (s.frames[g].empty()) continue;
@@ -506,7 +517,7 @@ void dispatch_loop(pd_server* sv) {
             DevSlot& s = *sp;
             if (s.state.load() == kSlotRunning && !s.uploaded) {
                 if (event_done(sv, s.ev_up))
-                    s.uploaded = true;
+                    frames_uploaded(sv, s);
                 else
                     uploading++;
             }
